@@ -1,0 +1,26 @@
+"""FP64 CPU oracle of the lattice method of arXiv:2006.15122.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py may import, call, link or execute anything in this
+package.  The CUDA library never does, and nothing here imports it: the two
+share no code, header, helper, table or constant generator.
+
+What it computes (each function cites the passage it follows):
+  core.py          ctypes front of lattice_oracle.c: scalar kernels, energies,
+                   VV2/VVn (section 4.3.2), staggered leapfrog scheme III
+                   (section 4.2.1), compact U(1) kernels, energies, Gauss law
+                   and staggered leapfrog (sections 5.3, 5.4)
+  ic.py            initial conditions of section 7
+  spectra.py       DFT convention and power spectra (sections 3.1, 4.4.2)
+  philox.py        Philox4x32-10, the counter-based generator of the draws
+
+Pins (tests/test_oracle_*.py, run with -m "not gpu") check it against closed
+forms: exact per-mode dispersion of the free lattice field, the Jacobi-
+elliptic homogeneous phi^4 solution, a high-accuracy ODE solve of the
+expanding homogeneous mode, symplectic convergence orders, reversibility,
+summation by parts, Parseval, the Gauss law to round-off, gauge invariance,
+energy conservation and Philox known-answer vectors.
+"""
+from . import core, ic, philox, spectra  # noqa: F401
+from .core import (VV2, VV4, VV6, VV8, VV10, ScalarLattice, ScalarModel, U1Lattice,  # noqa: F401
+                   U1Model)

@@ -1,0 +1,248 @@
+"""ctypes front of the oracle's C core, plus the integrator weights.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+"""
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        d = C.POINTER(C.c_double)
+        vp = C.c_void_p
+        for name, args, res in [
+            ("orc_scalar_kernel", [vp, d, C.c_double, d], None),
+            ("orc_scalar_energies", [vp, d, d, C.c_double, d], None),
+            ("orc_scalar_Ka", [vp, C.c_double, d], C.c_double),
+            ("orc_scalar_hubble_rhs", [vp, C.c_double, d], C.c_double),
+            ("orc_scalar_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d], None),
+            ("orc_scalar_lf3_prepare", [vp, C.c_double, d, d, C.c_double, d, d], None),
+            ("orc_scalar_lf3_step", [vp, C.c_double, d, d, d, d, d, d], None),
+            ("orc_u1_kernels", [vp, d, d, C.c_double, d, d], None),
+            ("orc_u1_energies", [vp, d, d, d, d, C.c_double, d], None),
+            ("orc_u1_Ka", [vp, C.c_double, d], C.c_double),
+            ("orc_u1_gauss", [vp, d, d, d, d, d, d], None),
+            ("orc_u1_lf_prepare", [vp, C.c_double, d, d, d, d, C.c_double, d, d, d], None),
+            ("orc_u1_lf_step", [vp, C.c_double, d, d, d, d, d, d, d, d], None),
+        ]:
+            f = getattr(_lib, name)
+            f.argtypes = args
+            f.restype = res
+    return _lib
+
+
+def _p(x):
+    assert x.dtype == np.float64 and x.flags.c_contiguous
+    return x.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _ScalarModelC(C.Structure):
+    _fields_ = [("N", C.c_int64), ("Ns", C.c_int32), ("pexp", C.c_int32), ("dx", C.c_double),
+                ("alpha", C.c_double), ("fmp2", C.c_double), ("lam", C.c_double), ("q", C.c_double)]
+
+
+class _U1ModelC(C.Structure):
+    _fields_ = [("N", C.c_int64), ("dx", C.c_double), ("alpha", C.c_double), ("fmp2", C.c_double),
+                ("lam", C.c_double), ("v2", C.c_double), ("e", C.c_double), ("kappa", C.c_double)]
+
+
+# --- Yoshida weights (section 3.4.1 and the appendix table of VVn weights) ---
+# VV4 is written in closed form, w1 = w3 = 1/(2 - 2^(1/3)), w2 = -2^(1/3)/(2 - 2^(1/3)),
+# because the printed w2 of the table makes the three weights sum to 1 - 2e-8.
+_C3 = 2.0 ** (1.0 / 3.0)
+VV2 = (1.0,)
+VV4 = (1.0 / (2.0 - _C3), -_C3 / (2.0 - _C3), 1.0 / (2.0 - _C3))
+_VV6_HALF = (0.78451361047755726382, 0.23557321335935813368, -1.1776799841788710069, 1.3151863206839112189)
+_VV8_HALF = (0.74167036435061295345, -0.40910082580003159400, 0.19075471029623837995, -0.57386247111608226666,
+             0.29906418130365592384, 0.33462491824529818378, 0.31529309239676659663, -0.79688793935291635402)
+_VV10_HALF = (-0.48159895600253002870, 0.0036303931544595926879, 0.50180317558723140279, 0.28298402624506254868,
+              0.80702967895372223806, -0.026090580538592205447, -0.87286590146318071547, -0.52373568062510581643,
+              0.44521844299952789252, 0.18612289547097907887, 0.23137327866438360633, -0.52191036590418628905,
+              0.74866113714499296793, 0.066736511890604057532, -0.80360324375670830316, 0.91249037635867994571)
+
+
+def _sym(half):
+    return tuple(half) + tuple(reversed(half[:-1]))
+
+
+VV6 = _sym(_VV6_HALF)
+VV8 = _sym(_VV8_HALF)
+VV10 = _sym(_VV10_HALF)
+
+
+@dataclass
+class ScalarModel:
+    """Program-unit scalar model of sections 4 and 8.1:
+    V = (lam/p)|phi|^p + (q/2) phi^2 chi^2, Ns = 1 or 2 fields."""
+    N: int
+    Ns: int
+    pexp: int
+    dx: float
+    alpha: float
+    fmp2: float
+    lam: float = 1.0
+    q: float = 0.0
+
+    def c(self):
+        return _ScalarModelC(self.N, self.Ns, self.pexp, self.dx, self.alpha, self.fmp2, self.lam, self.q)
+
+
+@dataclass
+class U1Model:
+    """Program-unit Abelian-Higgs model of section 5: V = (lam/4)(|phi|^2 - v2)^2,
+    gauge coupling e, kappa = (omega*/f*)^2."""
+    N: int
+    dx: float
+    alpha: float
+    fmp2: float
+    lam: float = 1.0
+    v2: float = 1.0
+    e: float = 1.0
+    kappa: float = 1.0
+
+    def c(self):
+        return _U1ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.e, self.kappa)
+
+
+def potential_terms(m, phi, chi=None):
+    """V_1 = (lam/p)|phi|^p, V_2 = (q/2) phi^2 chi^2 (numpy, elementwise)."""
+    v1 = m.lam / m.pexp * np.abs(phi) ** m.pexp
+    v2 = 0.5 * m.q * phi ** 2 * chi ** 2 if (m.Ns > 1 and chi is not None) else 0.0 * phi
+    return v1, v2
+
+
+def potential_curvature(m, phibar):
+    """d^2V/dphi_i^2 at homogeneous values phibar (section 8.1)."""
+    f0 = phibar[0]
+    f1 = phibar[1] if m.Ns > 1 else 0.0
+    out = [(m.pexp - 1) * m.lam * abs(f0) ** (m.pexp - 2) + (m.q * f1 * f1 if m.Ns > 1 else 0.0)]
+    if m.Ns > 1:
+        out.append(m.q * f0 * f0)
+    return out
+
+
+class ScalarLattice:
+    """Scalar lattice state (phi, pi: float64 arrays of shape (Ns, N, N, N)),
+    with a and b = a' in program units."""
+
+    def __init__(self, model, phi, pi, a=1.0, b=0.0):
+        self.m = model
+        self._mc = model.c()
+        self.phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(model.Ns, model.N, model.N, model.N).copy()
+        self.pi = np.ascontiguousarray(pi, dtype=np.float64).reshape(model.Ns, model.N, model.N, model.N).copy()
+        self.a = float(a)
+        self.b = float(b)
+        self.EKm = None  # E_K at the previous half step (leapfrog only)
+
+    def _mp(self):
+        return C.byref(self._mc)
+
+    def kernel(self, a=None):
+        K = np.zeros_like(self.phi)
+        lib().orc_scalar_kernel(self._mp(), _p(self.phi), self.a if a is None else a, _p(K))
+        return K
+
+    def energies(self):
+        out = np.zeros(6)
+        lib().orc_scalar_energies(self._mp(), _p(self.phi), _p(self.pi), self.a, _p(out))
+        return out
+
+    def Ka(self, E=None):
+        E = self.energies() if E is None else np.ascontiguousarray(E, dtype=np.float64)
+        return lib().orc_scalar_Ka(self._mp(), self.a, _p(E))
+
+    def hubble_rhs(self, E=None):
+        E = self.energies() if E is None else np.ascontiguousarray(E, dtype=np.float64)
+        return lib().orc_scalar_hubble_rhs(self._mp(), self.a, _p(E))
+
+    def vv_steps(self, weights, dt, n=1):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        a = C.c_double(self.a)
+        b = C.c_double(self.b)
+        for _ in range(n):
+            lib().orc_scalar_vv_step(self._mp(), len(w), _p(w), dt, _p(self.phi), _p(self.pi), C.byref(a), C.byref(b))
+        self.a, self.b = a.value, b.value
+
+    def lf3_prepare(self, dt):
+        b = C.c_double(self.b)
+        ekm = C.c_double(0.0)
+        lib().orc_scalar_lf3_prepare(self._mp(), dt, _p(self.phi), _p(self.pi), self.a, C.byref(b), C.byref(ekm))
+        self.b, self.EKm = b.value, ekm.value
+
+    def lf3_steps(self, dt, n=1, diag=False):
+        a, b, ekm = C.c_double(self.a), C.c_double(self.b), C.c_double(self.EKm)
+        rows = []
+        d = np.zeros(5)
+        for _ in range(n):
+            lib().orc_scalar_lf3_step(self._mp(), dt, _p(self.phi), _p(self.pi), C.byref(a), C.byref(b),
+                                      C.byref(ekm), _p(d))
+            if diag:
+                rows.append(d.copy())
+        self.a, self.b, self.EKm = a.value, b.value, ekm.value
+        return np.array(rows) if diag else None
+
+    def hubble_violation(self):
+        """Delta_e = |b^2 - rhs| / rhs of the Hubble constraint (synchronized state)."""
+        rhs = self.hubble_rhs()
+        return abs(self.b ** 2 - rhs) / rhs
+
+
+class U1Lattice:
+    """Compact U(1) state: phi, pi of shape (2, N, N, N) (real and imaginary
+    planes of the complex field), theta, piA of shape (3, N, N, N)."""
+
+    def __init__(self, model, phi, pi, theta, piA, a=1.0, b=0.0):
+        self.m = model
+        self._mc = model.c()
+        N = model.N
+        self.phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(2, N, N, N).copy()
+        self.pi = np.ascontiguousarray(pi, dtype=np.float64).reshape(2, N, N, N).copy()
+        self.theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(3, N, N, N).copy()
+        self.piA = np.ascontiguousarray(piA, dtype=np.float64).reshape(3, N, N, N).copy()
+        self.a, self.b = float(a), float(b)
+        self.EKm = None
+
+    def _mp(self):
+        return C.byref(self._mc)
+
+    def kernels(self):
+        Kp = np.zeros_like(self.phi)
+        KA = np.zeros_like(self.theta)
+        lib().orc_u1_kernels(self._mp(), _p(self.phi), _p(self.theta), self.a, _p(Kp), _p(KA))
+        return Kp, KA
+
+    def energies(self):
+        out = np.zeros(5)
+        lib().orc_u1_energies(self._mp(), _p(self.phi), _p(self.pi), _p(self.theta), _p(self.piA), self.a, _p(out))
+        return out
+
+    def gauss(self, return_fields=False):
+        N = self.m.N
+        lhs = np.zeros((N, N, N))
+        rhs = np.zeros((N, N, N))
+        out = np.zeros(3)
+        lib().orc_u1_gauss(self._mp(), _p(self.phi), _p(self.pi), _p(self.piA), _p(lhs), _p(rhs), _p(out))
+        dg = np.sqrt(out[0]) / np.sqrt(out[1] + out[2]) if out[1] + out[2] > 0 else np.sqrt(out[0])
+        return (dg, lhs, rhs) if return_fields else dg
+
+    def lf_prepare(self, dt):
+        b, ek, eka = C.c_double(self.b), C.c_double(0), C.c_double(0)
+        lib().orc_u1_lf_prepare(self._mp(), dt, _p(self.phi), _p(self.pi), _p(self.theta), _p(self.piA), self.a,
+                                C.byref(b), C.byref(ek), C.byref(eka))
+        self.b, self.EKm = b.value, (ek.value, eka.value)
+
+    def lf_steps(self, dt, n=1):
+        a, b = C.c_double(self.a), C.c_double(self.b)
+        ek, eka = C.c_double(self.EKm[0]), C.c_double(self.EKm[1])
+        for _ in range(n):
+            lib().orc_u1_lf_step(self._mp(), dt, _p(self.phi), _p(self.pi), _p(self.theta), _p(self.piA),
+                                 C.byref(a), C.byref(b), C.byref(ek), C.byref(eka))
+        self.a, self.b, self.EKm = a.value, b.value, (ek.value, eka.value)

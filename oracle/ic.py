@@ -1,0 +1,166 @@
+"""Initial conditions of section 7 in program units (FP64, numpy).
+
+TEST INFRASTRUCTURE ONLY (part of the oracle).
+
+Scalar singlets (section 7.1): each field is a homogeneous mode plus Gaussian
+vacuum fluctuations with, per Fourier mode n~ of the paper's transform,
+    |dphi(n~)|^2 = (w*/f*)^2 (N/dx)^3 / (2 a^2 w_k),   w_k = sqrt(k^2 + a^2 m^2),
+    dphi(n~)  = (|l| e^{i th_l} + |r| e^{i th_r}) / sqrt(2),
+    dphi'(n~) = a^{alpha-1} (i w_k/sqrt(2)) (|l| e^{i th_l} - |r| e^{i th_r}) - H dphi(n~),
+with Rayleigh moduli |l|, |r| (mean square the variance above) and uniform
+phases.  Readings where the paper is silent: the half-space of modes with
+n~_x >= 0 is drawn and the rest follows from f(-n~) = f(n~)*; modes equal to
+their own conjugate take sqrt(2) Re f; the zero mode carries no fluctuation;
+a tachyonic m^2 < 0 enters w_k as |m^2|; H is the program Hubble rate of the
+homogeneous mode alone, and b = a' then follows from the Hubble constraint of
+the full lattice.
+
+Charged scalar and U(1) field (section 7.2): the two real components of
+phi = (phi_0 + i phi_1)/sqrt(2) are drawn as above but with |l_n| = |r_n| and
+th_1r = th_0r + th_1l - th_0l, which makes the total charge vanish; the links
+start at unity (A = 0) and the electric momenta solve the lattice Gauss law
+sum_i D_i^- piA_i = (2e/kappa) Im[phi* pi] in Fourier space with the backward
+lattice momentum.
+
+Random draws: Philox4x32-10 with key = seed and counter (mode index in the
+half layout [z][y][x <= N/2], stream, draw, ...) -- see philox.py.
+"""
+import numpy as np
+
+from . import philox
+from .core import potential_curvature, potential_terms
+from .spectra import dft_forward, dft_inverse, mode_numbers
+
+
+def _half_lin(N, iz, iy, ix):
+    return (iz.astype(np.int64) * N + iy) * (N // 2 + 1) + ix
+
+
+def _sign_class(c, N):
+    """0 for components equal to their own negative mod N (0 and N/2), +1 for
+    0 < c < N/2, -1 otherwise (c is a signed mode number)."""
+    return np.where((c == 0) | (c == N // 2), 0, np.where(c > 0, 1, -1))
+
+
+def mode_map(N):
+    """For every full-lattice mode index (z, y, x): the half-layout index of
+    the mode whose draws define it, whether it is the conjugate of that mode,
+    and whether it is self-conjugate."""
+    idx = np.arange(N)
+    iz, iy, ix = np.meshgrid(idx, idx, idx, indexing="ij")
+    m = mode_numbers(N)
+    sz, sy, sx = _sign_class(m[iz], N), _sign_class(m[iy], N), _sign_class(m[ix], N)
+    canon = (sx > 0) | ((sx == 0) & (sy > 0)) | ((sx == 0) & (sy == 0) & (sz > 0))
+    selfc = (sx == 0) & (sy == 0) & (sz == 0)
+    conj = ~(canon | selfc)
+    niz, niy, nix = (-iz) % N, (-iy) % N, (-ix) % N
+    sz_ = np.where(conj, niz, iz)
+    sy_ = np.where(conj, niy, iy)
+    sx_ = np.where(conj, nix, ix)
+    lin = _half_lin(N, sz_, sy_, sx_)
+    kabs = np.sqrt(m[iz].astype(np.float64) ** 2 + m[iy] ** 2 + m[ix] ** 2)
+    zero = (m[iz] == 0) & (m[iy] == 0) & (m[ix] == 0)
+    return lin, conj, selfc, zero, kabs
+
+
+def _project(G, conj, selfc, zero):
+    F = np.where(conj, np.conj(G), G)
+    F = np.where(selfc, np.sqrt(2.0) * G.real + 0j, F)
+    return np.where(zero, 0j, F)
+
+
+def _omega(k, a, m2):
+    m2 = abs(m2) if m2 < 0 else m2
+    return np.sqrt(k * k + a * a * m2)
+
+
+def scalar_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scale=1.0, fluctuations=True):
+    """Fields and momenta (Ns, N, N, N) plus b = a' for the scalar model.
+    phibar, dphibar: homogeneous values and program-time derivatives."""
+    N, Ns = model.N, model.Ns
+    dx = 2.0 * np.pi / (kIR * N)
+    alpha = model.alpha
+    phibar = [float(x) for x in phibar[:Ns]]
+    dphibar = [float(x) for x in dphibar[:Ns]]
+    # program Hubble rate of the homogeneous mode: H^2 = a^{2 alpha}/3 (f*/m_p)^2 (K + V)
+    v1, v2 = potential_terms(model, np.array(phibar[0]), np.array(phibar[1]) if Ns > 1 else None)
+    EK0 = sum(d * d for d in dphibar) / (2.0 * a ** (2 * alpha))
+    H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + float(v1) + float(v2)), 0.0))
+    m2 = potential_curvature(model, phibar)
+    phi = np.zeros((Ns, N, N, N))
+    pi = np.zeros((Ns, N, N, N))
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    k = kIR * nabs
+    for i in range(Ns):
+        dphi = np.zeros((N, N, N))
+        ddphi = np.zeros((N, N, N))
+        if fluctuations:
+            w = _omega(k, a, m2[i])
+            with np.errstate(divide="ignore", invalid="ignore"):
+                T = np.where(zero, 0.0, (omega_over_fstar ** 2) * (N / dx) ** 3 / (2 * a * a * w))
+            T *= fluct_scale ** 2
+            u = philox.uniforms(lin, i, 0, seed)
+            L = np.sqrt(-T * np.log(u[0]))
+            R = np.sqrt(-T * np.log(u[1]))
+            el = np.exp(2j * np.pi * u[2])
+            er = np.exp(2j * np.pi * u[3])
+            G = (L * el + R * er) / np.sqrt(2.0)
+            Gd = a ** (alpha - 1.0) * (1j * w / np.sqrt(2.0)) * (L * el - R * er) - H * G
+            dphi = dft_inverse(_project(G, conj, selfc, zero)).real
+            ddphi = dft_inverse(_project(Gd, conj, selfc, zero)).real
+        phi[i] = phibar[i] + dphi
+        pi[i] = a ** (3.0 - alpha) * (dphibar[i] + ddphi)
+    return phi, pi, dx
+
+
+def hubble_b(model, phi, pi, a, energies):
+    """b = a' from the Hubble constraint b^2 = (1/3)(f*/m_p)^2 a^{2(alpha+1)} (E_K+E_G+E_V)."""
+    E = energies
+    return float(np.sqrt(max(model.fmp2 / 3.0 * a ** (2 * (model.alpha + 1)) * (E[0] + E[1] + E[2] + E[3] + E[4] + E[5]), 0.0)))
+
+
+def u1_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scale=1.0):
+    """Complex scalar (2, N, N, N) as Re/Im planes, its momentum, links
+    theta = 0 and Gauss-consistent electric momenta piA (3, N, N, N)."""
+    N = model.N
+    dx = 2.0 * np.pi / (kIR * N)
+    alpha = model.alpha
+    pb = [float(phibar[0]), float(phibar[1])]
+    db = [float(dphibar[0]), float(dphibar[1])]
+    s = 0.5 * (pb[0] ** 2 + pb[1] ** 2)
+    m2 = [0.5 * model.lam * (s - model.v2) + 0.5 * model.lam * pb[n] ** 2 for n in range(2)]
+    mod2 = s
+    Vbar = 0.25 * model.lam * (mod2 - model.v2) ** 2
+    EK0 = 0.5 * (db[0] ** 2 + db[1] ** 2) / a ** (2 * alpha)
+    H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    k = kIR * nabs
+    u = philox.uniforms(lin, 0, 0, seed)
+    v = philox.uniforms(lin, 0, 1, seed)
+    th0l, th0r, th1l = 2 * np.pi * u[2], 2 * np.pi * u[3], 2 * np.pi * v[0]
+    th1r = th0r + th1l - th0l
+    comps, dcomps = [], []
+    for n, (thl, thr) in enumerate([(th0l, th0r), (th1l, th1r)]):
+        w = _omega(k, a, m2[n])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            T = np.where(zero, 0.0, (omega_over_fstar ** 2) * (N / dx) ** 3 / (2 * a * a * w))
+        T *= fluct_scale ** 2
+        A = np.sqrt(-T * np.log(u[n]))
+        el, er = np.exp(1j * thl), np.exp(1j * thr)
+        G = A * (el + er) / np.sqrt(2.0)
+        Gd = a ** (alpha - 1.0) * (1j * w / np.sqrt(2.0)) * A * (el - er) - H * G
+        comps.append(pb[n] + dft_inverse(_project(G, conj, selfc, zero)).real)
+        dcomps.append(db[n] + dft_inverse(_project(Gd, conj, selfc, zero)).real)
+    phi = np.stack([comps[0], comps[1]]) / np.sqrt(2.0)
+    pi = a ** (3.0 - alpha) * np.stack([dcomps[0], dcomps[1]]) / np.sqrt(2.0)
+    # Gauss law in Fourier space: sum_i beta_i piA_i(n~) = R(n~), beta_i = (1 - e^{2 pi i n~_i/N})/dx
+    rho = phi[0] * pi[1] - phi[1] * pi[0]
+    R = dft_forward(2.0 * model.e / model.kappa * rho)
+    m = mode_numbers(N)
+    nz, ny, nx = np.meshgrid(m, m, m, indexing="ij")
+    betas = [(1.0 - np.exp(2j * np.pi * c / N)) / dx for c in (nx, ny, nz)]
+    den = sum(np.abs(bb) ** 2 for bb in betas)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        piA = np.stack([dft_inverse(np.where(den > 0, np.conj(bb) * R / den, 0.0)).real for bb in betas])
+    theta = np.zeros((3, N, N, N))
+    return phi, pi, theta, piA, dx

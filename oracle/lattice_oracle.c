@@ -1,0 +1,534 @@
+/*
+ * FP64 CPU oracle for the lattice evolution of arXiv:2006.15122
+ * ("The Art of Simulating the Early Universe -- Part I").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code, header, table or constant with the CUDA library and imports nothing
+ * from it.  It is written to be read against the paper: every function
+ * follows one passage, in the paper's order and notation, in plain FP64,
+ * with unmerged half-kicks and no fusion.
+ *
+ * Conventions (paper section 3.1):
+ *   site n = (n1,n2,n3), linear index (n3*N + n2)*N + n1, n1 fastest;
+ *   periodic boundary conditions in the three directions;
+ *   program variables of section 4.1: phi~ = phi/f_star, d eta~ = a^-alpha w_star dt,
+ *   dx~ = w_star dx, V~ = V/(f_star^2 w_star^2).
+ *
+ * Scalar sector (section 4): N_s real fields with momenta
+ *   pi_i = a^{3-alpha} phi_i'           (Hamiltonian form, section 4.2.3)
+ *   phi_i' = a^{-(3-alpha)} pi_i
+ *   pi_i'  = K_i = a^{1+alpha} L[phi_i] - a^{3+alpha} dV/dphi_i
+ *   L[f](n) = sum_k (f(n+k) + f(n-k) - 2 f(n)) / dx^2   (= sum_k D_k^- D_k^+ f)
+ *   b' = K_a = (1/3)(fstar/m_p)^2 a^{1+2 alpha} [(alpha-2)E_K + alpha E_G + (alpha+1) E_V]
+ *   E_K = sum_i <pi_i^2>/(2 a^6), E_G = sum_{i,k} <(D_k^+ phi_i)^2>/(2 a^2), E_V = <V>
+ * Potential (section 8.1, program units): V = (lam/p)|phi|^p + (q/2) phi^2 chi^2.
+ *
+ * U(1) sector (section 5, compact formulation 5.3): complex phi, momentum
+ * pi = a^{3-alpha} phi', link angles theta_i = e dx A_i (V_i = exp(-i theta_i)),
+ * electric momenta piA_i = a^{1-alpha} F_0i.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXF 2
+
+typedef struct {
+    int64_t N;     /* sites per dimension */
+    int32_t Ns;    /* number of real scalar fields (1 or 2) */
+    int32_t pexp;  /* exponent p of the inflaton term (2, 4 or 6) */
+    double dx;     /* lattice spacing, program units */
+    double alpha;  /* alpha-time exponent */
+    double fmp2;   /* (fstar/m_p)^2; 0 means a static background (a = 1, b = 0) */
+    double lam;    /* coefficient of (1/p)|phi|^p */
+    double q;      /* coupling of (q/2) phi^2 chi^2 (only with Ns = 2) */
+} orc_scalar_model;
+
+static inline int64_t wrap(int64_t i, int64_t N) { return (i % N + N) % N; }
+static inline int64_t site(int64_t N, int64_t x, int64_t y, int64_t z) { return (z * N + y) * N + x; }
+
+static double ipow(double x, int k) {
+    double r = 1.0;
+    for (int i = 0; i < k; ++i) r *= x;
+    return r;
+}
+
+/* ---------------------------------------------------------------- scalars */
+
+/* Potential terms of section 8.1: V_1 = (lam/p)|phi|^p, V_2 = (q/2) phi^2 chi^2. */
+static void potential_terms(const orc_scalar_model* m, double phi, double chi, double* v1, double* v2) {
+    *v1 = m->lam / m->pexp * ipow(fabs(phi), m->pexp);
+    *v2 = (m->Ns > 1) ? 0.5 * m->q * phi * phi * chi * chi : 0.0;
+}
+
+/* dV/dphi = lam |phi|^{p-2} phi + q chi^2 phi,   dV/dchi = q phi^2 chi (section 8.1). */
+static void potential_gradient(const orc_scalar_model* m, double phi, double chi, double* dphi, double* dchi) {
+    *dphi = m->lam * ipow(fabs(phi), m->pexp - 2) * phi;
+    *dchi = 0.0;
+    if (m->Ns > 1) {
+        *dphi += m->q * chi * chi * phi;
+        *dchi = m->q * phi * phi * chi;
+    }
+}
+
+/* Kernel of the scalar momenta, section 4.2.3 (Hamiltonian form):
+ * K_i(n) = a^{1+alpha} L[phi_i](n) - a^{3+alpha} dV/dphi_i(n). */
+void orc_scalar_kernel(const orc_scalar_model* m, const double* phi, double a, double* K) {
+    const int64_t N = m->N, V = N * N * N;
+    const double idx2 = 1.0 / (m->dx * m->dx);
+    const double a1 = pow(a, 1.0 + m->alpha), a3 = pow(a, 3.0 + m->alpha);
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                const double f0 = phi[n], f1 = (m->Ns > 1) ? phi[V + n] : 0.0;
+                double d0, d1;
+                potential_gradient(m, f0, f1, &d0, &d1);
+                for (int i = 0; i < m->Ns; ++i) {
+                    const double* f = phi + (int64_t)i * V;
+                    const double lap = (f[site(N, wrap(x + 1, N), y, z)] + f[site(N, wrap(x - 1, N), y, z)] +
+                                        f[site(N, x, wrap(y + 1, N), z)] + f[site(N, x, wrap(y - 1, N), z)] +
+                                        f[site(N, x, y, wrap(z + 1, N))] + f[site(N, x, y, wrap(z - 1, N))] -
+                                        6.0 * f[n]) * idx2;
+                    K[(int64_t)i * V + n] = a1 * lap - a3 * (i == 0 ? d0 : d1);
+                }
+            }
+}
+
+/* Energies of section 4.4.1 (with pi = a^{3-alpha} phi', so E_K carries a^-6).
+ * out[0..1] = E_K per field, out[2..3] = E_G per field, out[4] = <V_1>, out[5] = <V_2>. */
+void orc_scalar_energies(const orc_scalar_model* m, const double* phi, const double* pi, double a, double* out) {
+    const int64_t N = m->N, V = N * N * N;
+    double sk[ORC_MAXF] = {0, 0}, sg[ORC_MAXF] = {0, 0}, sv1 = 0, sv2 = 0;
+    for (int i = 0; i < m->Ns; ++i) {
+        const double* f = phi + (int64_t)i * V;
+        const double* p = pi + (int64_t)i * V;
+        double k = 0, g = 0;
+#pragma omp parallel for reduction(+ : k, g) schedule(static)
+        for (int64_t z = 0; z < N; ++z)
+            for (int64_t y = 0; y < N; ++y)
+                for (int64_t x = 0; x < N; ++x) {
+                    const int64_t n = site(N, x, y, z);
+                    const double gx = (f[site(N, wrap(x + 1, N), y, z)] - f[n]) / m->dx;
+                    const double gy = (f[site(N, x, wrap(y + 1, N), z)] - f[n]) / m->dx;
+                    const double gz = (f[site(N, x, y, wrap(z + 1, N))] - f[n]) / m->dx;
+                    k += p[n] * p[n];
+                    g += gx * gx + gy * gy + gz * gz;
+                }
+        sk[i] = k;
+        sg[i] = g;
+    }
+#pragma omp parallel for reduction(+ : sv1, sv2) schedule(static)
+    for (int64_t n = 0; n < V; ++n) {
+        double v1, v2;
+        potential_terms(m, phi[n], m->Ns > 1 ? phi[V + n] : 0.0, &v1, &v2);
+        sv1 += v1;
+        sv2 += v2;
+    }
+    const double a6 = pow(a, 6.0), a2 = a * a;
+    for (int i = 0; i < ORC_MAXF; ++i) {
+        out[i] = sk[i] / V / (2.0 * a6);
+        out[2 + i] = sg[i] / V / (2.0 * a2);
+    }
+    out[4] = sv1 / V;
+    out[5] = sv2 / V;
+}
+
+/* Scale-factor kernel K_a of section 4.3.2 from total E_K, E_G, E_V. */
+static double Ka_scalar(const orc_scalar_model* m, double a, double EK, double EG, double EV) {
+    return m->fmp2 / 3.0 * pow(a, 1.0 + 2.0 * m->alpha) *
+           ((m->alpha - 2.0) * EK + m->alpha * EG + (m->alpha + 1.0) * EV);
+}
+
+static void totals(const double* E, double* EK, double* EG, double* EV) {
+    *EK = E[0] + E[1];
+    *EG = E[2] + E[3];
+    *EV = E[4] + E[5];
+}
+
+double orc_scalar_Ka(const orc_scalar_model* m, double a, const double* E) {
+    double EK, EG, EV;
+    totals(E, &EK, &EG, &EV);
+    return Ka_scalar(m, a, EK, EG, EV);
+}
+
+/* Right-hand side of the Hubble constraint b^2 = (1/3)(fstar/m_p)^2 a^{2(alpha+1)} (E_K+E_G+E_V). */
+double orc_scalar_hubble_rhs(const orc_scalar_model* m, double a, const double* E) {
+    double EK, EG, EV;
+    totals(E, &EK, &EG, &EV);
+    return m->fmp2 / 3.0 * pow(a, 2.0 * (m->alpha + 1.0)) * (EK + EG + EV);
+}
+
+static void kick(const orc_scalar_model* m, const double* phi, double* pi, double a, double h, double* K) {
+    const int64_t V = m->N * m->N * m->N;
+    orc_scalar_kernel(m, phi, a, K);
+    for (int64_t n = 0; n < (int64_t)m->Ns * V; ++n) pi[n] += h * K[n];
+}
+
+static void drift(const orc_scalar_model* m, double* phi, const double* pi, double c) {
+    const int64_t V = m->N * m->N * m->N;
+    for (int64_t n = 0; n < (int64_t)m->Ns * V; ++n) phi[n] += c * pi[n];
+}
+
+/* One full step of the Yoshida-composed velocity-Verlet integrator VVn for
+ * scalars in a self-consistently expanding background (section 4.3.2).  For
+ * each sub-step p = 1..s with weight w_p:
+ *   b_1/2   = b + w_p dt/2 K_a[a, E(p-1)]
+ *   pi_1/2  = pi + w_p dt/2 K[a, phi]
+ *   a_1/2   = a + b_1/2 w_p dt/2
+ *   phi     = phi + w_p dt pi_1/2 a_1/2^{-(3-alpha)}
+ *   a       = a_1/2 + b_1/2 w_p dt/2
+ *   pi      = pi_1/2 + w_p dt/2 K[a, phi]
+ *   b       = b_1/2 + w_p dt/2 K_a[a, E(p)]
+ * s = 1, w = {1} is VV2 (section 4.2.3).  E(p-1) is the energy of the state
+ * before the sub-step, E(p) the one after it. */
+void orc_scalar_vv_step(const orc_scalar_model* m, int s, const double* w, double dt,
+                        double* phi, double* pi, double* a, double* b) {
+    const int64_t V = m->N * m->N * m->N;
+    double* K = (double*)malloc(sizeof(double) * (size_t)(m->Ns * V));
+    double E[6];
+    orc_scalar_energies(m, phi, pi, *a, E);
+    for (int p = 0; p < s; ++p) {
+        const double h = w[p] * dt;
+        const double bh = *b + 0.5 * h * orc_scalar_Ka(m, *a, E);
+        kick(m, phi, pi, *a, 0.5 * h, K);
+        const double ah = *a + 0.5 * h * bh;
+        drift(m, phi, pi, h * pow(ah, -(3.0 - m->alpha)));
+        *a = ah + 0.5 * h * bh;
+        kick(m, phi, pi, *a, 0.5 * h, K);
+        orc_scalar_energies(m, phi, pi, *a, E);
+        *b = bh + 0.5 * h * orc_scalar_Ka(m, *a, E);
+    }
+    free(K);
+}
+
+/* Scheme III of section 4.2.1 needs E_K at n+1/2, which contains a_{n+1/2} =
+ * a_n + dt b_{n+1/2}/2, while b_{n+1/2} itself depends on that E_K through the
+ * averaged kinetic energy.  The paper leaves this scalar fixed point implicit;
+ * it is solved here by plain fixed-point iteration to round-off, with
+ * S = sum_i <pi_i^2> at n+1/2 fixed. */
+static double lf3_solve_b(const orc_scalar_model* m, double dt, double a, double bm, double EKm, double S,
+                          double EG, double EV, double* EKp_out) {
+    double bp = bm, EKp = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        const double ah = a + 0.5 * dt * bp;
+        EKp = S / (2.0 * pow(ah, 6.0));
+        const double EKbar = 0.5 * (EKm + EKp);
+        const double bn = bm + dt * Ka_scalar(m, a, EKbar, EG, EV);
+        const double d = fabs(bn - bp);
+        bp = bn;
+        if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
+    }
+    const double ah = a + 0.5 * dt * bp;
+    *EKp_out = S / (2.0 * pow(ah, 6.0));
+    return bp;
+}
+
+/* Start scheme III from a synchronized state (phi, pi, a, b at eta_0): the
+ * half-step-behind momenta are taken with a backward half kick,
+ * pi_{-1/2} = pi - dt/2 K[a, phi] and b_{-1/2} = b - dt/2 K_a[a, E].
+ * Returns E_K at -1/2 in *EKm, with a_{-1/2} = a - dt b_{-1/2}/2. */
+void orc_scalar_lf3_prepare(const orc_scalar_model* m, double dt, const double* phi, double* pi, double a,
+                            double* b, double* EKm) {
+    const int64_t V = m->N * m->N * m->N;
+    double* K = (double*)malloc(sizeof(double) * (size_t)(m->Ns * V));
+    double E[6];
+    orc_scalar_energies(m, phi, pi, a, E);
+    *b = *b - 0.5 * dt * orc_scalar_Ka(m, a, E);
+    kick(m, phi, pi, a, -0.5 * dt, K);
+    const double ahm = a - 0.5 * dt * (*b);
+    double S = 0.0;
+    for (int64_t n = 0; n < (int64_t)m->Ns * V; ++n) S += pi[n] * pi[n];
+    *EKm = S / V / (2.0 * pow(ahm, 6.0));
+    free(K);
+}
+
+/* One step of staggered leapfrog scheme III (section 4.2.1), state
+ * (phi_n, a_n) at integer and (pi_{n-1/2}, b_{n-1/2}) at half-integer time:
+ *   pi_{+1/2} = pi_{-1/2} + dt K[a, phi]
+ *   b_{+1/2}  = b_{-1/2} + dt (1/3)(fstar/m_p)^2 a^{1+2alpha}[(alpha-2) <E_K> + alpha E_G + (alpha+1) E_V]
+ *   a_{+1}    = a + dt b_{+1/2},  a_{+1/2} = (a + a_{+1})/2
+ *   phi_{+1}  = phi + dt pi_{+1/2} a_{+1/2}^{-(3-alpha)}
+ * with <E_K> the average of E_K at -1/2 and +1/2.  *EKm carries E_K at the
+ * previous half step in and the new one out.  diag (may be NULL) receives
+ * {E_G(n), E_V(n), E_K(n+1/2), a_{n+1/2}, b_{n+1/2}}. */
+void orc_scalar_lf3_step(const orc_scalar_model* m, double dt, double* phi, double* pi, double* a, double* b,
+                         double* EKm, double* diag) {
+    const int64_t V = m->N * m->N * m->N;
+    double* K = (double*)malloc(sizeof(double) * (size_t)(m->Ns * V));
+    double E[6];
+    orc_scalar_energies(m, phi, pi, *a, E); /* E_G, E_V at n (E_K entries unused) */
+    const double EG = E[2] + E[3], EV = E[4] + E[5];
+    kick(m, phi, pi, *a, dt, K);
+    double S = 0.0;
+    for (int64_t n = 0; n < (int64_t)m->Ns * V; ++n) S += pi[n] * pi[n];
+    S /= (double)V;
+    double EKp;
+    const double bp = lf3_solve_b(m, dt, *a, *b, *EKm, S, EG, EV, &EKp);
+    const double an = *a + dt * bp;
+    const double ah = 0.5 * (*a + an);
+    drift(m, phi, pi, dt * pow(ah, -(3.0 - m->alpha)));
+    if (diag) {
+        diag[0] = EG;
+        diag[1] = EV;
+        diag[2] = EKp;
+        diag[3] = ah;
+        diag[4] = bp;
+    }
+    *a = an;
+    *b = bp;
+    *EKm = EKp;
+    free(K);
+}
+
+/* ------------------------------------------------------------------- U(1) */
+
+typedef struct {
+    int64_t N;
+    double dx, alpha, fmp2;
+    double lam, v2; /* V = (lam/4)(|phi|^2 - v2)^2 */
+    double e;       /* gauge coupling g_A Q_A */
+    double kappa;   /* (omega_star/f_star)^2 */
+} orc_u1_model;
+
+/* Plaquette angle theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n),
+ * so that V_ij = V_i V_{j,+i} V*_{i,+j} V*_j = exp(-i theta_ij) (U(1) toolkit, section 3.2.2). */
+static double plaq(const orc_u1_model* m, const double* th, int i, int j, int64_t x, int64_t y, int64_t z) {
+    const int64_t N = m->N, V = N * N * N;
+    int64_t c[3] = {x, y, z};
+    int64_t ci[3] = {x, y, z}, cj[3] = {x, y, z};
+    ci[i] = wrap(ci[i] + 1, N);
+    cj[j] = wrap(cj[j] + 1, N);
+    const double* ti = th + (int64_t)i * V;
+    const double* tj = th + (int64_t)j * V;
+    return ti[site(N, c[0], c[1], c[2])] + tj[site(N, ci[0], ci[1], ci[2])] - ti[site(N, cj[0], cj[1], cj[2])] -
+           tj[site(N, c[0], c[1], c[2])];
+}
+
+/* Kernels of the compact U(1) formulation (section 5.3):
+ * K_phi  = -a^{3+alpha} dV/dphi* + a^{1+alpha} sum_i D_i^- D_i^+ phi,
+ *          D_i^- D_i^+ phi = (V_i phi(n+i) - 2 phi + V_i*(n-i) phi(n-i))/dx^2,
+ *          dV/dphi* = (lam/2)(|phi|^2 - v2) phi;
+ * K_A,i = a^{1+alpha} (2e/dx)(1/kappa) Im[phi*(n) V_i(n) phi(n+i)]
+ *        + a^{alpha-1}/(e dx^3) sum_{j!=i} [Im V_ij(n) - Im V_ij(n-j)].
+ * phi is stored as (re, im) planes; K_phi likewise. */
+void orc_u1_kernels(const orc_u1_model* m, const double* phi, const double* th, double a, double* Kphi,
+                    double* KA) {
+    const int64_t N = m->N, V = N * N * N;
+    const double a1 = pow(a, 1.0 + m->alpha), a3 = pow(a, 3.0 + m->alpha), am = pow(a, m->alpha - 1.0);
+    const double dx = m->dx;
+    const double* pr = phi;
+    const double* pim = phi + V;
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                const int64_t c[3] = {x, y, z};
+                double lr = -6.0 * pr[n], li = -6.0 * pim[n];
+                for (int i = 0; i < 3; ++i) {
+                    int64_t cp[3] = {x, y, z}, cm[3] = {x, y, z};
+                    cp[i] = wrap(c[i] + 1, N);
+                    cm[i] = wrap(c[i] - 1, N);
+                    const int64_t np = site(N, cp[0], cp[1], cp[2]), nm = site(N, cm[0], cm[1], cm[2]);
+                    const double t = th[(int64_t)i * V + n], tm = th[(int64_t)i * V + nm];
+                    /* V_i phi(n+i), V_i = cos t - i sin t */
+                    const double ur = cos(t) * pr[np] + sin(t) * pim[np];
+                    const double ui = cos(t) * pim[np] - sin(t) * pr[np];
+                    /* V_i*(n-i) phi(n-i) */
+                    const double wr = cos(tm) * pr[nm] - sin(tm) * pim[nm];
+                    const double wi = cos(tm) * pim[nm] + sin(tm) * pr[nm];
+                    lr += ur + wr;
+                    li += ui + wi;
+                    /* current: Im[phi*(n) V_i phi(n+i)] = pr*ui - pim*ur */
+                    const double cur = pr[n] * ui - pim[n] * ur;
+                    double mag = 0.0;
+                    for (int j = 0; j < 3; ++j) {
+                        if (j == i) continue;
+                        int64_t cmj[3] = {x, y, z};
+                        cmj[j] = wrap(c[j] - 1, N);
+                        /* Im V_ij = -sin(theta_ij) */
+                        mag += -sin(plaq(m, th, i, j, x, y, z)) + sin(plaq(m, th, i, j, cmj[0], cmj[1], cmj[2]));
+                    }
+                    KA[(int64_t)i * V + n] =
+                        a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;
+                }
+                const double mod2 = pr[n] * pr[n] + pim[n] * pim[n];
+                const double dv = 0.5 * m->lam * (mod2 - m->v2);
+                Kphi[n] = -a3 * dv * pr[n] + a1 * lr / (dx * dx);
+                Kphi[V + n] = -a3 * dv * pim[n] + a1 * li / (dx * dx);
+            }
+}
+
+/* Energies of section 5.4.1 (compact):
+ * out[0] E_K^phi = <|pi|^2>/a^6,  out[1] E_G^phi = sum_i <|D_i^+ phi|^2>/a^2,
+ * out[2] E_V = <V>,  out[3] E_K^A = kappa/(2a^4) sum_i <piA_i^2>,
+ * out[4] E_G^A = kappa/(a^4 e^2 dx^4) sum_{i<j} <1 - cos theta_ij>. */
+void orc_u1_energies(const orc_u1_model* m, const double* phi, const double* pi, const double* th,
+                     const double* piA, double a, double* out) {
+    const int64_t N = m->N, V = N * N * N;
+    const double* pr = phi;
+    const double* pim = phi + V;
+    double sk = 0, sg = 0, sv = 0, ska = 0, sga = 0;
+#pragma omp parallel for reduction(+ : sk, sg, sv, ska, sga) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                const int64_t c[3] = {x, y, z};
+                sk += pi[n] * pi[n] + pi[V + n] * pi[V + n];
+                const double mod2 = pr[n] * pr[n] + pim[n] * pim[n];
+                sv += 0.25 * m->lam * (mod2 - m->v2) * (mod2 - m->v2);
+                for (int i = 0; i < 3; ++i) {
+                    int64_t cp[3] = {x, y, z};
+                    cp[i] = wrap(c[i] + 1, N);
+                    const int64_t np = site(N, cp[0], cp[1], cp[2]);
+                    const double t = th[(int64_t)i * V + n];
+                    const double ur = cos(t) * pr[np] + sin(t) * pim[np];
+                    const double ui = cos(t) * pim[np] - sin(t) * pr[np];
+                    const double dr = (ur - pr[n]) / m->dx, di = (ui - pim[n]) / m->dx;
+                    sg += dr * dr + di * di;
+                    ska += piA[(int64_t)i * V + n] * piA[(int64_t)i * V + n];
+                    for (int j = i + 1; j < 3; ++j) sga += 1.0 - cos(plaq(m, th, i, j, x, y, z));
+                }
+            }
+    const double a2 = a * a, a4 = a2 * a2, a6 = a4 * a2, dx4 = pow(m->dx, 4.0);
+    out[0] = sk / V / a6;
+    out[1] = sg / V / a2;
+    out[2] = sv / V;
+    out[3] = m->kappa * ska / V / (2.0 * a4);
+    out[4] = m->kappa * sga / V / (a4 * m->e * m->e * dx4);
+}
+
+/* K_a with the U(1) weights of section 5.1: the gauge energies enter with (alpha-1). */
+static double Ka_u1(const orc_u1_model* m, double a, double EKp, double EGp, double EV, double EKA, double EGA) {
+    return m->fmp2 / 3.0 * pow(a, 2.0 * m->alpha + 1.0) *
+           ((m->alpha - 2.0) * EKp + m->alpha * EGp + (m->alpha + 1.0) * EV + (m->alpha - 1.0) * (EKA + EGA));
+}
+
+double orc_u1_Ka(const orc_u1_model* m, double a, const double* E) {
+    return Ka_u1(m, a, E[0], E[1], E[2], E[3], E[4]);
+}
+
+/* Gauss-law residual of the compact U(1) sector (section 5.2, discrete Gauss law):
+ * G(n) = sum_i D_i^- piA_i(n) - (2e/kappa) Im[phi*(n) pi(n)].
+ * The sign of the charge term follows from the kernels above (both follow
+ * from one lattice action).  lhs/rhs receive the two terms per site; out[0] =
+ * <G^2>, out[1] = <lhs^2>, out[2] = <rhs^2>. */
+void orc_u1_gauss(const orc_u1_model* m, const double* phi, const double* pi, const double* piA, double* lhs,
+                  double* rhs, double* out) {
+    const int64_t N = m->N, V = N * N * N;
+    double g2 = 0, l2 = 0, r2 = 0;
+#pragma omp parallel for reduction(+ : g2, l2, r2) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                const int64_t c[3] = {x, y, z};
+                double div = 0.0;
+                for (int i = 0; i < 3; ++i) {
+                    int64_t cm[3] = {x, y, z};
+                    cm[i] = wrap(c[i] - 1, N);
+                    const int64_t nm = site(N, cm[0], cm[1], cm[2]);
+                    div += (piA[(int64_t)i * V + n] - piA[(int64_t)i * V + nm]) / m->dx;
+                }
+                /* Im[phi* pi] = re(phi) im(pi) - im(phi) re(pi) */
+                const double rho = phi[n] * pi[V + n] - phi[V + n] * pi[n];
+                const double r = 2.0 * m->e / m->kappa * rho;
+                if (lhs) lhs[n] = div;
+                if (rhs) rhs[n] = r;
+                g2 += (div - r) * (div - r);
+                l2 += div * div;
+                r2 += r * r;
+            }
+    out[0] = g2 / V;
+    out[1] = l2 / V;
+    out[2] = r2 / V;
+}
+
+/* Backward half kick that starts the compact staggered leapfrog from a
+ * synchronized state: pi_{-1/2} = pi - dt/2 K_phi, piA_{-1/2} = piA - dt/2 K_A,
+ * b_{-1/2} = b - dt/2 K_a[a, E].  *EKm receives E_K^phi + E_K^A at -1/2 with
+ * a_{-1/2} = a - dt b_{-1/2}/2 (the two kinetic terms scale as a^-6 and a^-4). */
+void orc_u1_lf_prepare(const orc_u1_model* m, double dt, const double* phi, double* pi, const double* th,
+                       double* piA, double a, double* b, double* EKm_phi, double* EKm_A) {
+    const int64_t V = m->N * m->N * m->N;
+    double* Kp = (double*)malloc(sizeof(double) * (size_t)(2 * V));
+    double* KA = (double*)malloc(sizeof(double) * (size_t)(3 * V));
+    double E[5];
+    orc_u1_energies(m, phi, pi, th, piA, a, E);
+    *b -= 0.5 * dt * orc_u1_Ka(m, a, E);
+    orc_u1_kernels(m, phi, th, a, Kp, KA);
+    double sp = 0, sa = 0;
+    for (int64_t n = 0; n < 2 * V; ++n) {
+        pi[n] -= 0.5 * dt * Kp[n];
+        sp += pi[n] * pi[n];
+    }
+    for (int64_t n = 0; n < 3 * V; ++n) {
+        piA[n] -= 0.5 * dt * KA[n];
+        sa += piA[n] * piA[n];
+    }
+    const double ahm = a - 0.5 * dt * (*b);
+    *EKm_phi = sp / V / pow(ahm, 6.0);
+    *EKm_A = m->kappa * sa / V / (2.0 * pow(ahm, 4.0));
+    free(Kp);
+    free(KA);
+}
+
+/* One step of the compact staggered leapfrog (section 5.3.1):
+ *   pi_{+1/2}  = pi_{-1/2} + dt K_phi[a, phi, V]
+ *   piA_{+1/2} = piA_{-1/2} + dt K_A[a, phi, V]
+ *   b_{+1/2}   = b_{-1/2} + dt K_a[a, <E_K^phi>, E_G^phi, E_V, <E_K^A>, E_G^A]
+ *   a_{+1}     = a + dt b_{+1/2}
+ *   phi_{+1}   = phi + dt pi_{+1/2} / a_{+1/2}^{3-alpha}
+ *   V_i,+1     = exp(-i e dx dt piA_{+1/2} / a_{+1/2}^{1-alpha}) V_i
+ * The link drift is the exact exponential (theta_i += e dx dt piA/a^{1-alpha}),
+ * which keeps |V_i| = 1; <E_K> averages the kinetic energies at -1/2 and +1/2
+ * and the implicit dependence on a_{+1/2} is iterated to round-off. */
+void orc_u1_lf_step(const orc_u1_model* m, double dt, double* phi, double* pi, double* th, double* piA,
+                    double* a, double* b, double* EKm_phi, double* EKm_A) {
+    const int64_t V = m->N * m->N * m->N;
+    double* Kp = (double*)malloc(sizeof(double) * (size_t)(2 * V));
+    double* KA = (double*)malloc(sizeof(double) * (size_t)(3 * V));
+    double E[5];
+    orc_u1_energies(m, phi, pi, th, piA, *a, E); /* E_G^phi, E_V, E_G^A at n */
+    orc_u1_kernels(m, phi, th, *a, Kp, KA);
+    double sp = 0, sa = 0;
+    for (int64_t n = 0; n < 2 * V; ++n) {
+        pi[n] += dt * Kp[n];
+        sp += pi[n] * pi[n];
+    }
+    for (int64_t n = 0; n < 3 * V; ++n) {
+        piA[n] += dt * KA[n];
+        sa += piA[n] * piA[n];
+    }
+    sp /= (double)V;
+    sa /= (double)V;
+    double bp = *b, EKp = 0, EKA = 0;
+    for (int it = 0; it < 200; ++it) {
+        const double ah = *a + 0.5 * dt * bp;
+        EKp = sp / pow(ah, 6.0);
+        EKA = m->kappa * sa / (2.0 * pow(ah, 4.0));
+        const double bn = *b + dt * Ka_u1(m, *a, 0.5 * (*EKm_phi + EKp), E[1], E[2], 0.5 * (*EKm_A + EKA), E[4]);
+        const double d = fabs(bn - bp);
+        bp = bn;
+        if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
+    }
+    const double an = *a + dt * bp;
+    const double ah = 0.5 * (*a + an);
+    EKp = sp / pow(ah, 6.0);
+    EKA = m->kappa * sa / (2.0 * pow(ah, 4.0));
+    const double cphi = dt * pow(ah, -(3.0 - m->alpha));
+    const double cth = m->e * m->dx * dt * pow(ah, -(1.0 - m->alpha));
+    for (int64_t n = 0; n < 2 * V; ++n) phi[n] += cphi * pi[n];
+    for (int64_t n = 0; n < 3 * V; ++n) th[n] += cth * piA[n];
+    *a = an;
+    *b = bp;
+    *EKm_phi = EKp;
+    *EKm_A = EKA;
+    free(Kp);
+    free(KA);
+}

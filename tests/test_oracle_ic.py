@@ -1,0 +1,122 @@
+"""Pins of the oracle's initial conditions (section 7), spectra (sections 3.1,
+4.4.2) and random draws (Philox4x32-10)."""
+import numpy as np
+import pytest
+
+from oracle import ScalarModel, U1Lattice, U1Model, philox
+from oracle.ic import mode_map, scalar_ic, u1_ic
+from oracle.spectra import dft_forward, shell_bins, spectrum
+
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open("tests/golden/philox4x32_10_kat.txt") if not l.startswith("#") and l.strip()]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        ctr, key, out = v[:4], v[4:6], v[6:10]
+        got = philox.philox4x32_10([np.array([c]) for c in ctr], key)
+        assert [int(g[0]) for g in got] == out
+
+
+def test_mode_map_is_a_hermitian_pairing():
+    N = 6
+    lin, conj, selfc, zero, kabs = mode_map(N)
+    # every half-layout source index is used by a mode and its conjugate, or by one self-conjugate mode
+    assert selfc.sum() == 8  # components in {0, N/2}
+    for z in range(N):
+        for y in range(N):
+            for x in range(N):
+                nz, ny, nx = (-z) % N, (-y) % N, (-x) % N
+                assert lin[z, y, x] == lin[nz, ny, nx]
+                if not selfc[z, y, x]:
+                    assert conj[z, y, x] != conj[nz, ny, nx]
+
+
+def _scalar_setup(N=16, kIR=0.5, seed=3):
+    dx = 2 * np.pi / (kIR * N)
+    m = ScalarModel(N=N, Ns=2, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, q=2.0)
+    phi, pi, _ = scalar_ic(m, kIR, [1.0, 0.0], [0.0, 0.0], seed=seed, omega_over_fstar=0.1)
+    return m, phi, pi, dx
+
+
+def test_vacuum_fluctuations_have_the_target_mode_variance():
+    """Per shell, <|dphi(n~)|^2> / ((w*/f*)^2 (N/dx)^3 / (2 a^2 w_k)) -> 1 within
+    its sampling error (|dphi|^2 is exponentially distributed, section 7.1),
+    and <|dphi'(n~) + H dphi(n~)|^2> carries the extra w_k^2."""
+    N, kIR = 16, 0.5
+    m, phi, pi, dx = _scalar_setup(N, kIR)
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    k = kIR * nabs
+    for i, m2 in enumerate([1.0 + 0.0, 2.0 * 1.0]):  # d2V/dphi2 = lam + q chi^2, d2V/dchi2 = q phi^2
+        w = np.sqrt(k ** 2 + m2)
+        T = np.where(zero, 1.0, 0.1 ** 2 * (N / dx) ** 3 / (2 * w))
+        P = np.abs(dft_forward(phi[i] - phi[i].mean())) ** 2 / T
+        Pd = np.abs(dft_forward(pi[i])) ** 2 / (T * w * w)
+        b, _, nb = shell_bins(N)
+        for s in range(1, nb):
+            sel = (b == s) & ~selfc
+            c = sel.sum()
+            if c < 60:
+                continue
+            tol = 5.0 * np.sqrt(2.0 / c)
+            assert abs(P[sel].mean() - 1) < tol, (i, s, P[sel].mean())
+            assert abs(Pd[sel].mean() - 1) < tol, (i, s, Pd[sel].mean())
+    assert abs(phi[0].mean() - 1.0) < 1e-14 and abs(phi[1].mean()) < 1e-14
+
+
+def test_ic_is_deterministic_in_the_seed():
+    _, a, _, _ = _scalar_setup(seed=11)
+    _, b, _, _ = _scalar_setup(seed=11)
+    _, c, _, _ = _scalar_setup(seed=12)
+    assert np.array_equal(a, b) and not np.allclose(a, c)
+
+
+def test_spectrum_parseval_and_plane_wave():
+    """Sum over shells of count * <|f(n~)|^2> / N^6 equals <f^2> (DFT identity of
+    section 3.1); a plane wave puts all its power in one shell."""
+    N, kIR = 12, 0.3
+    dx = 2 * np.pi / (kIR * N)
+    f = np.random.default_rng(0).standard_normal((N, N, N))
+    k, D, cnt = spectrum(f, dx, kIR)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        P = np.where(k > 0, D * 2 * np.pi ** 2 / k ** 3 / (dx / N) ** 3, 0.0)
+    F0 = abs(dft_forward(f)[0, 0, 0]) ** 2
+    assert abs((np.sum(P * cnt) + F0) / N ** 6 - (f ** 2).mean()) < 1e-12
+    x = np.arange(N)
+    wave = np.cos(2 * np.pi * 3 * x / N)[None, None, :] * np.ones((N, N, 1))
+    k, D, cnt = spectrum(wave, dx, kIR)
+    assert np.count_nonzero(D > 1e-20) == 1 and D[3] > 0
+    assert 3 * kIR <= k[3] < 4 * kIR  # k of a shell is k_IR times the mean |n~| of its modes
+    assert cnt.sum() == N ** 3
+
+
+def test_ic_spectrum_follows_vacuum_power_spectrum():
+    """Delta(k) of the initial fluctuations scatters around the continuum vacuum
+    spectrum k^3/(2 pi^2) (w*/f*)^2 / (2 w_k) (section 7.1)."""
+    N, kIR = 16, 0.5
+    m, phi, pi, dx = _scalar_setup(N, kIR)
+    k, D, cnt = spectrum(phi[1], dx, kIR)
+    w = np.sqrt(k ** 2 + 2.0)
+    target = k ** 3 / (2 * np.pi ** 2) * 0.1 ** 2 / (2 * w)
+    sel = cnt > 100
+    ratio = D[sel] / target[sel]
+    assert np.all(np.abs(ratio - 1) < 6 * np.sqrt(2.0 / cnt[sel]) + 0.05)
+
+
+def test_u1_ic_has_zero_charge_and_satisfies_gauss():
+    N = 12
+    m = U1Model(N=N, dx=0.5, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=1.0, kappa=1.0)
+    phi, pi, th, piA, dx = u1_ic(m, 2 * np.pi / (N * 0.5), [0.0, 0.0], [0.0, 0.0], seed=21, omega_over_fstar=1.0)
+    rho = phi[0] * pi[1] - phi[1] * pi[0]
+    assert abs(rho.sum()) < 1e-12 * np.abs(rho).sum()
+    lat = U1Lattice(m, phi, pi, th, piA)
+    assert lat.gauss() < 1e-14
+    assert np.all(th == 0.0)
+    # both components fluctuate with the same statistics
+    assert 0.5 < phi[0].var() / phi[1].var() < 2.0
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_isqrt_bins_are_exact(N):
+    b, nabs, nb = shell_bins(N)
+    assert np.all(b * b <= nabs ** 2 + 1e-9) and np.all((b + 1) ** 2 > nabs ** 2 - 1e-9)

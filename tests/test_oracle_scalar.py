@@ -1,0 +1,257 @@
+"""Pins of the oracle's scalar sector against what the paper and the mathematics fix.
+
+Each test would fail on a plausible slip in the oracle: a wrong sign or scale of
+the Laplacian, a dropped potential term, a wrong a-power in a kick, drift or
+in K_a, wrong Yoshida weights, a broken half-kick order.
+"""
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+from scipy.special import ellipj
+
+import oracle
+from oracle import ScalarLattice, ScalarModel
+from oracle.spectra import dft_forward, dft_inverse, mode_numbers
+from tests import inputs
+
+
+def _vv_map(h, w2):
+    """One velocity-Verlet step of x'' = -w2 x (kick h/2, drift h, kick h/2)."""
+    c = 1.0 - 0.5 * h * h * w2
+    return np.array([[c, h * np.ones_like(w2)], [-h * w2 * (1.0 - 0.25 * h * h * w2), c]])
+
+
+def _apply(M, X, P):
+    return M[0, 0] * X + M[0, 1] * P, M[1, 0] * X + M[1, 1] * P
+
+
+@pytest.mark.parametrize("weights,tol", [(oracle.VV2, 1e-12), (oracle.VV4, 1e-12)])
+def test_free_field_matches_exact_lattice_dispersion(weights, tol):
+    """Free massive field, static background: every mode of the paper's DFT is
+    an oscillator with w^2 = m^2 + sum_i 4 sin^2(pi n~_i/N)/dx^2 (section 3.2.1,
+    forward/backward lattice momenta), and VVn is a product of 2x2 maps."""
+    N, dx, m2, dt, steps = 8, 0.7, 0.5, 0.2, 10
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=m2)
+    phi = inputs.fields(1, N, seed=3, amp=0.8)
+    pi = inputs.fields(1, N, seed=4, amp=0.5)
+    lat = ScalarLattice(m, phi, pi)
+    lat.vv_steps(weights, dt, steps)
+    k = mode_numbers(N)
+    nz, ny, nx = np.meshgrid(k, k, k, indexing="ij")
+    w2 = m2 + sum(4 * np.sin(np.pi * c / N) ** 2 for c in (nx, ny, nz)) / dx ** 2
+    X, P = dft_forward(phi[0]), dft_forward(pi[0])
+    for _ in range(steps):
+        for w in weights:
+            X, P = _apply(_vv_map(w * dt, w2), X, P)
+    phi_x, pi_x = dft_inverse(X).real, dft_inverse(P).real
+    assert np.max(np.abs(lat.phi[0] - phi_x)) < tol * np.max(np.abs(phi_x))
+    assert np.max(np.abs(lat.pi[0] - pi_x)) < tol * np.max(np.abs(pi_x))
+    assert lat.a == 1.0 and lat.b == 0.0
+
+
+def test_summation_by_parts_links_laplacian_and_gradient_energy():
+    """sum_n phi L[phi] = - sum_{n,k} (D_k^+ phi)^2 on a periodic lattice."""
+    N, dx = 8, 0.3
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=0.0)
+    phi = inputs.fields(1, N, seed=5)
+    lat = ScalarLattice(m, phi, np.zeros_like(phi))
+    K = lat.kernel()
+    E = lat.energies()
+    lhs = float(np.sum(phi[0] * K[0]))
+    rhs = -2.0 * N ** 3 * E[2]
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+@pytest.mark.parametrize("a,alpha", [(1.0, 0.0), (1.37, 0.5), (2.1, 1.0)])
+def test_kernels_are_minus_gradient_of_paper_energies(a, alpha):
+    """With U = a^{3+alpha} N^3 (E_G + E_V) built from the energies of section
+    4.4.1, the kick is K_i(n) = -dU/dphi_i(n) and the drift rate
+    a^{-(3-alpha)} pi equals d(a^{3+alpha} N^3 E_K)/dpi (finite differences)."""
+    N = 6
+    m = ScalarModel(N=N, Ns=2, pexp=4, dx=0.45, alpha=alpha, fmp2=1.0, lam=0.8, q=3.0)
+    phi = inputs.fields(2, N, seed=11, amp=0.4, means=[1.0, 0.1])
+    pi = inputs.fields(2, N, seed=12, amp=0.6)
+    lat = ScalarLattice(m, phi, pi, a=a)
+    K = lat.kernel()
+    scale = a ** (3 + alpha) * N ** 3
+    eps = 1e-5
+    for (i, z, y, x) in [(0, 1, 2, 3), (1, 4, 0, 5), (0, 5, 5, 0), (1, 2, 3, 1)]:
+        g = []
+        for s in (+1, -1):
+            lat.phi[i, z, y, x] += s * eps
+            E = lat.energies()
+            g.append(scale * (E[2] + E[3] + E[4] + E[5]))
+            lat.phi[i, z, y, x] -= s * eps
+        dU = (g[0] - g[1]) / (2 * eps)
+        assert abs(K[i, z, y, x] + dU) < 1e-7 * (abs(dU) + 1.0)
+        h = []
+        for s in (+1, -1):
+            lat.pi[i, z, y, x] += s * eps
+            E = lat.energies()
+            h.append(scale * (E[0] + E[1]))
+            lat.pi[i, z, y, x] -= s * eps
+        dH = (h[0] - h[1]) / (2 * eps)
+        assert abs(dH - a ** (alpha - 3) * pi[i, z, y, x]) < 1e-7 * (abs(dH) + 1.0)
+
+
+def test_homogeneous_phi4_matches_jacobi_cn():
+    """Static phi^4: phi'' = -phi^3 has phi(t) = phi0 cn(phi0 t | m = 1/2); VV4
+    converges to it at fourth order and VV2 at second order."""
+    N, phi0, T = 4, 1.3, 3.0
+    m = ScalarModel(N=N, Ns=1, pexp=4, dx=1.0, alpha=0.0, fmp2=0.0, lam=1.0)
+    exact = phi0 * ellipj(phi0 * T, 0.5)[1]
+    errs = {}
+    for name, w in (("vv2", oracle.VV2), ("vv4", oracle.VV4)):
+        for dt in (0.02, 0.01):
+            lat = ScalarLattice(m, np.full((1, N, N, N), phi0), np.zeros((1, N, N, N)))
+            lat.vv_steps(w, dt, int(round(T / dt)))
+            assert np.ptp(lat.phi) == 0.0
+            errs[(name, dt)] = abs(lat.phi[0, 0, 0, 0] - exact)
+    assert errs[("vv4", 0.01)] < 1e-8
+    r2 = np.log2(errs[("vv2", 0.02)] / errs[("vv2", 0.01)])
+    r4 = np.log2(errs[("vv4", 0.02)] / errs[("vv4", 0.01)])
+    assert 1.9 < r2 < 2.1 and 3.8 < r4 < 4.2
+
+
+def _frw_reference(pexp, lam, fmp2, alpha, phi0, T):
+    """Textbook homogeneous FRW in cosmic time (phi'' + 3 H phi' + V' = 0,
+    a''/a = -(f*/m_p)^2 (rho + 3p)/6, rho = K + V, p = K - V), re-parametrised by
+    d eta = a^-alpha dt and integrated with DOP853 at rtol 1e-13."""
+    def V(f):
+        return lam / pexp * abs(f) ** pexp
+
+    def dV(f):
+        return lam * abs(f) ** (pexp - 2) * f
+
+    def rhs(_, y):
+        f, fd, a, ad = y
+        rho = 0.5 * fd * fd + V(f)
+        p = 0.5 * fd * fd - V(f)
+        H = ad / a
+        s = a ** alpha
+        return [s * fd, s * (-3 * H * fd - dV(f)), s * ad, s * (-a * fmp2 * (rho + 3 * p) / 6.0)]
+
+    ad0 = np.sqrt(fmp2 * V(phi0) / 3.0)
+    sol = solve_ivp(rhs, (0, T), [phi0, 0.0, 1.0, ad0], method="DOP853", rtol=1e-13, atol=1e-15)
+    f, fd, a, ad = sol.y[:, -1]
+    return f, a, ad0
+
+
+@pytest.mark.parametrize("pexp,alpha", [(2, 0.0), (4, 1.0), (4, 0.5)])
+def test_expanding_homogeneous_mode_matches_ode(pexp, alpha):
+    """The lattice homogeneous mode with self-consistent expansion follows the
+    textbook Friedmann system, with O(dt^2) (VV2) and O(dt^4) (VV4) errors."""
+    N, lam, fmp2, phi0, T = 2, 1.0, 1.5, 1.0, 4.0
+    m = ScalarModel(N=N, Ns=1, pexp=pexp, dx=1.0, alpha=alpha, fmp2=fmp2, lam=lam)
+    f_ref, a_ref, ad0 = _frw_reference(pexp, lam, fmp2, alpha, phi0, T)
+    errs = {}
+    for name, w in (("vv2", oracle.VV2), ("vv4", oracle.VV4)):
+        for dt in (0.04, 0.02):
+            lat = ScalarLattice(m, np.full((1, N, N, N), phi0), np.zeros((1, N, N, N)), a=1.0, b=ad0)
+            lat.vv_steps(w, dt, int(round(T / dt)))
+            errs[(name, dt)] = max(abs(lat.phi[0, 0, 0, 0] - f_ref), abs(lat.a - a_ref) / a_ref)
+    assert errs[("vv4", 0.02)] < 1e-7
+    r2 = np.log2(errs[("vv2", 0.04)] / errs[("vv2", 0.02)])
+    r4 = np.log2(errs[("vv4", 0.04)] / errs[("vv4", 0.02)])
+    assert 1.8 < r2 < 2.2 and 3.6 < r4 < 4.4
+
+
+def _fluct_lattice(dt_unused=None, alpha=0.0, pexp=2, Ns=2, q=2.0, fmp2=1.0, N=8):
+    m = ScalarModel(N=N, Ns=Ns, pexp=pexp, dx=0.6, alpha=alpha, fmp2=fmp2, lam=1.0, q=q)
+    phi = inputs.fields(Ns, N, seed=21, amp=0.05, kmax=2.5, means=[1.0] + [0.0] * (Ns - 1))
+    pi = inputs.fields(Ns, N, seed=22, amp=0.05, kmax=2.5)
+    lat = ScalarLattice(m, phi, pi)
+    lat.b = np.sqrt(lat.hubble_rhs())
+    return m, phi, pi, lat
+
+
+@pytest.mark.parametrize("weights,order", [(oracle.VV2, 2), (oracle.VV4, 4)])
+def test_hubble_constraint_converges_at_integrator_order(weights, order):
+    """Delta_e = |b^2 - rhs|/rhs at fixed time scales as dt^order (section
+    4.3.2: VVn satisfies the Hubble constraint to O(dt^n))."""
+    T = 2.0
+    de = []
+    for dt in (0.05, 0.025):
+        m, phi, pi, lat = _fluct_lattice(alpha=0.0)
+        lat.vv_steps(weights, dt, int(round(T / dt)))
+        de.append(lat.hubble_violation())
+    slope = np.log2(de[0] / de[1])
+    assert abs(slope - order) < 0.25 * order / 2 + 0.2, (de, slope)
+
+
+def test_vv_scheme_is_time_reversible():
+    """n steps forward then n steps with -dt return the initial state (section 3.5)."""
+    m, phi, pi, lat = _fluct_lattice(alpha=0.5, pexp=4)
+    a0, b0 = lat.a, lat.b
+    lat.vv_steps(oracle.VV4, 0.05, 20)
+    assert np.max(np.abs(lat.phi - phi)) > 1e-3
+    lat.vv_steps(oracle.VV4, -0.05, 20)
+    assert np.max(np.abs(lat.phi - phi)) < 1e-12
+    assert np.max(np.abs(lat.pi - pi)) < 1e-12
+    assert abs(lat.a - a0) < 1e-13 and abs(lat.b - b0) < 1e-13
+
+
+@pytest.mark.parametrize("weights,order", [(oracle.VV2, 2), (oracle.VV4, 4)])
+def test_static_two_field_energy_conservation(weights, order):
+    """Static background: the total energy of the coupled phi^2 chi^2 system is
+    conserved up to O(dt^order); a dropped coupling term would break it."""
+    T = 2.0
+    drift = []
+    for dt in (0.04, 0.02):
+        m = ScalarModel(N=8, Ns=2, pexp=2, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, q=8.0)
+        phi = inputs.fields(2, 8, seed=31, amp=0.3, kmax=2.0, means=[1.0, 0.0])
+        pi = inputs.fields(2, 8, seed=32, amp=0.3, kmax=2.0)
+        lat = ScalarLattice(m, phi, pi)
+        E0 = lat.energies().sum()
+        lat.vv_steps(weights, dt, int(round(T / dt)))
+        drift.append(abs(lat.energies().sum() - E0) / E0)
+    slope = np.log2(drift[0] / drift[1])
+    assert abs(slope - order) < 0.3, (drift, slope)
+
+
+def test_staggered_leapfrog_equals_vv2_in_static_background():
+    """In a static background scheme III is velocity-Verlet with momenta kept
+    half a step behind: the field trajectories coincide to round-off."""
+    m = ScalarModel(N=8, Ns=2, pexp=2, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, q=4.0)
+    phi = inputs.fields(2, 8, seed=41, amp=0.2, means=[1.0, 0.0])
+    pi = inputs.fields(2, 8, seed=42, amp=0.2)
+    vv = ScalarLattice(m, phi, pi)
+    lf = ScalarLattice(m, phi, pi)
+    lf.lf3_prepare(0.05)
+    vv.vv_steps(oracle.VV2, 0.05, 30)
+    lf.lf3_steps(0.05, 30)
+    assert np.max(np.abs(vv.phi - lf.phi)) < 1e-12
+
+
+def test_staggered_leapfrog_hubble_constraint_second_order():
+    """Scheme III verifies its Hubble constraint
+    b_{+1/2}^2 = (1/3)(f*/m_p)^2 a_{+1/2}^{2(alpha+1)} (E_K(+1/2) + <E_G> + <E_V>)
+    to O(dt^2) (section 4.2.1)."""
+    T = 2.0
+    de = []
+    for dt in (0.04, 0.02):
+        m, phi, pi, lat = _fluct_lattice(alpha=1.0, pexp=4, Ns=1)
+        lat.lf3_prepare(dt)
+        n = int(round(T / dt))
+        d = lat.lf3_steps(dt, n + 1, diag=True)
+        EG_bar = 0.5 * (d[n - 1, 0] + d[n, 0])
+        EV_bar = 0.5 * (d[n - 1, 1] + d[n, 1])
+        EK, ah, bh = d[n - 1, 2], d[n - 1, 3], d[n - 1, 4]
+        rhs = m.fmp2 / 3.0 * ah ** (2 * (m.alpha + 1)) * (EK + EG_bar + EV_bar)
+        de.append(abs(bh * bh - rhs) / rhs)
+    slope = np.log2(de[0] / de[1])
+    assert 1.7 < slope < 2.3, (de, slope)
+
+
+def test_yoshida_weights():
+    """Closed-form VV4 weights satisfy sum w = 1 and sum w^3 = 0 (fourth order);
+    the tabulated VV6/8/10 weights sum to one."""
+    w = np.array(oracle.VV4)
+    assert abs(w.sum() - 1) < 1e-15 and abs((w ** 3).sum()) < 1e-14
+    for ws in (oracle.VV6, oracle.VV8, oracle.VV10):
+        assert abs(sum(ws) - 1.0) < 1e-14
+    rows = [l.split() for l in open("tests/golden/yoshida_vv4_table.txt") if not l.startswith("#")]
+    printed = {r[0]: float(r[1]) for r in rows}
+    assert abs(printed["w1"] - w[0]) < 1e-15
+    # the printed w2 is off by 2e-8: the closed form is used instead
+    assert 1e-8 < abs(printed["w2"] - w[1]) < 1e-7

@@ -1,0 +1,152 @@
+"""Pins of the oracle's compact U(1) sector (section 5.3) against the
+mathematics: forces as gradients of the paper's energy functional, the Gauss
+law to round-off, gauge invariance, energy conservation and B = 0 at start."""
+import numpy as np
+import pytest
+
+from oracle import U1Lattice, U1Model
+from oracle.ic import u1_ic
+from tests import inputs
+
+
+def _random_state(N, seed, model, a=1.0):
+    phi = inputs.fields(2, N, seed=seed, amp=0.7, means=[0.5, -0.2])
+    pi = inputs.fields(2, N, seed=seed + 1, amp=0.4)
+    th = inputs.angles(N, seed + 2, scale=2.5)
+    piA = inputs.fields(3, N, seed=seed + 3, amp=0.3)
+    return U1Lattice(model, phi, pi, th, piA, a=a)
+
+
+@pytest.mark.parametrize("a,alpha", [(1.0, 0.0), (1.3, 0.5)])
+def test_u1_forces_are_minus_gradient_of_paper_energies(a, alpha):
+    """U = a^{3+alpha} N^3 (E_G^phi + E_V + E_G^A) from the energies of section
+    5.4.1; then K_phi = -dU/dphi* = -(1/2)(dU/dRe + i dU/dIm) and
+    K_A,i = -(e dx/kappa) dU/dtheta_i (theta_i = e dx A_i)."""
+    N = 5
+    m = U1Model(N=N, dx=0.55, alpha=alpha, fmp2=0.7, lam=1.3, v2=0.8, e=0.9, kappa=1.7)
+    lat = _random_state(N, 7, m, a=a)
+    Kp, KA = lat.kernels()
+    scale = a ** (3 + alpha) * N ** 3
+    eps = 1e-6
+
+    def U():
+        E = lat.energies()
+        return scale * (E[1] + E[2] + E[4])
+
+    for (c, z, y, x) in [(0, 1, 2, 3), (1, 4, 0, 2), (0, 0, 4, 4)]:
+        lat.phi[c, z, y, x] += eps
+        up = U()
+        lat.phi[c, z, y, x] -= 2 * eps
+        um = U()
+        lat.phi[c, z, y, x] += eps
+        d = (up - um) / (2 * eps)
+        assert abs(Kp[c, z, y, x] + 0.5 * d) < 1e-6 * (abs(d) + 1)
+    for (i, z, y, x) in [(0, 1, 2, 3), (1, 4, 0, 2), (2, 0, 4, 4), (2, 3, 3, 1)]:
+        lat.theta[i, z, y, x] += eps
+        up = U()
+        lat.theta[i, z, y, x] -= 2 * eps
+        um = U()
+        lat.theta[i, z, y, x] += eps
+        d = (up - um) / (2 * eps)
+        assert abs(KA[i, z, y, x] + m.e * m.dx / m.kappa * d) < 1e-6 * (abs(d) + 1)
+
+
+def test_u1_drift_rates_match_kinetic_energies():
+    """In a background with a fixed at a != 1 (f*/m_p = 0), one leapfrog step
+    drifts phi by dt d(a^{3+alpha}N^3 E_K^phi)/dpi* and theta_i by
+    (e dx/kappa) dt d(a^{3+alpha}N^3 E_K^A)/dpiA_i."""
+    N, a, alpha, dt = 4, 1.6, 0.5, 0.01
+    m = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=0.0, lam=1.0, v2=1.0, e=1.1, kappa=0.6)
+    lat = _random_state(N, 17, m, a=a)
+    lat.EKm = (0.0, 0.0)
+    phi0, th0 = lat.phi.copy(), lat.theta.copy()
+    lat.lf_steps(dt, 1)
+    # kinetic parts of a^{3+alpha} N^3 E: a^{alpha-3} sum |pi|^2 and a^{alpha-1} kappa sum piA^2 / 2
+    dphi_rate = a ** (alpha - 3) * lat.pi           # d/dpi* of a^{alpha-3} |pi|^2
+    dth_rate = m.e * m.dx / m.kappa * a ** (alpha - 1) * m.kappa * lat.piA
+    assert np.allclose((lat.phi - phi0) / dt, dphi_rate, rtol=1e-12, atol=1e-12)
+    assert np.allclose((lat.theta - th0) / dt, dth_rate, rtol=1e-12, atol=1e-12)
+    assert lat.a == a
+
+
+@pytest.mark.parametrize("fmp2,alpha", [(0.0, 0.0), (0.5, 0.5)])
+def test_gauss_law_holds_to_round_off(fmp2, alpha):
+    """Starting from the Gauss-consistent initial condition of section 7.2, the
+    compact leapfrog keeps the discrete Gauss law to machine precision."""
+    N, dt = 8, 0.05
+    m = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=fmp2, lam=1.0, v2=1.0, e=1.0, kappa=1.0)
+    kIR = 2 * np.pi / (N * 0.5)
+    phi, pi, th, piA, dx = u1_ic(m, kIR, [0.0, 0.0], [0.0, 0.0], seed=5, omega_over_fstar=1.0)
+    lat = U1Lattice(m, phi, pi, th, piA)
+    assert lat.gauss() < 1e-14
+    if fmp2 > 0:
+        E = lat.energies()
+        lat.b = np.sqrt(fmp2 / 3.0 * E.sum())
+    lat.lf_prepare(dt)
+    for _ in range(5):
+        lat.lf_steps(dt, 10)
+        assert lat.gauss() < 1e-13
+    assert np.max(np.abs(lat.theta)) > 1e-3  # the links did move
+
+
+def test_initial_magnetic_energy_is_exactly_zero():
+    N = 8
+    m = U1Model(N=N, dx=0.5, alpha=0.0, fmp2=0.0)
+    phi, pi, th, piA, dx = u1_ic(m, 2 * np.pi / 4.0, [0.0, 0.0], [0.0, 0.0], seed=9, omega_over_fstar=1.0)
+    E = U1Lattice(m, phi, pi, th, piA).energies()
+    assert E[4] == 0.0 and E[3] > 0.0
+
+
+def test_u1_energy_conservation_second_order():
+    """Static background: with E_K averaged over the two half steps, the total
+    energy of the compact leapfrog is conserved up to O(dt^2)."""
+    N, T = 6, 1.0
+    drift = []
+    for dt in (0.04, 0.02):
+        m = U1Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=1.3, kappa=0.8)
+        lat = _random_state(N, 27, m)
+        E0 = lat.energies().sum()
+        lat.lf_prepare(dt)
+        lat.lf_steps(dt, int(round(T / dt)))
+        # after n steps the state is (phi_n, pi_{n-1/2}); a forward half kick
+        # synchronizes the momenta with the fields
+        E = lat.energies()
+        Kp, KA = lat.kernels()
+        pis = lat.pi + 0.5 * dt * Kp
+        pas = lat.piA + 0.5 * dt * KA
+        EKs = (pis ** 2).sum() / N ** 3 + m.kappa * (pas ** 2).sum() / (2 * N ** 3)
+        drift.append(abs(EKs + E[1] + E[2] + E[4] - E0) / E0)
+    slope = np.log2(drift[0] / drift[1])
+    assert abs(slope - 2) < 0.3, (drift, slope)
+
+
+def test_gauge_invariance_of_the_evolution():
+    """phi -> e^{-i e alpha} phi, pi -> e^{-i e alpha} pi,
+    theta_i -> theta_i - e (alpha(n+i) - alpha(n)) commutes with the leapfrog
+    (U(1) toolkit, section 3.2.2)."""
+    N, dt = 6, 0.05
+    m = U1Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=0.8, kappa=1.0)
+    A = _random_state(N, 37, m)
+    al = inputs.rng(99).uniform(-2, 2, size=(N, N, N))
+
+    def transform(lat):
+        ph = np.exp(-1j * m.e * al)
+        c = (lat.phi[0] + 1j * lat.phi[1]) * ph
+        p = (lat.pi[0] + 1j * lat.pi[1]) * ph
+        th = lat.theta.copy()
+        for i, ax in enumerate((2, 1, 0)):
+            th[i] -= m.e * (np.roll(al, -1, axis=ax) - al)
+        return U1Lattice(m, np.stack([c.real, c.imag]), np.stack([p.real, p.imag]), th, lat.piA)
+
+    B = transform(A)
+    assert np.allclose(A.energies(), B.energies(), rtol=1e-12)
+    A.lf_prepare(dt)
+    B.lf_prepare(dt)
+    A.lf_steps(dt, 10)
+    B.lf_steps(dt, 10)
+    TA = transform(A)
+    assert np.max(np.abs(TA.phi - B.phi)) < 1e-11
+    assert np.max(np.abs(TA.pi - B.pi)) < 1e-11
+    dth = np.angle(np.exp(1j * (TA.theta - B.theta)))
+    assert np.max(np.abs(dth)) < 1e-11
+    assert np.max(np.abs(TA.piA - B.piA)) < 1e-11
