@@ -1,0 +1,255 @@
+"""Benchmark of the lattice hot path: site-updates/s of the 1024^3 two-field
+preheating lattice (V = phi^2/2 + q* phi^2 chi^2/2, q = 1e5 i.e. q* = 4e5),
+Yoshida VV4 steps with FP32 fluctuation arrays and FP64 means / background.
+
+One "step" is one full VV4 time step of every site of the lattice: three
+fused drift-stencil-kick-reduce passes plus the FP64 Friedmann update.  A
+site-update is one site advanced one full step (all fields).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--N 1024] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank evolves its own
+lattice (weak scaling, no data-path collective); value = total site-updates/s
+over all ranks from the max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Workload: the throughput configuration of the paper's two-field preheating model
+# (program units of sections 4.1 and 8.1; p = 2 so alpha = 0; f*/m_p and w*/f* of
+# the p = 2 benchmark of section 8.2), with the time step clamped to the VV4
+# stability bound of the highest chi mode (w_chi = sqrt(q*) phi = 632).
+KIR = 0.1
+QSTAR = 4.0e5
+FSTAR_MP = 1.396
+OMEGA_FSTAR = 5.13e-6
+DT = 0.002
+BYTES_PER_SITE_PASS = 32  # FP32: read and write delta-phi, delta-pi of two fields
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--N", type=int, default=1024)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(N):
+    return {"workload": "%d^3 two-field phi^2 chi^2 preheating lattice, q=1e5 (q*=4e5), Yoshida VV4, "
+                        "FP32 fluctuations + FP64 means/background, self-consistent expansion" % N,
+            "N": N, "fields": 2, "integrator": "VV4", "kIR": KIR, "dt": DT, "qstar": QSTAR,
+            "fstar_over_mp": FSTAR_MP, "omega_over_fstar": OMEGA_FSTAR,
+            "state_bytes": 2 * 2 * 4 * N ** 3,
+            "l2": "inputs (%.1f GB) exceed L2; no flush" % (2 * 2 * 4 * N ** 3 / 1e9)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sample_N=128, steps=1):
+    """The FP64 oracle as it stands, timed on this host's cores on a bounded
+    sample of the same workload (a smaller lattice of the same model)."""
+    import numpy as np
+
+    import oracle
+    from oracle.ic import scalar_ic
+
+    dx = 2 * math.pi / (KIR * sample_N)
+    om = oracle.ScalarModel(N=sample_N, Ns=2, pexp=2, dx=dx, alpha=0.0, fmp2=FSTAR_MP ** 2, lam=1.0, q=QSTAR)
+    phi, pi, _ = scalar_ic(om, KIR, [1.0, 0.0], [0.0, 0.0], seed=0, omega_over_fstar=OMEGA_FSTAR)
+    lat = oracle.ScalarLattice(om, phi, pi)
+    lat.b = math.sqrt(lat.hubble_rhs())
+    t0 = time.perf_counter()
+    lat.vv_steps(oracle.VV4, DT, steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": sample_N ** 3 * steps / dt, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+            "sample": "%d^3 lattice of the same model, %d VV4 step(s), FP64, %.1f s" % (sample_N, steps, dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N = min(args.N, 128)
+    vals = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        res = cpu_baseline(N, 1)
+        if i >= args.warmup:
+            vals.append(res["value"])
+    v = statistics.mean(vals)
+    cfg = workload_config(args.N)
+    line = {"impl": "reference", "metric": "site-updates/s", "value": v, "unit": "site-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * N ** 3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "value": v,
+                             "sample": "each step: one VV4 step of a %d^3 lattice of the same model" % N},
+            "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_2006_15122_gb300 as cl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    N = args.N
+    stream = torch.cuda.current_stream()
+    model = cl.make_model(n_fields=2, pexp=2, alpha=0.0, fstar_over_mp=FSTAR_MP, omega_over_fstar=OMEGA_FSTAR,
+                          lam=1.0, q=QSTAR)
+    grid = cl.make_grid(N, KIR, DT, "vv4", cl.CL_FP32)
+    lat = cl.Lattice(model, grid, cl.make_init(phi0=(1.0, 0.0), seed=rank), stream=stream)
+
+    for _ in range(args.warmup):
+        lat.evolve(1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.evolve(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mm = lat.measure_means()
+    npass = 3 * args.steps + 1
+    value = world * N ** 3 * args.steps / (ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = BYTES_PER_SITE_PASS * N ** 3
+    achieved = alg_bytes / (ms / 1e3 / npass) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API with pinned host buffers: every step
+        # uploads the four full FP64 arrays, advances one step, reads the means back
+        host = [torch.empty(N ** 3, dtype=torch.float64, pin_memory=True) for _ in range(4)]
+        for i, which in enumerate([cl.FIELD(0), cl.FIELD(1), cl.MOMENTUM(0), cl.MOMENTUM(1)]):
+            lat.get_field(which, host[i].view(N, N, N))
+        reps = 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for i, which in enumerate([cl.FIELD(0), cl.FIELD(1), cl.MOMENTUM(0), cl.MOMENTUM(1)]):
+                lat.set_field(which, host[i])
+            lat.set_background(mm["a"], mm["b"], mm["t"])
+            lat.evolve(1)
+            lat.measure_means()
+        t1 = time.perf_counter()
+        e2e = {"value": world * N ** 3 * reps / (t1 - t0), "unit": "site-updates/s",
+               "h2d_bytes_per_step": 4 * 8 * N ** 3, "d2h_bytes_per_step": 320,
+               "note": "per step: 4 full FP64 arrays H2D from pinned memory via lattice_set_field, one VV4 step, "
+                       "lattice_measure_means D2H"}
+    lat.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(128, 1)
+    if rank == 0:
+        prof = os.path.join(ROOT, "profiles", "scalar_pass_vv4_1024_fp32.md")
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(N), parallelism="replicas" if world > 1 else "single"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "scalar_pass_kernel<float,2,2>", "bytes_per_launch": alg_bytes,
+                         "launch_ms": ms / npass},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npass, "clocks": clk,
+            "hubble_violation": mm["hubble_violation"], "a": mm["a"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * cl_lattice.h -- C ABI of the GB300 lattice evolver for the method of
+ * arXiv:2006.15122, "The Art of Simulating the Early Universe -- Part I".
+ *
+ * The library evolves interacting real scalar fields, or a U(1)-charged
+ * complex scalar with a compact Abelian gauge field on link variables, on a
+ * periodic N^3 comoving lattice in a self-consistently expanding FLRW
+ * background, all in the paper's program variables (section 4.1):
+ *   phi~ = phi/f*,  d eta~ = a^-alpha w* dt,  dx~ = w* dx,  V~ = V/(f*^2 w*^2).
+ *
+ * Conventions shared by every call:
+ *  - No exceptions cross this boundary.  Every call returns a cl_status; a
+ *    human-readable reason of the last failure is in cl_last_error().
+ *  - A handle owns its device memory (cudaMalloc'd at lattice_init, freed at
+ *    lattice_destroy).  Host pointers passed in are only read or written
+ *    during the call.
+ *  - Work is ordered on the CUDA stream given to lattice_init (NULL = the
+ *    legacy default stream).  lattice_evolve only enqueues work; the
+ *    measure, get and save calls synchronize that stream before returning.
+ *  - Fields are stored as a double-precision homogeneous mean plus a
+ *    fluctuation array in the handle's precision (CL_FP64 or CL_FP32), laid
+ *    out SoA with site index (n3*N + n2)*N + n1 (n1 fastest, section 3.1).
+ *    Every field crossing the ABI is the full field (mean + fluctuation) in
+ *    double precision.
+ *  - Errors: CL_ERR_ARG for invalid arguments (nothing is changed),
+ *    CL_ERR_CUDA / CL_ERR_OOM for runtime failures, CL_ERR_UNSTABLE_DT when
+ *    the time step exceeds the integrator's linear stability bound,
+ *    CL_ERR_NONFINITE once a reduction has seen a NaN/Inf (the handle then
+ *    refuses to evolve), CL_ERR_STATE for calls that do not fit the
+ *    handle's state, CL_ERR_IO for checkpoint files that cannot be read,
+ *    written or verified.
+ */
+#ifndef CL_LATTICE_H
+#define CL_LATTICE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CL_OK = 0,
+    CL_ERR_ARG = 1,
+    CL_ERR_CUDA = 2,
+    CL_ERR_OOM = 3,
+    CL_ERR_UNSTABLE_DT = 4,
+    CL_ERR_NONFINITE = 5,
+    CL_ERR_TIMEOUT = 6,
+    CL_ERR_STATE = 7,
+    CL_ERR_IO = 8
+} cl_status;
+
+/* Model families.
+ * CL_MODEL_SCALAR: n_fields = 1 or 2 real singlets phi, chi with the program
+ *   potential of section 8.1, V = (lam/p)|phi|^p + (q/2) phi^2 chi^2.
+ * CL_MODEL_U1: one complex scalar phi = (phi_0 + i phi_1)/sqrt(2) with
+ *   V = (lam/4)(|phi|^2 - vev2)^2, coupled with charge e to a compact U(1)
+ *   gauge field in temporal gauge (section 5.3). */
+typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1 } cl_model_kind;
+
+/* Integrators (the paper's "switch", section 1.2):
+ * CL_INT_LF   staggered leapfrog: scheme III of section 4.2.1 for scalars,
+ *             the compact staggered leapfrog of section 5.3.1 for U(1);
+ * CL_INT_VV2  velocity-Verlet, section 4.2.3;
+ * CL_INT_VV4..CL_INT_VV10  Yoshida compositions of VV2 (section 4.3.2, weights
+ *             of the appendix table; VV4 in closed form). Scalar models only. */
+typedef enum {
+    CL_INT_LF = 0,
+    CL_INT_VV2 = 1,
+    CL_INT_VV4 = 2,
+    CL_INT_VV6 = 3,
+    CL_INT_VV8 = 4,
+    CL_INT_VV10 = 5
+} cl_integrator;
+
+typedef enum { CL_FP64 = 0, CL_FP32 = 1 } cl_precision;
+
+typedef struct {
+    int32_t kind;            /* cl_model_kind */
+    int32_t n_fields;        /* CL_MODEL_SCALAR: 1 or 2; ignored for CL_MODEL_U1 */
+    int32_t pexp;            /* p of (lam/p)|phi|^p: 2, 4 or 6 (scalar) */
+    int32_t reserved;
+    double alpha;            /* alpha-time exponent (section 4.1) */
+    double fstar_over_mp;    /* f_star/m_p; 0 selects a static background (a = 1, b = 0) */
+    double omega_over_fstar; /* w_star/f_star: amplitude factor of the vacuum fluctuations (section 7) */
+    double lam;              /* scalar: coefficient of (1/p)|phi|^p; U(1): lam of (lam/4)(|phi|^2 - vev2)^2 */
+    double q;                /* scalar, n_fields = 2: coupling of (q/2) phi^2 chi^2 */
+    double vev2;             /* U(1): vev2 */
+    double gauge_e;          /* U(1): gauge coupling e = g_A Q_A in program units */
+} cl_model;
+
+typedef struct {
+    int32_t N;          /* sites per dimension: multiple of 8, 8 <= N <= 2048 */
+    int32_t integrator; /* cl_integrator */
+    int32_t precision;  /* cl_precision of the fluctuation arrays */
+    int32_t force_dt;   /* nonzero: accept dt beyond the stability bound */
+    double kIR;         /* infrared momentum k_IR = 2 pi / L in program units (section 3.1) */
+    double dt;          /* time step d eta~ (program units) */
+} cl_grid;
+
+typedef struct {
+    double phi0[4];     /* homogeneous values: scalar fields, or (phi_0, phi_1) of U(1) */
+    double dphi0[4];    /* their program-time derivatives */
+    uint64_t seed;      /* key of the Philox4x32-10 draws of the fluctuations */
+    int32_t spectrum;   /* 0: homogeneous only; 1: vacuum fluctuations (section 7) */
+    int32_t reserved;
+    double fluct_scale; /* multiplies the fluctuation amplitude (1 = the paper's) */
+    double a0;          /* initial scale factor (1 in every configuration of the paper) */
+} cl_init;
+
+/* Volume averages and constraints (sections 4.4, 5.4, 8.2.1). */
+typedef struct {
+    double t;              /* program time */
+    double a, b;           /* scale factor and b = a' */
+    int64_t step;          /* completed steps */
+    double mean[4];        /* <f_c>: scalar fields, or Re/Im of phi for U(1) */
+    double mean2[4];       /* <f_c^2> */
+    double var[4];         /* <f_c^2> - <f_c>^2 */
+    double mean_pi[4];     /* <pi_c> */
+    double EK[4];          /* scalar: E_K per field; U(1): {E_K^phi, E_K^A} */
+    double EG[4];          /* scalar: E_G per field; U(1): {E_G^phi, E_G^A} */
+    double EV[4];          /* scalar: {<(lam/p)|phi|^p>, <(q/2)phi^2chi^2>}; U(1): {<V>} */
+    double rho;            /* total energy density E_K + E_G + E_V (program units) */
+    double w;              /* equation of state p/rho */
+    double hubble_violation; /* Delta_e = |b^2 - rhs| / rhs of the Hubble constraint */
+    double gauss_violation;  /* U(1): Delta_g = rms(G)/sqrt(<lhs^2> + <rhs^2>) */
+    double reserved[4];
+} cl_means;
+
+typedef struct cl_lattice cl_lattice;
+
+/* Status string of a code; never NULL. */
+const char* cl_status_str(cl_status s);
+/* Reason of the last failure on this handle (or of the last failed
+ * lattice_init when h is NULL); never NULL. */
+const char* cl_last_error(const cl_lattice* h);
+
+/* Create a lattice: allocate device memory, draw the initial conditions of
+ * section 7 on the device (Rayleigh moduli and uniform phases from
+ * Philox4x32-10 keyed by init->seed, inverse DFT by cuFFT), fix b from the
+ * Hubble constraint b^2 = (1/3)(f_star/m_p)^2 a^{2(alpha+1)} (E_K+E_G+E_V)
+ * (sections 4.1, 4.2.3), and, for U(1), set A = 0 and the electric momenta
+ * from the lattice Gauss law (section 7.2).  cuda_stream is a cudaStream_t
+ * or NULL.  Rejects dt beyond the linear stability bound of the integrator
+ * (omega_max dt < 2 for LF/VV2, < 1.5734 for VV4) unless grid->force_dt.
+ * On failure *out is NULL and cl_last_error(NULL) says why. */
+cl_status lattice_init(const cl_model* model, const cl_grid* grid, const cl_init* init, void* cuda_stream,
+                       cl_lattice** out);
+
+/* Advance nsteps full time steps with the handle's integrator (sections
+ * 4.2.1, 4.2.3, 4.3.2, 5.3.1): fused drift / stencil / kick / reduction
+ * passes on the device with the Friedmann update between passes, replayed as
+ * CUDA graphs.  Asynchronous on the handle's stream.  nsteps >= 0. */
+cl_status lattice_evolve(cl_lattice* h, int64_t nsteps);
+
+/* Volume averages, energies, w, Delta_e and (U(1)) Delta_g at the current
+ * time; synchronizes the stream.  For CL_INT_LF the momenta live half a step
+ * behind the fields, so EK is the kinetic energy at t - dt/2. */
+cl_status lattice_measure_means(cl_lattice* h, cl_means* out);
+
+/* Number of spectrum bins, floor(sqrt(3) N/2) + 1. */
+int32_t lattice_spectrum_bins(const cl_lattice* h);
+
+/* Power spectrum of section 3.1 / 4.4.2 / 5.4.2,
+ * Delta(k) = k^3/(2 pi^2) (dx/N)^3 <|f(n~)|^2>_R, averaged over the modes of
+ * each shell |n~| in [b, b+1), with k_b = k_IR times the mean |n~| of the
+ * shell.  field: scalar field index, or 0 for the complex U(1) scalar (Re and
+ * Im summed).  what: 0 the field, 1 its momentum.  k, Delta (double) and
+ * counts (int64) have lattice_spectrum_bins() entries (host memory).
+ * Synchronizes the stream. */
+cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, double* k, double* Delta,
+                                   int64_t* counts);
+
+/* Array indices of get/set: scalar models: 0..n-1 the fields, 4..4+n-1
+ * their momenta.  U(1): 0 Re phi, 1 Im phi, 4 Re pi, 5 Im pi, 8..10 the link
+ * angles theta_i = e dx A_i (V_i = exp(-i theta_i)), 12..14 the electric
+ * momenta piA_i. */
+#define CL_FIELD(i) (i)
+#define CL_MOMENTUM(i) (4 + (i))
+#define CL_LINK(i) (8 + (i))
+#define CL_EMOMENTUM(i) (12 + (i))
+
+/* Copy the full array `which` (N^3 doubles) to dst: host memory when
+ * on_device = 0, device memory of the handle's device otherwise.
+ * Synchronizes the stream. */
+cl_status lattice_get_field(cl_lattice* h, int32_t which, double* dst, int32_t on_device);
+
+/* Overwrite array `which` from src (N^3 doubles, host or device).  The
+ * handle splits it into its mean and fluctuation.  Ordered on the stream. */
+cl_status lattice_set_field(cl_lattice* h, int32_t which, const double* src, int32_t on_device);
+
+/* Set the background: scale factor a and b = a'.  A NaN b is replaced by
+ * the positive root of the Hubble constraint of the current fields.  Marks
+ * the state as synchronized (momenta at the fields' time). */
+cl_status lattice_set_background(cl_lattice* h, double a, double b, double t);
+
+/* Checkpoint: raw arrays, means and background with a header and a CRC-32;
+ * restore refuses files of another geometry, model or precision, or whose
+ * CRC does not match (CL_ERR_IO).  Continuation after restore is bitwise
+ * identical to uninterrupted evolution. */
+cl_status lattice_save(cl_lattice* h, const char* path);
+cl_status lattice_restore(cl_lattice* h, const char* path);
+
+/* Free everything the handle owns.  NULL is accepted. */
+cl_status lattice_destroy(cl_lattice* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CL_LATTICE_H */

@@ -1,0 +1,224 @@
+"""Python binding of libcl_lattice.so (include/cl_lattice.h).
+
+Argument marshalling only: every step of the lattice method runs in the CUDA
+library.  There is no CPU fallback; if the library is missing this module
+raises at load time.  PyTorch is used only to hand over CUDA streams and
+device buffers (torch tensors as sources/destinations of fields).
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# --- status codes and enums (mirror include/cl_lattice.h) ---
+CL_OK, CL_ERR_ARG, CL_ERR_CUDA, CL_ERR_OOM, CL_ERR_UNSTABLE_DT, CL_ERR_NONFINITE, CL_ERR_TIMEOUT, \
+    CL_ERR_STATE, CL_ERR_IO = range(9)
+CL_MODEL_SCALAR, CL_MODEL_U1 = 0, 1
+CL_INT_LF, CL_INT_VV2, CL_INT_VV4, CL_INT_VV6, CL_INT_VV8, CL_INT_VV10 = range(6)
+CL_FP64, CL_FP32 = 0, 1
+INTEGRATORS = {"lf": CL_INT_LF, "vv2": CL_INT_VV2, "vv4": CL_INT_VV4, "vv6": CL_INT_VV6, "vv8": CL_INT_VV8,
+               "vv10": CL_INT_VV10}
+
+
+def FIELD(i):
+    return i
+
+
+def MOMENTUM(i):
+    return 4 + i
+
+
+def LINK(i):
+    return 8 + i
+
+
+def EMOMENTUM(i):
+    return 12 + i
+
+
+class cl_model(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_fields", C.c_int32), ("pexp", C.c_int32), ("reserved", C.c_int32),
+                ("alpha", C.c_double), ("fstar_over_mp", C.c_double), ("omega_over_fstar", C.c_double),
+                ("lam", C.c_double), ("q", C.c_double), ("vev2", C.c_double), ("gauge_e", C.c_double)]
+
+
+class cl_grid(C.Structure):
+    _fields_ = [("N", C.c_int32), ("integrator", C.c_int32), ("precision", C.c_int32), ("force_dt", C.c_int32),
+                ("kIR", C.c_double), ("dt", C.c_double)]
+
+
+class cl_init(C.Structure):
+    _fields_ = [("phi0", C.c_double * 4), ("dphi0", C.c_double * 4), ("seed", C.c_uint64),
+                ("spectrum", C.c_int32), ("reserved", C.c_int32), ("fluct_scale", C.c_double), ("a0", C.c_double)]
+
+
+class cl_means(C.Structure):
+    _fields_ = [("t", C.c_double), ("a", C.c_double), ("b", C.c_double), ("step", C.c_int64),
+                ("mean", C.c_double * 4), ("mean2", C.c_double * 4), ("var", C.c_double * 4),
+                ("mean_pi", C.c_double * 4), ("EK", C.c_double * 4), ("EG", C.c_double * 4),
+                ("EV", C.c_double * 4), ("rho", C.c_double), ("w", C.c_double),
+                ("hubble_violation", C.c_double), ("gauss_violation", C.c_double), ("reserved", C.c_double * 4)]
+
+
+SYMBOLS = ["cl_status_str", "cl_last_error", "lattice_init", "lattice_evolve", "lattice_measure_means",
+           "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_get_field", "lattice_set_field",
+           "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy"]
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libcl_lattice.so (building it in-tree if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError("libcl_lattice.so is not built; run __graft_entry__.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    vp, d, i32, i64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64
+    pd = C.POINTER(C.c_double)
+    sig = {
+        "cl_status_str": ([C.c_int], C.c_char_p),
+        "cl_last_error": ([vp], C.c_char_p),
+        "lattice_init": ([C.POINTER(cl_model), C.POINTER(cl_grid), C.POINTER(cl_init), vp, C.POINTER(vp)], C.c_int),
+        "lattice_evolve": ([vp, i64], C.c_int),
+        "lattice_measure_means": ([vp, C.POINTER(cl_means)], C.c_int),
+        "lattice_spectrum_bins": ([vp], i32),
+        "lattice_measure_spectrum": ([vp, i32, i32, pd, pd, C.POINTER(C.c_int64)], C.c_int),
+        "lattice_get_field": ([vp, i32, vp, i32], C.c_int),
+        "lattice_set_field": ([vp, i32, vp, i32], C.c_int),
+        "lattice_set_background": ([vp, d, d, d], C.c_int),
+        "lattice_save": ([vp, C.c_char_p], C.c_int),
+        "lattice_restore": ([vp, C.c_char_p], C.c_int),
+        "lattice_destroy": ([vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+class LatticeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (load().cl_status_str(status).decode(), msg))
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != CL_OK:
+        raise LatticeError(status, load().cl_last_error(handle).decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dev_ptr(t):
+    """(pointer, on_device) of a float64 buffer: numpy array or torch tensor."""
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.float64 and t.flags.c_contiguous
+        return C.c_void_p(t.ctypes.data), 0
+    import torch  # only for device buffers
+    assert t.dtype == torch.float64 and t.is_contiguous()
+    return C.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0
+
+
+def make_model(kind=CL_MODEL_SCALAR, n_fields=1, pexp=2, alpha=0.0, fstar_over_mp=0.0, omega_over_fstar=1.0,
+               lam=1.0, q=0.0, vev2=1.0, gauge_e=1.0):
+    return cl_model(kind, n_fields, pexp, 0, alpha, fstar_over_mp, omega_over_fstar, lam, q, vev2, gauge_e)
+
+
+def make_grid(N, kIR, dt, integrator=CL_INT_VV2, precision=CL_FP64, force_dt=False):
+    if isinstance(integrator, str):
+        integrator = INTEGRATORS[integrator]
+    return cl_grid(N, integrator, precision, 1 if force_dt else 0, kIR, dt)
+
+
+def make_init(phi0=(0, 0, 0, 0), dphi0=(0, 0, 0, 0), seed=0, spectrum=1, fluct_scale=1.0, a0=1.0):
+    p = (C.c_double * 4)(*(list(phi0) + [0.0] * (4 - len(phi0))))
+    dp = (C.c_double * 4)(*(list(dphi0) + [0.0] * (4 - len(dphi0))))
+    return cl_init(p, dp, seed, spectrum, 0, fluct_scale, a0)
+
+
+class Lattice:
+    """Owner of one cl_lattice handle (see include/cl_lattice.h for semantics)."""
+
+    def __init__(self, model, grid, init, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.lattice_init(C.byref(model), C.byref(grid), C.byref(init), _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self.model, self.grid, self.init = model, grid, init
+        self.N = grid.N
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lattice_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def evolve(self, nsteps):
+        _check(load().lattice_evolve(self.h, int(nsteps)), self.h)
+
+    def measure_means(self):
+        m = cl_means()
+        _check(load().lattice_measure_means(self.h, C.byref(m)), self.h)
+        out = {}
+        for name, _ in cl_means._fields_:
+            v = getattr(m, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+    def spectrum(self, field=0, what=0):
+        nb = load().lattice_spectrum_bins(self.h)
+        k = np.zeros(nb)
+        D = np.zeros(nb)
+        c = np.zeros(nb, dtype=np.int64)
+        _check(load().lattice_measure_spectrum(self.h, field, what, k.ctypes.data_as(C.POINTER(C.c_double)),
+                                               D.ctypes.data_as(C.POINTER(C.c_double)),
+                                               c.ctypes.data_as(C.POINTER(C.c_int64))), self.h)
+        return k, D, c
+
+    def get_field(self, which, out=None):
+        N = self.N
+        if out is None:
+            out = np.zeros((N, N, N))
+        p, dev = _dev_ptr(out)
+        _check(load().lattice_get_field(self.h, which, p, dev), self.h)
+        return out
+
+    def set_field(self, which, src):
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.float64)
+        p, dev = _dev_ptr(src)
+        _check(load().lattice_set_field(self.h, which, p, dev), self.h)
+
+    def set_background(self, a, b=math.nan, t=0.0):
+        _check(load().lattice_set_background(self.h, a, b, t), self.h)
+
+    def save(self, path):
+        _check(load().lattice_save(self.h, path.encode()), self.h)
+
+    def restore(self, path):
+        _check(load().lattice_restore(self.h, path.encode()), self.h)

@@ -1,0 +1,217 @@
+// Internal declarations of the GB300 lattice library (not part of the ABI).
+//
+// State layout in HBM: every real field is split into a double-precision
+// homogeneous mean (held in DevState) and a fluctuation array of N^3 values
+// of type T (float or double), SoA, site index (z*N + y)*N + x.  Stencil
+// passes read one copy of the arrays and write the other (ping-pong), so a
+// pass never overwrites a value a neighbouring block still has to read.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cl_lattice.h"
+
+namespace cl {
+
+constexpr int kMaxComp = 4;   // real components per sector (scalar fields, or Re/Im)
+constexpr int kMaxSums = 48;  // reductions per pass
+constexpr int kMaxBlocks = 4096;
+
+// Background, means and bookkeeping shared by all passes; lives in device
+// memory and is updated by the last block of each pass (all FP64).
+struct DevState {
+    double a;        // scale factor at the fields' time (where the next kick is evaluated)
+    double b;        // a' (synchronized for VV; at the momenta's half step for LF)
+    double bh;       // b_{1/2} carried between the two half kicks of a VV sub-step
+    double t;        // program time of the fields
+    double cd;       // drift coefficient of the next pass for scalar fields: w dt a_{1/2}^{-(3-alpha)}
+    double cdA;      // drift coefficient of the next pass for link angles: e dx w dt a_{1/2}^{-(1-alpha)}
+    double A1, A3, Am;  // a^{1+alpha}, a^{3+alpha}, a^{alpha-1} at the kick
+    double EKm, EKAm;   // leapfrog: kinetic energies (field, gauge) at the previous half step
+    double ahm;         // leapfrog: a at the previous half step
+    double EGm, EVm, EGAm;  // leapfrog: gradient/potential/magnetic energies at the previous integer step
+    double phibar[kMaxComp], pibar[kMaxComp];  // homogeneous means
+    double sphi[kMaxComp], spi[kMaxComp];      // pending shifts: subtract from the stored arrays on read
+    double E[8];        // energies of the last pass: scalar {EK0,EK1,EG0,EG1,EV1,EV2}; U(1) {EKp,EGp,EV,EKA,EGA}
+    double sums[kMaxSums];  // normalized sums of the last pass
+    double hc;          // Hubble-constraint violation of the last synchronized point
+    double gauss[3];    // <G^2>, <lhs^2>, <rhs^2> of the last Gauss check
+    long long step;
+    int error;          // nonzero: a reduction saw NaN/Inf (evolution stops)
+    int staggered;      // leapfrog momenta live half a step behind the fields
+};
+
+// What the last block does with the sums of a pass.
+enum PassKind : int {
+    PK_VV_FIRST = 0,   // first kick of a VV evolve call (no drift before it)
+    PK_VV_MID = 1,     // merged kick between two VV sub-steps
+    PK_VV_LAST = 2,    // closing half kick
+    PK_LF = 3,         // leapfrog: kick, Friedmann fixed point, next drift
+    PK_LF_PREPARE = 4, // backward half kick starting the leapfrog
+    PK_MEASURE = 5,    // reductions only
+    PK_INIT_B = 6,     // reductions only, then b from the Hubble constraint
+    PK_LF_EKM = 7      // reductions only: E_K of the half-step-behind momenta
+};
+
+struct PassInfo {
+    int kind;
+    int pad;
+    double dt;      // time step
+    double wc, wn;  // weight of the sub-step just completed / of the next one
+    double h1, h;   // kick of the energy evaluation / of the stored momenta
+};
+
+struct ModelConst {
+    int kind, nf, pexp, N;
+    double alpha, fmp2, lam, q, vev2, e, kappa, dx, idx2;
+};
+
+// Per-lattice device resources.
+struct Buffers {
+    void* f[2][16];    // ping-pong copies of every stored array (type T)
+    int narr;
+    DevState* st;
+    double* partials;  // per-block partial sums
+    unsigned int* counter;
+};
+
+// Tile geometry of the stencil passes.
+struct Geometry {
+    int N, V, BX, BY, ZC;
+    int ntx, nty, ntz, ntiles, grid, threads;
+    size_t smem;
+};
+
+// Host-side handle.
+struct Lattice {
+    ModelConst mc;
+    cl_grid grid;
+    cl_init init;
+    int integ;
+    int prec;  // CL_FP64 / CL_FP32
+    size_t tsize;
+    cudaStream_t stream;
+    Buffers buf;
+    int cur;   // which ping-pong copy holds the current state
+    Geometry geo;
+    std::vector<double> weights;
+    long long steps_done;
+    std::string err;
+    // graphs cached by (steps, parity)
+    struct G { long long steps; int parity; int end_parity; cudaGraphExec_t exec; };
+    std::vector<G> graphs;
+    cufftHandle plan_c2r, plan_r2c;
+    bool plans;
+    double* work;      // FP64 scratch of N^3 (conversion, spectra)
+    void* cwork;       // complex FP64 scratch N*N*(N/2+1) (x2)
+    double* bins;      // spectrum accumulators
+    int sm_count;
+    cudaStream_t cstream;  // private stream used only to record graphs
+    bool staggered;        // host mirror of DevState::staggered
+};
+
+// ---- device helpers -------------------------------------------------------
+
+template <typename T> struct VecT;
+template <> struct VecT<float> { using type = float4; static constexpr int V = 4; };
+template <> struct VecT<double> { using type = double2; static constexpr int V = 2; };
+
+__device__ __forceinline__ void vload(const float* p, float (&r)[4]) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+}
+__device__ __forceinline__ void vload(const double* p, double (&r)[2]) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    r[0] = v.x; r[1] = v.y;
+}
+__device__ __forceinline__ void vstore(float* p, const float (&r)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void vstore(double* p, const double (&r)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+}
+__device__ __forceinline__ void vstore_cs(float* p, const float (&r)[4]) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(r[0], r[1], r[2], r[3]));
+}
+__device__ __forceinline__ void vstore_cs(double* p, const double (&r)[2]) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(r[0], r[1]));
+}
+
+// Kahan-compensated accumulator (Kahan 1965) in the kernel's precision.
+template <typename T> struct Kahan {
+    T s, c;
+    __device__ __forceinline__ void init() { s = T(0); c = T(0); }
+    __device__ __forceinline__ void add(T x) {
+        T y = x - c;
+        T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) - double(c); }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the nl existing lanes of a possibly partial warp (nl = 1..32);
+// the result is valid in lane 0.  Shuffles name only existing lanes.
+template <typename T> __device__ __forceinline__ T partial_warp_sum(T v, int lane, int nl) {
+    const unsigned mask = nl >= 32 ? 0xffffffffu : ((1u << nl) - 1u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T t = __shfl_down_sync(mask, v, o);
+        if (lane + o < nl) v += t;
+    }
+    return v;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC11 2011): ten rounds of
+// (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),
+// with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint32_t lo0 = M0 * c[0], hi0 = __umulhi(M0, c[0]);
+        const uint32_t lo1 = M1 * c[2], hi1 = __umulhi(M1, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+// ---- host entry points between translation units --------------------------
+
+// scalar_pass.cu
+cudaError_t scalar_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s);
+cudaError_t scalar_launch_drift(Lattice* L, int cur, cudaStream_t s);  // leapfrog closing drift (in place)
+void scalar_geometry(Lattice* L);
+
+// u1_pass.cu
+cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s);
+cudaError_t u1_launch_drift(Lattice* L, int cur, cudaStream_t s);
+cudaError_t u1_launch_gauss(Lattice* L, int cur, cudaStream_t s);
+void u1_geometry(Lattice* L);
+
+// ic.cu
+cl_status ic_generate(Lattice* L);
+cudaError_t launch_finish_drift(Lattice* L, cudaStream_t s);
+
+// fields.cu
+cudaError_t launch_get_field(Lattice* L, int which, double* dst, cudaStream_t s);
+cudaError_t launch_set_field(Lattice* L, int which, const double* src, cudaStream_t s);
+cudaError_t launch_spectrum(Lattice* L, int slot, int accumulate, cudaStream_t s);
+int spectrum_bins(int N);
+
+int array_count(const ModelConst& mc);
+int array_slot(const ModelConst& mc, int which);  // ABI index -> storage slot, -1 if invalid
+
+}  // namespace cl

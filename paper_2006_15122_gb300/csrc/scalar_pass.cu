@@ -1,0 +1,585 @@
+// Fused scalar-sector pass for sm_103a: drift -> 7-point Laplacian -> kick ->
+// volume reductions, one HBM read and one HBM write of every array per pass.
+//
+// Method (paper sections 4.2.1, 4.2.3, 4.3.2, Hamiltonian form):
+//   phi_i' = a^{-(3-alpha)} pi_i,
+//   pi_i'  = K_i = a^{1+alpha} L[phi_i] - a^{3+alpha} dV/dphi_i,
+//   L[f](n) = sum_k (f(n+k) + f(n-k) - 2 f(n)) / dx^2,
+//   b' = K_a = (1/3)(f*/m_p)^2 a^{1+2alpha} [(alpha-2) E_K + alpha E_G + (alpha+1) E_V],
+//   E_K = sum_i <pi_i^2>/(2a^6), E_G = sum_{i,k} <(D_k^+ phi_i)^2>/(2a^2), E_V = <V>,
+// with V = (lam/p)|phi|^p + (q/2) phi^2 chi^2 (section 8.1).
+//
+// One pass applies the drift that the previous pass prepared (its coefficient
+// needs the previous pass's volume averages through a(eta)), then the kick
+// K evaluated on the drifted fields, and reduces in the same sweep the sums
+// that give E_K, E_G, E_V and the means.  Adjacent half kicks of consecutive
+// velocity-Verlet sub-steps are merged into one kick; the kinetic energy of
+// the synchronized momenta (first half kick only) is formed in registers.
+// The last block to finish sums the per-block partials in a fixed order and
+// advances a, b and the homogeneous means in FP64 (last-block-done pattern),
+// so consecutive passes need no host round trip.
+//
+// Mean/fluctuation split: each field is phibar (FP64, in DevState) + delta
+// (array of T).  The kick of the mean is -a^{3+alpha} V'(phibar) in FP64; the
+// array gets a^{1+alpha} L[delta] - a^{3+alpha} [V'(phibar+delta) - V'(phibar)]
+// written as a polynomial in delta, so no large number is ever subtracted
+// in FP32.  The volume mean that the fluctuations pick up is moved into
+// phibar/pibar after every pass (a pending shift subtracted on the next
+// read), which keeps phi = phibar + delta exact.
+//
+// Tiling: a block of BX x BY threads owns a tile of BX*V x BY sites in x-y
+// (V = 4 floats or 2 doubles per thread, 16-byte accesses) and marches ZC
+// planes in z; z-neighbours live in registers, x-y neighbours of the drifted
+// plane in shared memory (double-buffered, one barrier per plane), halo
+// cells are loaded by the tile-edge threads.  Loads of plane z+2 and of the
+// halo of plane z+1 are issued before the compute of plane z.  The grid is
+// persistent (grid-stride over tiles, y-tiles fastest so that y-halos are
+// L2 hits of concurrently running tiles).
+#include <math.h>
+
+#include "cl_internal.cuh"
+
+namespace cl {
+
+template <typename T, int P> struct Power;
+// (lam/p)|phi|^p: lam * [(fb+d)^{p-1} - fb^{p-1}] and (1/p)[(fb+d)^p - fb^p] as polynomials in d
+template <typename T> struct Power<T, 2> {
+    static __device__ __forceinline__ T dforce(T fb, T d) { return d; }
+    static __device__ __forceinline__ T dvalue(T fb, T d) { return d * (fb + T(0.5) * d); }
+};
+template <typename T> struct Power<T, 4> {
+    static __device__ __forceinline__ T dforce(T fb, T d) { return d * (T(3) * fb * fb + d * (T(3) * fb + d)); }
+    static __device__ __forceinline__ T dvalue(T fb, T d) {
+        return T(0.25) * d * (T(4) * fb * fb * fb + d * (T(6) * fb * fb + d * (T(4) * fb + d)));
+    }
+};
+template <typename T> struct Power<T, 6> {
+    static __device__ __forceinline__ T dforce(T fb, T d) {
+        const T f2 = fb * fb;
+        return d * (T(5) * f2 * f2 + d * (T(10) * f2 * fb + d * (T(10) * f2 + d * (T(5) * fb + d))));
+    }
+    static __device__ __forceinline__ T dvalue(T fb, T d) {
+        const T f2 = fb * fb;
+        return d * (f2 * f2 * fb + d * (T(2.5) * f2 * f2 + d * (T(10.0 / 3.0) * f2 * fb +
+                                                              d * (T(2.5) * f2 + d * (fb + d * T(1.0 / 6.0))))));
+    }
+};
+
+struct ScalarArgs {
+    const void* in[4];  // slots 0..nf-1: delta phi, nf..2nf-1: delta pi (source copy)
+    void* out[4];       // same slots, destination copy
+    DevState* st;
+    double* partials;
+    unsigned int* counter;
+    ModelConst mc;
+    Geometry geo;
+    PassInfo pi;
+    int write;
+};
+
+// ------------------------------------------------------------------ finish
+
+__device__ double pow_ab(double a, double b) { return pow(a, b); }
+
+__device__ void potential_bar(const ModelConst& mc, const double* fb, double* V1, double* V2, double* dV) {
+    const double f0 = fb[0], f1 = mc.nf > 1 ? fb[1] : 0.0;
+    double ap = 1.0;
+    for (int i = 0; i < mc.pexp - 2; ++i) ap *= fabs(f0);
+    *V1 = mc.lam / mc.pexp * ap * f0 * f0;
+    *V2 = mc.nf > 1 ? 0.5 * mc.q * f0 * f0 * f1 * f1 : 0.0;
+    dV[0] = mc.lam * ap * f0 + (mc.nf > 1 ? mc.q * f1 * f1 * f0 : 0.0);
+    dV[1] = mc.nf > 1 ? mc.q * f0 * f0 * f1 : 0.0;
+}
+
+__device__ double Ka_of(const ModelConst& mc, double a, double EK, double EG, double EV) {
+    return mc.fmp2 / 3.0 * pow(a, 1.0 + 2.0 * mc.alpha) *
+           ((mc.alpha - 2.0) * EK + mc.alpha * EG + (mc.alpha + 1.0) * EV);
+}
+
+__device__ double hubble_rhs(const ModelConst& mc, double a, double Etot) {
+    return mc.fmp2 / 3.0 * pow(a, 2.0 * (mc.alpha + 1.0)) * Etot;
+}
+
+__device__ void set_kick_powers(DevState* st, const ModelConst& mc, double a) {
+    st->A1 = pow(a, 1.0 + mc.alpha);
+    st->A3 = pow(a, 3.0 + mc.alpha);
+    st->Am = pow(a, mc.alpha - 1.0);
+}
+
+// Scalar update of the last block (thread 0).  tot[] are sums / N^3.
+__device__ void scalar_finish(DevState* st, const double* tot, const ModelConst& mc, const PassInfo& pi, bool single) {
+    const int nf = mc.nf;
+    const double a = st->a;
+    double V1, V2, dV[2];
+    potential_bar(mc, st->phibar, &V1, &V2, dV);
+    double Kbar[2] = {0, 0}, EK[2] = {0, 0}, EG[2] = {0, 0}, S = 0;
+    const double a2 = a * a, a6 = a2 * a2 * a2;
+    for (int f = 0; f < nf; ++f) {
+        Kbar[f] = -st->A3 * dV[f];
+        const double pr = st->pibar[f] + pi.h1 * Kbar[f];
+        const double s2 = pr * pr + 2.0 * pr * tot[6 * f + 2] + tot[6 * f + 3];
+        S += s2;
+        EK[f] = s2 / (2.0 * a6);
+        EG[f] = tot[6 * f + 4] * mc.idx2 / (2.0 * a2);
+    }
+    const double EV1 = V1 + tot[6 * nf], EV2 = V2 + tot[6 * nf + 1];
+    const double EKt = EK[0] + EK[1], EGt = EG[0] + EG[1], EVt = EV1 + EV2;
+    st->E[0] = EK[0]; st->E[1] = EK[1]; st->E[2] = EG[0]; st->E[3] = EG[1]; st->E[4] = EV1; st->E[5] = EV2;
+    for (int s = 0; s < 6 * nf + 2 && s < kMaxSums; ++s) st->sums[s] = tot[s];
+    if (!isfinite(EKt + EGt + EVt)) { st->error = CL_ERR_NONFINITE; return; }
+
+    const int kind = pi.kind;
+    if (kind == PK_MEASURE) {
+        if (st->staggered) {  // scheme III Hubble constraint at the half step behind the fields
+            const double rhs = hubble_rhs(mc, st->ahm, st->EKm + 0.5 * (st->EGm + EGt) + 0.5 * (st->EVm + EVt));
+            st->hc = rhs > 0 ? fabs(st->b * st->b - rhs) / rhs : 0.0;
+        } else {
+            const double rhs = hubble_rhs(mc, a, EKt + EGt + EVt);
+            st->hc = rhs > 0 ? fabs(st->b * st->b - rhs) / rhs : 0.0;
+        }
+        return;
+    }
+    if (kind == PK_INIT_B) {
+        st->b = mc.fmp2 > 0 ? sqrt(fmax(hubble_rhs(mc, a, EKt + EGt + EVt), 0.0)) : 0.0;
+        st->hc = 0.0;
+        return;
+    }
+    if (kind == PK_LF_EKM) {  // E_K of the momenta half a step behind
+        const double ah6 = pow(st->ahm, 6.0);
+        st->EKm = S / (2.0 * ah6);
+        return;
+    }
+
+    double bsync = st->b;
+    if (kind == PK_VV_MID || kind == PK_VV_LAST) {
+        bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
+        const double rhs = hubble_rhs(mc, a, EKt + EGt + EVt);
+        st->hc = rhs > 0 ? fabs(bsync * bsync - rhs) / rhs : 0.0;
+    }
+    double bnext = 0.0, anew = a, ah = a;
+    if (kind == PK_VV_FIRST || kind == PK_VV_MID) {
+        bnext = bsync + 0.5 * pi.wn * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
+        st->bh = bnext;
+        anew = a + pi.wn * pi.dt * bnext;
+        ah = 0.5 * (a + anew);
+    } else if (kind == PK_VV_LAST) {
+        st->b = bsync;
+    } else if (kind == PK_LF) {
+        // Scheme III: b_{+1/2} = b_{-1/2} + dt K_a[a, (E_K(-1/2)+E_K(+1/2))/2, E_G, E_V],
+        // E_K(+1/2) = S / (2 a_{+1/2}^6), a_{+1/2} = a + dt b_{+1/2}/2: fixed point.
+        if (st->staggered && st->ahm > 0) {
+            const double rhs = hubble_rhs(mc, st->ahm, st->EKm + 0.5 * (st->EGm + EGt) + 0.5 * (st->EVm + EVt));
+            st->hc = rhs > 0 ? fabs(st->b * st->b - rhs) / rhs : 0.0;
+        }
+        double bp = st->b;
+        for (int it = 0; it < 100; ++it) {
+            const double ahh = a + 0.5 * pi.dt * bp;
+            const double EKp = S / (2.0 * pow(ahh, 6.0));
+            const double bn = st->b + pi.dt * Ka_of(mc, a, 0.5 * (st->EKm + EKp), EGt, EVt);
+            const double d = fabs(bn - bp);
+            bp = bn;
+            if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
+        }
+        anew = a + pi.dt * bp;
+        ah = 0.5 * (a + anew);
+        st->EKm = S / (2.0 * pow(ah, 6.0));
+        st->b = bp;
+        st->ahm = ah;
+        st->EGm = EGt;
+        st->EVm = EVt;
+    } else if (kind == PK_LF_PREPARE) {
+        const double bm = st->b - 0.5 * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
+        st->b = bm;
+        st->ahm = a - 0.5 * pi.dt * bm;
+        st->EGm = EGt;
+        st->EVm = EVt;
+        st->staggered = 1;
+    }
+    // kick of the means, then move the fluctuations' volume mean into them; the
+    // shift is rounded to the arrays' precision so that the FP64 means receive
+    // exactly what the arrays give up on their next read
+    for (int f = 0; f < nf; ++f) {
+        st->pibar[f] += pi.h * Kbar[f];
+        double sf = tot[6 * f + 0], sp = tot[6 * f + 5];
+        if (single) { sf = (double)(float)sf; sp = (double)(float)sp; }
+        st->sphi[f] = sf;
+        st->spi[f] = sp;
+        st->phibar[f] += sf;
+        st->pibar[f] += sp;
+    }
+    // prepare the drift of the next pass
+    double cd = 0.0, dtn = 0.0;
+    if (kind == PK_VV_FIRST || kind == PK_VV_MID) { cd = pi.wn * pi.dt * pow(ah, -(3.0 - mc.alpha)); dtn = pi.wn * pi.dt; }
+    if (kind == PK_LF) { cd = pi.dt * pow(ah, -(3.0 - mc.alpha)); dtn = pi.dt; }
+    st->cd = cd;
+    if (cd != 0.0) {
+        for (int f = 0; f < nf; ++f) st->phibar[f] += cd * st->pibar[f];
+        st->a = anew;
+        set_kick_powers(st, mc, anew);
+        st->t += dtn;
+    }
+}
+
+// --------------------------------------------------------------- the pass
+
+template <typename T, int NF, int P>
+__global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A) {
+    DevState* st = A.st;
+    if (st->error) return;
+    constexpr int V = VecT<T>::V;
+    constexpr int NS = 6 * NF + 2;
+    const int N = A.geo.N, BX = A.geo.BX, BY = A.geo.BY, ZC = A.geo.ZC;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int W = BX * V + 2 * V;   // shared row: V pad columns each side keep rows 16-byte aligned
+    const int PL = (BY + 2) * W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    // per-warp FP64 accumulators of the per-tile FP32/FP64 thread sums
+    __shared__ double bacc[8][16];
+    const int lin = ty * BX + tx;
+    const int lane = lin & 31, warp = lin >> 5, nwarps = (BX * BY + 31) >> 5;
+    const int nlanes = min(32, BX * BY - 32 * warp);  // lanes of this (possibly partial) warp
+    for (int i = lin; i < 8 * 16; i += BX * BY) (&bacc[0][0])[i] = 0.0;
+
+    const T cd = T(st->cd), A1 = T(st->A1), A3 = T(st->A3);
+    const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(A.mc.idx2);
+    const T lam = T(A.mc.lam), q = T(A.mc.q);
+    T fb[2], sf[2], sp[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        fb[f] = f < NF ? T(st->phibar[f]) : T(0);
+        sf[f] = f < NF ? T(st->sphi[f]) : T(0);
+        sp[f] = f < NF ? T(st->spi[f]) : T(0);
+    }
+    const T P0 = fb[0] * fb[0], C0 = fb[1] * fb[1];
+#define PHI_IN(f) (static_cast<const T*>(A.in[(f)]))
+#define PI_IN(f) (static_cast<const T*>(A.in[NF + (f)]))
+#define PHI_OUT(f) (static_cast<T*>(A.out[(f)]))
+#define PI_OUT(f) (static_cast<T*>(A.out[NF + (f)]))
+
+    // halo role of this thread (BX >= 2 and BY >= 2, so at most one per direction)
+    const bool yhalo = (ty == 0) || (ty == BY - 1);
+    const bool xhalo = (tx == 0) || (tx == BX - 1);
+    const int yh_row = (ty == 0) ? 0 : BY + 1;          // shared row of the y-halo
+    const int xh_col = (tx == 0) ? V - 1 : V + BX * V;  // shared column of the x-halo
+    int it = 0;
+    __syncthreads();
+
+    for (int tile = blockIdx.x; tile < A.geo.ntiles; tile += gridDim.x) {
+        const int tyi = tile % A.geo.nty;
+        const int rr = tile / A.geo.nty;
+        const int txi = rr % A.geo.ntx;
+        const int tzi = rr / A.geo.ntx;
+        const int x = txi * BX * V + tx * V;
+        const int y = tyi * BY + ty;
+        const int z0 = tzi * ZC;
+        const int yh = (ty == 0) ? (y == 0 ? N - 1 : y - 1) : (y == N - 1 ? 0 : y + 1);
+        const int xh = (tx == 0) ? (x == 0 ? N - 1 : x - 1) : (x + V == N ? 0 : x + V);
+        const size_t NN = (size_t)N * N;
+        const size_t row_own = (size_t)y * N + x, row_yh = (size_t)yh * N + x, row_xh = (size_t)y * N + xh;
+        auto zw = [&](int zz) -> int { return zz < 0 ? zz + N : (zz >= N ? zz - N : zz); };
+
+        T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
+        T hyf[NF][V], hyp[NF][V];  // raw y-halo (phi, pi) of the next plane to write
+        T hxf[NF], hxp[NF];        // raw x-halo
+        T ts[NS];                  // this tile's thread sums
+#pragma unroll
+        for (int k = 0; k < NS; ++k) ts[k] = T(0);
+
+        // prologue: planes z0-1, z0, z0+1 and the halo of z0
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T rf[V], rp[V];
+            size_t o = (size_t)zw(z0 - 1) * NN + row_own;
+            vload(PHI_IN(f) + o, rf);
+            vload(PI_IN(f) + o, rp);
+#pragma unroll
+            for (int v = 0; v < V; ++v) fm[f][v] = (rf[v] - sf[f]) + cd * (rp[v] - sp[f]);
+            o = (size_t)z0 * NN + row_own;
+            vload(PHI_IN(f) + o, rf);
+            vload(PI_IN(f) + o, rp);
+#pragma unroll
+            for (int v = 0; v < V; ++v) { pc[f][v] = rp[v] - sp[f]; fc[f][v] = (rf[v] - sf[f]) + cd * pc[f][v]; }
+            o = (size_t)zw(z0 + 1) * NN + row_own;
+            vload(PHI_IN(f) + o, rf);
+            vload(PI_IN(f) + o, rp);
+#pragma unroll
+            for (int v = 0; v < V; ++v) { pn[f][v] = rp[v] - sp[f]; fp[f][v] = (rf[v] - sf[f]) + cd * pn[f][v]; }
+            if (yhalo) {
+                vload(PHI_IN(f) + (size_t)z0 * NN + row_yh, hyf[f]);
+                vload(PI_IN(f) + (size_t)z0 * NN + row_yh, hyp[f]);
+            }
+            if (xhalo) {
+                hxf[f] = __ldg(PHI_IN(f) + (size_t)z0 * NN + row_xh);
+                hxp[f] = __ldg(PI_IN(f) + (size_t)z0 * NN + row_xh);
+            }
+        }
+
+        for (int zz = 0; zz < ZC; ++zz, ++it) {
+            const int z = z0 + zz;
+            T* buf = sm + (size_t)(it & 1) * NF * PL;
+            // (a) drifted plane z into shared memory, with its halo
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                vstore(buf + f * PL + (ty + 1) * W + V + tx * V, fc[f]);
+                if (yhalo) {
+                    T hv[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) hv[v] = (hyf[f][v] - sf[f]) + cd * (hyp[f][v] - sp[f]);
+                    vstore(buf + f * PL + yh_row * W + V + tx * V, hv);
+                }
+                if (xhalo) buf[f * PL + (ty + 1) * W + xh_col] = (hxf[f] - sf[f]) + cd * (hxp[f] - sp[f]);
+            }
+            // (b) halo of plane z+1 and own vectors of plane z+2 in flight during the compute
+            const bool more = (zz + 1 < ZC);
+            const bool next2 = (zz + 2 <= ZC);
+            const size_t o1 = (size_t)zw(z + 1) * NN, o2 = (size_t)zw(z + 2) * NN + row_own;
+            T rf[NF][V], rp[NF][V];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (more && yhalo) {
+                    vload(PHI_IN(f) + o1 + row_yh, hyf[f]);
+                    vload(PI_IN(f) + o1 + row_yh, hyp[f]);
+                }
+                if (more && xhalo) {
+                    hxf[f] = __ldg(PHI_IN(f) + o1 + row_xh);
+                    hxp[f] = __ldg(PI_IN(f) + o1 + row_xh);
+                }
+                if (next2) {
+                    vload(PHI_IN(f) + o2, rf[f]);
+                    vload(PI_IN(f) + o2, rp[f]);
+                }
+            }
+            __syncthreads();
+            // (c) stencil, kick, reductions for the V sites of this thread
+            T lap[NF][V];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T* row = buf + f * PL + (ty + 1) * W + V + tx * V;
+                T up[V], dn[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) { up[v] = row[v - W]; dn[v] = row[v + W]; }
+                const T left = row[-1], right = row[V];
+                T g = T(0);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const T xl = (v == 0) ? left : fc[f][v - 1];
+                    const T xr = (v == V - 1) ? right : fc[f][v + 1];
+                    const T c = fc[f][v];
+                    lap[f][v] = (xl + xr + up[v] + dn[v] + fm[f][v] + fp[f][v] - T(6) * c) * idx2;
+                    const T gx = xr - c, gy = dn[v] - c, gz = fp[f][v] - c;
+                    g += gx * gx + gy * gy + gz * gz;
+                }
+                ts[6 * f + 4] += g;
+            }
+            T pout[NF][V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T d0 = fc[0][v];
+                const T d1 = NF > 1 ? fc[NF > 1 ? 1 : 0][v] : T(0);
+                T F[2];
+                F[0] = lam * Power<T, P>::dforce(fb[0], d0);
+                F[1] = T(0);
+                ts[6 * NF] += lam * Power<T, P>::dvalue(fb[0], d0);
+                if (NF > 1) {
+                    const T dP = d0 * (T(2) * fb[0] + d0), dC = d1 * (T(2) * fb[1] + d1);
+                    F[0] += q * (C0 * d0 + dC * (fb[0] + d0));
+                    F[1] = q * (P0 * d1 + dP * (fb[1] + d1));
+                    ts[6 * NF + 1] += T(0.5) * q * (dP * C0 + P0 * dC + dP * dC);
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T K = A1 * lap[f][v] - A3 * F[f];
+                    const T pr = pc[f][v] + h1 * K;
+                    pout[f][v] = pc[f][v] + h * K;
+                    ts[6 * f + 0] += fc[f][v];
+                    ts[6 * f + 1] += fc[f][v] * fc[f][v];
+                    ts[6 * f + 2] += pr;
+                    ts[6 * f + 3] += pr * pr;
+                    ts[6 * f + 5] += pout[f][v];
+                }
+            }
+            if (A.write) {
+                const size_t o = (size_t)z * NN + row_own;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    vstore_cs(PHI_OUT(f) + o, fc[f]);
+                    vstore_cs(PI_OUT(f) + o, pout[f]);
+                }
+            }
+            // (d) rotate the z queue
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    fm[f][v] = fc[f][v];
+                    fc[f][v] = fp[f][v];
+                    pc[f][v] = pn[f][v];
+                }
+                if (next2) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        pn[f][v] = rp[f][v] - sp[f];
+                        fp[f][v] = (rf[f][v] - sf[f]) + cd * pn[f][v];
+                    }
+                }
+            }
+        }
+        // fold this tile's sums into the warp's FP64 accumulators
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const T v = partial_warp_sum(ts[k], lane, nlanes);
+            if (lane == 0) bacc[warp][k] += double(v);
+        }
+    }
+#undef PHI_IN
+#undef PI_IN
+#undef PHI_OUT
+#undef PI_OUT
+
+    // ---- block reduction (FP64) and last-block finish
+    __syncthreads();
+    if (lin < NS) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += bacc[w][lin];
+        A.partials[(size_t)blockIdx.x * NS + lin] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int last;
+    if (lin == 0) last = (atomicAdd(A.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // fixed-order FP64 Kahan sum of the partials: warp w handles sums w, w+nwarps, ...
+    __shared__ double tot[kMaxSums];
+    const double invV = 1.0 / ((double)N * N * N);
+    for (int s = warp; s < NS; s += nwarps) {
+        double ks = 0.0, kc = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += nlanes) {
+            const double xv = __ldcg(&A.partials[(size_t)b * NS + s]);
+            const double yk = xv - kc, tk = ks + yk;
+            kc = (tk - ks) - yk;
+            ks = tk;
+        }
+        const double r = partial_warp_sum(ks - kc, lane, nlanes);
+        if (lane == 0) tot[s] = r * invV;
+    }
+    __syncthreads();
+    if (lin == 0) {
+        *A.counter = 0u;
+        scalar_finish(st, tot, A.mc, A.pi, sizeof(T) == 4);
+    }
+}
+
+// In-place drift of the leapfrog closing step: delta_phi <- (delta_phi - sphi) + cd (delta_pi - spi).
+template <typename T>
+__global__ void scalar_drift_kernel(T* phi0, T* phi1, const T* pi0, const T* pi1, int nf, size_t n, DevState* st) {
+    if (st->error) return;
+    const T cd = T(st->cd);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int f = 0; f < nf; ++f) {
+        T* ph = f == 0 ? phi0 : phi1;
+        const T* pp = f == 0 ? pi0 : pi1;
+        const T sf = T(st->sphi[f]), sp = T(st->spi[f]);
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            ph[i] = (ph[i] - sf) + cd * (pp[i] - sp);
+    }
+}
+
+// --------------------------------------------------------------- host side
+
+void scalar_geometry(Lattice* L) {
+    Geometry& g = L->geo;
+    const int N = L->mc.N;
+    g.N = N;
+    g.V = (L->prec == CL_FP32) ? 4 : 2;
+    const int nv = N / g.V;
+    int bx = nv < 32 ? nv : 32;
+    while (nv % bx != 0) --bx;
+    g.BX = bx;
+    int by = 256 / g.BX;
+    if (by > N) by = N;
+    while (N % by != 0) --by;
+    g.BY = by;
+    int zc = N < 64 ? N : 64;
+    while (N % zc != 0) --zc;
+    g.ZC = zc;
+    g.ntx = N / (g.BX * g.V);
+    g.nty = N / g.BY;
+    g.ntz = N / g.ZC;
+    g.ntiles = g.ntx * g.nty * g.ntz;
+    g.threads = g.BX * g.BY;
+    const size_t W = (size_t)g.BX * g.V + 2 * g.V;
+    g.smem = 2 * (size_t)L->mc.nf * (g.BY + 2) * W * L->tsize;
+    int per_sm = 1;
+    const void* fn = nullptr;
+    if (L->prec == CL_FP32) {
+        if (L->mc.nf == 1) fn = (const void*)scalar_pass_kernel<float, 1, 2>;
+        else fn = (const void*)scalar_pass_kernel<float, 2, 2>;
+    } else {
+        if (L->mc.nf == 1) fn = (const void*)scalar_pass_kernel<double, 1, 2>;
+        else fn = (const void*)scalar_pass_kernel<double, 2, 2>;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = L->sm_count * per_sm;
+    if (grid > g.ntiles) grid = g.ntiles;
+    if (grid > kMaxBlocks) grid = kMaxBlocks;
+    g.grid = grid;
+}
+
+template <typename T, int NF, int P>
+static cudaError_t launch_t(Lattice* L, const ScalarArgs& A, cudaStream_t s) {
+    const Geometry& g = L->geo;
+    auto fn = scalar_pass_kernel<T, NF, P>;
+    fn<<<g.grid, dim3(g.BX, g.BY), g.smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF>
+static cudaError_t launch_p(Lattice* L, const ScalarArgs& A, cudaStream_t s) {
+    switch (L->mc.pexp) {
+        case 2: return launch_t<T, NF, 2>(L, A, s);
+        case 4: return launch_t<T, NF, 4>(L, A, s);
+        case 6: return launch_t<T, NF, 6>(L, A, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t scalar_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
+    ScalarArgs A;
+    const int nf = L->mc.nf;
+    for (int i = 0; i < 4; ++i) { A.in[i] = nullptr; A.out[i] = nullptr; }
+    for (int i = 0; i < 2 * nf; ++i) {
+        A.in[i] = L->buf.f[src][i];
+        A.out[i] = L->buf.f[dst][i];
+    }
+    A.st = L->buf.st;
+    A.partials = L->buf.partials;
+    A.counter = L->buf.counter;
+    A.mc = L->mc;
+    A.geo = L->geo;
+    A.pi = pi;
+    A.write = write ? 1 : 0;
+    if (L->prec == CL_FP32) return nf == 1 ? launch_p<float, 1>(L, A, s) : launch_p<float, 2>(L, A, s);
+    return nf == 1 ? launch_p<double, 1>(L, A, s) : launch_p<double, 2>(L, A, s);
+}
+
+cudaError_t scalar_launch_drift(Lattice* L, int cur, cudaStream_t s) {
+    const size_t n = (size_t)L->mc.N * L->mc.N * L->mc.N;
+    const int nf = L->mc.nf;
+    void** b = L->buf.f[cur];
+    const int grid = L->sm_count * 8;
+    if (L->prec == CL_FP32)
+        scalar_drift_kernel<float><<<grid, 256, 0, s>>>((float*)b[0], nf > 1 ? (float*)b[1] : nullptr,
+                                                        (const float*)b[nf], nf > 1 ? (const float*)b[nf + 1] : nullptr,
+                                                        nf, n, L->buf.st);
+    else
+        scalar_drift_kernel<double><<<grid, 256, 0, s>>>((double*)b[0], nf > 1 ? (double*)b[1] : nullptr,
+                                                         (const double*)b[nf],
+                                                         nf > 1 ? (const double*)b[nf + 1] : nullptr, nf, n, L->buf.st);
+    return cudaGetLastError();
+}
+
+}  // namespace cl

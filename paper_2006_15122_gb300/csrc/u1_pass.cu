@@ -1,0 +1,416 @@
+// Compact U(1) sector (paper section 5.3): a complex scalar phi with
+// momentum pi = a^{3-alpha} phi' and link angles theta_i = e dx A_i
+// (V_i = exp(-i theta_i)) with electric momenta piA_i = a^{1-alpha} F_0i.
+//
+// Kernels (section 5.3, both derived from one lattice action so that the
+// discrete Gauss law holds exactly):
+//   K_phi  = -a^{3+alpha} (lam/2)(|phi|^2 - v2) phi
+//            + a^{1+alpha} sum_i (V_i phi(n+i) - 2 phi + V_i*(n-i) phi(n-i)) / dx^2
+//   K_A,i  = a^{1+alpha} (2e/dx)(1/kappa) Im[phi*(n) V_i(n) phi(n+i)]
+//            + a^{alpha-1}/(e dx^3) sum_{j!=i} [Im V_ij(n) - Im V_ij(n-j)],
+//   V_ij(n) = V_i(n) V_j(n+i) V_i*(n+j) V_j*(n) = exp(-i theta_ij),
+//   theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n),
+// kappa = (w*/f*)^2.  Drifts (compact staggered leapfrog, section 5.3.1):
+//   phi <- phi + dt a_{1/2}^{-(3-alpha)} pi,
+//   V_i <- exp(-i e dx dt a_{1/2}^{-(1-alpha)} piA_i) V_i  (theta_i += ..., wrapped to [-pi, pi)),
+// the exact exponential of the link drift (unitary for any step).
+// Energies (section 5.4.1): E_K^phi = <|pi|^2>/a^6, E_G^phi = sum_i <|D_i^+ phi|^2>/a^2,
+// E_V = <V>, E_K^A = kappa/(2a^4) sum_i <piA_i^2>,
+// E_G^A = kappa/(a^4 e^2 dx^4) sum_{i<j} <1 - cos theta_ij>.
+//
+// One thread per site with a persistent grid-stride loop; neighbour values
+// come through L1/L2 and are drifted on the fly, so each array is read once
+// from HBM and written once per pass.  The last block does the FP64
+// leapfrog/Friedmann update as in the scalar pass.
+#include <math.h>
+
+#include "cl_internal.cuh"
+
+namespace cl {
+
+struct U1Args {
+    const void* in[10];
+    void* out[10];
+    DevState* st;
+    double* partials;
+    unsigned int* counter;
+    ModelConst mc;
+    PassInfo pi;
+    int write;
+};
+
+constexpr int U1NS = 11;
+
+template <typename T> __device__ __forceinline__ T wrap_angle(T t) {
+    const T twopi = T(6.283185307179586476925287);
+    return t - twopi * rint(t / twopi);
+}
+template <typename T> __device__ __forceinline__ void sc(T x, T* s, T* c);
+template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+__device__ double Ka_u1(const ModelConst& mc, double a, double EKp, double EGp, double EV, double EKA, double EGA) {
+    return mc.fmp2 / 3.0 * pow(a, 2.0 * mc.alpha + 1.0) *
+           ((mc.alpha - 2.0) * EKp + mc.alpha * EGp + (mc.alpha + 1.0) * EV + (mc.alpha - 1.0) * (EKA + EGA));
+}
+
+__device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc, const PassInfo& pi) {
+    const double a = st->a, a2 = a * a, a4 = a2 * a2, a6 = a4 * a2;
+    const double dx4 = mc.dx * mc.dx * mc.dx * mc.dx;
+    const double Sp = tot[6], SA = tot[9];
+    const double EKp = Sp / a6, EGp = tot[7] / a2, EV = tot[8];
+    const double EKA = mc.kappa * SA / (2.0 * a4), EGA = mc.kappa * tot[10] / (a4 * mc.e * mc.e * dx4);
+    st->E[0] = EKp; st->E[1] = EGp; st->E[2] = EV; st->E[3] = EKA; st->E[4] = EGA;
+    for (int s = 0; s < U1NS; ++s) st->sums[s] = tot[s];
+    const double Et = EKp + EGp + EV + EKA + EGA;
+    if (!isfinite(Et)) { st->error = CL_ERR_NONFINITE; return; }
+    auto rhs = [&](double aa, double E) { return mc.fmp2 / 3.0 * pow(aa, 2.0 * (mc.alpha + 1.0)) * E; };
+    const int kind = pi.kind;
+    if (kind == PK_MEASURE) {
+        if (st->staggered) {
+            const double r = rhs(st->ahm, st->EKm + st->EKAm + 0.5 * (st->EGm + EGp) + 0.5 * (st->EVm + EV) +
+                                              0.5 * (st->EGAm + EGA));
+            st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
+        } else {
+            const double r = rhs(a, Et);
+            st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
+        }
+        return;
+    }
+    if (kind == PK_INIT_B) {
+        st->b = mc.fmp2 > 0 ? sqrt(fmax(rhs(a, Et), 0.0)) : 0.0;
+        st->hc = 0.0;
+        return;
+    }
+    if (kind == PK_LF_EKM) {
+        st->EKm = Sp / pow(st->ahm, 6.0);
+        st->EKAm = mc.kappa * SA / (2.0 * pow(st->ahm, 4.0));
+        return;
+    }
+    if (kind == PK_LF_PREPARE) {
+        const double bm = st->b - 0.5 * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
+        st->b = bm;
+        st->ahm = a - 0.5 * pi.dt * bm;
+        st->EGm = EGp; st->EVm = EV; st->EGAm = EGA;
+        st->staggered = 1;
+        st->cd = 0.0;
+        st->cdA = 0.0;
+        return;
+    }
+    // PK_LF: b_{+1/2} with the averaged kinetic energies (fixed point in a_{+1/2})
+    if (st->staggered && st->ahm > 0) {
+        const double r = rhs(st->ahm, st->EKm + st->EKAm + 0.5 * (st->EGm + EGp) + 0.5 * (st->EVm + EV) +
+                                          0.5 * (st->EGAm + EGA));
+        st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
+    }
+    double bp = st->b, ekp = 0, eka = 0;
+    for (int it = 0; it < 100; ++it) {
+        const double ah = a + 0.5 * pi.dt * bp;
+        ekp = Sp / pow(ah, 6.0);
+        eka = mc.kappa * SA / (2.0 * pow(ah, 4.0));
+        const double bn = st->b + pi.dt * Ka_u1(mc, a, 0.5 * (st->EKm + ekp), EGp, EV, 0.5 * (st->EKAm + eka), EGA);
+        const double d = fabs(bn - bp);
+        bp = bn;
+        if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
+    }
+    const double an = a + pi.dt * bp, ah = 0.5 * (a + an);
+    st->EKm = Sp / pow(ah, 6.0);
+    st->EKAm = mc.kappa * SA / (2.0 * pow(ah, 4.0));
+    st->b = bp;
+    st->ahm = ah;
+    st->EGm = EGp; st->EVm = EV; st->EGAm = EGA;
+    st->cd = pi.dt * pow(ah, -(3.0 - mc.alpha));
+    st->cdA = mc.e * mc.dx * pi.dt * pow(ah, -(1.0 - mc.alpha));
+    st->a = an;
+    st->A1 = pow(an, 1.0 + mc.alpha);
+    st->A3 = pow(an, 3.0 + mc.alpha);
+    st->Am = pow(an, mc.alpha - 1.0);
+    st->t += pi.dt;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) u1_pass_kernel(const U1Args A) {
+    DevState* st = A.st;
+    if (st->error) return;
+    const int N = A.mc.N;
+    const T cd = T(st->cd), cdA = T(st->cdA), A1 = T(st->A1), A3 = T(st->A3), Am = T(st->Am);
+    const T h1 = T(A.pi.h1), h = T(A.pi.h);
+    const T dx = T(A.mc.dx), idx = T(1.0 / A.mc.dx), idx2 = T(A.mc.idx2);
+    const T lam = T(A.mc.lam), v2 = T(A.mc.vev2);
+    const T cJ = T(2.0 * A.mc.e / A.mc.dx / A.mc.kappa), cB = T(1.0 / (A.mc.e * A.mc.dx * A.mc.dx * A.mc.dx));
+    (void)dx;
+    const T* PR = static_cast<const T*>(A.in[0]);
+    const T* PIm = static_cast<const T*>(A.in[1]);
+    const T* QR = static_cast<const T*>(A.in[2]);
+    const T* QI = static_cast<const T*>(A.in[3]);
+    const T* TH[3] = {static_cast<const T*>(A.in[4]), static_cast<const T*>(A.in[5]), static_cast<const T*>(A.in[6])};
+    const T* EA[3] = {static_cast<const T*>(A.in[7]), static_cast<const T*>(A.in[8]), static_cast<const T*>(A.in[9])};
+    const size_t n3 = (size_t)N * N * N;
+    double acc[U1NS];
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) acc[s] = 0.0;
+    T ts[U1NS];
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) ts[s] = T(0);
+    int cnt = 0;
+
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+        const int c[3] = {x, y, z};
+        auto at = [&](int dxs, int dys, int dzs) -> size_t {
+            int xx = x + dxs, yy = y + dys, zz = z + dzs;
+            xx = xx < 0 ? xx + N : (xx >= N ? xx - N : xx);
+            yy = yy < 0 ? yy + N : (yy >= N ? yy - N : yy);
+            zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
+            return ((size_t)zz * N + yy) * N + xx;
+        };
+        (void)c;
+        // drifted values
+        auto phr = [&](size_t k) { return __ldg(PR + k) + cd * __ldg(QR + k); };
+        auto phi_ = [&](size_t k) { return __ldg(PIm + k) + cd * __ldg(QI + k); };
+        auto th = [&](int d, size_t k) { return __ldg(TH[d] + k) + cdA * __ldg(EA[d] + k); };
+        const T fr = phr(i), fi = phi_(i);
+        const T pr = __ldg(QR + i), pim = __ldg(QI + i);
+        T t0[3], ea[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { t0[d] = th(d, i); ea[d] = __ldg(EA[d] + i); }
+        // covariant Laplacian, current, gradient energy
+        T lr = T(-6) * fr, li = T(-6) * fi, grad = T(0);
+        T Kj[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int ox = d == 0, oy = d == 1, oz = d == 2;
+            const size_t np = at(ox, oy, oz), nm = at(-ox, -oy, -oz);
+            const T ur0 = phr(np), ui0 = phi_(np);
+            T s, cc;
+            sc<T>(t0[d], &s, &cc);
+            // V_i phi(n+i) = (cos t - i sin t)(ur0 + i ui0)
+            const T ur = cc * ur0 + s * ui0, ui = cc * ui0 - s * ur0;
+            const T tm = th(d, nm);
+            T sm, cm;
+            sc<T>(tm, &sm, &cm);
+            const T wr0 = phr(nm), wi0 = phi_(nm);
+            // V_i*(n-i) phi(n-i) = (cos tm + i sin tm)(wr0 + i wi0)
+            const T wr = cm * wr0 - sm * wi0, wi = cm * wi0 + sm * wr0;
+            lr += ur + wr;
+            li += ui + wi;
+            const T gr = ur - fr, gi = ui - fi;
+            grad += gr * gr + gi * gi;
+            Kj[d] = cJ * (fr * ui - fi * ur);  // (2e/dx)(1/kappa) Im[phi* V_i phi(n+i)]
+        }
+        // plaquettes
+        T mag[3] = {T(0), T(0), T(0)}, eB = T(0);
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii) {
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) {
+                if (jj == ii) continue;
+                const int oix = ii == 0, oiy = ii == 1, oiz = ii == 2;
+                const int ojx = jj == 0, ojy = jj == 1, ojz = jj == 2;
+                // theta_ij(n) and theta_ij(n - j)
+                const T pn = t0[ii] + th(jj, at(oix, oiy, oiz)) - th(ii, at(ojx, ojy, ojz)) - t0[jj];
+                const T pm = th(ii, at(-ojx, -ojy, -ojz)) + th(jj, at(oix - ojx, oiy - ojy, oiz - ojz)) - t0[ii] -
+                             th(jj, at(-ojx, -ojy, -ojz));
+                T sn, cn, smm, cmm;
+                sc<T>(pn, &sn, &cn);
+                sc<T>(pm, &smm, &cmm);
+                // Im V_ij = -sin(theta_ij)
+                mag[ii] += -sn + smm;
+                if (jj > ii) eB += T(1) - cn;
+            }
+        }
+        const T mod2 = fr * fr + fi * fi;
+        const T dv = T(0.5) * lam * (mod2 - v2);
+        const T Kr = -A3 * dv * fr + A1 * lr * idx2, Ki = -A3 * dv * fi + A1 * li * idx2;
+        const T prr = pr + h1 * Kr, pri = pim + h1 * Ki;
+        const T por = pr + h * Kr, poi = pim + h * Ki;
+        T sA = T(0), eo[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const T K = A1 * Kj[d] + Am * cB * mag[d];
+            const T er = ea[d] + h1 * K;
+            eo[d] = ea[d] + h * K;
+            sA += er * er;
+        }
+        ts[0] += fr; ts[1] += fi; ts[2] += fr * fr; ts[3] += fi * fi;
+        ts[4] += prr; ts[5] += pri; ts[6] += prr * prr + pri * pri;
+        ts[7] += grad * idx2;
+        ts[8] += T(0.25) * lam * (mod2 - v2) * (mod2 - v2);
+        ts[9] += sA;
+        ts[10] += eB;
+        if (A.write) {
+            static_cast<T*>(A.out[0])[i] = fr;
+            static_cast<T*>(A.out[1])[i] = fi;
+            static_cast<T*>(A.out[2])[i] = por;
+            static_cast<T*>(A.out[3])[i] = poi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                static_cast<T*>(A.out[4 + d])[i] = wrap_angle(t0[d]);
+                static_cast<T*>(A.out[7 + d])[i] = eo[d];
+            }
+        }
+        if (++cnt == 64) {  // fold into FP64 every 64 sites
+#pragma unroll
+            for (int s = 0; s < U1NS; ++s) { acc[s] += double(ts[s]); ts[s] = T(0); }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) acc[s] += double(ts[s]);
+    (void)idx;
+
+    // block reduction, partials, last block
+    __shared__ double red[8][U1NS];
+    const int lin = threadIdx.x, lane = lin & 31, warp = lin >> 5, nwarps = (blockDim.x + 31) >> 5;
+    const int nlanes = min(32, (int)blockDim.x - 32 * warp);
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) {
+        const double v = partial_warp_sum(acc[s], lane, nlanes);
+        if (lane == 0) red[warp][s] = v;
+    }
+    __syncthreads();
+    if (lin < U1NS) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += red[w][lin];
+        A.partials[(size_t)blockIdx.x * U1NS + lin] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int last;
+    if (lin == 0) last = (atomicAdd(A.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double tot[U1NS];
+    const double invV = 1.0 / (double)n3;
+    for (int s = warp; s < U1NS; s += nwarps) {
+        double ks = 0.0, kc = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += nlanes) {
+            const double xv = __ldcg(&A.partials[(size_t)b * U1NS + s]);
+            const double yk = xv - kc, tk = ks + yk;
+            kc = (tk - ks) - yk;
+            ks = tk;
+        }
+        const double r = partial_warp_sum(ks - kc, lane, nlanes);
+        if (lane == 0) tot[s] = r * invV;
+    }
+    __syncthreads();
+    if (lin == 0) {
+        *A.counter = 0u;
+        u1_finish(st, tot, A.mc, A.pi);
+    }
+}
+
+// Closing drift of the leapfrog (in place): phi += cd pi, theta += cdA piA (wrapped).
+template <typename T>
+__global__ void u1_drift_kernel(T* pr, T* pim, const T* qr, const T* qi, T* t0, T* t1, T* t2, const T* e0,
+                                const T* e1, const T* e2, size_t n, DevState* st) {
+    if (st->error) return;
+    const T cd = T(st->cd), cdA = T(st->cdA);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        pr[i] += cd * qr[i];
+        pim[i] += cd * qi[i];
+        t0[i] = wrap_angle(t0[i] + cdA * e0[i]);
+        t1[i] = wrap_angle(t1[i] + cdA * e1[i]);
+        t2[i] = wrap_angle(t2[i] + cdA * e2[i]);
+    }
+}
+
+// Gauss-law residual G = sum_i D_i^- piA_i - (2e/kappa) Im[phi* pi] (section 5.2), FP64 sums.
+template <typename T>
+__global__ void u1_gauss_kernel(const T* pr, const T* pim, const T* qr, const T* qi, const T* e0, const T* e1,
+                                const T* e2, int N, double idx, double c, DevState* st) {
+    const size_t n3 = (size_t)N * N * N;
+    double g2 = 0, l2 = 0, r2 = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+        const size_t mx = ((size_t)z * N + y) * N + (x == 0 ? N - 1 : x - 1);
+        const size_t my = ((size_t)z * N + (y == 0 ? N - 1 : y - 1)) * N + x;
+        const size_t mz = ((size_t)(z == 0 ? N - 1 : z - 1) * N + y) * N + x;
+        const double div = ((double)e0[i] - (double)e0[mx] + (double)e1[i] - (double)e1[my] + (double)e2[i] -
+                            (double)e2[mz]) * idx;
+        const double rho = c * ((double)pr[i] * (double)qi[i] - (double)pim[i] * (double)qr[i]);
+        g2 += (div - rho) * (div - rho);
+        l2 += div * div;
+        r2 += rho * rho;
+    }
+    g2 = warp_sum(g2);
+    l2 = warp_sum(l2);
+    r2 = warp_sum(r2);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&st->gauss[0], g2 / (double)n3);
+        atomicAdd(&st->gauss[1], l2 / (double)n3);
+        atomicAdd(&st->gauss[2], r2 / (double)n3);
+    }
+}
+
+__global__ void zero_gauss_kernel(DevState* st) { st->gauss[0] = st->gauss[1] = st->gauss[2] = 0.0; }
+
+void u1_geometry(Lattice* L) {
+    Geometry& g = L->geo;
+    g.N = L->mc.N;
+    g.threads = 256;
+    const size_t n3 = (size_t)g.N * g.N * g.N;
+    int per_sm = 1;
+    if (L->prec == CL_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u1_pass_kernel<float>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u1_pass_kernel<double>, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)L->sm_count * per_sm;
+    const long long need = (long long)((n3 + 255) / 256);
+    if (grid > need) grid = need;
+    if (grid > kMaxBlocks) grid = kMaxBlocks;
+    g.grid = (int)grid;
+    g.ntiles = g.grid;
+    g.smem = 0;
+}
+
+cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
+    U1Args A;
+    for (int i = 0; i < 10; ++i) {
+        A.in[i] = L->buf.f[src][i];
+        A.out[i] = L->buf.f[dst][i];
+    }
+    A.st = L->buf.st;
+    A.partials = L->buf.partials;
+    A.counter = L->buf.counter;
+    A.mc = L->mc;
+    A.pi = pi;
+    A.write = write ? 1 : 0;
+    if (L->prec == CL_FP32) u1_pass_kernel<float><<<L->geo.grid, 256, 0, s>>>(A);
+    else u1_pass_kernel<double><<<L->geo.grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t u1_launch_drift(Lattice* L, int cur, cudaStream_t s) {
+    void** b = L->buf.f[cur];
+    const size_t n = (size_t)L->mc.N * L->mc.N * L->mc.N;
+    const int grid = L->sm_count * 8;
+    if (L->prec == CL_FP32)
+        u1_drift_kernel<float><<<grid, 256, 0, s>>>((float*)b[0], (float*)b[1], (const float*)b[2], (const float*)b[3],
+                                                    (float*)b[4], (float*)b[5], (float*)b[6], (const float*)b[7],
+                                                    (const float*)b[8], (const float*)b[9], n, L->buf.st);
+    else
+        u1_drift_kernel<double><<<grid, 256, 0, s>>>((double*)b[0], (double*)b[1], (const double*)b[2],
+                                                     (const double*)b[3], (double*)b[4], (double*)b[5], (double*)b[6],
+                                                     (const double*)b[7], (const double*)b[8], (const double*)b[9], n,
+                                                     L->buf.st);
+    return cudaGetLastError();
+}
+
+cudaError_t u1_launch_gauss(Lattice* L, int cur, cudaStream_t s) {
+    void** b = L->buf.f[cur];
+    zero_gauss_kernel<<<1, 1, 0, s>>>(L->buf.st);
+    const int grid = L->sm_count * 4;
+    const double c = 2.0 * L->mc.e / L->mc.kappa, idx = 1.0 / L->mc.dx;
+    if (L->prec == CL_FP32)
+        u1_gauss_kernel<float><<<grid, 256, 0, s>>>((const float*)b[0], (const float*)b[1], (const float*)b[2],
+                                                    (const float*)b[3], (const float*)b[7], (const float*)b[8],
+                                                    (const float*)b[9], L->mc.N, idx, c, L->buf.st);
+    else
+        u1_gauss_kernel<double><<<grid, 256, 0, s>>>((const double*)b[0], (const double*)b[1], (const double*)b[2],
+                                                     (const double*)b[3], (const double*)b[7], (const double*)b[8],
+                                                     (const double*)b[9], L->mc.N, idx, c, L->buf.st);
+    return cudaGetLastError();
+}
+
+}  // namespace cl

@@ -1,0 +1,92 @@
+"""The C-ABI library builds, loads, exports every symbol include/cl_lattice.h
+declares, and validates arguments on the host (no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2006_15122_gb300 as cl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "cl_lattice.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lattice_\w+|cl_\w+)\s*\(", src)) - {"cl_status", "cl_lattice"})
+
+
+def test_header_declarations_match_binding():
+    assert _declared_functions() == sorted(cl.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cl.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", cl.library_path()], capture_output=True, text=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if " T " in l)
+    for name in _declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_header_compiles_as_c():
+    r = subprocess.run(["gcc", "-fsyntax-only", "-Wall", "-Werror", "-x", "c", os.path.join(ROOT, "include", "cl_lattice.h")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_status_strings():
+    lib = cl.load()
+    for s in range(9):
+        assert lib.cl_status_str(s)
+    assert lib.cl_last_error(None)
+
+
+def _init(model, grid, init):
+    lib = cl.load()
+    h = C.c_void_p()
+    st = lib.lattice_init(C.byref(model), C.byref(grid), C.byref(init), None, C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("N", [4, 12, 4096])
+def test_init_rejects_bad_lattice_size(N):
+    st, h = _init(cl.make_model(), cl.make_grid(N, 0.5, 0.01), cl.make_init())
+    assert st == cl.CL_ERR_ARG and not h.value
+    assert b"N must be" in cl.load().cl_last_error(None)
+
+
+def test_init_rejects_unstable_time_step():
+    """omega_max dt above the leapfrog/VV2 bound 2 (VV4: 1.5734) is refused before any device work."""
+    m = cl.make_model(n_fields=2, pexp=2, q=4e5, omega_over_fstar=5e-6, fstar_over_mp=1.4)
+    st, h = _init(m, cl.make_grid(64, 0.1, 0.005, "vv4"), cl.make_init(phi0=(1.0, 0.0)))
+    assert st == cl.CL_ERR_UNSTABLE_DT and not h.value
+    assert b"stability bound" in cl.load().cl_last_error(None)
+
+
+@pytest.mark.parametrize("bad", ["integrator", "pexp", "fields", "kir", "u1_vv"])
+def test_init_rejects_bad_arguments(bad):
+    m = cl.make_model(n_fields=1, pexp=2)
+    g = cl.make_grid(16, 0.5, 0.01)
+    if bad == "integrator":
+        g.integrator = 9
+    if bad == "pexp":
+        m.pexp = 3
+    if bad == "fields":
+        m.n_fields = 3
+    if bad == "kir":
+        g.kIR = -1.0
+    if bad == "u1_vv":
+        m.kind = cl.CL_MODEL_U1
+        g.integrator = cl.CL_INT_VV4
+    st, h = _init(m, g, cl.make_init())
+    assert st == cl.CL_ERR_ARG and not h.value
+
+
+def test_null_arguments_are_rejected():
+    lib = cl.load()
+    assert lib.lattice_evolve(None, 1) == cl.CL_ERR_ARG
+    assert lib.lattice_measure_means(None, None) == cl.CL_ERR_ARG
+    assert lib.lattice_destroy(None) == cl.CL_OK

@@ -1,0 +1,193 @@
+"""Parity of the CUDA scalar path (through the C ABI) with the FP64 oracle.
+
+FP64 runs must match the oracle to 1e-12 relative per step; FP32 runs to
+1e-5 relative pointwise on the fluctuation arrays for the first 100 steps
+and to 1e-3 on spectra and volume averages (max-norm relative error per
+array, ||x - y||_inf / ||y||_inf)."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2006_15122_gb300 as cl
+from oracle import ScalarLattice, ScalarModel
+from oracle.ic import scalar_ic
+from oracle.spectra import spectrum as oracle_spectrum
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = {"vv2": oracle.VV2, "vv4": oracle.VV4, "vv6": oracle.VV6}
+
+
+def rel(x, y):
+    return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
+
+
+def make_pair(N, Ns, pexp, alpha, fmp, lam, q, integ, prec, kIR=0.5, dt=0.01, seed=1, amp=0.2, means=None,
+              a=1.0, b=None, omega=1.0):
+    """A GPU lattice and an oracle lattice holding the same random state."""
+    dx = 2 * math.pi / (kIR * N)
+    m = cl.make_model(n_fields=Ns, pexp=pexp, alpha=alpha, fstar_over_mp=fmp, lam=lam, q=q, omega_over_fstar=omega)
+    g = cl.make_grid(N, kIR, dt, integ, prec)
+    lat = cl.Lattice(m, g, cl.make_init(phi0=means or [0.0] * Ns, spectrum=0))
+    om = ScalarModel(N=N, Ns=Ns, pexp=pexp, dx=dx, alpha=alpha, fmp2=fmp * fmp, lam=lam, q=q)
+    phi = inputs.fields(Ns, N, seed=seed, amp=amp, kmax=N / 4, means=means)
+    pi = inputs.fields(Ns, N, seed=seed + 7, amp=amp)
+    ref = ScalarLattice(om, phi, pi, a=a)
+    ref.b = np.sqrt(ref.hubble_rhs()) if (b is None and fmp > 0) else (b or 0.0)
+    for i in range(Ns):
+        lat.set_field(cl.FIELD(i), phi[i])
+        lat.set_field(cl.MOMENTUM(i), pi[i])
+    lat.set_background(a, ref.b, 0.0)
+    return lat, ref
+
+
+def fields_of(lat, Ns):
+    return (np.stack([lat.get_field(cl.FIELD(i)) for i in range(Ns)]),
+            np.stack([lat.get_field(cl.MOMENTUM(i)) for i in range(Ns)]))
+
+
+@pytest.mark.parametrize("N,Ns,pexp,alpha,integ", [
+    (24, 1, 4, 1.0, "vv2"), (40, 2, 2, 0.0, "vv4"), (64, 2, 4, 0.5, "vv4"), (32, 1, 6, 1.5, "vv6")])
+def test_fp64_single_step_matches_oracle(N, Ns, pexp, alpha, integ):
+    lat, ref = make_pair(N, Ns, pexp, alpha, fmp=1.2, lam=1.0, q=3.0, integ=integ, prec=cl.CL_FP64,
+                         means=[0.9, 0.1][:Ns])
+    lat.evolve(1)
+    ref.vv_steps(WEIGHTS[integ], 0.01, 1)
+    phi, pi = fields_of(lat, Ns)
+    for i in range(Ns):
+        assert rel(phi[i], ref.phi[i]) < 1e-12
+        assert rel(pi[i], ref.pi[i]) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-14 * ref.a and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
+    lat.close()
+
+
+def test_fp64_many_steps_vv4_and_means():
+    lat, ref = make_pair(48, 2, 2, 0.0, fmp=1.0, lam=1.0, q=5.0, integ="vv4", prec=cl.CL_FP64, means=[1.0, 0.0])
+    for _ in range(3):
+        lat.evolve(7)
+        ref.vv_steps(oracle.VV4, 0.01, 7)
+    phi, pi = fields_of(lat, 2)
+    assert rel(phi, ref.phi) < 1e-11 and rel(pi, ref.pi) < 1e-11
+    mm = lat.measure_means()
+    E = ref.energies()
+    assert np.allclose(mm["EK"][:2], E[0:2], rtol=1e-11) and np.allclose(mm["EG"][:2], E[2:4], rtol=1e-11)
+    assert np.allclose(mm["EV"][:2], E[4:6], rtol=1e-11)
+    assert abs(mm["mean"][0] - ref.phi[0].mean()) < 1e-12
+    assert abs(mm["var"][1] - ref.phi[1].var()) < 1e-11 * ref.phi[1].var()
+    assert abs(mm["hubble_violation"] - ref.hubble_violation()) < 1e-9
+    assert mm["step"] == 21 and abs(mm["t"] - 0.21) < 1e-12
+    lat.close()
+
+
+def test_fp64_leapfrog_matches_oracle():
+    lat, ref = make_pair(32, 2, 2, 0.5, fmp=1.0, lam=1.0, q=2.0, integ="lf", prec=cl.CL_FP64, means=[1.0, 0.0])
+    ref.lf3_prepare(0.01)
+    lat.evolve(5)
+    lat.evolve(6)
+    ref.lf3_steps(0.01, 11)
+    phi, pi = fields_of(lat, 2)
+    assert rel(phi, ref.phi) < 1e-12 and rel(pi, ref.pi) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
+    assert abs(mm["EK"][0] - ref.EKm) < 1e-12 * ref.EKm
+    lat.close()
+
+
+@pytest.mark.parametrize("N,prec", [(32, cl.CL_FP64), (48, cl.CL_FP32)])
+def test_initial_conditions_match_oracle(N, prec):
+    """Same seed, same Philox draws: the device ICs equal the oracle's (FP64
+    to 1e-12; FP32 to its rounding), and b comes from the Hubble constraint."""
+    kIR, omega, fmp = 0.5, 0.05, 1.0
+    dx = 2 * math.pi / (kIR * N)
+    m = cl.make_model(n_fields=2, pexp=2, lam=1.0, q=2.0, omega_over_fstar=omega, fstar_over_mp=fmp)
+    lat = cl.Lattice(m, cl.make_grid(N, kIR, 0.01, "vv2", prec), cl.make_init(phi0=(1.0, 0.0), dphi0=(-0.1, 0.0), seed=77))
+    om = ScalarModel(N=N, Ns=2, pexp=2, dx=dx, alpha=0.0, fmp2=fmp * fmp, lam=1.0, q=2.0)
+    phi, pi, _ = scalar_ic(om, kIR, [1.0, 0.0], [-0.1, 0.0], seed=77, omega_over_fstar=omega)
+    gphi, gpi = fields_of(lat, 2)
+    tol = 1e-12 if prec == cl.CL_FP64 else 1e-6
+    for i in range(2):
+        assert rel(gphi[i] - gphi[i].mean(), phi[i] - phi[i].mean()) < tol
+        assert rel(gpi[i], pi[i]) < tol
+    ref = ScalarLattice(om, phi, pi)
+    mm = lat.measure_means()
+    # the device evaluates the Hubble constraint on its stored (FP32-rounded) fluctuations
+    assert abs(mm["b"] - np.sqrt(ref.hubble_rhs())) < (1e-12 if prec == cl.CL_FP64 else 1e-7) * mm["b"]
+    lat.close()
+
+
+def test_fp32_pointwise_parity_100_steps():
+    """Two-field preheating-like state (mean 1 plus 1e-3 fluctuations), FP32
+    fluctuation arrays with FP64 means: 100 VV4 steps within 1e-5 relative."""
+    N = 32
+    lat, ref = make_pair(N, 2, 2, 0.0, fmp=1.4, lam=1.0, q=400.0, integ="vv4", prec=cl.CL_FP32, kIR=0.5, dt=0.005,
+                         amp=1e-3, means=[1.0, 0.0])
+    lat.evolve(100)
+    ref.vv_steps(oracle.VV4, 0.005, 100)
+    phi, pi = fields_of(lat, 2)
+    for i in range(2):
+        d_gpu = phi[i] - phi[i].mean()
+        d_ref = ref.phi[i] - ref.phi[i].mean()
+        assert rel(d_gpu, d_ref) < 1e-5, (i, rel(d_gpu, d_ref))
+        assert rel(pi[i] - pi[i].mean(), ref.pi[i] - ref.pi[i].mean()) < 1e-5
+    mm = lat.measure_means()
+    E = ref.energies()
+    assert abs(mm["a"] - ref.a) < 1e-9
+    assert np.allclose(mm["EK"][:2], E[0:2], rtol=1e-5) and np.allclose(mm["EG"][:2], E[2:4], rtol=1e-5)
+    lat.close()
+
+
+def test_spectrum_matches_oracle():
+    N, kIR = 32, 0.4
+    lat, ref = make_pair(N, 2, 2, 0.0, fmp=0.0, lam=1.0, q=1.0, integ="vv2", prec=cl.CL_FP64, kIR=kIR)
+    dx = 2 * math.pi / (kIR * N)
+    for f in range(2):
+        for what, arr in ((0, ref.phi[f]), (1, ref.pi[f])):
+            k, D, c = lat.spectrum(f, what)
+            k0, D0, c0 = oracle_spectrum(arr, dx, kIR)
+            assert np.array_equal(c, c0)
+            assert np.allclose(k, k0, rtol=1e-13)
+            # modes beyond the band limit of the input hold only rounding noise
+            assert np.allclose(D, D0, rtol=1e-10, atol=1e-10 * D0.max())
+    lat.close()
+
+
+def test_checkpoint_continuation_is_bitwise():
+    lat, _ = make_pair(32, 2, 2, 0.0, fmp=1.0, lam=1.0, q=2.0, integ="vv4", prec=cl.CL_FP32, means=[1.0, 0.0])
+    lat.evolve(3)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        lat.save(path)
+        lat.evolve(4)
+        a = fields_of(lat, 2)
+        ma = lat.measure_means()
+        lat.restore(path)
+        lat.evolve(4)
+        b = fields_of(lat, 2)
+        mb = lat.measure_means()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert ma["a"] == mb["a"] and ma["b"] == mb["b"]
+        with open(path, "r+b") as fp:
+            fp.seek(-5, 2)
+            fp.write(b"\x00\x01\x02\x03\x04")
+        with pytest.raises(cl.LatticeError) as e:
+            lat.restore(path)
+        assert e.value.status == cl.CL_ERR_IO
+    lat.close()
+
+
+def test_nonfinite_state_is_reported():
+    lat, _ = make_pair(16, 1, 2, 0.0, fmp=0.0, lam=1.0, q=0.0, integ="vv2", prec=cl.CL_FP32)
+    bad = np.zeros((16, 16, 16))
+    bad[3, 4, 5] = np.nan
+    lat.set_field(cl.MOMENTUM(0), bad)
+    lat.evolve(2)
+    with pytest.raises(cl.LatticeError) as e:
+        lat.measure_means()
+    assert e.value.status == cl.CL_ERR_NONFINITE
+    lat.close()

@@ -1,0 +1,100 @@
+"""Parity of the CUDA compact-U(1) path (through the C ABI) with the FP64
+oracle, and the Gauss law to round-off (section 5.3)."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2006_15122_gb300 as cl
+from oracle import U1Lattice, U1Model
+from oracle.ic import u1_ic
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(x, y):
+    return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
+
+
+def angle_err(a, b):
+    return float(np.max(np.abs(np.angle(np.exp(1j * (a - b))))))
+
+
+def gpu_u1(N, kIR, dt, prec, fmp=0.0, alpha=0.0, e=1.0, lam=1.0, v2=1.0, omega=1.0, spectrum=0, seed=0,
+           phi0=(0.0, 0.0)):
+    m = cl.make_model(kind=cl.CL_MODEL_U1, alpha=alpha, fstar_over_mp=fmp, omega_over_fstar=omega, lam=lam,
+                      vev2=v2, gauge_e=e)
+    g = cl.make_grid(N, kIR, dt, "lf", prec)
+    return cl.Lattice(m, g, cl.make_init(phi0=phi0, seed=seed, spectrum=spectrum))
+
+
+def get_all(lat):
+    phi = np.stack([lat.get_field(cl.FIELD(i)) for i in range(2)])
+    pi = np.stack([lat.get_field(cl.MOMENTUM(i)) for i in range(2)])
+    th = np.stack([lat.get_field(cl.LINK(i)) for i in range(3)])
+    pa = np.stack([lat.get_field(cl.EMOMENTUM(i)) for i in range(3)])
+    return phi, pi, th, pa
+
+
+@pytest.mark.parametrize("fmp,alpha", [(0.0, 0.0), (0.8, 0.5)])
+def test_u1_fp64_leapfrog_matches_oracle(fmp, alpha):
+    N, kIR, dt = 16, 2 * math.pi / (16 * 0.5), 0.05
+    lat = gpu_u1(N, kIR, dt, cl.CL_FP64, fmp=fmp, alpha=alpha, e=0.9, lam=1.2, v2=0.7, omega=1.1)
+    om = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.7, e=0.9, kappa=1.21)
+    phi = inputs.fields(2, N, seed=3, amp=0.6, kmax=4, means=[0.4, -0.1])
+    pi = inputs.fields(2, N, seed=4, amp=0.3, kmax=4)
+    th = inputs.angles(N, 5, scale=0.4)
+    pa = inputs.fields(3, N, seed=6, amp=0.2, kmax=4)
+    ref = U1Lattice(om, phi, pi, th, pa)
+    ref.b = math.sqrt(fmp * fmp / 3 * ref.energies().sum()) if fmp > 0 else 0.0
+    for i in range(2):
+        lat.set_field(cl.FIELD(i), phi[i])
+        lat.set_field(cl.MOMENTUM(i), pi[i])
+    for i in range(3):
+        lat.set_field(cl.LINK(i), th[i])
+        lat.set_field(cl.EMOMENTUM(i), pa[i])
+    lat.set_background(1.0, ref.b, 0.0)
+    ref.lf_prepare(dt)
+    lat.evolve(3)
+    lat.evolve(4)
+    ref.lf_steps(dt, 7)
+    gphi, gpi, gth, gpa = get_all(lat)
+    assert rel(gphi, ref.phi) < 1e-12
+    assert rel(gpi, ref.pi) < 1e-12
+    assert angle_err(gth, ref.theta) < 1e-12
+    assert rel(gpa, ref.piA) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 + 1e-12 * abs(ref.b)
+    lat.close()
+
+
+def test_u1_initial_conditions_match_oracle():
+    N, dx = 16, 0.5
+    kIR = 2 * math.pi / (N * dx)
+    lat = gpu_u1(N, kIR, 0.05, cl.CL_FP64, spectrum=1, seed=31)
+    om = U1Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=1.0, kappa=1.0)
+    phi, pi, th, pa, _ = u1_ic(om, kIR, [0.0, 0.0], [0.0, 0.0], seed=31, omega_over_fstar=1.0)
+    gphi, gpi, gth, gpa = get_all(lat)
+    assert rel(gphi, phi) < 1e-12 and rel(gpi, pi) < 1e-12 and rel(gpa, pa) < 1e-11
+    assert np.all(gth == 0.0)
+    mm = lat.measure_means()
+    assert mm["gauss_violation"] < 1e-13
+    assert mm["EG"][1] == 0.0  # magnetic energy exactly zero with unit links
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(cl.CL_FP64, 1e-13), (cl.CL_FP32, 1e-5)])
+def test_u1_gauss_law_is_preserved(prec, tol):
+    """The abelian-Higgs configuration (lam = e = v = 1, dx = 0.5, dt = 0.1 dx):
+    the Gauss constraint stays at round-off and does not drift."""
+    N, dx = 32, 0.5
+    lat = gpu_u1(N, 2 * math.pi / (N * dx), 0.05, prec, spectrum=1, seed=7)
+    g = []
+    for _ in range(5):
+        lat.evolve(20)
+        g.append(lat.measure_means()["gauss_violation"])
+    assert max(g) < tol, g
+    mm = lat.measure_means()
+    assert mm["EG"][1] > 0.0  # magnetic field has developed
+    lat.close()
