@@ -36,6 +36,8 @@
 // persistent (grid-stride over tiles, y-tiles fastest so that y-halos are
 // L2 hits of concurrently running tiles).
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "cl_internal.cuh"
 
@@ -108,6 +110,7 @@ __device__ void set_kick_powers(DevState* st, const ModelConst& mc, double a) {
 
 // Scalar update of the last block (thread 0).  tot[] are sums / N^3.
 __device__ void scalar_finish(DevState* st, const double* tot, const ModelConst& mc, const PassInfo& pi, bool single) {
+    if (st->error) return;
     const int nf = mc.nf;
     const double a = st->a;
     double V1, V2, dV[2];
@@ -222,24 +225,44 @@ __device__ void scalar_finish(DevState* st, const double* tot, const ModelConst&
 
 // --------------------------------------------------------------- the pass
 
+struct TileXYZ {
+    int x0, y0, z0;
+};
+
+__device__ __forceinline__ TileXYZ decode_tile(const Geometry& g, int tile) {
+    const int tyi = tile % g.nty;
+    const int rr = tile / g.nty;
+    const int txi = rr % g.ntx;
+    const int tzi = rr / g.ntx;
+    TileXYZ t;
+    t.x0 = txi * g.BX * g.V;
+    t.y0 = tyi * g.BY;
+    t.z0 = tzi * g.ZC;
+    return t;
+}
+
 template <typename T, int NF, int P>
 __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A) {
     DevState* st = A.st;
     if (st->error) return;
     constexpr int V = VecT<T>::V;
     constexpr int NS = 6 * NF + 2;
-    const int N = A.geo.N, BX = A.geo.BX, BY = A.geo.BY, ZC = A.geo.ZC;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int W = BX * V + 2 * V;   // shared row: V pad columns each side keep rows 16-byte aligned
-    const int PL = (BY + 2) * W;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* sm = reinterpret_cast<T*>(smraw);
-    // per-warp FP64 accumulators of the per-tile FP32/FP64 thread sums
+    constexpr int NA = 2 * NF;
+    const Geometry& G = A.geo;
+    const int N = G.N, BX = G.BX, BY = G.BY, ZC = G.ZC, S = G.S;
+    const int TX = BX * V, RW = TX + 2 * V, ROWS = BY + 2;
+    const int ASZ = ROWS * RW;  // elements of one array in one stage
+    const int STG = NA * ASZ;   // elements of one stage
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw + 128);
     __shared__ double bacc[8][16];
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int lin = ty * BX + tx;
-    const int lane = lin & 31, warp = lin >> 5, nwarps = (BX * BY + 31) >> 5;
-    const int nlanes = min(32, BX * BY - 32 * warp);  // lanes of this (possibly partial) warp
-    for (int i = lin; i < 8 * 16; i += BX * BY) (&bacc[0][0])[i] = 0.0;
+    const int nthr = BX * BY;
+    const int lane = lin & 31, warp = lin >> 5, nwarps = (nthr + 31) >> 5;
+    const int nlanes = min(32, nthr - 32 * warp);
+    const unsigned wmask = nlanes >= 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
+    for (int i = lin; i < 8 * 16; i += nthr) (&bacc[0][0])[i] = 0.0;
 
     const T cd = T(st->cd), A1 = T(st->A1), A3 = T(st->A3);
     const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(A.mc.idx2);
@@ -252,122 +275,162 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
         sp[f] = f < NF ? T(st->spi[f]) : T(0);
     }
     const T P0 = fb[0] * fb[0], C0 = fb[1] * fb[1];
-#define PHI_IN(f) (static_cast<const T*>(A.in[(f)]))
-#define PI_IN(f) (static_cast<const T*>(A.in[NF + (f)]))
-#define PHI_OUT(f) (static_cast<T*>(A.out[(f)]))
-#define PI_OUT(f) (static_cast<T*>(A.out[NF + (f)]))
 
-    // halo role of this thread (BX >= 2 and BY >= 2, so at most one per direction)
+    const int my_tiles = (blockIdx.x < (unsigned)G.ntiles) ? (G.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    // Load sequence of this block: for each of its tiles, planes z0-1 .. z0+ZC.  The
+    // producer side walks it with counters (tile k, plane p, stage slot) so that no
+    // division is needed per plane; the tile decode happens once per tile.
+    int ld_k = 0, ld_p = 0, ld_slot = 0;
+    TileXYZ ld_t = decode_tile(G, (int)blockIdx.x);
     const bool yhalo = (ty == 0) || (ty == BY - 1);
     const bool xhalo = (tx == 0) || (tx == BX - 1);
-    const int yh_row = (ty == 0) ? 0 : BY + 1;          // shared row of the y-halo
-    const int xh_col = (tx == 0) ? V - 1 : V + BX * V;  // shared column of the x-halo
-    int it = 0;
-    __syncthreads();
+    const int yh_row = (ty == 0) ? 0 : BY + 1;
+    const int xh_col = (tx == 0) ? V - 1 : V + TX;
 
-    for (int tile = blockIdx.x; tile < A.geo.ntiles; tile += gridDim.x) {
-        const int tyi = tile % A.geo.nty;
-        const int rr = tile / A.geo.nty;
-        const int txi = rr % A.geo.ntx;
-        const int tzi = rr / A.geo.ntx;
-        const int x = txi * BX * V + tx * V;
-        const int y = tyi * BY + ty;
-        const int z0 = tzi * ZC;
-        const int yh = (ty == 0) ? (y == 0 ? N - 1 : y - 1) : (y == N - 1 ? 0 : y + 1);
-        const int xh = (tx == 0) ? (x == 0 ? N - 1 : x - 1) : (x + V == N ? 0 : x + V);
-        const size_t NN = (size_t)N * N;
-        const size_t row_own = (size_t)y * N + x, row_yh = (size_t)yh * N + x, row_xh = (size_t)y * N + xh;
-        auto zw = [&](int zz) -> int { return zz < 0 ? zz + N : (zz >= N ? zz - N : zz); };
-
-        T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
-        T hyf[NF][V], hyp[NF][V];  // raw y-halo (phi, pi) of the next plane to write
-        T hxf[NF], hxp[NF];        // raw x-halo
-        T ts[NS];                  // this tile's thread sums
+    // Every thread copies its own part of the next load into its stage with cp.async:
+    // its 16-byte vector of every array, the y-halo row vector (first/last thread row)
+    // and the x-halo cell (first/last thread column), periodic indices.  One commit
+    // group per load, empty past the end, so every thread counts groups alike.
+    auto issue = [&]() {
+        if (ld_k < my_tiles) {
+            int z = ld_t.z0 - 1 + ld_p;
+            z = z < 0 ? z + N : (z >= N ? z - N : z);
+            T* dst = sm + ld_slot * STG;
+            const int x = ld_t.x0 + tx * V, y = ld_t.y0 + ty;
+            const size_t zoff = (size_t)z * N * N;
+            const int yh = (ty == 0) ? (y == 0 ? N - 1 : y - 1) : (y == N - 1 ? 0 : y + 1);
+            const int xh = (tx == 0) ? (x == 0 ? N - 1 : x - 1) : (x + V == N ? 0 : x + V);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) ts[k] = T(0);
+            for (int a = 0; a < NA; ++a) {
+                const T* src = static_cast<const T*>(A.in[a]) + zoff;
+                T* d = dst + a * ASZ;
+                cp_async16(d + (ty + 1) * RW + V + tx * V, src + (size_t)y * N + x);
+                if (yhalo) {
+                    cp_async16(d + yh_row * RW + V + tx * V, src + (size_t)yh * N + x);
+                    if (BY == 1) cp_async16(d + (BY + 1) * RW + V + tx * V, src + (size_t)(y == N - 1 ? 0 : y + 1) * N + x);
+                }
+                if (xhalo) {
+                    cp_async_elem(d + (ty + 1) * RW + xh_col, src + (size_t)y * N + xh);
+                    if (BX == 1) cp_async_elem(d + (ty + 1) * RW + V + TX, src + (size_t)y * N + (x + V == N ? 0 : x + V));
+                }
+            }
+            if (++ld_p == ZC + 2) {
+                ld_p = 0;
+                if (++ld_k < my_tiles) ld_t = decode_tile(G, (int)blockIdx.x + ld_k * (int)gridDim.x);
+            }
+            if (++ld_slot == S) ld_slot = 0;
+        }
+        cp_async_commit();
+    };
+    // wait until the third-newest load has landed for every thread (at most S-3
+    // newer groups may still be pending)
+    auto wait_for = [&]() {
+        switch (S) {
+            case 3: cp_async_wait<0>(); break;
+            case 4: cp_async_wait<1>(); break;
+            case 5: cp_async_wait<2>(); break;
+            case 6: cp_async_wait<3>(); break;
+            case 7: cp_async_wait<4>(); break;
+            default: cp_async_wait<5>(); break;
+        }
+        __syncthreads();
+    };
 
-        // prologue: planes z0-1, z0, z0+1 and the halo of z0
+    for (int L = 0; L < S; ++L) issue();
+    int sl_m = 0;  // stage slot of plane z-1; z and z+1 follow cyclically
+
+    // In-place drift of this thread's part of a landed stage: phi <- (phi - sphi) + cd (pi - spi)
+    // for its own vector and the halo cells it copied, so that neighbours read drifted
+    // values (each site is drifted once per pass).  Returns its own drifted vector and
+    // shifted momentum.
+    const T c0[2] = {sf[0] + cd * sp[0], sf[1] + cd * sp[1]};
+    auto drift_stage = [&](T* Sx, T (&fo)[NF][V], T (&po)[NF][V]) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
+            T* F = Sx + f * ASZ;
+            const T* Pp = Sx + (NF + f) * ASZ;
+            const int ob = (ty + 1) * RW + V + tx * V;
             T rf[V], rp[V];
-            size_t o = (size_t)zw(z0 - 1) * NN + row_own;
-            vload(PHI_IN(f) + o, rf);
-            vload(PI_IN(f) + o, rp);
+            vload_s(F + ob, rf);
+            vload_s(Pp + ob, rp);
 #pragma unroll
-            for (int v = 0; v < V; ++v) fm[f][v] = (rf[v] - sf[f]) + cd * (rp[v] - sp[f]);
-            o = (size_t)z0 * NN + row_own;
-            vload(PHI_IN(f) + o, rf);
-            vload(PI_IN(f) + o, rp);
-#pragma unroll
-            for (int v = 0; v < V; ++v) { pc[f][v] = rp[v] - sp[f]; fc[f][v] = (rf[v] - sf[f]) + cd * pc[f][v]; }
-            o = (size_t)zw(z0 + 1) * NN + row_own;
-            vload(PHI_IN(f) + o, rf);
-            vload(PI_IN(f) + o, rp);
-#pragma unroll
-            for (int v = 0; v < V; ++v) { pn[f][v] = rp[v] - sp[f]; fp[f][v] = (rf[v] - sf[f]) + cd * pn[f][v]; }
+            for (int v = 0; v < V; ++v) {
+                po[f][v] = rp[v] - sp[f];
+                fo[f][v] = (rf[v] + cd * rp[v]) - c0[f];
+            }
+            vstore(F + ob, fo[f]);
             if (yhalo) {
-                vload(PHI_IN(f) + (size_t)z0 * NN + row_yh, hyf[f]);
-                vload(PI_IN(f) + (size_t)z0 * NN + row_yh, hyp[f]);
+                const int oh = yh_row * RW + V + tx * V;
+                vload_s(F + oh, rf);
+                vload_s(Pp + oh, rp);
+#pragma unroll
+                for (int v = 0; v < V; ++v) rf[v] = (rf[v] + cd * rp[v]) - c0[f];
+                vstore(F + oh, rf);
+                if (BY == 1) {
+                    const int ob2 = (BY + 1) * RW + V + tx * V;
+                    vload_s(F + ob2, rf);
+                    vload_s(Pp + ob2, rp);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) rf[v] = (rf[v] + cd * rp[v]) - c0[f];
+                    vstore(F + ob2, rf);
+                }
             }
             if (xhalo) {
-                hxf[f] = __ldg(PHI_IN(f) + (size_t)z0 * NN + row_xh);
-                hxp[f] = __ldg(PI_IN(f) + (size_t)z0 * NN + row_xh);
+                const int oc = (ty + 1) * RW + xh_col;
+                F[oc] = (F[oc] + cd * Pp[oc]) - c0[f];
+                if (BX == 1) {
+                    const int oc2 = (ty + 1) * RW + V + TX;
+                    F[oc2] = (F[oc2] + cd * Pp[oc2]) - c0[f];
+                }
             }
         }
+    };
 
-        for (int zz = 0; zz < ZC; ++zz, ++it) {
-            const int z = z0 + zz;
-            T* buf = sm + (size_t)(it & 1) * NF * PL;
-            // (a) drifted plane z into shared memory, with its halo
+    for (int k = 0; k < my_tiles; ++k) {
+        const TileXYZ tt = decode_tile(G, (int)blockIdx.x + k * (int)gridDim.x);
+        const int x = tt.x0 + tx * V, y = tt.y0 + ty;
+        const size_t NN = (size_t)N * N;
+        const int ob = (ty + 1) * RW + V + tx * V;  // own vector inside an array block
+        T ts[NS];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                vstore(buf + f * PL + (ty + 1) * W + V + tx * V, fc[f]);
-                if (yhalo) {
-                    T hv[V];
-#pragma unroll
-                    for (int v = 0; v < V; ++v) hv[v] = (hyf[f][v] - sf[f]) + cd * (hyp[f][v] - sp[f]);
-                    vstore(buf + f * PL + yh_row * W + V + tx * V, hv);
-                }
-                if (xhalo) buf[f * PL + (ty + 1) * W + xh_col] = (hxf[f] - sf[f]) + cd * (hxp[f] - sp[f]);
+        for (int i = 0; i < NS; ++i) ts[i] = T(0);
+        T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
+        for (int zz = 0; zz < ZC; ++zz) {
+            wait_for();  // loads base+zz .. base+zz+2 (planes z-1, z, z+1) have landed
+            const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
+            const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
+            T* Sc = sm + sl_c * STG;
+            T* Sp = sm + sl_p * STG;
+            if (zz == 0) {
+                T* Sm = sm + sl_m * STG;
+                T dummy[NF][V];
+                drift_stage(Sm, fm, dummy);
+                drift_stage(Sc, fc, pc);
             }
-            // (b) halo of plane z+1 and own vectors of plane z+2 in flight during the compute
-            const bool more = (zz + 1 < ZC);
-            const bool next2 = (zz + 2 <= ZC);
-            const size_t o1 = (size_t)zw(z + 1) * NN, o2 = (size_t)zw(z + 2) * NN + row_own;
-            T rf[NF][V], rp[NF][V];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                if (more && yhalo) {
-                    vload(PHI_IN(f) + o1 + row_yh, hyf[f]);
-                    vload(PI_IN(f) + o1 + row_yh, hyp[f]);
-                }
-                if (more && xhalo) {
-                    hxf[f] = __ldg(PHI_IN(f) + o1 + row_xh);
-                    hxp[f] = __ldg(PI_IN(f) + o1 + row_xh);
-                }
-                if (next2) {
-                    vload(PHI_IN(f) + o2, rf[f]);
-                    vload(PI_IN(f) + o2, rp[f]);
-                }
-            }
-            __syncthreads();
-            // (c) stencil, kick, reductions for the V sites of this thread
+            drift_stage(Sp, fp, pn);
+            if (zz == 0) __syncthreads();  // halos of the tile's first plane are drifted
             T lap[NF][V];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                const T* row = buf + f * PL + (ty + 1) * W + V + tx * V;
-                T up[V], dn[V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) { up[v] = row[v - W]; dn[v] = row[v + W]; }
-                const T left = row[-1], right = row[V];
+                const T* cF = Sc + f * ASZ;
+                // x-neighbours: shuffles of the drifted own vectors, shared memory at row/warp edges
+                const T fromL = __shfl_up_sync(wmask, fc[f][V - 1], 1);
+                const T fromR = __shfl_down_sync(wmask, fc[f][0], 1);
+                const bool useL = (tx > 0) && (lane > 0), useR = (tx < BX - 1) && (lane < nlanes - 1);
+                const T left = useL ? fromL : cF[ob - 1];
+                const T right = useR ? fromR : cF[ob + V];
+                T u[V], d[V];
+                vload_s(cF + ob - RW, u);
+                vload_s(cF + ob + RW, d);
                 T g = T(0);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const T xl = (v == 0) ? left : fc[f][v - 1];
                     const T xr = (v == V - 1) ? right : fc[f][v + 1];
                     const T c = fc[f][v];
-                    lap[f][v] = (xl + xr + up[v] + dn[v] + fm[f][v] + fp[f][v] - T(6) * c) * idx2;
-                    const T gx = xr - c, gy = dn[v] - c, gz = fp[f][v] - c;
+                    lap[f][v] = (((xl + xr) + (u[v] + d[v])) + (fm[f][v] + fp[f][v]) - T(6) * c) * idx2;
+                    const T gx = xr - c, gy = d[v] - c, gz = fp[f][v] - c;
                     g += gx * gx + gy * gy + gz * gz;
                 }
                 ts[6 * f + 4] += g;
@@ -400,45 +463,38 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
                 }
             }
             if (A.write) {
-                const size_t o = (size_t)z * NN + row_own;
+                const size_t o = (size_t)(tt.z0 + zz) * NN + (size_t)y * N + x;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    vstore_cs(PHI_OUT(f) + o, fc[f]);
-                    vstore_cs(PI_OUT(f) + o, pout[f]);
+                    vstore_cs(static_cast<T*>(A.out[f]) + o, fc[f]);
+                    vstore_cs(static_cast<T*>(A.out[NF + f]) + o, pout[f]);
                 }
             }
-            // (d) rotate the z queue
+            __syncthreads();           // every thread is done with the stage of plane z-1
+            issue();                   // refill it with the next load in the sequence
+            sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
+            for (int f = 0; f < NF; ++f)
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     fm[f][v] = fc[f][v];
                     fc[f][v] = fp[f][v];
                     pc[f][v] = pn[f][v];
                 }
-                if (next2) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        pn[f][v] = rp[f][v] - sp[f];
-                        fp[f][v] = (rf[f][v] - sf[f]) + cd * pn[f][v];
-                    }
-                }
-            }
         }
-        // fold this tile's sums into the warp's FP64 accumulators
+        issue();  // stages of planes z0+ZC-1 and z0+ZC are free as well
+        issue();
+        sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
 #pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            const T v = partial_warp_sum(ts[k], lane, nlanes);
-            if (lane == 0) bacc[warp][k] += double(v);
+        for (int i = 0; i < NS; ++i) {
+            const T v = partial_warp_sum(ts[i], lane, nlanes);
+            if (lane == 0) bacc[warp][i] += double(v);
         }
     }
-#undef PHI_IN
-#undef PI_IN
-#undef PHI_OUT
-#undef PI_OUT
+    cp_async_wait<0>();
+    __syncthreads();
 
     // ---- block reduction (FP64) and last-block finish
-    __syncthreads();
     if (lin < NS) {
         double t = 0.0;
         for (int w = 0; w < nwarps; ++w) t += bacc[w][lin];
@@ -489,8 +545,30 @@ __global__ void scalar_drift_kernel(T* phi0, T* phi1, const T* pi0, const T* pi1
 
 // --------------------------------------------------------------- host side
 
+template <typename T, int NF> static const void* kptr_p(int pexp) {
+    if (pexp == 4) return (const void*)scalar_pass_kernel<T, NF, 4>;
+    if (pexp == 6) return (const void*)scalar_pass_kernel<T, NF, 6>;
+    return (const void*)scalar_pass_kernel<T, NF, 2>;
+}
+
+static const void* scalar_kernel_ptr(const Lattice* L) {
+    if (L->prec == CL_FP32) return L->mc.nf == 1 ? kptr_p<float, 1>(L->mc.pexp) : kptr_p<float, 2>(L->mc.pexp);
+    return L->mc.nf == 1 ? kptr_p<double, 1>(L->mc.pexp) : kptr_p<double, 2>(L->mc.pexp);
+}
+
+// Tile geometry.  CL_SCALAR_TILE="BY,ZC,S" (rows per tile, planes per z chunk,
+// ring stages) overrides the defaults; values that do not fit N are ignored.
 void scalar_geometry(Lattice* L) {
     Geometry& g = L->geo;
+    int want_by = 8, want_zc = 128, want_s = 4;
+    if (const char* env = getenv("CL_SCALAR_TILE")) {
+        int a = 0, b = 0, c = 0;
+        if (sscanf(env, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= 3 && c <= 8) {
+            want_by = a;
+            want_zc = b;
+            want_s = c;
+        }
+    }
     const int N = L->mc.N;
     g.N = N;
     g.V = (L->prec == CL_FP32) ? 4 : 2;
@@ -499,10 +577,11 @@ void scalar_geometry(Lattice* L) {
     while (nv % bx != 0) --bx;
     g.BX = bx;
     int by = 256 / g.BX;
+    if (g.BX == 32 && want_by < by) by = want_by;
     if (by > N) by = N;
     while (N % by != 0) --by;
     g.BY = by;
-    int zc = N < 64 ? N : 64;
+    int zc = N < want_zc ? N : want_zc;
     while (N % zc != 0) --zc;
     g.ZC = zc;
     g.ntx = N / (g.BX * g.V);
@@ -510,17 +589,14 @@ void scalar_geometry(Lattice* L) {
     g.ntz = N / g.ZC;
     g.ntiles = g.ntx * g.nty * g.ntz;
     g.threads = g.BX * g.BY;
-    const size_t W = (size_t)g.BX * g.V + 2 * g.V;
-    g.smem = 2 * (size_t)L->mc.nf * (g.BY + 2) * W * L->tsize;
+    const size_t RW = (size_t)g.BX * g.V + 2 * g.V;
+    const size_t stage = 2 * (size_t)L->mc.nf * (g.BY + 2) * RW * L->tsize;
+    g.S = want_s;
+    while (g.S > 3 && 128 + (size_t)g.S * stage > 227 * 1024) --g.S;
+    g.smem = 128 + (size_t)g.S * stage;
     int per_sm = 1;
-    const void* fn = nullptr;
-    if (L->prec == CL_FP32) {
-        if (L->mc.nf == 1) fn = (const void*)scalar_pass_kernel<float, 1, 2>;
-        else fn = (const void*)scalar_pass_kernel<float, 2, 2>;
-    } else {
-        if (L->mc.nf == 1) fn = (const void*)scalar_pass_kernel<double, 1, 2>;
-        else fn = (const void*)scalar_pass_kernel<double, 2, 2>;
-    }
+    const void* fn = scalar_kernel_ptr(L);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem);
     if (per_sm < 1) per_sm = 1;
     int grid = L->sm_count * per_sm;
