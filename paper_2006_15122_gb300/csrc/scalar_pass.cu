@@ -323,22 +323,24 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
         }
         cp_async_commit();
     };
-    // wait until the third-newest load has landed for every thread (at most S-3
-    // newer groups may still be pending)
-    auto wait_for = [&]() {
-        switch (S) {
-            case 3: cp_async_wait<0>(); break;
-            case 4: cp_async_wait<1>(); break;
-            case 5: cp_async_wait<2>(); break;
-            case 6: cp_async_wait<3>(); break;
-            case 7: cp_async_wait<4>(); break;
+    // wait until load `need` has landed for every thread: `issued - 1 - need`
+    // newer commit groups may stay pending
+    int issued = 0;
+    auto wait_for = [&](int need) {
+        switch (issued - 1 - need) {
+            case 0: cp_async_wait<0>(); break;
+            case 1: cp_async_wait<1>(); break;
+            case 2: cp_async_wait<2>(); break;
+            case 3: cp_async_wait<3>(); break;
+            case 4: cp_async_wait<4>(); break;
             default: cp_async_wait<5>(); break;
         }
         __syncthreads();
     };
 
-    for (int L = 0; L < S; ++L) issue();
-    int sl_m = 0;  // stage slot of plane z-1; z and z+1 follow cyclically
+    for (int L = 0; L < S; ++L, ++issued) issue();
+    int sl_m = 0;   // stage slot of plane z-1; z and z+1 follow cyclically
+    int need = 2;   // index of the load holding plane z+1
 
     // In-place drift of this thread's part of a landed stage: phi <- (phi - sphi) + cd (pi - spi)
     // for its own vector and the halo cells it copied, so that neighbours read drifted
@@ -396,8 +398,11 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
 #pragma unroll
         for (int i = 0; i < NS; ++i) ts[i] = T(0);
         T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
-        for (int zz = 0; zz < ZC; ++zz) {
-            wait_for();  // loads base+zz .. base+zz+2 (planes z-1, z, z+1) have landed
+        for (int zz = 0; zz < ZC; ++zz, ++need) {
+            wait_for(need);  // planes z-1, z, z+1 have landed
+            // the stage of plane z-2 was released by the previous iteration and every
+            // thread has passed the barrier above: refill it now (one barrier per plane)
+            if (zz > 0) { issue(); ++issued; }
             const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
             const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
             T* Sc = sm + sl_c * STG;
@@ -470,8 +475,6 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
                     vstore_cs(static_cast<T*>(A.out[NF + f]) + o, pout[f]);
                 }
             }
-            __syncthreads();           // every thread is done with the stage of plane z-1
-            issue();                   // refill it with the next load in the sequence
             sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
 #pragma unroll
             for (int f = 0; f < NF; ++f)
@@ -482,8 +485,12 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
                     pc[f][v] = pn[f][v];
                 }
         }
-        issue();  // stages of planes z0+ZC-1 and z0+ZC are free as well
+        __syncthreads();  // the tile's last three stages are free
         issue();
+        issue();
+        issue();
+        issued += 3;
+        need += 2;
         sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -560,7 +567,7 @@ static const void* scalar_kernel_ptr(const Lattice* L) {
 // ring stages) overrides the defaults; values that do not fit N are ignored.
 void scalar_geometry(Lattice* L) {
     Geometry& g = L->geo;
-    int want_by = 8, want_zc = 128, want_s = 4;
+    int want_by = 8, want_zc = 128, want_s = 5;
     if (const char* env = getenv("CL_SCALAR_TILE")) {
         int a = 0, b = 0, c = 0;
         if (sscanf(env, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= 3 && c <= 8) {
@@ -592,7 +599,7 @@ void scalar_geometry(Lattice* L) {
     const size_t RW = (size_t)g.BX * g.V + 2 * g.V;
     const size_t stage = 2 * (size_t)L->mc.nf * (g.BY + 2) * RW * L->tsize;
     g.S = want_s;
-    while (g.S > 3 && 128 + (size_t)g.S * stage > 227 * 1024) --g.S;
+    while (g.S > 4 && 128 + (size_t)g.S * stage > 227 * 1024) --g.S;
     g.smem = 128 + (size_t)g.S * stage;
     int per_sm = 1;
     const void* fn = scalar_kernel_ptr(L);
