@@ -65,7 +65,8 @@ class cl_means(C.Structure):
 
 SYMBOLS = ["cl_status_str", "cl_last_error", "lattice_init", "lattice_evolve", "lattice_measure_means",
            "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_get_field", "lattice_set_field",
-           "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy"]
+           "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy",
+           "lattice_energies_noalloc"]
 
 _lib = None
 
@@ -101,6 +102,7 @@ def load(build_if_missing=True):
         "lattice_save": ([vp, C.c_char_p], C.c_int),
         "lattice_restore": ([vp, C.c_char_p], C.c_int),
         "lattice_destroy": ([vp], C.c_int),
+        "lattice_energies_noalloc": ([C.POINTER(cl_model), i32, d, d, vp, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -154,6 +156,17 @@ def make_init(phi0=(0, 0, 0, 0), dphi0=(0, 0, 0, 0), seed=0, spectrum=1, fluct_s
     p = (C.c_double * 4)(*(list(phi0) + [0.0] * (4 - len(phi0))))
     dp = (C.c_double * 4)(*(list(dphi0) + [0.0] * (4 - len(dphi0))))
     return cl_init(p, dp, seed, spectrum, 0, fluct_scale, a0)
+
+
+def energies_noalloc(model, N, kIR, a, phi, pi, out, stream=None):
+    """lattice_energies_noalloc on caller-owned device tensors (float64, CUDA):
+    phi, pi of n_fields x N^3, out of 10 doubles; allocates nothing on the device."""
+    for t in (phi, pi, out):
+        p, dev = _dev_ptr(t)
+        if not dev:
+            raise ValueError("phi, pi and out must be CUDA float64 tensors")
+    _check(load().lattice_energies_noalloc(C.byref(model), int(N), float(kIR), float(a), _dev_ptr(phi)[0],
+                                           _dev_ptr(pi)[0], _dev_ptr(out)[0], _stream_ptr(stream)))
 
 
 class Lattice:

@@ -206,6 +206,11 @@ struct CkptHeader {
 
 }  // namespace
 
+namespace cl {
+// Records the reason of a failure that has no handle (reported by cl_last_error(NULL)).
+void set_global_error(const char* msg) { g_err = msg; }
+}  // namespace cl
+
 extern "C" {
 
 const char* cl_status_str(cl_status s) {
