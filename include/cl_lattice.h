@@ -205,6 +205,33 @@ cl_status lattice_restore(cl_lattice* h, const char* path);
 /* Free everything the handle owns.  NULL is accepted. */
 cl_status lattice_destroy(cl_lattice* h);
 
+/* ------------------------------------------------------------------ ensembles
+ * Batched parameter scans (a workload pattern around the paper's method, not a
+ * part of it): n independent lattices of the two-field model of section 8.1,
+ * V = phi^2/2 + (q/2) phi^2 chi^2 (model->pexp = 2, n_fields = 2), that differ
+ * in the coupling q[i], the size N[i] (multiples of 32, up to 1024) and the
+ * seed seeds[i], advanced together: one persistent kernel launch per
+ * integrator pass covers every member (velocity-Verlet VV2 or VV4, a time step
+ * grid->dt common to all members, which must satisfy every member's stability
+ * bound).  Each member is an ordinary lattice initialised as by lattice_init;
+ * ensemble_member() lends its handle for measurements (do not destroy it).
+ *
+ * ensemble_observe writes, per member, CL_OBS_SIZE floats: the daughter-field
+ * energy fraction (E_K[1] + E_G[1]) / rho, the equation of state w, and log10
+ * of the chi power spectrum (section 3.1) at the 32 momenta
+ * k_j = k_IR (k_max/k_IR)^((j + 1/2)/32), j = 0..31, k_max = sqrt(3) N_min k_IR / 2
+ * (N_min the smallest member), interpolated linearly in (log k, log Delta)
+ * between the shells.  *t (may be NULL) receives the program time.
+ * Synchronizes the stream. */
+typedef struct cl_ensemble cl_ensemble;
+#define CL_OBS_SIZE 34
+cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const int32_t* N, const uint64_t* seeds,
+                        const cl_grid* grid, const cl_init* init, void* cuda_stream, cl_ensemble** out);
+cl_status ensemble_evolve(cl_ensemble* e, int64_t nsteps);
+cl_status ensemble_observe(cl_ensemble* e, float* obs, double* t);
+cl_status ensemble_member(cl_ensemble* e, int32_t i, cl_lattice** out);
+cl_status ensemble_destroy(cl_ensemble* e);
+
 /* Volume-averaged energies and means of caller-owned scalar fields, computed
  * without allocating any device memory.  The paper has no counterpart: this
  * serves callers that cannot allocate -- code running under CUDA stream capture,

@@ -66,7 +66,9 @@ class cl_means(C.Structure):
 SYMBOLS = ["cl_status_str", "cl_last_error", "lattice_init", "lattice_evolve", "lattice_measure_means",
            "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_get_field", "lattice_set_field",
            "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy",
-           "lattice_energies_noalloc"]
+           "lattice_energies_noalloc", "ensemble_init", "ensemble_evolve", "ensemble_observe",
+           "ensemble_member", "ensemble_destroy"]
+CL_OBS_SIZE = 34
 
 _lib = None
 
@@ -103,6 +105,12 @@ def load(build_if_missing=True):
         "lattice_restore": ([vp, C.c_char_p], C.c_int),
         "lattice_destroy": ([vp], C.c_int),
         "lattice_energies_noalloc": ([C.POINTER(cl_model), i32, d, d, vp, vp, vp, vp], C.c_int),
+        "ensemble_init": ([i32, C.POINTER(cl_model), pd, C.POINTER(C.c_int32), C.POINTER(C.c_uint64),
+                           C.POINTER(cl_grid), C.POINTER(cl_init), vp, C.POINTER(vp)], C.c_int),
+        "ensemble_evolve": ([vp, i64], C.c_int),
+        "ensemble_observe": ([vp, C.POINTER(C.c_float), pd], C.c_int),
+        "ensemble_member": ([vp, i32, C.POINTER(vp)], C.c_int),
+        "ensemble_destroy": ([vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -235,3 +243,57 @@ class Lattice:
 
     def restore(self, path):
         _check(load().lattice_restore(self.h, path.encode()), self.h)
+
+
+class _Member(Lattice):
+    """Borrowed handle of an ensemble member (owned by the ensemble)."""
+
+    def __init__(self, h, N):
+        self.h = h
+        self.N = N
+
+    def close(self):
+        self.h = None
+
+
+class Ensemble:
+    """Owner of one cl_ensemble (see include/cl_lattice.h)."""
+
+    def __init__(self, model, q, Ns, seeds, grid, init, stream=None):
+        lib = load()
+        n = len(q)
+        qa = np.ascontiguousarray(q, dtype=np.float64)
+        Na = np.ascontiguousarray(Ns, dtype=np.int32)
+        sa = np.ascontiguousarray(seeds, dtype=np.uint64)
+        h = C.c_void_p()
+        _check(lib.ensemble_init(n, C.byref(model), qa.ctypes.data_as(C.POINTER(C.c_double)),
+                                 Na.ctypes.data_as(C.POINTER(C.c_int32)), sa.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                 C.byref(grid), C.byref(init), _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self.n = n
+        self.Ns = list(Na)
+
+    def evolve(self, nsteps):
+        _check(load().ensemble_evolve(self.h, int(nsteps)))
+
+    def observe(self):
+        out = np.zeros((self.n, CL_OBS_SIZE), dtype=np.float32)
+        t = C.c_double(0.0)
+        _check(load().ensemble_observe(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), C.byref(t)))
+        return out, t.value
+
+    def member(self, i):
+        h = C.c_void_p()
+        _check(load().ensemble_member(self.h, int(i), C.byref(h)))
+        return _Member(h, self.Ns[i])
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -113,7 +113,20 @@ struct Lattice {
     int sm_count;
     cudaStream_t cstream;  // private stream used only to record graphs
     bool staggered;        // host mirror of DevState::staggered
+    bool shared_fft;       // plans and FFT scratch belong to an ensemble
 };
+
+// cuFFT plans and FP64 scratch that the members of an ensemble of one lattice size share.
+struct SharedFFT {
+    cufftHandle c2r, r2c;
+    double* work;
+    void* cwork;
+};
+
+// lattice_init with optional shared FFT resources (lattice_api.cu).
+cl_status lattice_create(const cl_model* model, const cl_grid* grid, const cl_init* init, cudaStream_t stream,
+                         const SharedFFT* shared, cl_lattice** out);
+void set_global_error(const char* msg);
 
 // ---- device helpers -------------------------------------------------------
 

@@ -1,0 +1,646 @@
+// Batched ensembles: many independent scalar lattices (same model family,
+// different coupling q, size N and seed) advanced together, one persistent
+// kernel launch per integrator pass for all of them, replayed as CUDA graphs.
+//
+// Every member is an ordinary lattice (its own arrays, FP64 background and
+// means); the ensemble kernel walks one global list of 32 x 32 x ZC tiles
+// spanning all members.  Per tile it loads the member's scalars, streams the
+// planes through the same cp.async shared-memory ring as the single-lattice
+// pass, and reduces the tile's sums into that member's per-tile partials; the
+// block that completes a member's last tile sums them in a fixed order and
+// runs the member's FP64 background update (sections 4.2.3 and 4.3.2).
+// Members therefore advance in lockstep through the same schedule of passes,
+// with a time step common to all of them.
+//
+// Observations per member (workload pattern, section 4.4): the daughter-field
+// energy fraction eps_chi = (E_K[chi] + E_G[chi]) / rho, the equation of state
+// w = (E_K - E_G/3 - E_V)/rho, and log10 of the chi power spectrum (section 3.1)
+// at 32 log-spaced momenta in [k_IR, sqrt(3) N_min k_IR / 2], interpolated
+// linearly in (log k, log Delta) between the shells of the lattice.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cl_internal.cuh"
+#include "scalar_common.cuh"
+
+struct cl_lattice : public cl::Lattice {};
+
+namespace cl {
+
+struct EnsLat {
+    const void* buf[2][4];  // ping-pong copies of delta phi_0, delta phi_1, delta pi_0, delta pi_1
+    DevState* st;
+    double* partials;  // per tile: NS sums
+    unsigned int* counter;
+    ModelConst mc;
+    int N, ntx, nty, ntz, ntiles, tile_base;
+};
+
+struct EnsArgs {
+    const EnsLat* lat;
+    const int* tile_lat;  // global tile -> member
+    int ntiles;
+    int src;  // copy holding the input
+    int write;
+    PassInfo pi;
+    int BX, BY, ZC, S;
+};
+
+template <typename T, int NF, int P>
+__global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) {
+    constexpr int V = VecT<T>::V;
+    constexpr int NS = 6 * NF + 2;
+    constexpr int NA = 2 * NF;
+    const int BX = A.BX, BY = A.BY, ZC = A.ZC, S = A.S;
+    const int TX = BX * V, RW = TX + 2 * V, ROWS = BY + 2;
+    const int ASZ = ROWS * RW, STG = NA * ASZ;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw + 128);
+    __shared__ double red[8][16];
+    __shared__ double tot[16];
+    __shared__ unsigned int last;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int lin = ty * BX + tx, nthr = BX * BY;
+    const int lane = lin & 31, warp = lin >> 5, nwarps = (nthr + 31) >> 5;
+    const int nlanes = min(32, nthr - 32 * warp);
+    const unsigned wmask = nlanes >= 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
+    const int dst = 1 - A.src;
+    const int my_tiles = (blockIdx.x < (unsigned)A.ntiles) ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    const bool yhalo = (ty == 0) || (ty == BY - 1);
+    const bool xhalo = (tx == 0) || (tx == BX - 1);
+    const int yh_row = (ty == 0) ? 0 : BY + 1;
+    const int xh_col = (tx == 0) ? V - 1 : V + TX;
+
+    // producer side: member, origin and arrays of the tile being loaded
+    int ld_k = 0, ld_p = 0, ld_slot = 0;
+    int ld_N = 0, ld_x0 = 0, ld_y0 = 0, ld_z0 = 0;
+    const T* ld_src[NA];
+    auto ld_tile = [&](int k) {
+        const int g = (int)blockIdx.x + k * (int)gridDim.x;
+        const EnsLat& L = A.lat[A.tile_lat[g]];
+        const int loc = g - L.tile_base;
+        const int tyi = loc % L.nty, rr = loc / L.nty, txi = rr % L.ntx, tzi = rr / L.ntx;
+        ld_N = L.N;
+        ld_x0 = txi * TX;
+        ld_y0 = tyi * BY;
+        ld_z0 = tzi * ZC;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) ld_src[a] = static_cast<const T*>(L.buf[A.src][a]);
+    };
+    if (my_tiles > 0) ld_tile(0);
+    auto issue = [&]() {
+        if (ld_k < my_tiles) {
+            const int N = ld_N;
+            int z = ld_z0 - 1 + ld_p;
+            z = z < 0 ? z + N : (z >= N ? z - N : z);
+            T* dstm = sm + ld_slot * STG;
+            const int x = ld_x0 + tx * V, y = ld_y0 + ty;
+            const size_t zoff = (size_t)z * N * N;
+            const int yh = (ty == 0) ? (y == 0 ? N - 1 : y - 1) : (y == N - 1 ? 0 : y + 1);
+            const int xh = (tx == 0) ? (x == 0 ? N - 1 : x - 1) : (x + V == N ? 0 : x + V);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const T* src = ld_src[a] + zoff;
+                T* d = dstm + a * ASZ;
+                cp_async16(d + (ty + 1) * RW + V + tx * V, src + (size_t)y * N + x);
+                if (yhalo) cp_async16(d + yh_row * RW + V + tx * V, src + (size_t)yh * N + x);
+                if (xhalo) cp_async_elem(d + (ty + 1) * RW + xh_col, src + (size_t)y * N + xh);
+            }
+            if (++ld_p == ZC + 2) {
+                ld_p = 0;
+                if (++ld_k < my_tiles) ld_tile(ld_k);
+            }
+            if (++ld_slot == S) ld_slot = 0;
+        }
+        cp_async_commit();
+    };
+    int issued = 0;
+    auto wait_for = [&](int need) {
+        switch (issued - 1 - need) {
+            case 0: cp_async_wait<0>(); break;
+            case 1: cp_async_wait<1>(); break;
+            case 2: cp_async_wait<2>(); break;
+            case 3: cp_async_wait<3>(); break;
+            default: cp_async_wait<4>(); break;
+        }
+        __syncthreads();
+    };
+    for (int L = 0; L < S; ++L, ++issued) issue();
+    int sl_m = 0, need = 2;
+
+    for (int k = 0; k < my_tiles; ++k) {
+        const int g = (int)blockIdx.x + k * (int)gridDim.x;
+        const int m = A.tile_lat[g];
+        const EnsLat& L = A.lat[m];
+        const int N = L.N;
+        const int loc = g - L.tile_base;
+        const int tyi = loc % L.nty, rr = loc / L.nty, txi = rr % L.ntx, tzi = rr / L.ntx;
+        const int x = txi * TX + tx * V, y = tyi * BY + ty, z0 = tzi * ZC;
+        const DevState* st = L.st;
+        const bool dead = st->error != 0;
+        const T cd = T(st->cd), A1 = T(st->A1), A3 = T(st->A3);
+        const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(L.mc.idx2);
+        const T lam = T(L.mc.lam), q = T(L.mc.q);
+        T fb[2], sf[2], sp[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            fb[f] = f < NF ? T(st->phibar[f]) : T(0);
+            sf[f] = f < NF ? T(st->sphi[f]) : T(0);
+            sp[f] = f < NF ? T(st->spi[f]) : T(0);
+        }
+        const T P0 = fb[0] * fb[0], C0 = fb[1] * fb[1];
+        const T c0[2] = {sf[0] + cd * sp[0], sf[1] + cd * sp[1]};
+        const int ob = (ty + 1) * RW + V + tx * V;
+        auto drift_stage = [&](T* Sx, T (&fo)[NF][V], T (&po)[NF][V]) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T* F = Sx + f * ASZ;
+                const T* Pp = Sx + (NF + f) * ASZ;
+                T rf[V], rp[V];
+                vload_s(F + ob, rf);
+                vload_s(Pp + ob, rp);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    po[f][v] = rp[v] - sp[f];
+                    fo[f][v] = (rf[v] + cd * rp[v]) - c0[f];
+                }
+                vstore(F + ob, fo[f]);
+                if (yhalo) {
+                    const int oh = yh_row * RW + V + tx * V;
+                    vload_s(F + oh, rf);
+                    vload_s(Pp + oh, rp);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) rf[v] = (rf[v] + cd * rp[v]) - c0[f];
+                    vstore(F + oh, rf);
+                }
+                if (xhalo) {
+                    const int oc = (ty + 1) * RW + xh_col;
+                    F[oc] = (F[oc] + cd * Pp[oc]) - c0[f];
+                }
+            }
+        };
+        T ts[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) ts[i] = T(0);
+        T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
+        for (int zz = 0; zz < ZC; ++zz, ++need) {
+            wait_for(need);
+            if (zz > 0) { issue(); ++issued; }
+            const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
+            const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
+            T* Sc = sm + sl_c * STG;
+            T* Sp = sm + sl_p * STG;
+            if (zz == 0) {
+                T dummy[NF][V];
+                drift_stage(sm + sl_m * STG, fm, dummy);
+                drift_stage(Sc, fc, pc);
+            }
+            drift_stage(Sp, fp, pn);
+            if (zz == 0) __syncthreads();
+            T lap[NF][V];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T* cF = Sc + f * ASZ;
+                const T fromL = __shfl_up_sync(wmask, fc[f][V - 1], 1);
+                const T fromR = __shfl_down_sync(wmask, fc[f][0], 1);
+                const bool useL = (tx > 0) && (lane > 0), useR = (tx < BX - 1) && (lane < nlanes - 1);
+                const T left = useL ? fromL : cF[ob - 1];
+                const T right = useR ? fromR : cF[ob + V];
+                T u[V], d[V];
+                vload_s(cF + ob - RW, u);
+                vload_s(cF + ob + RW, d);
+                T gs = T(0);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const T xl = (v == 0) ? left : fc[f][v - 1];
+                    const T xr = (v == V - 1) ? right : fc[f][v + 1];
+                    const T c = fc[f][v];
+                    lap[f][v] = (((xl + xr) + (u[v] + d[v])) + (fm[f][v] + fp[f][v]) - T(6) * c) * idx2;
+                    const T gx = xr - c, gy = d[v] - c, gz = fp[f][v] - c;
+                    gs += gx * gx + gy * gy + gz * gz;
+                }
+                ts[6 * f + 4] += gs;
+            }
+            T pout[NF][V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T d0 = fc[0][v];
+                const T d1 = NF > 1 ? fc[NF > 1 ? 1 : 0][v] : T(0);
+                T F[2];
+                F[0] = lam * Power<T, P>::dforce(fb[0], d0);
+                F[1] = T(0);
+                ts[6 * NF] += lam * Power<T, P>::dvalue(fb[0], d0);
+                if (NF > 1) {
+                    const T dP = d0 * (T(2) * fb[0] + d0), dC = d1 * (T(2) * fb[1] + d1);
+                    F[0] += q * (C0 * d0 + dC * (fb[0] + d0));
+                    F[1] = q * (P0 * d1 + dP * (fb[1] + d1));
+                    ts[6 * NF + 1] += T(0.5) * q * (dP * C0 + P0 * dC + dP * dC);
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T K = A1 * lap[f][v] - A3 * F[f];
+                    const T pr = pc[f][v] + h1 * K;
+                    pout[f][v] = pc[f][v] + h * K;
+                    ts[6 * f + 0] += fc[f][v];
+                    ts[6 * f + 1] += fc[f][v] * fc[f][v];
+                    ts[6 * f + 2] += pr;
+                    ts[6 * f + 3] += pr * pr;
+                    ts[6 * f + 5] += pout[f][v];
+                }
+            }
+            if (A.write && !dead) {
+                const size_t o = ((size_t)(z0 + zz) * N + y) * N + x;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    vstore_cs(static_cast<T*>(const_cast<void*>(L.buf[dst][f])) + o, fc[f]);
+                    vstore_cs(static_cast<T*>(const_cast<void*>(L.buf[dst][NF + f])) + o, pout[f]);
+                }
+            }
+            sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    fm[f][v] = fc[f][v];
+                    fc[f][v] = fp[f][v];
+                    pc[f][v] = pn[f][v];
+                }
+        }
+        __syncthreads();  // the tile's last three stages are free
+        issue();
+        issue();
+        issue();
+        issued += 3;
+        need += 2;
+        sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
+        // tile sums -> member partials; the block finishing the member's last tile updates it
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const T v = partial_warp_sum(ts[i], lane, nlanes);
+            if (lane == 0) red[warp][i] = double(v);
+        }
+        __syncthreads();
+        if (lin < NS) {
+            double t = 0.0;
+            for (int w = 0; w < nwarps; ++w) t += red[w][lin];
+            L.partials[(size_t)loc * NS + lin] = t;
+        }
+        __threadfence();
+        __syncthreads();
+        if (lin == 0) last = (atomicAdd(L.counter, 1u) == (unsigned)L.ntiles - 1) ? 1u : 0u;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            if (lin < NS) {
+                double ks = 0.0, kc = 0.0;
+                for (int b = 0; b < L.ntiles; ++b) {
+                    const double xv = __ldcg(&L.partials[(size_t)b * NS + lin]);
+                    const double yk = xv - kc, tk = ks + yk;
+                    kc = (tk - ks) - yk;
+                    ks = tk;
+                }
+                tot[lin] = (ks - kc) / ((double)N * N * N);
+            }
+            __syncthreads();
+            if (lin == 0) {
+                *L.counter = 0u;
+                scalar_finish(L.st, tot, L.mc, A.pi, sizeof(T) == 4);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace cl
+
+// ------------------------------------------------------------------- host side
+
+struct cl_ensemble {
+    std::vector<cl_lattice*> mem;
+    std::map<int, cl::SharedFFT> fft;  // per lattice size
+    cl::EnsLat* d_lat = nullptr;
+    int* d_tile_lat = nullptr;
+    int ntiles = 0, grid = 0, BX = 8, BY = 32, ZC = 32, S = 5;
+    size_t smem = 0;
+    int prec = CL_FP32, nf = 2, pexp = 2;
+    int cur = 0;
+    double dt = 0, kIR = 0;
+    int nmin = 0;
+    long long steps = 0;
+    std::vector<double> weights;
+    cudaStream_t stream = nullptr, cstream = nullptr;
+    struct G { long long steps; int parity; int end_parity; cudaGraphExec_t exec; };
+    std::vector<G> graphs;
+    std::vector<cl::EnsLat> host_lat;
+};
+
+namespace {
+
+cl_status efail(cl_status s, const std::string& m) {
+    cl::set_global_error(m.c_str());
+    return s;
+}
+
+const void* ens_kernel(int prec, int nf, int pexp) {
+    if (nf != 2 || pexp != 2) return nullptr;
+    return prec == CL_FP32 ? (const void*)cl::ensemble_pass_kernel<float, 2, 2>
+                           : (const void*)cl::ensemble_pass_kernel<double, 2, 2>;
+}
+
+cudaError_t ens_launch(cl_ensemble* E, int src, const cl::PassInfo& pi, bool write, cudaStream_t s) {
+    cl::EnsArgs A;
+    A.lat = E->d_lat;
+    A.tile_lat = E->d_tile_lat;
+    A.ntiles = E->ntiles;
+    A.src = src;
+    A.write = write ? 1 : 0;
+    A.pi = pi;
+    A.BX = E->BX;
+    A.BY = E->BY;
+    A.ZC = E->ZC;
+    A.S = E->S;
+    const dim3 block(E->BX, E->BY);
+    if (E->prec == CL_FP32) cl::ensemble_pass_kernel<float, 2, 2><<<E->grid, block, E->smem, s>>>(A);
+    else cl::ensemble_pass_kernel<double, 2, 2><<<E->grid, block, E->smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+cl::PassInfo mkpass(int kind, double dt, double wc, double wn, double h1, double h) {
+    cl::PassInfo p;
+    p.kind = kind; p.pad = 0; p.dt = dt; p.wc = wc; p.wn = wn; p.h1 = h1; p.h = h;
+    return p;
+}
+
+cudaError_t ens_enqueue(cl_ensemble* E, long long m, int* cur, cudaStream_t s) {
+    const auto& w = E->weights;
+    const double dt = E->dt;
+    const long long S = (long long)w.size(), P = m * S;
+    cudaError_t e = ens_launch(E, *cur, mkpass(cl::PK_VV_FIRST, dt, 0, w[0], 0, 0.5 * w[0] * dt), true, s);
+    if (e != cudaSuccess) return e;
+    *cur ^= 1;
+    for (long long j = 1; j < P; ++j) {
+        const double wc = w[(j - 1) % S], wn = w[j % S];
+        e = ens_launch(E, *cur, mkpass(cl::PK_VV_MID, dt, wc, wn, 0.5 * wc * dt, 0.5 * (wc + wn) * dt), true, s);
+        if (e != cudaSuccess) return e;
+        *cur ^= 1;
+    }
+    const double wc = w[(P - 1) % S];
+    e = ens_launch(E, *cur, mkpass(cl::PK_VV_LAST, dt, wc, 0, 0.5 * wc * dt, 0.5 * wc * dt), true, s);
+    if (e != cudaSuccess) return e;
+    *cur ^= 1;
+    return cudaSuccess;
+}
+
+std::vector<double> ens_weights(int integ) {
+    const double c = cbrt(2.0);
+    if (integ == CL_INT_VV4) return {1.0 / (2.0 - c), -c / (2.0 - c), 1.0 / (2.0 - c)};
+    return {1.0};
+}
+
+}  // namespace
+
+extern "C" {
+
+cl_status ensemble_destroy(cl_ensemble* E) {
+    if (!E) return CL_OK;
+    for (auto& g : E->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto* L : E->mem) lattice_destroy(L);
+    for (auto& kv : E->fft) {
+        cufftDestroy(kv.second.c2r);
+        cufftDestroy(kv.second.r2c);
+        cudaFree(kv.second.work);
+        cudaFree(kv.second.cwork);
+    }
+    if (E->d_lat) cudaFree(E->d_lat);
+    if (E->d_tile_lat) cudaFree(E->d_tile_lat);
+    if (E->cstream) cudaStreamDestroy(E->cstream);
+    delete E;
+    return CL_OK;
+}
+
+cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const int32_t* Ns, const uint64_t* seeds,
+                        const cl_grid* grid, const cl_init* init, void* cuda_stream, cl_ensemble** out) {
+    if (!out) return efail(CL_ERR_ARG, "ensemble_init: out is NULL");
+    *out = nullptr;
+    if (n < 1 || !model || !q || !Ns || !seeds || !grid || !init)
+        return efail(CL_ERR_ARG, "ensemble_init: n >= 1 and non-NULL arrays required");
+    if (model->kind != CL_MODEL_SCALAR || model->n_fields != 2 || model->pexp != 2)
+        return efail(CL_ERR_ARG, "ensemble_init: ensembles run the two-field model V = phi^2/2 + q phi^2 chi^2/2");
+    if (grid->integrator != CL_INT_VV2 && grid->integrator != CL_INT_VV4)
+        return efail(CL_ERR_ARG, "ensemble_init: ensembles run VV2 or VV4");
+    for (int i = 0; i < n; ++i)
+        if (Ns[i] < 32 || Ns[i] % 32 != 0 || Ns[i] > 1024 || !(q[i] >= 0))
+            return efail(CL_ERR_ARG, "ensemble_init: every N must be a multiple of 32 in [32, 1024] and q >= 0");
+    cl_ensemble* E = new cl_ensemble();
+    E->prec = grid->precision;
+    E->dt = grid->dt;
+    E->kIR = grid->kIR;
+    E->weights = ens_weights(grid->integrator);
+    E->stream = (cudaStream_t)cuda_stream;
+    E->BX = E->prec == CL_FP32 ? 8 : 16;
+    E->BY = E->prec == CL_FP32 ? 32 : 16;
+    E->ZC = 32;
+    E->S = 5;
+    E->nmin = *std::min_element(Ns, Ns + n);
+    if (cudaStreamCreateWithFlags(&E->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+        ensemble_destroy(E);
+        return efail(CL_ERR_CUDA, "ensemble_init: stream creation failed");
+    }
+    // shared FFT resources per lattice size
+    for (int i = 0; i < n; ++i) {
+        const int N = Ns[i];
+        if (E->fft.count(N)) continue;
+        cl::SharedFFT f;
+        const size_t n3 = (size_t)N * N * N, nh = (size_t)N * N * (N / 2 + 1);
+        if (cufftPlan3d(&f.c2r, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS ||
+            cufftPlan3d(&f.r2c, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS || cudaMalloc(&f.work, n3 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&f.cwork, 2 * nh * sizeof(double2)) != cudaSuccess) {
+            ensemble_destroy(E);
+            return efail(CL_ERR_OOM, "ensemble_init: FFT resources");
+        }
+        cufftSetStream(f.c2r, E->stream);
+        cufftSetStream(f.r2c, E->stream);
+        E->fft[N] = f;
+    }
+    // members
+    for (int i = 0; i < n; ++i) {
+        cl_model m = *model;
+        m.q = q[i];
+        cl_grid g = *grid;
+        g.N = Ns[i];
+        cl_init in = *init;
+        in.seed = seeds[i];
+        cl_lattice* L = nullptr;
+        cl_status s = cl::lattice_create(&m, &g, &in, E->stream, &E->fft[Ns[i]], &L);
+        if (s != CL_OK) {
+            std::string msg = "ensemble_init: member " + std::to_string(i) + ": " + cl_last_error(nullptr);
+            ensemble_destroy(E);
+            return efail(s, msg);
+        }
+        E->mem.push_back(L);
+    }
+    // tile list
+    std::vector<int> tile_lat;
+    for (int i = 0; i < n; ++i) {
+        cl::Lattice* L = E->mem[i];
+        cl::EnsLat d;
+        for (int c = 0; c < 2; ++c)
+            for (int a = 0; a < 4; ++a) d.buf[c][a] = L->buf.f[c][a];
+        d.st = L->buf.st;
+        d.partials = L->buf.partials;
+        d.counter = L->buf.counter;
+        d.mc = L->mc;
+        d.N = L->mc.N;
+        const int V = E->prec == CL_FP32 ? 4 : 2;
+        d.ntx = d.N / (E->BX * V);
+        d.nty = d.N / E->BY;
+        d.ntz = d.N / E->ZC;
+        d.ntiles = d.ntx * d.nty * d.ntz;
+        d.tile_base = (int)tile_lat.size();
+        for (int t = 0; t < d.ntiles; ++t) tile_lat.push_back(i);
+        E->host_lat.push_back(d);
+    }
+    E->ntiles = (int)tile_lat.size();
+    if (cudaMalloc(&E->d_lat, sizeof(cl::EnsLat) * n) != cudaSuccess ||
+        cudaMalloc(&E->d_tile_lat, sizeof(int) * tile_lat.size()) != cudaSuccess) {
+        ensemble_destroy(E);
+        return efail(CL_ERR_OOM, "ensemble_init: tile list");
+    }
+    cudaMemcpy(E->d_lat, E->host_lat.data(), sizeof(cl::EnsLat) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(E->d_tile_lat, tile_lat.data(), sizeof(int) * tile_lat.size(), cudaMemcpyHostToDevice);
+    const int V = E->prec == CL_FP32 ? 4 : 2;
+    const size_t stage = 4 * (size_t)(E->BY + 2) * (E->BX * V + 2 * V) * (E->prec == CL_FP32 ? 4 : 8);
+    E->smem = 128 + E->S * stage;
+    const void* fn = ens_kernel(E->prec, 2, 2);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem);
+    int per_sm = 1, sms = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, E->BX * E->BY, E->smem);
+    if (per_sm < 1) per_sm = 1;
+    E->grid = std::min(E->ntiles, sms * per_sm);
+    if (cudaStreamSynchronize(E->stream) != cudaSuccess) {
+        ensemble_destroy(E);
+        return efail(CL_ERR_CUDA, "ensemble_init: synchronization");
+    }
+    *out = E;
+    return CL_OK;
+}
+
+cl_status ensemble_evolve(cl_ensemble* E, int64_t nsteps) {
+    if (!E || nsteps < 0) return efail(CL_ERR_ARG, "ensemble_evolve: bad arguments");
+    const long long chunk = 64;
+    long long left = nsteps;
+    while (left > 0) {
+        const long long m = left < chunk ? left : chunk;
+        cudaGraphExec_t exec = nullptr;
+        int endp = E->cur;
+        for (auto& g : E->graphs)
+            if (g.steps == m && g.parity == E->cur) { exec = g.exec; endp = g.end_parity; }
+        if (!exec) {
+            int cur = E->cur;
+            cudaGraph_t graph;
+            if (cudaStreamBeginCapture(E->cstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return efail(CL_ERR_CUDA, "ensemble_evolve: capture");
+            cudaError_t e = ens_enqueue(E, m, &cur, E->cstream);
+            cudaError_t e2 = cudaStreamEndCapture(E->cstream, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) return efail(CL_ERR_CUDA, "ensemble_evolve: recording");
+            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return efail(CL_ERR_CUDA, "ensemble_evolve: instantiate");
+            }
+            cudaGraphDestroy(graph);
+            cl_ensemble::G g;
+            g.steps = m;
+            g.parity = E->cur;
+            g.end_parity = cur;
+            g.exec = exec;
+            E->graphs.push_back(g);
+            endp = cur;
+        }
+        if (cudaGraphLaunch(exec, E->stream) != cudaSuccess) return efail(CL_ERR_CUDA, "ensemble_evolve: launch");
+        E->cur = endp;
+        left -= m;
+    }
+    E->steps += nsteps;
+    for (auto* L : E->mem) {
+        L->cur = E->cur;
+        L->steps_done = E->steps;
+    }
+    return CL_OK;
+}
+
+cl_status ensemble_member(cl_ensemble* E, int32_t i, cl_lattice** out) {
+    if (!E || !out || i < 0 || i >= (int)E->mem.size()) return efail(CL_ERR_ARG, "ensemble_member: bad index");
+    *out = E->mem[i];
+    return CL_OK;
+}
+
+cl_status ensemble_observe(cl_ensemble* E, float* obs, double* t) {
+    if (!E || !obs) return efail(CL_ERR_ARG, "ensemble_observe: NULL argument");
+    const int n = (int)E->mem.size();
+    // reductions of every member in one launch, then the chi spectra (cuFFT per member)
+    cudaError_t e = ens_launch(E, E->cur, mkpass(cl::PK_MEASURE, E->dt, 0, 0, 0, 0), false, E->stream);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cl::launch_spectrum(E->mem[i], 1, 0, E->stream);
+    std::vector<cl::DevState> st(n);
+    std::vector<std::vector<double>> bins(n);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync(&st[i], E->mem[i]->buf.st, sizeof(cl::DevState), cudaMemcpyDeviceToHost, E->stream);
+        bins[i].resize(3 * (size_t)cl::spectrum_bins(E->mem[i]->mc.N));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bins[i].data(), E->mem[i]->bins, bins[i].size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, E->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    if (e != cudaSuccess) return efail(CL_ERR_CUDA, std::string("ensemble_observe: ") + cudaGetErrorString(e));
+    const double kmax = sqrt(3.0) * 0.5 * E->nmin * E->kIR, kIR = E->kIR;
+    for (int i = 0; i < n; ++i) {
+        float* o = obs + (size_t)i * CL_OBS_SIZE;
+        const cl::DevState& s = st[i];
+        if (s.error) {
+            for (int j = 0; j < CL_OBS_SIZE; ++j) o[j] = NAN;
+            continue;
+        }
+        const double EK = s.E[0] + s.E[1], EG = s.E[2] + s.E[3], EV = s.E[4] + s.E[5];
+        const double rho = EK + EG + EV;
+        o[0] = (float)((s.E[1] + s.E[3]) / rho);
+        o[1] = (float)((EK - EG / 3.0 - EV) / rho);
+        // shell spectrum, then log-log interpolation at 32 log-spaced momenta
+        const int N = E->mem[i]->mc.N, nb = cl::spectrum_bins(N);
+        const double dx = E->mem[i]->mc.dx;
+        const double norm = pow(dx / N, 3.0) / (2.0 * M_PI * M_PI);
+        std::vector<double> lk, lD;
+        for (int b = 1; b < nb; ++b) {
+            const double c = bins[i][2 * (size_t)nb + b];
+            if (c <= 0) continue;
+            const double k = kIR * bins[i][(size_t)nb + b] / c;
+            const double D = k * k * k * norm * bins[i][b] / c;
+            if (D > 0) { lk.push_back(log(k)); lD.push_back(log10(D)); }
+        }
+        for (int j = 0; j < 32; ++j) {
+            const double lkj = log(kIR) + (j + 0.5) / 32.0 * (log(kmax) - log(kIR));
+            double v = NAN;
+            if (!lk.empty()) {
+                if (lkj <= lk.front()) v = lD.front();
+                else if (lkj >= lk.back()) v = lD.back();
+                else {
+                    size_t u = std::upper_bound(lk.begin(), lk.end(), lkj) - lk.begin();
+                    const double f = (lkj - lk[u - 1]) / (lk[u] - lk[u - 1]);
+                    v = lD[u - 1] + f * (lD[u] - lD[u - 1]);
+                }
+            }
+            o[2 + j] = (float)v;
+        }
+    }
+    if (t) *t = st.empty() ? 0.0 : st[0].t;
+    return CL_OK;
+}
+
+}  // extern "C"

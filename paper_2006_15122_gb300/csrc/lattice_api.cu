@@ -242,12 +242,14 @@ cl_status lattice_destroy(cl_lattice* h) {
     if (h->buf.st) cudaFree(h->buf.st);
     if (h->buf.partials) cudaFree(h->buf.partials);
     if (h->buf.counter) cudaFree(h->buf.counter);
-    if (h->work) cudaFree(h->work);
-    if (h->cwork) cudaFree(h->cwork);
     if (h->bins) cudaFree(h->bins);
-    if (h->plans) {
-        cufftDestroy(h->plan_c2r);
-        cufftDestroy(h->plan_r2c);
+    if (!h->shared_fft) {
+        if (h->work) cudaFree(h->work);
+        if (h->cwork) cudaFree(h->cwork);
+        if (h->plans) {
+            cufftDestroy(h->plan_c2r);
+            cufftDestroy(h->plan_r2c);
+        }
     }
     if (h->cstream) cudaStreamDestroy(h->cstream);
     delete h;
@@ -256,6 +258,13 @@ cl_status lattice_destroy(cl_lattice* h) {
 
 cl_status lattice_init(const cl_model* model, const cl_grid* grid, const cl_init* init, void* cuda_stream,
                        cl_lattice** out) {
+    return cl::lattice_create(model, grid, init, (cudaStream_t)cuda_stream, nullptr, out);
+}
+
+}  // extern "C"
+
+cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const cl_init* init, cudaStream_t cuda_stream,
+                             const cl::SharedFFT* shared, cl_lattice** out) {
     if (!out) return fail(nullptr, CL_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!model || !grid || !init) return fail(nullptr, CL_ERR_ARG, "model, grid and init must be non-NULL");
@@ -280,6 +289,7 @@ cl_status lattice_init(const cl_model* model, const cl_grid* grid, const cl_init
     memset(L->buf.f, 0, sizeof(L->buf.f));
     L->buf.st = nullptr; L->buf.partials = nullptr; L->buf.counter = nullptr;
     L->work = nullptr; L->cwork = nullptr; L->bins = nullptr; L->plans = false; L->cstream = nullptr;
+    L->shared_fft = shared != nullptr;
     L->grid = *grid;
     L->init = *init;
     if (!(L->init.a0 > 0)) L->init.a0 = 1.0;
@@ -347,24 +357,32 @@ cl_status lattice_init(const cl_model* model, const cl_grid* grid, const cl_init
     if ((e = cudaMalloc(&L->buf.st, sizeof(cl::DevState))) != cudaSuccess ||
         (e = cudaMalloc(&L->buf.partials, sizeof(double) * cl::kMaxBlocks * cl::kMaxSums)) != cudaSuccess ||
         (e = cudaMalloc(&L->buf.counter, sizeof(unsigned int))) != cudaSuccess ||
-        (e = cudaMalloc(&L->work, n * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&L->cwork, 2 * nh * sizeof(double2))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&L->cstream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&L->bins, 3 * sizeof(double) * (size_t)lattice_spectrum_bins(L))) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&L->cstream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (!shared && ((e = cudaMalloc(&L->work, n * sizeof(double))) != cudaSuccess ||
+                     (e = cudaMalloc(&L->cwork, 2 * nh * sizeof(double2))) != cudaSuccess))) {
         cl_status s = cuda_fail(nullptr, e, "allocating scratch");
         lattice_destroy(L);
         return s;
     }
     cudaMemsetAsync(L->buf.counter, 0, sizeof(unsigned int), L->stream);
     cudaMemsetAsync(L->buf.st, 0, sizeof(cl::DevState), L->stream);
-    if (cufftPlan3d(&L->plan_c2r, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS ||
-        cufftPlan3d(&L->plan_r2c, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS) {
-        lattice_destroy(L);
-        return fail(nullptr, CL_ERR_CUDA, "cuFFT plan creation failed");
+    if (shared) {
+        L->plan_c2r = shared->c2r;
+        L->plan_r2c = shared->r2c;
+        L->work = shared->work;
+        L->cwork = shared->cwork;
+        L->plans = true;
+    } else {
+        if (cufftPlan3d(&L->plan_c2r, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS ||
+            cufftPlan3d(&L->plan_r2c, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS) {
+            lattice_destroy(L);
+            return fail(nullptr, CL_ERR_CUDA, "cuFFT plan creation failed");
+        }
+        L->plans = true;
+        cufftSetStream(L->plan_c2r, L->stream);
+        cufftSetStream(L->plan_r2c, L->stream);
     }
-    L->plans = true;
-    cufftSetStream(L->plan_c2r, L->stream);
-    cufftSetStream(L->plan_r2c, L->stream);
     if (mc.kind == CL_MODEL_SCALAR) cl::scalar_geometry(L);
     else cl::u1_geometry(L);
 
@@ -384,6 +402,8 @@ cl_status lattice_init(const cl_model* model, const cl_grid* grid, const cl_init
     *out = L;
     return CL_OK;
 }
+
+extern "C" {
 
 cl_status lattice_evolve(cl_lattice* h, int64_t nsteps) {
     if (!h) return fail(nullptr, CL_ERR_ARG, "NULL handle");
