@@ -13,6 +13,7 @@ What it computes (each function cites the passage it follows):
   ic.py            initial conditions of section 7
   spectra.py       DFT convention and power spectra (sections 3.1, 4.4.2)
   philox.py        Philox4x32-10, the counter-based generator of the draws
+  mlp.py           FP64 reference of the surrogate MLP (forward, loss, gradient)
 
 Pins (tests/test_oracle_*.py, run with -m "not gpu") check it against closed
 forms: exact per-mode dispersion of the free lattice field, the Jacobi-
@@ -21,6 +22,6 @@ expanding homogeneous mode, symplectic convergence orders, reversibility,
 summation by parts, Parseval, the Gauss law to round-off, gauge invariance,
 energy conservation and Philox known-answer vectors.
 """
-from . import core, ic, philox, spectra  # noqa: F401
+from . import core, ic, mlp, philox, spectra  # noqa: F401
 from .core import (VV2, VV4, VV6, VV8, VV10, ScalarLattice, ScalarModel, U1Lattice,  # noqa: F401
                    U1Model)
