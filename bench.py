@@ -46,6 +46,15 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--scan", action="store_true",
+                   help="time the batched ensemble + surrogate parameter scan instead of the single lattice")
+    p.add_argument("--scan-runs", type=int, default=512)
+    p.add_argument("--scan-slices", type=int, default=64)
+    p.add_argument("--scan-steps-per-slice", type=int, default=32)
+    p.add_argument("--scan-heldout", type=int, default=64)
+    p.add_argument("--scan-seeds", type=int, default=6)
+    p.add_argument("--scan-plain", type=int, default=12)
+    p.add_argument("--scan-epochs", type=int, default=200)
     return p.parse_args()
 
 
@@ -156,10 +165,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_scan(args):
+    """Parameter scan of the two-field model over q log-uniform in [1e2, 1e5]:
+    (i) the plain method, one lattice at a time, timed on a sample cycling
+    through the sizes; (ii) one batched ensemble of all runs (autotuned tiles,
+    CUDA graphs), whose observations train the surrogate, which then answers
+    held-out couplings scored against fresh lattice runs."""
+    import numpy as np
+    import torch
+
+    import paper_2006_15122_gb300 as cl
+    from paper_2006_15122_gb300 import scan
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    spec = scan.ScanSpec(steps_per_slice=args.scan_steps_per_slice, n_slices=args.scan_slices)
+    n = args.scan_runs
+    qs = scan.log_uniform_q(n, 1e2, 1e5, seed=1234)
+    Ns = scan.cycle_sizes(n, spec.sizes)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    # (i) plain: one lattice at a time (warm one run of each size first: plans, graphs)
+    for N in spec.sizes:
+        scan.plain_observations(scan.ScanSpec(sizes=spec.sizes, steps_per_slice=1, n_slices=1), qs[0], N, 0, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.scan_plain):
+        scan.plain_observations(spec, qs[i], Ns[i], i, stream)
+    t_plain = (time.perf_counter() - t0) / max(args.scan_plain, 1)
+    # (ii) batched ensemble of every run
+    obs, times, info = scan.ensemble_observations(spec, qs, Ns, list(range(n)), stream=stream)
+    t_ens = info["init_s"] + info["tune_s"] + info["evolve_observe_s"]
+    X, Y = scan.training_pairs(qs, times, obs)
+    net, hist, t_train = scan.fit_surrogate(X, Y, epochs=args.scan_epochs, stream=stream)
+    # held-out couplings: fresh lattice runs (R seeds each, batched) as the judge
+    Q, R = args.scan_heldout, args.scan_seeds
+    qh = scan.log_uniform_q(Q, 1e2, 1e5, seed=4321)
+    Nh = scan.cycle_sizes(Q * R, spec.sizes)
+    ref, _, _ = scan.ensemble_observations(spec, np.repeat(qh, R), Nh, list(range(10 ** 6, 10 ** 6 + Q * R)),
+                                           stream=stream)
+    ref = ref.reshape(Q, R, spec.n_slices, -1)
+    Xq = np.stack([np.repeat(np.log10(qh), spec.n_slices), np.tile(times, Q)], axis=1)
+    net.predict(Xq)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pred = net.predict(Xq).reshape(Q, spec.n_slices, -1)
+    t_query = time.perf_counter() - t0
+    clk = clocks.stop()
+    err = scan.score(pred, ref)
+    net.close()
+    site_steps = sum(N ** 3 for N in Ns) * spec.steps_per_slice * spec.n_slices
+    runs_hr_plain = 3600.0 / t_plain
+    runs_hr_batched = 3600.0 * n / t_ens
+    runs_hr_surrogate = 3600.0 * Q / t_query
+    line = {
+        "metric": "ensemble scan runs/hr", "value": runs_hr_batched, "unit": "runs/hr", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32 lattice, bf16/f32 surrogate", "data": "synthetic",
+        "config": {"workload": "%d runs of the two-field q* = 4q model, q log-uniform in [1e2, 1e5] (seed 1234), "
+                               "N cycling %s, seeds 0..%d, VV4 dt %g, %d slices every %d steps (t_end %.3g), "
+                               "observables eps_chi, w and the 32-point log10 chi spectrum"
+                               % (n, list(spec.sizes), n - 1, spec.dt, spec.n_slices, spec.steps_per_slice,
+                                  times[-1]),
+                   "surrogate": "MLP 2-256-256-256-34 GELU, BF16 tensor-core GEMMs, FP32 accumulate, Adam, "
+                                "%d epochs, batch 512, %d training rows" % (args.scan_epochs, len(X)),
+                   "heldout": "%d q log-uniform in [1e2, 1e5] (seed 4321), %d fresh seeds each" % (Q, R)},
+        "plain_runs_per_hr": runs_hr_plain, "batched_runs_per_hr": runs_hr_batched,
+        "surrogate_runs_per_hr": runs_hr_surrogate,
+        "batched_speedup": runs_hr_batched / runs_hr_plain,
+        "seconds": {"plain_per_run": t_plain, "ensemble_total": t_ens, "ensemble_init": info["init_s"],
+                    "autotune": info["tune_s"], "ensemble_evolve_observe": info["evolve_observe_s"],
+                    "train": t_train, "query_all_heldout": t_query},
+        "site_updates_per_s_batched": site_steps / info["evolve_observe_s"],
+        "tile": info["tile"], "autotune": [[list(t), ms] for t, ms in info["candidates"]],
+        "train_loss_first_last": [float(hist[0]), float(hist[-1])],
+        "error": err, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.scan:
+        return run_scan(args)
     import torch
 
     import paper_2006_15122_gb300 as cl

@@ -219,8 +219,9 @@ cl_status lattice_destroy(cl_lattice* h);
  * ensemble_observe writes, per member, CL_OBS_SIZE floats: the daughter-field
  * energy fraction (E_K[1] + E_G[1]) / rho, the equation of state w, and log10
  * of the chi power spectrum (section 3.1) at the 32 momenta
- * k_j = k_IR (k_max/k_IR)^((j + 1/2)/32), j = 0..31, k_max = sqrt(3) N_min k_IR / 2
- * (N_min the smallest member), interpolated linearly in (log k, log Delta)
+ * k_j = k_IR (k_max/k_IR)^((j + 1/2)/32), j = 0..31, k_max = N_min k_IR / 2
+ * (N_min the smallest member: its Nyquist momentum along an axis; shells
+ * beyond it are incomplete), interpolated linearly in (log k, log Delta)
  * between the shells.  *t (may be NULL) receives the program time.
  * Synchronizes the stream. */
 typedef struct cl_ensemble cl_ensemble;
@@ -231,6 +232,33 @@ cl_status ensemble_evolve(cl_ensemble* e, int64_t nsteps);
 cl_status ensemble_observe(cl_ensemble* e, float* obs, double* t);
 cl_status ensemble_member(cl_ensemble* e, int32_t i, cl_lattice** out);
 cl_status ensemble_destroy(cl_ensemble* e);
+
+/* Tile shape of the ensemble pass, tile = {BX, BY, ZC, S}: a block of BX x BY
+ * threads (each thread owns 4 consecutive FP32 or 2 FP64 sites along x) walks
+ * ZC planes along z through S shared-memory stages.  Admissible shapes divide
+ * every member's N, make whole warps of at most 256 threads, fit the shared
+ * memory and 4 <= S <= 6; ensemble_init installs {8, 32, 32, 5} (FP32) or
+ * {16, 16, 32, 5} (FP64) and fails with CL_ERR_ARG when that shape does not
+ * fit.  set_tile rejects inadmissible shapes with CL_ERR_ARG (nothing
+ * changed). */
+cl_status ensemble_get_tile(const cl_ensemble* e, int32_t tile[4]);
+cl_status ensemble_set_tile(cl_ensemble* e, const int32_t tile[4]);
+/* Autotuner: times every admissible shape of a fixed candidate list on the
+ * ensemble's own members (one warm-up and three timed integrator passes each,
+ * CUDA events on the ensemble's stream), installs the fastest and leaves the
+ * ensemble's physical state as it was (the timing passes write only the spare
+ * copy of the fields and every member's scalar state is restored).  The first
+ * min(n_tried, max_report) shapes tried and their mean pass times in ms go to
+ * tiles (4 per shape) and ms when these are not NULL; *n_tried (may be NULL)
+ * receives the number tried.  Synchronizes the stream. */
+cl_status ensemble_autotune(cl_ensemble* e, int32_t max_report, int32_t* tiles, double* ms, int32_t* n_tried);
+
+/* The CL_OBS_SIZE observables of ensemble_observe for one lattice of the
+ * two-field model under a velocity-Verlet integrator (CL_ERR_ARG otherwise),
+ * the 32 spectrum momenta spread between k_IR and kmax (kmax <= 0 selects
+ * N k_IR / 2).  *t (may be NULL) receives the program time.
+ * Synchronizes the stream. */
+cl_status lattice_observe(cl_lattice* h, double kmax, float* obs, double* t);
 
 /* Volume-averaged energies and means of caller-owned scalar fields, computed
  * without allocating any device memory.  The paper has no counterpart: this
@@ -259,6 +287,73 @@ cl_status ensemble_destroy(cl_ensemble* e);
 #define CL_NOALLOC_MAX_N 2048
 cl_status lattice_energies_noalloc(const cl_model* model, int32_t N, double kIR, double a, const double* phi,
                                    const double* pi, double* out, void* cuda_stream);
+
+/* ------------------------------------------------------------------ surrogate
+ * A multilayer perceptron fitted to ensemble observations (a workload pattern
+ * around the paper's method, not a part of it): it maps n_in inputs (e.g.
+ * log10 q and the program time) to n_out observables (e.g. the CL_OBS_SIZE
+ * values of ensemble_observe), so that a parameter scan can be interpolated
+ * between the simulated couplings.
+ *
+ *   H_0 = X,  Z_l = H_l W_l^T + b_l,  H_{l+1} = GELU(Z_l) for the `depth`
+ *   hidden layers of `width` units,  Y = Z_depth (linear output),
+ *   loss = mean over samples and outputs of (Y - T)^2,
+ *   GELU(x) = x/2 (1 + erf(x/sqrt 2)).
+ *
+ * Every GEMM (forward, input gradient, weight gradient) runs on the tensor
+ * cores with BF16 operands and FP32 accumulation; parameters, Adam moments
+ * and the bias/GELU epilogues are FP32.  Weights start N(0, 1/fan_in) drawn by
+ * Philox4x32-10 keyed by `seed`, biases zero.
+ *
+ * All array arguments are HOST pointers, row-major: X is n x n_in, Y and T
+ * are n x n_out (float).  Calls are enqueued on cuda_stream (NULL = legacy
+ * default stream) and synchronize it before returning.  The handle owns its
+ * device memory; buffers grow with the largest batch seen.  Invalid sizes or
+ * NULL pointers give CL_ERR_ARG (nothing is changed), allocation failures
+ * CL_ERR_OOM, runtime failures CL_ERR_CUDA; the reason is in
+ * cl_last_error(NULL). */
+typedef struct cl_surrogate cl_surrogate;
+
+typedef struct {
+    int32_t epochs;      /* passes over the training set (>= 1) */
+    int32_t batch;       /* minibatch rows (>= 1; clipped to n) */
+    float lr;            /* Adam step size (> 0) */
+    float beta1, beta2;  /* Adam decay rates (<= 0 selects 0.9, 0.999) */
+    float eps;           /* Adam epsilon (<= 0 selects 1e-8) */
+    float weight_decay;  /* L2 coefficient added to the weight gradients (biases exempt) */
+    int32_t standardize; /* nonzero: fit on inputs and targets shifted and scaled to zero
+                            mean and unit variance per column (the mapping is kept and
+                            undone by surrogate_predict) */
+    float lr_end;        /* >= 0: cosine decay of the step size from lr to lr_end over the
+                            minibatch steps of this call; < 0: constant lr */
+    int32_t shuffle;     /* nonzero: a fresh order of the samples every epoch (Fisher-Yates,
+                            keyed by the handle's seed and its epoch count); 0: in order */
+} cl_train_cfg;
+
+/* n_in, n_out in [1, 1024], width in [1, 4096], depth (hidden layers) in
+ * [1, 16].  *out receives the handle. */
+cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t depth, uint64_t seed,
+                           void* cuda_stream, cl_surrogate** out);
+/* Number of trainable parameters: sum over layers of d_out*d_in + d_out. */
+int64_t surrogate_param_count(const cl_surrogate* s);
+/* Parameters as doubles in the order W_0 (d_1 x d_0 row-major), b_0, W_1, b_1, ...
+ * (surrogate_param_count values).  set rounds them to FP32. */
+cl_status surrogate_get_params(cl_surrogate* s, double* theta);
+cl_status surrogate_set_params(cl_surrogate* s, const double* theta);
+/* Loss and gradient of the raw (unstandardized) mean squared error over the n
+ * rows of X and T in one batch, without changing the parameters; grad (may be
+ * NULL) receives surrogate_param_count doubles in the order of get_params. */
+cl_status surrogate_loss_grad(cl_surrogate* s, const float* X, const float* T, int64_t n, double* loss,
+                              double* grad);
+/* Adam training on n rows (n <= 2^24).  loss_history (may be NULL) receives
+ * cfg->epochs floats: the mean squared error (in standardized units when
+ * cfg->standardize) accumulated over each epoch's minibatches. */
+cl_status surrogate_train(cl_surrogate* s, const float* X, const float* Y, int64_t n, const cl_train_cfg* cfg,
+                          float* loss_history);
+/* Y = network(X) for n rows (n <= 2^24), in the targets' original units. */
+cl_status surrogate_predict(cl_surrogate* s, const float* X, int64_t n, float* Y);
+/* Free everything the handle owns.  NULL is accepted. */
+cl_status surrogate_destroy(cl_surrogate* s);
 
 #ifdef __cplusplus
 }

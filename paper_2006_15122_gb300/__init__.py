@@ -63,11 +63,20 @@ class cl_means(C.Structure):
                 ("hubble_violation", C.c_double), ("gauss_violation", C.c_double), ("reserved", C.c_double * 4)]
 
 
+class cl_train_cfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("weight_decay", C.c_float), ("standardize", C.c_int32),
+                ("lr_end", C.c_float), ("shuffle", C.c_int32)]
+
+
 SYMBOLS = ["cl_status_str", "cl_last_error", "lattice_init", "lattice_evolve", "lattice_measure_means",
            "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_get_field", "lattice_set_field",
            "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy",
            "lattice_energies_noalloc", "ensemble_init", "ensemble_evolve", "ensemble_observe",
-           "ensemble_member", "ensemble_destroy"]
+           "ensemble_member", "ensemble_destroy", "ensemble_get_tile", "ensemble_set_tile",
+           "ensemble_autotune", "lattice_observe", "surrogate_create", "surrogate_param_count",
+           "surrogate_get_params", "surrogate_set_params", "surrogate_loss_grad", "surrogate_train",
+           "surrogate_predict", "surrogate_destroy"]
 CL_OBS_SIZE = 34
 
 _lib = None
@@ -89,7 +98,7 @@ def load(build_if_missing=True):
         _build.build()
     lib = C.CDLL(path)
     vp, d, i32, i64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64
-    pd = C.POINTER(C.c_double)
+    pd, pf = C.POINTER(C.c_double), C.POINTER(C.c_float)
     sig = {
         "cl_status_str": ([C.c_int], C.c_char_p),
         "cl_last_error": ([vp], C.c_char_p),
@@ -111,6 +120,18 @@ def load(build_if_missing=True):
         "ensemble_observe": ([vp, C.POINTER(C.c_float), pd], C.c_int),
         "ensemble_member": ([vp, i32, C.POINTER(vp)], C.c_int),
         "ensemble_destroy": ([vp], C.c_int),
+        "ensemble_get_tile": ([vp, C.POINTER(C.c_int32)], C.c_int),
+        "ensemble_set_tile": ([vp, C.POINTER(C.c_int32)], C.c_int),
+        "ensemble_autotune": ([vp, i32, C.POINTER(C.c_int32), pd, C.POINTER(C.c_int32)], C.c_int),
+        "lattice_observe": ([vp, d, pf, pd], C.c_int),
+        "surrogate_create": ([i32, i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
+        "surrogate_param_count": ([vp], i64),
+        "surrogate_get_params": ([vp, pd], C.c_int),
+        "surrogate_set_params": ([vp, pd], C.c_int),
+        "surrogate_loss_grad": ([vp, pf, pf, i64, pd, pd], C.c_int),
+        "surrogate_train": ([vp, pf, pf, i64, C.POINTER(cl_train_cfg), pf], C.c_int),
+        "surrogate_predict": ([vp, pf, i64, pf], C.c_int),
+        "surrogate_destroy": ([vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -221,6 +242,14 @@ class Lattice:
                                                c.ctypes.data_as(C.POINTER(C.c_int64))), self.h)
         return k, D, c
 
+    def observe(self, kmax=0.0):
+        """The CL_OBS_SIZE observables (see lattice_observe) and the program time."""
+        out = np.zeros(CL_OBS_SIZE, dtype=np.float32)
+        t = C.c_double(0.0)
+        _check(load().lattice_observe(self.h, float(kmax), out.ctypes.data_as(C.POINTER(C.c_float)), C.byref(t)),
+               self.h)
+        return out, t.value
+
     def get_field(self, which, out=None):
         N = self.N
         if out is None:
@@ -282,6 +311,23 @@ class Ensemble:
         _check(load().ensemble_observe(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), C.byref(t)))
         return out, t.value
 
+    def tile(self):
+        t = (C.c_int32 * 4)()
+        _check(load().ensemble_get_tile(self.h, t))
+        return tuple(t)
+
+    def set_tile(self, tile):
+        t = (C.c_int32 * 4)(*[int(v) for v in tile])
+        _check(load().ensemble_set_tile(self.h, t))
+
+    def autotune(self, max_report=16):
+        """Runs the tile autotuner; returns [(tile, ms per pass), ...] for the shapes tried."""
+        tiles = (C.c_int32 * (4 * max_report))()
+        ms = (C.c_double * max_report)()
+        n = C.c_int32(0)
+        _check(load().ensemble_autotune(self.h, int(max_report), tiles, ms, C.byref(n)))
+        return [(tuple(tiles[4 * i:4 * i + 4]), ms[i]) for i in range(min(n.value, max_report))]
+
     def member(self, i):
         h = C.c_void_p()
         _check(load().ensemble_member(self.h, int(i), C.byref(h)))
@@ -290,6 +336,80 @@ class Ensemble:
     def close(self):
         if getattr(self, "h", None):
             load().ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _f32(x, cols):
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != cols:
+        raise ValueError("expected an (n, %d) array, got shape %s" % (cols, a.shape))
+    return a
+
+
+class Surrogate:
+    """Owner of one cl_surrogate: BF16 tensor-core MLP (see include/cl_lattice.h)."""
+
+    def __init__(self, n_in, n_out, width=256, depth=3, seed=0, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.surrogate_create(int(n_in), int(n_out), int(width), int(depth), int(seed), _stream_ptr(stream),
+                                    C.byref(h)))
+        self.h = h
+        self.n_in, self.n_out, self.width, self.depth = int(n_in), int(n_out), int(width), int(depth)
+        self.dims = [self.n_in] + [self.width] * self.depth + [self.n_out]
+
+    def param_count(self):
+        return int(load().surrogate_param_count(self.h))
+
+    def get_params(self):
+        out = np.zeros(self.param_count(), dtype=np.float64)
+        _check(load().surrogate_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float64)
+        if t.size != self.param_count():
+            raise ValueError("expected %d parameters" % self.param_count())
+        _check(load().surrogate_set_params(self.h, t.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def loss_grad(self, X, T):
+        X, T = _f32(X, self.n_in), _f32(T, self.n_out)
+        loss = C.c_double(0.0)
+        g = np.zeros(self.param_count(), dtype=np.float64)
+        pf = C.POINTER(C.c_float)
+        _check(load().surrogate_loss_grad(self.h, X.ctypes.data_as(pf), T.ctypes.data_as(pf), X.shape[0],
+                                          C.byref(loss), g.ctypes.data_as(C.POINTER(C.c_double))))
+        return loss.value, g
+
+    def train(self, X, Y, epochs, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+              standardize=True, lr_end=-1.0, shuffle=False):
+        """Adam on (X, Y); lr_end >= 0 anneals the step size (cosine) to lr_end.
+        Returns the per-epoch mean squared error."""
+        X, Y = _f32(X, self.n_in), _f32(Y, self.n_out)
+        cfg = cl_train_cfg(int(epochs), int(batch), lr, beta1, beta2, eps, weight_decay, int(bool(standardize)),
+                           float(lr_end), int(bool(shuffle)))
+        hist = np.zeros(int(epochs), dtype=np.float32)
+        pf = C.POINTER(C.c_float)
+        _check(load().surrogate_train(self.h, X.ctypes.data_as(pf), Y.ctypes.data_as(pf), X.shape[0], C.byref(cfg),
+                                      hist.ctypes.data_as(pf)))
+        return hist
+
+    def predict(self, X):
+        X = _f32(X, self.n_in)
+        Y = np.zeros((X.shape[0], self.n_out), dtype=np.float32)
+        pf = C.POINTER(C.c_float)
+        _check(load().surrogate_predict(self.h, X.ctypes.data_as(pf), X.shape[0], Y.ctypes.data_as(pf)))
+        return Y
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().surrogate_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -285,6 +285,10 @@ cudaError_t launch_set_field(Lattice* L, int which, const double* src, cudaStrea
 cudaError_t launch_spectrum(Lattice* L, int slot, int accumulate, cudaStream_t s);
 int spectrum_bins(int N);
 
+// ensemble.cu: the CL_OBS_SIZE observables of a two-field lattice from its
+// measured state and chi shell sums (3 x spectrum_bins(N) doubles)
+void observables(const DevState& s, const double* bins, int N, double dx, double kIR, double kmax, float* o);
+
 int array_count(const ModelConst& mc);
 int array_slot(const ModelConst& mc, int which);  // ABI index -> storage slot, -1 if invalid
 

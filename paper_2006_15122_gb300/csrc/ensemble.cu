@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
     __shared__ double red[8][16];
     __shared__ double tot[16];
     __shared__ unsigned int last;
+    __shared__ T* s_out[2 * NF];  // destination arrays of the tile's member
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int lin = ty * BX + tx, nthr = BX * BY;
     const int lane = lin & 31, warp = lin >> 5, nwarps = (nthr + 31) >> 5;
@@ -142,6 +143,11 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
         const int loc = g - L.tile_base;
         const int tyi = loc % L.nty, rr = loc / L.nty, txi = rr % L.ntx, tzi = rr / L.ntx;
         const int x = txi * TX + tx * V, y = tyi * BY + ty, z0 = tzi * ZC;
+        // the member's output pointers go through shared memory: read from the
+        // member table inside the plane loop they would be reloaded from global
+        // memory every plane (the stores may alias the table); visible after the
+        // barrier of the first wait below, unused since the previous tile's end
+        if (lin < NA) s_out[lin] = static_cast<T*>(const_cast<void*>(L.buf[dst][lin]));
         const DevState* st = L.st;
         const bool dead = st->error != 0;
         const T cd = T(st->cd), A1 = T(st->A1), A3 = T(st->A3);
@@ -258,8 +264,8 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
                 const size_t o = ((size_t)(z0 + zz) * N + y) * N + x;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    vstore_cs(static_cast<T*>(const_cast<void*>(L.buf[dst][f])) + o, fc[f]);
-                    vstore_cs(static_cast<T*>(const_cast<void*>(L.buf[dst][NF + f])) + o, pout[f]);
+                    vstore_cs(s_out[f] + o, fc[f]);
+                    vstore_cs(s_out[NF + f] + o, pout[f]);
                 }
             }
             sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
@@ -318,6 +324,50 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
     cp_async_wait<0>();
 }
 
+
+// Observables of one lattice of the two-field model from its measured state
+// and chi shell sums: the chi energy fraction (E_K[1] + E_G[1]) / rho, the
+// equation of state w = (E_K - E_G/3 - E_V) / rho, and log10 of the power
+// spectrum (section 3.1) interpolated linearly in (log k, log10 Delta) at 32
+// log-spaced momenta between kIR and kmax (constant beyond the end shells).
+void observables(const DevState& s, const double* bins, int N, double dx, double kIR, double kmax, float* o) {
+    if (s.error) {
+        for (int j = 0; j < CL_OBS_SIZE; ++j) o[j] = NAN;
+        return;
+    }
+    const double EK = s.E[0] + s.E[1], EG = s.E[2] + s.E[3], EV = s.E[4] + s.E[5];
+    const double rho = EK + EG + EV;
+    o[0] = (float)((s.E[1] + s.E[3]) / rho);
+    o[1] = (float)((EK - EG / 3.0 - EV) / rho);
+    const int nb = spectrum_bins(N);
+    const double norm = pow(dx / N, 3.0) / (2.0 * M_PI * M_PI);
+    std::vector<double> lk, lD;
+    for (int b = 1; b < nb; ++b) {
+        const double c = bins[2 * (size_t)nb + b];
+        if (c <= 0) continue;
+        const double k = kIR * bins[(size_t)nb + b] / c;
+        const double D = k * k * k * norm * bins[b] / c;
+        if (D > 0) {
+            lk.push_back(log(k));
+            lD.push_back(log10(D));
+        }
+    }
+    for (int j = 0; j < 32; ++j) {
+        const double lkj = log(kIR) + (j + 0.5) / 32.0 * (log(kmax) - log(kIR));
+        double v = NAN;
+        if (!lk.empty()) {
+            if (lkj <= lk.front()) v = lD.front();
+            else if (lkj >= lk.back()) v = lD.back();
+            else {
+                const size_t u = std::upper_bound(lk.begin(), lk.end(), lkj) - lk.begin();
+                const double f = (lkj - lk[u - 1]) / (lk[u] - lk[u - 1]);
+                v = lD[u - 1] + f * (lD[u] - lD[u - 1]);
+            }
+        }
+        o[2 + j] = (float)v;
+    }
+}
+
 }  // namespace cl
 
 // ------------------------------------------------------------------- host side
@@ -339,6 +389,7 @@ struct cl_ensemble {
     struct G { long long steps; int parity; int end_parity; cudaGraphExec_t exec; };
     std::vector<G> graphs;
     std::vector<cl::EnsLat> host_lat;
+    int max_smem = 0;
 };
 
 namespace {
@@ -404,6 +455,74 @@ std::vector<double> ens_weights(int integ) {
     return {1.0};
 }
 
+
+// A tile shape (BX, BY, ZC, S) is admissible when it divides every member,
+// forms whole warps of at most 256 threads, fits the shared memory, and keeps
+// each member's per-tile partial sums inside its partials array.
+bool tile_ok(const cl_ensemble* E, const int32_t t[4], std::string* why) {
+    const int V = E->prec == CL_FP32 ? 4 : 2, BX = t[0], BY = t[1], ZC = t[2], S = t[3];
+    const int nthr = BX * BY;
+    if (BX < 2 || BY < 2 || nthr % 32 != 0 || nthr > 256 || ZC < 2 || S < 4 || S > 6) {
+        *why = "tile needs BX, BY >= 2, BX*BY a multiple of 32 up to 256, ZC >= 2 and 4 <= S <= 6";
+        return false;
+    }
+    const size_t stage = 4 * (size_t)(BY + 2) * (BX * V + 2 * V) * (E->prec == CL_FP32 ? 4 : 8);
+    if (128 + S * stage > (size_t)E->max_smem) {
+        *why = "tile stages exceed the shared memory of a block";
+        return false;
+    }
+    for (const auto& d : E->host_lat) {
+        if (d.N % (BX * V) || d.N % BY || d.N % ZC) {
+            *why = "tile does not divide N = " + std::to_string(d.N);
+            return false;
+        }
+        const long long nt = (long long)(d.N / (BX * V)) * (d.N / BY) * (d.N / ZC);
+        if (nt * 14 > (long long)cl::kMaxBlocks * cl::kMaxSums) {
+            *why = "too many tiles for N = " + std::to_string(d.N) + " (take larger tiles)";
+            return false;
+        }
+    }
+    return true;
+}
+
+// installs an admissible tile shape: tile list, shared memory and persistent grid
+cl_status apply_tile(cl_ensemble* E, const int32_t t[4]) {
+    const int V = E->prec == CL_FP32 ? 4 : 2;
+    E->BX = t[0]; E->BY = t[1]; E->ZC = t[2]; E->S = t[3];
+    std::vector<int> tile_lat;
+    for (size_t i = 0; i < E->host_lat.size(); ++i) {
+        cl::EnsLat& d = E->host_lat[i];
+        d.ntx = d.N / (E->BX * V);
+        d.nty = d.N / E->BY;
+        d.ntz = d.N / E->ZC;
+        d.ntiles = d.ntx * d.nty * d.ntz;
+        d.tile_base = (int)tile_lat.size();
+        for (int k = 0; k < d.ntiles; ++k) tile_lat.push_back((int)i);
+    }
+    if (E->d_tile_lat) cudaFree(E->d_tile_lat);
+    E->d_tile_lat = nullptr;
+    E->ntiles = (int)tile_lat.size();
+    if (cudaMalloc(&E->d_tile_lat, sizeof(int) * tile_lat.size()) != cudaSuccess)
+        return efail(CL_ERR_OOM, "ensemble: tile list");
+    cudaError_t e = cudaMemcpyAsync(E->d_lat, E->host_lat.data(), sizeof(cl::EnsLat) * E->host_lat.size(),
+                                    cudaMemcpyHostToDevice, E->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E->d_tile_lat, tile_lat.data(), sizeof(int) * tile_lat.size(), cudaMemcpyHostToDevice,
+                            E->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    if (e != cudaSuccess) return efail(CL_ERR_CUDA, std::string("ensemble: tile list upload: ") + cudaGetErrorString(e));
+    const size_t stage = 4 * (size_t)(E->BY + 2) * (E->BX * V + 2 * V) * (E->prec == CL_FP32 ? 4 : 8);
+    E->smem = 128 + E->S * stage;
+    int per_sm = 1, sms = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ens_kernel(E->prec, 2, 2), E->BX * E->BY, E->smem);
+    if (per_sm < 1) per_sm = 1;
+    E->grid = std::min(E->ntiles, sms * per_sm);
+    for (auto& g : E->graphs) cudaGraphExecDestroy(g.exec);
+    E->graphs.clear();
+    return CL_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -444,10 +563,6 @@ cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const
     E->kIR = grid->kIR;
     E->weights = ens_weights(grid->integrator);
     E->stream = (cudaStream_t)cuda_stream;
-    E->BX = E->prec == CL_FP32 ? 8 : 16;
-    E->BY = E->prec == CL_FP32 ? 32 : 16;
-    E->ZC = 32;
-    E->S = 5;
     E->nmin = *std::min_element(Ns, Ns + n);
     if (cudaStreamCreateWithFlags(&E->cstream, cudaStreamNonBlocking) != cudaSuccess) {
         ensemble_destroy(E);
@@ -486,8 +601,7 @@ cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const
         }
         E->mem.push_back(L);
     }
-    // tile list
-    std::vector<int> tile_lat;
+    // member table, then the tile list of the default shape
     for (int i = 0; i < n; ++i) {
         cl::Lattice* L = E->mem[i];
         cl::EnsLat d;
@@ -498,34 +612,35 @@ cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const
         d.counter = L->buf.counter;
         d.mc = L->mc;
         d.N = L->mc.N;
-        const int V = E->prec == CL_FP32 ? 4 : 2;
-        d.ntx = d.N / (E->BX * V);
-        d.nty = d.N / E->BY;
-        d.ntz = d.N / E->ZC;
-        d.ntiles = d.ntx * d.nty * d.ntz;
-        d.tile_base = (int)tile_lat.size();
-        for (int t = 0; t < d.ntiles; ++t) tile_lat.push_back(i);
         E->host_lat.push_back(d);
     }
-    E->ntiles = (int)tile_lat.size();
-    if (cudaMalloc(&E->d_lat, sizeof(cl::EnsLat) * n) != cudaSuccess ||
-        cudaMalloc(&E->d_tile_lat, sizeof(int) * tile_lat.size()) != cudaSuccess) {
+    if (cudaMalloc(&E->d_lat, sizeof(cl::EnsLat) * n) != cudaSuccess) {
         ensemble_destroy(E);
-        return efail(CL_ERR_OOM, "ensemble_init: tile list");
+        return efail(CL_ERR_OOM, "ensemble_init: member table");
     }
-    cudaMemcpy(E->d_lat, E->host_lat.data(), sizeof(cl::EnsLat) * n, cudaMemcpyHostToDevice);
-    cudaMemcpy(E->d_tile_lat, tile_lat.data(), sizeof(int) * tile_lat.size(), cudaMemcpyHostToDevice);
-    const int V = E->prec == CL_FP32 ? 4 : 2;
-    const size_t stage = 4 * (size_t)(E->BY + 2) * (E->BX * V + 2 * V) * (E->prec == CL_FP32 ? 4 : 8);
-    E->smem = 128 + E->S * stage;
-    const void* fn = ens_kernel(E->prec, 2, 2);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem);
-    int per_sm = 1, sms = 1, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, E->BX * E->BY, E->smem);
-    if (per_sm < 1) per_sm = 1;
-    E->grid = std::min(E->ntiles, sms * per_sm);
+    for (const void* fn : {(const void*)cl::ensemble_pass_kernel<float, 2, 2>, (const void*)cl::ensemble_pass_kernel<double, 2, 2>}) {
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, fn);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const int avail = optin - (int)fa.sharedSizeBytes;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
+        if (fn == ens_kernel(E->prec, 2, 2)) E->max_smem = avail;
+    }
+    cudaGetLastError();
+    const int32_t def[4] = {E->prec == CL_FP32 ? 8 : 16, E->prec == CL_FP32 ? 32 : 16, 32, 5};
+    std::string why;
+    if (!tile_ok(E, def, &why)) {
+        ensemble_destroy(E);
+        return efail(CL_ERR_ARG, "ensemble_init: " + why);
+    }
+    cl_status ts = apply_tile(E, def);
+    if (ts != CL_OK) {
+        std::string msg = cl_last_error(nullptr);
+        ensemble_destroy(E);
+        return efail(ts, msg);
+    }
     if (cudaStreamSynchronize(E->stream) != cudaSuccess) {
         ensemble_destroy(E);
         return efail(CL_ERR_CUDA, "ensemble_init: synchronization");
@@ -600,47 +715,90 @@ cl_status ensemble_observe(cl_ensemble* E, float* obs, double* t) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
     if (e != cudaSuccess) return efail(CL_ERR_CUDA, std::string("ensemble_observe: ") + cudaGetErrorString(e));
-    const double kmax = sqrt(3.0) * 0.5 * E->nmin * E->kIR, kIR = E->kIR;
-    for (int i = 0; i < n; ++i) {
-        float* o = obs + (size_t)i * CL_OBS_SIZE;
-        const cl::DevState& s = st[i];
-        if (s.error) {
-            for (int j = 0; j < CL_OBS_SIZE; ++j) o[j] = NAN;
-            continue;
-        }
-        const double EK = s.E[0] + s.E[1], EG = s.E[2] + s.E[3], EV = s.E[4] + s.E[5];
-        const double rho = EK + EG + EV;
-        o[0] = (float)((s.E[1] + s.E[3]) / rho);
-        o[1] = (float)((EK - EG / 3.0 - EV) / rho);
-        // shell spectrum, then log-log interpolation at 32 log-spaced momenta
-        const int N = E->mem[i]->mc.N, nb = cl::spectrum_bins(N);
-        const double dx = E->mem[i]->mc.dx;
-        const double norm = pow(dx / N, 3.0) / (2.0 * M_PI * M_PI);
-        std::vector<double> lk, lD;
-        for (int b = 1; b < nb; ++b) {
-            const double c = bins[i][2 * (size_t)nb + b];
-            if (c <= 0) continue;
-            const double k = kIR * bins[i][(size_t)nb + b] / c;
-            const double D = k * k * k * norm * bins[i][b] / c;
-            if (D > 0) { lk.push_back(log(k)); lD.push_back(log10(D)); }
-        }
-        for (int j = 0; j < 32; ++j) {
-            const double lkj = log(kIR) + (j + 0.5) / 32.0 * (log(kmax) - log(kIR));
-            double v = NAN;
-            if (!lk.empty()) {
-                if (lkj <= lk.front()) v = lD.front();
-                else if (lkj >= lk.back()) v = lD.back();
-                else {
-                    size_t u = std::upper_bound(lk.begin(), lk.end(), lkj) - lk.begin();
-                    const double f = (lkj - lk[u - 1]) / (lk[u] - lk[u - 1]);
-                    v = lD[u - 1] + f * (lD[u] - lD[u - 1]);
-                }
-            }
-            o[2 + j] = (float)v;
-        }
-    }
+    const double kmax = 0.5 * E->nmin * E->kIR;
+    for (int i = 0; i < n; ++i)
+        cl::observables(st[i], bins[i].data(), E->mem[i]->mc.N, E->mem[i]->mc.dx, E->kIR, kmax,
+                        obs + (size_t)i * CL_OBS_SIZE);
     if (t) *t = st.empty() ? 0.0 : st[0].t;
     return CL_OK;
+}
+
+cl_status ensemble_get_tile(const cl_ensemble* E, int32_t tile[4]) {
+    if (!E || !tile) return efail(CL_ERR_ARG, "ensemble_get_tile: NULL argument");
+    tile[0] = E->BX; tile[1] = E->BY; tile[2] = E->ZC; tile[3] = E->S;
+    return CL_OK;
+}
+
+cl_status ensemble_set_tile(cl_ensemble* E, const int32_t tile[4]) {
+    if (!E || !tile) return efail(CL_ERR_ARG, "ensemble_set_tile: NULL argument");
+    std::string why;
+    if (!tile_ok(E, tile, &why)) return efail(CL_ERR_ARG, "ensemble_set_tile: " + why);
+    return apply_tile(E, tile);
+}
+
+cl_status ensemble_autotune(cl_ensemble* E, int32_t max_report, int32_t* tiles, double* ms, int32_t* n_tried) {
+    if (!E || max_report < 0) return efail(CL_ERR_ARG, "ensemble_autotune: bad arguments");
+    static const int32_t c32[][4] = {{8, 32, 32, 5}, {8, 32, 16, 5}, {8, 32, 32, 4}, {8, 32, 32, 6}, {8, 16, 32, 5},
+                                     {8, 16, 16, 5}, {4, 32, 32, 5}, {8, 8, 32, 5},  {4, 16, 32, 5}, {8, 32, 8, 5}};
+    static const int32_t c64[][4] = {{16, 16, 32, 5}, {16, 16, 16, 5}, {16, 16, 32, 4}, {16, 8, 32, 5}, {8, 32, 32, 5},
+                                     {8, 16, 32, 5},  {16, 16, 8, 5},  {8, 8, 32, 5},   {16, 4, 32, 5}, {4, 32, 32, 5}};
+    const int nc = 10;
+    const int32_t(*cand)[4] = E->prec == CL_FP32 ? c32 : c64;
+    const int n = (int)E->mem.size();
+    const int32_t keep[4] = {E->BX, E->BY, E->ZC, E->S};
+    // snapshot of every member's scalar state: the timing passes write only the
+    // spare copy of the fields, so restoring the states undoes them
+    cl::DevState* snap = nullptr;
+    if (cudaMalloc(&snap, sizeof(cl::DevState) * n) != cudaSuccess) return efail(CL_ERR_OOM, "ensemble_autotune");
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(snap + i, E->mem[i]->buf.st, sizeof(cl::DevState), cudaMemcpyDeviceToDevice, E->stream);
+    auto restore = [&]() {
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(E->mem[i]->buf.st, snap + i, sizeof(cl::DevState), cudaMemcpyDeviceToDevice, E->stream);
+    };
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    const double w0 = E->weights[0], dt = E->dt;
+    const cl::PassInfo pass = mkpass(cl::PK_VV_MID, dt, w0, w0, 0.5 * w0 * dt, w0 * dt);
+    int best = -1, tried = 0;
+    float best_ms = 0;
+    cl_status st = CL_OK;
+    for (int c = 0; c < nc && e == cudaSuccess && st == CL_OK; ++c) {
+        std::string why;
+        if (!tile_ok(E, cand[c], &why)) continue;
+        st = apply_tile(E, cand[c]);
+        if (st != CL_OK) break;
+        const int reps = 3;
+        e = ens_launch(E, E->cur, pass, true, E->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev0, E->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = ens_launch(E, E->cur, pass, true, E->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev1, E->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+        float t = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev0, ev1);
+        restore();
+        t /= reps;
+        if (tried < max_report) {
+            if (tiles)
+                for (int j = 0; j < 4; ++j) tiles[4 * tried + j] = cand[c][j];
+            if (ms) ms[tried] = t;
+        }
+        ++tried;
+        if (best < 0 || t < best_ms) {
+            best = c;
+            best_ms = t;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaFree(snap);
+    if (n_tried) *n_tried = tried;
+    if (st != CL_OK) return st;
+    if (e != cudaSuccess) return efail(CL_ERR_CUDA, std::string("ensemble_autotune: ") + cudaGetErrorString(e));
+    return apply_tile(E, best >= 0 ? cand[best] : keep);
 }
 
 }  // extern "C"

@@ -495,6 +495,25 @@ cl_status lattice_measure_means(cl_lattice* h, cl_means* out) {
     return CL_OK;
 }
 
+cl_status lattice_observe(cl_lattice* h, double kmax, float* obs, double* t) {
+    if (!h || !obs) return fail(h, CL_ERR_ARG, "NULL argument");
+    if (h->mc.kind != CL_MODEL_SCALAR || h->mc.nf != 2 || h->staggered)
+        return fail(h, CL_ERR_ARG, "observables need the two-field scalar model under a velocity-Verlet integrator");
+    if (!(kmax > 0)) kmax = 0.5 * h->mc.N * h->grid.kIR;
+    cudaError_t e = launch_pass(h, h->cur, 1 - h->cur, make_pass(cl::PK_MEASURE, h->grid.dt, 0, 0, 0, 0), false, h->stream);
+    if (e == cudaSuccess) e = cl::launch_spectrum(h, 1, 0, h->stream);
+    cl::DevState st;
+    std::vector<double> hb(3 * (size_t)cl::spectrum_bins(h->mc.N));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->buf.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb.data(), h->bins, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "observables");
+    cl::observables(st, hb.data(), h->mc.N, h->mc.dx, h->grid.kIR, kmax, obs);
+    if (t) *t = st.t;
+    return CL_OK;
+}
+
 cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, double* k, double* Delta,
                                    int64_t* counts) {
     if (!h || !k || !Delta || !counts) return fail(h, CL_ERR_ARG, "NULL argument");

@@ -423,6 +423,12 @@ void scalar_geometry(Lattice* L) {
     g.BY = by;
     int zc = N < want_zc ? N : want_zc;
     while (N % zc != 0) --zc;
+    // small lattices: shorter z columns, then fewer rows, until the tiles can
+    // occupy every SM twice (a 32^3 lattice would otherwise be one tile)
+    const int target = 2 * L->sm_count;
+    auto count = [&](int byv, int zcv) { return (N / (g.BX * g.V)) * (N / byv) * (N / zcv); };
+    while (count(g.BY, zc) < target && zc % 2 == 0 && zc / 2 >= 4) zc /= 2;
+    while (count(g.BY, zc) < target && g.BY % 2 == 0 && g.BY / 2 >= 4 && g.BX * g.BY / 2 >= 64) g.BY /= 2;
     g.ZC = zc;
     g.ntx = N / (g.BX * g.V);
     g.nty = N / g.BY;

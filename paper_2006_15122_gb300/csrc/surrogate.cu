@@ -1,0 +1,676 @@
+// Surrogate multilayer perceptron on BF16 tensor cores (a workload pattern
+// around the paper's method, not a part of the paper): maps (log10 q, t) to the
+// lattice observables of an ensemble scan.
+//
+//   H_0 = X,  Z_l = H_l W_l^T + b_l,  H_{l+1} = GELU(Z_l),  Y = Z_L,
+//   loss = mean (Y - T)^2,  GELU(x) = x/2 (1 + erf(x/sqrt 2)),
+// trained by Adam on FP32 master weights; every GEMM (forward, input and
+// weight gradients) runs on the tensor cores with BF16 operands and FP32
+// accumulation (mma.sync m16n8k16), the bias/GELU epilogues fused.
+// Matrices are stored row-major with every dimension padded with zeros to a
+// multiple of 32 (batch: 64), so that the GEMM needs no K-edge handling and the
+// padding stays zero through forward and backward passes.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "cl_internal.cuh"
+
+namespace cl {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------- GEMM
+// C[M x N] = A[M x K] . B[N x K]^T  (A, B bf16 row-major; K a multiple of 32)
+constexpr int GM = 64, GN = 64, GK = 32, SKP = GK + 8;  // shared row stride 40 bf16 (80 bytes)
+
+struct GemmArgs {
+    const bf16* A;
+    int lda;
+    const bf16* B;
+    int ldb;
+    float* C;
+    int ldc;
+    int M, N, K;
+    int mode;           // 0: C = acc;  1: C = Z = acc + bias, H = bf16(GELU(Z));  2: C = acc + bias
+    const float* bias;  // length >= Nvalid
+    bf16* H;
+    int ldh;
+    int Mvalid, Nvalid;  // outside: written as zero (keeps the padding zero)
+};
+
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_prime_f(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+__global__ void __launch_bounds__(128) gemm_tn_kernel(const GemmArgs g) {
+    __shared__ __align__(16) bf16 sA[2][GM * SKP];
+    __shared__ __align__(16) bf16 sB[2][GN * SKP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bm = blockIdx.y * GM, bn = blockIdx.x * GN;
+    const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    // each thread copies two 16-byte chunks of A and of B per k-tile (64 rows x 4 chunks)
+    auto load = [&](int buf, int k0) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int idx = tid + c * 128, row = idx >> 2, ch = idx & 3;
+            const int ra = bm + row, rb = bn + row;
+            cp_async16_zfill(&sA[buf][row * SKP + ch * 8], g.A + (size_t)(ra < g.M ? ra : 0) * g.lda + k0 + ch * 8, ra < g.M);
+            cp_async16_zfill(&sB[buf][row * SKP + ch * 8], g.B + (size_t)(rb < g.N ? rb : 0) * g.ldb + k0 + ch * 8, rb < g.N);
+        }
+        cp_async_commit();
+    };
+    const int nk = g.K / GK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) {
+            load((kt + 1) & 1, (kt + 1) * GK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const bf16* a = sA[kt & 1];
+        const bf16* b = sB[kt & 1];
+#pragma unroll
+        for (int kk = 0; kk < GK; kk += 16) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                ldmatrix_x4(af[i][0], af[i][1], af[i][2], af[i][3],
+                            &a[(wr + 16 * i + (lane & 15)) * SKP + kk + 8 * (lane >> 4)]);
+            uint32_t bfr[4][2];
+#pragma unroll
+            for (int jp = 0; jp < 2; ++jp) {
+                const int q = lane >> 3;
+                uint32_t r0, r1, r2, r3;
+                ldmatrix_x4(r0, r1, r2, r3, &b[(wc + 16 * jp + (q >> 1) * 8 + (lane & 7)) * SKP + kk + (q & 1) * 8]);
+                bfr[2 * jp][0] = r0;
+                bfr[2 * jp][1] = r1;
+                bfr[2 * jp + 1][0] = r2;
+                bfr[2 * jp + 1][1] = r3;
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
+        }
+        __syncthreads();
+    }
+    // epilogue: fragment (i, j) holds rows wr+16i+lane/4 (+8), columns wc+8j+2(lane%4) (+1)
+    const int gr = lane >> 2, tc = (lane & 3) * 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = bm + wr + 16 * i + gr + 8 * h;
+                if (r >= g.M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int c = bn + wc + 8 * j + tc + e;
+                    if (c >= g.N) continue;
+                    const bool valid = r < g.Mvalid && c < g.Nvalid;
+                    float v = acc[i][j][2 * h + e];
+                    if (g.mode != 0) v = valid ? v + g.bias[c] : 0.f;
+                    g.C[(size_t)r * g.ldc + c] = v;
+                    if (g.mode == 1) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(valid ? gelu_f(v) : 0.f);
+                }
+            }
+}
+
+// ---------------------------------------------------------------- helpers
+__global__ void transpose_bf16_kernel(const bf16* in, int ldi, bf16* out, int ldo, int R, int Cc) {
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < R && c < Cc) ? in[(size_t)r * ldi + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < Cc && r < R) out[(size_t)c * ldo + r] = t[threadIdx.x][k];
+    }
+}
+
+__global__ void f32_to_bf16_kernel(const float* in, bf16* out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16(in[i]);
+}
+
+// standardized inputs into the padded bf16 H_0 (rows >= n and columns >= n_in are zero)
+// row r of the batch is sample idx[r0 + r] (r0 + r when idx is NULL)
+__device__ __forceinline__ size_t sample_row(const int* idx, int64_t r0, int r) {
+    return idx ? (size_t)idx[r0 + r] : (size_t)(r0 + r);
+}
+
+__global__ void load_inputs_kernel(const float* X, const int* idx, int64_t r0, int n, int n_in, const float* mu,
+                                   const float* sd, bf16* H0, int ld, int Bp) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)Bp * ld; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ld), c = (int)(i % ld);
+        float v = 0.f;
+        if (r < n && c < n_in) v = (X[sample_row(idx, r0, r) * n_in + c] - mu[c]) / sd[c];
+        H0[i] = __float2bfloat16(v);
+    }
+}
+
+// dY = 2 (Y - T_std) / (n n_out) into fp32 and bf16 (padding zero), and the loss sum
+__global__ void loss_grad_kernel(const float* Y, int ldy, const float* T, const int* idx, int64_t r0, int n, int n_out,
+                                 const float* mu, const float* sd, float* dZ, bf16* dZb, int ld, int Bp, double* loss) {
+    double s = 0.0;
+    const float scale = 2.0f / ((float)n * (float)n_out);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)Bp * ld; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ld), c = (int)(i % ld);
+        float g = 0.f;
+        if (r < n && c < n_out) {
+            const float d = Y[(size_t)r * ldy + c] - (T[sample_row(idx, r0, r) * n_out + c] - mu[c]) / sd[c];
+            s += (double)d * d;
+            g = scale * d;
+        }
+        dZ[i] = g;
+        dZb[i] = __float2bfloat16(g);
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
+}
+
+// dZ = dH * GELU'(Z) (fp32 and bf16)
+__global__ void gelu_back_kernel(const float* dH, const float* Z, float* dZ, bf16* dZb, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float g = dH[i] * gelu_prime_f(Z[i]);
+        dZ[i] = g;
+        dZb[i] = __float2bfloat16(g);
+    }
+}
+
+// column sums of dZ (rows < Bp) -> bias gradient
+__global__ void colsum_kernel(const float* dZ, int ld, int rows, int cols, float* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += dZ[(size_t)r * ld + c];
+    out[c] = s;
+}
+
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2, float wd, bf16* wb) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i] + wd * w[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wn = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wn;
+        if (wb) wb[i] = __float2bfloat16(wn);
+    }
+}
+
+// W ~ N(0, 1/fan_in) in the valid region (Box-Muller on Philox draws), zero padding
+__global__ void init_weights_kernel(float* W, int rows, int cols, int ld, int ldrows, float sd, uint32_t k0,
+                                    uint32_t k1, uint32_t stream) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)ldrows * ld; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ld), c = (int)(i % ld);
+        float v = 0.f;
+        if (r < rows && c < cols) {
+            uint32_t ctr[4] = {(uint32_t)i, stream, 0u, 0u};
+            philox4x32_10(ctr, k0, k1);
+            const float u1 = ((float)ctr[0] + 0.5f) * 2.3283064365386963e-10f;
+            const float u2 = ((float)ctr[1] + 0.5f) * 2.3283064365386963e-10f;
+            v = sd * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+        }
+        W[i] = v;
+    }
+}
+
+__global__ void destandardize_kernel(const float* Y, int ldy, int n, int n_out, const float* mu, const float* sd,
+                                     float* out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)n * n_out; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / n_out), c = (int)(i % n_out);
+        out[i] = Y[(size_t)r * ldy + c] * sd[c] + mu[c];
+    }
+}
+
+}  // namespace cl
+
+// ---------------------------------------------------------------- host side
+
+struct cl_surrogate {
+    int n_in, n_out, width, depth, L;
+    std::vector<int> d, P;  // true and padded dims of layer inputs/outputs (size L+1)
+    std::vector<float*> W, gW, mW, vW, b, gb, mb, vb;
+    std::vector<cl::bf16*> Wb, WbT;
+    cudaStream_t stream;
+    int Bp = 0;  // batch capacity (padded)
+    std::vector<float*> Z;         // per layer: Bp x P[l+1] fp32
+    std::vector<cl::bf16*> H;      // per layer input: Bp x P[l] bf16
+    std::vector<cl::bf16*> HT;     // transposes: P[l] x Bp
+    float* dZ = nullptr;           // Bp x maxP fp32
+    float* dH = nullptr;           // Bp x maxP fp32
+    cl::bf16* dZb = nullptr;       // Bp x maxP
+    cl::bf16* dZbT = nullptr;      // maxP x Bp
+    float *Xd = nullptr, *Td = nullptr;  // raw data (n x n_in / n x n_out) for the current call
+    size_t cap_n = 0;
+    float *mu_in, *sd_in, *mu_out, *sd_out;  // standardization (device, length n_in / n_out)
+    std::vector<float> h_mu_in, h_sd_in, h_mu_out, h_sd_out;
+    double* dloss = nullptr;
+    long long adam_t = 0;
+    long long epochs_done = 0;
+    uint64_t seed = 0;
+    int sms = 1;
+};
+
+namespace {
+
+inline int pad32(int x) { return (x + 31) / 32 * 32; }
+
+cl_status sfail(cl_status s, const std::string& m) {
+    cl::set_global_error(m.c_str());
+    return s;
+}
+
+void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ldb, float* C, int ldc, int M, int N,
+          int K, int mode, const float* bias, cl::bf16* H, int ldh, int Mvalid, int Nvalid) {
+    cl::GemmArgs g;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc; g.M = M; g.N = N; g.K = K;
+    g.mode = mode; g.bias = bias; g.H = H; g.ldh = ldh; g.Mvalid = Mvalid; g.Nvalid = Nvalid;
+    dim3 grid((N + cl::GN - 1) / cl::GN, (M + cl::GM - 1) / cl::GM);
+    cl::gemm_tn_kernel<<<grid, 128, 0, S->stream>>>(g);
+}
+
+void transpose(cl_surrogate* S, const cl::bf16* in, int ldi, cl::bf16* out, int ldo, int R, int C) {
+    dim3 grid((C + 31) / 32, (R + 31) / 32);
+    cl::transpose_bf16_kernel<<<grid, dim3(32, 8), 0, S->stream>>>(in, ldi, out, ldo, R, C);
+}
+
+cl_status ensure_batch(cl_surrogate* S, int n) {
+    const int Bp = (n + 63) / 64 * 64;
+    if (Bp <= S->Bp) return CL_OK;
+    for (auto p : S->Z) cudaFree(p);
+    for (auto p : S->H) cudaFree(p);
+    for (auto p : S->HT) cudaFree(p);
+    cudaFree(S->dZ); cudaFree(S->dH); cudaFree(S->dZb); cudaFree(S->dZbT);
+    S->Z.assign(S->L, nullptr);
+    S->H.assign(S->L, nullptr);
+    S->HT.assign(S->L, nullptr);
+    int maxP = 0;
+    for (int p : S->P) maxP = std::max(maxP, p);
+    bool ok = true;
+    for (int l = 0; l < S->L; ++l) {
+        ok = ok && cudaMalloc(&S->Z[l], sizeof(float) * Bp * S->P[l + 1]) == cudaSuccess;
+        ok = ok && cudaMalloc(&S->H[l], sizeof(cl::bf16) * Bp * S->P[l]) == cudaSuccess;
+        ok = ok && cudaMalloc(&S->HT[l], sizeof(cl::bf16) * Bp * S->P[l]) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&S->dZ, sizeof(float) * Bp * maxP) == cudaSuccess;
+    ok = ok && cudaMalloc(&S->dH, sizeof(float) * Bp * maxP) == cudaSuccess;
+    ok = ok && cudaMalloc(&S->dZb, sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
+    ok = ok && cudaMalloc(&S->dZbT, sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
+    if (!ok) return sfail(CL_ERR_OOM, "surrogate: activation buffers");
+    S->Bp = Bp;
+    return CL_OK;
+}
+
+cl_status ensure_data(cl_surrogate* S, size_t n) {
+    if (n <= S->cap_n) return CL_OK;
+    cudaFree(S->Xd);
+    cudaFree(S->Td);
+    if (cudaMalloc(&S->Xd, sizeof(float) * n * S->n_in) != cudaSuccess ||
+        cudaMalloc(&S->Td, sizeof(float) * n * S->n_out) != cudaSuccess)
+        return sfail(CL_ERR_OOM, "surrogate: data buffers");
+    S->cap_n = n;
+    return CL_OK;
+}
+
+void refresh_bf16(cl_surrogate* S) {
+    for (int l = 0; l < S->L; ++l) {
+        const size_t n = (size_t)S->P[l + 1] * S->P[l];
+        cl::f32_to_bf16_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->W[l], S->Wb[l], n);
+    }
+}
+
+// forward over batch rows r = 0..n-1, sample idx[r0 + r] (r0 + r without idx) of
+// the data in S->Xd, standardized by mu/sd
+void forward(cl_surrogate* S, const int* idx, int64_t r0, int n) {
+    cl::load_inputs_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->Xd, idx, r0, n, S->n_in, S->mu_in, S->sd_in, S->H[0],
+                                                              S->P[0], S->Bp);
+    for (int l = 0; l < S->L; ++l) {
+        const bool last = l == S->L - 1;
+        gemm(S, S->H[l], S->P[l], S->Wb[l], S->P[l], S->Z[l], S->P[l + 1], S->Bp, S->P[l + 1], S->P[l], last ? 2 : 1,
+             S->b[l], last ? nullptr : S->H[l + 1], S->P[l + 1], n, S->d[l + 1]);
+    }
+}
+
+// backward: gradients of the mean squared error into gW, gb (loss sum added into S->dloss)
+void backward(cl_surrogate* S, const int* idx, int64_t r0, int n) {
+    const int L = S->L, Bp = S->Bp;
+    cl::loss_grad_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->Z[L - 1], S->P[L], S->Td, idx, r0, n, S->n_out,
+                                                            S->mu_out, S->sd_out, S->dZ, S->dZb, S->P[L], Bp,
+                                                            S->dloss);
+    for (int l = L - 1; l >= 0; --l) {
+        const int Pin = S->P[l], Pout = S->P[l + 1];
+        // bias gradient and weight gradient dW = dZ^T H_l
+        cl::colsum_kernel<<<(Pout + 127) / 128, 128, 0, S->stream>>>(S->dZ, Pout, Bp, Pout, S->gb[l]);
+        transpose(S, S->dZb, Pout, S->dZbT, Bp, Bp, Pout);
+        transpose(S, S->H[l], Pin, S->HT[l], Bp, Bp, Pin);
+        gemm(S, S->dZbT, Bp, S->HT[l], Bp, S->gW[l], Pin, Pout, Pin, Bp, 0, nullptr, nullptr, 0, Pout, Pin);
+        if (l > 0) {
+            // dH = dZ W_l, then dZ_{l-1} = dH * GELU'(Z_{l-1})
+            transpose(S, S->Wb[l], Pin, S->WbT[l], Pout, Pout, Pin);
+            gemm(S, S->dZb, Pout, S->WbT[l], Pout, S->dH, Pin, Bp, Pin, Pout, 0, nullptr, nullptr, 0, Bp, Pin);
+            cl::gelu_back_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->dH, S->Z[l - 1], S->dZ, S->dZb, (size_t)Bp * Pin);
+        }
+    }
+}
+
+void set_identity_scaling(cl_surrogate* S) {
+    S->h_mu_in.assign(S->n_in, 0.f);
+    S->h_sd_in.assign(S->n_in, 1.f);
+    S->h_mu_out.assign(S->n_out, 0.f);
+    S->h_sd_out.assign(S->n_out, 1.f);
+}
+
+void upload_scaling(cl_surrogate* S) {
+    cudaMemcpyAsync(S->mu_in, S->h_mu_in.data(), sizeof(float) * S->n_in, cudaMemcpyHostToDevice, S->stream);
+    cudaMemcpyAsync(S->sd_in, S->h_sd_in.data(), sizeof(float) * S->n_in, cudaMemcpyHostToDevice, S->stream);
+    cudaMemcpyAsync(S->mu_out, S->h_mu_out.data(), sizeof(float) * S->n_out, cudaMemcpyHostToDevice, S->stream);
+    cudaMemcpyAsync(S->sd_out, S->h_sd_out.data(), sizeof(float) * S->n_out, cudaMemcpyHostToDevice, S->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+cl_status surrogate_destroy(cl_surrogate* S) {
+    if (!S) return CL_OK;
+    for (auto* v : {&S->W, &S->gW, &S->mW, &S->vW, &S->b, &S->gb, &S->mb, &S->vb})
+        for (auto p : *v) cudaFree(p);
+    for (auto p : S->Wb) cudaFree(p);
+    for (auto p : S->WbT) cudaFree(p);
+    for (auto p : S->Z) cudaFree(p);
+    for (auto p : S->H) cudaFree(p);
+    for (auto p : S->HT) cudaFree(p);
+    cudaFree(S->dZ); cudaFree(S->dH); cudaFree(S->dZb); cudaFree(S->dZbT);
+    cudaFree(S->Xd); cudaFree(S->Td);
+    cudaFree(S->mu_in); cudaFree(S->sd_in); cudaFree(S->mu_out); cudaFree(S->sd_out);
+    cudaFree(S->dloss);
+    delete S;
+    return CL_OK;
+}
+
+cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t depth, uint64_t seed, void* stream,
+                           cl_surrogate** out) {
+    if (!out) return sfail(CL_ERR_ARG, "surrogate_create: out is NULL");
+    *out = nullptr;
+    if (n_in < 1 || n_in > 1024 || n_out < 1 || n_out > 1024 || width < 1 || width > 4096 || depth < 1 || depth > 16)
+        return sfail(CL_ERR_ARG, "surrogate_create: n_in, n_out in [1, 1024], width in [1, 4096], depth in [1, 16]");
+    cl_surrogate* S = new cl_surrogate();
+    S->n_in = n_in; S->n_out = n_out; S->width = width; S->depth = depth; S->L = depth + 1;
+    S->stream = (cudaStream_t)stream;
+    S->seed = seed;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, dev);
+    S->d.push_back(n_in);
+    for (int i = 0; i < depth; ++i) S->d.push_back(width);
+    S->d.push_back(n_out);
+    for (int x : S->d) S->P.push_back(pad32(x));
+    bool ok = true;
+    for (int l = 0; l < S->L; ++l) {
+        const size_t nw = (size_t)S->P[l + 1] * S->P[l], nb = S->P[l + 1];
+        float *w, *gw, *mw, *vw, *bb, *gbb, *mbb, *vbb;
+        cl::bf16 *wb, *wbt;
+        ok = ok && cudaMalloc(&w, nw * 4) == cudaSuccess && cudaMalloc(&gw, nw * 4) == cudaSuccess &&
+             cudaMalloc(&mw, nw * 4) == cudaSuccess && cudaMalloc(&vw, nw * 4) == cudaSuccess &&
+             cudaMalloc(&bb, nb * 4) == cudaSuccess && cudaMalloc(&gbb, nb * 4) == cudaSuccess &&
+             cudaMalloc(&mbb, nb * 4) == cudaSuccess && cudaMalloc(&vbb, nb * 4) == cudaSuccess &&
+             cudaMalloc(&wb, nw * 2) == cudaSuccess && cudaMalloc(&wbt, nw * 2) == cudaSuccess;
+        if (!ok) break;
+        S->W.push_back(w); S->gW.push_back(gw); S->mW.push_back(mw); S->vW.push_back(vw);
+        S->b.push_back(bb); S->gb.push_back(gbb); S->mb.push_back(mbb); S->vb.push_back(vbb);
+        S->Wb.push_back(wb); S->WbT.push_back(wbt);
+        cudaMemsetAsync(gw, 0, nw * 4, S->stream); cudaMemsetAsync(mw, 0, nw * 4, S->stream);
+        cudaMemsetAsync(vw, 0, nw * 4, S->stream); cudaMemsetAsync(bb, 0, nb * 4, S->stream);
+        cudaMemsetAsync(gbb, 0, nb * 4, S->stream); cudaMemsetAsync(mbb, 0, nb * 4, S->stream);
+        cudaMemsetAsync(vbb, 0, nb * 4, S->stream);
+        cl::init_weights_kernel<<<S->sms * 4, 256, 0, S->stream>>>(w, S->d[l + 1], S->d[l], S->P[l], S->P[l + 1],
+                                                                   1.0f / sqrtf((float)S->d[l]),
+                                                                   (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
+                                                                   (uint32_t)l);
+    }
+    ok = ok && cudaMalloc(&S->mu_in, 4 * n_in) == cudaSuccess && cudaMalloc(&S->sd_in, 4 * n_in) == cudaSuccess &&
+         cudaMalloc(&S->mu_out, 4 * n_out) == cudaSuccess && cudaMalloc(&S->sd_out, 4 * n_out) == cudaSuccess &&
+         cudaMalloc(&S->dloss, sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        surrogate_destroy(S);
+        return sfail(CL_ERR_OOM, "surrogate_create: parameters");
+    }
+    set_identity_scaling(S);
+    upload_scaling(S);
+    refresh_bf16(S);
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+        surrogate_destroy(S);
+        return sfail(CL_ERR_CUDA, "surrogate_create: initialisation");
+    }
+    *out = S;
+    return CL_OK;
+}
+
+int64_t surrogate_param_count(const cl_surrogate* S) {
+    if (!S) return 0;
+    int64_t n = 0;
+    for (int l = 0; l < S->L; ++l) n += (int64_t)S->d[l + 1] * S->d[l] + S->d[l + 1];
+    return n;
+}
+
+// theta: W_0 (d1 x d0 row-major), b_0, W_1, b_1, ... in double
+static cl_status copy_params(cl_surrogate* S, double* out, const double* in, bool grads) {
+    std::vector<float> buf;
+    size_t o = 0;
+    for (int l = 0; l < S->L; ++l) {
+        const int r = S->d[l + 1], c = S->d[l], ld = S->P[l];
+        float* Wd = grads ? S->gW[l] : S->W[l];
+        float* bd = grads ? S->gb[l] : S->b[l];
+        buf.resize((size_t)r * c);
+        if (in) {
+            for (size_t i = 0; i < buf.size(); ++i) buf[i] = (float)in[o + i];
+            cudaMemcpy2DAsync(Wd, ld * 4, buf.data(), c * 4, c * 4, r, cudaMemcpyHostToDevice, S->stream);
+            cudaStreamSynchronize(S->stream);
+        } else {
+            cudaMemcpy2DAsync(buf.data(), c * 4, Wd, ld * 4, c * 4, r, cudaMemcpyDeviceToHost, S->stream);
+            cudaStreamSynchronize(S->stream);
+            for (size_t i = 0; i < buf.size(); ++i) out[o + i] = buf[i];
+        }
+        o += buf.size();
+        buf.resize(r);
+        if (in) {
+            for (int i = 0; i < r; ++i) buf[i] = (float)in[o + i];
+            cudaMemcpyAsync(bd, buf.data(), r * 4, cudaMemcpyHostToDevice, S->stream);
+            cudaStreamSynchronize(S->stream);
+        } else {
+            cudaMemcpyAsync(buf.data(), bd, r * 4, cudaMemcpyDeviceToHost, S->stream);
+            cudaStreamSynchronize(S->stream);
+            for (int i = 0; i < r; ++i) out[o + i] = buf[i];
+        }
+        o += r;
+    }
+    if (in) refresh_bf16(S);
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    return e == cudaSuccess ? CL_OK : sfail(CL_ERR_CUDA, "surrogate: parameter copy");
+}
+
+cl_status surrogate_get_params(cl_surrogate* S, double* theta) {
+    if (!S || !theta) return sfail(CL_ERR_ARG, "surrogate_get_params: NULL argument");
+    return copy_params(S, theta, nullptr, false);
+}
+
+cl_status surrogate_set_params(cl_surrogate* S, const double* theta) {
+    if (!S || !theta) return sfail(CL_ERR_ARG, "surrogate_set_params: NULL argument");
+    return copy_params(S, nullptr, theta, false);
+}
+
+cl_status surrogate_loss_grad(cl_surrogate* S, const float* X, const float* T, int64_t n, double* loss, double* grad) {
+    if (!S || !X || !T || n < 1 || n > (1 << 24)) return sfail(CL_ERR_ARG, "surrogate_loss_grad: bad arguments");
+    cl_status s = ensure_batch(S, (int)n);
+    if (s == CL_OK) s = ensure_data(S, n);
+    if (s != CL_OK) return s;
+    // raw inputs and targets: identity scaling for this call
+    std::vector<float> mi = S->h_mu_in, si = S->h_sd_in, mo = S->h_mu_out, so = S->h_sd_out;
+    set_identity_scaling(S);
+    upload_scaling(S);
+    cudaMemcpyAsync(S->Xd, X, sizeof(float) * n * S->n_in, cudaMemcpyHostToDevice, S->stream);
+    cudaMemcpyAsync(S->Td, T, sizeof(float) * n * S->n_out, cudaMemcpyHostToDevice, S->stream);
+    cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
+    forward(S, nullptr, 0, (int)n);
+    backward(S, nullptr, 0, (int)n);
+    double l = 0;
+    cudaMemcpyAsync(&l, S->dloss, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    S->h_mu_in = mi; S->h_sd_in = si; S->h_mu_out = mo; S->h_sd_out = so;
+    upload_scaling(S);
+    if (e != cudaSuccess) return sfail(CL_ERR_CUDA, std::string("surrogate_loss_grad: ") + cudaGetErrorString(e));
+    if (loss) *loss = l / ((double)n * S->n_out);
+    if (grad) return copy_params(S, grad, nullptr, true);
+    return CL_OK;
+}
+
+cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64_t n, const cl_train_cfg* cfg,
+                          float* loss_history) {
+    if (!S || !X || !Y || !cfg || n < 1 || n > (1 << 24) || cfg->epochs < 1 || cfg->batch < 1 || !(cfg->lr > 0))
+        return sfail(CL_ERR_ARG, "surrogate_train: bad arguments");
+    const int bs = (int)std::min<int64_t>(cfg->batch, n);
+    cl_status s = ensure_batch(S, bs);
+    if (s == CL_OK) s = ensure_data(S, n);
+    if (s != CL_OK) return s;
+    // standardization of inputs and outputs from the training set
+    set_identity_scaling(S);
+    if (cfg->standardize) {
+        for (int c = 0; c < S->n_in; ++c) {
+            double m = 0, v = 0;
+            for (int64_t i = 0; i < n; ++i) m += X[i * S->n_in + c];
+            m /= n;
+            for (int64_t i = 0; i < n; ++i) v += (X[i * S->n_in + c] - m) * (X[i * S->n_in + c] - m);
+            S->h_mu_in[c] = (float)m;
+            S->h_sd_in[c] = (float)std::max(sqrt(v / n), 1e-12);
+        }
+        for (int c = 0; c < S->n_out; ++c) {
+            double m = 0, v = 0;
+            for (int64_t i = 0; i < n; ++i) m += Y[i * S->n_out + c];
+            m /= n;
+            for (int64_t i = 0; i < n; ++i) v += (Y[i * S->n_out + c] - m) * (Y[i * S->n_out + c] - m);
+            S->h_mu_out[c] = (float)m;
+            S->h_sd_out[c] = (float)std::max(sqrt(v / n), 1e-12);
+        }
+    }
+    upload_scaling(S);
+    cudaMemcpyAsync(S->Xd, X, sizeof(float) * n * S->n_in, cudaMemcpyHostToDevice, S->stream);
+    cudaMemcpyAsync(S->Td, Y, sizeof(float) * n * S->n_out, cudaMemcpyHostToDevice, S->stream);
+    const float b1 = cfg->beta1 > 0 ? cfg->beta1 : 0.9f, b2 = cfg->beta2 > 0 ? cfg->beta2 : 0.999f;
+    const float eps = cfg->eps > 0 ? cfg->eps : 1e-8f;
+    const int64_t per_epoch = (n + bs - 1) / bs, total = per_epoch * cfg->epochs;
+    int* d_perm = nullptr;
+    std::vector<int> perm;
+    if (cfg->shuffle) {
+        if (cudaMalloc(&d_perm, sizeof(int) * n) != cudaSuccess) return sfail(CL_ERR_OOM, "surrogate_train: order");
+        perm.resize(n);
+    }
+    int64_t step = 0;
+    for (int ep = 0; ep < cfg->epochs; ++ep) {
+        cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
+        if (cfg->shuffle) {
+            // Fisher-Yates with a 64-bit LCG (Knuth's MMIX constants) keyed by the
+            // handle's seed and the epoch
+            for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
+            uint64_t x = S->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(S->epochs_done + 1));
+            for (int64_t i = n - 1; i > 0; --i) {
+                x = x * 6364136223846793005ull + 1442695040888963407ull;
+                const int64_t j = (int64_t)((x >> 33) % (uint64_t)(i + 1));
+                std::swap(perm[i], perm[j]);
+            }
+            cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
+            cudaStreamSynchronize(S->stream);  // perm is reused next epoch
+        }
+        for (int64_t r0 = 0; r0 < n; r0 += bs, ++step) {
+            const int nb = (int)std::min<int64_t>(bs, n - r0);
+            forward(S, d_perm, r0, nb);
+            backward(S, d_perm, r0, nb);
+            ++S->adam_t;
+            const float c1 = 1.f - powf(b1, (float)S->adam_t), c2 = 1.f - powf(b2, (float)S->adam_t);
+            float lr = cfg->lr;
+            if (cfg->lr_end >= 0)
+                lr = cfg->lr_end + 0.5f * (cfg->lr - cfg->lr_end) * (1.f + cosf(3.14159265358979f * (float)step / (float)total));
+            for (int l = 0; l < S->L; ++l) {
+                const size_t nw = (size_t)S->P[l + 1] * S->P[l];
+                cl::adam_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->W[l], S->gW[l], S->mW[l], S->vW[l], nw, lr, b1,
+                                                                   b2, eps, c1, c2, cfg->weight_decay, S->Wb[l]);
+                cl::adam_kernel<<<1, 256, 0, S->stream>>>(S->b[l], S->gb[l], S->mb[l], S->vb[l], S->P[l + 1], lr, b1,
+                                                          b2, eps, c1, c2, 0.f, nullptr);
+            }
+        }
+        ++S->epochs_done;
+        if (loss_history) {
+            double l = 0;
+            cudaMemcpyAsync(&l, S->dloss, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+            if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+                cudaFree(d_perm);
+                return sfail(CL_ERR_CUDA, "surrogate_train");
+            }
+            loss_history[ep] = (float)(l / ((double)n * S->n_out));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    cudaFree(d_perm);
+    return e == cudaSuccess ? CL_OK : sfail(CL_ERR_CUDA, std::string("surrogate_train: ") + cudaGetErrorString(e));
+}
+
+cl_status surrogate_predict(cl_surrogate* S, const float* X, int64_t n, float* Y) {
+    if (!S || !X || !Y || n < 1 || n > (1 << 24)) return sfail(CL_ERR_ARG, "surrogate_predict: bad arguments");
+    cl_status s = ensure_batch(S, (int)std::min<int64_t>(n, 8192));
+    if (s == CL_OK) s = ensure_data(S, n);
+    if (s != CL_OK) return s;
+    float* Yd = S->Td;  // reuse the target buffer for the outputs
+    cudaMemcpyAsync(S->Xd, X, sizeof(float) * n * S->n_in, cudaMemcpyHostToDevice, S->stream);
+    for (int64_t r0 = 0; r0 < n; r0 += S->Bp) {
+        const int nb = (int)std::min<int64_t>(S->Bp, n - r0);
+        forward(S, nullptr, r0, nb);
+        cl::destandardize_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->Z[S->L - 1], S->P[S->L], nb, S->n_out, S->mu_out,
+                                                                    S->sd_out, Yd + r0 * S->n_out);
+    }
+    cudaMemcpyAsync(Y, Yd, sizeof(float) * n * S->n_out, cudaMemcpyDeviceToHost, S->stream);
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    return e == cudaSuccess ? CL_OK : sfail(CL_ERR_CUDA, std::string("surrogate_predict: ") + cudaGetErrorString(e));
+}
+
+}  // extern "C"

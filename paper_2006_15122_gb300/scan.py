@@ -1,0 +1,151 @@
+"""Parameter scans over the resonance coupling q of the two-field model
+V = phi^2/2 + (q*/2) phi^2 chi^2, q* = 4q (section 8.1): a batched ensemble of lattices
+observed at uniform time slices, a surrogate network fitted to those
+observations, and the one-lattice-at-a-time method the surrogate stands in for.
+
+Every step runs in the library (ensemble_*, lattice_*, surrogate_* through the
+C ABI); this module only sequences the calls, arranges the observations as
+training pairs (log10 q, t) -> CL_OBS_SIZE observables, and scores
+predictions against fresh lattice runs.
+"""
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (CL_FP32, CL_INT_VV4, CL_OBS_SIZE, Ensemble, Lattice, Surrogate, make_grid, make_init,
+               make_model)
+
+
+@dataclass
+class ScanSpec:
+    """Model, grid and observation schedule shared by every run of a scan."""
+    fstar_over_mp: float = 1.396
+    omega_over_fstar: float = 5.13e-6
+    kIR: float = 0.1
+    dt: float = 0.002
+    integrator: int = CL_INT_VV4
+    precision: int = CL_FP32
+    sizes: tuple = (32, 64, 96)
+    steps_per_slice: int = 32
+    n_slices: int = 64
+    phi0: float = 1.0
+    nmin: int = field(default=0)
+
+    def __post_init__(self):
+        if not self.nmin:
+            self.nmin = min(self.sizes)
+
+    @property
+    def kmax(self):
+        """Upper end of the observed spectrum: the axis Nyquist momentum of the smallest lattice."""
+        return 0.5 * self.nmin * self.kIR
+
+    def times(self):
+        return self.dt * self.steps_per_slice * np.arange(1, self.n_slices + 1)
+
+    def model(self, q=0.0):
+        """Program-unit model of resonance parameter q = g^2 Phi^2 / (4 m^2): with
+        omega_star = m and phi_star = Phi the coupling of (1/2) q* phi^2 chi^2 is
+        q* = g^2 Phi^2 / m^2 = 4 q (section 8.1)."""
+        return make_model(n_fields=2, pexp=2, lam=1.0, q=4.0 * q, omega_over_fstar=self.omega_over_fstar,
+                          fstar_over_mp=self.fstar_over_mp)
+
+    def grid(self, N):
+        return make_grid(N, self.kIR, self.dt, self.integrator, self.precision)
+
+    def init(self, seed=0):
+        return make_init(phi0=(self.phi0, 0.0), seed=seed)
+
+
+def log_uniform_q(n, lo, hi, seed):
+    """n couplings log-uniform in [lo, hi] (numpy PCG64 stream of `seed`)."""
+    return 10.0 ** np.random.default_rng(seed).uniform(math.log10(lo), math.log10(hi), n)
+
+
+def cycle_sizes(n, sizes):
+    return [sizes[i % len(sizes)] for i in range(n)]
+
+
+def ensemble_observations(spec, qs, Ns, seeds, autotune=True, stream=None):
+    """Observations of a batched ensemble at spec.n_slices uniform slices
+    (qs: resonance parameters q, see ScanSpec.model).
+
+    Returns (obs of shape (n, n_slices, CL_OBS_SIZE), times, info) where info
+    holds the wall-clock seconds of initialisation, tuning and evolution (each
+    phase ends synchronized) and the tile shape used."""
+    t0 = time.perf_counter()
+    ens = Ensemble(spec.model(), 4.0 * np.asarray(qs, dtype=np.float64), Ns, seeds, spec.grid(spec.nmin),
+                   spec.init(), stream=stream)
+    t1 = time.perf_counter()
+    tuned = ens.autotune() if autotune else []
+    t2 = time.perf_counter()
+    obs = np.zeros((len(qs), spec.n_slices, CL_OBS_SIZE), dtype=np.float32)
+    times = np.zeros(spec.n_slices)
+    for j in range(spec.n_slices):
+        ens.evolve(spec.steps_per_slice)
+        obs[:, j, :], times[j] = ens.observe()
+    t3 = time.perf_counter()
+    info = {"init_s": t1 - t0, "tune_s": t2 - t1, "evolve_observe_s": t3 - t2, "tile": ens.tile(),
+            "candidates": tuned}
+    ens.close()
+    return obs, times, info
+
+
+def plain_observations(spec, q, N, seed, stream=None):
+    """The same observations from one lattice evolved on its own (the method
+    without batching): (obs (n_slices, CL_OBS_SIZE), times)."""
+    m = spec.model(q)
+    lat = Lattice(m, spec.grid(N), spec.init(seed), stream=stream)
+    obs = np.zeros((spec.n_slices, CL_OBS_SIZE), dtype=np.float32)
+    times = np.zeros(spec.n_slices)
+    for j in range(spec.n_slices):
+        lat.evolve(spec.steps_per_slice)
+        obs[j], times[j] = lat.observe(spec.kmax)
+    lat.close()
+    return obs, times
+
+
+def training_pairs(qs, times, obs):
+    """(log10 q, t) -> observables, one row per run and slice."""
+    n, S = len(qs), len(times)
+    X = np.stack([np.repeat(np.log10(qs), S), np.tile(times, n)], axis=1).astype(np.float32)
+    Y = obs.reshape(n * S, -1).astype(np.float32)
+    ok = np.all(np.isfinite(Y), axis=1)
+    return X[ok], Y[ok]
+
+
+def fit_surrogate(X, Y, width=256, depth=3, epochs=200, batch=512, lr=2e-3, lr_end=2e-5, seed=0, stream=None):
+    """Surrogate network fitted to (X, Y): Adam with a cosine-annealed step size,
+    samples shuffled every epoch.  Returns (net, per-epoch loss, seconds)."""
+    net = Surrogate(X.shape[1], Y.shape[1], width, depth, seed=seed, stream=stream)
+    t0 = time.perf_counter()
+    hist = net.train(X, Y, epochs=epochs, batch=batch, lr=lr, lr_end=lr_end, shuffle=True)
+    return net, hist, time.perf_counter() - t0
+
+
+def score(pred, ref_runs):
+    """Errors of predictions against fresh lattice runs.
+
+    pred: (Q, S, CL_OBS_SIZE); ref_runs: (Q, R, S, CL_OBS_SIZE), R seeds per
+    held-out q.  The reference is the mean over seeds (of log10 Delta for the
+    spectrum).  Returns absolute errors of the chi energy fraction and of w,
+    relative errors |10^(pred - ref) - 1| of the spectrum, and the same measures
+    for single runs around their seed mean (the seed-scatter floor)."""
+    ref = np.nanmean(ref_runs, axis=1)
+    e_eps = np.abs(pred[..., 0] - ref[..., 0])
+    e_w = np.abs(pred[..., 1] - ref[..., 1])
+    e_spec = np.abs(10.0 ** (pred[..., 2:].astype(np.float64) - ref[..., 2:]) - 1.0)
+    dev = ref_runs - ref[:, None]
+    f_eps = np.abs(dev[..., 0])
+    f_w = np.abs(dev[..., 1])
+    f_spec = np.abs(10.0 ** dev[..., 2:].astype(np.float64) - 1.0)
+
+    def summ(a):
+        a = a[np.isfinite(a)]
+        return {"median": float(np.median(a)), "p95": float(np.percentile(a, 95)), "max": float(np.max(a)),
+                "within_2pct": float(np.mean(a <= 0.02))}
+
+    return {"eps_chi_abs": summ(e_eps), "w_abs": summ(e_w), "spectrum_rel": summ(e_spec),
+            "floor": {"eps_chi_abs": summ(f_eps), "w_abs": summ(f_w), "spectrum_rel": summ(f_spec)}}

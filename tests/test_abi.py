@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "cl_lattice.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^(?:cl_status|int32_t|const char\s*\*)\s*(\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^(?:cl_status|int32_t|int64_t|const char\s*\*)\s*(\w+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declarations_match_binding():
@@ -90,3 +90,22 @@ def test_null_arguments_are_rejected():
     assert lib.lattice_evolve(None, 1) == cl.CL_ERR_ARG
     assert lib.lattice_measure_means(None, None) == cl.CL_ERR_ARG
     assert lib.lattice_destroy(None) == cl.CL_OK
+
+
+@pytest.mark.parametrize("dims", [(0, 34, 256, 3), (2, 0, 256, 3), (2, 34, 0, 3), (2, 34, 256, 0), (2, 34, 5000, 3),
+                                  (2, 34, 256, 17)])
+def test_surrogate_create_rejects_bad_sizes(dims):
+    lib = cl.load()
+    h = C.c_void_p()
+    assert lib.surrogate_create(*dims, 0, None, C.byref(h)) == cl.CL_ERR_ARG and not h.value
+    assert b"surrogate_create" in lib.cl_last_error(None)
+
+
+def test_surrogate_null_arguments_are_rejected():
+    lib = cl.load()
+    assert lib.surrogate_create(2, 34, 256, 3, 0, None, None) == cl.CL_ERR_ARG
+    assert lib.surrogate_param_count(None) == 0
+    assert lib.surrogate_train(None, None, None, 1, None, None) == cl.CL_ERR_ARG
+    assert lib.surrogate_predict(None, None, 1, None) == cl.CL_ERR_ARG
+    assert lib.surrogate_loss_grad(None, None, None, 1, None, None) == cl.CL_ERR_ARG
+    assert lib.surrogate_destroy(None) == cl.CL_OK

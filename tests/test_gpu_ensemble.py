@@ -69,7 +69,7 @@ def test_ensemble_observations_agree_with_members():
     obs, t = ens.observe()
     assert obs.shape == (3, cl.CL_OBS_SIZE) and np.all(np.isfinite(obs))
     assert abs(t - 25 * 0.004) < 1e-9
-    kmax = math.sqrt(3) * 0.5 * min(Ns) * kIR
+    kmax = 0.5 * min(Ns) * kIR
     for i in range(3):
         m = ens.member(i)
         mm = m.measure_means()
