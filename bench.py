@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-scan", action="store_true", help="leave the ensemble scan out of the default line")
     p.add_argument("--scan", action="store_true",
                    help="time the batched ensemble + surrogate parameter scan instead of the single lattice")
     p.add_argument("--scan-runs", type=int, default=512)
@@ -54,7 +55,7 @@ def parse():
     p.add_argument("--scan-heldout", type=int, default=64)
     p.add_argument("--scan-seeds", type=int, default=6)
     p.add_argument("--scan-plain", type=int, default=12)
-    p.add_argument("--scan-epochs", type=int, default=200)
+    p.add_argument("--scan-epochs", type=int, default=400)
     return p.parse_args()
 
 
@@ -65,6 +66,31 @@ def workload_config(N):
             "fstar_over_mp": FSTAR_MP, "omega_over_fstar": OMEGA_FSTAR,
             "state_bytes": 2 * 2 * 4 * N ** 3,
             "l2": "inputs (%.1f GB) exceed L2; no flush" % (2 * 2 * 4 * N ** 3 / 1e9)}
+
+
+TRAFFIC = os.path.join(ROOT, "profiles", "scalar_pass_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2006_15122_gb300", "csrc", f) for f in ("scalar_pass.cu", "scalar_common.cuh")]
+
+
+def kernel_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(N):
+    """DRAM bytes of one pass from the committed ncu capture, scaled to N^3
+    sites; None when the kernel's sources changed since the capture."""
+    try:
+        d = json.load(open(TRAFFIC))
+    except Exception:
+        return None
+    if d.get("source_sha256") != kernel_digest():
+        return None
+    return d["dram_bytes_per_site_pass"] * N ** 3
 
 
 def measured_peaks():
@@ -121,25 +147,43 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(sample_N=128, steps=1):
-    """The FP64 oracle as it stands, timed on this host's cores on a bounded
-    sample of the same workload (a smaller lattice of the same model)."""
-    import numpy as np
+class OracleSample:
+    """The FP64 oracle as it stands on a smaller lattice of the same model
+    (bounded sample of the workload), stepped on this host's cores."""
 
-    import oracle
-    from oracle.ic import scalar_ic
+    def __init__(self, sample_N=128):
+        import oracle
+        from oracle.ic import scalar_ic
 
-    dx = 2 * math.pi / (KIR * sample_N)
-    om = oracle.ScalarModel(N=sample_N, Ns=2, pexp=2, dx=dx, alpha=0.0, fmp2=FSTAR_MP ** 2, lam=1.0, q=QSTAR)
-    phi, pi, _ = scalar_ic(om, KIR, [1.0, 0.0], [0.0, 0.0], seed=0, omega_over_fstar=OMEGA_FSTAR)
-    lat = oracle.ScalarLattice(om, phi, pi)
-    lat.b = math.sqrt(lat.hubble_rhs())
-    t0 = time.perf_counter()
-    lat.vv_steps(oracle.VV4, DT, steps)
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": sample_N ** 3 * steps / dt, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
-            "sample": "%d^3 lattice of the same model, %d VV4 step(s), FP64, %.1f s" % (sample_N, steps, dt)}
+        self.oracle, self.N = oracle, sample_N
+        dx = 2 * math.pi / (KIR * sample_N)
+        om = oracle.ScalarModel(N=sample_N, Ns=2, pexp=2, dx=dx, alpha=0.0, fmp2=FSTAR_MP ** 2, lam=1.0, q=QSTAR)
+        phi, pi, _ = scalar_ic(om, KIR, [1.0, 0.0], [0.0, 0.0], seed=0, omega_over_fstar=OMEGA_FSTAR)
+        self.lat = oracle.ScalarLattice(om, phi, pi)
+        self.lat.b = math.sqrt(self.lat.hubble_rhs())
+
+    def step(self, n=1):
+        """Seconds for n VV4 steps."""
+        t0 = time.perf_counter()
+        self.lat.vv_steps(self.oracle.VV4, DT, n)
+        return time.perf_counter() - t0
+
+
+def oracle_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(sample_N=128, budget_s=12.0):
+    """The oracle timed on a bounded sample: VV4 steps of a sample_N^3 lattice
+    of the same model until about budget_s seconds of CPU work."""
+    o = OracleSample(sample_N)
+    steps, spent = 0, 0.0
+    while spent < budget_s:
+        spent += o.step(1)
+        steps += 1
+    return {"value": sample_N ** 3 * steps / spent, "unit": "site-updates/s", "cores": oracle_cores(),
+            "kind": "oracle", "sample": "%d^3 lattice of the same model, %d VV4 steps, FP64, %.1f s"
+                                        % (sample_N, steps, spent)}
 
 
 def run_reference(args):
@@ -147,38 +191,35 @@ def run_reference(args):
     if rank != 0:
         return
     N = min(args.N, 128)
+    o = OracleSample(N)
     vals = []
-    res = None
     for i in range(args.warmup + args.steps):
-        res = cpu_baseline(N, 1)
+        dt = o.step(1)
         if i >= args.warmup:
-            vals.append(res["value"])
+            vals.append(N ** 3 / dt)
     v = statistics.mean(vals)
     cfg = workload_config(args.N)
     line = {"impl": "reference", "metric": "site-updates/s", "value": v, "unit": "site-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * N ** 3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "value": v,
+            "cpu_baseline": {"kind": "oracle", "cores": oracle_cores(), "value": v,
                              "sample": "each step: one VV4 step of a %d^3 lattice of the same model" % N},
             "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_scan(args):
+def scan_measurement(args, stream):
     """Parameter scan of the two-field model over q log-uniform in [1e2, 1e5]:
     (i) the plain method, one lattice at a time, timed on a sample cycling
     through the sizes; (ii) one batched ensemble of all runs (autotuned tiles,
     CUDA graphs), whose observations train the surrogate, which then answers
-    held-out couplings scored against fresh lattice runs."""
+    held-out couplings scored against fresh lattice runs.  Returns the line."""
     import numpy as np
     import torch
 
-    import paper_2006_15122_gb300 as cl
     from paper_2006_15122_gb300 import scan
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    stream = torch.cuda.current_stream()
     spec = scan.ScanSpec(steps_per_slice=args.scan_steps_per_slice, n_slices=args.scan_slices)
     n = args.scan_runs
     qs = scan.log_uniform_q(n, 1e2, 1e5, seed=1234)
@@ -240,7 +281,14 @@ def run_scan(args):
         "train_loss_first_last": [float(hist[0]), float(hist[-1])],
         "error": err, "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_scan(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps(scan_measurement(args, torch.cuda.current_stream())), flush=True)
 
 
 def main():
@@ -320,7 +368,19 @@ def main():
     lat.close()
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(128, 1)
+        cpu = cpu_baseline(128)
+    ens = None
+    if rank == 0 and not args.no_scan:
+        if world > 1:
+            ens = {"skipped": "the scan runs on one GPU (bench.py --scan)"}
+        else:
+            try:
+                sl = scan_measurement(args, stream)
+                ens = {k: sl[k] for k in ("value", "unit", "plain_runs_per_hr", "batched_runs_per_hr",
+                                          "surrogate_runs_per_hr", "batched_speedup", "site_updates_per_s_batched",
+                                          "tile", "seconds", "error", "config", "clocks")}
+            except Exception as exc:  # the lattice number above stands on its own
+                ens = {"error_running": repr(exc)}
     if rank == 0:
         prof = os.path.join(ROOT, "profiles", "scalar_pass_vv4_1024_fp32.md")
         line = {
@@ -329,11 +389,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(N), parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_kind": peak_kind,
+                         "traffic": measured_traffic(N), "peak_kind": peak_kind,
                          "kernel": "scalar_pass_kernel<float,2,2>", "bytes_per_launch": alg_bytes,
                          "launch_ms": ms / npass},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npass, "clocks": clk,
             "hubble_violation": mm["hubble_violation"], "a": mm["a"],
+            "ensemble_scan": ens,
         }
         print(json.dumps(line), flush=True)
     if dist:

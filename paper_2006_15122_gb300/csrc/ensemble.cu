@@ -3,19 +3,21 @@
 // kernel launch per integrator pass for all of them, replayed as CUDA graphs.
 //
 // Every member is an ordinary lattice (its own arrays, FP64 background and
-// means); the ensemble kernel walks one global list of 32 x 32 x ZC tiles
-// spanning all members.  Per tile it loads the member's scalars, streams the
-// planes through the same cp.async shared-memory ring as the single-lattice
-// pass, and reduces the tile's sums into that member's per-tile partials; the
-// block that completes a member's last tile sums them in a fixed order and
-// runs the member's FP64 background update (sections 4.2.3 and 4.3.2).
-// Members therefore advance in lockstep through the same schedule of passes,
-// with a time step common to all of them.
+// means); the ensemble kernel walks one global list of tiles (shape chosen by
+// the autotuner) spanning all members.  Per tile it loads the member's
+// scalars, streams the planes through the same cp.async shared-memory ring as
+// the single-lattice pass, and stores the tile's sums into that member's
+// per-tile partials.  A second, small kernel then sums each member's partials
+// in a fixed order (one warp per member) and runs the member's FP64 background
+// update (sections 4.2.3 and 4.3.2); the kernel boundary orders the partials,
+// so the pass needs no memory fence or atomic per tile (a fence would wait for
+// the tile's streaming stores to drain).  Members advance in lockstep through
+// the same schedule of passes, with a time step common to all of them.
 //
 // Observations per member (workload pattern, section 4.4): the daughter-field
 // energy fraction eps_chi = (E_K[chi] + E_G[chi]) / rho, the equation of state
 // w = (E_K - E_G/3 - E_V)/rho, and log10 of the chi power spectrum (section 3.1)
-// at 32 log-spaced momenta in [k_IR, sqrt(3) N_min k_IR / 2], interpolated
+// at 32 log-spaced momenta in [k_IR, N_min k_IR / 2], interpolated
 // linearly in (log k, log Delta) between the shells of the lattice.
 #include <math.h>
 #include <string.h>
@@ -36,7 +38,6 @@ struct EnsLat {
     const void* buf[2][4];  // ping-pong copies of delta phi_0, delta phi_1, delta pi_0, delta pi_1
     DevState* st;
     double* partials;  // per tile: NS sums
-    unsigned int* counter;
     ModelConst mc;
     int N, ntx, nty, ntz, ntiles, tile_base;
 };
@@ -62,8 +63,6 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw + 128);
     __shared__ double red[8][16];
-    __shared__ double tot[16];
-    __shared__ unsigned int last;
     __shared__ T* s_out[2 * NF];  // destination arrays of the tile's member
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int lin = ty * BX + tx, nthr = BX * BY;
@@ -195,6 +194,9 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
 #pragma unroll
         for (int i = 0; i < NS; ++i) ts[i] = T(0);
         T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
+        // FP32: unrolled by two, the z-queue rotation is renamed away every other
+        // plane (FP64 keeps the loop rolled: unrolled it would spill)
+#pragma unroll(sizeof(T) == 4 ? 2 : 1)
         for (int zz = 0; zz < ZC; ++zz, ++need) {
             wait_for(need);
             if (zz > 0) { issue(); ++issued; }
@@ -285,7 +287,8 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
         issued += 3;
         need += 2;
         sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
-        // tile sums -> member partials; the block finishing the member's last tile updates it
+        // tile sums -> the member's per-tile partials (plain stores: the finish
+        // kernel that follows the pass reads them, ordered by the kernel boundary)
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const T v = partial_warp_sum(ts[i], lane, nlanes);
@@ -297,33 +300,34 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
             for (int w = 0; w < nwarps; ++w) t += red[w][lin];
             L.partials[(size_t)loc * NS + lin] = t;
         }
-        __threadfence();
-        __syncthreads();
-        if (lin == 0) last = (atomicAdd(L.counter, 1u) == (unsigned)L.ntiles - 1) ? 1u : 0u;
-        __syncthreads();
-        if (last) {
-            __threadfence();
-            if (lin < NS) {
-                double ks = 0.0, kc = 0.0;
-                for (int b = 0; b < L.ntiles; ++b) {
-                    const double xv = __ldcg(&L.partials[(size_t)b * NS + lin]);
-                    const double yk = xv - kc, tk = ks + yk;
-                    kc = (tk - ks) - yk;
-                    ks = tk;
-                }
-                tot[lin] = (ks - kc) / ((double)N * N * N);
-            }
-            __syncthreads();
-            if (lin == 0) {
-                *L.counter = 0u;
-                scalar_finish(L.st, tot, L.mc, A.pi, sizeof(T) == 4);
-            }
-        }
-        __syncthreads();
     }
     cp_async_wait<0>();
 }
 
+
+// Member finish of a pass: warp-strided Kahan sums of the member's per-tile
+// partials (lane l takes tiles l, l+32, ...; fixed order, then a fixed shuffle
+// tree), normalised to volume averages, then the FP64 background update.
+template <typename T>
+__global__ void __launch_bounds__(32) ensemble_finish_kernel(const EnsLat* lat, const PassInfo pi) {
+    constexpr int NS = 14;
+    const EnsLat& L = lat[blockIdx.x];
+    __shared__ double tot[16];
+    const int lane = threadIdx.x;
+    const double invV = 1.0 / ((double)L.N * L.N * L.N);
+    for (int s = 0; s < NS; ++s) {
+        double ks = 0.0, kc = 0.0;
+        for (int b = lane; b < L.ntiles; b += 32) {
+            const double yk = L.partials[(size_t)b * NS + s] - kc, tk = ks + yk;
+            kc = (tk - ks) - yk;
+            ks = tk;
+        }
+        const double r = warp_sum(ks - kc);
+        if (lane == 0) tot[s] = r * invV;
+    }
+    __syncwarp();
+    if (lane == 0) scalar_finish(L.st, tot, L.mc, pi, sizeof(T) == 4);
+}
 
 // Observables of one lattice of the two-field model from its measured state
 // and chi shell sums: the chi energy fraction (E_K[1] + E_G[1]) / rho, the
@@ -418,8 +422,14 @@ cudaError_t ens_launch(cl_ensemble* E, int src, const cl::PassInfo& pi, bool wri
     A.ZC = E->ZC;
     A.S = E->S;
     const dim3 block(E->BX, E->BY);
-    if (E->prec == CL_FP32) cl::ensemble_pass_kernel<float, 2, 2><<<E->grid, block, E->smem, s>>>(A);
-    else cl::ensemble_pass_kernel<double, 2, 2><<<E->grid, block, E->smem, s>>>(A);
+    const int n = (int)E->host_lat.size();
+    if (E->prec == CL_FP32) {
+        cl::ensemble_pass_kernel<float, 2, 2><<<E->grid, block, E->smem, s>>>(A);
+        cl::ensemble_finish_kernel<float><<<n, 32, 0, s>>>(E->d_lat, pi);
+    } else {
+        cl::ensemble_pass_kernel<double, 2, 2><<<E->grid, block, E->smem, s>>>(A);
+        cl::ensemble_finish_kernel<double><<<n, 32, 0, s>>>(E->d_lat, pi);
+    }
     return cudaGetLastError();
 }
 
@@ -609,7 +619,6 @@ cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const
             for (int a = 0; a < 4; ++a) d.buf[c][a] = L->buf.f[c][a];
         d.st = L->buf.st;
         d.partials = L->buf.partials;
-        d.counter = L->buf.counter;
         d.mc = L->mc;
         d.N = L->mc.N;
         E->host_lat.push_back(d);
@@ -738,11 +747,13 @@ cl_status ensemble_set_tile(cl_ensemble* E, const int32_t tile[4]) {
 
 cl_status ensemble_autotune(cl_ensemble* E, int32_t max_report, int32_t* tiles, double* ms, int32_t* n_tried) {
     if (!E || max_report < 0) return efail(CL_ERR_ARG, "ensemble_autotune: bad arguments");
-    static const int32_t c32[][4] = {{8, 32, 32, 5}, {8, 32, 16, 5}, {8, 32, 32, 4}, {8, 32, 32, 6}, {8, 16, 32, 5},
-                                     {8, 16, 16, 5}, {4, 32, 32, 5}, {8, 8, 32, 5},  {4, 16, 32, 5}, {8, 32, 8, 5}};
-    static const int32_t c64[][4] = {{16, 16, 32, 5}, {16, 16, 16, 5}, {16, 16, 32, 4}, {16, 8, 32, 5}, {8, 32, 32, 5},
-                                     {8, 16, 32, 5},  {16, 16, 8, 5},  {8, 8, 32, 5},   {16, 4, 32, 5}, {4, 32, 32, 5}};
-    const int nc = 10;
+    static const int32_t c32[][4] = {{8, 32, 32, 5}, {8, 32, 16, 5}, {8, 32, 32, 4}, {8, 16, 32, 4}, {8, 16, 32, 5},
+                                     {8, 16, 32, 6}, {8, 16, 16, 5}, {8, 8, 32, 5},  {8, 8, 32, 6},  {16, 16, 32, 5},
+                                     {16, 8, 32, 5}, {4, 32, 32, 5}};
+    static const int32_t c64[][4] = {{16, 16, 32, 5}, {16, 16, 16, 5}, {16, 16, 32, 4}, {16, 8, 32, 5}, {16, 8, 32, 6},
+                                     {8, 32, 32, 5},  {8, 16, 32, 5},  {16, 16, 8, 5},  {8, 8, 32, 5},  {16, 4, 32, 5},
+                                     {32, 8, 32, 5},  {4, 32, 32, 5}};
+    const int nc = 12;
     const int32_t(*cand)[4] = E->prec == CL_FP32 ? c32 : c64;
     const int n = (int)E->mem.size();
     const int32_t keep[4] = {E->BX, E->BY, E->ZC, E->S};

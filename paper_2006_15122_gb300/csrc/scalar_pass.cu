@@ -231,6 +231,10 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
 #pragma unroll
         for (int i = 0; i < NS; ++i) ts[i] = T(0);
         T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
+        // FP32: unrolled by two, the register rotation of the z-queue (fm <- fc <- fp)
+        // is renamed away in every other plane instead of moved (FP64 keeps the
+        // loop rolled: unrolled it would spill)
+#pragma unroll(sizeof(T) == 4 ? 2 : 1)
         for (int zz = 0; zz < ZC; ++zz, ++need) {
             wait_for(need);  // planes z-1, z, z+1 have landed
             // the stage of plane z-2 was released by the previous iteration and every
