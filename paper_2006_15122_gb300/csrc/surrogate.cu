@@ -225,8 +225,27 @@ __global__ void colsum_kernel(const float* dZ, int ld, int rows, int cols, float
     out[c] = s;
 }
 
-__global__ void adam_kernel(float* w, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, float wd, bf16* wb) {
+// Optimizer state on the device, so that a captured training epoch can be
+// replayed unchanged: the Adam step count, the schedule position and the
+// hyper-parameters of the current call.
+struct TrainDev {
+    long long t;      // Adam steps taken by this handle (bias corrections use t + 1)
+    long long sched;  // minibatch steps taken in this call (cosine schedule position)
+    long long total;  // minibatch steps of this call
+    float lr, lr_end, b1, b2, eps, wd;
+};
+
+// Adam on FP32 master weights; the BF16 copy (when wb != NULL) is refreshed in
+// the same pass.  decay = 1 applies the L2 coefficient (weights), 0 not (biases).
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, size_t n, const TrainDev* td, int decay,
+                            bf16* wb) {
+    const float t = (float)(td->t + 1);
+    const float b1 = td->b1, b2 = td->b2, eps = td->eps, wd = decay ? td->wd : 0.f;
+    const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
+    float lr = td->lr;
+    if (td->lr_end >= 0.f)
+        lr = td->lr_end + 0.5f * (td->lr - td->lr_end) *
+                              (1.f + cospif((float)td->sched / (float)(td->total > 0 ? td->total : 1)));
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i] + wd * w[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -237,6 +256,11 @@ __global__ void adam_kernel(float* w, const float* g, float* m, float* v, size_t
         w[i] = wn;
         if (wb) wb[i] = __float2bfloat16(wn);
     }
+}
+
+__global__ void adam_advance_kernel(TrainDev* td) {
+    td->t += 1;
+    td->sched += 1;
 }
 
 // W ~ N(0, 1/fan_in) in the valid region (Box-Muller on Philox draws), zero padding
@@ -287,7 +311,16 @@ struct cl_surrogate {
     float *mu_in, *sd_in, *mu_out, *sd_out;  // standardization (device, length n_in / n_out)
     std::vector<float> h_mu_in, h_sd_in, h_mu_out, h_sd_out;
     double* dloss = nullptr;
-    long long adam_t = 0;
+    cl::TrainDev* tdev = nullptr;  // device optimizer state
+    int* d_perm = nullptr;         // sample order of the current epoch
+    int64_t perm_cap = 0;
+    cudaStream_t cstream = nullptr;  // private stream for graph capture
+    // captured training epoch, valid for (n, batch, shuffled) and the buffers
+    // it was captured with (gen counts reallocations)
+    cudaGraphExec_t epoch_exec = nullptr;
+    int64_t g_n = -1;
+    int g_bs = -1, g_shuf = -1;
+    long long g_gen = -1, gen = 0;
     long long epochs_done = 0;
     uint64_t seed = 0;
     int sms = 1;
@@ -340,6 +373,7 @@ cl_status ensure_batch(cl_surrogate* S, int n) {
     ok = ok && cudaMalloc(&S->dZbT, sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
     if (!ok) return sfail(CL_ERR_OOM, "surrogate: activation buffers");
     S->Bp = Bp;
+    ++S->gen;
     return CL_OK;
 }
 
@@ -351,6 +385,7 @@ cl_status ensure_data(cl_surrogate* S, size_t n) {
         cudaMalloc(&S->Td, sizeof(float) * n * S->n_out) != cudaSuccess)
         return sfail(CL_ERR_OOM, "surrogate: data buffers");
     S->cap_n = n;
+    ++S->gen;
     return CL_OK;
 }
 
@@ -426,6 +461,10 @@ cl_status surrogate_destroy(cl_surrogate* S) {
     cudaFree(S->Xd); cudaFree(S->Td);
     cudaFree(S->mu_in); cudaFree(S->sd_in); cudaFree(S->mu_out); cudaFree(S->sd_out);
     cudaFree(S->dloss);
+    cudaFree(S->tdev);
+    cudaFree(S->d_perm);
+    if (S->epoch_exec) cudaGraphExecDestroy(S->epoch_exec);
+    if (S->cstream) cudaStreamDestroy(S->cstream);
     delete S;
     return CL_OK;
 }
@@ -472,7 +511,8 @@ cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t d
     }
     ok = ok && cudaMalloc(&S->mu_in, 4 * n_in) == cudaSuccess && cudaMalloc(&S->sd_in, 4 * n_in) == cudaSuccess &&
          cudaMalloc(&S->mu_out, 4 * n_out) == cudaSuccess && cudaMalloc(&S->sd_out, 4 * n_out) == cudaSuccess &&
-         cudaMalloc(&S->dloss, sizeof(double)) == cudaSuccess;
+         cudaMalloc(&S->dloss, sizeof(double)) == cudaSuccess && cudaMalloc(&S->tdev, sizeof(cl::TrainDev)) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         surrogate_destroy(S);
         return sfail(CL_ERR_OOM, "surrogate_create: parameters");
@@ -480,6 +520,7 @@ cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t d
     set_identity_scaling(S);
     upload_scaling(S);
     refresh_bf16(S);
+    cudaMemsetAsync(S->tdev, 0, sizeof(cl::TrainDev), S->stream);
     if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
         surrogate_destroy(S);
         return sfail(CL_ERR_CUDA, "surrogate_create: initialisation");
@@ -597,21 +638,79 @@ cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64
     upload_scaling(S);
     cudaMemcpyAsync(S->Xd, X, sizeof(float) * n * S->n_in, cudaMemcpyHostToDevice, S->stream);
     cudaMemcpyAsync(S->Td, Y, sizeof(float) * n * S->n_out, cudaMemcpyHostToDevice, S->stream);
-    const float b1 = cfg->beta1 > 0 ? cfg->beta1 : 0.9f, b2 = cfg->beta2 > 0 ? cfg->beta2 : 0.999f;
-    const float eps = cfg->eps > 0 ? cfg->eps : 1e-8f;
-    const int64_t per_epoch = (n + bs - 1) / bs, total = per_epoch * cfg->epochs;
-    int* d_perm = nullptr;
+    const int64_t per_epoch = (n + bs - 1) / bs;
+    cl::TrainDev td;
+    // keep the handle's Adam step count, reset the schedule to this call
+    if (cudaMemcpyAsync(&td, S->tdev, sizeof(td), cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+        cudaStreamSynchronize(S->stream) != cudaSuccess)
+        return sfail(CL_ERR_CUDA, "surrogate_train: optimizer state");
+    td.sched = 0;
+    td.total = per_epoch * cfg->epochs;
+    td.lr = cfg->lr;
+    td.lr_end = cfg->lr_end;
+    td.b1 = cfg->beta1 > 0 ? cfg->beta1 : 0.9f;
+    td.b2 = cfg->beta2 > 0 ? cfg->beta2 : 0.999f;
+    td.eps = cfg->eps > 0 ? cfg->eps : 1e-8f;
+    td.wd = cfg->weight_decay;
+    cudaMemcpyAsync(S->tdev, &td, sizeof(td), cudaMemcpyHostToDevice, S->stream);
+    const int shuf = cfg->shuffle ? 1 : 0;
     std::vector<int> perm;
-    if (cfg->shuffle) {
-        if (cudaMalloc(&d_perm, sizeof(int) * n) != cudaSuccess) return sfail(CL_ERR_OOM, "surrogate_train: order");
+    if (shuf) {
+        if (n > S->perm_cap) {
+            cudaFree(S->d_perm);
+            S->d_perm = nullptr;
+            if (cudaMalloc(&S->d_perm, sizeof(int) * n) != cudaSuccess) return sfail(CL_ERR_OOM, "surrogate_train: order");
+            S->perm_cap = n;
+            ++S->gen;
+        }
         perm.resize(n);
     }
-    int64_t step = 0;
+    // one epoch = memset of the loss sum + every minibatch's forward, backward
+    // and Adam update, captured once as a CUDA graph and replayed per epoch
+    if (!S->epoch_exec || S->g_n != n || S->g_bs != bs || S->g_shuf != shuf || S->g_gen != S->gen) {
+        if (S->epoch_exec) cudaGraphExecDestroy(S->epoch_exec);
+        S->epoch_exec = nullptr;
+        cudaStream_t user = S->stream;
+        S->stream = S->cstream;
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
+            const int* idx = shuf ? S->d_perm : nullptr;
+            for (int64_t r0 = 0; r0 < n; r0 += bs) {
+                const int nb = (int)std::min<int64_t>(bs, n - r0);
+                forward(S, idx, r0, nb);
+                backward(S, idx, r0, nb);
+                for (int l = 0; l < S->L; ++l) {
+                    const size_t nw = (size_t)S->P[l + 1] * S->P[l];
+                    cl::adam_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->W[l], S->gW[l], S->mW[l], S->vW[l], nw,
+                                                                       S->tdev, 1, S->Wb[l]);
+                    cl::adam_kernel<<<1, 256, 0, S->stream>>>(S->b[l], S->gb[l], S->mb[l], S->vb[l], S->P[l + 1],
+                                                              S->tdev, 0, nullptr);
+                }
+                cl::adam_advance_kernel<<<1, 1, 0, S->stream>>>(S->tdev);
+            }
+            e = cudaStreamEndCapture(S->stream, &graph);
+        }
+        S->stream = user;
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&S->epoch_exec, graph, 0);
+            cudaGraphDestroy(graph);
+        }
+        if (e != cudaSuccess) {
+            S->epoch_exec = nullptr;
+            cudaGetLastError();
+            return sfail(CL_ERR_CUDA, std::string("surrogate_train: epoch graph: ") + cudaGetErrorString(e));
+        }
+        S->g_n = n;
+        S->g_bs = bs;
+        S->g_shuf = shuf;
+        S->g_gen = S->gen;
+    }
     for (int ep = 0; ep < cfg->epochs; ++ep) {
-        cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
-        if (cfg->shuffle) {
+        if (shuf) {
             // Fisher-Yates with a 64-bit LCG (Knuth's MMIX constants) keyed by the
-            // handle's seed and the epoch
+            // handle's seed and its epoch count
             for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
             uint64_t x = S->seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(S->epochs_done + 1));
             for (int64_t i = n - 1; i > 0; --i) {
@@ -619,39 +718,19 @@ cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64
                 const int64_t j = (int64_t)((x >> 33) % (uint64_t)(i + 1));
                 std::swap(perm[i], perm[j]);
             }
-            cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
-            cudaStreamSynchronize(S->stream);  // perm is reused next epoch
+            cudaMemcpyAsync(S->d_perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
         }
-        for (int64_t r0 = 0; r0 < n; r0 += bs, ++step) {
-            const int nb = (int)std::min<int64_t>(bs, n - r0);
-            forward(S, d_perm, r0, nb);
-            backward(S, d_perm, r0, nb);
-            ++S->adam_t;
-            const float c1 = 1.f - powf(b1, (float)S->adam_t), c2 = 1.f - powf(b2, (float)S->adam_t);
-            float lr = cfg->lr;
-            if (cfg->lr_end >= 0)
-                lr = cfg->lr_end + 0.5f * (cfg->lr - cfg->lr_end) * (1.f + cosf(3.14159265358979f * (float)step / (float)total));
-            for (int l = 0; l < S->L; ++l) {
-                const size_t nw = (size_t)S->P[l + 1] * S->P[l];
-                cl::adam_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->W[l], S->gW[l], S->mW[l], S->vW[l], nw, lr, b1,
-                                                                   b2, eps, c1, c2, cfg->weight_decay, S->Wb[l]);
-                cl::adam_kernel<<<1, 256, 0, S->stream>>>(S->b[l], S->gb[l], S->mb[l], S->vb[l], S->P[l + 1], lr, b1,
-                                                          b2, eps, c1, c2, 0.f, nullptr);
-            }
-        }
+        if (cudaGraphLaunch(S->epoch_exec, S->stream) != cudaSuccess) return sfail(CL_ERR_CUDA, "surrogate_train: launch");
         ++S->epochs_done;
-        if (loss_history) {
+        if (loss_history || shuf) {
+            // the host order buffer is rewritten next epoch: wait for this one
             double l = 0;
-            cudaMemcpyAsync(&l, S->dloss, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-            if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
-                cudaFree(d_perm);
-                return sfail(CL_ERR_CUDA, "surrogate_train");
-            }
-            loss_history[ep] = (float)(l / ((double)n * S->n_out));
+            if (loss_history) cudaMemcpyAsync(&l, S->dloss, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+            if (cudaStreamSynchronize(S->stream) != cudaSuccess) return sfail(CL_ERR_CUDA, "surrogate_train");
+            if (loss_history) loss_history[ep] = (float)(l / ((double)n * S->n_out));
         }
     }
     cudaError_t e = cudaStreamSynchronize(S->stream);
-    cudaFree(d_perm);
     return e == cudaSuccess ? CL_OK : sfail(CL_ERR_CUDA, std::string("surrogate_train: ") + cudaGetErrorString(e));
 }
 
