@@ -32,6 +32,7 @@ def lib():
             ("orc_u1_gauss", [vp, d, d, d, d, d, d], None),
             ("orc_u1_lf_prepare", [vp, C.c_double, d, d, d, d, C.c_double, d, d, d], None),
             ("orc_u1_lf_step", [vp, C.c_double, d, d, d, d, d, d, d, d], None),
+            ("orc_u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
         ]:
             f = getattr(_lib, name)
             f.argtypes = args
@@ -238,6 +239,15 @@ class U1Lattice:
         lib().orc_u1_lf_prepare(self._mp(), dt, _p(self.phi), _p(self.pi), _p(self.theta), _p(self.piA), self.a,
                                 C.byref(b), C.byref(ek), C.byref(eka))
         self.b, self.EKm = b.value, (ek.value, eka.value)
+
+    def vv_steps(self, weights, dt, n=1):
+        """Compact velocity-Verlet VVn (sections 5.3.2, 5.3.3) on synchronized data."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        a, b = C.c_double(self.a), C.c_double(self.b)
+        for _ in range(n):
+            lib().orc_u1_vv_step(self._mp(), len(w), _p(w), dt, _p(self.phi), _p(self.pi), _p(self.theta),
+                                 _p(self.piA), C.byref(a), C.byref(b))
+        self.a, self.b = a.value, b.value
 
     def lf_steps(self, dt, n=1):
         a, b = C.c_double(self.a), C.c_double(self.b)

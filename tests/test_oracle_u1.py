@@ -150,3 +150,76 @@ def test_gauge_invariance_of_the_evolution():
     dth = np.angle(np.exp(1j * (TA.theta - B.theta)))
     assert np.max(np.abs(dth)) < 1e-11
     assert np.max(np.abs(TA.piA - B.piA)) < 1e-11
+
+
+def _vv(name):
+    from oracle import core
+    return {"vv2": core.VV2, "vv4": core.VV4, "vv6": core.VV6}[name]
+
+
+def test_u1_vv2_positions_equal_leapfrog_static():
+    """Static background: VV2 (half kick, drift, half kick) composed over n
+    steps is the staggered leapfrog started with a half kick, so fields and
+    links agree to round-off and the leapfrog momenta, advanced half a step,
+    are VV2's (section 5.3.1 vs 5.3.2)."""
+    N, dt, n = 5, 0.03, 12
+    m = U1Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=1.2, kappa=0.9)
+    A = _random_state(N, 41, m)
+    B = _random_state(N, 41, m)
+    A.vv_steps(_vv("vv2"), dt, n)
+    B.lf_prepare(dt)
+    B.lf_steps(dt, n)
+    assert np.max(np.abs(A.phi - B.phi)) < 1e-12
+    assert np.max(np.abs(A.theta - B.theta)) < 1e-12
+    Kp, KA = B.kernels()
+    assert np.max(np.abs(A.pi - (B.pi + 0.5 * dt * Kp))) < 1e-12
+    assert np.max(np.abs(A.piA - (B.piA + 0.5 * dt * KA))) < 1e-12
+
+
+@pytest.mark.parametrize("integ", ["vv2", "vv4"])
+def test_u1_vv_keeps_gauss_law(integ):
+    """Kicks and drifts of the compact VVn each keep the discrete Gauss law, so
+    the composed step does too, also in an expanding background."""
+    N, dt = 8, 0.04
+    m = U1Model(N=N, dx=0.5, alpha=0.5, fmp2=0.5, lam=1.0, v2=1.0, e=1.0, kappa=1.0)
+    phi, pi, th, piA, _ = u1_ic(m, 2 * np.pi / (N * 0.5), [0.0, 0.0], [0.0, 0.0], seed=6, omega_over_fstar=1.0)
+    lat = U1Lattice(m, phi, pi, th, piA)
+    lat.b = np.sqrt(0.5 / 3.0 * lat.energies().sum())
+    for _ in range(4):
+        lat.vv_steps(_vv(integ), dt, 5)
+        assert lat.gauss() < 1e-13
+    assert lat.a > 1.0
+
+
+@pytest.mark.parametrize("integ,order", [("vv2", 2), ("vv4", 4)])
+def test_u1_vv_convergence_order(integ, order):
+    """Global error after a fixed time against a VV6 solution at a small step:
+    slope 2 for VV2 and 4 for VV4 (sections 4.3.2, 5.3.3)."""
+    N, T = 4, 0.4
+    m = U1Model(N=N, dx=0.7, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=1.1, kappa=0.8)
+    ref = _random_state(N, 53, m)
+    ref.vv_steps(_vv("vv6"), T / 256, 256)
+    errs = []
+    for k in (8, 16):
+        lat = _random_state(N, 53, m)
+        lat.vv_steps(_vv(integ), T / k, k)
+        errs.append(max(np.max(np.abs(lat.phi - ref.phi)), np.max(np.abs(lat.theta - ref.theta)),
+                        np.max(np.abs(lat.pi - ref.pi)), np.max(np.abs(lat.piA - ref.piA))))
+    slope = np.log2(errs[0] / errs[1])
+    assert abs(slope - order) < 0.3, (errs, slope)
+
+
+def test_u1_vv4_is_time_reversible_with_expansion():
+    """The composed step is symmetric: n steps forward and n steps with -dt
+    return the fields, links, momenta, a and b (expanding background)."""
+    N, dt, n = 5, 0.02, 10
+    m = U1Model(N=N, dx=0.6, alpha=0.5, fmp2=0.8, lam=1.0, v2=1.0, e=1.0, kappa=1.0)
+    lat = _random_state(N, 61, m)
+    lat.b = np.sqrt(0.8 / 3.0 * lat.energies().sum())
+    s0 = (lat.phi.copy(), lat.pi.copy(), lat.theta.copy(), lat.piA.copy(), lat.a, lat.b)
+    lat.vv_steps(_vv("vv4"), dt, n)
+    assert lat.a > 1.0 + 1e-3
+    lat.vv_steps(_vv("vv4"), -dt, n)
+    for x, y in zip((lat.phi, lat.pi, lat.theta, lat.piA), s0[:4]):
+        assert np.max(np.abs(x - y)) < 1e-11
+    assert abs(lat.a - s0[4]) < 1e-13 and abs(lat.b - s0[5]) < 1e-12
