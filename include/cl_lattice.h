@@ -62,9 +62,9 @@ typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1 } cl_model_kind;
 /* Integrators (the paper's "switch", section 1.2):
  * CL_INT_LF   staggered leapfrog: scheme III of section 4.2.1 for scalars,
  *             the compact staggered leapfrog of section 5.3.1 for U(1);
- * CL_INT_VV2  velocity-Verlet, section 4.2.3;
- * CL_INT_VV4..CL_INT_VV10  Yoshida compositions of VV2 (section 4.3.2, weights
- *             of the appendix table; VV4 in closed form). Scalar models only. */
+ * CL_INT_VV2  velocity-Verlet, section 4.2.3 (scalars) and 5.3.2 (compact U(1));
+ * CL_INT_VV4..CL_INT_VV10  Yoshida compositions of VV2 (sections 4.3.2 and
+ *             5.3.3, weights of the appendix table; VV4 in closed form). */
 typedef enum {
     CL_INT_LF = 0,
     CL_INT_VV2 = 1,

@@ -277,7 +277,7 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         if (model->pexp != 2 && model->pexp != 4 && model->pexp != 6) return fail(nullptr, CL_ERR_ARG, "pexp must be 2, 4 or 6");
         if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_VV10) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
     } else if (model->kind == CL_MODEL_U1) {
-        if (grid->integrator != CL_INT_LF) return fail(nullptr, CL_ERR_ARG, "the U(1) model runs the compact staggered leapfrog");
+        if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_VV10) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
         if (!(model->gauge_e > 0)) return fail(nullptr, CL_ERR_ARG, "gauge_e must be positive");
     } else {
         return fail(nullptr, CL_ERR_ARG, "unknown model kind");

@@ -10,7 +10,8 @@
 //            + a^{alpha-1}/(e dx^3) sum_{j!=i} [Im V_ij(n) - Im V_ij(n-j)],
 //   V_ij(n) = V_i(n) V_j(n+i) V_i*(n+j) V_j*(n) = exp(-i theta_ij),
 //   theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n),
-// kappa = (w*/f*)^2.  Drifts (compact staggered leapfrog, section 5.3.1):
+// kappa = (w*/f*)^2.  Drifts (compact staggered leapfrog, section 5.3.1, and
+// the compact velocity-Verlet VV2..VV10 of sections 5.3.2-5.3.3 with dt -> w_p dt):
 //   phi <- phi + dt a_{1/2}^{-(3-alpha)} pi,
 //   V_i <- exp(-i e dx dt a_{1/2}^{-(1-alpha)} piA_i) V_i  (theta_i += ..., wrapped to [-pi, pi)),
 // the exact exponential of the link drift (unitary for any step).
@@ -95,6 +96,35 @@ __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc,
         st->staggered = 1;
         st->cd = 0.0;
         st->cdA = 0.0;
+        return;
+    }
+    if (kind == PK_VV_FIRST || kind == PK_VV_MID || kind == PK_VV_LAST) {
+        // compact velocity-Verlet VVn (sections 5.3.2, 5.3.3): this pass closed
+        // the kick of sub-step p-1 (energies E(p-1) of the synchronized momenta)
+        // and opened the one of sub-step p; the next pass drifts with a_{1/2}
+        double bsync = st->b;
+        if (kind != PK_VV_FIRST) bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
+        {
+            const double r = rhs(a, Et);
+            st->hc = r > 0 ? fabs(bsync * bsync - r) / r : 0.0;
+        }
+        if (kind == PK_VV_LAST) {
+            st->b = bsync;
+            st->cd = 0.0;
+            st->cdA = 0.0;
+            return;
+        }
+        const double h = pi.wn * pi.dt;
+        const double bn = bsync + 0.5 * h * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
+        st->bh = bn;
+        const double an = a + h * bn, ah = 0.5 * (a + an);
+        st->cd = h * pow(ah, -(3.0 - mc.alpha));
+        st->cdA = mc.e * mc.dx * h * pow(ah, -(1.0 - mc.alpha));
+        st->a = an;
+        st->A1 = pow(an, 1.0 + mc.alpha);
+        st->A3 = pow(an, 3.0 + mc.alpha);
+        st->Am = pow(an, mc.alpha - 1.0);
+        st->t += h;
         return;
     }
     // PK_LF: b_{+1/2} with the averaged kinetic energies (fixed point in a_{+1/2})

@@ -66,7 +66,7 @@ def test_init_rejects_unstable_time_step():
     assert b"stability bound" in cl.load().cl_last_error(None)
 
 
-@pytest.mark.parametrize("bad", ["integrator", "pexp", "fields", "kir", "u1_vv"])
+@pytest.mark.parametrize("bad", ["integrator", "pexp", "fields", "kir", "u1_charge", "u1_integrator"])
 def test_init_rejects_bad_arguments(bad):
     m = cl.make_model(n_fields=1, pexp=2)
     g = cl.make_grid(16, 0.5, 0.01)
@@ -78,9 +78,14 @@ def test_init_rejects_bad_arguments(bad):
         m.n_fields = 3
     if bad == "kir":
         g.kIR = -1.0
-    if bad == "u1_vv":
+    if bad == "u1_charge":
         m.kind = cl.CL_MODEL_U1
+        m.gauge_e = 0.0
         g.integrator = cl.CL_INT_VV4
+    if bad == "u1_integrator":
+        m.kind = cl.CL_MODEL_U1
+        m.gauge_e = 1.0
+        g.integrator = 6
     st, h = _init(m, g, cl.make_init())
     assert st == cl.CL_ERR_ARG and not h.value
 

@@ -22,10 +22,10 @@ def angle_err(a, b):
 
 
 def gpu_u1(N, kIR, dt, prec, fmp=0.0, alpha=0.0, e=1.0, lam=1.0, v2=1.0, omega=1.0, spectrum=0, seed=0,
-           phi0=(0.0, 0.0)):
+           phi0=(0.0, 0.0), integ="lf"):
     m = cl.make_model(kind=cl.CL_MODEL_U1, alpha=alpha, fstar_over_mp=fmp, omega_over_fstar=omega, lam=lam,
                       vev2=v2, gauge_e=e)
-    g = cl.make_grid(N, kIR, dt, "lf", prec)
+    g = cl.make_grid(N, kIR, dt, integ, prec)
     return cl.Lattice(m, g, cl.make_init(phi0=phi0, seed=seed, spectrum=spectrum))
 
 
@@ -97,4 +97,54 @@ def test_u1_gauss_law_is_preserved(prec, tol):
     assert max(g) < tol, g
     mm = lat.measure_means()
     assert mm["EG"][1] > 0.0  # magnetic field has developed
+    lat.close()
+
+
+@pytest.mark.parametrize("integ,fmp,alpha", [("vv2", 0.0, 0.0), ("vv4", 0.8, 0.5), ("vv6", 0.5, 0.0)])
+def test_u1_fp64_velocity_verlet_matches_oracle(integ, fmp, alpha):
+    """Compact VV2/VVn (sections 5.3.2, 5.3.3): merged-kick passes on the GPU
+    against the unmerged oracle step, 7 steps in two evolve calls."""
+    import oracle
+    N, kIR, dt = 16, 2 * math.pi / (16 * 0.5), 0.04
+    lat = gpu_u1(N, kIR, dt, cl.CL_FP64, fmp=fmp, alpha=alpha, e=0.9, lam=1.2, v2=0.7, omega=1.1, integ=integ)
+    om = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.7, e=0.9, kappa=1.21)
+    phi = inputs.fields(2, N, seed=13, amp=0.6, kmax=4, means=[0.4, -0.1])
+    pi = inputs.fields(2, N, seed=14, amp=0.3, kmax=4)
+    th = inputs.angles(N, 15, scale=0.4)
+    pa = inputs.fields(3, N, seed=16, amp=0.2, kmax=4)
+    ref = U1Lattice(om, phi, pi, th, pa)
+    ref.b = math.sqrt(fmp * fmp / 3 * ref.energies().sum()) if fmp > 0 else 0.0
+    for i in range(2):
+        lat.set_field(cl.FIELD(i), phi[i])
+        lat.set_field(cl.MOMENTUM(i), pi[i])
+    for i in range(3):
+        lat.set_field(cl.LINK(i), th[i])
+        lat.set_field(cl.EMOMENTUM(i), pa[i])
+    lat.set_background(1.0, ref.b, 0.0)
+    lat.evolve(3)
+    lat.evolve(4)
+    ref.vv_steps({"vv2": oracle.VV2, "vv4": oracle.VV4, "vv6": oracle.VV6}[integ], dt, 7)
+    gphi, gpi, gth, gpa = get_all(lat)
+    assert rel(gphi, ref.phi) < 1e-12
+    assert rel(gpi, ref.pi) < 1e-12
+    assert angle_err(gth, ref.theta) < 1e-12
+    assert rel(gpa, ref.piA) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 + 1e-12 * abs(ref.b)
+    assert abs(mm["t"] - 7 * dt) < 1e-12
+    E = ref.energies()
+    assert abs(mm["EK"][0] - E[0]) < 1e-11 * E.sum() and abs(mm["EK"][1] - E[3]) < 1e-11 * E.sum()
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(cl.CL_FP64, 1e-13), (cl.CL_FP32, 1e-5)])
+def test_u1_velocity_verlet_keeps_gauss_law(prec, tol):
+    N, dx = 32, 0.5
+    lat = gpu_u1(N, 2 * math.pi / (N * dx), 0.05, prec, spectrum=1, seed=8, integ="vv4")
+    g = []
+    for _ in range(4):
+        lat.evolve(10)
+        g.append(lat.measure_means()["gauss_violation"])
+    assert max(g) < tol, g
+    assert lat.measure_means()["EG"][1] > 0.0
     lat.close()
