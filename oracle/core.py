@@ -33,6 +33,7 @@ def lib():
             ("orc_u1_lf_prepare", [vp, C.c_double, d, d, d, d, C.c_double, d, d, d], None),
             ("orc_u1_lf_step", [vp, C.c_double, d, d, d, d, d, d, d, d], None),
             ("orc_u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
+            ("orc_scalar_vv_step_fluid", [vp, vp, C.c_int, d, C.c_double, d, d, d], None),
         ]:
             f = getattr(_lib, name)
             f.argtypes = args
@@ -94,6 +95,30 @@ class ScalarModel:
 
     def c(self):
         return _ScalarModelC(self.N, self.Ns, self.pexp, self.dx, self.alpha, self.fmp2, self.lam, self.q)
+
+
+class _FluidC(C.Structure):
+    _fields_ = [("a0", C.c_double), ("H0", C.c_double), ("p", C.c_double)]
+
+
+@dataclass
+class Fluid:
+    """Scale factor sourced by an external fluid of equation of state w
+    (section 4.1): a(eta) = a0 (1 + H0 eta / p)^p, p = 2/(3(1 + w) - 2 alpha)."""
+    a0: float
+    H0: float
+    w: float
+    alpha: float
+
+    @property
+    def p(self):
+        return 2.0 / (3.0 * (1.0 + self.w) - 2.0 * self.alpha)
+
+    def a(self, t):
+        return self.a0 * (1.0 + self.H0 * t / self.p) ** self.p
+
+    def b(self, t):
+        return self.a0 * self.H0 * (1.0 + self.H0 * t / self.p) ** (self.p - 1.0)
 
 
 @dataclass
@@ -171,6 +196,19 @@ class ScalarLattice:
         for _ in range(n):
             lib().orc_scalar_vv_step(self._mp(), len(w), _p(w), dt, _p(self.phi), _p(self.pi), C.byref(a), C.byref(b))
         self.a, self.b = a.value, b.value
+
+    def vv_steps_fluid(self, fluid, weights, dt, n=1):
+        """VVn with the scale factor of an external fluid (section 4.1):
+        fluid = Fluid(a0, H0, w, alpha); self.t is the program time."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        f = _FluidC(fluid.a0, fluid.H0, fluid.p)
+        t = C.c_double(getattr(self, "t", 0.0))
+        for _ in range(n):
+            lib().orc_scalar_vv_step_fluid(self._mp(), C.byref(f), len(w), _p(w), dt, _p(self.phi), _p(self.pi),
+                                           C.byref(t))
+        self.t = t.value
+        self.a = fluid.a(self.t)
+        self.b = fluid.b(self.t)
 
     def lf3_prepare(self, dt):
         b = C.c_double(self.b)

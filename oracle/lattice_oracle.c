@@ -577,3 +577,37 @@ void orc_u1_vv_step(const orc_u1_model* m, int s, const double* w, double dt, do
     free(Kp);
     free(KA);
 }
+
+/* ------------------------------------------------ prescribed background */
+
+/* Expansion sourced by an external fluid of constant equation of state w
+ * (section 4.1): a(eta) = a0 (1 + H0 (eta - eta0)/p)^p with
+ * p = 2/(3(1 + w) - 2 alpha) and H0 the program Hubble rate a'/a at eta0 = 0. */
+typedef struct {
+    double a0, H0, p;
+} orc_fluid;
+
+static double fluid_a(const orc_fluid* f, double t) { return f->a0 * pow(1.0 + f->H0 * t / f->p, f->p); }
+
+/* One step of the Yoshida-composed velocity-Verlet VVn for scalars when the
+ * scale factor is prescribed (section 4.1 with the integrator of section
+ * 4.3.2): for each sub-step p with h = w_p dt,
+ *   pi_1/2 = pi + h/2 K[a(t), phi]
+ *   a_1/2  = (a(t) + a(t + h))/2
+ *   phi    = phi + h pi_1/2 a_1/2^{-(3-alpha)}
+ *   pi     = pi_1/2 + h/2 K[a(t + h), phi],   t <- t + h,
+ * i.e. the self-consistent scheme with the b, a updates replaced by a(t). */
+void orc_scalar_vv_step_fluid(const orc_scalar_model* m, const orc_fluid* f, int s, const double* w, double dt,
+                              double* phi, double* pi, double* t) {
+    const int64_t V = m->N * m->N * m->N;
+    double* K = (double*)malloc(sizeof(double) * (size_t)(m->Ns * V));
+    for (int p = 0; p < s; ++p) {
+        const double h = w[p] * dt;
+        const double a = fluid_a(f, *t), an = fluid_a(f, *t + h);
+        kick(m, phi, pi, a, 0.5 * h, K);
+        drift(m, phi, pi, h * pow(0.5 * (a + an), -(3.0 - m->alpha)));
+        kick(m, phi, pi, an, 0.5 * h, K);
+        *t += h;
+    }
+    free(K);
+}

@@ -255,3 +255,60 @@ def test_yoshida_weights():
     assert abs(printed["w1"] - w[0]) < 1e-15
     # the printed w2 is off by 2e-8: the closed form is used instead
     assert 1e-8 < abs(printed["w2"] - w[1]) < 1e-7
+
+
+def test_fluid_background_massless_modes_match_closed_form():
+    """Radiation fluid (w = 1/3) in conformal time (alpha = 1): p = 1 and
+    a = a0 (1 + H0 eta) has a'' = 0, so for a free massless field u = a phi_k
+    obeys u'' = -w^2 u with the lattice eigenvalue w^2 = sum_i 4 sin^2(pi n_i/N)/dx^2
+    (section 3.2.1): u(eta) = u0 cos(w eta) + u0' sin(w eta)/w, and
+    pi = a^2 phi' = a u' - a' u.  VV4 at a small step reaches it to O(dt^4)."""
+    from oracle.core import Fluid
+    N, dx, a0, H0, T = 8, 0.7, 1.3, 0.8, 1.0
+    fl = Fluid(a0=a0, H0=H0, w=1.0 / 3.0, alpha=1.0)
+    assert abs(fl.p - 1.0) < 1e-15
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=1.0, fmp2=0.0, lam=0.0)
+    phi = inputs.fields(1, N, seed=5, amp=0.8, means=[0.3])
+    pi = inputs.fields(1, N, seed=6, amp=0.5, means=[0.1])
+    errs = []
+    for dt in (0.01, 0.005):
+        lat = ScalarLattice(m, phi, pi, a=a0)
+        lat.t = 0.0
+        lat.vv_steps_fluid(fl, oracle.VV4, dt, int(round(T / dt)))
+        k = mode_numbers(N)
+        nz, ny, nx = np.meshgrid(k, k, k, indexing="ij")
+        w = np.sqrt(4 * (np.sin(np.pi * nx / N) ** 2 + np.sin(np.pi * ny / N) ** 2 + np.sin(np.pi * nz / N) ** 2)) / dx
+        F0, P0 = dft_forward(phi[0]), dft_forward(pi[0])
+        u0 = a0 * F0
+        du0 = a0 * H0 * F0 + P0 / a0          # a' phi + a phi', phi' = pi / a^2
+        ws = np.where(w > 0, w, 1.0)
+        u = u0 * np.cos(w * T) + np.where(w > 0, du0 * np.sin(w * T) / ws, du0 * T)
+        du = -u0 * w * np.sin(w * T) + du0 * np.cos(w * T)
+        aT, bT = fl.a(T), fl.b(T)
+        phi_ex = dft_inverse(u / aT).real
+        pi_ex = dft_inverse(aT * du - bT * u).real
+        errs.append(max(np.max(np.abs(lat.phi[0] - phi_ex)), np.max(np.abs(lat.pi[0] - pi_ex))))
+        assert abs(lat.a - aT) < 1e-12 and abs(lat.t - T) < 1e-12
+    assert errs[1] < 1e-6, errs
+    assert 3.6 < np.log2(errs[0] / errs[1]) < 4.4, errs
+
+
+def test_fluid_background_homogeneous_mode_matches_ode():
+    """Matter fluid (w = 0), alpha = 0: a = a0 (1 + 3 H0 t/2)^(2/3).  The
+    homogeneous phi^4 mode follows phi' = a^-3 pi, pi' = -a^3 lam phi^3
+    (Hamiltonian form of section 4.2.3) integrated by DOP853."""
+    from oracle.core import Fluid
+    fl = Fluid(a0=1.0, H0=0.6, w=0.0, alpha=0.0)
+    lam, phi0, T, N = 1.0, 1.0, 4.0, 2
+    m = ScalarModel(N=N, Ns=1, pexp=4, dx=1.0, alpha=0.0, fmp2=0.0, lam=lam)
+
+    def rhs(t, y):
+        a = fl.a(t)
+        return [y[1] / a ** 3, -a ** 3 * lam * y[0] ** 3]
+
+    sol = solve_ivp(rhs, (0, T), [phi0, 0.0], method="DOP853", rtol=1e-13, atol=1e-15)
+    lat = ScalarLattice(m, np.full((1, N, N, N), phi0), np.zeros((1, N, N, N)))
+    lat.t = 0.0
+    lat.vv_steps_fluid(fl, oracle.VV4, 0.01, 400)
+    assert abs(lat.phi[0, 0, 0, 0] - sol.y[0, -1]) < 1e-8
+    assert abs(lat.pi[0, 0, 0, 0] - sol.y[1, -1]) < 1e-8
