@@ -76,11 +76,20 @@ typedef enum {
 
 typedef enum { CL_FP64 = 0, CL_FP32 = 1 } cl_precision;
 
+/* Expansion (section 4.1).
+ * CL_BG_FRIEDMANN: self-consistent, b' = K_a from the volume-averaged energies
+ *   (fstar_over_mp = 0 selects a static background, a = a0, b = 0);
+ * CL_BG_FLUID: sourced by an external fluid of constant equation of state
+ *   fluid_w, a(t) = a0 (1 + hubble0 t / p)^p with p = 2/(3(1 + fluid_w) - 2 alpha)
+ *   and hubble0 the program Hubble rate a'/a at t = 0 (scalar model under the
+ *   velocity-Verlet integrators; the Hubble constraint is then reported as 0). */
+typedef enum { CL_BG_FRIEDMANN = 0, CL_BG_FLUID = 1 } cl_background;
+
 typedef struct {
     int32_t kind;            /* cl_model_kind */
     int32_t n_fields;        /* CL_MODEL_SCALAR: 1 or 2; ignored for CL_MODEL_U1 */
     int32_t pexp;            /* p of (lam/p)|phi|^p: 2, 4 or 6 (scalar) */
-    int32_t reserved;
+    int32_t background;      /* cl_background */
     double alpha;            /* alpha-time exponent (section 4.1) */
     double fstar_over_mp;    /* f_star/m_p; 0 selects a static background (a = 1, b = 0) */
     double omega_over_fstar; /* w_star/f_star: amplitude factor of the vacuum fluctuations (section 7) */
@@ -88,6 +97,8 @@ typedef struct {
     double q;                /* scalar, n_fields = 2: coupling of (q/2) phi^2 chi^2 */
     double vev2;             /* U(1): vev2 */
     double gauge_e;          /* U(1): gauge coupling e = g_A Q_A in program units */
+    double fluid_w;          /* CL_BG_FLUID: equation of state w of the fluid */
+    double hubble0;          /* CL_BG_FLUID: program Hubble rate a'/a at t = 0 */
 } cl_model;
 
 typedef struct {
@@ -190,9 +201,10 @@ cl_status lattice_get_field(cl_lattice* h, int32_t which, double* dst, int32_t o
  * handle splits it into its mean and fluctuation.  Ordered on the stream. */
 cl_status lattice_set_field(cl_lattice* h, int32_t which, const double* src, int32_t on_device);
 
-/* Set the background: scale factor a and b = a'.  A NaN b is replaced by
- * the positive root of the Hubble constraint of the current fields.  Marks
- * the state as synchronized (momenta at the fields' time). */
+/* Set the background: scale factor a and b = a' at program time t.  A NaN b
+ * is replaced by the positive root of the Hubble constraint of the current
+ * fields.  Under CL_BG_FLUID a and b are ignored and follow t.  Marks the
+ * state as synchronized (momenta at the fields' time). */
 cl_status lattice_set_background(cl_lattice* h, double a, double b, double t);
 
 /* Checkpoint: raw arrays, means and background with a header and a CRC-32;

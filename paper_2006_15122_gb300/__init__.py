@@ -19,6 +19,7 @@ CL_OK, CL_ERR_ARG, CL_ERR_CUDA, CL_ERR_OOM, CL_ERR_UNSTABLE_DT, CL_ERR_NONFINITE
 CL_MODEL_SCALAR, CL_MODEL_U1 = 0, 1
 CL_INT_LF, CL_INT_VV2, CL_INT_VV4, CL_INT_VV6, CL_INT_VV8, CL_INT_VV10 = range(6)
 CL_FP64, CL_FP32 = 0, 1
+CL_BG_FRIEDMANN, CL_BG_FLUID = 0, 1
 INTEGRATORS = {"lf": CL_INT_LF, "vv2": CL_INT_VV2, "vv4": CL_INT_VV4, "vv6": CL_INT_VV6, "vv8": CL_INT_VV8,
                "vv10": CL_INT_VV10}
 
@@ -40,9 +41,10 @@ def EMOMENTUM(i):
 
 
 class cl_model(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("n_fields", C.c_int32), ("pexp", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("kind", C.c_int32), ("n_fields", C.c_int32), ("pexp", C.c_int32), ("background", C.c_int32),
                 ("alpha", C.c_double), ("fstar_over_mp", C.c_double), ("omega_over_fstar", C.c_double),
-                ("lam", C.c_double), ("q", C.c_double), ("vev2", C.c_double), ("gauge_e", C.c_double)]
+                ("lam", C.c_double), ("q", C.c_double), ("vev2", C.c_double), ("gauge_e", C.c_double),
+                ("fluid_w", C.c_double), ("hubble0", C.c_double)]
 
 
 class cl_grid(C.Structure):
@@ -171,8 +173,9 @@ def _dev_ptr(t):
 
 
 def make_model(kind=CL_MODEL_SCALAR, n_fields=1, pexp=2, alpha=0.0, fstar_over_mp=0.0, omega_over_fstar=1.0,
-               lam=1.0, q=0.0, vev2=1.0, gauge_e=1.0):
-    return cl_model(kind, n_fields, pexp, 0, alpha, fstar_over_mp, omega_over_fstar, lam, q, vev2, gauge_e)
+               lam=1.0, q=0.0, vev2=1.0, gauge_e=1.0, background=CL_BG_FRIEDMANN, fluid_w=0.0, hubble0=0.0):
+    return cl_model(kind, n_fields, pexp, background, alpha, fstar_over_mp, omega_over_fstar, lam, q, vev2, gauge_e,
+                    fluid_w, hubble0)
 
 
 def make_grid(N, kIR, dt, integrator=CL_INT_VV2, precision=CL_FP64, force_dt=False):

@@ -69,7 +69,18 @@ struct PassInfo {
 struct ModelConst {
     int kind, nf, pexp, N;
     double alpha, fmp2, lam, q, vev2, e, kappa, dx, idx2;
+    // prescribed background (section 4.1): a(t) = bg_a0 (1 + bg_H0 t / bg_p)^bg_p when bg != 0
+    int bg;
+    double bg_p, bg_H0, bg_a0;
 };
+
+// Scale factor and its program-time derivative of the prescribed background.
+__host__ __device__ inline double bg_a(const ModelConst& mc, double t) {
+    return mc.bg_a0 * pow(1.0 + mc.bg_H0 * t / mc.bg_p, mc.bg_p);
+}
+__host__ __device__ inline double bg_b(const ModelConst& mc, double t) {
+    return mc.bg_a0 * mc.bg_H0 * pow(1.0 + mc.bg_H0 * t / mc.bg_p, mc.bg_p - 1.0);
+}
 
 // Per-lattice device resources.
 struct Buffers {

@@ -283,6 +283,15 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         return fail(nullptr, CL_ERR_ARG, "unknown model kind");
     }
     if (!(model->omega_over_fstar > 0)) return fail(nullptr, CL_ERR_ARG, "omega_over_fstar must be positive");
+    if (model->background != CL_BG_FRIEDMANN && model->background != CL_BG_FLUID)
+        return fail(nullptr, CL_ERR_ARG, "unknown background");
+    if (model->background == CL_BG_FLUID) {
+        const double den = 3.0 * (1.0 + model->fluid_w) - 2.0 * model->alpha;
+        if (!(den > 0) || !isfinite(model->fluid_w) || !(model->hubble0 >= 0) || !isfinite(model->hubble0))
+            return fail(nullptr, CL_ERR_ARG, "fluid background needs 3(1 + w) - 2 alpha > 0 and hubble0 >= 0");
+        if (grid->integrator == CL_INT_LF || model->kind != CL_MODEL_SCALAR)
+            return fail(nullptr, CL_ERR_ARG, "the fluid background runs the scalar model under velocity-Verlet");
+    }
     if (init->a0 < 0 || !isfinite(init->a0)) return fail(nullptr, CL_ERR_ARG, "a0 must be positive (0 selects 1)");
 
     cl_lattice* L = new cl_lattice();
@@ -316,6 +325,10 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     mc.kappa = model->omega_over_fstar * model->omega_over_fstar;
     mc.dx = 2.0 * M_PI / (grid->kIR * N);
     mc.idx2 = 1.0 / (mc.dx * mc.dx);
+    mc.bg = model->background == CL_BG_FLUID ? 1 : 0;
+    mc.bg_p = mc.bg ? 2.0 / (3.0 * (1.0 + model->fluid_w) - 2.0 * model->alpha) : 1.0;
+    mc.bg_H0 = mc.bg ? model->hubble0 : 0.0;
+    mc.bg_a0 = L->init.a0;
 
     // linear stability of the highest lattice mode
     {
@@ -598,6 +611,11 @@ __global__ void set_background_kernel(cl::DevState* st, double a, double b, doub
 
 extern "C" cl_status lattice_set_background(cl_lattice* h, double a, double b, double t) {
     if (!h) return fail(nullptr, CL_ERR_ARG, "NULL handle");
+    if (h->mc.bg) {  // prescribed background: a and b follow t
+        if (!isfinite(t)) return fail(h, CL_ERR_ARG, "t must be finite");
+        a = cl::bg_a(h->mc, t);
+        b = cl::bg_b(h->mc, t);
+    }
     if (!(a > 0) || !isfinite(a)) return fail(h, CL_ERR_ARG, "a must be positive");
     // a pending leapfrog drift is never left between calls, so shifts of phi are already applied
     set_background_kernel<<<1, 1, 0, h->stream>>>(h->buf.st, a, isnan(b) ? 0.0 : b, t, h->mc.alpha);

@@ -86,7 +86,9 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
 
     const int kind = pi.kind;
     if (kind == PK_MEASURE) {
-        if (st->staggered) {  // scheme III Hubble constraint at the half step behind the fields
+        if (mc.bg) {
+            st->hc = 0.0;
+        } else if (st->staggered) {  // scheme III Hubble constraint at the half step behind the fields
             const double rhs = hubble_rhs(mc, st->ahm, st->EKm + 0.5 * (st->EGm + EGt) + 0.5 * (st->EVm + EVt));
             st->hc = rhs > 0 ? fabs(st->b * st->b - rhs) / rhs : 0.0;
         } else {
@@ -96,7 +98,8 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
         return;
     }
     if (kind == PK_INIT_B) {
-        st->b = mc.fmp2 > 0 ? sqrt(fmax(hubble_rhs(mc, a, EKt + EGt + EVt), 0.0)) : 0.0;
+        if (mc.bg) st->b = bg_b(mc, st->t);
+        else st->b = mc.fmp2 > 0 ? sqrt(fmax(hubble_rhs(mc, a, EKt + EGt + EVt), 0.0)) : 0.0;
         st->hc = 0.0;
         return;
     }
@@ -107,19 +110,32 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
     }
 
     double bsync = st->b;
-    if (kind == PK_VV_MID || kind == PK_VV_LAST) {
-        bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
-        const double rhs = hubble_rhs(mc, a, EKt + EGt + EVt);
-        st->hc = rhs > 0 ? fabs(bsync * bsync - rhs) / rhs : 0.0;
-    }
     double bnext = 0.0, anew = a, ah = a;
-    if (kind == PK_VV_FIRST || kind == PK_VV_MID) {
-        bnext = bsync + 0.5 * pi.wn * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
-        st->bh = bnext;
-        anew = a + pi.wn * pi.dt * bnext;
-        ah = 0.5 * (a + anew);
-    } else if (kind == PK_VV_LAST) {
-        st->b = bsync;
+    if (kind == PK_VV_FIRST || kind == PK_VV_MID || kind == PK_VV_LAST) {
+        if (mc.bg) {
+            // prescribed background: a and b follow the program time; the
+            // Hubble constraint does not apply (reported as 0)
+            st->hc = 0.0;
+            st->b = bg_b(mc, st->t);
+            if (kind != PK_VV_LAST) {
+                anew = bg_a(mc, st->t + pi.wn * pi.dt);
+                ah = 0.5 * (a + anew);
+            }
+        } else {
+            if (kind == PK_VV_MID || kind == PK_VV_LAST) {
+                bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
+                const double rhs = hubble_rhs(mc, a, EKt + EGt + EVt);
+                st->hc = rhs > 0 ? fabs(bsync * bsync - rhs) / rhs : 0.0;
+            }
+            if (kind == PK_VV_LAST) {
+                st->b = bsync;
+            } else {
+                bnext = bsync + 0.5 * pi.wn * pi.dt * Ka_of(mc, a, EKt, EGt, EVt);
+                st->bh = bnext;
+                anew = a + pi.wn * pi.dt * bnext;
+                ah = 0.5 * (a + anew);
+            }
+        }
     } else if (kind == PK_LF) {
         // Scheme III: b_{+1/2} = b_{-1/2} + dt K_a[a, (E_K(-1/2)+E_K(+1/2))/2, E_G, E_V],
         // E_K(+1/2) = S / (2 a_{+1/2}^6), a_{+1/2} = a + dt b_{+1/2}/2: fixed point.

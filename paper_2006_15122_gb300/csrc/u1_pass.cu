@@ -68,7 +68,9 @@ __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc,
     auto rhs = [&](double aa, double E) { return mc.fmp2 / 3.0 * pow(aa, 2.0 * (mc.alpha + 1.0)) * E; };
     const int kind = pi.kind;
     if (kind == PK_MEASURE) {
-        if (st->staggered) {
+        if (mc.bg) {
+            st->hc = 0.0;
+        } else if (st->staggered) {
             const double r = rhs(st->ahm, st->EKm + st->EKAm + 0.5 * (st->EGm + EGp) + 0.5 * (st->EVm + EV) +
                                               0.5 * (st->EGAm + EGA));
             st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
@@ -79,7 +81,8 @@ __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc,
         return;
     }
     if (kind == PK_INIT_B) {
-        st->b = mc.fmp2 > 0 ? sqrt(fmax(rhs(a, Et), 0.0)) : 0.0;
+        if (mc.bg) st->b = bg_b(mc, st->t);
+        else st->b = mc.fmp2 > 0 ? sqrt(fmax(rhs(a, Et), 0.0)) : 0.0;
         st->hc = 0.0;
         return;
     }
@@ -103,8 +106,11 @@ __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc,
         // the kick of sub-step p-1 (energies E(p-1) of the synchronized momenta)
         // and opened the one of sub-step p; the next pass drifts with a_{1/2}
         double bsync = st->b;
-        if (kind != PK_VV_FIRST) bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
-        {
+        if (mc.bg) {
+            bsync = bg_b(mc, st->t);  // prescribed background (section 4.1)
+            st->hc = 0.0;
+        } else {
+            if (kind != PK_VV_FIRST) bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
             const double r = rhs(a, Et);
             st->hc = r > 0 ? fabs(bsync * bsync - r) / r : 0.0;
         }
@@ -115,9 +121,16 @@ __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc,
             return;
         }
         const double h = pi.wn * pi.dt;
-        const double bn = bsync + 0.5 * h * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
-        st->bh = bn;
-        const double an = a + h * bn, ah = 0.5 * (a + an);
+        double an;
+        if (mc.bg) {
+            st->b = bsync;
+            an = bg_a(mc, st->t + h);
+        } else {
+            const double bn = bsync + 0.5 * h * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
+            st->bh = bn;
+            an = a + h * bn;
+        }
+        const double ah = 0.5 * (a + an);
         st->cd = h * pow(ah, -(3.0 - mc.alpha));
         st->cdA = mc.e * mc.dx * h * pow(ah, -(1.0 - mc.alpha));
         st->a = an;

@@ -191,3 +191,42 @@ def test_nonfinite_state_is_reported():
         lat.measure_means()
     assert e.value.status == cl.CL_ERR_NONFINITE
     lat.close()
+
+
+@pytest.mark.parametrize("integ,w,alpha", [("vv4", 1.0 / 3.0, 1.0), ("vv2", 0.0, 0.0)])
+def test_fluid_background_matches_oracle(integ, w, alpha):
+    """Prescribed expansion of an external fluid (section 4.1): the GPU passes
+    against the oracle's VVn with a(t) = a0 (1 + H0 t/p)^p, 9 steps in two calls."""
+    from oracle.core import Fluid
+    N, kIR, dt, H0, a0 = 24, 0.6, 0.01, 0.7, 1.2
+    model = cl.make_model(n_fields=2, pexp=2, alpha=alpha, lam=1.0, q=30.0, omega_over_fstar=0.05,
+                          background=cl.CL_BG_FLUID, fluid_w=w, hubble0=H0)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, integ, cl.CL_FP64), cl.make_init(phi0=(1.0, 0.0), a0=a0))
+    om = ScalarModel(N=N, Ns=2, pexp=2, dx=2 * math.pi / (kIR * N), alpha=alpha, fmp2=0.0, lam=1.0, q=30.0)
+    phi = inputs.fields(2, N, seed=71, amp=0.05, kmax=4, means=[1.0, 0.0])
+    pi = inputs.fields(2, N, seed=72, amp=0.05, kmax=4)
+    for f in range(2):
+        lat.set_field(cl.FIELD(f), phi[f])
+        lat.set_field(cl.MOMENTUM(f), pi[f])
+    lat.set_background(0.0, 0.0, 0.0)
+    fl = Fluid(a0=a0, H0=H0, w=w, alpha=alpha)
+    ref = ScalarLattice(om, phi, pi, a=a0)
+    ref.t = 0.0
+    lat.evolve(4)
+    lat.evolve(5)
+    ref.vv_steps_fluid(fl, {"vv2": oracle.VV2, "vv4": oracle.VV4}[integ], dt, 9)
+    gphi = np.stack([lat.get_field(cl.FIELD(f)) for f in range(2)])
+    gpi = np.stack([lat.get_field(cl.MOMENTUM(f)) for f in range(2)])
+    assert rel(gphi - gphi.mean(axis=(1, 2, 3), keepdims=True), ref.phi - ref.phi.mean(axis=(1, 2, 3), keepdims=True)) < 1e-11
+    assert rel(gpi, ref.pi) < 1e-11
+    mm = lat.measure_means()
+    assert abs(mm["a"] - fl.a(9 * dt)) < 1e-13 and abs(mm["b"] - fl.b(9 * dt)) < 1e-13
+    assert abs(mm["t"] - 9 * dt) < 1e-13 and mm["hubble_violation"] == 0.0
+    lat.close()
+
+
+def test_fluid_background_rejects_leapfrog_and_bad_w():
+    for integ, w in (("lf", 0.0), ("vv2", -2.0)):
+        model = cl.make_model(n_fields=1, pexp=2, background=cl.CL_BG_FLUID, fluid_w=w, hubble0=0.5)
+        with pytest.raises(cl.LatticeError):
+            cl.Lattice(model, cl.make_grid(16, 0.5, 0.01, integ, cl.CL_FP64), cl.make_init())
