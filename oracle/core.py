@@ -34,6 +34,7 @@ def lib():
             ("orc_u1_lf_step", [vp, C.c_double, d, d, d, d, d, d, d, d], None),
             ("orc_u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
             ("orc_scalar_vv_step_fluid", [vp, vp, C.c_int, d, C.c_double, d, d, d], None),
+            ("orc_scalar_rk4_step", [vp, C.c_double, d, d, d, d], None),
         ]:
             f = getattr(_lib, name)
             f.argtypes = args
@@ -209,6 +210,17 @@ class ScalarLattice:
         self.t = t.value
         self.a = fluid.a(self.t)
         self.b = fluid.b(self.t)
+
+    def rk4_steps(self, dt, n=1):
+        """Explicit RK4 of section 4.3.1.  The scheme integrates the velocities
+        v = phi'; self.pi (Hamiltonian momenta a^{3-alpha} phi') is converted
+        to v before and back after the steps."""
+        v = np.ascontiguousarray(self.pi / self.a ** (3.0 - self.m.alpha))
+        a, b = C.c_double(self.a), C.c_double(self.b)
+        for _ in range(n):
+            lib().orc_scalar_rk4_step(self._mp(), dt, _p(self.phi), _p(v), C.byref(a), C.byref(b))
+        self.a, self.b = a.value, b.value
+        self.pi = v * self.a ** (3.0 - self.m.alpha)
 
     def lf3_prepare(self, dt):
         b = C.c_double(self.b)

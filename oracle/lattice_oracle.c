@@ -611,3 +611,93 @@ void orc_scalar_vv_step_fluid(const orc_scalar_model* m, const orc_fluid* f, int
     }
     free(K);
 }
+
+/* ----------------------------------------------------- explicit RK4 */
+
+/* Right-hand side of the scalar system in the form of the explicit
+ * Runge-Kutta scheme (section 4.3.1): velocities v = phi' (not the Hamiltonian
+ * momenta), k_i = a^{-2(1-alpha)} L[phi_i] - (3-alpha)(b/a) v_i - a^{2 alpha} dV/dphi_i
+ * and k_a = K_a[a, E_K, E_G, E_V] with E_K = sum_i <v_i^2>/(2 a^{2 alpha}). */
+static double rk4_rhs(const orc_scalar_model* m, const double* phi, const double* v, double a, double b,
+                      double* k) {
+    const int64_t N = m->N, V = N * N * N;
+    const double c1 = pow(a, -2.0 * (1.0 - m->alpha)), c2 = (3.0 - m->alpha) * b / a, c3 = pow(a, 2.0 * m->alpha);
+    const double idx2 = 1.0 / (m->dx * m->dx);
+    double sk = 0.0, sg = 0.0, sv = 0.0;
+#pragma omp parallel for reduction(+ : sk, sg, sv) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                const int64_t nb[6] = {site(N, wrap(x + 1, N), y, z), site(N, wrap(x - 1, N), y, z),
+                                       site(N, x, wrap(y + 1, N), z), site(N, x, wrap(y - 1, N), z),
+                                       site(N, x, y, wrap(z + 1, N)), site(N, x, y, wrap(z - 1, N))};
+                double dV[ORC_MAXF] = {0.0, 0.0}, v1 = 0.0, v2 = 0.0;
+                potential_gradient(m, phi[n], m->Ns > 1 ? phi[V + n] : 0.0, &dV[0], &dV[1]);
+                potential_terms(m, phi[n], m->Ns > 1 ? phi[V + n] : 0.0, &v1, &v2);
+                sv += v1 + v2;
+                for (int f = 0; f < m->Ns; ++f) {
+                    const double* p = phi + (int64_t)f * V;
+                    double lap = -6.0 * p[n];
+                    for (int j = 0; j < 6; ++j) lap += p[nb[j]];
+                    lap *= idx2;
+                    k[(int64_t)f * V + n] = c1 * lap - c2 * v[(int64_t)f * V + n] - c3 * dV[f];
+                    sk += v[(int64_t)f * V + n] * v[(int64_t)f * V + n];
+                    for (int j = 0; j < 6; j += 2) {
+                        const double g = p[nb[j]] - p[n];
+                        sg += g * g * idx2;
+                    }
+                }
+            }
+    const double EK = sk / V / (2.0 * pow(a, 2.0 * m->alpha)), EG = sg / V / (2.0 * a * a), EV = sv / V;
+    return m->fmp2 / 3.0 * pow(a, 1.0 + 2.0 * m->alpha) * ((m->alpha - 2.0) * EK + m->alpha * EG + (m->alpha + 1.0) * EV);
+}
+
+/* One step of the explicit RK4 of section 4.3.1 (Butcher weights
+ * b_21 = b_32 = 1/2, b_43 = 1 and 1/6, 1/3, 1/3, 1/6):
+ *   stage p = 1..4:  y^(p) = y(n0) + dt b_{p,p-1} d^(p-1)   (y^(1) = y(n0)),
+ *                    d^(p) = (v^(p), k^(p), b^(p), k_a^(p)) = derivatives of (phi, v, a, b) at y^(p),
+ *   y(n0 + 1) = y(n0) + dt/6 (d^(1) + 2 d^(2) + 2 d^(3) + d^(4)).
+ * phi and v (= phi', not the Hamiltonian momentum) are updated in place. */
+void orc_scalar_rk4_step(const orc_scalar_model* m, double dt, double* phi, double* v, double* a, double* b) {
+    const int64_t V = m->N * m->N * m->N, M = (int64_t)m->Ns * V;
+    double* ps = (double*)malloc(sizeof(double) * (size_t)M);
+    double* vs = (double*)malloc(sizeof(double) * (size_t)M);
+    double* k = (double*)malloc(sizeof(double) * (size_t)M);
+    double* acc_phi = (double*)malloc(sizeof(double) * (size_t)M);
+    double* acc_v = (double*)malloc(sizeof(double) * (size_t)M);
+    const double c[4] = {0.0, 0.5, 0.5, 1.0}, w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    memcpy(ps, phi, sizeof(double) * (size_t)M);
+    memcpy(vs, v, sizeof(double) * (size_t)M);
+    memcpy(acc_phi, phi, sizeof(double) * (size_t)M);
+    memcpy(acc_v, v, sizeof(double) * (size_t)M);
+    double ap = *a, bp = *b, ka = 0.0, acc_a = *a, acc_b = *b;
+    for (int p = 0; p < 4; ++p) {
+        if (p > 0) {
+            for (int64_t n = 0; n < M; ++n) {
+                const double vprev = vs[n];
+                ps[n] = phi[n] + c[p] * dt * vprev;
+                vs[n] = v[n] + c[p] * dt * k[n];
+            }
+            const double an = *a + c[p] * dt * bp, bn = *b + c[p] * dt * ka;
+            ap = an;
+            bp = bn;
+        }
+        ka = rk4_rhs(m, ps, vs, ap, bp, k);
+        for (int64_t n = 0; n < M; ++n) {
+            acc_phi[n] += w[p] * dt * vs[n];
+            acc_v[n] += w[p] * dt * k[n];
+        }
+        acc_a += w[p] * dt * bp;
+        acc_b += w[p] * dt * ka;
+    }
+    memcpy(phi, acc_phi, sizeof(double) * (size_t)M);
+    memcpy(v, acc_v, sizeof(double) * (size_t)M);
+    *a = acc_a;
+    *b = acc_b;
+    free(ps);
+    free(vs);
+    free(k);
+    free(acc_phi);
+    free(acc_v);
+}

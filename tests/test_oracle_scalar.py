@@ -312,3 +312,42 @@ def test_fluid_background_homogeneous_mode_matches_ode():
     lat.vv_steps_fluid(fl, oracle.VV4, 0.01, 400)
     assert abs(lat.phi[0, 0, 0, 0] - sol.y[0, -1]) < 1e-8
     assert abs(lat.pi[0, 0, 0, 0] - sol.y[1, -1]) < 1e-8
+
+
+def test_rk4_free_field_converges_to_exact_modes():
+    """Static background: each lattice mode of a free massive field is an
+    oscillator with w^2 = m^2 + sum_i 4 sin^2(pi n_i/N)/dx^2; the explicit RK4
+    of section 4.3.1 reaches the exact solution with a global O(dt^4) error."""
+    N, dx, m2, T = 8, 0.7, 0.5, 1.0
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=m2)
+    phi = inputs.fields(1, N, seed=13, amp=0.8)
+    pi = inputs.fields(1, N, seed=14, amp=0.5)
+    k = mode_numbers(N)
+    nz, ny, nx = np.meshgrid(k, k, k, indexing="ij")
+    w = np.sqrt(m2 + 4 * (np.sin(np.pi * nx / N) ** 2 + np.sin(np.pi * ny / N) ** 2 + np.sin(np.pi * nz / N) ** 2) / dx ** 2)
+    X0, P0 = dft_forward(phi[0]), dft_forward(pi[0])
+    phi_ex = dft_inverse(X0 * np.cos(w * T) + P0 / w * np.sin(w * T)).real
+    pi_ex = dft_inverse(-X0 * w * np.sin(w * T) + P0 * np.cos(w * T)).real
+    errs = []
+    for dt in (0.02, 0.01):
+        lat = ScalarLattice(m, phi, pi)
+        lat.rk4_steps(dt, int(round(T / dt)))
+        errs.append(max(np.max(np.abs(lat.phi[0] - phi_ex)), np.max(np.abs(lat.pi[0] - pi_ex))))
+    assert errs[1] < 1e-6, errs
+    assert 3.7 < np.log2(errs[0] / errs[1]) < 4.3, errs
+
+
+@pytest.mark.parametrize("pexp,alpha", [(2, 0.0), (4, 1.0)])
+def test_rk4_expanding_homogeneous_mode_matches_ode(pexp, alpha):
+    """RK4 with self-consistent expansion against the textbook Friedmann
+    system (DOP853): error O(dt^4) in phi and a."""
+    N, lam, fmp2, phi0, T = 2, 1.0, 1.5, 1.0, 4.0
+    m = ScalarModel(N=N, Ns=1, pexp=pexp, dx=1.0, alpha=alpha, fmp2=fmp2, lam=lam)
+    f_ref, a_ref, ad0 = _frw_reference(pexp, lam, fmp2, alpha, phi0, T)
+    errs = []
+    for dt in (0.04, 0.02):
+        lat = ScalarLattice(m, np.full((1, N, N, N), phi0), np.zeros((1, N, N, N)), a=1.0, b=ad0)
+        lat.rk4_steps(dt, int(round(T / dt)))
+        errs.append(max(abs(lat.phi[0, 0, 0, 0] - f_ref), abs(lat.a - a_ref) / a_ref))
+    assert errs[1] < 1e-7, errs
+    assert 3.6 < np.log2(errs[0] / errs[1]) < 4.4, errs
