@@ -64,14 +64,18 @@ typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1 } cl_model_kind;
  *             the compact staggered leapfrog of section 5.3.1 for U(1);
  * CL_INT_VV2  velocity-Verlet, section 4.2.3 (scalars) and 5.3.2 (compact U(1));
  * CL_INT_VV4..CL_INT_VV10  Yoshida compositions of VV2 (sections 4.3.2 and
- *             5.3.3, weights of the appendix table; VV4 in closed form). */
+ *             5.3.3, weights of the appendix table; VV4 in closed form);
+ * CL_INT_RK4  explicit fourth-order Runge-Kutta in the velocity form of
+ *             section 4.3.1 (scalar model, CL_FP64, self-consistent background;
+ *             not symplectic: the paper's reference for the others). */
 typedef enum {
     CL_INT_LF = 0,
     CL_INT_VV2 = 1,
     CL_INT_VV4 = 2,
     CL_INT_VV6 = 3,
     CL_INT_VV8 = 4,
-    CL_INT_VV10 = 5
+    CL_INT_VV10 = 5,
+    CL_INT_RK4 = 6
 } cl_integrator;
 
 typedef enum { CL_FP64 = 0, CL_FP32 = 1 } cl_precision;

@@ -41,6 +41,7 @@ struct DevState {
     double sums[kMaxSums];  // normalized sums of the last pass
     double hc;          // Hubble-constraint violation of the last synchronized point
     double gauss[3];    // <G^2>, <lhs^2>, <rhs^2> of the last Gauss check
+    double rk[4];       // RK4: a and b at the step's start, and their stage-weighted sums
     long long step;
     int error;          // nonzero: a reduction saw NaN/Inf (evolution stops)
     int staggered;      // leapfrog momenta live half a step behind the fields
@@ -125,6 +126,8 @@ struct Lattice {
     cudaStream_t cstream;  // private stream used only to record graphs
     bool staggered;        // host mirror of DevState::staggered
     bool shared_fft;       // plans and FFT scratch belong to an ensemble
+    void* rk_T1[4];        // RK4: second stage copy (the first is the spare ping-pong copy)
+    void* rk_A[4];         // RK4: accumulator
 };
 
 // cuFFT plans and FP64 scratch that the members of an ensemble of one lattice size share.
@@ -279,6 +282,9 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 cudaError_t scalar_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s);
 cudaError_t scalar_launch_drift(Lattice* L, int cur, cudaStream_t s);  // leapfrog closing drift (in place)
 void scalar_geometry(Lattice* L);
+
+// rk4.cu: m explicit RK4 steps of the state in copy `cur` (FP64 scalar model)
+cudaError_t rk4_enqueue(Lattice* L, long long m, int cur, cudaStream_t s);
 
 // u1_pass.cu
 cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s);

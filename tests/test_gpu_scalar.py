@@ -230,3 +230,55 @@ def test_fluid_background_rejects_leapfrog_and_bad_w():
         model = cl.make_model(n_fields=1, pexp=2, background=cl.CL_BG_FLUID, fluid_w=w, hubble0=0.5)
         with pytest.raises(cl.LatticeError):
             cl.Lattice(model, cl.make_grid(16, 0.5, 0.01, integ, cl.CL_FP64), cl.make_init())
+
+
+@pytest.mark.parametrize("N,alpha,pexp", [(24, 0.0, 2), (16, 1.0, 4)])
+def test_rk4_matches_oracle(N, alpha, pexp):
+    """Explicit RK4 of section 4.3.1 on the GPU (four stage passes per step,
+    full fields in FP64) against the oracle's RK4, 5 steps in two calls, with
+    self-consistent expansion."""
+    kIR, dt, fmp = 0.6, 0.01, 0.9
+    model = cl.make_model(n_fields=2, pexp=pexp, alpha=alpha, lam=1.0, q=20.0, omega_over_fstar=0.05,
+                          fstar_over_mp=fmp)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, "rk4", cl.CL_FP64), cl.make_init(phi0=(1.0, 0.0)))
+    om = ScalarModel(N=N, Ns=2, pexp=pexp, dx=2 * math.pi / (kIR * N), alpha=alpha, fmp2=fmp * fmp, lam=1.0, q=20.0)
+    phi = inputs.fields(2, N, seed=81, amp=0.05, kmax=4, means=[1.0, 0.0])
+    pi = inputs.fields(2, N, seed=82, amp=0.05, kmax=4)
+    for f in range(2):
+        lat.set_field(cl.FIELD(f), phi[f])
+        lat.set_field(cl.MOMENTUM(f), pi[f])
+    ref = ScalarLattice(om, phi, pi)
+    ref.b = math.sqrt(ref.hubble_rhs())
+    lat.set_background(1.0, ref.b, 0.0)
+    lat.evolve(2)
+    lat.evolve(3)
+    ref.rk4_steps(dt, 5)
+    gphi = np.stack([lat.get_field(cl.FIELD(f)) for f in range(2)])
+    gpi = np.stack([lat.get_field(cl.MOMENTUM(f)) for f in range(2)])
+    assert rel(gphi, ref.phi) < 1e-12
+    assert rel(gpi, ref.pi) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b) + 1e-14
+    assert abs(mm["t"] - 5 * dt) < 1e-13
+    lat.close()
+
+
+def test_rk4_hubble_constraint_order_four():
+    """The Hubble constraint of RK4 converges at fourth order in dt."""
+    vals = []
+    for dt in (0.02, 0.01):
+        model = cl.make_model(n_fields=1, pexp=4, alpha=1.0, lam=1.0, omega_over_fstar=0.01, fstar_over_mp=1.0)
+        lat = cl.Lattice(model, cl.make_grid(16, 0.5, dt, "rk4", cl.CL_FP64), cl.make_init(phi0=(1.0,), seed=3,
+                                                                                      fluct_scale=100.0))
+        lat.evolve(int(round(2.0 / dt)))
+        vals.append(lat.measure_means()["hubble_violation"])
+        lat.close()
+    assert 3.5 < math.log2(vals[0] / vals[1]) < 4.5, vals
+
+
+def test_rk4_rejects_fp32_and_fluid():
+    with pytest.raises(cl.LatticeError):
+        cl.Lattice(cl.make_model(n_fields=1), cl.make_grid(16, 0.5, 0.01, "rk4", cl.CL_FP32), cl.make_init())
+    with pytest.raises(cl.LatticeError):
+        cl.Lattice(cl.make_model(n_fields=1, background=cl.CL_BG_FLUID, hubble0=0.5),
+                   cl.make_grid(16, 0.5, 0.01, "rk4", cl.CL_FP64), cl.make_init())
