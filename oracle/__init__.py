@@ -9,7 +9,10 @@ What it computes (each function cites the passage it follows):
   core.py          ctypes front of lattice_oracle.c: scalar kernels, energies,
                    VV2/VVn (section 4.3.2), staggered leapfrog scheme III
                    (section 4.2.1), compact U(1) kernels, energies, Gauss law
-                   and staggered leapfrog (sections 5.3, 5.4)
+                   and staggered leapfrog (sections 5.3, 5.4), compact U(1) VVn
+                   (5.3.2, 5.3.3), prescribed fluid background (4.1), explicit
+                   RK4 (4.3.1), SU(2)-Higgs kernels, energies, Gauss law and
+                   VVn (section 6)
   ic.py            initial conditions of section 7
   spectra.py       DFT convention and power spectra (sections 3.1, 4.4.2)
   philox.py        Philox4x32-10, the counter-based generator of the draws
@@ -23,5 +26,5 @@ summation by parts, Parseval, the Gauss law to round-off, gauge invariance,
 energy conservation and Philox known-answer vectors.
 """
 from . import core, ic, mlp, philox, spectra  # noqa: F401
-from .core import (VV2, VV4, VV6, VV8, VV10, ScalarLattice, ScalarModel, U1Lattice,  # noqa: F401
-                   U1Model)
+from .core import (VV2, VV4, VV6, VV8, VV10, ScalarLattice, ScalarModel, SU2Lattice,  # noqa: F401
+                   SU2Model, U1Lattice, U1Model)

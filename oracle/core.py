@@ -35,6 +35,11 @@ def lib():
             ("orc_u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
             ("orc_scalar_vv_step_fluid", [vp, vp, C.c_int, d, C.c_double, d, d, d], None),
             ("orc_scalar_rk4_step", [vp, C.c_double, d, d, d, d], None),
+            ("orc_su2_kernels", [vp, d, d, C.c_double, d, d], None),
+            ("orc_su2_energies", [vp, d, d, d, d, C.c_double, d], None),
+            ("orc_su2_Ka", [vp, C.c_double, d], C.c_double),
+            ("orc_su2_gauss", [vp, d, d, d, d, d], None),
+            ("orc_su2_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
         ]:
             f = getattr(_lib, name)
             f.argtypes = args
@@ -306,3 +311,73 @@ class U1Lattice:
             lib().orc_u1_lf_step(self._mp(), dt, _p(self.phi), _p(self.pi), _p(self.theta), _p(self.piA),
                                  C.byref(a), C.byref(b), C.byref(ek), C.byref(eka))
         self.a, self.b, self.EKm = a.value, b.value, (ek.value, eka.value)
+
+
+class _SU2ModelC(C.Structure):
+    _fields_ = [("N", C.c_int64), ("dx", C.c_double), ("alpha", C.c_double), ("fmp2", C.c_double),
+                ("lam", C.c_double), ("v2", C.c_double), ("g", C.c_double), ("kappa", C.c_double)]
+
+
+@dataclass
+class SU2Model:
+    """Program-unit SU(2)-Higgs model of section 6: V = (lam/4)(|Phi|^2 - v2)^2,
+    gauge coupling g = g_B Q_B, kappa = (omega*/f*)^2."""
+    N: int
+    dx: float
+    alpha: float
+    fmp2: float
+    lam: float = 1.0
+    v2: float = 1.0
+    g: float = 1.0
+    kappa: float = 1.0
+
+    def c(self):
+        return _SU2ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.g, self.kappa)
+
+
+class SU2Lattice:
+    """SU(2) state: phi, pi of shape (4, N, N, N) (Re/Im of the two doublet
+    components), links u of shape (3, 4, N, N, N) (unit quaternions
+    q0 + i q.sigma), piB of shape (3, 3, N, N, N)."""
+
+    def __init__(self, model, phi, pi, u, piB, a=1.0, b=0.0):
+        N = model.N
+        self.m = model
+        self.phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(4, N, N, N).copy()
+        self.pi = np.ascontiguousarray(pi, dtype=np.float64).reshape(4, N, N, N).copy()
+        self.u = np.ascontiguousarray(u, dtype=np.float64).reshape(3, 4, N, N, N).copy()
+        self.piB = np.ascontiguousarray(piB, dtype=np.float64).reshape(3, 3, N, N, N).copy()
+        self.a, self.b = a, b
+
+    def _mp(self):
+        self._mc = self.m.c()
+        return C.byref(self._mc)
+
+    def kernels(self):
+        Kp = np.zeros_like(self.phi)
+        KB = np.zeros_like(self.piB)
+        lib().orc_su2_kernels(self._mp(), _p(self.phi), _p(self.u), self.a, _p(Kp), _p(KB))
+        return Kp, KB
+
+    def energies(self):
+        out = np.zeros(5)
+        lib().orc_su2_energies(self._mp(), _p(self.phi), _p(self.pi), _p(self.u), _p(self.piB), self.a, _p(out))
+        return out
+
+    def Ka(self):
+        E = np.ascontiguousarray(self.energies())
+        return lib().orc_su2_Ka(self._mp(), self.a, _p(E))
+
+    def gauss(self):
+        out = np.zeros(3)
+        lib().orc_su2_gauss(self._mp(), _p(self.phi), _p(self.pi), _p(self.u), _p(self.piB), _p(out))
+        return out[0] / max(out[1] + out[2], 1e-300)
+
+    def vv_steps(self, weights, dt, n=1):
+        """SU(2) velocity-Verlet VVn (sections 6.2.2, 6.2.3) on synchronized data."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        a, b = C.c_double(self.a), C.c_double(self.b)
+        for _ in range(n):
+            lib().orc_su2_vv_step(self._mp(), len(w), _p(w), dt, _p(self.phi), _p(self.pi), _p(self.u),
+                                  _p(self.piB), C.byref(a), C.byref(b))
+        self.a, self.b = a.value, b.value

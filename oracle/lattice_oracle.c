@@ -701,3 +701,280 @@ void orc_scalar_rk4_step(const orc_scalar_model* m, double dt, double* phi, doub
     free(acc_phi);
     free(acc_v);
 }
+
+/* ------------------------------------------------------------------- SU(2) */
+
+/* SU(2) sector with a Higgs doublet (section 6, compact formulation 6.2):
+ *   Phi = (Phi_1, Phi_2) complex, stored as phi[0..3] = (Re Phi_1, Im Phi_1, Re Phi_2, Im Phi_2);
+ *   pi = a^{3-alpha} Phi' in the same layout;
+ *   links U_i = exp(-i g dx B_i^a sigma^a/2) stored as unit quaternions
+ *     U = q0 + i (q1 sigma_1 + q2 sigma_2 + q3 sigma_3)  (SU(2) toolkit, section 3.2.3),
+ *     u[(i*4 + c)*V + n] = q_c of U_i(n);
+ *   piB_i^a = a^{1-alpha} G_0i^a, piB[(i*3 + a)*V + n].
+ * Energies (section 6.3.1), kappa = (w_star/f_star)^2, g = g_B Q_B:
+ *   E_K^Phi = <pi^dag pi>/a^6, E_G^Phi = sum_i <|D_i^+ Phi|^2>/a^2,
+ *   D_i^+ Phi = (U_i Phi(n+i) - Phi(n))/dx, E_V = <(lam/4)(|Phi|^2 - v2)^2>,
+ *   E_K^B = kappa/(2 a^4) sum_{a,i} <(piB_i^a)^2>,
+ *   E_G^B = 2 kappa/(a^4 dx^4 g^2) sum_{i<j} <2 - Tr U_ij>  (per plaquette; the
+ *           printed "2 - sum" is read as the sum over the three plaquettes of 2 - Tr),
+ *   U_ij(n) = U_i(n) U_j(n+i) U_i^dag(n+j) U_j^dag(n).
+ * Kernels: both follow from the Hamiltonian
+ *   H = a^{alpha-3} sum pi^dag pi + a^{alpha-1}/(2 kappa) sum (kappa piB)^2 + W,
+ *   W = a^{3+alpha} N^3 (E_G^Phi + E_V + E_G^B),
+ * with (B, kappa piB) canonical and B varied along U -> exp(-i g dx dB^a sigma^a/2) U:
+ *   K_Phi = -a^{3+alpha}(lam/2)(|Phi|^2 - v2) Phi + a^{1+alpha} sum_i (U_i Phi(n+i) - 2 Phi + U_i^dag(n-i) Phi(n-i))/dx^2,
+ *   K_B,i^a = a^{1+alpha} (g/(kappa dx)) Im[Phi^dag sigma^a U_i Phi(n+i)]
+ *           + a^{alpha-1} (2/(g dx^3)) sum_{j != i} (P_a[U_ij(n)] - P_a[U_j^dag(n-j) U_ij(n-j) U_j(n-j)]),
+ * P_a the sigma^a component q_a of a quaternion (the projection that the printed
+ * matrix form of the kernel leaves implicit).  Gauge invariance of H gives the
+ * discrete Gauss law (conserved exactly by kicks and exact drifts):
+ *   (1/dx) sum_i [piB_i(n) - U_i^dag(n-i) piB_i(n-i) U_i(n-i)]^a = (g/kappa) Im[Phi^dag sigma^a pi],
+ * the transported term being the adjoint action on piB_i = piB_i^a sigma^a. */
+typedef struct {
+    int64_t N;
+    double dx, alpha, fmp2, lam, v2, g, kappa;
+} orc_su2_model;
+
+static void qmul(const double* p, const double* q, double* r) {
+    /* (p0 + i p.s)(q0 + i q.s) = (p0 q0 - p.q) + i (p0 q + q0 p - p x q).s */
+    const double r0 = p[0] * q[0] - p[1] * q[1] - p[2] * q[2] - p[3] * q[3];
+    const double r1 = p[0] * q[1] + q[0] * p[1] - (p[2] * q[3] - p[3] * q[2]);
+    const double r2 = p[0] * q[2] + q[0] * p[2] - (p[3] * q[1] - p[1] * q[3]);
+    const double r3 = p[0] * q[3] + q[0] * p[3] - (p[1] * q[2] - p[2] * q[1]);
+    r[0] = r0; r[1] = r1; r[2] = r2; r[3] = r3;
+}
+static void qconj(const double* q, double* r) { r[0] = q[0]; r[1] = -q[1]; r[2] = -q[2]; r[3] = -q[3]; }
+
+/* U Phi with U = [[q0 + i q3, q2 + i q1], [-q2 + i q1, q0 - i q3]] acting on (Phi_1, Phi_2). */
+static void umul(const double* q, const double* f, double* o) {
+    const double ar = q[0], ai = q[3], br = q[2], bi = q[1], cr = -q[2], ci = q[1], dr = q[0], di = -q[3];
+    o[0] = ar * f[0] - ai * f[1] + br * f[2] - bi * f[3];
+    o[1] = ar * f[1] + ai * f[0] + br * f[3] + bi * f[2];
+    o[2] = cr * f[0] - ci * f[1] + dr * f[2] - di * f[3];
+    o[3] = cr * f[1] + ci * f[0] + dr * f[3] + di * f[2];
+}
+
+/* Im[x^dag sigma^a y] for doublets x, y, a = 1, 2, 3. */
+static void im_sigma(const double* x, const double* y, double* out) {
+    /* sigma_1 y = (y2, y1); sigma_2 y = (-i y2, i y1); sigma_3 y = (y1, -y2) */
+    /* x^dag z = conj(x1) z1 + conj(x2) z2; Im = x1r z1i - x1i z1r + x2r z2i - x2i z2r */
+    double z[4];
+    z[0] = y[2]; z[1] = y[3]; z[2] = y[0]; z[3] = y[1];
+    out[0] = x[0] * z[1] - x[1] * z[0] + x[2] * z[3] - x[3] * z[2];
+    z[0] = y[3]; z[1] = -y[2]; z[2] = -y[1]; z[3] = y[0];
+    out[1] = x[0] * z[1] - x[1] * z[0] + x[2] * z[3] - x[3] * z[2];
+    z[0] = y[0]; z[1] = y[1]; z[2] = -y[2]; z[3] = -y[3];
+    out[2] = x[0] * z[1] - x[1] * z[0] + x[2] * z[3] - x[3] * z[2];
+}
+
+static void getq(const double* u, int64_t V, int i, int64_t n, double* q) {
+    for (int c = 0; c < 4; ++c) q[c] = u[((int64_t)i * 4 + c) * V + n];
+}
+static void getf(const double* f, int64_t V, int64_t n, double* o) {
+    for (int c = 0; c < 4; ++c) o[c] = f[(int64_t)c * V + n];
+}
+static int64_t shift(int64_t N, int64_t x, int64_t y, int64_t z, int d, int s) {
+    int64_t c[3] = {x, y, z};
+    c[d] = wrap(c[d] + s, N);
+    return site(N, c[0], c[1], c[2]);
+}
+
+/* plaquette U_ij at site n (coordinates x, y, z) */
+static void plaquette(const orc_su2_model* m, const double* u, int i, int j, int64_t x, int64_t y, int64_t z,
+                      double* P) {
+    const int64_t N = m->N, V = N * N * N, n = site(N, x, y, z);
+    double Ui[4], Uj_i[4], Ui_j[4], Uj[4], t1[4], t2[4], c1[4], c2[4];
+    getq(u, V, i, n, Ui);
+    getq(u, V, j, shift(N, x, y, z, i, 1), Uj_i);
+    getq(u, V, i, shift(N, x, y, z, j, 1), Ui_j);
+    getq(u, V, j, n, Uj);
+    qconj(Ui_j, c1);
+    qconj(Uj, c2);
+    qmul(Ui, Uj_i, t1);
+    qmul(t1, c1, t2);
+    qmul(t2, c2, P);
+}
+
+void orc_su2_kernels(const orc_su2_model* m, const double* phi, const double* u, double a, double* Kp, double* KB) {
+    const int64_t N = m->N, V = N * N * N;
+    const double A1 = pow(a, 1.0 + m->alpha), A3 = pow(a, 3.0 + m->alpha), Am = pow(a, m->alpha - 1.0);
+    const double idx2 = 1.0 / (m->dx * m->dx);
+    const double cJ = m->g / (m->kappa * m->dx), cM = 2.0 / (m->g * m->dx * m->dx * m->dx);
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                double f[4], lap[4] = {0, 0, 0, 0};
+                getf(phi, V, n, f);
+                for (int c = 0; c < 4; ++c) lap[c] = -6.0 * f[c];
+                for (int i = 0; i < 3; ++i) {
+                    const int64_t np = shift(N, x, y, z, i, 1), nm = shift(N, x, y, z, i, -1);
+                    double q[4], qm[4], qmc[4], fp[4], fm[4], t[4], t2[4];
+                    getq(u, V, i, n, q);
+                    getq(u, V, i, nm, qm);
+                    qconj(qm, qmc);
+                    getf(phi, V, np, fp);
+                    getf(phi, V, nm, fm);
+                    umul(q, fp, t);
+                    umul(qmc, fm, t2);
+                    for (int c = 0; c < 4; ++c) lap[c] += t[c] + t2[c];
+                    /* current term of K_B,i */
+                    double js[3];
+                    im_sigma(f, t, js);
+                    /* magnetic term: plaquettes containing U_i(n) */
+                    double mag[3] = {0, 0, 0};
+                    for (int j = 0; j < 3; ++j) {
+                        if (j == i) continue;
+                        double P1[4], P2[4], Uj[4], Ujc[4], s1[4], Q[4];
+                        plaquette(m, u, i, j, x, y, z, P1);
+                        int64_t cm[3] = {x, y, z};
+                        cm[j] = wrap(cm[j] - 1, N);
+                        plaquette(m, u, i, j, cm[0], cm[1], cm[2], P2);
+                        getq(u, V, j, site(N, cm[0], cm[1], cm[2]), Uj);
+                        qconj(Uj, Ujc);
+                        qmul(Ujc, P2, s1);
+                        qmul(s1, Uj, Q);
+                        for (int c = 0; c < 3; ++c) mag[c] += P1[c + 1] - Q[c + 1];
+                    }
+                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];
+                }
+                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
+                const double dv = 0.5 * m->lam * (mod2 - m->v2);
+                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;
+            }
+}
+
+void orc_su2_energies(const orc_su2_model* m, const double* phi, const double* pi, const double* u,
+                      const double* piB, double a, double* out) {
+    const int64_t N = m->N, V = N * N * N;
+    double sk = 0, sg = 0, sv = 0, skb = 0, sgb = 0;
+#pragma omp parallel for reduction(+ : sk, sg, sv, skb, sgb) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                double f[4], p[4];
+                getf(phi, V, n, f);
+                getf(pi, V, n, p);
+                for (int c = 0; c < 4; ++c) sk += p[c] * p[c];
+                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
+                sv += 0.25 * m->lam * (mod2 - m->v2) * (mod2 - m->v2);
+                for (int i = 0; i < 3; ++i) {
+                    double q[4], fp[4], t[4];
+                    getq(u, V, i, n, q);
+                    getf(phi, V, shift(N, x, y, z, i, 1), fp);
+                    umul(q, fp, t);
+                    for (int c = 0; c < 4; ++c) sg += (t[c] - f[c]) * (t[c] - f[c]);
+                    for (int c = 0; c < 3; ++c) skb += piB[((int64_t)i * 3 + c) * V + n] * piB[((int64_t)i * 3 + c) * V + n];
+                    for (int j = i + 1; j < 3; ++j) {
+                        double P[4];
+                        plaquette(m, u, i, j, x, y, z, P);
+                        sgb += 2.0 - 2.0 * P[0];
+                    }
+                }
+            }
+    const double a2 = a * a, a4 = a2 * a2, a6 = a4 * a2, dx4 = m->dx * m->dx * m->dx * m->dx;
+    out[0] = sk / V / a6;
+    out[1] = sg / V / (m->dx * m->dx) / a2;
+    out[2] = sv / V;
+    out[3] = m->kappa * skb / V / (2.0 * a4);
+    out[4] = 2.0 * m->kappa * sgb / V / (a4 * dx4 * m->g * m->g);
+}
+
+static double Ka_su2(const orc_su2_model* m, double a, const double* E) {
+    return m->fmp2 / 3.0 * pow(a, 2.0 * m->alpha + 1.0) *
+           ((m->alpha - 2.0) * E[0] + m->alpha * E[1] + (m->alpha + 1.0) * E[2] + (m->alpha - 1.0) * (E[3] + E[4]));
+}
+
+double orc_su2_Ka(const orc_su2_model* m, double a, const double* E) { return Ka_su2(m, a, E); }
+
+/* Gauss residual: out = {<|G|^2>, <|lhs|^2>, <|rhs|^2>} summed over the three colours. */
+void orc_su2_gauss(const orc_su2_model* m, const double* phi, const double* pi, const double* u, const double* piB,
+                   double* out) {
+    const int64_t N = m->N, V = N * N * N;
+    double g2 = 0, l2 = 0, r2 = 0;
+#pragma omp parallel for reduction(+ : g2, l2, r2) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                double div[3] = {0, 0, 0};
+                for (int i = 0; i < 3; ++i) {
+                    const int64_t nm = shift(N, x, y, z, i, -1);
+                    double q[4], qc[4], e[4] = {0, 0, 0, 0}, t[4], tr[4];
+                    getq(u, V, i, nm, q);
+                    qconj(q, qc);
+                    for (int c = 0; c < 3; ++c) e[c + 1] = piB[((int64_t)i * 3 + c) * V + nm];
+                    qmul(qc, e, t);
+                    qmul(t, q, tr);
+                    for (int c = 0; c < 3; ++c) div[c] += (piB[((int64_t)i * 3 + c) * V + n] - tr[c + 1]) / m->dx;
+                }
+                double f[4], p[4], rho[3];
+                getf(phi, V, n, f);
+                getf(pi, V, n, p);
+                im_sigma(f, p, rho);
+                for (int c = 0; c < 3; ++c) {
+                    const double r = m->g / m->kappa * rho[c];
+                    g2 += (div[c] - r) * (div[c] - r);
+                    l2 += div[c] * div[c];
+                    r2 += r * r;
+                }
+            }
+    out[0] = g2 / V;
+    out[1] = l2 / V;
+    out[2] = r2 / V;
+}
+
+/* Link drift U_i <- exp(-i c piB_i^a sigma^a/2) U_i (the exact exponential of the
+ * momentum drift of section 6.2, unitary for any step): quaternion
+ * (cos(|c piB|/2), -sin(|c piB|/2) piB/|piB|) multiplied from the left. */
+static void su2_drift(const orc_su2_model* m, double* phi, const double* pi, double* u, const double* piB,
+                      double cphi, double cU) {
+    const int64_t V = m->N * m->N * m->N;
+    for (int64_t n = 0; n < 4 * V; ++n) phi[n] += cphi * pi[n];
+    for (int i = 0; i < 3; ++i)
+        for (int64_t n = 0; n < V; ++n) {
+            double e[3], q[4], r[4], ex[4];
+            for (int c = 0; c < 3; ++c) e[c] = cU * piB[((int64_t)i * 3 + c) * V + n];
+            const double th = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            const double s = th > 0 ? sin(0.5 * th) / th : 0.5;
+            ex[0] = cos(0.5 * th);
+            for (int c = 0; c < 3; ++c) ex[c + 1] = -s * e[c];
+            getq(u, V, i, n, q);
+            qmul(ex, q, r);
+            for (int c = 0; c < 4; ++c) u[((int64_t)i * 4 + c) * V + n] = r[c];
+        }
+}
+
+/* One full step of the SU(2) velocity-Verlet VVn (sections 6.2.2-6.2.3, the
+ * Yoshida composition of section 4.3.2): for each sub-step with h = w_p dt,
+ * half kicks of pi, piB and b with the kernels at the sub-step's start, a' = a + h b_1/2,
+ * drifts with a_1/2 = (a + a')/2 (phi += h pi/a_1/2^{3-alpha}; links by the exact
+ * exponential with c = g dx h/a_1/2^{1-alpha}), half kicks at the end and the closing
+ * half kick of b with the energies after the sub-step. */
+void orc_su2_vv_step(const orc_su2_model* m, int s, const double* w, double dt, double* phi, double* pi, double* u,
+                     double* piB, double* a, double* b) {
+    const int64_t V = m->N * m->N * m->N;
+    double* Kp = (double*)malloc(sizeof(double) * (size_t)(4 * V));
+    double* KB = (double*)malloc(sizeof(double) * (size_t)(9 * V));
+    double E[5];
+    orc_su2_energies(m, phi, pi, u, piB, *a, E);
+    for (int p = 0; p < s; ++p) {
+        const double h = w[p] * dt;
+        orc_su2_kernels(m, phi, u, *a, Kp, KB);
+        for (int64_t n = 0; n < 4 * V; ++n) pi[n] += 0.5 * h * Kp[n];
+        for (int64_t n = 0; n < 9 * V; ++n) piB[n] += 0.5 * h * KB[n];
+        const double bh = *b + 0.5 * h * Ka_su2(m, *a, E);
+        const double an = *a + h * bh, ah = 0.5 * (*a + an);
+        su2_drift(m, phi, pi, u, piB, h * pow(ah, -(3.0 - m->alpha)), m->g * m->dx * h * pow(ah, -(1.0 - m->alpha)));
+        *a = an;
+        orc_su2_kernels(m, phi, u, *a, Kp, KB);
+        for (int64_t n = 0; n < 4 * V; ++n) pi[n] += 0.5 * h * Kp[n];
+        for (int64_t n = 0; n < 9 * V; ++n) piB[n] += 0.5 * h * KB[n];
+        orc_su2_energies(m, phi, pi, u, piB, *a, E);
+        *b = bh + 0.5 * h * Ka_su2(m, *a, E);
+    }
+    free(Kp);
+    free(KB);
+}
