@@ -52,12 +52,19 @@ typedef enum {
 } cl_status;
 
 /* Model families.
+ * CL_MODEL_SU2: a complex doublet Phi = (Phi_1, Phi_2), stored as its four real
+ *   components (Re Phi_1, Im Phi_1, Re Phi_2, Im Phi_2) = CL_FIELD(0..3), with
+ *   V = (lam/4)(|Phi|^2 - vev2)^2, coupled with g = gauge_e to a compact SU(2)
+ *   gauge field in temporal gauge (section 6): links U_i = q0 + i q.sigma as unit
+ *   quaternions CL_SU2_LINK(i, c), electric momenta CL_SU2_EMOMENTUM(i, a).
+ *   It starts from a homogeneous doublet (init->spectrum = 0, zero charge)
+ *   with unit links; other states are loaded with lattice_set_field.
  * CL_MODEL_SCALAR: n_fields = 1 or 2 real singlets phi, chi with the program
  *   potential of section 8.1, V = (lam/p)|phi|^p + (q/2) phi^2 chi^2.
  * CL_MODEL_U1: one complex scalar phi = (phi_0 + i phi_1)/sqrt(2) with
  *   V = (lam/4)(|phi|^2 - vev2)^2, coupled with charge e to a compact U(1)
  *   gauge field in temporal gauge (section 5.3). */
-typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1 } cl_model_kind;
+typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1, CL_MODEL_SU2 = 2 } cl_model_kind;
 
 /* Integrators (the paper's "switch", section 1.2):
  * CL_INT_LF   staggered leapfrog: scheme III of section 4.2.1 for scalars,
@@ -195,6 +202,8 @@ cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, d
 #define CL_MOMENTUM(i) (4 + (i))
 #define CL_LINK(i) (8 + (i))
 #define CL_EMOMENTUM(i) (12 + (i))
+#define CL_SU2_LINK(i, c) (16 + 4 * (i) + (c))     /* quaternion component c of U_i */
+#define CL_SU2_EMOMENTUM(i, a) (28 + 3 * (i) + (a)) /* piB_i^a */
 
 /* Copy the full array `which` (N^3 doubles) to dst: host memory when
  * on_device = 0, device memory of the handle's device otherwise.

@@ -16,7 +16,7 @@ from . import build as _build
 # --- status codes and enums (mirror include/cl_lattice.h) ---
 CL_OK, CL_ERR_ARG, CL_ERR_CUDA, CL_ERR_OOM, CL_ERR_UNSTABLE_DT, CL_ERR_NONFINITE, CL_ERR_TIMEOUT, \
     CL_ERR_STATE, CL_ERR_IO = range(9)
-CL_MODEL_SCALAR, CL_MODEL_U1 = 0, 1
+CL_MODEL_SCALAR, CL_MODEL_U1, CL_MODEL_SU2 = 0, 1, 2
 CL_INT_LF, CL_INT_VV2, CL_INT_VV4, CL_INT_VV6, CL_INT_VV8, CL_INT_VV10, CL_INT_RK4 = range(7)
 CL_FP64, CL_FP32 = 0, 1
 CL_BG_FRIEDMANN, CL_BG_FLUID = 0, 1
@@ -34,6 +34,14 @@ def MOMENTUM(i):
 
 def LINK(i):
     return 8 + i
+
+
+def SU2_LINK(i, c):
+    return 16 + 4 * i + c
+
+
+def SU2_EMOMENTUM(i, a):
+    return 28 + 3 * i + a
 
 
 def EMOMENTUM(i):

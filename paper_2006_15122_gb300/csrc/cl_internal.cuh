@@ -85,7 +85,7 @@ __host__ __device__ inline double bg_b(const ModelConst& mc, double t) {
 
 // Per-lattice device resources.
 struct Buffers {
-    void* f[2][16];    // ping-pong copies of every stored array (type T)
+    void* f[2][32];    // ping-pong copies of every stored array (type T)
     int narr;
     DevState* st;
     double* partials;  // per-block partial sums
@@ -291,6 +291,13 @@ cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, boo
 cudaError_t u1_launch_drift(Lattice* L, int cur, cudaStream_t s);
 cudaError_t u1_launch_gauss(Lattice* L, int cur, cudaStream_t s);
 void u1_geometry(Lattice* L);
+
+// su2_pass.cu
+cudaError_t su2_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s);
+cudaError_t su2_launch_drift(Lattice* L, int cur, cudaStream_t s);
+cudaError_t su2_launch_gauss(Lattice* L, int cur, cudaStream_t s);
+cudaError_t su2_fill(Lattice* L, const double* phi, const double* pi);
+void su2_geometry(Lattice* L);
 
 // ic.cu
 cl_status ic_generate(Lattice* L);

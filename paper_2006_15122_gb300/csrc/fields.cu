@@ -11,12 +11,21 @@
 
 namespace cl {
 
-int array_count(const ModelConst& mc) { return mc.kind == CL_MODEL_SCALAR ? 2 * mc.nf : 10; }
+int array_count(const ModelConst& mc) {
+    if (mc.kind == CL_MODEL_SCALAR) return 2 * mc.nf;
+    return mc.kind == CL_MODEL_SU2 ? 29 : 10;
+}
 
 int array_slot(const ModelConst& mc, int which) {
     if (mc.kind == CL_MODEL_SCALAR) {
         if (which >= 0 && which < mc.nf) return which;
         if (which >= 4 && which < 4 + mc.nf) return mc.nf + which - 4;
+        return -1;
+    }
+    if (mc.kind == CL_MODEL_SU2) {  // Phi 0-3, pi 4-7, links 16 + 4 i + c, piB 28 + 3 i + a
+        if (which >= 0 && which < 8) return which;
+        if (which >= 16 && which < 28) return which - 8;
+        if (which >= 28 && which < 37) return which - 8;
         return -1;
     }
     if (which == 0 || which == 1) return which;

@@ -205,6 +205,11 @@ cl_status ic_generate(Lattice* L) {
                 else store_real_kernel<double><<<grid, 256, 0, s>>>(L->work, (double*)dst, n, scale);
             }
         }
+    } else if (mc.kind == CL_MODEL_SU2) {
+        // SU(2): homogeneous doublet (stored components), unit links, zero electric field
+        double pb[4];
+        for (int c = 0; c < 4; ++c) pb[c] = pow(a, 3.0 - mc.alpha) * in.dphi0[c];
+        if (su2_fill(L, in.phi0, pb) != cudaSuccess) return CL_ERR_CUDA;
     } else {
         // U(1): components phi_0, phi_1 of phi = (phi_0 + i phi_1)/sqrt(2); no mean split
         const double pb[2] = {in.phi0[0], in.phi0[1]}, db[2] = {in.dphi0[0], in.dphi0[1]};

@@ -89,11 +89,14 @@ double stability_limit(const std::vector<double>& w) {
 
 cudaError_t launch_pass(cl::Lattice* L, int src, int dst, const cl::PassInfo& pi, bool write, cudaStream_t s) {
     if (L->mc.kind == CL_MODEL_SCALAR) return cl::scalar_launch_pass(L, src, dst, pi, write, s);
+    if (L->mc.kind == CL_MODEL_SU2) return cl::su2_launch_pass(L, src, dst, pi, write, s);
     return cl::u1_launch_pass(L, src, dst, pi, write, s);
 }
 
 cudaError_t launch_drift(cl::Lattice* L, int cur, cudaStream_t s) {
-    cudaError_t e = L->mc.kind == CL_MODEL_SCALAR ? cl::scalar_launch_drift(L, cur, s) : cl::u1_launch_drift(L, cur, s);
+    cudaError_t e = L->mc.kind == CL_MODEL_SCALAR ? cl::scalar_launch_drift(L, cur, s)
+                    : L->mc.kind == CL_MODEL_SU2  ? cl::su2_launch_drift(L, cur, s)
+                                                  : cl::u1_launch_drift(L, cur, s);
     if (e != cudaSuccess) return e;
     return cl::launch_finish_drift(L, s);
 }
@@ -238,7 +241,7 @@ cl_status lattice_destroy(cl_lattice* h) {
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     for (int c = 0; c < 2; ++c)
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < 32; ++i)
             if (h->buf.f[c][i]) cudaFree(h->buf.f[c][i]);
     for (int i = 0; i < 4; ++i) {
         if (h->rk_T1[i]) cudaFree(h->rk_T1[i]);
@@ -283,9 +286,20 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_RK4) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
         if (grid->integrator == CL_INT_RK4 && (grid->precision != CL_FP64 || model->background != CL_BG_FRIEDMANN))
             return fail(nullptr, CL_ERR_ARG, "RK4 runs in FP64 with the self-consistent background");
-    } else if (model->kind == CL_MODEL_U1) {
+    } else if (model->kind == CL_MODEL_U1 || model->kind == CL_MODEL_SU2) {
         if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_VV10) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
         if (!(model->gauge_e > 0)) return fail(nullptr, CL_ERR_ARG, "gauge_e must be positive");
+        if (model->kind == CL_MODEL_SU2) {
+            if (init->spectrum) return fail(nullptr, CL_ERR_ARG, "the SU(2) model starts from a homogeneous doublet (spectrum = 0)");
+            // a uniform charge Im[Phi^dag sigma^a pi] cannot satisfy the Gauss law on a periodic lattice
+            const double* f = init->phi0;
+            const double* p = init->dphi0;
+            const double q1 = f[0] * p[3] - f[1] * p[2] + f[2] * p[1] - f[3] * p[0];
+            const double q2 = -f[0] * p[2] - f[1] * p[3] + f[2] * p[0] + f[3] * p[1];
+            const double q3 = f[0] * p[1] - f[1] * p[0] - f[2] * p[3] + f[3] * p[2];
+            if (fabs(q1) + fabs(q2) + fabs(q3) > 1e-12 * (1.0 + fabs(f[0]) + fabs(f[1]) + fabs(f[2]) + fabs(f[3])))
+                return fail(nullptr, CL_ERR_ARG, "the homogeneous SU(2) charge Im[Phi^dag sigma^a Phi'] must vanish");
+        }
     } else {
         return fail(nullptr, CL_ERR_ARG, "unknown model kind");
     }
@@ -349,6 +363,10 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
             for (int i = 0; i < mc.pexp - 2; ++i) ap *= fabs(f0);
             m2 = std::max(fabs((mc.pexp - 1) * mc.lam * ap + (mc.nf > 1 ? mc.q * f1 * f1 : 0.0)),
                           mc.nf > 1 ? fabs(mc.q * f0 * f0) : 0.0);
+        } else if (mc.kind == CL_MODEL_SU2) {
+            double s2 = 0.0;
+            for (int c = 0; c < 4; ++c) s2 += init->phi0[c] * init->phi0[c];
+            m2 = fabs(0.5 * mc.lam * (s2 - mc.vev2)) + mc.lam * s2 + mc.e * mc.e * s2 / (2.0 * mc.kappa);
         } else {
             const double s2 = 0.5 * (init->phi0[0] * init->phi0[0] + init->phi0[1] * init->phi0[1]);
             m2 = fabs(0.5 * mc.lam * (s2 - mc.vev2)) + mc.lam * s2 + 2.0 * mc.e * mc.e * s2 / mc.kappa;
@@ -415,6 +433,7 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         cufftSetStream(L->plan_r2c, L->stream);
     }
     if (mc.kind == CL_MODEL_SCALAR) cl::scalar_geometry(L);
+    else if (mc.kind == CL_MODEL_SU2) cl::su2_geometry(L);
     else cl::u1_geometry(L);
 
     cl_status s = cl::ic_generate(L);
@@ -470,6 +489,7 @@ cl_status lattice_measure_means(cl_lattice* h, cl_means* out) {
     if (!h || !out) return fail(h, CL_ERR_ARG, "NULL argument");
     cudaError_t e = launch_pass(h, h->cur, 1 - h->cur, make_pass(cl::PK_MEASURE, h->grid.dt, 0, 0, 0, 0), false, h->stream);
     if (e == cudaSuccess && h->mc.kind == CL_MODEL_U1) e = cl::u1_launch_gauss(h, h->cur, h->stream);
+    if (e == cudaSuccess && h->mc.kind == CL_MODEL_SU2) e = cl::su2_launch_gauss(h, h->cur, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "measure pass");
     cl::DevState st;
     cl_status s = read_state(h, &st);
@@ -553,6 +573,9 @@ cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, d
     if (h->mc.kind == CL_MODEL_SCALAR) {
         if (field < 0 || field >= h->mc.nf) return fail(h, CL_ERR_ARG, "field index out of range");
         slots.push_back(what == 0 ? field : h->mc.nf + field);
+    } else if (h->mc.kind == CL_MODEL_SU2) {  // the doublet: spectra summed over its four components
+        if (field != 0) return fail(h, CL_ERR_ARG, "the SU(2) model has one doublet (index 0)");
+        for (int c = 0; c < 4; ++c) slots.push_back(what == 0 ? c : 4 + c);
     } else {
         if (field != 0) return fail(h, CL_ERR_ARG, "the U(1) model has one complex field (index 0)");
         slots.push_back(what == 0 ? 0 : 2);

@@ -1,0 +1,120 @@
+"""Parity of the CUDA SU(2)-Higgs path (through the C ABI) with the FP64
+oracle, and the discrete Gauss law to round-off (section 6)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2006_15122_gb300 as cl
+from oracle import SU2Model
+from tests.test_oracle_su2 import gauss_state, random_state
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(x, y):
+    return float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300))
+
+
+def gpu_su2(m, integ, prec, fmp=0.0):
+    model = cl.make_model(kind=cl.CL_MODEL_SU2, alpha=m.alpha, fstar_over_mp=fmp, omega_over_fstar=math.sqrt(m.kappa),
+                          lam=m.lam, vev2=m.v2, gauge_e=m.g)
+    kIR = 2 * math.pi / (m.N * m.dx)
+    return cl.Lattice(model, cl.make_grid(m.N, kIR, 0.04, integ, prec), cl.make_init(phi0=(0.5, 0.0, 0.0, 0.0), spectrum=0))
+
+
+def load(lat, ref):
+    for c in range(4):
+        lat.set_field(cl.FIELD(c), ref.phi[c])
+        lat.set_field(cl.MOMENTUM(c), ref.pi[c])
+    for i in range(3):
+        for c in range(4):
+            lat.set_field(cl.SU2_LINK(i, c), ref.u[i, c])
+        for a in range(3):
+            lat.set_field(cl.SU2_EMOMENTUM(i, a), ref.piB[i, a])
+    lat.set_background(ref.a, ref.b, 0.0)
+
+
+def fetch(lat, N):
+    phi = np.stack([lat.get_field(cl.FIELD(c)) for c in range(4)])
+    pi = np.stack([lat.get_field(cl.MOMENTUM(c)) for c in range(4)])
+    u = np.stack([np.stack([lat.get_field(cl.SU2_LINK(i, c)) for c in range(4)]) for i in range(3)])
+    piB = np.stack([np.stack([lat.get_field(cl.SU2_EMOMENTUM(i, a)) for a in range(3)]) for i in range(3)])
+    return phi, pi, u, piB
+
+
+@pytest.mark.parametrize("integ,fmp,alpha", [("vv2", 0.0, 0.0), ("vv4", 0.7, 0.5)])
+def test_su2_fp64_velocity_verlet_matches_oracle(integ, fmp, alpha):
+    N, dt = 8, 0.04
+    m = SU2Model(N=N, dx=0.6, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.8, g=0.9, kappa=1.21)
+    ref = random_state(N, m, 7)
+    if fmp > 0:
+        ref.b = math.sqrt(fmp * fmp / 3.0 * ref.energies().sum())
+    lat = gpu_su2(m, integ, cl.CL_FP64, fmp)
+    load(lat, ref)
+    lat.evolve(3)
+    lat.evolve(4)
+    ref.vv_steps({"vv2": oracle.VV2, "vv4": oracle.VV4}[integ], dt, 7)
+    phi, pi, u, piB = fetch(lat, N)
+    assert rel(phi, ref.phi) < 1e-12
+    assert rel(pi, ref.pi) < 1e-12
+    assert np.max(np.abs(u - ref.u)) < 1e-12
+    assert rel(piB, ref.piB) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 * (1 + abs(ref.b))
+    E = ref.energies()
+    got = [mm["EK"][0], mm["EG"][0], mm["EV"][0], mm["EK"][1], mm["EG"][1]]
+    assert np.allclose(got, E, rtol=1e-11, atol=1e-14), (got, E)
+    lat.close()
+
+
+def test_su2_leapfrog_equals_velocity_verlet_positions_static():
+    """Static background: the staggered leapfrog started by a half kick moves
+    fields and links exactly as VV2 does (oracle VV2 as reference)."""
+    N, dt, n = 8, 0.04, 9
+    m = SU2Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=1.1, kappa=0.9)
+    ref = random_state(N, m, 17)
+    lat = gpu_su2(m, "lf", cl.CL_FP64)
+    load(lat, ref)
+    lat.evolve(n)
+    ref.vv_steps(oracle.VV2, dt, n)
+    phi, _, u, _ = fetch(lat, N)
+    assert rel(phi, ref.phi) < 1e-12
+    assert np.max(np.abs(u - ref.u)) < 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(cl.CL_FP64, 1e-13), (cl.CL_FP32, 1e-5)])
+def test_su2_gauss_law_is_preserved(prec, tol):
+    N = 16
+    m = SU2Model(N=N, dx=0.5, alpha=0.5, fmp2=0.36, lam=1.0, v2=1.0, g=1.1, kappa=0.9)
+    ref = gauss_state(N, m, 23)
+    ref.b = math.sqrt(0.36 / 3.0 * ref.energies().sum())
+    lat = gpu_su2(m, "vv4", prec, 0.6)
+    load(lat, ref)
+    g = [lat.measure_means()["gauss_violation"]]
+    for _ in range(4):
+        lat.evolve(10)
+        g.append(lat.measure_means()["gauss_violation"])
+    assert max(g) < tol, g
+    u = np.stack([lat.get_field(cl.SU2_LINK(i, c)) for i in range(3) for c in range(1, 4)])
+    assert np.max(np.abs(u)) > 1e-3  # the links moved off the identity
+    lat.close()
+
+
+def test_su2_homogeneous_start_and_refusals():
+    m = SU2Model(N=16, dx=0.5, alpha=0.0, fmp2=0.0)
+    lat = gpu_su2(m, "vv2", cl.CL_FP64)
+    assert np.all(lat.get_field(cl.FIELD(0)) == 0.5) and np.all(lat.get_field(cl.SU2_LINK(1, 0)) == 1.0)
+    mm = lat.measure_means()
+    assert mm["gauss_violation"] == 0.0 and mm["EG"][1] == 0.0
+    lat.evolve(5)
+    assert np.allclose(lat.get_field(cl.FIELD(0)), lat.get_field(cl.FIELD(0)).mean(), rtol=0, atol=1e-14)
+    lat.close()
+    model = cl.make_model(kind=cl.CL_MODEL_SU2, gauge_e=1.0)
+    with pytest.raises(cl.LatticeError):  # vacuum fluctuations are not drawn for SU(2)
+        cl.Lattice(model, cl.make_grid(16, 0.5, 0.04, "vv2", cl.CL_FP64), cl.make_init(spectrum=1))
+    with pytest.raises(cl.LatticeError):  # a uniform charge violates the Gauss law
+        cl.Lattice(model, cl.make_grid(16, 0.5, 0.04, "vv2", cl.CL_FP64),
+                   cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), dphi0=(0.0, 0.0, 0.0, 1.0), spectrum=0))
