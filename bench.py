@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-scan", action="store_true", help="leave the ensemble scan out of the default line")
+    p.add_argument("--no-gauge", action="store_true", help="leave the U(1) / SU(2) pass timings out")
     p.add_argument("--scan", action="store_true",
                    help="time the batched ensemble + surrogate parameter scan instead of the single lattice")
     p.add_argument("--scan-runs", type=int, default=512)
@@ -284,6 +285,47 @@ def scan_measurement(args, stream):
     return line
 
 
+def gauge_measurement(kind, N, steps, stream):
+    """Event-timed passes of the gauge sectors on a lattice of the same shape as
+    their workloads (FP32): the compact U(1) staggered leapfrog (lam = e = v = 1,
+    dx = 0.5, dt = 0.1 dx; one pass per step) and the SU(2)-Higgs VV2 (one
+    drift + kick per step).  Algorithmic bytes per site and pass: one read and
+    one write of every stored array, 10 arrays (U(1)) or 29 arrays (SU(2)) of
+    4 B."""
+    import torch
+
+    import paper_2006_15122_gb300 as cl
+
+    dx = 0.5
+    kIR = 2 * math.pi / (N * dx)
+    if kind == "u1":
+        model = cl.make_model(kind=cl.CL_MODEL_U1, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
+        init = cl.make_init(seed=7)
+        integ, narr, kernel = "lf", 10, "u1_pass_kernel<float>"
+    else:
+        model = cl.make_model(kind=cl.CL_MODEL_SU2, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
+        init = cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), spectrum=0)
+        integ, narr, kernel = "vv2", 29, "su2_drift_kernel<float> + su2_kick_kernel<float>"
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, 0.1 * dx, integ, cl.CL_FP32), init, stream=stream)
+    lat.evolve(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.evolve(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mm = lat.measure_means()
+    lat.close()
+    npass = steps + (1 if kind == "su2" else 0)
+    alg = 2 * narr * 4 * N ** 3
+    achieved = alg / (ms / 1e3 / npass) / 1e9
+    peak, _ = measured_peaks()
+    return {"N": N, "integrator": integ, "steps": steps, "ms_per_step": ms / steps, "kernel": kernel,
+            "bytes_per_pass": alg, "achieved_GBs": achieved, "frac": achieved / peak,
+            "site_updates_per_s": N ** 3 * steps / (ms / 1e3), "gauss_violation": mm["gauss_violation"]}
+
+
 def run_scan(args):
     import torch
 
@@ -369,6 +411,12 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(128)
+    gauge = None
+    if rank == 0 and not args.no_gauge:
+        try:
+            gauge = {"u1": gauge_measurement("u1", 256, 20, stream), "su2": gauge_measurement("su2", 128, 10, stream)}
+        except Exception as exc:
+            gauge = {"error_running": repr(exc)}
     ens = None
     if rank == 0 and not args.no_scan:
         if world > 1:
@@ -394,7 +442,7 @@ def main():
                          "launch_ms": ms / npass},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npass, "clocks": clk,
             "hubble_violation": mm["hubble_violation"], "a": mm["a"],
-            "ensemble_scan": ens,
+            "ensemble_scan": ens, "gauge_passes": gauge,
         }
         print(json.dumps(line), flush=True)
     if dist:

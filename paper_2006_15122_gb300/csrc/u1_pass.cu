@@ -48,7 +48,11 @@ template <typename T> __device__ __forceinline__ T wrap_angle(T t) {
     return t - twopi * rint(t / twopi);
 }
 template <typename T> __device__ __forceinline__ void sc(T x, T* s, T* c);
-template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+// FP32: the hardware approximation (the arguments are sums of at most four
+// wrapped angles, |x| <= 4 pi); every thread evaluates a shared plaquette from
+// the same inputs in the same order, so the cancellations behind the Gauss law
+// stay exact
+template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { __sincosf(x, s, c); }
 template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
 template <typename T>
@@ -121,8 +125,20 @@ __global__ void __launch_bounds__(256) u1_pass_kernel(const U1Args A) {
             grad += gr * gr + gi * gi;
             Kj[d] = cJ * (fr * ui - fi * ur);  // (2e/dx)(1/kappa) Im[phi* V_i phi(n+i)]
         }
-        // plaquettes
-        T mag[3] = {T(0), T(0), T(0)}, eB = T(0);
+        // plaquettes at n, one per unordered pair (theta_ji = -theta_ij): pairs (0,1), (0,2), (1,2)
+        T sp[3], eB = T(0);
+#pragma unroll
+        for (int pr_ = 0; pr_ < 3; ++pr_) {
+            const int ii = pr_ == 2 ? 1 : 0, jj = pr_ == 0 ? 1 : 2;
+            const int oix = ii == 0, oiy = ii == 1, oiz = ii == 2;
+            const int ojx = jj == 0, ojy = jj == 1, ojz = jj == 2;
+            const T pn = t0[ii] + th(jj, at(oix, oiy, oiz)) - th(ii, at(ojx, ojy, ojz)) - t0[jj];
+            T cn;
+            sc<T>(pn, &sp[pr_], &cn);
+            eB += T(1) - cn;
+        }
+        // forces: sum_j [Im V_ij(n) - Im V_ij(n-j)], Im V_ij = -sin(theta_ij)
+        T mag[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int ii = 0; ii < 3; ++ii) {
 #pragma unroll
@@ -130,16 +146,13 @@ __global__ void __launch_bounds__(256) u1_pass_kernel(const U1Args A) {
                 if (jj == ii) continue;
                 const int oix = ii == 0, oiy = ii == 1, oiz = ii == 2;
                 const int ojx = jj == 0, ojy = jj == 1, ojz = jj == 2;
-                // theta_ij(n) and theta_ij(n - j)
-                const T pn = t0[ii] + th(jj, at(oix, oiy, oiz)) - th(ii, at(ojx, ojy, ojz)) - t0[jj];
+                const int pr_ = ii + jj - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+                const T sn = ii < jj ? sp[pr_] : -sp[pr_];
                 const T pm = th(ii, at(-ojx, -ojy, -ojz)) + th(jj, at(oix - ojx, oiy - ojy, oiz - ojz)) - t0[ii] -
                              th(jj, at(-ojx, -ojy, -ojz));
-                T sn, cn, smm, cmm;
-                sc<T>(pn, &sn, &cn);
+                T smm, cmm;
                 sc<T>(pm, &smm, &cmm);
-                // Im V_ij = -sin(theta_ij)
                 mag[ii] += -sn + smm;
-                if (jj > ii) eB += T(1) - cn;
             }
         }
         const T mod2 = fr * fr + fi * fi;
