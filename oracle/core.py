@@ -35,6 +35,7 @@ def lib():
             ("orc_u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
             ("orc_scalar_vv_step_fluid", [vp, vp, C.c_int, d, C.c_double, d, d, d], None),
             ("orc_scalar_rk4_step", [vp, C.c_double, d, d, d, d], None),
+            ("orc_scalar_gl_step", [vp, C.c_int, d, d, C.c_double, C.c_double, C.c_int, d, d, d, d], C.c_int),
             ("orc_su2_kernels", [vp, d, d, C.c_double, d, d], None),
             ("orc_su2_energies", [vp, d, d, d, d, C.c_double, d], None),
             ("orc_su2_Ka", [vp, C.c_double, d], C.c_double),
@@ -101,6 +102,27 @@ class ScalarModel:
 
     def c(self):
         return _ScalarModelC(self.N, self.Ns, self.pexp, self.dx, self.alpha, self.fmp2, self.lam, self.q)
+
+
+def gl_tableau(s):
+    """Butcher tableau (A, c) of the s-stage Gauss-Legendre method from its
+    definition (section 3.4.2): collocation at the roots tau_i of the shifted
+    Legendre polynomial P_s(2 tau - 1), A_ij = int_0^{tau_i} l_j, c_j = int_0^1 l_j
+    with l_j the Lagrange basis on the nodes."""
+    x, _ = np.polynomial.legendre.leggauss(s)
+    tau = (x + 1.0) / 2.0
+    A = np.zeros((s, s))
+    c = np.zeros(s)
+    for j in range(s):
+        lj = np.poly1d([1.0])
+        for k in range(s):
+            if k != j:
+                lj = lj * np.poly1d([1.0, -tau[k]]) / (tau[j] - tau[k])
+        P = lj.integ()
+        c[j] = P(1.0) - P(0.0)
+        for i in range(s):
+            A[i, j] = P(tau[i]) - P(0.0)
+    return A, c
 
 
 class _FluidC(C.Structure):
@@ -226,6 +248,20 @@ class ScalarLattice:
             lib().orc_scalar_rk4_step(self._mp(), dt, _p(self.phi), _p(v), C.byref(a), C.byref(b))
         self.a, self.b = a.value, b.value
         self.pi = v * self.a ** (3.0 - self.m.alpha)
+
+    def gl_steps(self, s, dt, n=1, tol=1e-14, maxit=60):
+        """Gauss-Legendre implicit RK with s stages (order 2s; sections 3.4.2, 4.3.3,
+        Scheme II).  Returns the fixed-point sweeps of the last step."""
+        A, c = gl_tableau(s)
+        A = np.ascontiguousarray(A)
+        c = np.ascontiguousarray(c)
+        a, b = C.c_double(self.a), C.c_double(self.b)
+        it = 0
+        for _ in range(n):
+            it = lib().orc_scalar_gl_step(self._mp(), s, _p(A), _p(c), dt, tol, maxit, _p(self.phi), _p(self.pi),
+                                          C.byref(a), C.byref(b))
+        self.a, self.b = a.value, b.value
+        return it
 
     def lf3_prepare(self, dt):
         b = C.c_double(self.b)

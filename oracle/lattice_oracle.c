@@ -978,3 +978,81 @@ void orc_su2_vv_step(const orc_su2_model* m, int s, const double* w, double dt, 
     free(Kp);
     free(KB);
 }
+
+/* ------------------------------------------------ Gauss-Legendre (implicit RK) */
+
+/* One step of the s-stage Gauss-Legendre implicit Runge-Kutta method of
+ * sections 3.4.2 and 4.3.3 in Scheme II (Hamiltonian variables):
+ *   y = (phi, pi, a, b),  F(y) = (a^{-(3-alpha)} pi, K[a, phi], b, K_a[a, E(y)]),
+ *   Y^(l) = y(n0) + dt sum_m A_lm D^(m),  D^(l) = F(Y^(l)),
+ *   y(n0 + 1) = y(n0) + dt sum_m c_m D^(m),
+ * with the Butcher tableau (A, c) of order 2s.  The stage equations are solved
+ * by Jacobi fixed-point iteration from D = 0 (the first sweep gives F(y(n0))
+ * for every stage) until ||D_new - D_old||_2 <= tol ||D_new||_2 over all
+ * fields, stages and the two scalars, or maxit sweeps.  Returns the sweeps. */
+int orc_scalar_gl_step(const orc_scalar_model* m, int s, const double* A, const double* c, double dt, double tol,
+                       int maxit, double* phi, double* pi, double* a, double* b) {
+    const int64_t V = m->N * m->N * m->N, M = (int64_t)m->Ns * V;
+    double* D0 = (double*)calloc((size_t)(2 * s * M), sizeof(double)); /* stage l: dphi at 2lM, dpi at (2l+1)M */
+    double* D1 = (double*)calloc((size_t)(2 * s * M), sizeof(double));
+    double* ps = (double*)malloc(sizeof(double) * (size_t)M);
+    double* qs = (double*)malloc(sizeof(double) * (size_t)M);
+    double Da0[5] = {0}, Db0[5] = {0}, Da1[5] = {0}, Db1[5] = {0};
+    double* Dold = D0;
+    double* Dnew = D1;
+    double *Daold = Da0, *Dbold = Db0, *Danew = Da1, *Dbnew = Db1;
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+        double dd = 0.0, nn = 0.0;
+        for (int l = 0; l < s; ++l) {
+            double al = *a, bl = *b;
+            for (int mm = 0; mm < s; ++mm) {
+                al += dt * A[l * s + mm] * Daold[mm];
+                bl += dt * A[l * s + mm] * Dbold[mm];
+            }
+            for (int64_t n = 0; n < M; ++n) {
+                double x = phi[n], y = pi[n];
+                for (int mm = 0; mm < s; ++mm) {
+                    x += dt * A[l * s + mm] * Dold[(int64_t)(2 * mm) * M + n];
+                    y += dt * A[l * s + mm] * Dold[(int64_t)(2 * mm + 1) * M + n];
+                }
+                ps[n] = x;
+                qs[n] = y;
+            }
+            double* dphi = Dnew + (int64_t)(2 * l) * M;
+            double* dpi = Dnew + (int64_t)(2 * l + 1) * M;
+            orc_scalar_kernel(m, ps, al, dpi);
+            const double cdr = pow(al, -(3.0 - m->alpha));
+            for (int64_t n = 0; n < M; ++n) dphi[n] = cdr * qs[n];
+            double E[6];
+            orc_scalar_energies(m, ps, qs, al, E);
+            Danew[l] = bl;
+            Dbnew[l] = orc_scalar_Ka(m, al, E);
+            for (int64_t n = 0; n < M; ++n) {
+                const double e1 = dphi[n] - Dold[(int64_t)(2 * l) * M + n], e2 = dpi[n] - Dold[(int64_t)(2 * l + 1) * M + n];
+                dd += e1 * e1 + e2 * e2;
+                nn += dphi[n] * dphi[n] + dpi[n] * dpi[n];
+            }
+            dd += (Danew[l] - Daold[l]) * (Danew[l] - Daold[l]) + (Dbnew[l] - Dbold[l]) * (Dbnew[l] - Dbold[l]);
+            nn += Danew[l] * Danew[l] + Dbnew[l] * Dbnew[l];
+        }
+        double* t = Dold; Dold = Dnew; Dnew = t;
+        t = Daold; Daold = Danew; Danew = t;
+        t = Dbold; Dbold = Dbnew; Dbnew = t;
+        if (dd <= tol * tol * nn) break;
+    }
+    for (int64_t n = 0; n < M; ++n)
+        for (int mm = 0; mm < s; ++mm) {
+            phi[n] += dt * c[mm] * Dold[(int64_t)(2 * mm) * M + n];
+            pi[n] += dt * c[mm] * Dold[(int64_t)(2 * mm + 1) * M + n];
+        }
+    double da = 0.0, db = 0.0;
+    for (int mm = 0; mm < s; ++mm) {
+        da += dt * c[mm] * Daold[mm];
+        db += dt * c[mm] * Dbold[mm];
+    }
+    *a += da;
+    *b += db;
+    free(D0); free(D1); free(ps); free(qs);
+    return it > maxit ? maxit : it;
+}

@@ -351,3 +351,99 @@ def test_rk4_expanding_homogeneous_mode_matches_ode(pexp, alpha):
         errs.append(max(abs(lat.phi[0, 0, 0, 0] - f_ref), abs(lat.a - a_ref) / a_ref))
     assert errs[1] < 1e-7, errs
     assert 3.6 < np.log2(errs[0] / errs[1]) < 4.4, errs
+
+
+def _printed_tableaux():
+    """The paper's printed Gauss-Legendre tableaux (tests/golden), evaluated
+    with sqrt and the four operations only."""
+    import ast
+    import math
+    import os
+    import re
+
+    allowed = (ast.Expression, ast.BinOp, ast.UnaryOp, ast.Add, ast.Sub, ast.Mult, ast.Div, ast.USub, ast.Call,
+               ast.Name, ast.Load, ast.Constant)
+
+    def ev(expr, env):
+        tree = ast.parse(expr, mode="eval")
+        assert all(isinstance(n, allowed) for n in ast.walk(tree)), expr
+        return eval(compile(tree, "<tableau>", "eval"), {"__builtins__": {}}, dict(env, sqrt=math.sqrt))
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "gauss_legendre_tableaux.txt")
+    tabs, s, env = {}, None, {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        m = re.match(r"\[s=(\d)\]", line)
+        if m:
+            s, env = int(m.group(1)), {}
+            tabs[s] = {"A": [], "c": None}
+        elif line.startswith("def "):
+            name, expr = line[4:].split("=", 1)
+            env[name.strip()] = ev(expr.strip(), env)
+        elif line.startswith("row "):
+            tabs[s]["A"].append([ev(e.strip(), env) for e in line[4:].split(";")])
+        elif line.startswith("c "):
+            tabs[s]["c"] = [ev(e.strip(), env) for e in line[2:].split(";")]
+    return {k: (np.array(v["A"]), np.array(v["c"])) for k, v in tabs.items()}
+
+
+def _collocation_ok(A, c):
+    """Order conditions of the s-stage Gauss method: B(2s) sum_j c_j tau_j^(k-1) = 1/k
+    (k <= 2s) and C(s) sum_j A_ij tau_j^(k-1) = tau_i^k / k (k <= s), tau_i = row sums."""
+    s = len(c)
+    tau = A.sum(axis=1)
+    ok = all(abs((c * tau ** (k - 1)).sum() - 1.0 / k) < 1e-13 for k in range(1, 2 * s + 1))
+    return ok and all(np.max(np.abs(A @ tau ** (k - 1) - tau ** k / k)) < 1e-13 for k in range(1, s + 1))
+
+
+def test_gauss_legendre_tableaux_from_definition_match_printed_tables():
+    """The tableaux computed from the collocation definition equal the printed
+    ones for s = 2, 3, 4 and satisfy the order conditions for s = 2..5; the
+    printed s = 5 table violates them (misprints), so the definition is used."""
+    from oracle.core import gl_tableau
+    printed = _printed_tableaux()
+    for s in (2, 3, 4):
+        A, c = gl_tableau(s)
+        assert np.max(np.abs(A - printed[s][0])) < 1e-14 and np.max(np.abs(c - printed[s][1])) < 1e-14, s
+    for s in (2, 3, 4, 5):
+        assert _collocation_ok(*gl_tableau(s)), s
+    assert not _collocation_ok(*printed[5])
+    assert np.max(np.abs(gl_tableau(5)[1] - printed[5][1])) < 1e-14  # the printed weights are right
+
+
+@pytest.mark.parametrize("s,order", [(2, 4), (3, 6)])
+def test_gauss_legendre_free_field_converges_to_exact_modes(s, order):
+    """Static background: the s-stage Gauss-Legendre method reaches the exact
+    lattice modes with a global error O(dt^(2s))."""
+    N, dx, m2, T = 8, 0.7, 0.5, 1.0
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=m2)
+    phi = inputs.fields(1, N, seed=13, amp=0.8)
+    pi = inputs.fields(1, N, seed=14, amp=0.5)
+    k = mode_numbers(N)
+    nz, ny, nx = np.meshgrid(k, k, k, indexing="ij")
+    w = np.sqrt(m2 + 4 * (np.sin(np.pi * nx / N) ** 2 + np.sin(np.pi * ny / N) ** 2 + np.sin(np.pi * nz / N) ** 2) / dx ** 2)
+    X0, P0 = dft_forward(phi[0]), dft_forward(pi[0])
+    phi_ex = dft_inverse(X0 * np.cos(w * T) + P0 / w * np.sin(w * T)).real
+    errs = []
+    for dt in (0.1, 0.05):
+        lat = ScalarLattice(m, phi, pi)
+        lat.gl_steps(s, dt, int(round(T / dt)))
+        errs.append(np.max(np.abs(lat.phi[0] - phi_ex)))
+    assert abs(np.log2(errs[0] / errs[1]) - order) < 0.4, errs
+
+
+def test_gauss_legendre_expanding_homogeneous_mode_matches_ode():
+    """Two-stage Gauss-Legendre with self-consistent expansion against the
+    Friedmann system (DOP853): global order 4."""
+    N, lam, fmp2, phi0, T = 2, 1.0, 1.5, 1.0, 4.0
+    m = ScalarModel(N=N, Ns=1, pexp=4, dx=1.0, alpha=1.0, fmp2=fmp2, lam=lam)
+    f_ref, a_ref, ad0 = _frw_reference(4, lam, fmp2, 1.0, phi0, T)
+    errs = []
+    for dt in (0.08, 0.04):
+        lat = ScalarLattice(m, np.full((1, N, N, N), phi0), np.zeros((1, N, N, N)), a=1.0, b=ad0)
+        lat.gl_steps(2, dt, int(round(T / dt)))
+        errs.append(max(abs(lat.phi[0, 0, 0, 0] - f_ref), abs(lat.a - a_ref) / a_ref))
+    assert errs[1] < 1e-7, errs
+    assert 3.6 < np.log2(errs[0] / errs[1]) < 4.4, errs
