@@ -74,7 +74,11 @@ typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1, CL_MODEL_SU2 = 2 } cl_model
  *             5.3.3, weights of the appendix table; VV4 in closed form);
  * CL_INT_RK4  explicit fourth-order Runge-Kutta in the velocity form of
  *             section 4.3.1 (scalar model, CL_FP64, self-consistent background;
- *             not symplectic: the paper's reference for the others). */
+ *             not symplectic: the paper's reference for the others);
+ * CL_INT_GL2..CL_INT_GL5  implicit Gauss-Legendre Runge-Kutta with s = 2..5
+ *             stages, order 2s (sections 3.4.2, 4.3.3, Scheme II; same
+ *             restrictions as RK4; stages solved by fixed-point iteration to a
+ *             relative 1e-14). */
 typedef enum {
     CL_INT_LF = 0,
     CL_INT_VV2 = 1,
@@ -82,7 +86,11 @@ typedef enum {
     CL_INT_VV6 = 3,
     CL_INT_VV8 = 4,
     CL_INT_VV10 = 5,
-    CL_INT_RK4 = 6
+    CL_INT_RK4 = 6,
+    CL_INT_GL2 = 7,
+    CL_INT_GL3 = 8,
+    CL_INT_GL4 = 9,
+    CL_INT_GL5 = 10
 } cl_integrator;
 
 typedef enum { CL_FP64 = 0, CL_FP32 = 1 } cl_precision;

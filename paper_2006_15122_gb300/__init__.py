@@ -17,11 +17,13 @@ from . import build as _build
 CL_OK, CL_ERR_ARG, CL_ERR_CUDA, CL_ERR_OOM, CL_ERR_UNSTABLE_DT, CL_ERR_NONFINITE, CL_ERR_TIMEOUT, \
     CL_ERR_STATE, CL_ERR_IO = range(9)
 CL_MODEL_SCALAR, CL_MODEL_U1, CL_MODEL_SU2 = 0, 1, 2
-CL_INT_LF, CL_INT_VV2, CL_INT_VV4, CL_INT_VV6, CL_INT_VV8, CL_INT_VV10, CL_INT_RK4 = range(7)
+CL_INT_LF, CL_INT_VV2, CL_INT_VV4, CL_INT_VV6, CL_INT_VV8, CL_INT_VV10, CL_INT_RK4, CL_INT_GL2, CL_INT_GL3, \
+    CL_INT_GL4, CL_INT_GL5 = range(11)
 CL_FP64, CL_FP32 = 0, 1
 CL_BG_FRIEDMANN, CL_BG_FLUID = 0, 1
 INTEGRATORS = {"lf": CL_INT_LF, "vv2": CL_INT_VV2, "vv4": CL_INT_VV4, "vv6": CL_INT_VV6, "vv8": CL_INT_VV8,
-               "vv10": CL_INT_VV10, "rk4": CL_INT_RK4}
+               "vv10": CL_INT_VV10, "rk4": CL_INT_RK4, "gl2": CL_INT_GL2, "gl3": CL_INT_GL3, "gl4": CL_INT_GL4,
+               "gl5": CL_INT_GL5}
 
 
 def FIELD(i):

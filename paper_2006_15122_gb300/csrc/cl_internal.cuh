@@ -41,7 +41,9 @@ struct DevState {
     double sums[kMaxSums];  // normalized sums of the last pass
     double hc;          // Hubble-constraint violation of the last synchronized point
     double gauss[3];    // <G^2>, <lhs^2>, <rhs^2> of the last Gauss check
-    double rk[4];       // RK4: a and b at the step's start, and their stage-weighted sums
+    double rk[4];       // RK4 / Gauss-Legendre: a and b at the step's start (RK4: and their stage sums)
+    double gl_Da[2][5], gl_Db[2][5];  // Gauss-Legendre: scalar stage derivatives (two buffers)
+    int gl_cur, gl_conv, gl_it;       // latest buffer, converged flag, sweeps of this step
     long long step;
     int error;          // nonzero: a reduction saw NaN/Inf (evolution stops)
     int staggered;      // leapfrog momenta live half a step behind the fields
@@ -128,6 +130,7 @@ struct Lattice {
     bool shared_fft;       // plans and FFT scratch belong to an ensemble
     void* rk_T1[4];        // RK4: second stage copy (the first is the spare ping-pong copy)
     void* rk_A[4];         // RK4: accumulator
+    void* gl_D[2][5][4];   // Gauss-Legendre: stage derivatives, two buffers
 };
 
 // cuFFT plans and FP64 scratch that the members of an ensemble of one lattice size share.
@@ -285,6 +288,8 @@ void scalar_geometry(Lattice* L);
 
 // rk4.cu: m explicit RK4 steps of the state in copy `cur` (FP64 scalar model)
 cudaError_t rk4_enqueue(Lattice* L, long long m, int cur, cudaStream_t s);
+// gl.cu: m Gauss-Legendre steps of the state in copy `cur` (FP64 scalar model)
+cudaError_t gl_enqueue(Lattice* L, long long m, int cur, cudaStream_t s);
 
 // u1_pass.cu
 cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s);

@@ -117,6 +117,7 @@ cl::PassInfo make_pass(int kind, double dt, double wc, double wn, double h1, dou
 cudaError_t enqueue_steps(cl::Lattice* L, long long m, int* cur, cudaStream_t s) {
     const double dt = L->grid.dt;
     if (L->integ == CL_INT_RK4) return cl::rk4_enqueue(L, m, *cur, s);  // the state stays in copy `cur`
+    if (L->integ >= CL_INT_GL2) return cl::gl_enqueue(L, m, *cur, s);
     if (L->integ == CL_INT_LF) {
         for (long long j = 0; j < m; ++j) {
             cudaError_t e = launch_pass(L, *cur, 1 - *cur, make_pass(cl::PK_LF, dt, 0, 0, dt, dt), true, s);
@@ -246,6 +247,9 @@ cl_status lattice_destroy(cl_lattice* h) {
     for (int i = 0; i < 4; ++i) {
         if (h->rk_T1[i]) cudaFree(h->rk_T1[i]);
         if (h->rk_A[i]) cudaFree(h->rk_A[i]);
+        for (int b = 0; b < 2; ++b)
+            for (int l = 0; l < 5; ++l)
+                if (h->gl_D[b][l][i]) cudaFree(h->gl_D[b][l][i]);
     }
     if (h->buf.st) cudaFree(h->buf.st);
     if (h->buf.partials) cudaFree(h->buf.partials);
@@ -283,9 +287,9 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     if (model->kind == CL_MODEL_SCALAR) {
         if (model->n_fields < 1 || model->n_fields > 2) return fail(nullptr, CL_ERR_ARG, "n_fields must be 1 or 2");
         if (model->pexp != 2 && model->pexp != 4 && model->pexp != 6) return fail(nullptr, CL_ERR_ARG, "pexp must be 2, 4 or 6");
-        if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_RK4) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
-        if (grid->integrator == CL_INT_RK4 && (grid->precision != CL_FP64 || model->background != CL_BG_FRIEDMANN))
-            return fail(nullptr, CL_ERR_ARG, "RK4 runs in FP64 with the self-consistent background");
+        if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_GL5) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
+        if (grid->integrator >= CL_INT_RK4 && (grid->precision != CL_FP64 || model->background != CL_BG_FRIEDMANN))
+            return fail(nullptr, CL_ERR_ARG, "RK4 and Gauss-Legendre run in FP64 with the self-consistent background");
     } else if (model->kind == CL_MODEL_U1 || model->kind == CL_MODEL_SU2) {
         if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_VV10) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
         if (!(model->gauge_e > 0)) return fail(nullptr, CL_ERR_ARG, "gauge_e must be positive");
@@ -319,6 +323,7 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     memset(L->buf.f, 0, sizeof(L->buf.f));
     memset(L->rk_T1, 0, sizeof(L->rk_T1));
     memset(L->rk_A, 0, sizeof(L->rk_A));
+    memset(L->gl_D, 0, sizeof(L->gl_D));
     L->buf.st = nullptr; L->buf.partials = nullptr; L->buf.counter = nullptr;
     L->work = nullptr; L->cwork = nullptr; L->bins = nullptr; L->plans = false; L->cstream = nullptr;
     L->shared_fft = shared != nullptr;
@@ -373,7 +378,8 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         }
         const double w2 = pow(a, 2.0 * mc.alpha - 2.0) * 12.0 * mc.idx2 + pow(a, 2.0 * mc.alpha) * m2;
         // RK4: the stability interval of the oscillator on the imaginary axis is |w dt| < 2 sqrt(2)
-        const double lim = L->integ == CL_INT_RK4 ? 2.8 : stability_limit(L->weights);
+        // Gauss-Legendre is A-stable; the bound 2 keeps its fixed-point stage iteration contracting
+        const double lim = L->integ == CL_INT_RK4 ? 2.8 : (L->integ >= CL_INT_GL2 ? 2.0 : stability_limit(L->weights));
         if (!grid->force_dt && sqrt(w2) * grid->dt >= lim) {
             char msg[256];
             snprintf(msg, sizeof msg, "omega_max dt = %.4g exceeds the stability bound %.4g of this integrator",
@@ -394,6 +400,15 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
             e = cudaMalloc(&L->buf.f[c][i], n * L->tsize);
             if (e != cudaSuccess) { cl_status s = cuda_fail(nullptr, e, "allocating fields"); lattice_destroy(L); return s; }
         }
+    if (L->integ >= CL_INT_GL2)
+        for (int b = 0; b < 2; ++b)
+            for (int l = 0; l < L->integ - CL_INT_GL2 + 2; ++l)
+                for (int i = 0; i < L->buf.narr; ++i)
+                    if ((e = cudaMalloc(&L->gl_D[b][l][i], n * sizeof(double))) != cudaSuccess) {
+                        cl_status s = cuda_fail(nullptr, e, "allocating Gauss-Legendre stages");
+                        lattice_destroy(L);
+                        return s;
+                    }
     if (L->integ == CL_INT_RK4)
         for (int i = 0; i < L->buf.narr; ++i)
             if ((e = cudaMalloc(&L->rk_T1[i], n * sizeof(double))) != cudaSuccess ||

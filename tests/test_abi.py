@@ -71,7 +71,7 @@ def test_init_rejects_bad_arguments(bad):
     m = cl.make_model(n_fields=1, pexp=2)
     g = cl.make_grid(16, 0.5, 0.01)
     if bad == "integrator":
-        g.integrator = 9
+        g.integrator = 42
     if bad == "pexp":
         m.pexp = 3
     if bad == "fields":

@@ -282,3 +282,33 @@ def test_rk4_rejects_fp32_and_fluid():
     with pytest.raises(cl.LatticeError):
         cl.Lattice(cl.make_model(n_fields=1, background=cl.CL_BG_FLUID, hubble0=0.5),
                    cl.make_grid(16, 0.5, 0.01, "rk4", cl.CL_FP64), cl.make_init())
+
+
+@pytest.mark.parametrize("s,N", [(2, 16), (3, 24), (5, 8)])
+def test_gauss_legendre_matches_oracle(s, N):
+    """Implicit Gauss-Legendre (sections 3.4.2, 4.3.3) on the GPU: fixed-point
+    stage sweeps with a device-side convergence flag, against the oracle's
+    Gauss-Legendre step, 3 steps in two calls, self-consistent expansion."""
+    kIR, dt, fmp = 0.6, 0.02, 0.9
+    model = cl.make_model(n_fields=2, pexp=2, alpha=0.0, lam=1.0, q=20.0, omega_over_fstar=0.05, fstar_over_mp=fmp)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, "gl%d" % s, cl.CL_FP64), cl.make_init(phi0=(1.0, 0.0)))
+    om = ScalarModel(N=N, Ns=2, pexp=2, dx=2 * math.pi / (kIR * N), alpha=0.0, fmp2=fmp * fmp, lam=1.0, q=20.0)
+    phi = inputs.fields(2, N, seed=91, amp=0.05, kmax=N / 4, means=[1.0, 0.0])
+    pi = inputs.fields(2, N, seed=92, amp=0.05, kmax=N / 4)
+    for f in range(2):
+        lat.set_field(cl.FIELD(f), phi[f])
+        lat.set_field(cl.MOMENTUM(f), pi[f])
+    ref = ScalarLattice(om, phi, pi)
+    ref.b = math.sqrt(ref.hubble_rhs())
+    lat.set_background(1.0, ref.b, 0.0)
+    lat.evolve(1)
+    lat.evolve(2)
+    ref.gl_steps(s, dt, 3)
+    gphi = np.stack([lat.get_field(cl.FIELD(f)) for f in range(2)])
+    gpi = np.stack([lat.get_field(cl.MOMENTUM(f)) for f in range(2)])
+    assert rel(gphi, ref.phi) < 1e-12
+    assert rel(gpi, ref.pi) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
+    assert abs(mm["t"] - 3 * dt) < 1e-13
+    lat.close()
