@@ -164,3 +164,81 @@ def u1_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scal
         piA = np.stack([dft_inverse(np.where(den > 0, np.conj(bb) * R / den, 0.0)).real for bb in betas])
     theta = np.zeros((3, N, N, N))
     return phi, pi, theta, piA, dx
+
+
+def su2_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scale=1.0):
+    """Higgs doublet of the SU(2) sector with vacuum fluctuations and a
+    Gauss-consistent start (section 7 for the doublet, section 6 for the Gauss law).
+
+    phibar, dphibar: the four stored components (Re Phi_1, Im Phi_1, Re Phi_2,
+    Im Phi_2) of the homogeneous doublet and their program-time derivatives,
+    with zero homogeneous charge.  Each canonical real component
+    sqrt(2) Phi_c fluctuates like a real scalar (the singlet draws of
+    scalar_ic, Philox stream c) with curvature m_c^2 = (lam/2)(|Phi|^2 - v2) +
+    lam Phi_c^2.  The total colour charges Q^a = sum_n Im[Phi^dag sigma^a pi] are
+    then removed by pi -> pi - sum_a (Q^a / sum_n |Phi|^2) i sigma^a Phi (since
+    Im[Phi^dag sigma^a i sigma^b Phi] = delta_ab |Phi|^2), links start at unity and
+    piB solves sum_i D_i^- piB_i^a = (g/kappa) Im[Phi^dag sigma^a pi] colour by colour
+    in Fourier space.  Returns (phi (4,N,N,N), pi, u (3,4,N,N,N), piB (3,3,N,N,N), dx)."""
+    N = model.N
+    dx = 2.0 * np.pi / (kIR * N)
+    alpha = model.alpha
+    pb = [float(x) for x in phibar[:4]]
+    db = [float(x) for x in dphibar[:4]]
+    s2 = sum(x * x for x in pb)
+    m2 = [0.5 * model.lam * (s2 - model.v2) + model.lam * pb[c] ** 2 for c in range(4)]
+    Vbar = 0.25 * model.lam * (s2 - model.v2) ** 2
+    EK0 = sum(d * d for d in db) / a ** (2 * alpha)
+    H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    k = kIR * nabs
+    phi = np.zeros((4, N, N, N))
+    pi = np.zeros((4, N, N, N))
+    for c in range(4):
+        w = _omega(k, a, m2[c])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            T = np.where(zero, 0.0, (omega_over_fstar ** 2) * (N / dx) ** 3 / (2 * a * a * w))
+        T *= fluct_scale ** 2
+        u = philox.uniforms(lin, c, 0, seed)
+        L = np.sqrt(-T * np.log(u[0]))
+        R = np.sqrt(-T * np.log(u[1]))
+        el = np.exp(2j * np.pi * u[2])
+        er = np.exp(2j * np.pi * u[3])
+        G = (L * el + R * er) / np.sqrt(2.0)
+        Gd = a ** (alpha - 1.0) * (1j * w / np.sqrt(2.0)) * (L * el - R * er) - H * G
+        dphi = dft_inverse(_project(G, conj, selfc, zero)).real
+        ddphi = dft_inverse(_project(Gd, conj, selfc, zero)).real
+        phi[c] = pb[c] + dphi / np.sqrt(2.0)
+        pi[c] = a ** (3.0 - alpha) * (db[c] + ddphi / np.sqrt(2.0))
+    # remove the total colour charges
+    F1, F2 = phi[0] + 1j * phi[1], phi[2] + 1j * phi[3]
+    P1, P2 = pi[0] + 1j * pi[1], pi[2] + 1j * pi[3]
+    rho = _su2_charge(phi, pi)
+    cq = rho.sum(axis=(1, 2, 3)) / (phi ** 2).sum()
+    P1 = P1 - (cq[0] * 1j * F2 + cq[1] * F2 + cq[2] * 1j * F1)
+    P2 = P2 - (cq[0] * 1j * F1 - cq[1] * F1 - cq[2] * 1j * F2)
+    pi = np.stack([P1.real, P1.imag, P2.real, P2.imag])
+    rho = _su2_charge(phi, pi)
+    # Gauss law with unit links, colour by colour
+    m = mode_numbers(N)
+    nz, ny, nx = np.meshgrid(m, m, m, indexing="ij")
+    betas = [(1.0 - np.exp(2j * np.pi * cc / N)) / dx for cc in (nx, ny, nz)]
+    den = sum(np.abs(bb) ** 2 for bb in betas)
+    piB = np.zeros((3, 3, N, N, N))
+    for ca in range(3):
+        R = dft_forward(model.g / model.kappa * rho[ca])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            for i, bb in enumerate(betas):
+                piB[i, ca] = dft_inverse(np.where(den > 0, np.conj(bb) * R / den, 0.0)).real
+    u = np.zeros((3, 4, N, N, N))
+    u[:, 0] = 1.0
+    return phi, pi, u, piB, dx
+
+
+def _su2_charge(phi, pi):
+    """Im[Phi^dag sigma^a pi], a = 1..3, for doublets in the (Re, Im, Re, Im) layout."""
+    x1, x2 = phi[0] + 1j * phi[1], phi[2] + 1j * phi[3]
+    y1, y2 = pi[0] + 1j * pi[1], pi[2] + 1j * pi[3]
+    return np.stack([np.imag(np.conj(x1) * y2 + np.conj(x2) * y1),
+                     np.imag(np.conj(x1) * (-1j * y2) + np.conj(x2) * (1j * y1)),
+                     np.imag(np.conj(x1) * y1 - np.conj(x2) * y2)])

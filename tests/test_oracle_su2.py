@@ -213,3 +213,37 @@ def test_su2_energy_conservation_static():
         lat.vv_steps(VV4, dt, int(round(0.8 / dt)))
         drift.append(abs(lat.energies().sum() - E0) / E0)
     assert drift[1] < 1e-6 and np.log2(drift[0] / drift[1]) > 3.0, drift
+
+
+def test_su2_vacuum_initial_conditions_satisfy_the_gauss_law():
+    """The doublet's vacuum draw has no total colour charge after the projection,
+    the electric momenta solve the Gauss law with unit links to round-off, the
+    magnetic energy is exactly zero and each canonical component carries the
+    variance of a real scalar of its curvature (Rayleigh draws, section 7)."""
+    from oracle.ic import su2_ic
+    N, dx = 16, 0.5
+    m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=1.2, kappa=0.8)
+    phi, pi, u, piB, _ = su2_ic(m, 2 * np.pi / (N * dx), [0.4, 0.0, 0.0, 0.3], [0.0, 0.0, 0.0, 0.0], seed=3,
+                                omega_over_fstar=0.3)
+    lat = SU2Lattice(m, phi, pi, u, piB)
+    assert lat.gauss() < 1e-28
+    assert lat.energies()[4] == 0.0 and lat.energies()[3] > 0.0
+    assert abs(phi[0].mean() - 0.4) < 1e-12 and abs(phi[3].mean() - 0.3) < 1e-12
+    # vacuum fluctuations: a nonzero, finite spread in every component
+    assert np.all(phi.reshape(4, -1).std(axis=1) > 1e-4) and np.all(np.isfinite(pi))
+
+
+def test_su2_vacuum_component_is_a_scaled_singlet_draw():
+    """Component 0 of the doublet fluctuates exactly like the real scalar of
+    the same curvature drawn on the same Philox stream, divided by sqrt(2)
+    (canonical component sqrt(2) Phi_c)."""
+    from oracle import ScalarModel
+    from oracle.ic import scalar_ic, su2_ic
+    N, dx, lam, v2 = 8, 0.6, 1.3, 0.5
+    m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=lam, v2=v2, g=1.0, kappa=1.0)
+    kIR = 2 * np.pi / (N * dx)
+    phi, pi, _, _, _ = su2_ic(m, kIR, [0.0, 0.0, 0.0, 0.0], [0.0] * 4, seed=11, omega_over_fstar=0.2)
+    m2 = 0.5 * lam * (0.0 - v2)  # curvature of component 0 at Phi = 0 (tachyonic: |m^2| enters)
+    sm = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=m2)
+    sphi, spi, _ = scalar_ic(sm, kIR, [0.0], [0.0], seed=11, omega_over_fstar=0.2)
+    assert np.max(np.abs(phi[0] - sphi[0] / np.sqrt(2.0))) < 1e-15
