@@ -57,8 +57,10 @@ typedef enum {
  *   V = (lam/4)(|Phi|^2 - vev2)^2, coupled with g = gauge_e to a compact SU(2)
  *   gauge field in temporal gauge (section 6): links U_i = q0 + i q.sigma as unit
  *   quaternions CL_SU2_LINK(i, c), electric momenta CL_SU2_EMOMENTUM(i, a).
- *   It starts from a homogeneous doublet (init->spectrum = 0, zero charge)
- *   with unit links; other states are loaded with lattice_set_field.
+ *   It starts from a homogeneous, uncharged doublet with unit links, plus (with
+ *   init->spectrum) vacuum fluctuations of every canonical component sqrt(2) Phi_c,
+ *   the total colour charges projected out of pi, and electric momenta from
+ *   the Gauss law.
  * CL_MODEL_SCALAR: n_fields = 1 or 2 real singlets phi, chi with the program
  *   potential of section 8.1, V = (lam/p)|phi|^p + (q/2) phi^2 chi^2.
  * CL_MODEL_U1: one complex scalar phi = (phi_0 + i phi_1)/sqrt(2) with

@@ -111,6 +111,69 @@ __global__ void store_u1_kernel(const double* src, T* dst, size_t n, double scal
         dst[i] = T((src[i] * scale + add) * 0.70710678118654752);
 }
 
+// SU(2): Im[Phi^dag sigma^a pi] of the stored doublet components (a = 0..2)
+template <typename T>
+__device__ __forceinline__ double su2_rho(const T* const* b, size_t i, int a) {
+    const double f0 = b[0][i], f1 = b[1][i], f2 = b[2][i], f3 = b[3][i];
+    const double p0 = b[4][i], p1 = b[5][i], p2 = b[6][i], p3 = b[7][i];
+    if (a == 0) return f0 * p3 - f1 * p2 + f2 * p1 - f3 * p0;
+    if (a == 1) return -f0 * p2 - f1 * p3 + f2 * p0 + f3 * p1;
+    return f0 * p1 - f1 * p0 - f2 * p3 + f3 * p2;
+}
+
+struct Su2Ptrs {
+    void* b[8];  // Phi 0-3, pi 4-7
+};
+
+// per-block partial sums of the three colour charges and of |Phi|^2
+template <typename T>
+__global__ void su2_charge_sums_kernel(const Su2Ptrs P, size_t n, double* partials) {
+    const T* const* b = reinterpret_cast<const T* const*>(P.b);
+    double s[4] = {0, 0, 0, 0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) s[a] += su2_rho(b, i, a);
+        for (int c = 0; c < 4; ++c) s[3] += (double)b[c][i] * (double)b[c][i];
+    }
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(s[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
+    }
+}
+
+// pi <- pi - sum_a c_a i sigma^a Phi with c_a = Q_a / sum |Phi|^2 (fixed-order sum of the partials)
+template <typename T>
+__global__ void su2_uncharge_kernel(Su2Ptrs P, size_t n, const double* partials, int nblocks) {
+    T* const* b = reinterpret_cast<T* const*>(P.b);
+    double q[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nblocks; ++k)
+        for (int j = 0; j < 4; ++j) q[j] += partials[(size_t)k * 4 + j];
+    const double c0 = q[0] / q[3], c1 = q[1] / q[3], c2 = q[2] / q[3];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double f0 = b[0][i], f1 = b[1][i], f2 = b[2][i], f3 = b[3][i];
+        // i s1 Phi = (-f3, f2, -f1, f0), i s2 Phi = (f2, f3, -f0, -f1), i s3 Phi = (-f1, f0, f3, -f2)
+        b[4][i] = T((double)b[4][i] - (c0 * -f3 + c1 * f2 + c2 * -f1));
+        b[5][i] = T((double)b[5][i] - (c0 * f2 + c1 * f3 + c2 * f0));
+        b[6][i] = T((double)b[6][i] - (c0 * -f1 + c1 * -f0 + c2 * f3));
+        b[7][i] = T((double)b[7][i] - (c0 * f0 + c1 * -f1 + c2 * -f2));
+    }
+}
+
+// (g/kappa) Im[Phi^dag sigma^a pi] into a real FP64 array
+template <typename T>
+__global__ void su2_charge_kernel(const Su2Ptrs P, double* rho, size_t n, int a, double c) {
+    const T* const* b = reinterpret_cast<const T* const*>(P.b);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        rho[i] = c * su2_rho(b, i, a);
+}
+
 // charge density (2e/kappa) Im[phi* pi] into a real FP64 array
 template <typename T>
 __global__ void u1_charge_kernel(const T* pr, const T* pim, const T* qr, const T* qi, double* rho, size_t n, double c) {
@@ -206,10 +269,67 @@ cl_status ic_generate(Lattice* L) {
             }
         }
     } else if (mc.kind == CL_MODEL_SU2) {
-        // SU(2): homogeneous doublet (stored components), unit links, zero electric field
+        // SU(2): the homogeneous doublet (stored components), unit links, zero
+        // electric field; with a spectrum, every canonical component sqrt(2) Phi_c
+        // draws the singlet vacuum fluctuations of its curvature (stream c), the
+        // total colour charges are projected out of pi along i sigma^a Phi and the
+        // electric momenta solve the unit-link Gauss law colour by colour
         double pb[4];
         for (int c = 0; c < 4; ++c) pb[c] = pow(a, 3.0 - mc.alpha) * in.dphi0[c];
         if (su2_fill(L, in.phi0, pb) != cudaSuccess) return CL_ERR_CUDA;
+        if (in.spectrum) {
+            double s2 = 0.0, EK0 = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                s2 += in.phi0[c] * in.phi0[c];
+                EK0 += in.dphi0[c] * in.dphi0[c];
+            }
+            EK0 /= pow(a, 2.0 * mc.alpha);
+            const double Vb = 0.25 * mc.lam * (s2 - mc.vev2) * (s2 - mc.vev2);
+            const double H = sqrt(fmax(pow(a, 2.0 * mc.alpha) / 3.0 * mc.fmp2 * (EK0 + Vb), 0.0));
+            void** b = L->buf.f[L->cur];
+            for (int c = 0; c < 4; ++c) {
+                const double m2 = 0.5 * mc.lam * (s2 - mc.vev2) + mc.lam * in.phi0[c] * in.phi0[c];
+                for (int which = 0; which < 2; ++which) {
+                    ICParams P;
+                    P.N = N; P.stream = c; P.which = which; P.u1comp = -1;
+                    P.kIR = L->grid.kIR; P.a = a; P.alpha = mc.alpha; P.H = H;
+                    P.T0 = base; P.m2 = fabs(m2);
+                    P.k0 = (uint32_t)(in.seed & 0xffffffffu); P.k1 = (uint32_t)(in.seed >> 32);
+                    ic_modes_kernel<<<grid, 256, 0, s>>>((double2*)L->cwork, P);
+                    if (z2d(L) != cudaSuccess) return CL_ERR_CUDA;
+                    const double scale = (which == 0 ? 1.0 : pow(a, 3.0 - mc.alpha)) / (double)n;
+                    const double ad = 1.4142135623730951 * (which == 0 ? in.phi0[c] : pow(a, 3.0 - mc.alpha) * in.dphi0[c]);
+                    void* dst = b[which == 0 ? c : 4 + c];
+                    if (L->prec == CL_FP32) store_u1_kernel<float><<<grid, 256, 0, s>>>(L->work, (float*)dst, n, scale, ad);
+                    else store_u1_kernel<double><<<grid, 256, 0, s>>>(L->work, (double*)dst, n, scale, ad);
+                }
+            }
+            Su2Ptrs P;
+            for (int k = 0; k < 8; ++k) P.b[k] = b[k];
+            const int cg = L->sm_count * 4;
+            if (L->prec == CL_FP32) {
+                su2_charge_sums_kernel<float><<<cg, 256, 0, s>>>(P, n, L->buf.partials);
+                su2_uncharge_kernel<float><<<grid, 256, 0, s>>>(P, n, L->buf.partials, cg);
+            } else {
+                su2_charge_sums_kernel<double><<<cg, 256, 0, s>>>(P, n, L->buf.partials);
+                su2_uncharge_kernel<double><<<grid, 256, 0, s>>>(P, n, L->buf.partials, cg);
+            }
+            double2* Rk = (double2*)L->cwork;
+            const size_t nh = (size_t)N * N * (N / 2 + 1);
+            double2* Yk = Rk + nh;
+            for (int ca = 0; ca < 3; ++ca) {
+                if (L->prec == CL_FP32) su2_charge_kernel<float><<<grid, 256, 0, s>>>(P, L->work, n, ca, mc.e / mc.kappa);
+                else su2_charge_kernel<double><<<grid, 256, 0, s>>>(P, L->work, n, ca, mc.e / mc.kappa);
+                if (cufftExecD2Z(L->plan_r2c, L->work, (cufftDoubleComplex*)Rk) != CUFFT_SUCCESS) return CL_ERR_CUDA;
+                for (int i = 0; i < 3; ++i) {
+                    u1_gauss_solve_kernel<<<grid, 256, 0, s>>>(Rk, Yk, N, dx, i);
+                    if (cufftExecZ2D(L->plan_c2r, (cufftDoubleComplex*)Yk, L->work) != CUFFT_SUCCESS) return CL_ERR_CUDA;
+                    void* dst = b[20 + 3 * i + ca];
+                    if (L->prec == CL_FP32) store_real_kernel<float><<<grid, 256, 0, s>>>(L->work, (float*)dst, n, 1.0);
+                    else store_real_kernel<double><<<grid, 256, 0, s>>>(L->work, (double*)dst, n, 1.0);
+                }
+            }
+        }
     } else {
         // U(1): components phi_0, phi_1 of phi = (phi_0 + i phi_1)/sqrt(2); no mean split
         const double pb[2] = {in.phi0[0], in.phi0[1]}, db[2] = {in.dphi0[0], in.dphi0[1]};

@@ -294,7 +294,6 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_VV10) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
         if (!(model->gauge_e > 0)) return fail(nullptr, CL_ERR_ARG, "gauge_e must be positive");
         if (model->kind == CL_MODEL_SU2) {
-            if (init->spectrum) return fail(nullptr, CL_ERR_ARG, "the SU(2) model starts from a homogeneous doublet (spectrum = 0)");
             // a uniform charge Im[Phi^dag sigma^a pi] cannot satisfy the Gauss law on a periodic lattice
             const double* f = init->phi0;
             const double* p = init->dphi0;

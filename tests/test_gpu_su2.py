@@ -113,8 +113,32 @@ def test_su2_homogeneous_start_and_refusals():
     assert np.allclose(lat.get_field(cl.FIELD(0)), lat.get_field(cl.FIELD(0)).mean(), rtol=0, atol=1e-14)
     lat.close()
     model = cl.make_model(kind=cl.CL_MODEL_SU2, gauge_e=1.0)
-    with pytest.raises(cl.LatticeError):  # vacuum fluctuations are not drawn for SU(2)
-        cl.Lattice(model, cl.make_grid(16, 0.5, 0.04, "vv2", cl.CL_FP64), cl.make_init(spectrum=1))
     with pytest.raises(cl.LatticeError):  # a uniform charge violates the Gauss law
         cl.Lattice(model, cl.make_grid(16, 0.5, 0.04, "vv2", cl.CL_FP64),
                    cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), dphi0=(0.0, 0.0, 0.0, 1.0), spectrum=0))
+
+
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32])
+def test_su2_vacuum_initial_conditions_match_oracle(prec):
+    """lattice_init with vacuum fluctuations: the doublet, its momenta (with
+    the colour charges projected out) and the Gauss-consistent electric momenta
+    against the oracle's SU(2) initial conditions; Gauss law at round-off."""
+    from oracle.ic import su2_ic
+    N, dx, omega = 16, 0.5, 0.3
+    m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=1.2, kappa=omega * omega)
+    kIR = 2 * math.pi / (N * dx)
+    model = cl.make_model(kind=cl.CL_MODEL_SU2, omega_over_fstar=omega, lam=1.0, vev2=1.0, gauge_e=1.2)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, 0.04, "vv2", prec),
+                     cl.make_init(phi0=(0.4, 0.0, 0.0, 0.3), seed=5, spectrum=1))
+    phi, pi, u, piB, _ = su2_ic(m, kIR, [0.4, 0.0, 0.0, 0.3], [0.0] * 4, seed=5, omega_over_fstar=omega)
+    gphi, gpi, gu, gpiB = fetch(lat, N)
+    tol = 1e-12 if prec == cl.CL_FP64 else 2e-6
+    assert rel(gphi, phi) < tol and rel(gpi, pi) < tol, (rel(gphi, phi), rel(gpi, pi))
+    assert rel(gpiB, piB) < 10 * tol, rel(gpiB, piB)
+    assert np.all(gu[:, 0] == 1.0) and np.all(gu[:, 1:] == 0.0)
+    mm = lat.measure_means()
+    assert mm["gauss_violation"] < (1e-13 if prec == cl.CL_FP64 else 1e-5)
+    assert mm["EG"][1] == 0.0
+    lat.evolve(10)
+    assert lat.measure_means()["gauss_violation"] < (1e-13 if prec == cl.CL_FP64 else 1e-5)
+    lat.close()
