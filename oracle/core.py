@@ -60,7 +60,8 @@ class _ScalarModelC(C.Structure):
 
 class _U1ModelC(C.Structure):
     _fields_ = [("N", C.c_int64), ("dx", C.c_double), ("alpha", C.c_double), ("fmp2", C.c_double),
-                ("lam", C.c_double), ("v2", C.c_double), ("e", C.c_double), ("kappa", C.c_double)]
+                ("lam", C.c_double), ("v2", C.c_double), ("e", C.c_double), ("kappa", C.c_double),
+                ("pot", C.c_int32), ("p", C.c_int32)]
 
 
 # --- Yoshida weights (section 3.4.1 and the appendix table of VVn weights) ---
@@ -151,8 +152,9 @@ class Fluid:
 
 @dataclass
 class U1Model:
-    """Program-unit Abelian-Higgs model of section 5: V = (lam/4)(|phi|^2 - v2)^2,
-    gauge coupling e, kappa = (omega*/f*)^2."""
+    """Program-unit charged scalar of section 5 with V = (lam/4)(|phi|^2 - v2)^2
+    (Abelian-Higgs, pot = 0) or the monomial inflaton V = (lam/p)(2|phi|^2)^(p/2)
+    of section 8 (pot = 1); gauge coupling e, kappa = (omega*/f*)^2."""
     N: int
     dx: float
     alpha: float
@@ -161,9 +163,12 @@ class U1Model:
     v2: float = 1.0
     e: float = 1.0
     kappa: float = 1.0
+    pot: int = 0
+    p: int = 4
 
     def c(self):
-        return _U1ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.e, self.kappa)
+        return _U1ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.e, self.kappa, self.pot,
+                         self.p)
 
 
 def potential_terms(m, phi, chi=None):
@@ -351,13 +356,15 @@ class U1Lattice:
 
 class _SU2ModelC(C.Structure):
     _fields_ = [("N", C.c_int64), ("dx", C.c_double), ("alpha", C.c_double), ("fmp2", C.c_double),
-                ("lam", C.c_double), ("v2", C.c_double), ("g", C.c_double), ("kappa", C.c_double)]
+                ("lam", C.c_double), ("v2", C.c_double), ("g", C.c_double), ("kappa", C.c_double),
+                ("pot", C.c_int32), ("p", C.c_int32)]
 
 
 @dataclass
 class SU2Model:
-    """Program-unit SU(2)-Higgs model of section 6: V = (lam/4)(|Phi|^2 - v2)^2,
-    gauge coupling g = g_B Q_B, kappa = (omega*/f*)^2."""
+    """Program-unit SU(2)-Higgs model of section 6: V = (lam/4)(|Phi|^2 - v2)^2
+    (pot = 0) or the monomial inflaton (lam/p)(2|Phi|^2)^(p/2) of section 8
+    (pot = 1); gauge coupling g = g_B Q_B, kappa = (omega*/f*)^2."""
     N: int
     dx: float
     alpha: float
@@ -366,9 +373,12 @@ class SU2Model:
     v2: float = 1.0
     g: float = 1.0
     kappa: float = 1.0
+    pot: int = 0
+    p: int = 4
 
     def c(self):
-        return _SU2ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.g, self.kappa)
+        return _SU2ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.g, self.kappa, self.pot,
+                          self.p)
 
 
 class SU2Lattice:

@@ -289,10 +289,23 @@ void orc_scalar_lf3_step(const orc_scalar_model* m, double dt, double* phi, doub
 typedef struct {
     int64_t N;
     double dx, alpha, fmp2;
-    double lam, v2; /* V = (lam/4)(|phi|^2 - v2)^2 */
+    double lam, v2; /* V = (lam/4)(|phi|^2 - v2)^2, or the monomial inflaton below */
     double e;       /* gauge coupling g_A Q_A */
     double kappa;   /* (omega_star/f_star)^2 */
+    int32_t pot;    /* 0: Abelian-Higgs; 1: V = (lam/p)(2|phi|^2)^(p/2) (section 8.1 with |phi| -> sqrt(2)|phi|) */
+    int32_t p;
 } orc_u1_model;
+
+/* V(|phi|^2) of the charged scalar and V' = dV/d|phi|^2 (so that dV/dphi* = V' phi). */
+static double gauge_potential(int pot, int p, double lam, double v2, double mod2, double* dv) {
+    if (pot == 0) {
+        *dv = 0.5 * lam * (mod2 - v2);
+        return 0.25 * lam * (mod2 - v2) * (mod2 - v2);
+    }
+    const double s = 2.0 * mod2;
+    *dv = lam * pow(s, 0.5 * p - 1.0);
+    return lam / p * pow(s, 0.5 * p);
+}
 
 /* Plaquette angle theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n),
  * so that V_ij = V_i V_{j,+i} V*_{i,+j} V*_j = exp(-i theta_ij) (U(1) toolkit, section 3.2.2). */
@@ -357,7 +370,8 @@ void orc_u1_kernels(const orc_u1_model* m, const double* phi, const double* th, 
                         a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;
                 }
                 const double mod2 = pr[n] * pr[n] + pim[n] * pim[n];
-                const double dv = 0.5 * m->lam * (mod2 - m->v2);
+                double dv;
+                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);
                 Kphi[n] = -a3 * dv * pr[n] + a1 * lr / (dx * dx);
                 Kphi[V + n] = -a3 * dv * pim[n] + a1 * li / (dx * dx);
             }
@@ -381,7 +395,8 @@ void orc_u1_energies(const orc_u1_model* m, const double* phi, const double* pi,
                 const int64_t c[3] = {x, y, z};
                 sk += pi[n] * pi[n] + pi[V + n] * pi[V + n];
                 const double mod2 = pr[n] * pr[n] + pim[n] * pim[n];
-                sv += 0.25 * m->lam * (mod2 - m->v2) * (mod2 - m->v2);
+                double dv;
+                sv += gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);
                 for (int i = 0; i < 3; ++i) {
                     int64_t cp[3] = {x, y, z};
                     cp[i] = wrap(c[i] + 1, N);
@@ -733,6 +748,8 @@ void orc_scalar_rk4_step(const orc_scalar_model* m, double dt, double* phi, doub
 typedef struct {
     int64_t N;
     double dx, alpha, fmp2, lam, v2, g, kappa;
+    int32_t pot;  /* 0: (lam/4)(|Phi|^2 - v2)^2; 1: (lam/p)(2|Phi|^2)^(p/2) */
+    int32_t p;
 } orc_su2_model;
 
 static void qmul(const double* p, const double* q, double* r) {
@@ -840,7 +857,8 @@ void orc_su2_kernels(const orc_su2_model* m, const double* phi, const double* u,
                     for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];
                 }
                 const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
-                const double dv = 0.5 * m->lam * (mod2 - m->v2);
+                double dv;
+                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);
                 for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;
             }
 }
@@ -859,7 +877,8 @@ void orc_su2_energies(const orc_su2_model* m, const double* phi, const double* p
                 getf(pi, V, n, p);
                 for (int c = 0; c < 4; ++c) sk += p[c] * p[c];
                 const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
-                sv += 0.25 * m->lam * (mod2 - m->v2) * (mod2 - m->v2);
+                double dv;
+                sv += gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);
                 for (int i = 0; i < 3; ++i) {
                     double q[4], fp[4], t[4];
                     getq(u, V, i, n, q);

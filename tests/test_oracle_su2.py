@@ -89,13 +89,14 @@ def gauss_state(N, model, seed):
     return SU2Lattice(model, phi, pi, u, piB)
 
 
-@pytest.mark.parametrize("a,alpha", [(1.0, 0.0), (1.4, 0.5)])
-def test_su2_forces_are_minus_gradient_of_paper_energies(a, alpha):
+@pytest.mark.parametrize("a,alpha,pot", [(1.0, 0.0, 0), (1.4, 0.5, 0), (1.4, 0.5, 1)])
+def test_su2_forces_are_minus_gradient_of_paper_energies(a, alpha, pot):
     """W = a^{3+alpha} N^3 (E_G^Phi + E_V + E_G^B) from the energies of section
     6.3.1: K_Phi = -dW/dPhi* = -(1/2) dW/d(component), and K_B,i^a =
-    -(g dx/kappa) dW/d eps along U_i(n) -> exp(-i eps sigma^a/2) U_i(n)."""
+    -(g dx/kappa) dW/d eps along U_i(n) -> exp(-i eps sigma^a/2) U_i(n).
+    Both potentials: Higgs and the monomial inflaton (p = 4)."""
     N = 4
-    m = SU2Model(N=N, dx=0.6, alpha=alpha, fmp2=0.3, lam=1.3, v2=0.7, g=0.9, kappa=1.6)
+    m = SU2Model(N=N, dx=0.6, alpha=alpha, fmp2=0.3, lam=1.3, v2=0.7, g=0.9, kappa=1.6, pot=pot, p=4)
     lat = random_state(N, m, 5, a=a)
     Kp, KB = lat.kernels()
     scale = a ** (3 + alpha) * N ** 3

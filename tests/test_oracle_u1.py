@@ -17,13 +17,14 @@ def _random_state(N, seed, model, a=1.0):
     return U1Lattice(model, phi, pi, th, piA, a=a)
 
 
-@pytest.mark.parametrize("a,alpha", [(1.0, 0.0), (1.3, 0.5)])
-def test_u1_forces_are_minus_gradient_of_paper_energies(a, alpha):
+@pytest.mark.parametrize("a,alpha,pot,p", [(1.0, 0.0, 0, 4), (1.3, 0.5, 0, 4), (1.3, 0.5, 1, 4), (0.8, 1.0, 1, 6)])
+def test_u1_forces_are_minus_gradient_of_paper_energies(a, alpha, pot, p):
     """U = a^{3+alpha} N^3 (E_G^phi + E_V + E_G^A) from the energies of section
     5.4.1; then K_phi = -dU/dphi* = -(1/2)(dU/dRe + i dU/dIm) and
-    K_A,i = -(e dx/kappa) dU/dtheta_i (theta_i = e dx A_i)."""
+    K_A,i = -(e dx/kappa) dU/dtheta_i (theta_i = e dx A_i). Both potentials:
+    Abelian-Higgs and the monomial inflaton."""
     N = 5
-    m = U1Model(N=N, dx=0.55, alpha=alpha, fmp2=0.7, lam=1.3, v2=0.8, e=0.9, kappa=1.7)
+    m = U1Model(N=N, dx=0.55, alpha=alpha, fmp2=0.7, lam=1.3, v2=0.8, e=0.9, kappa=1.7, pot=pot, p=p)
     lat = _random_state(N, 7, m, a=a)
     Kp, KA = lat.kernels()
     scale = a ** (3 + alpha) * N ** 3
@@ -223,3 +224,30 @@ def test_u1_vv4_is_time_reversible_with_expansion():
     for x, y in zip((lat.phi, lat.pi, lat.theta, lat.piA), s0[:4]):
         assert np.max(np.abs(x - y)) < 1e-11
     assert abs(lat.a - s0[4]) < 1e-13 and abs(lat.b - s0[5]) < 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_u1_monomial_homogeneous_oscillation_period(p):
+    """A homogeneous real phi = chi/sqrt(2) in V = (lam/p)(2|phi|^2)^(p/2) with
+    a = 1 fixed obeys chi'' = -lam chi^(p-1): for p = 2 a harmonic oscillation
+    of period 2 pi/sqrt(lam); for p = 4 the quartic oscillator, whose period is
+    4 sqrt(2) I/(chi0 sqrt(lam)) with I = int_0^1 du/sqrt(1 - u^4) =
+    Gamma(1/4)^2/(4 sqrt(2 pi)). After one period the field is back at its
+    start (the oracle's VV10 at a fine step)."""
+    from math import gamma, pi, sqrt
+    from oracle import VV10
+    N, lam, chi0 = 4, 1.7, 1.3
+    m = U1Model(N=N, dx=0.5, alpha=0.0, fmp2=0.0, lam=lam, e=0.8, kappa=1.0, pot=1, p=p)
+    phi = np.zeros((2, N, N, N))
+    phi[0] = chi0 / sqrt(2.0)
+    lat = U1Lattice(m, phi, np.zeros_like(phi), np.zeros((3, N, N, N)), np.zeros((3, N, N, N)))
+    if p == 2:
+        T = 2 * pi / sqrt(lam)
+    else:
+        T = 4 * sqrt(2.0) * gamma(0.25) ** 2 / (4 * sqrt(2 * pi)) / (chi0 * sqrt(lam))
+    n = 400
+    lat.vv_steps(VV10, T / n, n // 2)
+    assert abs(lat.phi[0, 0, 0, 0] * sqrt(2.0) + chi0) < 1e-10  # half a period: -chi0
+    lat.vv_steps(VV10, T / n, n // 2)
+    assert np.max(np.abs(lat.phi[0] * sqrt(2.0) - chi0)) < 1e-10
+    assert np.max(np.abs(lat.phi[1])) == 0.0 and np.max(np.abs(lat.theta)) == 0.0
