@@ -57,6 +57,11 @@ def parse():
     p.add_argument("--scan-seeds", type=int, default=6)
     p.add_argument("--scan-plain", type=int, default=12)
     p.add_argument("--scan-epochs", type=int, default=400)
+    p.add_argument("--accuracy", action="store_true",
+                   help="print the Friedmann-constraint error of every integrator on the U(1) inflaton instead")
+    p.add_argument("--acc-N", type=int, default=64)
+    p.add_argument("--acc-eta", type=float, default=100.0)
+    p.add_argument("--acc-integrators", default="lf,vv2,vv4,vv6,vv8,vv10")
     return p.parse_args()
 
 
@@ -326,6 +331,78 @@ def gauge_measurement(kind, N, steps, stream):
             "site_updates_per_s": N ** 3 * steps / (ms / 1e3), "gauss_violation": mm["gauss_violation"]}
 
 
+def u1_inflaton_setup(p=4, M_over_mp=10.0, Lambda4_GeV4=4.3e65, qA=1.0e2):
+    """Program units of the U(1)-charged monomial inflaton (section 8): the
+    amplitude where slow roll ends, phi* = (M/2) asinh(sqrt(2) p m_p/M), sets
+    f* = phi*; omega* = Lambda^2 M^(-p/2) phi*^((p-2)/2) gives omega*/f* =
+    Lambda^2 M^(-p/2) phi*^((p-4)/2); alpha = 3(p-2)/(p+2); the program
+    potential is (1/p)(2|phi|^2)^(p/2) (lam = 1) and q_A* = e^2 f*^2/omega*^2 fixes
+    e.  The homogeneous start is |phi| = phi* split evenly over the two real
+    components, moving radially inwards at the slow-roll velocity
+    phi' = -V'/(3 H) with H^2 = (f*/m_p)^2 (phi'^2/2 + V)/3 (a = 1)."""
+    m_p = 2.435e18  # reduced Planck mass in GeV
+    M = M_over_mp * m_p
+    phis = 0.5 * M * math.asinh(math.sqrt(2.0) * p * m_p / M)
+    fmp = phis / m_p
+    om = math.sqrt(Lambda4_GeV4) * M ** (-p / 2) * phis ** ((p - 4) / 2)
+    e = math.sqrt(qA) * om
+    alpha = 3.0 * (p - 2) / (p + 2)
+    H = 0.0
+    v = 0.0
+    for _ in range(200):
+        H = math.sqrt(fmp * fmp / 3.0 * (0.5 * v * v + 1.0 / p))
+        v = 1.0 / (3.0 * H)
+    c = 1.0 / math.sqrt(2.0)
+    return {"p": p, "alpha": alpha, "fstar_over_mp": fmp, "omega_over_fstar": om, "gauge_e": e, "qA": qA,
+            "phi0": (c, c), "dphi0": (-v * c, -v * c), "H0": H}
+
+
+def accuracy_measurement(args, stream):
+    """Friedmann-constraint error Delta_e (section 8.2, accuracy tests) of every
+    integrator on the U(1)-charged p = 4 inflaton at k_IR = 0.6, dt = 0.01,
+    FP64, from one vacuum-fluctuation start; sampled every 5 program-time
+    units, with the device time of each run."""
+    import torch
+
+    import paper_2006_15122_gb300 as cl
+
+    st = u1_inflaton_setup()
+    N, kIR, dt = args.acc_N, 0.6, 0.01
+    nsteps = int(round(args.acc_eta / dt))
+    every = int(round(5.0 / dt))
+    out = {"model": "U(1) charged inflaton, V = (1/p)(2|phi|^2)^(p/2)", "setup": st, "N": N, "kIR": kIR, "dt": dt,
+           "eta_end": nsteps * dt, "precision": "f64", "runs": {}}
+    for integ in args.acc_integrators.split(","):
+        model = cl.make_model(kind=cl.CL_MODEL_U1, alpha=st["alpha"], fstar_over_mp=st["fstar_over_mp"],
+                              omega_over_fstar=st["omega_over_fstar"], lam=1.0, gauge_e=st["gauge_e"],
+                              potential=cl.CL_POT_MONOMIAL, pexp=st["p"])
+        lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, integ, cl.CL_FP64), cl.make_init(
+            phi0=st["phi0"], dphi0=st["dphi0"], seed=1, spectrum=1), stream=stream)
+        t, de, dg, a, eg = [], [], [], [], []
+        ms = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        done = 0
+        while done < nsteps:
+            k = min(every, nsteps - done)
+            e0.record(stream)
+            lat.evolve(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done += k
+            mm = lat.measure_means()
+            t.append(mm["t"])
+            de.append(mm["hubble_violation"])
+            dg.append(mm["gauss_violation"])
+            a.append(mm["a"])
+            eg.append((mm["EK"][1] + mm["EG"][1]) / mm["rho"])
+        lat.close()
+        out["runs"][integ] = {"t": t, "delta_e": de, "max_gauss_violation": max(dg), "a": a,
+                              "gauge_energy_fraction": eg, "device_ms": ms, "ms_per_step": ms / nsteps,
+                              "delta_e_end": de[-1], "delta_e_max": max(de)}
+    return out
+
+
 def run_scan(args):
     import torch
 
@@ -339,6 +416,11 @@ def main():
         return run_reference(args)
     if args.scan:
         return run_scan(args)
+    if args.accuracy:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(accuracy_measurement(args, torch.cuda.current_stream())), flush=True)
+        return
     import torch
 
     import paper_2006_15122_gb300 as cl

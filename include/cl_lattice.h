@@ -106,10 +106,18 @@ typedef enum { CL_FP64 = 0, CL_FP32 = 1 } cl_precision;
  *   velocity-Verlet integrators; the Hubble constraint is then reported as 0). */
 typedef enum { CL_BG_FRIEDMANN = 0, CL_BG_FLUID = 1 } cl_background;
 
+/* Potential of the charged scalar of CL_MODEL_U1 / CL_MODEL_SU2 (|phi|^2 is
+ * |phi|^2 for U(1) and Phi^dag Phi for SU(2)):
+ *   CL_POT_HIGGS     V = (lam/4)(|phi|^2 - vev2)^2 (sections 5, 6);
+ *   CL_POT_MONOMIAL  V = (lam/p)(2|phi|^2)^(p/2), p = pexp: the inflaton of the
+ *                    gauge working examples (section 8) as a charged field,
+ *                    2|phi|^2 being the squared canonical norm. */
+typedef enum { CL_POT_HIGGS = 0, CL_POT_MONOMIAL = 1 } cl_gauge_potential;
+
 typedef struct {
     int32_t kind;            /* cl_model_kind */
     int32_t n_fields;        /* CL_MODEL_SCALAR: 1 or 2; ignored for CL_MODEL_U1 */
-    int32_t pexp;            /* p of (lam/p)|phi|^p: 2, 4 or 6 (scalar) */
+    int32_t pexp;            /* p of (lam/p)|phi|^p (scalar) or of the monomial gauge potential: 2, 4 or 6 */
     int32_t background;      /* cl_background */
     double alpha;            /* alpha-time exponent (section 4.1) */
     double fstar_over_mp;    /* f_star/m_p; 0 selects a static background (a = 1, b = 0) */
@@ -120,6 +128,8 @@ typedef struct {
     double gauge_e;          /* U(1): gauge coupling e = g_A Q_A in program units */
     double fluid_w;          /* CL_BG_FLUID: equation of state w of the fluid */
     double hubble0;          /* CL_BG_FLUID: program Hubble rate a'/a at t = 0 */
+    int32_t potential;       /* U(1), SU(2): cl_gauge_potential */
+    int32_t reserved;        /* must be 0 */
 } cl_model;
 
 typedef struct {

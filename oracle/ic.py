@@ -119,6 +119,19 @@ def hubble_b(model, phi, pi, a, energies):
     return float(np.sqrt(max(model.fmp2 / 3.0 * a ** (2 * (model.alpha + 1)) * (E[0] + E[1] + E[2] + E[3] + E[4] + E[5]), 0.0)))
 
 
+def _charged_potential(model, mod2):
+    """V, dV/dmod2 and d^2V/dmod2^2 of a gauge model's charged scalar at
+    mod2 = |phi|^2: (lam/4)(mod2 - v2)^2 (sections 5, 6) or the monomial
+    (lam/p)(2 mod2)^(p/2) of section 8 (2 mod2 is the squared canonical norm).
+    Along a canonical real component chi the curvature is dV/dmod2 + chi^2 d^2V/dmod2^2."""
+    lam = model.lam
+    if getattr(model, "pot", 0) == 0:
+        return 0.25 * lam * (mod2 - model.v2) ** 2, 0.5 * lam * (mod2 - model.v2), 0.5 * lam
+    p, S = model.p, 2.0 * mod2
+    d2 = 0.0 if p == 2 else lam * (p - 2) * S ** (p / 2 - 2)
+    return lam / p * S ** (p / 2), lam * S ** (p / 2 - 1), d2
+
+
 def u1_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scale=1.0):
     """Complex scalar (2, N, N, N) as Re/Im planes, its momentum, links
     theta = 0 and Gauss-consistent electric momenta piA (3, N, N, N)."""
@@ -128,9 +141,8 @@ def u1_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scal
     pb = [float(phibar[0]), float(phibar[1])]
     db = [float(dphibar[0]), float(dphibar[1])]
     s = 0.5 * (pb[0] ** 2 + pb[1] ** 2)
-    m2 = [0.5 * model.lam * (s - model.v2) + 0.5 * model.lam * pb[n] ** 2 for n in range(2)]
-    mod2 = s
-    Vbar = 0.25 * model.lam * (mod2 - model.v2) ** 2
+    Vbar, dv, d2 = _charged_potential(model, s)
+    m2 = [dv + d2 * pb[n] ** 2 for n in range(2)]
     EK0 = 0.5 * (db[0] ** 2 + db[1] ** 2) / a ** (2 * alpha)
     H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
     lin, conj, selfc, zero, nabs = mode_map(N)
@@ -174,8 +186,8 @@ def su2_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_sca
     Im Phi_2) of the homogeneous doublet and their program-time derivatives,
     with zero homogeneous charge.  Each canonical real component
     sqrt(2) Phi_c fluctuates like a real scalar (the singlet draws of
-    scalar_ic, Philox stream c) with curvature m_c^2 = (lam/2)(|Phi|^2 - v2) +
-    lam Phi_c^2.  The total colour charges Q^a = sum_n Im[Phi^dag sigma^a pi] are
+    scalar_ic, Philox stream c) with the potential's curvature along that
+    component (Higgs: m_c^2 = (lam/2)(|Phi|^2 - v2) + lam Phi_c^2).  The total colour charges Q^a = sum_n Im[Phi^dag sigma^a pi] are
     then removed by pi -> pi - sum_a (Q^a / sum_n |Phi|^2) i sigma^a Phi (since
     Im[Phi^dag sigma^a i sigma^b Phi] = delta_ab |Phi|^2), links start at unity and
     piB solves sum_i D_i^- piB_i^a = (g/kappa) Im[Phi^dag sigma^a pi] colour by colour
@@ -186,8 +198,8 @@ def su2_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_sca
     pb = [float(x) for x in phibar[:4]]
     db = [float(x) for x in dphibar[:4]]
     s2 = sum(x * x for x in pb)
-    m2 = [0.5 * model.lam * (s2 - model.v2) + model.lam * pb[c] ** 2 for c in range(4)]
-    Vbar = 0.25 * model.lam * (s2 - model.v2) ** 2
+    Vbar, dv, d2 = _charged_potential(model, s2)
+    m2 = [dv + d2 * 2.0 * pb[c] ** 2 for c in range(4)]  # canonical component sqrt(2) Phi_c
     EK0 = sum(d * d for d in db) / a ** (2 * alpha)
     H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
     lin, conj, selfc, zero, nabs = mode_map(N)

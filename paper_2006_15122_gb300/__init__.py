@@ -21,6 +21,7 @@ CL_INT_LF, CL_INT_VV2, CL_INT_VV4, CL_INT_VV6, CL_INT_VV8, CL_INT_VV10, CL_INT_R
     CL_INT_GL4, CL_INT_GL5 = range(11)
 CL_FP64, CL_FP32 = 0, 1
 CL_BG_FRIEDMANN, CL_BG_FLUID = 0, 1
+CL_POT_HIGGS, CL_POT_MONOMIAL = 0, 1
 INTEGRATORS = {"lf": CL_INT_LF, "vv2": CL_INT_VV2, "vv4": CL_INT_VV4, "vv6": CL_INT_VV6, "vv8": CL_INT_VV8,
                "vv10": CL_INT_VV10, "rk4": CL_INT_RK4, "gl2": CL_INT_GL2, "gl3": CL_INT_GL3, "gl4": CL_INT_GL4,
                "gl5": CL_INT_GL5}
@@ -54,7 +55,7 @@ class cl_model(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_fields", C.c_int32), ("pexp", C.c_int32), ("background", C.c_int32),
                 ("alpha", C.c_double), ("fstar_over_mp", C.c_double), ("omega_over_fstar", C.c_double),
                 ("lam", C.c_double), ("q", C.c_double), ("vev2", C.c_double), ("gauge_e", C.c_double),
-                ("fluid_w", C.c_double), ("hubble0", C.c_double)]
+                ("fluid_w", C.c_double), ("hubble0", C.c_double), ("potential", C.c_int32), ("reserved", C.c_int32)]
 
 
 class cl_grid(C.Structure):
@@ -183,9 +184,10 @@ def _dev_ptr(t):
 
 
 def make_model(kind=CL_MODEL_SCALAR, n_fields=1, pexp=2, alpha=0.0, fstar_over_mp=0.0, omega_over_fstar=1.0,
-               lam=1.0, q=0.0, vev2=1.0, gauge_e=1.0, background=CL_BG_FRIEDMANN, fluid_w=0.0, hubble0=0.0):
+               lam=1.0, q=0.0, vev2=1.0, gauge_e=1.0, background=CL_BG_FRIEDMANN, fluid_w=0.0, hubble0=0.0,
+               potential=CL_POT_HIGGS):
     return cl_model(kind, n_fields, pexp, background, alpha, fstar_over_mp, omega_over_fstar, lam, q, vev2, gauge_e,
-                    fluid_w, hubble0)
+                    fluid_w, hubble0, potential, 0)
 
 
 def make_grid(N, kIR, dt, integrator=CL_INT_VV2, precision=CL_FP64, force_dt=False):

@@ -75,7 +75,42 @@ struct ModelConst {
     // prescribed background (section 4.1): a(t) = bg_a0 (1 + bg_H0 t / bg_p)^bg_p when bg != 0
     int bg;
     double bg_p, bg_H0, bg_a0;
+    int gpot;  // charged-scalar potential of the gauge models (cl_gauge_potential)
 };
+
+// Potential of the charged scalar of the gauge models as a function of
+// mod2 = |phi|^2 (U(1)) or Phi^dag Phi (SU(2)), with *dv = dV/d(mod2), so that
+// the force on phi is -dv phi: (lam/4)(mod2 - v2)^2 (sections 5, 6) or the
+// monomial (lam/p)(2 mod2)^(p/2) with p = 2, 4, 6 (section 8).
+template <class T>
+__host__ __device__ inline T gauge_pot(int gpot, int p, T lam, T v2, T mod2, T* dv) {
+    if (gpot == 0) {
+        *dv = T(0.5) * lam * (mod2 - v2);
+        return T(0.25) * lam * (mod2 - v2) * (mod2 - v2);
+    }
+    const T s = T(2) * mod2;
+    T sp = T(1);  // s^(p/2 - 1)
+    for (int k = 2; k < p; k += 2) sp *= s;
+    *dv = lam * sp;
+    return lam / T(p) * sp * s;
+}
+
+// d^2V/d(mod2)^2 of gauge_pot.
+inline double gauge_pot_d2(int gpot, int p, double lam, double mod2) {
+    if (gpot == 0) return 0.5 * lam;
+    double sp = 1.0;  // (2 mod2)^(p/2 - 2)
+    for (int k = 4; k < p; k += 2) sp *= 2.0 * mod2;
+    return p > 2 ? lam * (p - 2) * sp : 0.0;
+}
+
+// Curvature of the potential along a canonical real component chi of the
+// charged scalar (the squared canonical norm being 2 mod2):
+// dV/dmod2 + chi^2 d^2V/dmod2^2.
+inline double gauge_curvature(int gpot, int p, double lam, double v2, double mod2, double chi) {
+    double dv;
+    gauge_pot<double>(gpot, p, lam, v2, mod2, &dv);
+    return dv + chi * chi * gauge_pot_d2(gpot, p, lam, mod2);
+}
 
 // Scale factor and its program-time derivative of the prescribed background.
 __host__ __device__ inline double bg_a(const ModelConst& mc, double t) {

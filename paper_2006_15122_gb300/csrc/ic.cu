@@ -284,11 +284,12 @@ cl_status ic_generate(Lattice* L) {
                 EK0 += in.dphi0[c] * in.dphi0[c];
             }
             EK0 /= pow(a, 2.0 * mc.alpha);
-            const double Vb = 0.25 * mc.lam * (s2 - mc.vev2) * (s2 - mc.vev2);
+            double dvb;
+            const double Vb = gauge_pot<double>(mc.gpot, mc.pexp, mc.lam, mc.vev2, s2, &dvb);
             const double H = sqrt(fmax(pow(a, 2.0 * mc.alpha) / 3.0 * mc.fmp2 * (EK0 + Vb), 0.0));
             void** b = L->buf.f[L->cur];
             for (int c = 0; c < 4; ++c) {
-                const double m2 = 0.5 * mc.lam * (s2 - mc.vev2) + mc.lam * in.phi0[c] * in.phi0[c];
+                const double m2 = gauge_curvature(mc.gpot, mc.pexp, mc.lam, mc.vev2, s2, 1.4142135623730951 * in.phi0[c]);
                 for (int which = 0; which < 2; ++which) {
                     ICParams P;
                     P.N = N; P.stream = c; P.which = which; P.u1comp = -1;
@@ -334,11 +335,12 @@ cl_status ic_generate(Lattice* L) {
         // U(1): components phi_0, phi_1 of phi = (phi_0 + i phi_1)/sqrt(2); no mean split
         const double pb[2] = {in.phi0[0], in.phi0[1]}, db[2] = {in.dphi0[0], in.dphi0[1]};
         const double sq = 0.5 * (pb[0] * pb[0] + pb[1] * pb[1]);
-        const double Vb = 0.25 * mc.lam * (sq - mc.vev2) * (sq - mc.vev2);
+        double dvb;
+        const double Vb = gauge_pot<double>(mc.gpot, mc.pexp, mc.lam, mc.vev2, sq, &dvb);
         const double EK0 = 0.5 * (db[0] * db[0] + db[1] * db[1]) / pow(a, 2.0 * mc.alpha);
         const double H = sqrt(fmax(pow(a, 2.0 * mc.alpha) / 3.0 * mc.fmp2 * (EK0 + Vb), 0.0));
         for (int comp = 0; comp < 2; ++comp) {
-            const double m2 = 0.5 * mc.lam * (sq - mc.vev2) + 0.5 * mc.lam * pb[comp] * pb[comp];
+            const double m2 = gauge_curvature(mc.gpot, mc.pexp, mc.lam, mc.vev2, sq, pb[comp]);
             for (int which = 0; which < 2; ++which) {
                 void* dst = L->buf.f[L->cur][which == 0 ? comp : 2 + comp];
                 const double add = which == 0 ? pb[comp] : db[comp];

@@ -197,6 +197,16 @@ uint32_t crc32_update(uint32_t crc, const unsigned char* p, size_t n) {
     return ~crc;
 }
 
+// Bound on the curvature of the gauge models' potential at the homogeneous
+// start, mod2 = |phi|^2 = S/2 with S the squared canonical norm: along a
+// canonical component chi it is dV/dmod2 + chi^2 d^2V/dmod2^2, at most
+// |dV/dmod2| + 2 mod2 |d^2V/dmod2^2|.
+double gauge_m2_bound(const cl::ModelConst& mc, double mod2) {
+    double dv;
+    cl::gauge_pot<double>(mc.gpot, mc.pexp, mc.lam, mc.vev2, mod2, &dv);
+    return fabs(dv) + 2.0 * mod2 * fabs(cl::gauge_pot_d2(mc.gpot, mc.pexp, mc.lam, mod2));
+}
+
 struct CkptHeader {
     char magic[8];
     int32_t version, prec, narr, staggered;
@@ -293,6 +303,10 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     } else if (model->kind == CL_MODEL_U1 || model->kind == CL_MODEL_SU2) {
         if (grid->integrator < CL_INT_LF || grid->integrator > CL_INT_VV10) return fail(nullptr, CL_ERR_ARG, "unknown integrator");
         if (!(model->gauge_e > 0)) return fail(nullptr, CL_ERR_ARG, "gauge_e must be positive");
+        if (model->potential != CL_POT_HIGGS && model->potential != CL_POT_MONOMIAL)
+            return fail(nullptr, CL_ERR_ARG, "unknown gauge potential");
+        if (model->potential == CL_POT_MONOMIAL && model->pexp != 2 && model->pexp != 4 && model->pexp != 6)
+            return fail(nullptr, CL_ERR_ARG, "pexp must be 2, 4 or 6");
         if (model->kind == CL_MODEL_SU2) {
             // a uniform charge Im[Phi^dag sigma^a pi] cannot satisfy the Gauss law on a periodic lattice
             const double* f = init->phi0;
@@ -352,6 +366,7 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     mc.kappa = model->omega_over_fstar * model->omega_over_fstar;
     mc.dx = 2.0 * M_PI / (grid->kIR * N);
     mc.idx2 = 1.0 / (mc.dx * mc.dx);
+    mc.gpot = mc.kind == CL_MODEL_SCALAR ? 0 : model->potential;
     mc.bg = model->background == CL_BG_FLUID ? 1 : 0;
     mc.bg_p = mc.bg ? 2.0 / (3.0 * (1.0 + model->fluid_w) - 2.0 * model->alpha) : 1.0;
     mc.bg_H0 = mc.bg ? model->hubble0 : 0.0;
@@ -370,10 +385,10 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         } else if (mc.kind == CL_MODEL_SU2) {
             double s2 = 0.0;
             for (int c = 0; c < 4; ++c) s2 += init->phi0[c] * init->phi0[c];
-            m2 = fabs(0.5 * mc.lam * (s2 - mc.vev2)) + mc.lam * s2 + mc.e * mc.e * s2 / (2.0 * mc.kappa);
+            m2 = gauge_m2_bound(mc, s2) + mc.e * mc.e * s2 / (2.0 * mc.kappa);
         } else {
             const double s2 = 0.5 * (init->phi0[0] * init->phi0[0] + init->phi0[1] * init->phi0[1]);
-            m2 = fabs(0.5 * mc.lam * (s2 - mc.vev2)) + mc.lam * s2 + 2.0 * mc.e * mc.e * s2 / mc.kappa;
+            m2 = gauge_m2_bound(mc, s2) + 2.0 * mc.e * mc.e * s2 / mc.kappa;
         }
         const double w2 = pow(a, 2.0 * mc.alpha - 2.0) * 12.0 * mc.idx2 + pow(a, 2.0 * mc.alpha) * m2;
         // RK4: the stability interval of the oscillator on the imaginary axis is |w dt| < 2 sqrt(2)
@@ -708,6 +723,7 @@ extern "C" cl_status lattice_save(cl_lattice* h, const char* path) {
     hd.model.gauge_e = h->mc.e;
     hd.model.fstar_over_mp = sqrt(h->mc.fmp2);
     hd.model.omega_over_fstar = sqrt(h->mc.kappa);
+    hd.model.potential = h->mc.gpot;
     hd.steps = h->steps_done;
     hd.nbytes = st.size() + (uint64_t)h->buf.narr * arr.size();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
             for (int k = 0; k < 3; ++k) KB[i][k] = A1 * cJ * js[k] + Am * cM * mag[k];
         }
         const T mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
-        const T dv = T(0.5) * lam * (mod2 - v2);
+        T dv;
+        const T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
         T sp = T(0), pr0 = T(0), pr1 = T(0);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
         acc[4] += double(pr0); acc[5] += double(pr1);
         acc[6] += double(sp);
         acc[7] += double(grad * idx2);
-        acc[8] += double(T(0.25) * lam * (mod2 - v2) * (mod2 - v2));
+        acc[8] += double(vpot);
         acc[9] += double(sA);
         acc[10] += double(eB);
     }

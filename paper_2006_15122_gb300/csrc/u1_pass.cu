@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(256) u1_pass_kernel(const U1Args A) {
             }
         }
         const T mod2 = fr * fr + fi * fi;
-        const T dv = T(0.5) * lam * (mod2 - v2);
+        T dv;
+        const T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
         const T Kr = -A3 * dv * fr + A1 * lr * idx2, Ki = -A3 * dv * fi + A1 * li * idx2;
         const T prr = pr + h1 * Kr, pri = pim + h1 * Ki;
         const T por = pr + h * Kr, poi = pim + h * Ki;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(256) u1_pass_kernel(const U1Args A) {
         ts[0] += fr; ts[1] += fi; ts[2] += fr * fr; ts[3] += fi * fi;
         ts[4] += prr; ts[5] += pri; ts[6] += prr * prr + pri * pri;
         ts[7] += grad * idx2;
-        ts[8] += T(0.25) * lam * (mod2 - v2) * (mod2 - v2);
+        ts[8] += vpot;
         ts[9] += sA;
         ts[10] += eB;
         if (A.write) {

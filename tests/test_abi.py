@@ -66,7 +66,8 @@ def test_init_rejects_unstable_time_step():
     assert b"stability bound" in cl.load().cl_last_error(None)
 
 
-@pytest.mark.parametrize("bad", ["integrator", "pexp", "fields", "kir", "u1_charge", "u1_integrator"])
+@pytest.mark.parametrize("bad", ["integrator", "pexp", "fields", "kir", "u1_charge", "u1_integrator",
+                                 "gauge_potential", "gauge_pexp"])
 def test_init_rejects_bad_arguments(bad):
     m = cl.make_model(n_fields=1, pexp=2)
     g = cl.make_grid(16, 0.5, 0.01)
@@ -86,6 +87,11 @@ def test_init_rejects_bad_arguments(bad):
         m.kind = cl.CL_MODEL_U1
         m.gauge_e = 1.0
         g.integrator = 6
+    if bad in ("gauge_potential", "gauge_pexp"):
+        m.kind = cl.CL_MODEL_SU2
+        m.gauge_e = 1.0
+        m.potential = 2 if bad == "gauge_potential" else cl.CL_POT_MONOMIAL
+        m.pexp = 3
     st, h = _init(m, g, cl.make_init())
     assert st == cl.CL_ERR_ARG and not h.value
 

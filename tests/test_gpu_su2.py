@@ -19,7 +19,7 @@ def rel(x, y):
 
 def gpu_su2(m, integ, prec, fmp=0.0):
     model = cl.make_model(kind=cl.CL_MODEL_SU2, alpha=m.alpha, fstar_over_mp=fmp, omega_over_fstar=math.sqrt(m.kappa),
-                          lam=m.lam, vev2=m.v2, gauge_e=m.g)
+                          lam=m.lam, vev2=m.v2, gauge_e=m.g, potential=m.pot, pexp=m.p)
     kIR = 2 * math.pi / (m.N * m.dx)
     return cl.Lattice(model, cl.make_grid(m.N, kIR, 0.04, integ, prec), cl.make_init(phi0=(0.5, 0.0, 0.0, 0.0), spectrum=0))
 
@@ -44,10 +44,11 @@ def fetch(lat, N):
     return phi, pi, u, piB
 
 
-@pytest.mark.parametrize("integ,fmp,alpha", [("vv2", 0.0, 0.0), ("vv4", 0.7, 0.5)])
-def test_su2_fp64_velocity_verlet_matches_oracle(integ, fmp, alpha):
+@pytest.mark.parametrize("integ,fmp,alpha,pot", [("vv2", 0.0, 0.0, 0), ("vv4", 0.7, 0.5, 0), ("vv4", 0.7, 1.0, 1)])
+def test_su2_fp64_velocity_verlet_matches_oracle(integ, fmp, alpha, pot):
+    """Higgs potential and (pot = 1) the monomial inflaton (lam/4)(2|Phi|^2)^2."""
     N, dt = 8, 0.04
-    m = SU2Model(N=N, dx=0.6, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.8, g=0.9, kappa=1.21)
+    m = SU2Model(N=N, dx=0.6, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.8, g=0.9, kappa=1.21, pot=pot, p=4)
     ref = random_state(N, m, 7)
     if fmp > 0:
         ref.b = math.sqrt(fmp * fmp / 3.0 * ref.energies().sum())
@@ -118,16 +119,17 @@ def test_su2_homogeneous_start_and_refusals():
                    cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), dphi0=(0.0, 0.0, 0.0, 1.0), spectrum=0))
 
 
-@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32])
-def test_su2_vacuum_initial_conditions_match_oracle(prec):
+@pytest.mark.parametrize("prec,pot", [(cl.CL_FP64, 0), (cl.CL_FP32, 0), (cl.CL_FP64, 1)])
+def test_su2_vacuum_initial_conditions_match_oracle(prec, pot):
     """lattice_init with vacuum fluctuations: the doublet, its momenta (with
     the colour charges projected out) and the Gauss-consistent electric momenta
     against the oracle's SU(2) initial conditions; Gauss law at round-off."""
     from oracle.ic import su2_ic
     N, dx, omega = 16, 0.5, 0.3
-    m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=1.2, kappa=omega * omega)
+    m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=1.2, kappa=omega * omega, pot=pot, p=4)
     kIR = 2 * math.pi / (N * dx)
-    model = cl.make_model(kind=cl.CL_MODEL_SU2, omega_over_fstar=omega, lam=1.0, vev2=1.0, gauge_e=1.2)
+    model = cl.make_model(kind=cl.CL_MODEL_SU2, omega_over_fstar=omega, lam=1.0, vev2=1.0, gauge_e=1.2,
+                          potential=pot, pexp=4)
     lat = cl.Lattice(model, cl.make_grid(N, kIR, 0.04, "vv2", prec),
                      cl.make_init(phi0=(0.4, 0.0, 0.0, 0.3), seed=5, spectrum=1))
     phi, pi, u, piB, _ = su2_ic(m, kIR, [0.4, 0.0, 0.0, 0.3], [0.0] * 4, seed=5, omega_over_fstar=omega)

@@ -22,11 +22,11 @@ def angle_err(a, b):
 
 
 def gpu_u1(N, kIR, dt, prec, fmp=0.0, alpha=0.0, e=1.0, lam=1.0, v2=1.0, omega=1.0, spectrum=0, seed=0,
-           phi0=(0.0, 0.0), integ="lf"):
+           phi0=(0.0, 0.0), integ="lf", pot=0, p=4, dphi0=(0.0, 0.0)):
     m = cl.make_model(kind=cl.CL_MODEL_U1, alpha=alpha, fstar_over_mp=fmp, omega_over_fstar=omega, lam=lam,
-                      vev2=v2, gauge_e=e)
+                      vev2=v2, gauge_e=e, potential=pot, pexp=p)
     g = cl.make_grid(N, kIR, dt, integ, prec)
-    return cl.Lattice(m, g, cl.make_init(phi0=phi0, seed=seed, spectrum=spectrum))
+    return cl.Lattice(m, g, cl.make_init(phi0=phi0, dphi0=dphi0, seed=seed, spectrum=spectrum))
 
 
 def get_all(lat):
@@ -147,4 +147,65 @@ def test_u1_velocity_verlet_keeps_gauss_law(prec, tol):
         g.append(lat.measure_means()["gauss_violation"])
     assert max(g) < tol, g
     assert lat.measure_means()["EG"][1] > 0.0
+    lat.close()
+
+
+@pytest.mark.parametrize("integ,fmp,alpha,p", [("vv4", 0.8, 1.0, 4), ("vv2", 0.5, 0.0, 6), ("lf", 0.0, 0.0, 2)])
+def test_u1_monomial_inflaton_matches_oracle(integ, fmp, alpha, p):
+    """Charged inflaton V = (lam/p)(2|phi|^2)^(p/2) (section 8) with expansion:
+    fields, links, momenta, background and E_V against the oracle."""
+    import oracle
+    N, dx, dt = 16, 0.5, 0.04
+    kIR = 2 * math.pi / (N * dx)
+    lat = gpu_u1(N, kIR, dt, cl.CL_FP64, fmp=fmp, alpha=alpha, e=0.9, lam=1.2, omega=1.1, integ=integ, pot=1, p=p,
+                 phi0=(0.9, 0.0))
+    om = U1Model(N=N, dx=dx, alpha=alpha, fmp2=fmp * fmp, lam=1.2, e=0.9, kappa=1.21, pot=1, p=p)
+    phi = inputs.fields(2, N, seed=23, amp=0.6, kmax=4, means=[0.6, -0.2])
+    pi = inputs.fields(2, N, seed=24, amp=0.3, kmax=4)
+    th = inputs.angles(N, 25, scale=0.4)
+    pa = inputs.fields(3, N, seed=26, amp=0.2, kmax=4)
+    ref = U1Lattice(om, phi, pi, th, pa)
+    ref.b = math.sqrt(fmp * fmp / 3 * ref.energies().sum()) if fmp > 0 else 0.0
+    for i in range(2):
+        lat.set_field(cl.FIELD(i), phi[i])
+        lat.set_field(cl.MOMENTUM(i), pi[i])
+    for i in range(3):
+        lat.set_field(cl.LINK(i), th[i])
+        lat.set_field(cl.EMOMENTUM(i), pa[i])
+    lat.set_background(1.0, ref.b, 0.0)
+    E0 = ref.energies()
+    assert lat.measure_means()["EV"] == pytest.approx(E0[2], rel=1e-13)
+    if integ == "lf":
+        ref.lf_prepare(dt)
+        lat.evolve(7)
+        ref.lf_steps(dt, 7)
+    else:
+        lat.evolve(7)
+        ref.vv_steps({"vv2": oracle.VV2, "vv4": oracle.VV4}[integ], dt, 7)
+    gphi, gpi, gth, gpa = get_all(lat)
+    assert rel(gphi, ref.phi) < 1e-12
+    assert rel(gpi, ref.pi) < 1e-12
+    assert angle_err(gth, ref.theta) < 1e-12
+    assert rel(gpa, ref.piA) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 + 1e-12 * abs(ref.b)
+    if integ != "lf":
+        assert mm["EV"] == pytest.approx(ref.energies()[2], rel=1e-11)
+    lat.close()
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_u1_monomial_initial_conditions_match_oracle(p):
+    """Vacuum fluctuations about a homogeneous inflaton phi0 = (1.3, 0.4)/sqrt(2)
+    with the monomial potential's curvature along each component and the
+    Hubble rate of its energy (section 7), fp64 against the oracle."""
+    N, dx = 16, 0.5
+    kIR = 2 * math.pi / (N * dx)
+    lat = gpu_u1(N, kIR, 0.02, cl.CL_FP64, fmp=0.7, alpha=1.0, e=0.8, lam=1.1, spectrum=1, seed=41, pot=1, p=p,
+                 phi0=(1.3, 0.4), dphi0=(-0.26, -0.08), omega=0.6)
+    om = U1Model(N=N, dx=dx, alpha=1.0, fmp2=0.49, lam=1.1, e=0.8, kappa=0.36, pot=1, p=p)
+    phi, pi, th, pa, _ = u1_ic(om, kIR, [1.3, 0.4], [-0.26, -0.08], seed=41, omega_over_fstar=0.6)
+    gphi, gpi, gth, gpa = get_all(lat)
+    assert rel(gphi, phi) < 1e-12 and rel(gpi, pi) < 1e-12 and rel(gpa, pa) < 1e-11
+    assert np.all(gth == 0.0)
     lat.close()

@@ -251,3 +251,21 @@ def test_u1_monomial_homogeneous_oscillation_period(p):
     lat.vv_steps(VV10, T / n, n // 2)
     assert np.max(np.abs(lat.phi[0] * sqrt(2.0) - chi0)) < 1e-10
     assert np.max(np.abs(lat.phi[1])) == 0.0 and np.max(np.abs(lat.theta)) == 0.0
+
+
+@pytest.mark.parametrize("pot,p", [(0, 4), (1, 2), (1, 4), (1, 6)])
+def test_charged_potential_curvature_is_the_second_derivative(pot, p):
+    """The curvature that sets the vacuum fluctuations (section 7) along a
+    canonical component chi_0 of (chi_0, chi_1), mod2 = (chi_0^2 + chi_1^2)/2,
+    against central second differences of V itself."""
+    from oracle.ic import _charged_potential
+    m = U1Model(N=4, dx=1.0, alpha=0.0, fmp2=0.0, lam=1.3, v2=0.7, pot=pot, p=p)
+    chi1 = 0.4
+    for chi0 in (0.3, 1.1, -0.8):
+        h = 1e-4
+        V = [_charged_potential(m, 0.5 * ((chi0 + d) ** 2 + chi1 ** 2))[0] for d in (-h, 0.0, h)]
+        num = (V[0] - 2 * V[1] + V[2]) / (h * h)
+        _, dv, d2 = _charged_potential(m, 0.5 * (chi0 ** 2 + chi1 ** 2))
+        assert abs(dv + d2 * chi0 ** 2 - num) < 1e-6 * (1 + abs(num))
+        if pot == 1 and p == 2:
+            assert dv + d2 * chi0 ** 2 == pytest.approx(m.lam, rel=1e-15)  # plain mass term lam chi^2/2
