@@ -11,8 +11,9 @@ What it computes (each function cites the passage it follows):
                    (section 4.2.1), compact U(1) kernels, energies, Gauss law
                    and staggered leapfrog (sections 5.3, 5.4), compact U(1) VVn
                    (5.3.2, 5.3.3), prescribed fluid background (4.1), explicit
-                   RK4 (4.3.1), SU(2)-Higgs kernels, energies, Gauss law and
-                   VVn (section 6)
+                   RK4 (4.3.1), Gauss-Legendre (3.4.2, 4.3.3), SU(2)-Higgs
+                   kernels, energies, Gauss law and VVn (section 6), and the
+                   SU(2) x U(1) doublet with a singlet (section 8.3)
   ic.py            initial conditions of section 7
   spectra.py       DFT convention and power spectra (sections 3.1, 4.4.2)
   philox.py        Philox4x32-10, the counter-based generator of the draws
@@ -27,4 +28,4 @@ energy conservation and Philox known-answer vectors.
 """
 from . import core, ic, mlp, philox, spectra  # noqa: F401
 from .core import (VV2, VV4, VV6, VV8, VV10, ScalarLattice, ScalarModel, SU2Lattice,  # noqa: F401
-                   SU2Model, U1Lattice, U1Model)
+                   SU2Model, SU2U1Lattice, SU2U1Model, U1Lattice, U1Model)

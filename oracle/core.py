@@ -41,6 +41,11 @@ def lib():
             ("orc_su2_Ka", [vp, C.c_double, d], C.c_double),
             ("orc_su2_gauss", [vp, d, d, d, d, d], None),
             ("orc_su2_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d], None),
+            ("orc_su2u1_kernels", [vp, d, d, d, d, C.c_double, d, d, d, d], None),
+            ("orc_su2u1_energies", [vp, d, d, d, d, d, d, d, d, C.c_double, d], None),
+            ("orc_su2u1_Ka", [vp, C.c_double, d], C.c_double),
+            ("orc_su2u1_gauss", [vp, d, d, d, d, d, d], None),
+            ("orc_su2u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d, d, d, d, d], None),
         ]:
             f = getattr(_lib, name)
             f.argtypes = args
@@ -426,4 +431,98 @@ class SU2Lattice:
         for _ in range(n):
             lib().orc_su2_vv_step(self._mp(), len(w), _p(w), dt, _p(self.phi), _p(self.pi), _p(self.u),
                                   _p(self.piB), C.byref(a), C.byref(b))
+        self.a, self.b = a.value, b.value
+
+
+class _SU2U1ModelC(C.Structure):
+    _fields_ = [("N", C.c_int64), ("dx", C.c_double), ("alpha", C.c_double), ("fmp2", C.c_double),
+                ("lam", C.c_double), ("v2", C.c_double), ("g", C.c_double), ("kappa", C.c_double),
+                ("pot", C.c_int32), ("p", C.c_int32), ("eA", C.c_double), ("q", C.c_double),
+                ("chi", C.c_int32), ("pad", C.c_int32)]
+
+
+@dataclass
+class SU2U1Model:
+    """Program-unit doublet of the working example of section 8.3: SU(2)
+    coupling g = g_B Q_B, U(1) coupling eA = g_A Q_A (0: no U(1) sector), a
+    real singlet chi (chi = 1) with V_int = q |Phi|^2 chi^2, and the Higgs
+    (pot = 0) or monomial (pot = 1) potential of the doublet."""
+    N: int
+    dx: float
+    alpha: float
+    fmp2: float
+    lam: float = 1.0
+    v2: float = 1.0
+    g: float = 1.0
+    kappa: float = 1.0
+    pot: int = 0
+    p: int = 4
+    eA: float = 1.0
+    q: float = 0.0
+    chi: int = 1
+
+    def c(self):
+        return _SU2U1ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.g, self.kappa, self.pot,
+                            self.p, self.eA, self.q, self.chi, 0)
+
+    def su2(self):
+        return SU2Model(N=self.N, dx=self.dx, alpha=self.alpha, fmp2=self.fmp2, lam=self.lam, v2=self.v2, g=self.g,
+                        kappa=self.kappa, pot=self.pot, p=self.p)
+
+
+class SU2U1Lattice:
+    """SU(2) x U(1) + chi state: the SU(2) arrays of SU2Lattice plus link
+    angles theta and electric momenta piA of shape (3, N, N, N) and the singlet
+    chi, pchi of shape (N, N, N)."""
+
+    def __init__(self, model, phi, pi, u, piB, theta=None, piA=None, chi=None, pchi=None, a=1.0, b=0.0):
+        N = model.N
+        self.m = model
+        arr = lambda x, shape: (np.zeros(shape) if x is None else
+                                np.ascontiguousarray(x, dtype=np.float64).reshape(shape).copy())
+        self.phi = arr(phi, (4, N, N, N))
+        self.pi = arr(pi, (4, N, N, N))
+        self.u = arr(u, (3, 4, N, N, N))
+        self.piB = arr(piB, (3, 3, N, N, N))
+        self.theta = arr(theta, (3, N, N, N))
+        self.piA = arr(piA, (3, N, N, N))
+        self.chi = arr(chi, (N, N, N))
+        self.pchi = arr(pchi, (N, N, N))
+        self.a, self.b = a, b
+
+    def _mp(self):
+        self._mc = self.m.c()
+        return C.byref(self._mc)
+
+    def kernels(self):
+        Kp, KB = np.zeros_like(self.phi), np.zeros_like(self.piB)
+        KA, Kc = np.zeros_like(self.piA), np.zeros_like(self.chi)
+        lib().orc_su2u1_kernels(self._mp(), _p(self.phi), _p(self.u), _p(self.theta), _p(self.chi), self.a, _p(Kp),
+                                _p(KB), _p(KA), _p(Kc))
+        return Kp, KB, KA, Kc
+
+    def energies(self):
+        """E_K^Phi, E_G^Phi, E_V, E_K^B, E_G^B, E_K^A, E_G^A, E_K^chi, E_G^chi."""
+        out = np.zeros(9)
+        lib().orc_su2u1_energies(self._mp(), _p(self.phi), _p(self.pi), _p(self.u), _p(self.piB), _p(self.theta),
+                                 _p(self.piA), _p(self.chi), _p(self.pchi), self.a, _p(out))
+        return out
+
+    def Ka(self):
+        E = np.ascontiguousarray(self.energies())
+        return lib().orc_su2u1_Ka(self._mp(), self.a, _p(E))
+
+    def gauss(self):
+        """(SU(2), U(1)) Gauss residuals <G^2>/(<lhs^2> + <rhs^2>)."""
+        out = np.zeros(6)
+        lib().orc_su2u1_gauss(self._mp(), _p(self.phi), _p(self.pi), _p(self.u), _p(self.piB), _p(self.piA), _p(out))
+        return out[0] / max(out[1] + out[2], 1e-300), out[3] / max(out[4] + out[5], 1e-300)
+
+    def vv_steps(self, weights, dt, n=1):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        a, b = C.c_double(self.a), C.c_double(self.b)
+        for _ in range(n):
+            lib().orc_su2u1_vv_step(self._mp(), len(w), _p(w), dt, _p(self.phi), _p(self.pi), _p(self.u),
+                                    _p(self.piB), _p(self.theta), _p(self.piA), _p(self.chi), _p(self.pchi),
+                                    C.byref(a), C.byref(b))
         self.a, self.b = a.value, b.value

@@ -998,6 +998,275 @@ void orc_su2_vv_step(const orc_su2_model* m, int s, const double* w, double dt, 
     free(KB);
 }
 
+/* ------------------------------------------------ SU(2) x U(1) + singlet */
+
+/* The doublet of the working example of section 8.3: Phi charged under SU(2)
+ * (links U_i, coupling g = g_B Q_B) and U(1) (link angles theta_i, V_i =
+ * exp(-i theta_i), coupling eA = g_A Q_A), plus a real singlet chi with
+ * V_int = q |Phi|^2 chi^2.  The parallel transporter of Phi is W_i = V_i U_i
+ * (the phase commutes with U_i), so the covariant hopping terms of section 6
+ * carry the extra phase and the two gauge sectors see the same hop:
+ *   K_Phi   = -a^{3+alpha}(V'(|Phi|^2) + q chi^2) Phi
+ *             + a^{1+alpha} sum_i (W_i Phi(n+i) - 2 Phi + W_i^dag(n-i) Phi(n-i))/dx^2,
+ *   K_B,i^a = a^{1+alpha}(g/(kappa dx)) Im[Phi^dag sigma^a W_i Phi(n+i)] + (SU(2) magnetic term),
+ *   K_A,i   = a^{1+alpha}(2 eA/(kappa dx)) Im[Phi^dag W_i Phi(n+i)]
+ *             + a^{alpha-1}/(eA dx^3) sum_{j!=i} [Im V_ij(n) - Im V_ij(n-j)],
+ *   K_chi   = -a^{3+alpha} 2 q |Phi|^2 chi + a^{1+alpha} L[chi],
+ * with two Gauss laws: the SU(2) one of section 6 and
+ *   (1/dx) sum_i [piA_i(n) - piA_i(n-i)] = (2 eA/kappa) Im[Phi^dag pi].
+ * eA = 0 switches the U(1) sector off, chi = 0 the singlet. */
+typedef struct {
+    int64_t N;
+    double dx, alpha, fmp2, lam, v2, g, kappa;
+    int32_t pot, p;
+    double eA, q;
+    int32_t chi, pad;
+} orc_su2u1_model;
+
+static orc_su2_model su2_part(const orc_su2u1_model* m) {
+    orc_su2_model s;
+    s.N = m->N; s.dx = m->dx; s.alpha = m->alpha; s.fmp2 = m->fmp2; s.lam = m->lam; s.v2 = m->v2;
+    s.g = m->g; s.kappa = m->kappa; s.pot = m->pot; s.p = m->p;
+    return s;
+}
+
+/* W_i Phi(m) = e^{-i t} (U Phi(m)) with U the quaternion q */
+static void whop(const double* q, double t, const double* f, double* o) {
+    double u[4];
+    umul(q, f, u);
+    const double c = cos(t), s = sin(t);
+    o[0] = c * u[0] + s * u[1];
+    o[1] = c * u[1] - s * u[0];
+    o[2] = c * u[2] + s * u[3];
+    o[3] = c * u[3] - s * u[2];
+}
+
+/* Im[x^dag y] for doublets */
+static double im_dot(const double* x, const double* y) {
+    return x[0] * y[1] - x[1] * y[0] + x[2] * y[3] - x[3] * y[2];
+}
+
+static double plaq_u1(int64_t N, const double* th, int i, int j, int64_t x, int64_t y, int64_t z) {
+    const int64_t V = N * N * N, n = site(N, x, y, z);
+    return th[(int64_t)i * V + n] + th[(int64_t)j * V + shift(N, x, y, z, i, 1)] -
+           th[(int64_t)i * V + shift(N, x, y, z, j, 1)] - th[(int64_t)j * V + n];
+}
+
+void orc_su2u1_kernels(const orc_su2u1_model* m, const double* phi, const double* u, const double* th,
+                       const double* chi, double a, double* Kp, double* KB, double* KA, double* Kc) {
+    const int64_t N = m->N, V = N * N * N;
+    const orc_su2_model s2 = su2_part(m);
+    const double A1 = pow(a, 1.0 + m->alpha), A3 = pow(a, 3.0 + m->alpha), Am = pow(a, m->alpha - 1.0);
+    const double idx2 = 1.0 / (m->dx * m->dx);
+    const double cJ = m->g / (m->kappa * m->dx), cM = 2.0 / (m->g * m->dx * m->dx * m->dx);
+    const int u1 = m->eA != 0.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                double f[4], lap[4];
+                getf(phi, V, n, f);
+                for (int c = 0; c < 4; ++c) lap[c] = -6.0 * f[c];
+                double lchi = 0.0;
+                for (int i = 0; i < 3; ++i) {
+                    const int64_t np = shift(N, x, y, z, i, 1), nm = shift(N, x, y, z, i, -1);
+                    double q[4], qm[4], qmc[4], fp[4], fm[4], t[4], tb[4];
+                    getq(u, V, i, n, q);
+                    getq(u, V, i, nm, qm);
+                    qconj(qm, qmc);
+                    getf(phi, V, np, fp);
+                    getf(phi, V, nm, fm);
+                    const double ti = u1 ? th[(int64_t)i * V + n] : 0.0;
+                    const double tm = u1 ? th[(int64_t)i * V + nm] : 0.0;
+                    whop(q, ti, fp, t);
+                    whop(qmc, -tm, fm, tb); /* W^dag(n-i) = U^dag(n-i) e^{+i theta(n-i)} */
+                    for (int c = 0; c < 4; ++c) lap[c] += t[c] + tb[c];
+                    double js[3];
+                    im_sigma(f, t, js);
+                    double mag[3] = {0, 0, 0};
+                    for (int j = 0; j < 3; ++j) {
+                        if (j == i) continue;
+                        double P1[4], P2[4], Uj[4], Ujc[4], s1[4], Q[4];
+                        plaquette(&s2, u, i, j, x, y, z, P1);
+                        int64_t cm[3] = {x, y, z};
+                        cm[j] = wrap(cm[j] - 1, N);
+                        plaquette(&s2, u, i, j, cm[0], cm[1], cm[2], P2);
+                        getq(u, V, j, site(N, cm[0], cm[1], cm[2]), Uj);
+                        qconj(Uj, Ujc);
+                        qmul(Ujc, P2, s1);
+                        qmul(s1, Uj, Q);
+                        for (int c = 0; c < 3; ++c) mag[c] += P1[c + 1] - Q[c + 1];
+                    }
+                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];
+                    if (u1) {
+                        double magA = 0.0;
+                        for (int j = 0; j < 3; ++j) {
+                            if (j == i) continue;
+                            int64_t cm[3] = {x, y, z};
+                            cm[j] = wrap(cm[j] - 1, N);
+                            /* Im V_ij = -sin(theta_ij) */
+                            magA += -sin(plaq_u1(N, th, i, j, x, y, z)) + sin(plaq_u1(N, th, i, j, cm[0], cm[1], cm[2]));
+                        }
+                        KA[(int64_t)i * V + n] = A1 * 2.0 * m->eA / (m->kappa * m->dx) * im_dot(f, t) +
+                                                 Am / (m->eA * m->dx * m->dx * m->dx) * magA;
+                    }
+                    if (m->chi) lchi += chi[np] + chi[nm];
+                }
+                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
+                double dv;
+                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);
+                const double c2 = m->chi ? chi[n] * chi[n] : 0.0;
+                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * (dv + m->q * c2) * f[c] + A1 * lap[c] * idx2;
+                if (m->chi)
+                    Kc[n] = -A3 * 2.0 * m->q * mod2 * chi[n] + A1 * (lchi - 6.0 * chi[n]) * idx2;
+            }
+}
+
+/* out[0..8] = E_K^Phi, E_G^Phi, E_V (potential + interaction), E_K^B, E_G^B,
+ * E_K^A, E_G^A, E_K^chi = <pchi^2>/(2a^6), E_G^chi = sum_i <(D_i^+ chi)^2>/(2a^2). */
+void orc_su2u1_energies(const orc_su2u1_model* m, const double* phi, const double* pi, const double* u,
+                        const double* piB, const double* th, const double* piA, const double* chi,
+                        const double* pchi, double a, double* out) {
+    const int64_t N = m->N, V = N * N * N;
+    const int u1 = m->eA != 0.0;
+    const orc_su2_model s2 = su2_part(m);
+    double sk = 0, sg = 0, sv = 0, skb = 0, sgb = 0, ska = 0, sga = 0, skc = 0, sgc = 0;
+#pragma omp parallel for reduction(+ : sk, sg, sv, skb, sgb, ska, sga, skc, sgc) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                double f[4], p[4];
+                getf(phi, V, n, f);
+                getf(pi, V, n, p);
+                for (int c = 0; c < 4; ++c) sk += p[c] * p[c];
+                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
+                double dv;
+                sv += gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);
+                if (m->chi) {
+                    sv += m->q * mod2 * chi[n] * chi[n];
+                    skc += pchi[n] * pchi[n];
+                }
+                for (int i = 0; i < 3; ++i) {
+                    const int64_t np = shift(N, x, y, z, i, 1);
+                    double q[4], fp[4], t[4];
+                    getq(u, V, i, n, q);
+                    getf(phi, V, np, fp);
+                    whop(q, u1 ? th[(int64_t)i * V + n] : 0.0, fp, t);
+                    for (int c = 0; c < 4; ++c) sg += (t[c] - f[c]) * (t[c] - f[c]);
+                    for (int c = 0; c < 3; ++c) skb += piB[((int64_t)i * 3 + c) * V + n] * piB[((int64_t)i * 3 + c) * V + n];
+                    if (u1) ska += piA[(int64_t)i * V + n] * piA[(int64_t)i * V + n];
+                    if (m->chi) sgc += (chi[np] - chi[n]) * (chi[np] - chi[n]);
+                    for (int j = i + 1; j < 3; ++j) {
+                        double P[4];
+                        plaquette(&s2, u, i, j, x, y, z, P);
+                        sgb += 2.0 - 2.0 * P[0];
+                        if (u1) sga += 1.0 - cos(plaq_u1(N, th, i, j, x, y, z));
+                    }
+                }
+            }
+    const double a2 = a * a, a4 = a2 * a2, a6 = a4 * a2, dx2 = m->dx * m->dx, dx4 = dx2 * dx2;
+    out[0] = sk / V / a6;
+    out[1] = sg / V / dx2 / a2;
+    out[2] = sv / V;
+    out[3] = m->kappa * skb / V / (2.0 * a4);
+    out[4] = 2.0 * m->kappa * sgb / V / (a4 * dx4 * m->g * m->g);
+    out[5] = u1 ? m->kappa * ska / V / (2.0 * a4) : 0.0;
+    out[6] = u1 ? m->kappa * sga / V / (a4 * dx4 * m->eA * m->eA) : 0.0;
+    out[7] = skc / V / (2.0 * a6);
+    out[8] = sgc / V / dx2 / (2.0 * a2);
+}
+
+/* K_a of section 4 with every scalar (Phi, chi) weighted as a scalar and every
+ * gauge energy with (alpha - 1). */
+double orc_su2u1_Ka(const orc_su2u1_model* m, double a, const double* E) {
+    return m->fmp2 / 3.0 * pow(a, 2.0 * m->alpha + 1.0) *
+           ((m->alpha - 2.0) * (E[0] + E[7]) + m->alpha * (E[1] + E[8]) + (m->alpha + 1.0) * E[2] +
+            (m->alpha - 1.0) * (E[3] + E[4] + E[5] + E[6]));
+}
+
+/* Gauss residuals: out[0..2] the SU(2) law (as orc_su2_gauss, the electric
+ * momenta transported with U only: the phase drops out of the adjoint action),
+ * out[3..5] = {<G^2>, <lhs^2>, <rhs^2>} of the U(1) law. */
+void orc_su2u1_gauss(const orc_su2u1_model* m, const double* phi, const double* pi, const double* u,
+                     const double* piB, const double* piA, double* out) {
+    const orc_su2_model s2 = su2_part(m);
+    orc_su2_gauss(&s2, phi, pi, u, piB, out);
+    out[3] = out[4] = out[5] = 0.0;
+    if (m->eA == 0.0) return;
+    const int64_t N = m->N, V = N * N * N;
+    double g2 = 0, l2 = 0, r2 = 0;
+#pragma omp parallel for reduction(+ : g2, l2, r2) schedule(static)
+    for (int64_t z = 0; z < N; ++z)
+        for (int64_t y = 0; y < N; ++y)
+            for (int64_t x = 0; x < N; ++x) {
+                const int64_t n = site(N, x, y, z);
+                double div = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    div += (piA[(int64_t)i * V + n] - piA[(int64_t)i * V + shift(N, x, y, z, i, -1)]) / m->dx;
+                double f[4], p[4];
+                getf(phi, V, n, f);
+                getf(pi, V, n, p);
+                const double r = 2.0 * m->eA / m->kappa * im_dot(f, p);
+                g2 += (div - r) * (div - r);
+                l2 += div * div;
+                r2 += r * r;
+            }
+    out[3] = g2 / V;
+    out[4] = l2 / V;
+    out[5] = r2 / V;
+}
+
+/* One VVn step of the combined model, the structure of orc_su2_vv_step with
+ * the U(1) links drifted by the exact phase (theta += eA dx h a_1/2^{alpha-1} piA)
+ * and chi drifted like Phi. */
+void orc_su2u1_vv_step(const orc_su2u1_model* m, int s, const double* w, double dt, double* phi, double* pi,
+                       double* u, double* piB, double* th, double* piA, double* chi, double* pchi, double* a,
+                       double* b) {
+    const int64_t V = m->N * m->N * m->N;
+    const int u1 = m->eA != 0.0;
+    const orc_su2_model s2 = su2_part(m);
+    double* Kp = (double*)malloc(sizeof(double) * (size_t)(4 * V));
+    double* KB = (double*)malloc(sizeof(double) * (size_t)(9 * V));
+    double* KA = (double*)malloc(sizeof(double) * (size_t)(3 * V));
+    double* Kc = (double*)malloc(sizeof(double) * (size_t)V);
+    double E[9];
+    orc_su2u1_energies(m, phi, pi, u, piB, th, piA, chi, pchi, *a, E);
+    for (int p = 0; p < s; ++p) {
+        const double h = w[p] * dt;
+        for (int half = 0; half < 2; ++half) {
+            if (half == 1) {
+                const double bh = *b + 0.5 * h * orc_su2u1_Ka(m, *a, E);
+                const double an = *a + h * bh, ah = 0.5 * (*a + an);
+                const double cphi = h * pow(ah, -(3.0 - m->alpha));
+                su2_drift(&s2, phi, pi, u, piB, cphi, m->g * m->dx * h * pow(ah, -(1.0 - m->alpha)));
+                if (u1) {
+                    const double cth = m->eA * m->dx * h * pow(ah, -(1.0 - m->alpha));
+                    for (int64_t n = 0; n < 3 * V; ++n) th[n] += cth * piA[n];
+                }
+                if (m->chi)
+                    for (int64_t n = 0; n < V; ++n) chi[n] += cphi * pchi[n];
+                *a = an;
+                *b = bh;
+            }
+            orc_su2u1_kernels(m, phi, u, th, chi, *a, Kp, KB, KA, Kc);
+            for (int64_t n = 0; n < 4 * V; ++n) pi[n] += 0.5 * h * Kp[n];
+            for (int64_t n = 0; n < 9 * V; ++n) piB[n] += 0.5 * h * KB[n];
+            if (u1)
+                for (int64_t n = 0; n < 3 * V; ++n) piA[n] += 0.5 * h * KA[n];
+            if (m->chi)
+                for (int64_t n = 0; n < V; ++n) pchi[n] += 0.5 * h * Kc[n];
+        }
+        orc_su2u1_energies(m, phi, pi, u, piB, th, piA, chi, pchi, *a, E);
+        *b += 0.5 * h * orc_su2u1_Ka(m, *a, E);
+    }
+    free(Kp);
+    free(KB);
+    free(KA);
+    free(Kc);
+}
+
 /* ------------------------------------------------ Gauss-Legendre (implicit RK) */
 
 /* One step of the s-stage Gauss-Legendre implicit Runge-Kutta method of
