@@ -89,25 +89,11 @@ def scalar_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_
     m2 = potential_curvature(model, phibar)
     phi = np.zeros((Ns, N, N, N))
     pi = np.zeros((Ns, N, N, N))
-    lin, conj, selfc, zero, nabs = mode_map(N)
-    k = kIR * nabs
     for i in range(Ns):
         dphi = np.zeros((N, N, N))
         ddphi = np.zeros((N, N, N))
         if fluctuations:
-            w = _omega(k, a, m2[i])
-            with np.errstate(divide="ignore", invalid="ignore"):
-                T = np.where(zero, 0.0, (omega_over_fstar ** 2) * (N / dx) ** 3 / (2 * a * a * w))
-            T *= fluct_scale ** 2
-            u = philox.uniforms(lin, i, 0, seed)
-            L = np.sqrt(-T * np.log(u[0]))
-            R = np.sqrt(-T * np.log(u[1]))
-            el = np.exp(2j * np.pi * u[2])
-            er = np.exp(2j * np.pi * u[3])
-            G = (L * el + R * er) / np.sqrt(2.0)
-            Gd = a ** (alpha - 1.0) * (1j * w / np.sqrt(2.0)) * (L * el - R * er) - H * G
-            dphi = dft_inverse(_project(G, conj, selfc, zero)).real
-            ddphi = dft_inverse(_project(Gd, conj, selfc, zero)).real
+            dphi, ddphi = _singlet_draw(N, alpha, kIR, m2[i], H, seed, i, omega_over_fstar, a, fluct_scale)
         phi[i] = phibar[i] + dphi
         pi[i] = a ** (3.0 - alpha) * (dphibar[i] + ddphi)
     return phi, pi, dx
@@ -192,6 +178,16 @@ def su2_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_sca
     Im[Phi^dag sigma^a i sigma^b Phi] = delta_ab |Phi|^2), links start at unity and
     piB solves sum_i D_i^- piB_i^a = (g/kappa) Im[Phi^dag sigma^a pi] colour by colour
     in Fourier space.  Returns (phi (4,N,N,N), pi, u (3,4,N,N,N), piB (3,3,N,N,N), dx)."""
+    phi, pi, dx = _doublet_draw(model, kIR, phibar, dphibar, seed, omega_over_fstar, a, fluct_scale)
+    phi, pi, piB = _su2_gauss_start(model, phi, pi, dx)
+    u = np.zeros((3, 4, model.N, model.N, model.N))
+    u[:, 0] = 1.0
+    return phi, pi, u, piB, dx
+
+
+def _doublet_draw(model, kIR, phibar, dphibar, seed, omega_over_fstar, a, fluct_scale):
+    """The doublet with the vacuum fluctuations of its four canonical
+    components (Philox streams 0..3), before any charge is removed."""
     N = model.N
     dx = 2.0 * np.pi / (kIR * N)
     alpha = model.alpha
@@ -222,7 +218,24 @@ def su2_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_sca
         ddphi = dft_inverse(_project(Gd, conj, selfc, zero)).real
         phi[c] = pb[c] + dphi / np.sqrt(2.0)
         pi[c] = a ** (3.0 - alpha) * (db[c] + ddphi / np.sqrt(2.0))
-    # remove the total colour charges
+    return phi, pi, dx
+
+
+def _gauss_solve(N, dx, R):
+    """piX_i(n~) = conj(beta_i) R(n~) / sum_j |beta_j|^2 with beta_i =
+    (1 - e^{2 pi i n~_i/N})/dx, the solution of sum_i D_i^- piX_i = rho for
+    R = DFT(rho) with R(0) = 0; returns the three components in position space."""
+    m = mode_numbers(N)
+    nz, ny, nx = np.meshgrid(m, m, m, indexing="ij")
+    betas = [(1.0 - np.exp(2j * np.pi * cc / N)) / dx for cc in (nx, ny, nz)]
+    den = sum(np.abs(bb) ** 2 for bb in betas)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return [dft_inverse(np.where(den > 0, np.conj(bb) * R / den, 0.0)).real for bb in betas]
+
+
+def _su2_gauss_start(model, phi, pi, dx):
+    """Removes the total colour charges and solves the SU(2) Gauss law with unit links."""
+    N = model.N
     F1, F2 = phi[0] + 1j * phi[1], phi[2] + 1j * phi[3]
     P1, P2 = pi[0] + 1j * pi[1], pi[2] + 1j * pi[3]
     rho = _su2_charge(phi, pi)
@@ -232,19 +245,98 @@ def su2_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_sca
     pi = np.stack([P1.real, P1.imag, P2.real, P2.imag])
     rho = _su2_charge(phi, pi)
     # Gauss law with unit links, colour by colour
-    m = mode_numbers(N)
-    nz, ny, nx = np.meshgrid(m, m, m, indexing="ij")
-    betas = [(1.0 - np.exp(2j * np.pi * cc / N)) / dx for cc in (nx, ny, nz)]
-    den = sum(np.abs(bb) ** 2 for bb in betas)
     piB = np.zeros((3, 3, N, N, N))
     for ca in range(3):
-        R = dft_forward(model.g / model.kappa * rho[ca])
-        with np.errstate(divide="ignore", invalid="ignore"):
-            for i, bb in enumerate(betas):
-                piB[i, ca] = dft_inverse(np.where(den > 0, np.conj(bb) * R / den, 0.0)).real
+        for i, sol in enumerate(_gauss_solve(N, dx, dft_forward(model.g / model.kappa * rho[ca]))):
+            piB[i, ca] = sol
+    return phi, pi, piB
+
+
+def _singlet_draw(N, alpha, kIR, m2, H, seed, stream, omega_over_fstar, a, fluct_scale):
+    """Vacuum fluctuations of a real scalar of curvature m2 (section 7): the
+    Rayleigh moduli and uniform phases of the left- and right-moving waves of
+    every mode drawn on Philox stream `stream`; returns the fluctuation of the
+    field and of its program-time derivative in position space."""
+    dx = 2.0 * np.pi / (kIR * N)
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    k = kIR * nabs
+    w = _omega(k, a, m2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        T = np.where(zero, 0.0, (omega_over_fstar ** 2) * (N / dx) ** 3 / (2 * a * a * w))
+    T *= fluct_scale ** 2
+    u = philox.uniforms(lin, stream, 0, seed)
+    L = np.sqrt(-T * np.log(u[0]))
+    R = np.sqrt(-T * np.log(u[1]))
+    el = np.exp(2j * np.pi * u[2])
+    er = np.exp(2j * np.pi * u[3])
+    G = (L * el + R * er) / np.sqrt(2.0)
+    Gd = a ** (alpha - 1.0) * (1j * w / np.sqrt(2.0)) * (L * el - R * er) - H * G
+    return dft_inverse(_project(G, conj, selfc, zero)).real, dft_inverse(_project(Gd, conj, selfc, zero)).real
+
+
+def _generator(b, F1, F2):
+    """T_b Phi for T_0 = 1 (the U(1) charge) and the Pauli matrices T_1..3."""
+    return [(F1, F2), (F2, F1), (-1j * F2, 1j * F1), (F1, -F2)][b]
+
+
+def su2u1_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scale=1.0):
+    """Initial conditions of the SU(2) x U(1) doublet with a singlet (sections 7
+    and 8.3).  The doublet is drawn as in su2_ic.  With the U(1) sector
+    (model.eA != 0) the four total charges Q_b = sum_n Im[Phi^dag T_b pi] (T_0 = 1,
+    T_a = sigma^a) are removed together: pi -> pi - sum_b c_b i T_b Phi with
+    M c = Q, M_ab = sum_n Re[Phi^dag T_a T_b Phi] (the U(1) direction is not
+    orthogonal to the colour ones); without it the colour charges alone, as in
+    su2_ic.  The singlet chi (model.chi) has zero homogeneous mode and velocity
+    and the vacuum fluctuations of a real scalar of curvature 2 q |Phi|^2
+    (Philox stream 4).  Links start at unity, angles at zero; piB and piA solve
+    the two Gauss laws in Fourier space.  Returns (phi, pi, u, piB, theta, piA,
+    chi, pchi, dx)."""
+    N = model.N
+    phi, pi, dx = _doublet_draw(model, kIR, phibar, dphibar, seed, omega_over_fstar, a, fluct_scale)
+    chi = np.zeros((N, N, N))
+    pchi = np.zeros((N, N, N))
+    if model.chi:
+        s2 = sum(float(x) ** 2 for x in phibar[:4])
+        Vbar, _, _ = _charged_potential(model, s2)
+        EK0 = sum(float(d) ** 2 for d in dphibar[:4]) / a ** (2 * model.alpha)
+        H = np.sqrt(max(a ** (2 * model.alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
+        chi, dchi = _singlet_draw(N, model.alpha, kIR, 2.0 * model.q * s2, H, seed, 4, omega_over_fstar, a,
+                                  fluct_scale)
+        pchi = a ** (3.0 - model.alpha) * dchi
+    piA = np.zeros((3, N, N, N))
+    if model.eA == 0.0:
+        phi, pi, piB = _su2_gauss_start(model, phi, pi, dx)
+    else:
+        F1, F2 = phi[0] + 1j * phi[1], phi[2] + 1j * phi[3]
+        P1, P2 = pi[0] + 1j * pi[1], pi[2] + 1j * pi[3]
+
+        def charges(Q1, Q2):
+            out = []
+            for b in range(4):
+                G1, G2 = _generator(b, Q1, Q2)
+                out.append(np.imag(np.conj(F1) * G1 + np.conj(F2) * G2))
+            return np.stack(out)
+
+        M = np.zeros((4, 4))
+        for ia in range(4):
+            for ib in range(4):
+                G1, G2 = _generator(ib, F1, F2)
+                H1, H2 = _generator(ia, G1, G2)
+                M[ia, ib] = np.sum(np.real(np.conj(F1) * H1 + np.conj(F2) * H2))
+        c = np.linalg.solve(M, charges(P1, P2).sum(axis=(1, 2, 3)))
+        for b in range(4):
+            G1, G2 = _generator(b, F1, F2)
+            P1, P2 = P1 - c[b] * 1j * G1, P2 - c[b] * 1j * G2
+        pi = np.stack([P1.real, P1.imag, P2.real, P2.imag])
+        rho = charges(P1, P2)
+        piB = np.zeros((3, 3, N, N, N))
+        for ca in range(3):
+            for i, sol in enumerate(_gauss_solve(N, dx, dft_forward(model.g / model.kappa * rho[1 + ca]))):
+                piB[i, ca] = sol
+        piA = np.stack(_gauss_solve(N, dx, dft_forward(2.0 * model.eA / model.kappa * rho[0])))
     u = np.zeros((3, 4, N, N, N))
     u[:, 0] = 1.0
-    return phi, pi, u, piB, dx
+    return phi, pi, u, piB, np.zeros((3, N, N, N)), piA, chi, pchi, dx
 
 
 def _su2_charge(phi, pi):

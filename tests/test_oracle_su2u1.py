@@ -240,3 +240,35 @@ def test_su2u1_energy_conservation_static():
         lat.vv_steps(VV4, dt, int(round(0.8 / dt)))
         drift.append(abs(lat.energies().sum() - E0) / E0)
     assert drift[1] < 1e-6 and np.log2(drift[0] / drift[1]) > 3.0, drift
+
+
+def test_su2u1_vacuum_initial_conditions():
+    """The combined start: both Gauss laws at round-off with unit links, zero
+    angles and zero magnetic energies; without the U(1) sector it is the SU(2)
+    start; the singlet is the real-scalar draw of its curvature 2 q |Phi|^2 on
+    Philox stream 4 (section 7)."""
+    from oracle.ic import _singlet_draw, su2_ic, su2u1_ic
+    N, dx, omega = 16, 0.5, 0.3
+    kIR = 2 * np.pi / (N * dx)
+    pb = [0.4, 0.0, 0.0, 0.3]
+    m = SU2U1Model(N=N, dx=dx, alpha=1.0, fmp2=0.0, lam=1.0, g=1.2, kappa=omega ** 2, pot=1, p=4, eA=0.9, q=2.0)
+    phi, pi, u, piB, th, piA, chi, pchi, _ = su2u1_ic(m, kIR, pb, [0.0] * 4, seed=3, omega_over_fstar=omega)
+    lat = SU2U1Lattice(m, phi, pi, u, piB, th, piA, chi, pchi)
+    g = lat.gauss()
+    assert g[0] < 1e-28 and g[1] < 1e-28, g
+    E = lat.energies()
+    assert E[4] == 0.0 and E[6] == 0.0 and E[3] > 0 and E[5] > 0 and E[7] > 0 and E[8] > 0
+    assert np.max(np.abs(charges(phi, pi).sum(axis=(1, 2, 3)))) < 1e-10
+    # no U(1) sector: identical to the SU(2) start
+    m0 = SU2U1Model(N=N, dx=dx, alpha=1.0, fmp2=0.0, lam=1.0, g=1.2, kappa=omega ** 2, pot=1, p=4, eA=0.0, q=2.0)
+    phi0, pi0, _, piB0, _, piA0, _, _, _ = su2u1_ic(m0, kIR, pb, [0.0] * 4, seed=3, omega_over_fstar=omega)
+    sphi, spi, _, spiB, _ = su2_ic(m0.su2(), kIR, pb, [0.0] * 4, seed=3, omega_over_fstar=omega)
+    assert np.max(np.abs(phi0 - sphi)) == 0.0 and np.max(np.abs(pi0 - spi)) == 0.0
+    assert np.max(np.abs(piB0 - spiB)) == 0.0 and np.all(piA0 == 0.0)
+    # the singlet: zero mean, the real-scalar draw (the one scalar_ic makes, pinned
+    # by the shell statistics of the scalar initial conditions) of curvature
+    # 2 q |Phi|^2 = 1 on stream 4
+    assert abs(2 * m.q * sum(x * x for x in pb) - 1.0) < 1e-15
+    f, fd = _singlet_draw(N, 1.0, kIR, 1.0, 0.0, 3, 4, omega, 1.0, 1.0)
+    assert np.max(np.abs(f - chi)) == 0.0 and np.max(np.abs(fd - pchi)) == 0.0
+    assert abs(chi.mean()) < 1e-14 and chi.std() > 0.0
