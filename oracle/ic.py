@@ -274,66 +274,66 @@ def _singlet_draw(N, alpha, kIR, m2, H, seed, stream, omega_over_fstar, a, fluct
     return dft_inverse(_project(G, conj, selfc, zero)).real, dft_inverse(_project(Gd, conj, selfc, zero)).real
 
 
-def _generator(b, F1, F2):
-    """T_b Phi for T_0 = 1 (the U(1) charge) and the Pauli matrices T_1..3."""
-    return [(F1, F2), (F2, F1), (-1j * F2, 1j * F1), (F1, -F2)][b]
-
-
 def su2u1_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_scale=1.0):
     """Initial conditions of the SU(2) x U(1) doublet with a singlet (sections 7
-    and 8.3).  The doublet is drawn as in su2_ic.  With the U(1) sector
-    (model.eA != 0) the four total charges Q_b = sum_n Im[Phi^dag T_b pi] (T_0 = 1,
-    T_a = sigma^a) are removed together: pi -> pi - sum_b c_b i T_b Phi with
-    M c = Q, M_ab = sum_n Re[Phi^dag T_a T_b Phi] (the U(1) direction is not
-    orthogonal to the colour ones); without it the colour charges alone, as in
-    su2_ic.  The singlet chi (model.chi) has zero homogeneous mode and velocity
-    and the vacuum fluctuations of a real scalar of curvature 2 q |Phi|^2
-    (Philox stream 4).  Links start at unity, angles at zero; piB and piA solve
-    the two Gauss laws in Fourier space.  Returns (phi, pi, u, piB, theta, piA,
-    chi, pchi, dx)."""
+    and 8.3), with the charge constraints of section 7.2: every canonical
+    component sqrt(2) Phi_c of the doublet gets left- and right-moving waves
+    of one Rayleigh modulus (|l_c| = |r_c|) and phases with a common
+    difference, th_c^r = th_0^r + th_c^l - th_0^l, so that the zero modes of the
+    U(1) and the three SU(2) charges vanish mode by mode.  That cancellation
+    needs one frequency for all four components: they are drawn with the mean
+    of the four curvatures (each component's own when the homogeneous value is
+    split evenly over the components).  Draws: moduli from Philox counter
+    (mode, 0, 0), phases th_0^l, th_0^r, th_1^l, th_2^l from (mode, 0, 1) and th_3^l
+    from (mode, 0, 2).  The singlet chi (model.chi) has zero homogeneous mode
+    and velocity and the real-scalar fluctuations of curvature 2 q |Phi|^2
+    (Philox stream 4).  Links start at unity and angles at zero; piB and piA
+    solve the two Gauss laws in Fourier space.  Returns (phi, pi, u, piB,
+    theta, piA, chi, pchi, dx)."""
     N = model.N
-    phi, pi, dx = _doublet_draw(model, kIR, phibar, dphibar, seed, omega_over_fstar, a, fluct_scale)
+    dx = 2.0 * np.pi / (kIR * N)
+    alpha = model.alpha
+    pb = [float(x) for x in phibar[:4]]
+    db = [float(x) for x in dphibar[:4]]
+    s2 = sum(x * x for x in pb)
+    Vbar, dv, d2 = _charged_potential(model, s2)
+    m2 = float(np.mean([dv + d2 * 2.0 * pb[c] ** 2 for c in range(4)]))
+    EK0 = sum(d * d for d in db) / a ** (2 * alpha)
+    H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    k = kIR * nabs
+    w = _omega(k, a, m2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        T = np.where(zero, 0.0, (omega_over_fstar ** 2) * (N / dx) ** 3 / (2 * a * a * w))
+    T *= fluct_scale ** 2
+    u = philox.uniforms(lin, 0, 0, seed)
+    v = philox.uniforms(lin, 0, 1, seed)
+    x = philox.uniforms(lin, 0, 2, seed)
+    thl = [2 * np.pi * v[0], 2 * np.pi * v[2], 2 * np.pi * v[3], 2 * np.pi * x[0]]
+    th0r = 2 * np.pi * v[1]
+    phi = np.zeros((4, N, N, N))
+    pi = np.zeros((4, N, N, N))
+    for c in range(4):
+        A = np.sqrt(-T * np.log(u[c]))
+        el, er = np.exp(1j * thl[c]), np.exp(1j * (th0r + thl[c] - thl[0]))
+        G = A * (el + er) / np.sqrt(2.0)
+        Gd = a ** (alpha - 1.0) * (1j * w / np.sqrt(2.0)) * A * (el - er) - H * G
+        phi[c] = pb[c] + dft_inverse(_project(G, conj, selfc, zero)).real / np.sqrt(2.0)
+        pi[c] = a ** (3.0 - alpha) * (db[c] + dft_inverse(_project(Gd, conj, selfc, zero)).real / np.sqrt(2.0))
     chi = np.zeros((N, N, N))
     pchi = np.zeros((N, N, N))
     if model.chi:
-        s2 = sum(float(x) ** 2 for x in phibar[:4])
-        Vbar, _, _ = _charged_potential(model, s2)
-        EK0 = sum(float(d) ** 2 for d in dphibar[:4]) / a ** (2 * model.alpha)
-        H = np.sqrt(max(a ** (2 * model.alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))
-        chi, dchi = _singlet_draw(N, model.alpha, kIR, 2.0 * model.q * s2, H, seed, 4, omega_over_fstar, a,
-                                  fluct_scale)
-        pchi = a ** (3.0 - model.alpha) * dchi
+        chi, dchi = _singlet_draw(N, alpha, kIR, 2.0 * model.q * s2, H, seed, 4, omega_over_fstar, a, fluct_scale)
+        pchi = a ** (3.0 - alpha) * dchi
+    rho = _su2_charge(phi, pi)
+    piB = np.zeros((3, 3, N, N, N))
+    for ca in range(3):
+        for i, sol in enumerate(_gauss_solve(N, dx, dft_forward(model.g / model.kappa * rho[ca]))):
+            piB[i, ca] = sol
     piA = np.zeros((3, N, N, N))
-    if model.eA == 0.0:
-        phi, pi, piB = _su2_gauss_start(model, phi, pi, dx)
-    else:
-        F1, F2 = phi[0] + 1j * phi[1], phi[2] + 1j * phi[3]
-        P1, P2 = pi[0] + 1j * pi[1], pi[2] + 1j * pi[3]
-
-        def charges(Q1, Q2):
-            out = []
-            for b in range(4):
-                G1, G2 = _generator(b, Q1, Q2)
-                out.append(np.imag(np.conj(F1) * G1 + np.conj(F2) * G2))
-            return np.stack(out)
-
-        M = np.zeros((4, 4))
-        for ia in range(4):
-            for ib in range(4):
-                G1, G2 = _generator(ib, F1, F2)
-                H1, H2 = _generator(ia, G1, G2)
-                M[ia, ib] = np.sum(np.real(np.conj(F1) * H1 + np.conj(F2) * H2))
-        c = np.linalg.solve(M, charges(P1, P2).sum(axis=(1, 2, 3)))
-        for b in range(4):
-            G1, G2 = _generator(b, F1, F2)
-            P1, P2 = P1 - c[b] * 1j * G1, P2 - c[b] * 1j * G2
-        pi = np.stack([P1.real, P1.imag, P2.real, P2.imag])
-        rho = charges(P1, P2)
-        piB = np.zeros((3, 3, N, N, N))
-        for ca in range(3):
-            for i, sol in enumerate(_gauss_solve(N, dx, dft_forward(model.g / model.kappa * rho[1 + ca]))):
-                piB[i, ca] = sol
-        piA = np.stack(_gauss_solve(N, dx, dft_forward(2.0 * model.eA / model.kappa * rho[0])))
+    if model.eA != 0.0:
+        rho0 = phi[0] * pi[1] - phi[1] * pi[0] + phi[2] * pi[3] - phi[3] * pi[2]  # Im[Phi^dag pi]
+        piA = np.stack(_gauss_solve(N, dx, dft_forward(2.0 * model.eA / model.kappa * rho0)))
     u = np.zeros((3, 4, N, N, N))
     u[:, 0] = 1.0
     return phi, pi, u, piB, np.zeros((3, N, N, N)), piA, chi, pchi, dx
