@@ -61,6 +61,17 @@ typedef enum {
  *   init->spectrum) vacuum fluctuations of every canonical component sqrt(2) Phi_c,
  *   the total colour charges projected out of pi, and electric momenta from
  *   the Gauss law.
+ *   SU(2) x U(1) + chi (the working example of section 8.3): gauge_e_u1 > 0
+ *   also charges the doublet under a compact U(1) (link angles CL_LINK(i),
+ *   electric momenta CL_EMOMENTUM(i); the parallel transporter of Phi is
+ *   exp(-i theta_i) U_i) and n_fields = 2 adds a real singlet chi
+ *   (CL_SINGLET, CL_SINGLET_MOMENTUM) with V_int = q |Phi|^2 chi^2.  Such a
+ *   model starts from the constrained vacuum draws of section 7.2 (|l| = |r|
+ *   per component, one l-r phase difference and one frequency, the mean
+ *   curvature of the four components, for all of them), which leave no U(1)
+ *   or SU(2) charge; chi starts with zero mean and velocity and the
+ *   fluctuations of curvature 2 q |Phi|^2; both Gauss laws are solved for the
+ *   electric momenta.  Energies are reported per sector (lattice_measure_means).
  * CL_MODEL_SCALAR: n_fields = 1 or 2 real singlets phi, chi with the program
  *   potential of section 8.1, V = (lam/p)|phi|^p + (q/2) phi^2 chi^2.
  * CL_MODEL_U1: one complex scalar phi = (phi_0 + i phi_1)/sqrt(2) with
@@ -129,7 +140,8 @@ typedef struct {
     double fluid_w;          /* CL_BG_FLUID: equation of state w of the fluid */
     double hubble0;          /* CL_BG_FLUID: program Hubble rate a'/a at t = 0 */
     int32_t potential;       /* U(1), SU(2): cl_gauge_potential */
-    int32_t reserved;        /* must be 0 */
+    int32_t reserved;        /* set to 0 */
+    double gauge_e_u1;       /* SU(2): U(1) coupling eA = g_A Q_A of the doublet (section 8.3); 0: no U(1) sector */
 } cl_model;
 
 typedef struct {
@@ -160,13 +172,14 @@ typedef struct {
     double mean2[4];       /* <f_c^2> */
     double var[4];         /* <f_c^2> - <f_c>^2 */
     double mean_pi[4];     /* <pi_c> */
-    double EK[4];          /* scalar: E_K per field; U(1): {E_K^phi, E_K^A} */
-    double EG[4];          /* scalar: E_G per field; U(1): {E_G^phi, E_G^A} */
-    double EV[4];          /* scalar: {<(lam/p)|phi|^p>, <(q/2)phi^2chi^2>}; U(1): {<V>} */
+    double EK[4];          /* scalar: E_K per field; U(1): {E_K^phi, E_K^A}; SU(2): {E_K^Phi, E_K^B, E_K^A, E_K^chi} */
+    double EG[4];          /* scalar: E_G per field; U(1): {E_G^phi, E_G^A}; SU(2): {E_G^Phi, E_G^B, E_G^A, E_G^chi} */
+    double EV[4];          /* scalar: {<(lam/p)|phi|^p>, <(q/2)phi^2chi^2>}; U(1): {<V>};
+                              SU(2): {<V(|Phi|^2) + q |Phi|^2 chi^2>} */
     double rho;            /* total energy density E_K + E_G + E_V (program units) */
     double w;              /* equation of state p/rho */
     double hubble_violation; /* Delta_e = |b^2 - rhs| / rhs of the Hubble constraint */
-    double gauss_violation;  /* U(1): Delta_g = rms(G)/sqrt(<lhs^2> + <rhs^2>) */
+    double gauss_violation;  /* U(1), SU(2): Delta_g = rms(G)/sqrt(<lhs^2> + <rhs^2>), sums over every Gauss law */
     double reserved[4];
 } cl_means;
 
@@ -208,7 +221,8 @@ int32_t lattice_spectrum_bins(const cl_lattice* h);
  * Delta(k) = k^3/(2 pi^2) (dx/N)^3 <|f(n~)|^2>_R, averaged over the modes of
  * each shell |n~| in [b, b+1), with k_b = k_IR times the mean |n~| of the
  * shell.  field: scalar field index, or 0 for the complex U(1) scalar (Re and
- * Im summed).  what: 0 the field, 1 its momentum.  k, Delta (double) and
+ * Im summed), or for SU(2) 0 the doublet (four components summed) and 1 the
+ * singlet chi.  what: 0 the field, 1 its momentum.  k, Delta (double) and
  * counts (int64) have lattice_spectrum_bins() entries (host memory).
  * Synchronizes the stream. */
 cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, double* k, double* Delta,
@@ -224,6 +238,11 @@ cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, d
 #define CL_EMOMENTUM(i) (12 + (i))
 #define CL_SU2_LINK(i, c) (16 + 4 * (i) + (c))     /* quaternion component c of U_i */
 #define CL_SU2_EMOMENTUM(i, a) (28 + 3 * (i) + (a)) /* piB_i^a */
+/* CL_MODEL_SU2 with gauge_e_u1 > 0: the U(1) link angles and electric momenta
+ * of the doublet are CL_LINK(i) and CL_EMOMENTUM(i); with n_fields = 2 the
+ * real singlet chi and its momentum: */
+#define CL_SINGLET 37
+#define CL_SINGLET_MOMENTUM 38
 
 /* Copy the full array `which` (N^3 doubles) to dst: host memory when
  * on_device = 0, device memory of the handle's device otherwise.

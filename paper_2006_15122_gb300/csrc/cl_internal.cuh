@@ -76,6 +76,10 @@ struct ModelConst {
     int bg;
     double bg_p, bg_H0, bg_a0;
     int gpot;  // charged-scalar potential of the gauge models (cl_gauge_potential)
+    // SU(2) x U(1) + chi: U(1) coupling of the doublet (0: none), singlet present,
+    // and ext = either of the two (the 37-array layout)
+    double e2;
+    int chi, ext;
 };
 
 // Potential of the charged scalar of the gauge models as a function of

@@ -13,7 +13,8 @@ namespace cl {
 
 int array_count(const ModelConst& mc) {
     if (mc.kind == CL_MODEL_SCALAR) return 2 * mc.nf;
-    return mc.kind == CL_MODEL_SU2 ? 29 : 10;
+    if (mc.kind == CL_MODEL_SU2) return mc.ext ? 37 : 29;
+    return 10;
 }
 
 int array_slot(const ModelConst& mc, int which) {
@@ -26,6 +27,10 @@ int array_slot(const ModelConst& mc, int which) {
         if (which >= 0 && which < 8) return which;
         if (which >= 16 && which < 28) return which - 8;
         if (which >= 28 && which < 37) return which - 8;
+        // U(1) angles 29-31, piA 32-34, chi 35, pchi 36
+        if (mc.e2 > 0 && which >= 8 && which <= 10) return 29 + which - 8;
+        if (mc.e2 > 0 && which >= 12 && which <= 14) return 32 + which - 12;
+        if (mc.chi && (which == 37 || which == 38)) return 35 + which - 37;
         return -1;
     }
     if (which == 0 || which == 1) return which;

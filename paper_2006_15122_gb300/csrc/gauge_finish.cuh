@@ -19,14 +19,28 @@ static __device__ double Ka_u1(const ModelConst& mc, double a, double EKp, doubl
            ((mc.alpha - 2.0) * EKp + mc.alpha * EGp + (mc.alpha + 1.0) * EV + (mc.alpha - 1.0) * (EKA + EGA));
 }
 
-static __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc, const PassInfo& pi) {
+// SU(2) x U(1) + chi (ns = 15) adds {<sum piA_sync^2>, <sum_{i<j} (1 - cos theta_ij)>,
+// <pchi_sync^2>, <sum_i (D_i^+ chi)^2>/dx^2}; the background update then sees the
+// scalar sectors (Phi, chi) and the gauge sectors (SU(2), U(1)) in aggregate,
+// which is exact because every energy of one class scales with the same power
+// of a (chi's kinetic and gradient energies carry the 1/2 of a real field).
+static __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc, const PassInfo& pi,
+                                 int ns = U1NS) {
     const double a = st->a, a2 = a * a, a4 = a2 * a2, a6 = a4 * a2;
     const double dx4 = mc.dx * mc.dx * mc.dx * mc.dx;
-    const double Sp = tot[6], SA = tot[9];
-    const double EKp = Sp / a6, EGp = tot[7] / a2, EV = tot[8];
-    const double EKA = mc.kappa * SA / (2.0 * a4), EGA = mc.kappa * tot[10] / (a4 * mc.e * mc.e * dx4);
+    double Sp = tot[6], SA = tot[9], SG = tot[7], SM = tot[10] / (mc.e * mc.e);
+    if (ns > U1NS) {
+        Sp += 0.5 * tot[13];
+        SG += 0.5 * tot[14];
+        if (mc.e2 > 0) {
+            SA += tot[11];
+            SM += tot[12] / (mc.e2 * mc.e2);
+        }
+    }
+    const double EKp = Sp / a6, EGp = SG / a2, EV = tot[8];
+    const double EKA = mc.kappa * SA / (2.0 * a4), EGA = mc.kappa * SM / (a4 * dx4);
     st->E[0] = EKp; st->E[1] = EGp; st->E[2] = EV; st->E[3] = EKA; st->E[4] = EGA;
-    for (int s = 0; s < U1NS; ++s) st->sums[s] = tot[s];
+    for (int s = 0; s < ns; ++s) st->sums[s] = tot[s];
     const double Et = EKp + EGp + EV + EKA + EGA;
     if (!isfinite(Et)) { st->error = CL_ERR_NONFINITE; return; }
     auto rhs = [&](double aa, double E) { return mc.fmp2 / 3.0 * pow(aa, 2.0 * (mc.alpha + 1.0)) * E; };

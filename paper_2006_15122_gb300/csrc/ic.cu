@@ -16,7 +16,12 @@
 //
 // Charged scalar with U(1) (section 7.2): the two real components of
 // phi = (phi_0 + i phi_1)/sqrt(2) use |l_n| = |r_n| and
-// th_1r = th_0r + th_1l - th_0l, so that the total charge vanishes; the links
+// th_1r = th_0r + th_1l - th_0l, so that the total charge vanishes.  The
+// doublet of SU(2) x U(1) + chi does the same for its four components
+// (th_c^r = th_0^r + th_c^l - th_0^l; moduli from counter (mode, 0, 0), th_0^l,
+// th_0^r, th_1^l, th_2^l from (mode, 0, 1), th_3^l from (mode, 0, 2)) with one
+// frequency for all of them, which zeroes the U(1) and the three SU(2)
+// charges mode by mode.  The links
 // start at unity and the electric momenta solve the lattice Gauss law
 // sum_i D_i^- piA_i = (2e/kappa) Im[phi* pi] in Fourier space with the
 // backward lattice momentum (forward exponent -: gamma_i = (1 - e^{-2 pi i k_i/N})/dx).
@@ -30,7 +35,8 @@ struct ICParams {
     int N;
     int stream;   // Philox stream (field index)
     int which;    // 0: field, 1: program-time derivative
-    int u1comp;   // -1 scalar singlet; 0/1 component of the charged scalar
+    int u1comp;   // -1 scalar singlet; else the component of the charged scalar (0/1) or doublet (0..3)
+    int doublet;  // the doublet's constrained draws (SU(2) x U(1) + chi)
     double kIR, a, alpha, H;
     double T0;    // (w*/f*)^2 (N/dx)^3 / (2 a^2) * fluct_scale^2
     double m2;    // |m^2| of this component
@@ -70,6 +76,18 @@ __global__ void ic_modes_kernel(double2* X, ICParams P) {
             R = sqrt(-T * log(u01(c[1])));
             thl = 2.0 * M_PI * u01(c[2]);
             thr = 2.0 * M_PI * u01(c[3]);
+        } else if (P.doublet) {
+            // |l_c| = |r_c|; th_c^r = th_0^r + th_c^l - th_0^l
+            uint32_t d[4] = {(uint32_t)(lin & 0xffffffffu), (uint32_t)(lin >> 32), 0u, 1u};
+            uint32_t e[4] = {(uint32_t)(lin & 0xffffffffu), (uint32_t)(lin >> 32), 0u, 2u};
+            philox4x32_10(d, P.k0, P.k1);
+            philox4x32_10(e, P.k0, P.k1);
+            const double th0l = 2.0 * M_PI * u01(d[0]), th0r = 2.0 * M_PI * u01(d[1]);
+            const int cc = P.u1comp;
+            const double tl = cc == 0 ? th0l : 2.0 * M_PI * u01(cc == 1 ? d[2] : (cc == 2 ? d[3] : e[0]));
+            L = R = sqrt(-T * log(u01(c[cc])));
+            thl = tl;
+            thr = th0r + tl - th0l;
         } else {
             // |l_n| = |r_n|; th_1r = th_0r + th_1l - th_0l
             uint32_t d[4] = {(uint32_t)(lin & 0xffffffffu), (uint32_t)(lin >> 32), 0u, 1u};
@@ -166,6 +184,17 @@ __global__ void su2_uncharge_kernel(Su2Ptrs P, size_t n, const double* partials,
     }
 }
 
+// (2 eA/kappa) Im[Phi^dag pi] of the doublet into a real FP64 array
+template <typename T>
+__global__ void su2_u1_charge_kernel(const Su2Ptrs P, double* rho, size_t n, double c) {
+    const T* const* b = reinterpret_cast<const T* const*>(P.b);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double f0 = b[0][i], f1 = b[1][i], f2 = b[2][i], f3 = b[3][i];
+        const double p0 = b[4][i], p1 = b[5][i], p2 = b[6][i], p3 = b[7][i];
+        rho[i] = c * (f0 * p1 - f1 * p0 + f2 * p3 - f3 * p2);
+    }
+}
+
 // (g/kappa) Im[Phi^dag sigma^a pi] into a real FP64 array
 template <typename T>
 __global__ void su2_charge_kernel(const Su2Ptrs P, double* rho, size_t n, int a, double c) {
@@ -256,7 +285,7 @@ cl_status ic_generate(Lattice* L) {
                     if (cudaMemsetAsync(dst, 0, n * L->tsize, s) != cudaSuccess) return CL_ERR_CUDA;
                     continue;
                 }
-                ICParams P;
+                ICParams P{};
                 P.N = N; P.stream = f; P.which = which; P.u1comp = -1;
                 P.kIR = L->grid.kIR; P.a = a; P.alpha = mc.alpha; P.H = H;
                 P.T0 = base; P.m2 = fabs(m2[f]);
@@ -288,11 +317,17 @@ cl_status ic_generate(Lattice* L) {
             const double Vb = gauge_pot<double>(mc.gpot, mc.pexp, mc.lam, mc.vev2, s2, &dvb);
             const double H = sqrt(fmax(pow(a, 2.0 * mc.alpha) / 3.0 * mc.fmp2 * (EK0 + Vb), 0.0));
             void** b = L->buf.f[L->cur];
+            // SU(2) x U(1) + chi: the constrained draws share the mean curvature of the components
+            double m2mean = 0.0;
+            for (int c = 0; c < 4; ++c)
+                m2mean += gauge_curvature(mc.gpot, mc.pexp, mc.lam, mc.vev2, s2, 1.4142135623730951 * in.phi0[c]);
+            m2mean /= 4.0;
             for (int c = 0; c < 4; ++c) {
-                const double m2 = gauge_curvature(mc.gpot, mc.pexp, mc.lam, mc.vev2, s2, 1.4142135623730951 * in.phi0[c]);
+                const double m2 = mc.ext ? m2mean
+                                         : gauge_curvature(mc.gpot, mc.pexp, mc.lam, mc.vev2, s2, 1.4142135623730951 * in.phi0[c]);
                 for (int which = 0; which < 2; ++which) {
-                    ICParams P;
-                    P.N = N; P.stream = c; P.which = which; P.u1comp = -1;
+                    ICParams P{};
+                    P.N = N; P.stream = c; P.which = which; P.u1comp = mc.ext ? c : -1; P.doublet = mc.ext;
                     P.kIR = L->grid.kIR; P.a = a; P.alpha = mc.alpha; P.H = H;
                     P.T0 = base; P.m2 = fabs(m2);
                     P.k0 = (uint32_t)(in.seed & 0xffffffffu); P.k1 = (uint32_t)(in.seed >> 32);
@@ -305,10 +340,27 @@ cl_status ic_generate(Lattice* L) {
                     else store_u1_kernel<double><<<grid, 256, 0, s>>>(L->work, (double*)dst, n, scale, ad);
                 }
             }
+            if (mc.chi) {  // the singlet: zero mean and velocity, curvature 2 q |Phi|^2, Philox stream 4
+                for (int which = 0; which < 2; ++which) {
+                    ICParams P{};
+                    P.N = N; P.stream = 4; P.which = which; P.u1comp = -1;
+                    P.kIR = L->grid.kIR; P.a = a; P.alpha = mc.alpha; P.H = H;
+                    P.T0 = base; P.m2 = fabs(2.0 * mc.q * s2);
+                    P.k0 = (uint32_t)(in.seed & 0xffffffffu); P.k1 = (uint32_t)(in.seed >> 32);
+                    ic_modes_kernel<<<grid, 256, 0, s>>>((double2*)L->cwork, P);
+                    if (z2d(L) != cudaSuccess) return CL_ERR_CUDA;
+                    const double scale = (which == 0 ? 1.0 : pow(a, 3.0 - mc.alpha)) / (double)n;
+                    void* dst = b[35 + which];
+                    if (L->prec == CL_FP32) store_real_kernel<float><<<grid, 256, 0, s>>>(L->work, (float*)dst, n, scale);
+                    else store_real_kernel<double><<<grid, 256, 0, s>>>(L->work, (double*)dst, n, scale);
+                }
+            }
             Su2Ptrs P;
             for (int k = 0; k < 8; ++k) P.b[k] = b[k];
             const int cg = L->sm_count * 4;
-            if (L->prec == CL_FP32) {
+            if (mc.ext) {
+                // no projection: the constrained draws carry no charge
+            } else if (L->prec == CL_FP32) {
                 su2_charge_sums_kernel<float><<<cg, 256, 0, s>>>(P, n, L->buf.partials);
                 su2_uncharge_kernel<float><<<grid, 256, 0, s>>>(P, n, L->buf.partials, cg);
             } else {
@@ -318,6 +370,18 @@ cl_status ic_generate(Lattice* L) {
             double2* Rk = (double2*)L->cwork;
             const size_t nh = (size_t)N * N * (N / 2 + 1);
             double2* Yk = Rk + nh;
+            if (mc.e2 > 0) {  // U(1) Gauss law sum_i D_i^- piA_i = (2 eA/kappa) Im[Phi^dag pi]
+                if (L->prec == CL_FP32) su2_u1_charge_kernel<float><<<grid, 256, 0, s>>>(P, L->work, n, 2.0 * mc.e2 / mc.kappa);
+                else su2_u1_charge_kernel<double><<<grid, 256, 0, s>>>(P, L->work, n, 2.0 * mc.e2 / mc.kappa);
+                if (cufftExecD2Z(L->plan_r2c, L->work, (cufftDoubleComplex*)Rk) != CUFFT_SUCCESS) return CL_ERR_CUDA;
+                for (int i = 0; i < 3; ++i) {
+                    u1_gauss_solve_kernel<<<grid, 256, 0, s>>>(Rk, Yk, N, dx, i);
+                    if (cufftExecZ2D(L->plan_c2r, (cufftDoubleComplex*)Yk, L->work) != CUFFT_SUCCESS) return CL_ERR_CUDA;
+                    void* dst = b[32 + i];
+                    if (L->prec == CL_FP32) store_real_kernel<float><<<grid, 256, 0, s>>>(L->work, (float*)dst, n, 1.0);
+                    else store_real_kernel<double><<<grid, 256, 0, s>>>(L->work, (double*)dst, n, 1.0);
+                }
+            }
             for (int ca = 0; ca < 3; ++ca) {
                 if (L->prec == CL_FP32) su2_charge_kernel<float><<<grid, 256, 0, s>>>(P, L->work, n, ca, mc.e / mc.kappa);
                 else su2_charge_kernel<double><<<grid, 256, 0, s>>>(P, L->work, n, ca, mc.e / mc.kappa);
@@ -348,7 +412,7 @@ cl_status ic_generate(Lattice* L) {
                 if (!in.spectrum) {
                     cudaMemsetAsync(L->work, 0, n * sizeof(double), s);
                 } else {
-                    ICParams P;
+                    ICParams P{};
                     P.N = N; P.stream = 0; P.which = which; P.u1comp = comp;
                     P.kIR = L->grid.kIR; P.a = a; P.alpha = mc.alpha; P.H = H;
                     P.T0 = base; P.m2 = fabs(m2);

@@ -308,6 +308,18 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         if (model->potential == CL_POT_MONOMIAL && model->pexp != 2 && model->pexp != 4 && model->pexp != 6)
             return fail(nullptr, CL_ERR_ARG, "pexp must be 2, 4 or 6");
         if (model->kind == CL_MODEL_SU2) {
+            if (model->n_fields != 1 && model->n_fields != 2)
+                return fail(nullptr, CL_ERR_ARG, "SU(2): n_fields is 1, or 2 with the singlet chi");
+            if (!(model->gauge_e_u1 >= 0) || !isfinite(model->gauge_e_u1))
+                return fail(nullptr, CL_ERR_ARG, "gauge_e_u1 must be >= 0");
+            // ... and the U(1) charge Im[Phi^dag pi]
+            if (model->gauge_e_u1 > 0) {
+                const double* f = init->phi0;
+                const double* p = init->dphi0;
+                const double q0 = f[0] * p[1] - f[1] * p[0] + f[2] * p[3] - f[3] * p[2];
+                if (fabs(q0) > 1e-12 * (1.0 + fabs(f[0]) + fabs(f[1]) + fabs(f[2]) + fabs(f[3])))
+                    return fail(nullptr, CL_ERR_ARG, "the homogeneous U(1) charge Im[Phi^dag Phi'] must vanish");
+            }
             // a uniform charge Im[Phi^dag sigma^a pi] cannot satisfy the Gauss law on a periodic lattice
             const double* f = init->phi0;
             const double* p = init->dphi0;
@@ -367,6 +379,9 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     mc.dx = 2.0 * M_PI / (grid->kIR * N);
     mc.idx2 = 1.0 / (mc.dx * mc.dx);
     mc.gpot = mc.kind == CL_MODEL_SCALAR ? 0 : model->potential;
+    mc.e2 = mc.kind == CL_MODEL_SU2 ? model->gauge_e_u1 : 0.0;
+    mc.chi = mc.kind == CL_MODEL_SU2 && model->n_fields == 2 ? 1 : 0;
+    mc.ext = mc.e2 > 0 || mc.chi ? 1 : 0;
     mc.bg = model->background == CL_BG_FLUID ? 1 : 0;
     mc.bg_p = mc.bg ? 2.0 / (3.0 * (1.0 + model->fluid_w) - 2.0 * model->alpha) : 1.0;
     mc.bg_H0 = mc.bg ? model->hubble0 : 0.0;
@@ -385,7 +400,10 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         } else if (mc.kind == CL_MODEL_SU2) {
             double s2 = 0.0;
             for (int c = 0; c < 4; ++c) s2 += init->phi0[c] * init->phi0[c];
-            m2 = gauge_m2_bound(mc, s2) + mc.e * mc.e * s2 / (2.0 * mc.kappa);
+            // gauge masses g^2 |Phi|^2/(2 kappa) and (U(1)) 2 eA^2 |Phi|^2/kappa bound the mixed mass matrix;
+            // the singlet's curvature is 2 q |Phi|^2
+            m2 = gauge_m2_bound(mc, s2) + mc.e * mc.e * s2 / (2.0 * mc.kappa) + 2.0 * mc.e2 * mc.e2 * s2 / mc.kappa;
+            if (mc.chi) m2 = std::max(m2, fabs(2.0 * mc.q * s2));
         } else {
             const double s2 = 0.5 * (init->phi0[0] * init->phi0[0] + init->phi0[1] * init->phi0[1]);
             m2 = gauge_m2_bound(mc, s2) + 2.0 * mc.e * mc.e * s2 / mc.kappa;
@@ -564,6 +582,24 @@ cl_status lattice_measure_means(cl_lattice* h, cl_means* out) {
         out->EK[0] = EKp; out->EK[1] = EKA;
         out->EG[0] = st.E[1]; out->EG[1] = st.E[4];
         out->EV[0] = st.E[2];
+        if (h->mc.ext) {
+            // per sector from the sums of the last pass (st.E holds the scalar and gauge aggregates);
+            // under the leapfrog the kinetic entries EK[0], EK[1] keep the aggregates at t - dt/2
+            const cl::ModelConst& mc = h->mc;
+            const double a = st.a, a2 = a * a, a4 = a2 * a2, a6 = a4 * a2, dx4 = mc.dx * mc.dx * mc.dx * mc.dx;
+            const double* S = st.sums;
+            if (!h->staggered) {
+                out->EK[0] = S[6] / a6;
+                out->EK[1] = mc.kappa * S[9] / (2.0 * a4);
+                out->EK[2] = mc.e2 > 0 ? mc.kappa * S[11] / (2.0 * a4) : 0.0;
+                out->EK[3] = mc.chi ? 0.5 * S[13] / a6 : 0.0;
+            }
+            out->EG[0] = S[7] / a2;
+            out->EG[1] = mc.kappa * S[10] / (a4 * mc.e * mc.e * dx4);
+            out->EG[2] = mc.e2 > 0 ? mc.kappa * S[12] / (a4 * mc.e2 * mc.e2 * dx4) : 0.0;
+            out->EG[3] = mc.chi ? 0.5 * S[14] / a2 : 0.0;
+            out->EV[0] = st.E[2];
+        }
         out->rho = EKp + EKA + st.E[1] + st.E[2] + st.E[4];
         // scalar p = K - G/3 - V; gauge radiation p = (E_K^A + E_G^A)/3
         const double p = EKp - st.E[1] / 3.0 - st.E[2] + (EKA + st.E[4]) / 3.0;
@@ -603,8 +639,12 @@ cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, d
         if (field < 0 || field >= h->mc.nf) return fail(h, CL_ERR_ARG, "field index out of range");
         slots.push_back(what == 0 ? field : h->mc.nf + field);
     } else if (h->mc.kind == CL_MODEL_SU2) {  // the doublet: spectra summed over its four components
-        if (field != 0) return fail(h, CL_ERR_ARG, "the SU(2) model has one doublet (index 0)");
-        for (int c = 0; c < 4; ++c) slots.push_back(what == 0 ? c : 4 + c);
+        if (field == 1 && h->mc.chi) {
+            slots.push_back(what == 0 ? 35 : 36);  // the singlet
+        } else {
+            if (field != 0) return fail(h, CL_ERR_ARG, "the SU(2) model has one doublet (index 0) and the singlet (1)");
+            for (int c = 0; c < 4; ++c) slots.push_back(what == 0 ? c : 4 + c);
+        }
     } else {
         if (field != 0) return fail(h, CL_ERR_ARG, "the U(1) model has one complex field (index 0)");
         slots.push_back(what == 0 ? 0 : 2);
@@ -724,6 +764,8 @@ extern "C" cl_status lattice_save(cl_lattice* h, const char* path) {
     hd.model.fstar_over_mp = sqrt(h->mc.fmp2);
     hd.model.omega_over_fstar = sqrt(h->mc.kappa);
     hd.model.potential = h->mc.gpot;
+    hd.model.gauge_e_u1 = h->mc.e2;
+    if (h->mc.kind == CL_MODEL_SU2) hd.model.n_fields = h->mc.chi ? 2 : 1;
     hd.steps = h->steps_done;
     hd.nbytes = st.size() + (uint64_t)h->buf.narr * arr.size();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -755,7 +797,8 @@ extern "C" cl_status lattice_restore(cl_lattice* h, const char* path) {
         return fail(h, CL_ERR_IO, "not a lattice checkpoint");
     }
     if (hd.prec != h->prec || hd.narr != h->buf.narr || hd.grid.N != h->mc.N || hd.model.kind != h->mc.kind ||
-        hd.model.n_fields != h->mc.nf || hd.grid.integrator != h->integ) {
+        hd.model.n_fields != (h->mc.kind == CL_MODEL_SU2 ? (h->mc.chi ? 2 : 1) : h->mc.nf) ||
+        hd.grid.integrator != h->integ) {
         fclose(fp);
         return fail(h, CL_ERR_IO, "checkpoint of another geometry, model, integrator or precision");
     }

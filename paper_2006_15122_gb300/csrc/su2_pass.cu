@@ -19,6 +19,21 @@
 // volume sums and runs the FP64 background update in its last block, shared
 // with the U(1) sector.  Array slots: 0-3 Phi (Re/Im of the two components),
 // 4-7 pi, 8-19 links (4 i + c), 20-28 piB (3 i + a).
+//
+// SU(2) x U(1) + chi (section 8.3; the EXT kernels): the doublet also carries
+// a U(1) charge eA (link angles theta_i, V_i = exp(-i theta_i), electric
+// momenta piA_i; slots 29-31, 32-34) and couples to a real singlet chi (slots
+// 35, 36) through V_int = q |Phi|^2 chi^2.  The transporter of Phi becomes
+// W_i = V_i U_i, and
+//   K_Phi  = -a^{3+alpha}(V' + q chi^2) Phi + a^{1+alpha} sum_i (W_i Phi(n+i) - 2 Phi + W_i^dag(n-i) Phi(n-i))/dx^2,
+//   K_B    as above with W_i Phi(n+i) in the current,
+//   K_A,i  = a^{1+alpha}(2 eA/(kappa dx)) Im[Phi^dag W_i Phi(n+i)]
+//            + a^{alpha-1}/(eA dx^3) sum_{j!=i} [sin theta_ij(n-j) - sin theta_ij(n)],
+//   K_chi  = -a^{3+alpha} 2 q |Phi|^2 chi + a^{1+alpha} L[chi],
+// theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n); the U(1)
+// Gauss law is (1/dx) sum_i [piA_i(n) - piA_i(n-i)] = (2 eA/kappa) Im[Phi^dag pi].
+// Four more volume sums (sync piA^2, sum_{i<j} (1 - cos theta_ij), sync pchi^2,
+// grad chi^2) enter the shared background update.
 #include <math.h>
 
 #include "cl_internal.cuh"
@@ -26,7 +41,8 @@
 
 namespace cl {
 
-constexpr int kSu2Arrays = 29;
+constexpr int kSu2Arrays = 37;  // 29 without the U(1) sector and the singlet
+constexpr int kSu2ExtNS = 15;   // volume sums of the EXT kernels
 
 struct Su2Args {
     void* a[kSu2Arrays];  // kick: the copy updated in place
@@ -64,6 +80,26 @@ template <typename T> __device__ __forceinline__ void im_sigma(const T* x, const
 
 __device__ __forceinline__ void half_sincos(float t, float* s, float* c) { sincosf(0.5f * t, s, c); }
 __device__ __forceinline__ void half_sincos(double t, double* s, double* c) { sincos(0.5 * t, s, c); }
+
+// U(1) phases: FP32 takes the hardware approximation on wrapped angles (sums of
+// at most four angles in [-pi, pi]), as the compact U(1) sector does
+__device__ __forceinline__ void phase_sc(float t, float* s, float* c) { __sincosf(t, s, c); }
+__device__ __forceinline__ void phase_sc(double t, double* s, double* c) { sincos(t, s, c); }
+template <typename T> __device__ __forceinline__ T wrap_phase(T t) {
+    const T twopi = T(6.283185307179586476925287);
+    return t - twopi * rint(t / twopi);
+}
+// (a + i b) -> e^{-i t}(a + i b) on both components of a doublet, given (sin t, cos t)
+template <typename T> __device__ __forceinline__ void phase_minus(T* v, T s, T c) {
+    const T v0 = c * v[0] + s * v[1], v1 = c * v[1] - s * v[0];
+    const T v2 = c * v[2] + s * v[3], v3 = c * v[3] - s * v[2];
+    v[0] = v0; v[1] = v1; v[2] = v2; v[3] = v3;
+}
+template <typename T> __device__ __forceinline__ void phase_plus(T* v, T s, T c) { phase_minus(v, -s, c); }
+// Im[x^dag y] for doublets
+template <typename T> __device__ __forceinline__ T im_dot(const T* x, const T* y) {
+    return x[0] * y[1] - x[1] * y[0] + x[2] * y[3] - x[3] * y[2];
+}
 
 template <typename T> __device__ __forceinline__ void ldq(T* const* a, int i, size_t n, T* q) {
 #pragma unroll
@@ -103,8 +139,9 @@ __device__ __forceinline__ void plaq(T* const* a, int i, int j, size_t m, int x,
     qmul(t2, c, P);
 }
 
-template <typename T>
+template <typename T, bool EXT>
 __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
+    constexpr int NS = EXT ? kSu2ExtNS : U1NS;
     DevState* st = A.st;
     if (st->error) return;
     const int N = A.mc.N;
@@ -113,10 +150,14 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
     const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(A.mc.idx2);
     const T lam = T(A.mc.lam), v2 = T(A.mc.vev2);
     const T cJ = T(A.mc.e / (A.mc.kappa * A.mc.dx)), cM = T(2.0 / (A.mc.e * A.mc.dx * A.mc.dx * A.mc.dx));
+    const bool hasA = EXT && A.mc.e2 > 0, hasC = EXT && A.mc.chi;
+    const T cJA = hasA ? T(2.0 * A.mc.e2 / (A.mc.kappa * A.mc.dx)) : T(0);
+    const T cMA = hasA ? T(1.0 / (A.mc.e2 * A.mc.dx * A.mc.dx * A.mc.dx)) : T(0);
+    const T qc = T(A.mc.q);
     const size_t n3 = (size_t)N * N * N;
-    double acc[U1NS];
+    double acc[NS];
 #pragma unroll
-    for (int s = 0; s < U1NS; ++s) acc[s] = 0.0;
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
     for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((size_t)N * N));
         T f[4], lap[4], grad = T(0), eB = T(0);
@@ -124,6 +165,24 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) lap[c] = T(-6) * f[c];
         T KB[3][3];
+        // U(1) sector: forward plaquette angles theta_01, theta_02, theta_12 at n (sines, cosines)
+        T KA[3] = {T(0), T(0), T(0)}, eBA = T(0), chi0 = T(0), lchi = T(0), gchi = T(0);
+        T psn[3] = {T(0), T(0), T(0)};
+        if (hasA) {
+            T th0[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) th0[d] = arr[29 + d][n];
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+                const int ii = pr == 2 ? 1 : 0, jj = pr == 0 ? 1 : 2;
+                const T p = th0[ii] + arr[29 + jj][nb<T>(n, x, y, z, N, ii, 1)] - arr[29 + ii][nb<T>(n, x, y, z, N, jj, 1)] -
+                            th0[jj];
+                T cs;
+                phase_sc(p, &psn[pr], &cs);
+                eBA += T(1) - cs;
+            }
+        }
+        if (hasC) chi0 = arr[35][n];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const size_t np = nb<T>(n, x, y, z, N, i, 1), nm = nb<T>(n, x, y, z, N, i, -1);
@@ -135,6 +194,18 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
             ldf(arr, nm, fm);
             umul(q, fp, t);
             umul(c, fm, t2);
+            if (hasA) {  // W_i Phi(n+i) = e^{-i theta_i(n)} U_i Phi(n+i); W_i^dag(n-i) = U^dag e^{+i theta_i(n-i)}
+                T sn, cs;
+                phase_sc(arr[29 + i][n], &sn, &cs);
+                phase_minus(t, sn, cs);
+                phase_sc(arr[29 + i][nm], &sn, &cs);
+                phase_plus(t2, sn, cs);
+            }
+            if (hasC) {
+                const T cp = arr[35][np];
+                lchi += cp + arr[35][nm];
+                gchi += (cp - chi0) * (cp - chi0);
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 lap[k] += t[k] + t2[k];
@@ -163,10 +234,35 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) KB[i][k] = A1 * cJ * js[k] + Am * cM * mag[k];
+            if (hasA) {
+                // sum_{j != i} [sin theta_ij(n-j) - sin theta_ij(n)], theta_ji = -theta_ij
+                T magA = T(0);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (j == i) continue;
+                    const int ii = i < j ? i : j, jj = i < j ? j : i;
+                    const T sgn = i < j ? T(1) : T(-1);
+                    const size_t mj = nb<T>(n, x, y, z, N, j, -1);
+                    const int xj = j == 0 ? (x == 0 ? N - 1 : x - 1) : x;
+                    const int yj = j == 1 ? (y == 0 ? N - 1 : y - 1) : y;
+                    const int zj = j == 2 ? (z == 0 ? N - 1 : z - 1) : z;
+                    // theta_ij(n-j) = theta_i(n-j) + theta_j(n-j+i) - theta_i(n) - theta_j(n-j)
+                    const T pm = arr[29 + i][mj] + arr[29 + j][nb<T>(mj, xj, yj, zj, N, i, 1)] - arr[29 + i][n] -
+                                 arr[29 + j][mj];
+                    T smm, cmm;
+                    phase_sc(pm, &smm, &cmm);
+                    magA += smm - sgn * psn[ii + jj - 1];
+                }
+                KA[i] = A1 * cJA * im_dot(f, t) + Am * cMA * magA;
+            }
         }
         const T mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
         T dv;
-        const T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
+        T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
+        if (hasC) {
+            dv += qc * chi0 * chi0;
+            vpot += qc * mod2 * chi0 * chi0;
+        }
         T sp = T(0), pr0 = T(0), pr1 = T(0);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -196,21 +292,41 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
         acc[8] += double(vpot);
         acc[9] += double(sA);
         acc[10] += double(eB);
+        if (hasA) {
+            T sAA = T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T e = arr[32 + i][n];
+                const T es = e + h1 * KA[i];
+                sAA += es * es;
+                if (A.write) arr[32 + i][n] = e + h * KA[i];
+            }
+            acc[11 % NS] += double(sAA);
+            acc[12 % NS] += double(eBA);
+        }
+        if (hasC) {
+            const T Kc = -A3 * T(2) * qc * mod2 * chi0 + A1 * (lchi - T(6) * chi0) * idx2;
+            const T p = arr[36][n];
+            const T ps = p + h1 * Kc;
+            if (A.write) arr[36][n] = p + h * Kc;
+            acc[13 % NS] += double(ps * ps);
+            acc[14 % NS] += double(gchi * idx2);
+        }
     }
     // block reduction, partials, last block
-    __shared__ double red[8][U1NS];
+    __shared__ double red[8][NS];
     const int lin = threadIdx.x, lane = lin & 31, warp = lin >> 5, nwarps = (blockDim.x + 31) >> 5;
     const int nlanes = min(32, (int)blockDim.x - 32 * warp);
 #pragma unroll
-    for (int s = 0; s < U1NS; ++s) {
+    for (int s = 0; s < NS; ++s) {
         const double v = partial_warp_sum(acc[s], lane, nlanes);
         if (lane == 0) red[warp][s] = v;
     }
     __syncthreads();
-    if (lin < U1NS) {
+    if (lin < NS) {
         double t = 0.0;
         for (int w = 0; w < nwarps; ++w) t += red[w][lin];
-        A.partials[(size_t)blockIdx.x * U1NS + lin] = t;
+        A.partials[(size_t)blockIdx.x * NS + lin] = t;
     }
     __threadfence();
     __syncthreads();
@@ -219,12 +335,12 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    __shared__ double tot[U1NS];
+    __shared__ double tot[NS];
     const double invV = 1.0 / (double)n3;
-    for (int s = warp; s < U1NS; s += nwarps) {
+    for (int s = warp; s < NS; s += nwarps) {
         double ks = 0.0, kc = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += nlanes) {
-            const double yk = __ldcg(&A.partials[(size_t)b * U1NS + s]) - kc, tk = ks + yk;
+            const double yk = __ldcg(&A.partials[(size_t)b * NS + s]) - kc, tk = ks + yk;
             kc = (tk - ks) - yk;
             ks = tk;
         }
@@ -234,14 +350,15 @@ __global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
     __syncthreads();
     if (lin == 0) {
         *A.counter = 0u;
-        u1_finish(st, tot, A.mc, A.pi);
+        u1_finish(st, tot, A.mc, A.pi, NS);
     }
 }
 
 // Drift with the coefficients prepared by the last pass: phi += cd pi,
 // U_i <- exp(-i cdA piB_i.sigma/2) U_i (renormalised); momenta copied.
+// EXT: also theta_i += (eA/g) cdA piA_i (wrapped to [-pi, pi]) and chi += cd pchi.
 // src and dst may coincide (pointwise).
-template <typename T>
+template <typename T, bool EXT>
 __global__ void su2_drift_kernel(const Su2Args S, const Su2Args D) {
     const DevState* st = S.st;
     if (st->error) return;
@@ -276,12 +393,25 @@ __global__ void su2_drift_kernel(const Su2Args S, const Su2Args D) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) dst[20 + 3 * i + k][n] = e[k];
         }
+        if (EXT) {
+            const T cA = S.mc.e2 > 0 ? T(st->cdA * (S.mc.e2 / S.mc.e)) : T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T e = src[32 + i][n];
+                dst[29 + i][n] = S.mc.e2 > 0 ? wrap_phase(src[29 + i][n] + cA * e) : src[29 + i][n];
+                dst[32 + i][n] = e;
+            }
+            const T pc = src[36][n];
+            dst[35][n] = src[35][n] + cd * pc;
+            dst[36][n] = pc;
+        }
     }
 }
 
 // Gauss residual G^a = (1/dx) sum_i [piB_i(n) - (U_i^dag(n-i) piB_i(n-i) U_i(n-i))]^a
-//                      - (g/kappa) Im[Phi^dag sigma^a pi], FP64 sums into st->gauss.
-template <typename T>
+//                      - (g/kappa) Im[Phi^dag sigma^a pi], FP64 sums into st->gauss;
+// EXT with the U(1) sector adds G^0 = (1/dx) sum_i [piA_i(n) - piA_i(n-i)] - (2 eA/kappa) Im[Phi^dag pi].
+template <typename T, bool EXT>
 __global__ void su2_gauss_kernel(const Su2Args A) {
     const int N = A.mc.N;
     const size_t n3 = (size_t)N * N * N;
@@ -314,6 +444,15 @@ __global__ void su2_gauss_kernel(const Su2Args A) {
             l2 += div[k] * div[k];
             r2 += r * r;
         }
+        if (EXT && A.mc.e2 > 0) {
+            double d0 = 0.0;
+            for (int i = 0; i < 3; ++i)
+                d0 += ((double)arr[32 + i][n] - (double)arr[32 + i][nb<T>(n, x, y, z, N, i, -1)]) * idx;
+            const double r = 2.0 * A.mc.e2 / A.mc.kappa * im_dot(f, p);
+            g2 += (d0 - r) * (d0 - r);
+            l2 += d0 * d0;
+            r2 += r * r;
+        }
     }
     g2 = warp_sum(g2);
     l2 = warp_sum(l2);
@@ -325,10 +464,11 @@ __global__ void su2_gauss_kernel(const Su2Args A) {
     }
 }
 
-// Homogeneous initial state: Phi = phi0, pi = a^{3-alpha} dphi0, unit links, zero piB.
+// Homogeneous initial state: Phi = phi0, pi = a^{3-alpha} dphi0, unit links, zero piB
+// (and zero angles, piA, chi, pchi).
 template <typename T>
-__global__ void su2_fill_kernel(const Su2Args A, double f0, double f1, double f2, double f3, double p0, double p1,
-                                double p2, double p3) {
+__global__ void su2_fill_kernel(const Su2Args A, int narr, double f0, double f1, double f2, double f3, double p0,
+                                double p1, double p2, double p3) {
     const size_t n3 = (size_t)A.mc.N * A.mc.N * A.mc.N;
     T* const* arr = reinterpret_cast<T* const*>(A.a);
     const double v[8] = {f0, f1, f2, f3, p0, p1, p2, p3};
@@ -336,7 +476,7 @@ __global__ void su2_fill_kernel(const Su2Args A, double f0, double f1, double f2
         for (int k = 0; k < 8; ++k) arr[k][n] = T(v[k]);
         for (int i = 0; i < 3; ++i)
             for (int c = 0; c < 4; ++c) arr[8 + 4 * i + c][n] = T(c == 0 ? 1.0 : 0.0);
-        for (int k = 20; k < kSu2Arrays; ++k) arr[k][n] = T(0);
+        for (int k = 20; k < narr; ++k) arr[k][n] = T(0);
     }
 }
 
@@ -344,7 +484,7 @@ __global__ void zero_su2_gauss_kernel(DevState* st) { st->gauss[0] = st->gauss[1
 
 static Su2Args su2_args(Lattice* L, int copy) {
     Su2Args A;
-    for (int k = 0; k < kSu2Arrays; ++k) A.a[k] = L->buf.f[copy][k];
+    for (int k = 0; k < kSu2Arrays; ++k) A.a[k] = k < L->buf.narr ? L->buf.f[copy][k] : nullptr;
     A.st = L->buf.st;
     A.partials = L->buf.partials;
     A.counter = L->buf.counter;
@@ -358,8 +498,13 @@ void su2_geometry(Lattice* L) {
     g.threads = 256;
     const size_t n3 = (size_t)g.N * g.N * g.N;
     int per_sm = 1;
-    if (L->prec == CL_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, su2_kick_kernel<float>, 256, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, su2_kick_kernel<double>, 256, 0);
+    const bool ext = L->mc.ext != 0;
+    if (L->prec == CL_FP32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ext ? su2_kick_kernel<float, true> : su2_kick_kernel<float, false>,
+                                                      256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, ext ? su2_kick_kernel<double, true> : su2_kick_kernel<double, false>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)L->sm_count * per_sm;
     const long long need = (long long)((n3 + 255) / 256);
@@ -375,12 +520,21 @@ cudaError_t su2_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bo
     D.pi = pi;
     D.write = write ? 1 : 0;
     const int dg = L->sm_count * 8;
-    if (L->prec == CL_FP32) {
-        su2_drift_kernel<float><<<dg, 256, 0, s>>>(S, D);
-        su2_kick_kernel<float><<<L->geo.grid, 256, 0, s>>>(D);
+    const int grid = L->geo.grid;
+    if (L->mc.ext) {
+        if (L->prec == CL_FP32) {
+            su2_drift_kernel<float, true><<<dg, 256, 0, s>>>(S, D);
+            su2_kick_kernel<float, true><<<grid, 256, 0, s>>>(D);
+        } else {
+            su2_drift_kernel<double, true><<<dg, 256, 0, s>>>(S, D);
+            su2_kick_kernel<double, true><<<grid, 256, 0, s>>>(D);
+        }
+    } else if (L->prec == CL_FP32) {
+        su2_drift_kernel<float, false><<<dg, 256, 0, s>>>(S, D);
+        su2_kick_kernel<float, false><<<grid, 256, 0, s>>>(D);
     } else {
-        su2_drift_kernel<double><<<dg, 256, 0, s>>>(S, D);
-        su2_kick_kernel<double><<<L->geo.grid, 256, 0, s>>>(D);
+        su2_drift_kernel<double, false><<<dg, 256, 0, s>>>(S, D);
+        su2_kick_kernel<double, false><<<grid, 256, 0, s>>>(D);
     }
     return cudaGetLastError();
 }
@@ -388,8 +542,14 @@ cudaError_t su2_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bo
 cudaError_t su2_launch_drift(Lattice* L, int cur, cudaStream_t s) {
     Su2Args S = su2_args(L, cur);
     const int dg = L->sm_count * 8;
-    if (L->prec == CL_FP32) su2_drift_kernel<float><<<dg, 256, 0, s>>>(S, S);
-    else su2_drift_kernel<double><<<dg, 256, 0, s>>>(S, S);
+    if (L->mc.ext) {
+        if (L->prec == CL_FP32) su2_drift_kernel<float, true><<<dg, 256, 0, s>>>(S, S);
+        else su2_drift_kernel<double, true><<<dg, 256, 0, s>>>(S, S);
+    } else if (L->prec == CL_FP32) {
+        su2_drift_kernel<float, false><<<dg, 256, 0, s>>>(S, S);
+    } else {
+        su2_drift_kernel<double, false><<<dg, 256, 0, s>>>(S, S);
+    }
     return cudaGetLastError();
 }
 
@@ -397,18 +557,25 @@ cudaError_t su2_launch_gauss(Lattice* L, int cur, cudaStream_t s) {
     Su2Args A = su2_args(L, cur);
     zero_su2_gauss_kernel<<<1, 1, 0, s>>>(L->buf.st);
     const int grid = L->sm_count * 4;
-    if (L->prec == CL_FP32) su2_gauss_kernel<float><<<grid, 256, 0, s>>>(A);
-    else su2_gauss_kernel<double><<<grid, 256, 0, s>>>(A);
+    if (L->mc.ext) {
+        if (L->prec == CL_FP32) su2_gauss_kernel<float, true><<<grid, 256, 0, s>>>(A);
+        else su2_gauss_kernel<double, true><<<grid, 256, 0, s>>>(A);
+    } else if (L->prec == CL_FP32) {
+        su2_gauss_kernel<float, false><<<grid, 256, 0, s>>>(A);
+    } else {
+        su2_gauss_kernel<double, false><<<grid, 256, 0, s>>>(A);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t su2_fill(Lattice* L, const double* f, const double* p) {
     Su2Args A = su2_args(L, L->cur);
     const int grid = L->sm_count * 4;
+    const int narr = L->buf.narr;
     if (L->prec == CL_FP32)
-        su2_fill_kernel<float><<<grid, 256, 0, L->stream>>>(A, f[0], f[1], f[2], f[3], p[0], p[1], p[2], p[3]);
+        su2_fill_kernel<float><<<grid, 256, 0, L->stream>>>(A, narr, f[0], f[1], f[2], f[3], p[0], p[1], p[2], p[3]);
     else
-        su2_fill_kernel<double><<<grid, 256, 0, L->stream>>>(A, f[0], f[1], f[2], f[3], p[0], p[1], p[2], p[3]);
+        su2_fill_kernel<double><<<grid, 256, 0, L->stream>>>(A, narr, f[0], f[1], f[2], f[3], p[0], p[1], p[2], p[3]);
     return cudaGetLastError();
 }
 
