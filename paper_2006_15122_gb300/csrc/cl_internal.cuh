@@ -20,6 +20,7 @@ namespace cl {
 
 constexpr int kMaxComp = 4;   // real components per sector (scalar fields, or Re/Im)
 constexpr int kMaxSums = 48;  // reductions per pass
+constexpr int kMaxArrays = 40;  // stored arrays per copy (SU(2) x U(1) + chi: 37)
 constexpr int kMaxBlocks = 4096;
 
 // Background, means and bookkeeping shared by all passes; lives in device
@@ -126,7 +127,7 @@ __host__ __device__ inline double bg_b(const ModelConst& mc, double t) {
 
 // Per-lattice device resources.
 struct Buffers {
-    void* f[2][32];    // ping-pong copies of every stored array (type T)
+    void* f[2][kMaxArrays];  // ping-pong copies of every stored array (type T)
     int narr;
     DevState* st;
     double* partials;  // per-block partial sums

@@ -252,7 +252,7 @@ cl_status lattice_destroy(cl_lattice* h) {
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     for (int c = 0; c < 2; ++c)
-        for (int i = 0; i < 32; ++i)
+        for (int i = 0; i < cl::kMaxArrays; ++i)
             if (h->buf.f[c][i]) cudaFree(h->buf.f[c][i]);
     for (int i = 0; i < 4; ++i) {
         if (h->rk_T1[i]) cudaFree(h->rk_T1[i]);
@@ -425,6 +425,12 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    L->buf.narr = 0;
+    if (cl::array_count(mc) > cl::kMaxArrays) {
+        cl_status s = fail(nullptr, CL_ERR_ARG, "internal: too many arrays for this build");
+        lattice_destroy(L);
+        return s;
+    }
     L->buf.narr = cl::array_count(mc);
     const size_t n = (size_t)N * N * N;
     for (int c = 0; c < 2; ++c)
