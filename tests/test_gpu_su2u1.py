@@ -173,7 +173,7 @@ def test_su2u1_vacuum_initial_conditions_match_oracle(prec):
     lat.evolve(10)
     assert lat.measure_means()["gauss_violation"] < (1e-13 if prec == cl.CL_FP64 else 1e-5)
     k, D, cnt = lat.spectrum(1)  # the singlet's spectrum
-    assert np.all(np.isfinite(D)) and D[1:].max() > 0 and cnt.sum() == N ** 3 - 1
+    assert np.all(np.isfinite(D)) and D[1:].max() > 0 and cnt.sum() == N ** 3
     lat.close()
 
 
