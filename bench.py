@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--acc-N", type=int, default=64)
     p.add_argument("--acc-eta", type=float, default=100.0)
     p.add_argument("--acc-integrators", default="lf,vv2,vv4,vv6,vv8,vv10")
+    p.add_argument("--acc-model", default="u1", choices=["u1", "su2u1"],
+                   help="u1: the U(1) inflaton; su2u1: the SU(2) x U(1) doublet with a singlet")
     return p.parse_args()
 
 
@@ -358,10 +360,13 @@ def u1_inflaton_setup(p=4, M_over_mp=10.0, Lambda4_GeV4=4.3e65, qA=1.0e2):
 
 
 def accuracy_measurement(args, stream):
-    """Friedmann-constraint error Delta_e (section 8.2, accuracy tests) of every
-    integrator on the U(1)-charged p = 4 inflaton at k_IR = 0.6, dt = 0.01,
-    FP64, from one vacuum-fluctuation start; sampled at the start and every 5
-    program-time units, with the device time of each run."""
+    """Friedmann-constraint error Delta_e (sections 8.2 and 8.3, accuracy tests)
+    of the chosen integrators on the p = 4 working examples at k_IR = 0.6,
+    dt = 0.01, FP64, from one vacuum-fluctuation start: the U(1)-charged
+    inflaton (q_A* = 100), or the SU(2) x U(1) doublet with a singlet
+    (q_A* = q_B* = q* = 100).  Sampled at the start and every 5 program-time
+    units, with the device time of each run and the energy fractions of the
+    sectors."""
     import torch
 
     import paper_2006_15122_gb300 as cl
@@ -370,15 +375,31 @@ def accuracy_measurement(args, stream):
     N, kIR, dt = args.acc_N, 0.6, 0.01
     nsteps = int(round(args.acc_eta / dt))
     every = int(round(5.0 / dt))
-    out = {"model": "U(1) charged inflaton, V = (1/p)(2|phi|^2)^(p/2)", "setup": st, "N": N, "kIR": kIR, "dt": dt,
-           "eta_end": nsteps * dt, "precision": "f64", "runs": {}}
+    su2 = args.acc_model == "su2u1"
+    if su2:
+        # the doublet's stored components: |Phi|^2 = 1/2 (canonical norm 1) split evenly, radial velocity
+        c = 1.0 / math.sqrt(8.0)
+        v = st["dphi0"][0] * math.sqrt(2.0)  # the radial canonical speed
+        st = dict(st, phi0=(c, c, c, c), dphi0=(v * c, v * c, v * c, v * c), qB=st["qA"], q=st["qA"],
+                  gauge_e_su2=2.0 * math.sqrt(st["qA"]) * st["omega_over_fstar"])
+        name = "SU(2) x U(1) doublet + singlet, V = (1/p)(2|Phi|^2)^(p/2) + q |Phi|^2 chi^2"
+    else:
+        name = "U(1) charged inflaton, V = (1/p)(2|phi|^2)^(p/2)"
+    out = {"model": name, "setup": st, "N": N, "kIR": kIR, "dt": dt, "eta_end": nsteps * dt, "precision": "f64",
+           "runs": {}}
     for integ in args.acc_integrators.split(","):
-        model = cl.make_model(kind=cl.CL_MODEL_U1, alpha=st["alpha"], fstar_over_mp=st["fstar_over_mp"],
-                              omega_over_fstar=st["omega_over_fstar"], lam=1.0, gauge_e=st["gauge_e"],
-                              potential=cl.CL_POT_MONOMIAL, pexp=st["p"])
+        if su2:
+            model = cl.make_model(kind=cl.CL_MODEL_SU2, n_fields=2, alpha=st["alpha"],
+                                  fstar_over_mp=st["fstar_over_mp"], omega_over_fstar=st["omega_over_fstar"], lam=1.0,
+                                  q=st["q"], gauge_e=st["gauge_e_su2"], gauge_e_u1=st["gauge_e"],
+                                  potential=cl.CL_POT_MONOMIAL, pexp=st["p"])
+        else:
+            model = cl.make_model(kind=cl.CL_MODEL_U1, alpha=st["alpha"], fstar_over_mp=st["fstar_over_mp"],
+                                  omega_over_fstar=st["omega_over_fstar"], lam=1.0, gauge_e=st["gauge_e"],
+                                  potential=cl.CL_POT_MONOMIAL, pexp=st["p"])
         lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, integ, cl.CL_FP64), cl.make_init(
             phi0=st["phi0"], dphi0=st["dphi0"], seed=1, spectrum=1), stream=stream)
-        t, de, dg, a, eg = [], [], [], [], []
+        t, de, dg, a, frac = [], [], [], [], []
 
         def sample():
             mm = lat.measure_means()
@@ -386,7 +407,14 @@ def accuracy_measurement(args, stream):
             de.append(mm["hubble_violation"])
             dg.append(mm["gauss_violation"])
             a.append(mm["a"])
-            eg.append((mm["EK"][1] + mm["EG"][1]) / mm["rho"])
+            r = mm["rho"]
+            if su2:
+                frac.append({"inflaton": (mm["EK"][0] + mm["EG"][0] + mm["EV"][0]) / r,
+                             "su2": (mm["EK"][1] + mm["EG"][1]) / r, "u1": (mm["EK"][2] + mm["EG"][2]) / r,
+                             "chi": (mm["EK"][3] + mm["EG"][3]) / r})
+            else:
+                frac.append({"inflaton": (mm["EK"][0] + mm["EG"][0] + mm["EV"][0]) / r,
+                             "u1": (mm["EK"][1] + mm["EG"][1]) / r})
 
         sample()
         ms = 0.0
@@ -402,9 +430,9 @@ def accuracy_measurement(args, stream):
             done += k
             sample()
         lat.close()
-        out["runs"][integ] = {"t": t, "delta_e": de, "gauss_violation": dg, "a": a,
-                              "gauge_energy_fraction": eg, "device_ms": ms, "ms_per_step": ms / nsteps,
-                              "delta_e_end": de[-1], "delta_e_max": max(de)}
+        out["runs"][integ] = {"t": t, "delta_e": de, "gauss_violation": dg, "a": a, "energy_fractions": frac,
+                              "device_ms": ms, "ms_per_step": ms / nsteps, "delta_e_end": de[-1],
+                              "delta_e_max": max(de)}
     return out
 
 
