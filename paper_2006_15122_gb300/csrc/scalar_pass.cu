@@ -400,28 +400,31 @@ static const void* scalar_kernel_ptr(const Lattice* L) {
     return L->mc.nf == 1 ? kptr_p<double, 1>(L->mc.pexp) : kptr_p<double, 2>(L->mc.pexp);
 }
 
-// Tile geometry.  CL_SCALAR_TILE="BY,ZC,S" (rows per tile, planes per z chunk,
-// ring stages) overrides the defaults; values that do not fit N are ignored.
+// Tile geometry.  CL_SCALAR_TILE="BY,ZC,S[,BX]" (rows per tile, planes per z
+// chunk, ring stages, threads per row: 16, 32 or 64) overrides the defaults;
+// values that do not fit N are ignored.
 void scalar_geometry(Lattice* L) {
     Geometry& g = L->geo;
-    int want_by = 8, want_zc = 128, want_s = 5;
+    int want_by = 8, want_zc = 128, want_s = 5, want_bx = 32;
     if (const char* env = getenv("CL_SCALAR_TILE")) {
-        int a = 0, b = 0, c = 0;
-        if (sscanf(env, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= 3 && c <= 8) {
+        int a = 0, b = 0, c = 0, d = 0;
+        const int got = sscanf(env, "%d,%d,%d,%d", &a, &b, &c, &d);
+        if (got >= 3 && a > 0 && b > 0 && c >= 3 && c <= 8) {
             want_by = a;
             want_zc = b;
             want_s = c;
+            if (got == 4 && (d == 16 || d == 32 || d == 64)) want_bx = d;
         }
     }
     const int N = L->mc.N;
     g.N = N;
     g.V = (L->prec == CL_FP32) ? 4 : 2;
     const int nv = N / g.V;
-    int bx = nv < 32 ? nv : 32;
+    int bx = nv < want_bx ? nv : want_bx;
     while (nv % bx != 0) --bx;
     g.BX = bx;
     int by = 256 / g.BX;
-    if (g.BX == 32 && want_by < by) by = want_by;
+    if (g.BX == want_bx && want_by < by) by = want_by;
     if (by > N) by = N;
     while (N % by != 0) --by;
     g.BY = by;
