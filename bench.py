@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-scan", action="store_true", help="leave the ensemble scan out of the default line")
     p.add_argument("--no-gauge", action="store_true", help="leave the U(1) / SU(2) pass timings out")
+    p.add_argument("--gauge-only", default="", choices=["", "u1", "su2", "su2u1"],
+                   help="print only the event-timed passes of one gauge sector")
+    p.add_argument("--gauge-N", type=int, default=0)
+    p.add_argument("--gauge-steps", type=int, default=20)
     p.add_argument("--scan", action="store_true",
                    help="time the batched ensemble + surrogate parameter scan instead of the single lattice")
     p.add_argument("--scan-runs", type=int, default=512)
@@ -296,9 +300,9 @@ def gauge_measurement(kind, N, steps, stream):
     """Event-timed passes of the gauge sectors on a lattice of the same shape as
     their workloads (FP32): the compact U(1) staggered leapfrog (lam = e = v = 1,
     dx = 0.5, dt = 0.1 dx; one pass per step) and the SU(2)-Higgs VV2 (one
-    drift + kick per step).  Algorithmic bytes per site and pass: one read and
-    one write of every stored array, 10 arrays (U(1)) or 29 arrays (SU(2)) of
-    4 B."""
+    drift + kick per step), also with the U(1) sector and the singlet.
+    Algorithmic bytes per site and pass: one read and one write of every stored
+    array, 10 arrays (U(1)), 29 (SU(2)) or 37 (SU(2) x U(1) + chi) of 4 B."""
     import torch
 
     import paper_2006_15122_gb300 as cl
@@ -309,10 +313,15 @@ def gauge_measurement(kind, N, steps, stream):
         model = cl.make_model(kind=cl.CL_MODEL_U1, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
         init = cl.make_init(seed=7)
         integ, narr, kernel = "lf", 10, "u1_pass_kernel<float>"
-    else:
+    elif kind == "su2":
         model = cl.make_model(kind=cl.CL_MODEL_SU2, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
         init = cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), spectrum=0)
-        integ, narr, kernel = "vv2", 29, "su2_drift_kernel<float> + su2_kick_kernel<float>"
+        integ, narr, kernel = "vv2", 29, "su2_drift_kernel<float,false> + su2_kick_kernel<float,false>"
+    else:  # SU(2) x U(1) + chi with the same couplings
+        model = cl.make_model(kind=cl.CL_MODEL_SU2, n_fields=2, lam=1.0, vev2=1.0, gauge_e=1.0, gauge_e_u1=1.0, q=1.0,
+                              omega_over_fstar=1.0)
+        init = cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), spectrum=0)
+        integ, narr, kernel = "vv2", 37, "su2_drift_kernel<float,true> + su2_kick_kernel<float,true>"
     lat = cl.Lattice(model, cl.make_grid(N, kIR, 0.1 * dx, integ, cl.CL_FP32), init, stream=stream)
     lat.evolve(3)
     torch.cuda.synchronize()
@@ -324,7 +333,7 @@ def gauge_measurement(kind, N, steps, stream):
     ms = e0.elapsed_time(e1)
     mm = lat.measure_means()
     lat.close()
-    npass = steps + (1 if kind == "su2" else 0)
+    npass = steps + (0 if kind == "u1" else 1)
     alg = 2 * narr * 4 * N ** 3
     achieved = alg / (ms / 1e3 / npass) / 1e9
     peak, _ = measured_peaks()
@@ -449,6 +458,13 @@ def main():
         return run_reference(args)
     if args.scan:
         return run_scan(args)
+    if args.gauge_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        N = args.gauge_N or (256 if args.gauge_only == "u1" else 128)
+        print(json.dumps(gauge_measurement(args.gauge_only, N, args.gauge_steps, torch.cuda.current_stream())),
+              flush=True)
+        return
     if args.accuracy:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -529,7 +545,8 @@ def main():
     gauge = None
     if rank == 0 and not args.no_gauge:
         try:
-            gauge = {"u1": gauge_measurement("u1", 256, 20, stream), "su2": gauge_measurement("su2", 128, 10, stream)}
+            gauge = {"u1": gauge_measurement("u1", 256, 20, stream), "su2": gauge_measurement("su2", 128, 10, stream),
+                     "su2u1": gauge_measurement("su2u1", 128, 10, stream)}
         except Exception as exc:
             gauge = {"error_running": repr(exc)}
     ens = None
