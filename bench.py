@@ -323,7 +323,7 @@ def gauge_measurement(kind, N, steps, stream):
         init = cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), spectrum=0)
         integ, narr, kernel = "vv2", 37, "su2_drift_kernel<float,true> + su2_kick_kernel<float,true>"
     lat = cl.Lattice(model, cl.make_grid(N, kIR, 0.1 * dx, integ, cl.CL_FP32), init, stream=stream)
-    lat.evolve(3)
+    lat.evolve(steps)  # warm-up of the same length: the CUDA graph of `steps` steps is captured here
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

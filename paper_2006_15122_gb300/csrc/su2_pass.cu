@@ -140,7 +140,7 @@ __device__ __forceinline__ void plaq(T* const* a, int i, int j, size_t m, int x,
 }
 
 template <typename T, bool EXT>
-__global__ void __launch_bounds__(256) su2_kick_kernel(const Su2Args A) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(const Su2Args A) {
     constexpr int NS = EXT ? kSu2ExtNS : U1NS;
     DevState* st = A.st;
     if (st->error) return;

@@ -56,7 +56,7 @@ template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* 
 template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
 template <typename T>
-__global__ void __launch_bounds__(256) u1_pass_kernel(const U1Args A) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(const U1Args A) {
     DevState* st = A.st;
     if (st->error) return;
     const int N = A.mc.N;
