@@ -19,9 +19,10 @@
 // E_V = <V>, E_K^A = kappa/(2a^4) sum_i <piA_i^2>,
 // E_G^A = kappa/(a^4 e^2 dx^4) sum_{i<j} <1 - cos theta_ij>.
 //
-// Each array is read once from HBM (plus halo re-reads, mostly L2 hits) and
-// written once per pass; the last block does the FP64 leapfrog/Friedmann
-// update as in the scalar pass.
+// One thread per site with a persistent grid-stride loop; neighbour values
+// come through L1/L2 and are drifted on the fly, so each array is read once
+// from HBM and written once per pass.  The last block does the FP64
+// leapfrog/Friedmann update as in the scalar pass.
 #include <math.h>
 
 #include "cl_internal.cuh"
@@ -54,271 +55,160 @@ template <typename T> __device__ __forceinline__ void sc(T x, T* s, T* c);
 template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { __sincosf(x, s, c); }
 template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
-// Tile of BX x BY sites marching ZC planes in z (one site per thread).  The
-// planes z0-1 .. z0+ZC of all ten arrays, with x/y halos and the two corners
-// that the halo plaquettes need, stream through an S-stage shared-memory ring
-// (cp.async, one barrier per plane) and are drifted in place.  Every site's
-// link phases (cos, sin theta_i) and forward plaquette sines are evaluated
-// once, by the thread that owns the site or (for the tile's left column and
-// bottom row) by the edge thread that loaded it, and kept in a three-plane
-// ring, so 6 sincos per site instead of 15 and each shared plaquette is the
-// same number wherever it enters (the Gauss-law cancellation stays exact).
-// The kick of plane q runs one iteration after its plaquettes, when the
-// neighbours' values are visible.
-struct U1TileXY {
-    int x0, y0, z0;
-};
-
-__device__ __forceinline__ U1TileXY u1_decode_tile(const Geometry& g, int tile) {
-    const int tyi = tile % g.nty;
-    const int rr = tile / g.nty;
-    U1TileXY t;
-    t.x0 = (rr % g.ntx) * g.BX;
-    t.y0 = tyi * g.BY;
-    t.z0 = (rr / g.ntx) * g.ZC;
-    return t;
-}
-
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(const U1Args A, const Geometry G) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(const U1Args A) {
     DevState* st = A.st;
     if (st->error) return;
-    const int N = G.N, BX = G.BX, BY = G.BY, ZC = G.ZC, S = G.S;
-    const int RW = BX + 2, ASZ = RW * (BY + 2), STG = 10 * ASZ;  // stage: 10 arrays with halos
-    const int PW = BX + 1, PSZ = PW * (BY + 1), SLOT = 9 * PSZ;   // plane of link phases / plaquette sines
-    extern __shared__ __align__(128) unsigned char smraw[];
-    T* sm = reinterpret_cast<T*>(smraw);
-    T* pl = sm + (size_t)S * STG;
-    __shared__ double bacc[8][U1NS];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int lin = ty * BX + tx, nthr = BX * BY;
-    const int lane = lin & 31, warp = lin >> 5, nwarps = (nthr + 31) >> 5;
-    const int nlanes = min(32, nthr - 32 * warp);
-    for (int i = lin; i < 8 * U1NS; i += nthr) (&bacc[0][0])[i] = 0.0;
-
+    const int N = A.mc.N;
     const T cd = T(st->cd), cdA = T(st->cdA), A1 = T(st->A1), A3 = T(st->A3), Am = T(st->Am);
-    const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(A.mc.idx2);
+    const T h1 = T(A.pi.h1), h = T(A.pi.h);
+    const T dx = T(A.mc.dx), idx = T(1.0 / A.mc.dx), idx2 = T(A.mc.idx2);
     const T lam = T(A.mc.lam), v2 = T(A.mc.vev2);
     const T cJ = T(2.0 * A.mc.e / A.mc.dx / A.mc.kappa), cB = T(1.0 / (A.mc.e * A.mc.dx * A.mc.dx * A.mc.dx));
-    const size_t NN = (size_t)N * N;
-
-    const int my_tiles = (blockIdx.x < (unsigned)G.ntiles) ? (G.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto wrapN = [&](int v) { return v < 0 ? v + N : (v >= N ? v - N : v); };
-    const int oc = (ty + 1) * RW + tx + 1;  // own cell in a stage array
-    const int po = (ty + 1) * PW + tx + 1;  // own cell in a plaquette-ring array
-
-    // loader: plane (z0 - 1 + ld_p) of tile ld_k into stage ld_slot; every thread copies its own
-    // cell, edge threads the halo cells and the two corners (top-left, bottom-right)
-    int ld_k = 0, ld_p = 0, ld_slot = 0;
-    U1TileXY ld_t = u1_decode_tile(G, (int)blockIdx.x);
-    auto issue = [&]() {
-        if (ld_k < my_tiles) {
-            const int z = wrapN(ld_t.z0 - 1 + ld_p);
-            T* dst = sm + (size_t)ld_slot * STG;
-            const int x = ld_t.x0 + tx, y = ld_t.y0 + ty;
-            const int xl = wrapN(ld_t.x0 - 1), xr = wrapN(ld_t.x0 + BX), yb = wrapN(ld_t.y0 - 1), yt = wrapN(ld_t.y0 + BY);
+    (void)dx;
+    const T* PR = static_cast<const T*>(A.in[0]);
+    const T* PIm = static_cast<const T*>(A.in[1]);
+    const T* QR = static_cast<const T*>(A.in[2]);
+    const T* QI = static_cast<const T*>(A.in[3]);
+    const T* TH[3] = {static_cast<const T*>(A.in[4]), static_cast<const T*>(A.in[5]), static_cast<const T*>(A.in[6])};
+    const T* EA[3] = {static_cast<const T*>(A.in[7]), static_cast<const T*>(A.in[8]), static_cast<const T*>(A.in[9])};
+    const size_t n3 = (size_t)N * N * N;
+    double acc[U1NS];
 #pragma unroll
-            for (int a = 0; a < 10; ++a) {
-                const T* src = static_cast<const T*>(A.in[a]) + (size_t)z * NN;
-                T* d = dst + a * ASZ;
-                cp_async_elem(d + oc, src + (size_t)y * N + x);
-                if (tx == 0) cp_async_elem(d + (ty + 1) * RW, src + (size_t)y * N + xl);
-                if (tx == BX - 1) cp_async_elem(d + (ty + 1) * RW + BX + 1, src + (size_t)y * N + xr);
-                if (ty == 0) cp_async_elem(d + tx + 1, src + (size_t)yb * N + x);
-                if (ty == BY - 1) cp_async_elem(d + (BY + 1) * RW + tx + 1, src + (size_t)yt * N + x);
-                if (tx == 0 && ty == BY - 1) cp_async_elem(d + (BY + 1) * RW, src + (size_t)yt * N + xl);
-                if (tx == BX - 1 && ty == 0) cp_async_elem(d + BX + 1, src + (size_t)yb * N + xr);
-            }
-            if (++ld_p == ZC + 2) {
-                ld_p = 0;
-                if (++ld_k < my_tiles) ld_t = u1_decode_tile(G, (int)blockIdx.x + ld_k * (int)gridDim.x);
-            }
-            if (++ld_slot == S) ld_slot = 0;
+    for (int s = 0; s < U1NS; ++s) acc[s] = 0.0;
+    T ts[U1NS];
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) ts[s] = T(0);
+    int cnt = 0;
+
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+        const int c[3] = {x, y, z};
+        auto at = [&](int dxs, int dys, int dzs) -> size_t {
+            int xx = x + dxs, yy = y + dys, zz = z + dzs;
+            xx = xx < 0 ? xx + N : (xx >= N ? xx - N : xx);
+            yy = yy < 0 ? yy + N : (yy >= N ? yy - N : yy);
+            zz = zz < 0 ? zz + N : (zz >= N ? zz - N : zz);
+            return ((size_t)zz * N + yy) * N + xx;
+        };
+        (void)c;
+        // drifted values
+        auto phr = [&](size_t k) { return __ldg(PR + k) + cd * __ldg(QR + k); };
+        auto phi_ = [&](size_t k) { return __ldg(PIm + k) + cd * __ldg(QI + k); };
+        auto th = [&](int d, size_t k) { return __ldg(TH[d] + k) + cdA * __ldg(EA[d] + k); };
+        const T fr = phr(i), fi = phi_(i);
+        const T pr = __ldg(QR + i), pim = __ldg(QI + i);
+        T t0[3], ea[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { t0[d] = th(d, i); ea[d] = __ldg(EA[d] + i); }
+        // covariant Laplacian, current, gradient energy
+        T lr = T(-6) * fr, li = T(-6) * fi, grad = T(0);
+        T Kj[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int ox = d == 0, oy = d == 1, oz = d == 2;
+            const size_t np = at(ox, oy, oz), nm = at(-ox, -oy, -oz);
+            const T ur0 = phr(np), ui0 = phi_(np);
+            T s, cc;
+            sc<T>(t0[d], &s, &cc);
+            // V_i phi(n+i) = (cos t - i sin t)(ur0 + i ui0)
+            const T ur = cc * ur0 + s * ui0, ui = cc * ui0 - s * ur0;
+            const T tm = th(d, nm);
+            T sm, cm;
+            sc<T>(tm, &sm, &cm);
+            const T wr0 = phr(nm), wi0 = phi_(nm);
+            // V_i*(n-i) phi(n-i) = (cos tm + i sin tm)(wr0 + i wi0)
+            const T wr = cm * wr0 - sm * wi0, wi = cm * wi0 + sm * wr0;
+            lr += ur + wr;
+            li += ui + wi;
+            const T gr = ur - fr, gi = ui - fi;
+            grad += gr * gr + gi * gi;
+            Kj[d] = cJ * (fr * ui - fi * ur);  // (2e/dx)(1/kappa) Im[phi* V_i phi(n+i)]
         }
-        cp_async_commit();
-    };
-    int issued = 0;
-    auto wait_for = [&](int need) {
-        switch (issued - 1 - need) {
-            case 0: cp_async_wait<0>(); break;
-            case 1: cp_async_wait<1>(); break;
-            case 2: cp_async_wait<2>(); break;
-            case 3: cp_async_wait<3>(); break;
-            default: cp_async_wait<4>(); break;
+        // plaquettes at n, one per unordered pair (theta_ji = -theta_ij): pairs (0,1), (0,2), (1,2)
+        T sp[3], eB = T(0);
+#pragma unroll
+        for (int pr_ = 0; pr_ < 3; ++pr_) {
+            const int ii = pr_ == 2 ? 1 : 0, jj = pr_ == 0 ? 1 : 2;
+            const int oix = ii == 0, oiy = ii == 1, oiz = ii == 2;
+            const int ojx = jj == 0, ojy = jj == 1, ojz = jj == 2;
+            const T pn = t0[ii] + th(jj, at(oix, oiy, oiz)) - th(ii, at(ojx, ojy, ojz)) - t0[jj];
+            T cn;
+            sc<T>(pn, &sp[pr_], &cn);
+            eB += T(1) - cn;
         }
-        __syncthreads();
-    };
-    // in-place drift of one cell of a stage: phi += cd pi, theta_d += cdA piA_d
-    auto drift_cell = [&](T* sg, int c) {
-        sg[c] = sg[c] + cd * sg[2 * ASZ + c];
-        sg[ASZ + c] = sg[ASZ + c] + cd * sg[3 * ASZ + c];
+        // forces: sum_j [Im V_ij(n) - Im V_ij(n-j)], Im V_ij = -sin(theta_ij)
+        T mag[3] = {T(0), T(0), T(0)};
 #pragma unroll
-        for (int d = 0; d < 3; ++d) sg[(4 + d) * ASZ + c] = sg[(4 + d) * ASZ + c] + cdA * sg[(7 + d) * ASZ + c];
-    };
-
-    for (int L = 0; L < S; ++L, ++issued) issue();
-    int need = 0;  // load index of the next plane to land
-    int sb = 0;    // stage slot of the tile's plane -1
-
-    for (int k = 0; k < my_tiles; ++k) {
-        const U1TileXY tt = u1_decode_tile(G, (int)blockIdx.x + k * (int)gridDim.x);
-        const int x = tt.x0 + tx, y = tt.y0 + ty;
-        auto stage = [&](int pz) { int i = sb + pz + 1; i %= S; return sm + (size_t)i * STG; };
-        auto slot = [&](int pz) { return pl + (size_t)((pz + 3) % 3) * SLOT; };
-        T ts[U1NS];
+        for (int ii = 0; ii < 3; ++ii) {
 #pragma unroll
-        for (int i = 0; i < U1NS; ++i) ts[i] = T(0);
-        T thn[3] = {T(0), T(0), T(0)};   // own drifted theta at plane p+1
-        T phm[2] = {T(0), T(0)};         // own drifted phi at plane q-1 of the kick
-
-        for (int p = -2; p <= ZC; ++p) {
-            if (p <= ZC - 1) {
-                wait_for(need);  // plane p+1 has landed; every earlier write is visible
-                ++need;
-            } else {
-                __syncthreads();
-            }
-            if (p >= 1) { issue(); ++issued; }  // the stage of plane p-2 is free
-            if (p <= ZC - 1) {                 // drift plane p+1: own cell and the halo cells this thread loaded
-                T* sg = stage(p + 1);
-                drift_cell(sg, oc);
-                if (tx == 0) drift_cell(sg, (ty + 1) * RW);
-                if (tx == BX - 1) drift_cell(sg, (ty + 1) * RW + BX + 1);
-                if (ty == 0) drift_cell(sg, tx + 1);
-                if (ty == BY - 1) drift_cell(sg, (BY + 1) * RW + tx + 1);
-                if (tx == 0 && ty == BY - 1) drift_cell(sg, (BY + 1) * RW);
-                if (tx == BX - 1 && ty == 0) drift_cell(sg, BX + 1);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) thn[d] = sg[(4 + d) * ASZ + oc];
-            }
-            if (p >= -1 && p <= ZC - 1) {  // link phases and forward plaquettes of plane p
-                const T* Sg = stage(p);
-                const T* Sn = stage(p + 1);
-                T* P = slot(p);
-                const T* G0 = Sg + 4 * ASZ;
-                const T* G1 = Sg + 5 * ASZ;
-                const T* G2 = Sg + 6 * ASZ;
-                const T t0 = G0[oc], t1 = G1[oc], t2 = G2[oc];
-                T c, s;
-                sc<T>(t0, &s, &c); P[0 * PSZ + po] = c; P[1 * PSZ + po] = s;
-                sc<T>(t1, &s, &c); P[2 * PSZ + po] = c; P[3 * PSZ + po] = s;
-                sc<T>(t2, &s, &c); P[4 * PSZ + po] = c; P[5 * PSZ + po] = s;
-                // theta_ij(n) = theta_i(n) + theta_j(n+i) - theta_i(n+j) - theta_j(n)
-                const T q01 = t0 + G1[oc + 1] - G0[oc + RW] - t1;
-                const T q02 = t0 + G2[oc + 1] - thn[0] - t2;
-                const T q12 = t1 + G2[oc + RW] - thn[1] - t2;
-                T c01, c02, c12;
-                sc<T>(q01, &s, &c01); P[6 * PSZ + po] = s;
-                sc<T>(q02, &s, &c02); P[7 * PSZ + po] = s;
-                sc<T>(q12, &s, &c12); P[8 * PSZ + po] = s;
-                if (p >= 0) ts[10] += (T(1) - c01) + (T(1) - c02) + (T(1) - c12);
-                if (tx == 0) {  // left halo site (x0-1, y): V_0, theta_01, theta_02
-                    const int cm = (ty + 1) * RW, pm = (ty + 1) * PW;
-                    const T m0 = G0[cm], m1 = G1[cm], m2 = G2[cm];
-                    sc<T>(m0, &s, &c); P[0 * PSZ + pm] = c; P[1 * PSZ + pm] = s;
-                    sc<T>(m0 + G1[cm + 1] - G0[cm + RW] - m1, &s, &c); P[6 * PSZ + pm] = s;
-                    sc<T>(m0 + G2[cm + 1] - Sn[4 * ASZ + cm] - m2, &s, &c); P[7 * PSZ + pm] = s;
-                }
-                if (ty == 0) {  // bottom halo site (x, y0-1): V_1, theta_01, theta_12
-                    const int cm = tx + 1, pm = tx + 1;
-                    const T m0 = G0[cm], m1 = G1[cm], m2 = G2[cm];
-                    sc<T>(m1, &s, &c); P[2 * PSZ + pm] = c; P[3 * PSZ + pm] = s;
-                    sc<T>(m0 + G1[cm + 1] - G0[cm + RW] - m1, &s, &c); P[6 * PSZ + pm] = s;
-                    sc<T>(m1 + G2[cm + RW] - Sn[5 * ASZ + cm] - m2, &s, &c); P[8 * PSZ + pm] = s;
-                }
-            }
-            if (p >= 1) {  // kick of plane q = p - 1
-                const int q = p - 1;
-                const T* Sq = stage(q);
-                const T* Su = stage(p);
-                const T* P = slot(q);
-                const T* Pm = slot(q - 1);
-                const T fr = Sq[oc], fi = Sq[ASZ + oc];
-                const T pr = Sq[2 * ASZ + oc], pim = Sq[3 * ASZ + oc];
-                // neighbours of the site: forward and backward phi, link phases of V_d(n) and V_d(n-d)
-                const T fpr[3] = {Sq[oc + 1], Sq[oc + RW], Su[oc]};
-                const T fpi[3] = {Sq[ASZ + oc + 1], Sq[ASZ + oc + RW], Su[ASZ + oc]};
-                const T fmr[3] = {Sq[oc - 1], Sq[oc - RW], phm[0]};
-                const T fmi[3] = {Sq[ASZ + oc - 1], Sq[ASZ + oc - RW], phm[1]};
-                const T cm_[3] = {P[0 * PSZ + po - 1], P[2 * PSZ + po - PW], Pm[4 * PSZ + po]};
-                const T sm_[3] = {P[1 * PSZ + po - 1], P[3 * PSZ + po - PW], Pm[5 * PSZ + po]};
-                T lr = T(-6) * fr, li = T(-6) * fi, grad = T(0), Kj[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const T cc = P[(2 * d) * PSZ + po], s = P[(2 * d + 1) * PSZ + po];
-                    // V_d phi(n+d) = (cos t - i sin t)(ur0 + i ui0)
-                    const T ur = cc * fpr[d] + s * fpi[d], ui = cc * fpi[d] - s * fpr[d];
-                    // V_d*(n-d) phi(n-d) = (cos tm + i sin tm)(wr0 + i wi0)
-                    const T wr = cm_[d] * fmr[d] - sm_[d] * fmi[d], wi = cm_[d] * fmi[d] + sm_[d] * fmr[d];
-                    lr += ur + wr;
-                    li += ui + wi;
-                    const T gr = ur - fr, gi = ui - fi;
-                    grad += gr * gr + gi * gi;
-                    Kj[d] = cJ * (fr * ui - fi * ur);  // (2e/dx)(1/kappa) Im[phi* V_d phi(n+d)]
-                }
-                // sum_{j != i} [Im V_ij(n) - Im V_ij(n-j)], Im V_ij = -sin(theta_ij), theta_ji = -theta_ij
-                const T S01 = P[6 * PSZ + po], S02 = P[7 * PSZ + po], S12 = P[8 * PSZ + po];
-                T mag[3];
-                mag[0] = (-S01 + P[6 * PSZ + po - PW]) + (-S02 + Pm[7 * PSZ + po]);
-                mag[1] = (S01 - P[6 * PSZ + po - 1]) + (-S12 + Pm[8 * PSZ + po]);
-                mag[2] = (S02 - P[7 * PSZ + po - 1]) + (S12 - P[8 * PSZ + po - PW]);
-                const T mod2 = fr * fr + fi * fi;
-                T dv;
-                const T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
-                const T Kr = -A3 * dv * fr + A1 * lr * idx2, Ki = -A3 * dv * fi + A1 * li * idx2;
-                const T prr = pr + h1 * Kr, pri = pim + h1 * Ki;
-                const T por = pr + h * Kr, poi = pim + h * Ki;
-                T sA = T(0), eo[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const T K = A1 * Kj[d] + Am * cB * mag[d];
-                    const T ea = Sq[(7 + d) * ASZ + oc];
-                    const T er = ea + h1 * K;
-                    eo[d] = ea + h * K;
-                    sA += er * er;
-                }
-                ts[0] += fr; ts[1] += fi; ts[2] += fr * fr; ts[3] += fi * fi;
-                ts[4] += prr; ts[5] += pri; ts[6] += prr * prr + pri * pri;
-                ts[7] += grad * idx2;
-                ts[8] += vpot;
-                ts[9] += sA;
-                if (A.write) {
-                    const size_t o = (size_t)(tt.z0 + q) * NN + (size_t)y * N + x;
-                    static_cast<T*>(A.out[0])[o] = fr;
-                    static_cast<T*>(A.out[1])[o] = fi;
-                    static_cast<T*>(A.out[2])[o] = por;
-                    static_cast<T*>(A.out[3])[o] = poi;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        static_cast<T*>(A.out[4 + d])[o] = wrap_angle(Sq[(4 + d) * ASZ + oc]);
-                        static_cast<T*>(A.out[7 + d])[o] = eo[d];
-                    }
-                }
-            }
-            if (p >= 0) {  // own drifted phi at plane p-1 for the next kick
-                const T* Sm = stage(p - 1);
-                phm[0] = Sm[oc];
-                phm[1] = Sm[ASZ + oc];
+            for (int jj = 0; jj < 3; ++jj) {
+                if (jj == ii) continue;
+                const int oix = ii == 0, oiy = ii == 1, oiz = ii == 2;
+                const int ojx = jj == 0, ojy = jj == 1, ojz = jj == 2;
+                const int pr_ = ii + jj - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+                const T sn = ii < jj ? sp[pr_] : -sp[pr_];
+                const T pm = th(ii, at(-ojx, -ojy, -ojz)) + th(jj, at(oix - ojx, oiy - ojy, oiz - ojz)) - t0[ii] -
+                             th(jj, at(-ojx, -ojy, -ojz));
+                T smm, cmm;
+                sc<T>(pm, &smm, &cmm);
+                mag[ii] += -sn + smm;
             }
         }
-        __syncthreads();  // the stages of planes ZC-1 and ZC are free
-        issue();
-        issue();
-        issued += 2;
-        sb = (sb + ZC + 2) % S;
+        const T mod2 = fr * fr + fi * fi;
+        T dv;
+        const T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
+        const T Kr = -A3 * dv * fr + A1 * lr * idx2, Ki = -A3 * dv * fi + A1 * li * idx2;
+        const T prr = pr + h1 * Kr, pri = pim + h1 * Ki;
+        const T por = pr + h * Kr, poi = pim + h * Ki;
+        T sA = T(0), eo[3];
 #pragma unroll
-        for (int i = 0; i < U1NS; ++i) {
-            const T v = partial_warp_sum(ts[i], lane, nlanes);
-            if (lane == 0) bacc[warp][i] += double(v);
+        for (int d = 0; d < 3; ++d) {
+            const T K = A1 * Kj[d] + Am * cB * mag[d];
+            const T er = ea[d] + h1 * K;
+            eo[d] = ea[d] + h * K;
+            sA += er * er;
+        }
+        ts[0] += fr; ts[1] += fi; ts[2] += fr * fr; ts[3] += fi * fi;
+        ts[4] += prr; ts[5] += pri; ts[6] += prr * prr + pri * pri;
+        ts[7] += grad * idx2;
+        ts[8] += vpot;
+        ts[9] += sA;
+        ts[10] += eB;
+        if (A.write) {
+            static_cast<T*>(A.out[0])[i] = fr;
+            static_cast<T*>(A.out[1])[i] = fi;
+            static_cast<T*>(A.out[2])[i] = por;
+            static_cast<T*>(A.out[3])[i] = poi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                static_cast<T*>(A.out[4 + d])[i] = wrap_angle(t0[d]);
+                static_cast<T*>(A.out[7 + d])[i] = eo[d];
+            }
+        }
+        if (++cnt == 64) {  // fold into FP64 every 64 sites
+#pragma unroll
+            for (int s = 0; s < U1NS; ++s) { acc[s] += double(ts[s]); ts[s] = T(0); }
+            cnt = 0;
         }
     }
-    cp_async_wait<0>();
-    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) acc[s] += double(ts[s]);
+    (void)idx;
 
-    // block reduction (FP64), partials, last block
+    // block reduction, partials, last block
+    __shared__ double red[8][U1NS];
+    const int lin = threadIdx.x, lane = lin & 31, warp = lin >> 5, nwarps = (blockDim.x + 31) >> 5;
+    const int nlanes = min(32, (int)blockDim.x - 32 * warp);
+#pragma unroll
+    for (int s = 0; s < U1NS; ++s) {
+        const double v = partial_warp_sum(acc[s], lane, nlanes);
+        if (lane == 0) red[warp][s] = v;
+    }
+    __syncthreads();
     if (lin < U1NS) {
         double t = 0.0;
-        for (int w = 0; w < nwarps; ++w) t += bacc[w][lin];
+        for (int w = 0; w < nwarps; ++w) t += red[w][lin];
         A.partials[(size_t)blockIdx.x * U1NS + lin] = t;
     }
     __threadfence();
@@ -329,7 +219,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
     if (!last) return;
     __threadfence();
     __shared__ double tot[U1NS];
-    const double invV = 1.0 / ((double)N * N * N);
+    const double invV = 1.0 / (double)n3;
     for (int s = warp; s < U1NS; s += nwarps) {
         double ks = 0.0, kc = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += nlanes) {
@@ -393,46 +283,22 @@ __global__ void u1_gauss_kernel(const T* pr, const T* pim, const T* qr, const T*
 
 __global__ void zero_gauss_kernel(DevState* st) { st->gauss[0] = st->gauss[1] = st->gauss[2] = 0.0; }
 
-// Tile geometry of the U(1) pass: BX x BY = 32 x 8 sites (smaller when N is
-// smaller), S = 5 stages, and the z-chunk ZC in {128, ..., 8} that best
-// balances the tiles over the resident blocks against the two extra planes a
-// chunk loads.
 void u1_geometry(Lattice* L) {
     Geometry& g = L->geo;
-    const int N = L->mc.N;
-    g.N = N;
-    g.V = 1;
-    g.BX = N < 32 ? N : 32;
-    g.BY = N < 8 ? N : 8;
-    g.S = 5;
-    g.threads = g.BX * g.BY;
-    g.ntx = N / g.BX;
-    g.nty = N / g.BY;
-    const size_t ts = L->prec == CL_FP32 ? 4 : 8;
-    g.smem = ts * ((size_t)g.S * 10 * (g.BX + 2) * (g.BY + 2) + 3 * 9 * (size_t)(g.BX + 1) * (g.BY + 1));
-    const void* fn = L->prec == CL_FP32 ? (const void*)u1_pass_kernel<float> : (const void*)u1_pass_kernel<double>;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-    cudaGetLastError();
+    g.N = L->mc.N;
+    g.threads = 256;
+    const size_t n3 = (size_t)g.N * g.N * g.N;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem);
+    if (L->prec == CL_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u1_pass_kernel<float>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u1_pass_kernel<double>, 256, 0);
     if (per_sm < 1) per_sm = 1;
-    const long long resident = (long long)L->sm_count * per_sm;
-    double best = -1.0;
-    int zc_best = 8 < N ? 8 : N;
-    for (int zc = 128; zc >= 8; zc /= 2) {
-        if (zc > N || N % zc != 0) continue;
-        const long long nt = (long long)g.ntx * g.nty * (N / zc);
-        const long long grid = nt < resident ? nt : resident;
-        const long long rounds = (nt + grid - 1) / grid;
-        const double eff = (double)nt / (double)(rounds * resident) * zc / (zc + 2.0);
-        if (eff > best + 1e-9) { best = eff; zc_best = zc; }
-    }
-    g.ZC = zc_best;
-    g.ntz = N / g.ZC;
-    g.ntiles = g.ntx * g.nty * g.ntz;
-    long long grid = resident < g.ntiles ? resident : g.ntiles;
+    long long grid = (long long)L->sm_count * per_sm;
+    const long long need = (long long)((n3 + 255) / 256);
+    if (grid > need) grid = need;
     if (grid > kMaxBlocks) grid = kMaxBlocks;
     g.grid = (int)grid;
+    g.ntiles = g.grid;
+    g.smem = 0;
 }
 
 cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
@@ -447,10 +313,8 @@ cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, boo
     A.mc = L->mc;
     A.pi = pi;
     A.write = write ? 1 : 0;
-    const Geometry& g = L->geo;
-    const dim3 block(g.BX, g.BY);
-    if (L->prec == CL_FP32) u1_pass_kernel<float><<<g.grid, block, g.smem, s>>>(A, g);
-    else u1_pass_kernel<double><<<g.grid, block, g.smem, s>>>(A, g);
+    if (L->prec == CL_FP32) u1_pass_kernel<float><<<L->geo.grid, 256, 0, s>>>(A);
+    else u1_pass_kernel<double><<<L->geo.grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
