@@ -312,3 +312,35 @@ def test_gauss_legendre_matches_oracle(s, N):
     assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
     assert abs(mm["t"] - 3 * dt) < 1e-13
     lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(cl.CL_FP64, 1e-5), (cl.CL_FP32, 2e-3)])
+def test_parametric_resonance_matches_mathieu_floquet(prec, tol):
+    """The GPU lattice in the linear regime of phi^2 chi^2 preheating (static
+    background, q* = 10, one chi mode at k_L = 0.5): its amplitude follows the
+    Mathieu equation chi'' + (k_L^2 + q* cos^2 t) chi = 0 over eight periods
+    and grows per period by the Floquet multiplier of the monodromy matrix
+    (the mean/fluctuation split carries phi = cos t exactly in FP64)."""
+    from tests.test_oracle_scalar import _mathieu_reference
+    N, qs = 8, 10.0
+    dx = 2.0 * math.sin(math.pi / N) / 0.5
+    kIR = 2 * math.pi / (N * dx)
+    k2 = (2.0 * math.sin(math.pi / N) / dx) ** 2
+    steps = int(round(math.pi / 0.01))
+    dt = math.pi / steps
+    m = cl.make_model(n_fields=2, pexp=2, lam=1.0, q=qs, omega_over_fstar=1.0)
+    lat = cl.Lattice(m, cl.make_grid(N, kIR, dt, "vv4", prec), cl.make_init(phi0=(1.0, 0.0), spectrum=0))
+    x = np.arange(N)
+    mode = np.ascontiguousarray(np.broadcast_to(np.cos(2 * np.pi * x / N)[None, None, :], (N, N, N)))
+    eps = 1e-6
+    lat.set_field(cl.FIELD(1), eps * mode)
+    sol, lam_max = _mathieu_reference(k2, qs, 1.0, 8 * np.pi)
+    amps = []
+    for n in range(8):
+        lat.evolve(steps)
+        c = (lat.get_field(cl.FIELD(1)) * mode).sum() / (mode * mode).sum() / eps
+        amps.append(c)
+        ref = sol.sol((n + 1) * np.pi)[0]
+        assert abs(c - ref) < tol * max(1.0, abs(ref)), (n, c, ref)
+    assert abs(amps[-1] / amps[-2] - lam_max) < 0.02 * lam_max
+    lat.close()
