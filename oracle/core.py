@@ -66,7 +66,7 @@ class _ScalarModelC(C.Structure):
 class _U1ModelC(C.Structure):
     _fields_ = [("N", C.c_int64), ("dx", C.c_double), ("alpha", C.c_double), ("fmp2", C.c_double),
                 ("lam", C.c_double), ("v2", C.c_double), ("e", C.c_double), ("kappa", C.c_double),
-                ("pot", C.c_int32), ("p", C.c_int32)]
+                ("pot", C.c_int32), ("p", C.c_int32), ("noncompact", C.c_int32), ("pad", C.c_int32)]
 
 
 # --- Yoshida weights (section 3.4.1 and the appendix table of VVn weights) ---
@@ -159,7 +159,9 @@ class Fluid:
 class U1Model:
     """Program-unit charged scalar of section 5 with V = (lam/4)(|phi|^2 - v2)^2
     (Abelian-Higgs, pot = 0) or the monomial inflaton V = (lam/p)(2|phi|^2)^(p/2)
-    of section 8 (pot = 1); gauge coupling e, kappa = (omega*/f*)^2."""
+    of section 8 (pot = 1); gauge coupling e, kappa = (omega*/f*)^2; the compact
+    (section 5.3) or, with noncompact = 1, the non-compact (section 5.2) gauge
+    kinetics."""
     N: int
     dx: float
     alpha: float
@@ -170,10 +172,11 @@ class U1Model:
     kappa: float = 1.0
     pot: int = 0
     p: int = 4
+    noncompact: int = 0
 
     def c(self):
         return _U1ModelC(self.N, self.dx, self.alpha, self.fmp2, self.lam, self.v2, self.e, self.kappa, self.pot,
-                         self.p)
+                         self.p, self.noncompact, 0)
 
 
 def potential_terms(m, phi, chi=None):

@@ -294,7 +294,16 @@ typedef struct {
     double kappa;   /* (omega_star/f_star)^2 */
     int32_t pot;    /* 0: Abelian-Higgs; 1: V = (lam/p)(2|phi|^2)^(p/2) (section 8.1 with |phi| -> sqrt(2)|phi|) */
     int32_t p;
+    int32_t noncompact; /* 1: the non-compact gauge kinetics of section 5.2 */
+    int32_t pad;
 } orc_u1_model;
+
+/* Magnetic part of the gauge field's action per plaquette angle theta_ij and
+ * its derivative: compact (section 5.3) 1 - cos theta_ij and sin theta_ij;
+ * non-compact (section 5.2) (D_i^+ A_j - D_j^+ A_i)^2 (e dx^2)^2 / 2 = theta_ij^2 / 2
+ * and theta_ij (the angles theta_i = e dx A_i are then plain real fields). */
+static double u1_mag_energy(const orc_u1_model* m, double t) { return m->noncompact ? 0.5 * t * t : 1.0 - cos(t); }
+static double u1_mag_force(const orc_u1_model* m, double t) { return m->noncompact ? t : sin(t); }
 
 /* V(|phi|^2) of the charged scalar and V' = dV/d|phi|^2 (so that dV/dphi* = V' phi). */
 static double gauge_potential(int pot, int p, double lam, double v2, double mod2, double* dv) {
@@ -363,8 +372,9 @@ void orc_u1_kernels(const orc_u1_model* m, const double* phi, const double* th, 
                         if (j == i) continue;
                         int64_t cmj[3] = {x, y, z};
                         cmj[j] = wrap(c[j] - 1, N);
-                        /* Im V_ij = -sin(theta_ij) */
-                        mag += -sin(plaq(m, th, i, j, x, y, z)) + sin(plaq(m, th, i, j, cmj[0], cmj[1], cmj[2]));
+                        /* Im V_ij = -sin(theta_ij); non-compact: -theta_ij */
+                        mag += -u1_mag_force(m, plaq(m, th, i, j, x, y, z)) +
+                               u1_mag_force(m, plaq(m, th, i, j, cmj[0], cmj[1], cmj[2]));
                     }
                     KA[(int64_t)i * V + n] =
                         a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;
@@ -380,7 +390,8 @@ void orc_u1_kernels(const orc_u1_model* m, const double* phi, const double* th, 
 /* Energies of section 5.4.1 (compact):
  * out[0] E_K^phi = <|pi|^2>/a^6,  out[1] E_G^phi = sum_i <|D_i^+ phi|^2>/a^2,
  * out[2] E_V = <V>,  out[3] E_K^A = kappa/(2a^4) sum_i <piA_i^2>,
- * out[4] E_G^A = kappa/(a^4 e^2 dx^4) sum_{i<j} <1 - cos theta_ij>. */
+ * out[4] E_G^A = kappa/(a^4 e^2 dx^4) sum_{i<j} <1 - cos theta_ij> (compact) or
+ *        <theta_ij^2/2> (non-compact, section 5.2). */
 void orc_u1_energies(const orc_u1_model* m, const double* phi, const double* pi, const double* th,
                      const double* piA, double a, double* out) {
     const int64_t N = m->N, V = N * N * N;
@@ -407,7 +418,7 @@ void orc_u1_energies(const orc_u1_model* m, const double* phi, const double* pi,
                     const double dr = (ur - pr[n]) / m->dx, di = (ui - pim[n]) / m->dx;
                     sg += dr * dr + di * di;
                     ska += piA[(int64_t)i * V + n] * piA[(int64_t)i * V + n];
-                    for (int j = i + 1; j < 3; ++j) sga += 1.0 - cos(plaq(m, th, i, j, x, y, z));
+                    for (int j = i + 1; j < 3; ++j) sga += u1_mag_energy(m, plaq(m, th, i, j, x, y, z));
                 }
             }
     const double a2 = a * a, a4 = a2 * a2, a6 = a4 * a2, dx4 = pow(m->dx, 4.0);

@@ -17,14 +17,16 @@ def _random_state(N, seed, model, a=1.0):
     return U1Lattice(model, phi, pi, th, piA, a=a)
 
 
-@pytest.mark.parametrize("a,alpha,pot,p", [(1.0, 0.0, 0, 4), (1.3, 0.5, 0, 4), (1.3, 0.5, 1, 4), (0.8, 1.0, 1, 6)])
-def test_u1_forces_are_minus_gradient_of_paper_energies(a, alpha, pot, p):
+@pytest.mark.parametrize("a,alpha,pot,p,nc", [(1.0, 0.0, 0, 4, 0), (1.3, 0.5, 0, 4, 0), (1.3, 0.5, 1, 4, 0),
+                                              (0.8, 1.0, 1, 6, 0), (1.3, 0.5, 0, 4, 1)])
+def test_u1_forces_are_minus_gradient_of_paper_energies(a, alpha, pot, p, nc):
     """U = a^{3+alpha} N^3 (E_G^phi + E_V + E_G^A) from the energies of section
     5.4.1; then K_phi = -dU/dphi* = -(1/2)(dU/dRe + i dU/dIm) and
     K_A,i = -(e dx/kappa) dU/dtheta_i (theta_i = e dx A_i). Both potentials:
-    Abelian-Higgs and the monomial inflaton."""
+    Abelian-Higgs and the monomial inflaton; compact and (nc = 1) non-compact
+    gauge kinetics (section 5.2)."""
     N = 5
-    m = U1Model(N=N, dx=0.55, alpha=alpha, fmp2=0.7, lam=1.3, v2=0.8, e=0.9, kappa=1.7, pot=pot, p=p)
+    m = U1Model(N=N, dx=0.55, alpha=alpha, fmp2=0.7, lam=1.3, v2=0.8, e=0.9, kappa=1.7, pot=pot, p=p, noncompact=nc)
     lat = _random_state(N, 7, m, a=a)
     Kp, KA = lat.kernels()
     scale = a ** (3 + alpha) * N ** 3
@@ -70,12 +72,13 @@ def test_u1_drift_rates_match_kinetic_energies():
     assert lat.a == a
 
 
-@pytest.mark.parametrize("fmp2,alpha", [(0.0, 0.0), (0.5, 0.5)])
-def test_gauss_law_holds_to_round_off(fmp2, alpha):
+@pytest.mark.parametrize("fmp2,alpha,nc", [(0.0, 0.0, 0), (0.5, 0.5, 0), (0.5, 0.5, 1)])
+def test_gauss_law_holds_to_round_off(fmp2, alpha, nc):
     """Starting from the Gauss-consistent initial condition of section 7.2, the
-    compact leapfrog keeps the discrete Gauss law to machine precision."""
+    compact (and the non-compact) leapfrog keeps the discrete Gauss law to
+    machine precision."""
     N, dt = 8, 0.05
-    m = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=fmp2, lam=1.0, v2=1.0, e=1.0, kappa=1.0)
+    m = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=fmp2, lam=1.0, v2=1.0, e=1.0, kappa=1.0, noncompact=nc)
     kIR = 2 * np.pi / (N * 0.5)
     phi, pi, th, piA, dx = u1_ic(m, kIR, [0.0, 0.0], [0.0, 0.0], seed=5, omega_over_fstar=1.0)
     lat = U1Lattice(m, phi, pi, th, piA)
@@ -121,12 +124,13 @@ def test_u1_energy_conservation_second_order():
     assert abs(slope - 2) < 0.3, (drift, slope)
 
 
-def test_gauge_invariance_of_the_evolution():
+@pytest.mark.parametrize("nc", [0, 1])
+def test_gauge_invariance_of_the_evolution(nc):
     """phi -> e^{-i e alpha} phi, pi -> e^{-i e alpha} pi,
     theta_i -> theta_i - e (alpha(n+i) - alpha(n)) commutes with the leapfrog
-    (U(1) toolkit, section 3.2.2)."""
+    (U(1) toolkit, section 3.2.2), compact and non-compact."""
     N, dt = 6, 0.05
-    m = U1Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=0.8, kappa=1.0)
+    m = U1Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, e=0.8, kappa=1.0, noncompact=nc)
     A = _random_state(N, 37, m)
     al = inputs.rng(99).uniform(-2, 2, size=(N, N, N))
 
@@ -269,3 +273,39 @@ def test_charged_potential_curvature_is_the_second_derivative(pot, p):
         assert abs(dv + d2 * chi0 ** 2 - num) < 1e-6 * (1 + abs(num))
         if pot == 1 and p == 2:
             assert dv + d2 * chi0 ** 2 == pytest.approx(m.lam, rel=1e-15)  # plain mass term lam chi^2/2
+
+
+@pytest.mark.parametrize("integ", ["vv2", "vv4"])
+def test_noncompact_free_photon_is_the_exact_lattice_mode(integ):
+    """Without charged matter (phi = pi = 0) the non-compact gauge field of
+    section 5.2 is a free lattice photon: a transverse mode A_y(x) = cos(2 pi x/N)
+    (so sum_i D_i^- A_i = 0) has omega^2 = k_L^2 = 4 sin^2(pi/N)/dx^2, and one VV2
+    step maps (A, A') by the exact 2 x 2 matrix of that oscillator; VV4 is the
+    Yoshida product of three such maps (static background, e = 1.3)."""
+    N, dx, dt, n = 8, 0.7, 0.05, 40
+    e, kappa = 1.3, 0.9
+    m = U1Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=0.0, e=e, kappa=kappa, noncompact=1)
+    x = np.arange(N)
+    prof = np.broadcast_to(np.cos(2 * np.pi * x / N)[None, None, :], (N, N, N))
+    A0, V0 = 0.3, -0.2  # amplitude of A_y and of A_y' = piA_y (a = 1, alpha = 0)
+    th = np.zeros((3, N, N, N))
+    th[1] = e * dx * A0 * prof
+    piA = np.zeros((3, N, N, N))
+    piA[1] = V0 * prof
+    zero = np.zeros((2, N, N, N))
+    lat = U1Lattice(m, zero, zero, th, piA)
+    w2 = 4 * np.sin(np.pi / N) ** 2 / dx ** 2
+
+    def vv2_map(h):
+        return np.array([[1 - h * h * w2 / 2, h], [-h * w2 * (1 - h * h * w2 / 4), 1 - h * h * w2 / 2]])
+
+    w = _vv(integ)
+    M = np.eye(2)
+    for wp in w:
+        M = vv2_map(wp * dt) @ M
+    ref = np.linalg.matrix_power(M, n) @ np.array([A0, V0])
+    lat.vv_steps(w, dt, n)
+    got_A = lat.theta[1] / (e * dx)
+    assert np.max(np.abs(got_A - ref[0] * prof)) < 1e-12
+    assert np.max(np.abs(lat.piA[1] - ref[1] * prof)) < 1e-12
+    assert np.max(np.abs(lat.theta[0])) == 0.0 and np.max(np.abs(lat.theta[2])) == 0.0
