@@ -76,7 +76,9 @@ typedef enum {
  *   potential of section 8.1, V = (lam/p)|phi|^p + (q/2) phi^2 chi^2.
  * CL_MODEL_U1: one complex scalar phi = (phi_0 + i phi_1)/sqrt(2) with
  *   V = (lam/4)(|phi|^2 - vev2)^2, coupled with charge e to a compact U(1)
- *   gauge field in temporal gauge (section 5.3). */
+ *   gauge field in temporal gauge (section 5.3), or with noncompact = 1 to the
+ *   non-compact one (section 5.2: magnetic term (D_i^+ A_j - D_j^+ A_i)^2, link
+ *   angles theta_i = e dx A_i kept unwrapped). */
 typedef enum { CL_MODEL_SCALAR = 0, CL_MODEL_U1 = 1, CL_MODEL_SU2 = 2 } cl_model_kind;
 
 /* Integrators (the paper's "switch", section 1.2):
@@ -140,7 +142,7 @@ typedef struct {
     double fluid_w;          /* CL_BG_FLUID: equation of state w of the fluid */
     double hubble0;          /* CL_BG_FLUID: program Hubble rate a'/a at t = 0 */
     int32_t potential;       /* U(1), SU(2): cl_gauge_potential */
-    int32_t reserved;        /* set to 0 */
+    int32_t noncompact;      /* U(1): 1 selects the non-compact gauge kinetics of section 5.2 (0: compact) */
     double gauge_e_u1;       /* SU(2): U(1) coupling eA = g_A Q_A of the doublet (section 8.3); 0: no U(1) sector */
 } cl_model;
 

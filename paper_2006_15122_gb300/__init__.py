@@ -58,7 +58,7 @@ class cl_model(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_fields", C.c_int32), ("pexp", C.c_int32), ("background", C.c_int32),
                 ("alpha", C.c_double), ("fstar_over_mp", C.c_double), ("omega_over_fstar", C.c_double),
                 ("lam", C.c_double), ("q", C.c_double), ("vev2", C.c_double), ("gauge_e", C.c_double),
-                ("fluid_w", C.c_double), ("hubble0", C.c_double), ("potential", C.c_int32), ("reserved", C.c_int32),
+                ("fluid_w", C.c_double), ("hubble0", C.c_double), ("potential", C.c_int32), ("noncompact", C.c_int32),
                 ("gauge_e_u1", C.c_double)]
 
 
@@ -189,9 +189,9 @@ def _dev_ptr(t):
 
 def make_model(kind=CL_MODEL_SCALAR, n_fields=1, pexp=2, alpha=0.0, fstar_over_mp=0.0, omega_over_fstar=1.0,
                lam=1.0, q=0.0, vev2=1.0, gauge_e=1.0, background=CL_BG_FRIEDMANN, fluid_w=0.0, hubble0=0.0,
-               potential=CL_POT_HIGGS, gauge_e_u1=0.0):
+               potential=CL_POT_HIGGS, gauge_e_u1=0.0, noncompact=0):
     return cl_model(kind, n_fields, pexp, background, alpha, fstar_over_mp, omega_over_fstar, lam, q, vev2, gauge_e,
-                    fluid_w, hubble0, potential, 0, gauge_e_u1)
+                    fluid_w, hubble0, potential, noncompact, gauge_e_u1)
 
 
 def make_grid(N, kIR, dt, integrator=CL_INT_VV2, precision=CL_FP64, force_dt=False):

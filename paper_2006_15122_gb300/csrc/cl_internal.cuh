@@ -81,6 +81,7 @@ struct ModelConst {
     // and ext = either of the two (the 37-array layout)
     double e2;
     int chi, ext;
+    int nc;  // U(1): non-compact gauge kinetics (section 5.2)
 };
 
 // Potential of the charged scalar of the gauge models as a function of

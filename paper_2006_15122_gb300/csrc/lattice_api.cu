@@ -305,6 +305,8 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
         if (!(model->gauge_e > 0)) return fail(nullptr, CL_ERR_ARG, "gauge_e must be positive");
         if (model->potential != CL_POT_HIGGS && model->potential != CL_POT_MONOMIAL)
             return fail(nullptr, CL_ERR_ARG, "unknown gauge potential");
+        if (model->noncompact != 0 && (model->noncompact != 1 || model->kind != CL_MODEL_U1))
+            return fail(nullptr, CL_ERR_ARG, "noncompact is 0, or 1 for the U(1) model");
         if (model->potential == CL_POT_MONOMIAL && model->pexp != 2 && model->pexp != 4 && model->pexp != 6)
             return fail(nullptr, CL_ERR_ARG, "pexp must be 2, 4 or 6");
         if (model->kind == CL_MODEL_SU2) {
@@ -382,6 +384,7 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     mc.e2 = mc.kind == CL_MODEL_SU2 ? model->gauge_e_u1 : 0.0;
     mc.chi = mc.kind == CL_MODEL_SU2 && model->n_fields == 2 ? 1 : 0;
     mc.ext = mc.e2 > 0 || mc.chi ? 1 : 0;
+    mc.nc = mc.kind == CL_MODEL_U1 && model->noncompact ? 1 : 0;
     mc.bg = model->background == CL_BG_FLUID ? 1 : 0;
     mc.bg_p = mc.bg ? 2.0 / (3.0 * (1.0 + model->fluid_w) - 2.0 * model->alpha) : 1.0;
     mc.bg_H0 = mc.bg ? model->hubble0 : 0.0;
@@ -771,6 +774,7 @@ extern "C" cl_status lattice_save(cl_lattice* h, const char* path) {
     hd.model.omega_over_fstar = sqrt(h->mc.kappa);
     hd.model.potential = h->mc.gpot;
     hd.model.gauge_e_u1 = h->mc.e2;
+    hd.model.noncompact = h->mc.nc;
     if (h->mc.kind == CL_MODEL_SU2) hd.model.n_fields = h->mc.chi ? 2 : 1;
     hd.steps = h->steps_done;
     hd.nbytes = st.size() + (uint64_t)h->buf.narr * arr.size();

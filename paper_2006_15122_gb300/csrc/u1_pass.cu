@@ -15,6 +15,9 @@
 //   phi <- phi + dt a_{1/2}^{-(3-alpha)} pi,
 //   V_i <- exp(-i e dx dt a_{1/2}^{-(1-alpha)} piA_i) V_i  (theta_i += ..., wrapped to [-pi, pi)),
 // the exact exponential of the link drift (unitary for any step).
+// Non-compact formulation (section 5.2, mc.nc): the same kernels with sin theta_ij
+// replaced by theta_ij (the lattice curl of curl A) and 1 - cos theta_ij by
+// theta_ij^2/2 in E_G^A; the angles theta_i = e dx A_i are then not wrapped.
 // Energies (section 5.4.1): E_K^phi = <|pi|^2>/a^6, E_G^phi = sum_i <|D_i^+ phi|^2>/a^2,
 // E_V = <V>, E_K^A = kappa/(2a^4) sum_i <piA_i^2>,
 // E_G^A = kappa/(a^4 e^2 dx^4) sum_{i<j} <1 - cos theta_ij>.
@@ -54,6 +57,12 @@ template <typename T> __device__ __forceinline__ void sc(T x, T* s, T* c);
 // stay exact
 template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* c) { __sincosf(x, s, c); }
 template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
+// link phases of the non-compact formulation: its angles are not wrapped, so FP32
+// takes the range-reduced sincosf
+template <typename T> __device__ __forceinline__ void sc_link(bool nc, T x, T* s, T* c) {
+    if (sizeof(T) == 4 && nc) sincosf(float(x), reinterpret_cast<float*>(s), reinterpret_cast<float*>(c));
+    else sc<T>(x, s, c);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(const U1Args A) {
@@ -65,6 +74,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
     const T dx = T(A.mc.dx), idx = T(1.0 / A.mc.dx), idx2 = T(A.mc.idx2);
     const T lam = T(A.mc.lam), v2 = T(A.mc.vev2);
     const T cJ = T(2.0 * A.mc.e / A.mc.dx / A.mc.kappa), cB = T(1.0 / (A.mc.e * A.mc.dx * A.mc.dx * A.mc.dx));
+    const bool nc = A.mc.nc != 0;  // non-compact: the plaquette angle itself replaces sin, theta^2/2 replaces 1 - cos
     (void)dx;
     const T* PR = static_cast<const T*>(A.in[0]);
     const T* PIm = static_cast<const T*>(A.in[1]);
@@ -110,12 +120,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
             const size_t np = at(ox, oy, oz), nm = at(-ox, -oy, -oz);
             const T ur0 = phr(np), ui0 = phi_(np);
             T s, cc;
-            sc<T>(t0[d], &s, &cc);
+            sc_link<T>(nc, t0[d], &s, &cc);
             // V_i phi(n+i) = (cos t - i sin t)(ur0 + i ui0)
             const T ur = cc * ur0 + s * ui0, ui = cc * ui0 - s * ur0;
             const T tm = th(d, nm);
             T sm, cm;
-            sc<T>(tm, &sm, &cm);
+            sc_link<T>(nc, tm, &sm, &cm);
             const T wr0 = phr(nm), wi0 = phi_(nm);
             // V_i*(n-i) phi(n-i) = (cos tm + i sin tm)(wr0 + i wi0)
             const T wr = cm * wr0 - sm * wi0, wi = cm * wi0 + sm * wr0;
@@ -133,9 +143,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
             const int oix = ii == 0, oiy = ii == 1, oiz = ii == 2;
             const int ojx = jj == 0, ojy = jj == 1, ojz = jj == 2;
             const T pn = t0[ii] + th(jj, at(oix, oiy, oiz)) - th(ii, at(ojx, ojy, ojz)) - t0[jj];
-            T cn;
-            sc<T>(pn, &sp[pr_], &cn);
-            eB += T(1) - cn;
+            if (nc) {
+                sp[pr_] = pn;
+                eB += T(0.5) * pn * pn;
+            } else {
+                T cn;
+                sc<T>(pn, &sp[pr_], &cn);
+                eB += T(1) - cn;
+            }
         }
         // forces: sum_j [Im V_ij(n) - Im V_ij(n-j)], Im V_ij = -sin(theta_ij)
         T mag[3] = {T(0), T(0), T(0)};
@@ -150,8 +165,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
                 const T sn = ii < jj ? sp[pr_] : -sp[pr_];
                 const T pm = th(ii, at(-ojx, -ojy, -ojz)) + th(jj, at(oix - ojx, oiy - ojy, oiz - ojz)) - t0[ii] -
                              th(jj, at(-ojx, -ojy, -ojz));
-                T smm, cmm;
-                sc<T>(pm, &smm, &cmm);
+                T smm = pm, cmm;
+                if (!nc) sc<T>(pm, &smm, &cmm);
                 mag[ii] += -sn + smm;
             }
         }
@@ -182,7 +197,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
             static_cast<T*>(A.out[3])[i] = poi;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                static_cast<T*>(A.out[4 + d])[i] = wrap_angle(t0[d]);
+                static_cast<T*>(A.out[4 + d])[i] = nc ? t0[d] : wrap_angle(t0[d]);
                 static_cast<T*>(A.out[7 + d])[i] = eo[d];
             }
         }
@@ -238,18 +253,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
     }
 }
 
-// Closing drift of the leapfrog (in place): phi += cd pi, theta += cdA piA (wrapped).
+// Closing drift of the leapfrog (in place): phi += cd pi, theta += cdA piA (wrapped when compact).
 template <typename T>
 __global__ void u1_drift_kernel(T* pr, T* pim, const T* qr, const T* qi, T* t0, T* t1, T* t2, const T* e0,
-                                const T* e1, const T* e2, size_t n, DevState* st) {
+                                const T* e1, const T* e2, size_t n, DevState* st, int nc) {
     if (st->error) return;
     const T cd = T(st->cd), cdA = T(st->cdA);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         pr[i] += cd * qr[i];
         pim[i] += cd * qi[i];
-        t0[i] = wrap_angle(t0[i] + cdA * e0[i]);
-        t1[i] = wrap_angle(t1[i] + cdA * e1[i]);
-        t2[i] = wrap_angle(t2[i] + cdA * e2[i]);
+        const T a0 = t0[i] + cdA * e0[i], a1 = t1[i] + cdA * e1[i], a2 = t2[i] + cdA * e2[i];
+        t0[i] = nc ? a0 : wrap_angle(a0);
+        t1[i] = nc ? a1 : wrap_angle(a1);
+        t2[i] = nc ? a2 : wrap_angle(a2);
     }
 }
 
@@ -325,12 +341,12 @@ cudaError_t u1_launch_drift(Lattice* L, int cur, cudaStream_t s) {
     if (L->prec == CL_FP32)
         u1_drift_kernel<float><<<grid, 256, 0, s>>>((float*)b[0], (float*)b[1], (const float*)b[2], (const float*)b[3],
                                                     (float*)b[4], (float*)b[5], (float*)b[6], (const float*)b[7],
-                                                    (const float*)b[8], (const float*)b[9], n, L->buf.st);
+                                                    (const float*)b[8], (const float*)b[9], n, L->buf.st, L->mc.nc);
     else
         u1_drift_kernel<double><<<grid, 256, 0, s>>>((double*)b[0], (double*)b[1], (const double*)b[2],
                                                      (const double*)b[3], (double*)b[4], (double*)b[5], (double*)b[6],
                                                      (const double*)b[7], (const double*)b[8], (const double*)b[9], n,
-                                                     L->buf.st);
+                                                     L->buf.st, L->mc.nc);
     return cudaGetLastError();
 }
 

@@ -22,9 +22,9 @@ def angle_err(a, b):
 
 
 def gpu_u1(N, kIR, dt, prec, fmp=0.0, alpha=0.0, e=1.0, lam=1.0, v2=1.0, omega=1.0, spectrum=0, seed=0,
-           phi0=(0.0, 0.0), integ="lf", pot=0, p=4, dphi0=(0.0, 0.0)):
+           phi0=(0.0, 0.0), integ="lf", pot=0, p=4, dphi0=(0.0, 0.0), nc=0):
     m = cl.make_model(kind=cl.CL_MODEL_U1, alpha=alpha, fstar_over_mp=fmp, omega_over_fstar=omega, lam=lam,
-                      vev2=v2, gauge_e=e, potential=pot, pexp=p)
+                      vev2=v2, gauge_e=e, potential=pot, pexp=p, noncompact=nc)
     g = cl.make_grid(N, kIR, dt, integ, prec)
     return cl.Lattice(m, g, cl.make_init(phi0=phi0, dphi0=dphi0, seed=seed, spectrum=spectrum))
 
@@ -208,4 +208,56 @@ def test_u1_monomial_initial_conditions_match_oracle(p):
     gphi, gpi, gth, gpa = get_all(lat)
     assert rel(gphi, phi) < 1e-12 and rel(gpi, pi) < 1e-12 and rel(gpa, pa) < 1e-11
     assert np.all(gth == 0.0)
+    lat.close()
+
+
+@pytest.mark.parametrize("integ,fmp,alpha", [("lf", 0.0, 0.0), ("vv2", 0.8, 0.5), ("vv4", 0.5, 1.0)])
+def test_u1_noncompact_matches_oracle(integ, fmp, alpha):
+    """Non-compact gauge kinetics (section 5.2): fields, unwrapped angles and
+    momenta against the oracle after 7 steps, FP64, with expansion; large
+    angles (|theta| up to 2.5) so that the compact and non-compact forms differ."""
+    import oracle
+    N, kIR, dt = 16, 2 * math.pi / (16 * 0.5), 0.04
+    lat = gpu_u1(N, kIR, dt, cl.CL_FP64, fmp=fmp, alpha=alpha, e=0.9, lam=1.2, v2=0.7, omega=1.1, integ=integ, nc=1)
+    om = U1Model(N=N, dx=0.5, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.7, e=0.9, kappa=1.21, noncompact=1)
+    phi = inputs.fields(2, N, seed=33, amp=0.6, kmax=4, means=[0.4, -0.1])
+    pi = inputs.fields(2, N, seed=34, amp=0.3, kmax=4)
+    th = inputs.angles(N, 35, scale=2.5)
+    pa = inputs.fields(3, N, seed=36, amp=0.2, kmax=4)
+    ref = U1Lattice(om, phi, pi, th, pa)
+    ref.b = math.sqrt(fmp * fmp / 3 * ref.energies().sum()) if fmp > 0 else 0.0
+    for i in range(2):
+        lat.set_field(cl.FIELD(i), phi[i])
+        lat.set_field(cl.MOMENTUM(i), pi[i])
+    for i in range(3):
+        lat.set_field(cl.LINK(i), th[i])
+        lat.set_field(cl.EMOMENTUM(i), pa[i])
+    lat.set_background(1.0, ref.b, 0.0)
+    assert lat.measure_means()["EG"][1] == pytest.approx(ref.energies()[4], rel=1e-12)
+    if integ == "lf":
+        ref.lf_prepare(dt)
+        lat.evolve(7)
+        ref.lf_steps(dt, 7)
+    else:
+        lat.evolve(7)
+        ref.vv_steps({"vv2": oracle.VV2, "vv4": oracle.VV4}[integ], dt, 7)
+    gphi, gpi, gth, gpa = get_all(lat)
+    assert rel(gphi, ref.phi) < 1e-12 and rel(gpi, ref.pi) < 1e-12
+    assert np.max(np.abs(gth - ref.theta)) < 1e-12  # unwrapped: equal as numbers, not just as phases
+    assert rel(gpa, ref.piA) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 + 1e-12 * abs(ref.b)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(cl.CL_FP64, 1e-13), (cl.CL_FP32, 1e-5)])
+def test_u1_noncompact_keeps_gauss_law(prec, tol):
+    N, dx = 32, 0.5
+    lat = gpu_u1(N, 2 * math.pi / (N * dx), 0.05, prec, spectrum=1, seed=8, integ="vv4", nc=1)
+    g = []
+    for _ in range(4):
+        lat.evolve(10)
+        g.append(lat.measure_means()["gauss_violation"])
+    assert max(g) < tol, g
+    assert lat.measure_means()["EG"][1] > 0.0
     lat.close()
