@@ -230,6 +230,20 @@ int32_t lattice_spectrum_bins(const cl_lattice* h);
 cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, double* k, double* Delta,
                                    int64_t* counts);
 
+/* Power spectra of the gauge fields (sections 5.4 and 6.3), with the shells,
+ * k and normalisation of lattice_measure_spectrum and the components summed:
+ *   sector 0: the U(1) field (CL_MODEL_U1, or CL_MODEL_SU2 with gauge_e_u1 > 0);
+ *             what 0: E_i = piA_i / a^{1-alpha};
+ *             what 1: B_i = sin(theta_jk)/(e dx^2) (compact) or theta_jk/(e dx^2)
+ *             = eps_ijk D_j^+ A_k (non-compact), (i, j, k) cyclic, theta_jk the
+ *             plaquette angle at n;
+ *   sector 1: the SU(2) field (CL_MODEL_SU2); what 0: E_i^a = piB_i^a / a^{1-alpha};
+ *             what 1: B_i^a = -2 q_a[U_jk(n)]/(g dx^2), the sigma^a part of the
+ *             plaquette quaternion (the trace form of section 6.3).
+ * CL_ERR_ARG when the model has no such sector.  Synchronizes the stream. */
+cl_status lattice_measure_gauge_spectrum(cl_lattice* h, int32_t sector, int32_t what, double* k, double* Delta,
+                                         int64_t* counts);
+
 /* Array indices of get/set: scalar models: 0..n-1 the fields, 4..4+n-1
  * their momenta.  U(1): 0 Re phi, 1 Im phi, 4 Re pi, 5 Im pi, 8..10 the link
  * angles theta_i = e dx A_i (V_i = exp(-i theta_i)), 12..14 the electric

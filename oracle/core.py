@@ -344,6 +344,16 @@ class U1Lattice:
                                 C.byref(b), C.byref(ek), C.byref(eka))
         self.b, self.EKm = b.value, (ek.value, eka.value)
 
+    def electric(self):
+        """E_i = piA_i / a^{1-alpha} (section 5.4), shape (3, N, N, N)."""
+        return self.piA / self.a ** (1.0 - self.m.alpha)
+
+    def magnetic(self):
+        """B_i with (i, j, k) cyclic (section 5.4): sin(theta_jk)/(e dx^2) in the
+        compact formulation (-Im V_jk/(e dx^2), V_jk = exp(-i theta_jk)), the
+        lattice curl theta_jk/(e dx^2) = eps_ijk D_j^+ A_k in the non-compact one."""
+        return _u1_magnetic(self.theta, self.m.e, self.m.dx, self.m.noncompact)
+
     def vv_steps(self, weights, dt, n=1):
         """Compact velocity-Verlet VVn (sections 5.3.2, 5.3.3) on synchronized data."""
         w = np.ascontiguousarray(weights, dtype=np.float64)
@@ -426,6 +436,15 @@ class SU2Lattice:
         out = np.zeros(3)
         lib().orc_su2_gauss(self._mp(), _p(self.phi), _p(self.pi), _p(self.u), _p(self.piB), _p(out))
         return out[0] / max(out[1] + out[2], 1e-300)
+
+    def electric(self):
+        """E_i^a = piB_i^a / a^{1-alpha} (section 6.3), shape (3, 3, N, N, N)."""
+        return self.piB / self.a ** (1.0 - self.m.alpha)
+
+    def magnetic(self):
+        """B_i^a = (eps_ijk/(2 g dx^2)) Tr[(i sigma^a/2)(U_jk - U_kj)] (section 6.3),
+        i.e. -2 q_a[U_jk]/(g dx^2) for (i, j, k) cyclic, shape (3, 3, N, N, N)."""
+        return _su2_magnetic(self.u, self.m.g, self.m.dx)
 
     def vv_steps(self, weights, dt, n=1):
         """SU(2) velocity-Verlet VVn (sections 6.2.2, 6.2.3) on synchronized data."""
@@ -521,6 +540,14 @@ class SU2U1Lattice:
         lib().orc_su2u1_gauss(self._mp(), _p(self.phi), _p(self.pi), _p(self.u), _p(self.piB), _p(self.piA), _p(out))
         return out[0] / max(out[1] + out[2], 1e-300), out[3] / max(out[4] + out[5], 1e-300)
 
+    def electric(self, sector):
+        """E of the U(1) (sector 0) or SU(2) (sector 1) field."""
+        return (self.piA if sector == 0 else self.piB) / self.a ** (1.0 - self.m.alpha)
+
+    def magnetic(self, sector):
+        return _u1_magnetic(self.theta, self.m.eA, self.m.dx, 0) if sector == 0 else _su2_magnetic(self.u, self.m.g,
+                                                                                                      self.m.dx)
+
     def vv_steps(self, weights, dt, n=1):
         w = np.ascontiguousarray(weights, dtype=np.float64)
         a, b = C.c_double(self.a), C.c_double(self.b)
@@ -529,3 +556,35 @@ class SU2U1Lattice:
                                     _p(self.piB), _p(self.theta), _p(self.piA), _p(self.chi), _p(self.pchi),
                                     C.byref(a), C.byref(b))
         self.a, self.b = a.value, b.value
+
+
+def _shift(a, d):
+    """a(n + d^) on the periodic lattice, arrays indexed [z, y, x], d = 0, 1, 2 for x, y, z."""
+    return np.roll(a, -1, axis=a.ndim - 1 - d)
+
+
+def _u1_magnetic(theta, e, dx, noncompact):
+    out = np.zeros_like(theta)
+    for i in range(3):
+        j, k = (i + 1) % 3, (i + 2) % 3
+        t = theta[j] + _shift(theta[k], j) - _shift(theta[j], k) - theta[k]
+        out[i] = (t if noncompact else np.sin(t)) / (e * dx * dx)
+    return out
+
+
+def _qmul(p, q):
+    r0 = p[0] * q[0] - p[1] * q[1] - p[2] * q[2] - p[3] * q[3]
+    r1 = p[0] * q[1] + q[0] * p[1] - (p[2] * q[3] - p[3] * q[2])
+    r2 = p[0] * q[2] + q[0] * p[2] - (p[3] * q[1] - p[1] * q[3])
+    r3 = p[0] * q[3] + q[0] * p[3] - (p[1] * q[2] - p[2] * q[1])
+    return np.stack([r0, r1, r2, r3])
+
+
+def _su2_magnetic(u, g, dx):
+    conj = np.array([1.0, -1.0, -1.0, -1.0])[:, None, None, None]
+    out = np.zeros((3, 3) + u.shape[2:])
+    for i in range(3):
+        j, k = (i + 1) % 3, (i + 2) % 3
+        P = _qmul(_qmul(_qmul(u[j], _shift(u[k], j)), conj * _shift(u[j], k)), conj * u[k])
+        out[i] = -2.0 * P[1:] / (g * dx * dx)
+    return out

@@ -87,7 +87,7 @@ class cl_train_cfg(C.Structure):
 
 
 SYMBOLS = ["cl_status_str", "cl_last_error", "lattice_init", "lattice_evolve", "lattice_measure_means",
-           "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_get_field", "lattice_set_field",
+           "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_measure_gauge_spectrum", "lattice_get_field", "lattice_set_field",
            "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy",
            "lattice_energies_noalloc", "ensemble_init", "ensemble_evolve", "ensemble_observe",
            "ensemble_member", "ensemble_destroy", "ensemble_get_tile", "ensemble_set_tile",
@@ -124,6 +124,7 @@ def load(build_if_missing=True):
         "lattice_measure_means": ([vp, C.POINTER(cl_means)], C.c_int),
         "lattice_spectrum_bins": ([vp], i32),
         "lattice_measure_spectrum": ([vp, i32, i32, pd, pd, C.POINTER(C.c_int64)], C.c_int),
+        "lattice_measure_gauge_spectrum": ([vp, i32, i32, pd, pd, C.POINTER(C.c_int64)], C.c_int),
         "lattice_get_field": ([vp, i32, vp, i32], C.c_int),
         "lattice_set_field": ([vp, i32, vp, i32], C.c_int),
         "lattice_set_background": ([vp, d, d, d], C.c_int),
@@ -259,6 +260,18 @@ class Lattice:
         _check(load().lattice_measure_spectrum(self.h, field, what, k.ctypes.data_as(C.POINTER(C.c_double)),
                                                D.ctypes.data_as(C.POINTER(C.c_double)),
                                                c.ctypes.data_as(C.POINTER(C.c_int64))), self.h)
+        return k, D, c
+
+    def gauge_spectrum(self, sector=0, what=0):
+        """Spectrum of the electric (what 0) or magnetic (what 1) field of the
+        U(1) (sector 0) or SU(2) (sector 1) gauge field."""
+        nb = load().lattice_spectrum_bins(self.h)
+        k = np.zeros(nb)
+        D = np.zeros(nb)
+        c = np.zeros(nb, dtype=np.int64)
+        _check(load().lattice_measure_gauge_spectrum(self.h, sector, what, k.ctypes.data_as(C.POINTER(C.c_double)),
+                                                     D.ctypes.data_as(C.POINTER(C.c_double)),
+                                                     c.ctypes.data_as(C.POINTER(C.c_int64))), self.h)
         return k, D, c
 
     def observe(self, kmax=0.0):

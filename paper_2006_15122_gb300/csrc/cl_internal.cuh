@@ -353,6 +353,9 @@ cudaError_t launch_finish_drift(Lattice* L, cudaStream_t s);
 cudaError_t launch_get_field(Lattice* L, int which, double* dst, cudaStream_t s);
 cudaError_t launch_set_field(Lattice* L, int which, const double* src, cudaStream_t s);
 cudaError_t launch_spectrum(Lattice* L, int slot, int accumulate, cudaStream_t s);
+// Gauge-field spectra: sector 0 U(1), 1 SU(2); what 0 electric momenta, 1 magnetic
+// field; accumulates every component into L->bins and returns their number.
+cudaError_t launch_gauge_spectrum(Lattice* L, int sector, int what, int* ncomp, cudaStream_t s);
 int spectrum_bins(int N);
 
 // ensemble.cu: the CL_OBS_SIZE observables of a two-field lattice from its

@@ -159,6 +159,125 @@ __global__ void bin_kernel(const double2* F, int N, int nbins, double* out /* 3*
         if (h[i] != 0.0) atomicAdd(&out[i], h[i]);
 }
 
+// FFT of the FP64 work array and shell binning into L->bins (added when accumulate)
+static cudaError_t spectrum_of_work(Lattice* L, int accumulate, cudaStream_t s) {
+    const int N = L->mc.N;
+    const int nbins = spectrum_bins(N);
+    if (cufftExecD2Z(L->plan_r2c, L->work, (cufftDoubleComplex*)L->cwork) != CUFFT_SUCCESS) return cudaErrorUnknown;
+    if (!accumulate) cudaMemsetAsync(L->bins, 0, 3 * (size_t)nbins * sizeof(double), s);
+    const size_t smem = 3 * (size_t)nbins * sizeof(double);
+    bin_kernel<<<L->sm_count * 2, 512, smem, s>>>((const double2*)L->cwork, N, nbins, L->bins);
+    return cudaGetLastError();
+}
+
+// Magnetic field of the U(1) sector, component i (sections 5.4, 5.2):
+// B_i = f(theta_jk(n))/(e dx^2) with (i, j, k) cyclic, theta_jk the plaquette
+// angle, f = sin (compact: B_i = -Im V_jk/(e dx^2)) or the identity (non-compact:
+// B_i = eps_ijk D_j^+ A_k).
+template <typename T>
+__global__ void u1_magnetic_kernel(const T* tj, const T* tk, int N, int j, int k, double c, int nc, double* out) {
+    const size_t n3 = (size_t)N * N * N;
+    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((size_t)N * N));
+        const int c0[3] = {x, y, z};
+        int pj[3] = {x, y, z}, pk[3] = {x, y, z};
+        pj[j] = c0[j] + 1 == N ? 0 : c0[j] + 1;
+        pk[k] = c0[k] + 1 == N ? 0 : c0[k] + 1;
+        const size_t nj = ((size_t)pj[2] * N + pj[1]) * N + pj[0], nk = ((size_t)pk[2] * N + pk[1]) * N + pk[0];
+        const double t = (double)tj[n] + (double)tk[nj] - (double)tj[nk] - (double)tk[n];
+        out[n] = c * (nc ? t : sin(t));
+    }
+}
+
+// Magnetic field of the SU(2) sector, component (i, a) (section 6.3):
+// B_i^a = -2 q_a[U_jk(n)]/(g dx^2), (i, j, k) cyclic, U_jk = U_j(n) U_k(n+j) U_j^dag(n+k) U_k^dag(n)
+// as a unit quaternion q0 + i q.sigma.
+__device__ __forceinline__ void qmul_d(const double* p, const double* q, double* r) {
+    const double r0 = p[0] * q[0] - p[1] * q[1] - p[2] * q[2] - p[3] * q[3];
+    const double r1 = p[0] * q[1] + q[0] * p[1] - (p[2] * q[3] - p[3] * q[2]);
+    const double r2 = p[0] * q[2] + q[0] * p[2] - (p[3] * q[1] - p[1] * q[3]);
+    const double r3 = p[0] * q[3] + q[0] * p[3] - (p[1] * q[2] - p[2] * q[1]);
+    r[0] = r0; r[1] = r1; r[2] = r2; r[3] = r3;
+}
+struct Links4 {
+    const void* u[12];  // U_i component c at 4 i + c
+};
+template <typename T>
+__global__ void su2_magnetic_kernel(Links4 U, int N, int j, int k, int a, double c, double* out) {
+    const size_t n3 = (size_t)N * N * N;
+    const T* const* u = reinterpret_cast<const T* const*>(U.u);
+    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((size_t)N * N));
+        const int c0[3] = {x, y, z};
+        int pj[3] = {x, y, z}, pk[3] = {x, y, z};
+        pj[j] = c0[j] + 1 == N ? 0 : c0[j] + 1;
+        pk[k] = c0[k] + 1 == N ? 0 : c0[k] + 1;
+        const size_t nj = ((size_t)pj[2] * N + pj[1]) * N + pj[0], nk = ((size_t)pk[2] * N + pk[1]) * N + pk[0];
+        double Uj[4], Ukj[4], Ujk[4], Uk[4], t1[4], t2[4], P[4];
+        for (int q = 0; q < 4; ++q) {
+            const double sg = q == 0 ? 1.0 : -1.0;
+            Uj[q] = (double)u[4 * j + q][n];
+            Ukj[q] = (double)u[4 * k + q][nj];
+            Ujk[q] = sg * (double)u[4 * j + q][nk];  // U_j^dag(n+k)
+            Uk[q] = sg * (double)u[4 * k + q][n];    // U_k^dag(n)
+        }
+        qmul_d(Uj, Ukj, t1);
+        qmul_d(t1, Ujk, t2);
+        qmul_d(t2, Uk, P);
+        out[n] = c * P[1 + a];
+    }
+}
+
+cudaError_t launch_gauge_spectrum(Lattice* L, int sector, int what, int* ncomp, cudaStream_t s) {
+    const int N = L->mc.N;
+    const int grid = L->sm_count * 8;
+    const size_t n3 = (size_t)N * N * N;
+    cudaError_t e = cudaSuccess;
+    int nc = 0;
+    void** b = L->buf.f[L->cur];
+    if (sector == 0) {  // U(1): angles and electric momenta
+        const int th = L->mc.kind == CL_MODEL_U1 ? 4 : 29, ea = L->mc.kind == CL_MODEL_U1 ? 7 : 32;
+        const double eg = L->mc.kind == CL_MODEL_U1 ? L->mc.e : L->mc.e2;
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+            if (what == 0) {
+                e = launch_get_field(L, ea + i, L->work, s);
+            } else {
+                const int j = (i + 1) % 3, k = (i + 2) % 3;
+                const double c = 1.0 / (eg * L->mc.dx * L->mc.dx);
+                if (L->prec == CL_FP32)
+                    u1_magnetic_kernel<float><<<grid, 256, 0, s>>>((const float*)b[th + j], (const float*)b[th + k], N, j, k,
+                                                                   c, L->mc.nc, L->work);
+                else
+                    u1_magnetic_kernel<double><<<grid, 256, 0, s>>>((const double*)b[th + j], (const double*)b[th + k], N,
+                                                                    j, k, c, L->mc.nc, L->work);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = spectrum_of_work(L, i > 0, s);
+            ++nc;
+        }
+    } else {  // SU(2): links 8 + 4 i + c, electric momenta 20 + 3 i + a
+        Links4 U;
+        for (int q = 0; q < 12; ++q) U.u[q] = b[8 + q];
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+                if (what == 0) {
+                    e = launch_get_field(L, 20 + 3 * i + a, L->work, s);
+                } else {
+                    const int j = (i + 1) % 3, k = (i + 2) % 3;
+                    const double c = -2.0 / (L->mc.e * L->mc.dx * L->mc.dx);
+                    if (L->prec == CL_FP32) su2_magnetic_kernel<float><<<grid, 256, 0, s>>>(U, N, j, k, a, c, L->work);
+                    else su2_magnetic_kernel<double><<<grid, 256, 0, s>>>(U, N, j, k, a, c, L->work);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = spectrum_of_work(L, nc > 0, s);
+                ++nc;
+            }
+    }
+    (void)n3;
+    *ncomp = nc;
+    return e;
+}
+
 cudaError_t launch_spectrum(Lattice* L, int slot, int accumulate, cudaStream_t s) {
     const int N = L->mc.N;
     const int nbins = spectrum_bins(N);

@@ -639,6 +639,38 @@ cl_status lattice_observe(cl_lattice* h, double kmax, float* obs, double* t) {
     return CL_OK;
 }
 
+cl_status lattice_measure_gauge_spectrum(cl_lattice* h, int32_t sector, int32_t what, double* k, double* Delta,
+                                         int64_t* counts) {
+    if (!h || !k || !Delta || !counts) return fail(h, CL_ERR_ARG, "NULL argument");
+    if (what != 0 && what != 1) return fail(h, CL_ERR_ARG, "what must be 0 (electric) or 1 (magnetic)");
+    const bool u1 = h->mc.kind == CL_MODEL_U1 || (h->mc.kind == CL_MODEL_SU2 && h->mc.e2 > 0);
+    if (sector == 0 ? !u1 : (sector != 1 || h->mc.kind != CL_MODEL_SU2))
+        return fail(h, CL_ERR_ARG, "this model has no such gauge sector");
+    int ncomp = 0;
+    cudaError_t e = cl::launch_gauge_spectrum(h, sector, what, &ncomp, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gauge spectrum");
+    cl::DevState st;
+    cl_status s = read_state(h, &st);
+    if (s != CL_OK) return s;
+    const int nb = lattice_spectrum_bins(h);
+    std::vector<double> hb(3 * (size_t)nb);
+    e = cudaMemcpyAsync(hb.data(), h->bins, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gauge spectrum readback");
+    const double N = h->mc.N, dx = h->mc.dx;
+    // E_i = piA_i / a^{1-alpha} (E_i^a = piB_i^a / a^{1-alpha})
+    const double scale = what == 0 ? pow(st.a, 2.0 * h->mc.alpha - 2.0) : 1.0;
+    const double norm = pow(dx / N, 3.0) / (2.0 * M_PI * M_PI) * scale;
+    for (int b = 0; b < nb; ++b) {
+        const double c = hb[2 * (size_t)nb + b] / (double)ncomp;
+        counts[b] = (int64_t)llround(c);
+        const double mean_n = c > 0 ? hb[(size_t)nb + b] / (double)ncomp / c : 0.0;
+        k[b] = h->grid.kIR * mean_n;
+        Delta[b] = c > 0 ? k[b] * k[b] * k[b] * norm * hb[b] / c : 0.0;
+    }
+    return CL_OK;
+}
+
 cl_status lattice_measure_spectrum(cl_lattice* h, int32_t field, int32_t what, double* k, double* Delta,
                                    int64_t* counts) {
     if (!h || !k || !Delta || !counts) return fail(h, CL_ERR_ARG, "NULL argument");

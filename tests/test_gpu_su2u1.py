@@ -187,3 +187,30 @@ def test_su2u1_refusals():
         cl.Lattice(cl.make_model(**dict(base, n_fields=3)), g, cl.make_init(spectrum=0))
     with pytest.raises(cl.LatticeError):
         cl.Lattice(cl.make_model(**dict(base, gauge_e_u1=-1.0)), g, cl.make_init(spectrum=0))
+
+
+def test_su2u1_gauge_field_spectra_match_oracle():
+    """Electric and magnetic spectra of both gauge sectors (sections 5.4, 6.3)
+    against the oracle's fields of the same evolved state."""
+    from oracle.spectra import spectrum
+    N = 8
+    m = SU2U1Model(N=N, dx=0.6, alpha=1.0, fmp2=0.49, lam=1.2, v2=0.8, g=0.9, kappa=1.21, pot=1, p=4, eA=0.7, q=1.3)
+    ref = random_state(N, m, 7)
+    ref.b = math.sqrt(0.49 / 3.0 * ref.energies().sum())
+    lat = gpu_lattice(m, "vv4", cl.CL_FP64, 0.7)
+    load(lat, ref)
+    lat.evolve(5)
+    got = fetch(lat, m)
+    mm = lat.measure_means()
+    probe = SU2U1Lattice(m, got["phi"], got["pi"], got["u"], got["piB"], got["theta"], got["piA"], got["chi"],
+                         got["pchi"], a=mm["a"])
+    kIR = 2 * math.pi / (N * m.dx)
+    for sector in (0, 1):
+        for what in (0, 1):
+            fld = probe.electric(sector) if what == 0 else probe.magnetic(sector)
+            fld = fld.reshape((-1,) + fld.shape[-3:])
+            k, D, c = lat.gauge_spectrum(sector, what)
+            rk, rD, rc = spectrum(fld, m.dx, kIR)
+            assert np.array_equal(c, rc)
+            assert np.max(np.abs(D - rD)) < 1e-10 * np.max(rD), (sector, what)
+    lat.close()

@@ -261,3 +261,26 @@ def test_u1_noncompact_keeps_gauss_law(prec, tol):
     assert max(g) < tol, g
     assert lat.measure_means()["EG"][1] > 0.0
     lat.close()
+
+
+@pytest.mark.parametrize("nc", [0, 1])
+def test_u1_gauge_field_spectra_match_oracle(nc):
+    """Electric and magnetic spectra of the U(1) field (section 5.4) against the
+    oracle's fields E_i = piA_i/a^{1-alpha} and B_i of the same (expanded) state."""
+    from oracle.spectra import spectrum
+    N, dx = 16, 0.5
+    kIR = 2 * math.pi / (N * dx)
+    lat = gpu_u1(N, kIR, 0.04, cl.CL_FP64, fmp=0.6, alpha=0.5, e=0.9, omega=1.1, integ="vv2", nc=nc, spectrum=1, seed=4)
+    lat.evolve(20)
+    mm = lat.measure_means()
+    gphi, gpi, gth, gpa = get_all(lat)
+    om = U1Model(N=N, dx=dx, alpha=0.5, fmp2=0.36, lam=1.0, v2=1.0, e=0.9, kappa=1.21, noncompact=nc)
+    ref = U1Lattice(om, gphi, gpi, gth, gpa, a=mm["a"])
+    for what, fld in ((0, ref.electric()), (1, ref.magnetic())):
+        k, D, c = lat.gauge_spectrum(0, what)
+        rk, rD, rc = spectrum(fld, dx, kIR)
+        assert np.array_equal(c, rc) and np.allclose(k, rk, rtol=1e-14)
+        assert np.max(np.abs(D - rD)) < 1e-10 * np.max(rD), (what, np.max(np.abs(D - rD)), np.max(rD))
+    with pytest.raises(cl.LatticeError):
+        lat.gauge_spectrum(1, 0)  # no SU(2) sector here
+    lat.close()

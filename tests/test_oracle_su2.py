@@ -248,3 +248,26 @@ def test_su2_vacuum_component_is_a_scaled_singlet_draw():
     sm = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=m2)
     sphi, spi, _ = scalar_ic(sm, kIR, [0.0], [0.0], seed=11, omega_over_fstar=0.2)
     assert np.max(np.abs(phi[0] - sphi[0] / np.sqrt(2.0))) < 1e-15
+
+
+def test_su2_magnetic_field_of_an_abelian_configuration():
+    """Links exp(-i phi_i sigma^3/2) commute, so every plaquette is
+    exp(-i Phi_jk sigma^3/2) with Phi_jk the summed angles: the SU(2) magnetic
+    field of section 6.3 then has only a = 3, B_i^3 = 2 sin(Phi_jk/2)/(g dx^2)
+    (the curl of A for small angles); its small-field <|B|^2> is 2 a^4 E_G^B/kappa."""
+    from oracle.core import _u1_magnetic
+    N, g, dx = 6, 1.3, 0.7
+    m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=g, kappa=0.9)
+    phi_ = inputs.angles(N, 61, scale=1.2)
+    u = np.zeros((3, 4, N, N, N))
+    u[:, 0] = np.cos(0.5 * phi_)
+    u[:, 3] = -np.sin(0.5 * phi_)
+    lat = SU2Lattice(m, np.zeros((4, N, N, N)), np.zeros((4, N, N, N)), u, np.zeros((3, 3, N, N, N)))
+    B = lat.magnetic()
+    assert np.max(np.abs(B[:, :2])) < 1e-14
+    assert np.max(np.abs(B[:, 2] - _u1_magnetic(0.5 * phi_, 0.5 * g, dx, 0))) < 1e-12
+    u[:, 0] = np.cos(0.005 * phi_)
+    u[:, 3] = -np.sin(0.005 * phi_)
+    small = SU2Lattice(m, np.zeros((4, N, N, N)), np.zeros((4, N, N, N)), u, np.zeros((3, 3, N, N, N)))
+    B2 = (small.magnetic() ** 2).sum(axis=(0, 1)).mean()
+    assert B2 == pytest.approx(2 * small.energies()[4] / m.kappa, rel=1e-3)

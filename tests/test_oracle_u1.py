@@ -309,3 +309,20 @@ def test_noncompact_free_photon_is_the_exact_lattice_mode(integ):
     assert np.max(np.abs(got_A - ref[0] * prof)) < 1e-12
     assert np.max(np.abs(lat.piA[1] - ref[1] * prof)) < 1e-12
     assert np.max(np.abs(lat.theta[0])) == 0.0 and np.max(np.abs(lat.theta[2])) == 0.0
+
+
+@pytest.mark.parametrize("nc,a,alpha", [(1, 1.0, 0.0), (1, 1.4, 0.5), (0, 1.2, 1.0)])
+def test_u1_field_strengths_carry_the_gauge_energies(nc, a, alpha):
+    """E_i = piA_i/a^{1-alpha} and B_i (section 5.4): <|E|^2> = 2 a^{2+2alpha} E_K^A/kappa
+    exactly; non-compact <|B|^2> = 2 a^4 E_G^A/kappa exactly (E_G^A is half the
+    squared lattice curl); compact, with small angles, the same to O(theta^2)."""
+    N = 6
+    m = U1Model(N=N, dx=0.6, alpha=alpha, fmp2=0.0, lam=1.0, v2=1.0, e=0.9, kappa=1.3, noncompact=nc)
+    lat = _random_state(N, 19, m, a=a)
+    if not nc:
+        lat.theta *= 0.01
+    E = lat.energies()
+    assert (lat.electric() ** 2).sum(axis=0).mean() == pytest.approx(2 * a ** (2 + 2 * alpha) * E[3] / m.kappa,
+                                                                     rel=1e-13)
+    B2 = (lat.magnetic() ** 2).sum(axis=0).mean()
+    assert B2 == pytest.approx(2 * a ** 4 * E[4] / m.kappa, rel=1e-13 if nc else 1e-3)
