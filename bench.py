@@ -251,7 +251,7 @@ def scan_measurement(args, stream):
     t_ens = info["init_s"] + info["tune_s"] + info["evolve_observe_s"]
     X, Y = scan.training_pairs(qs, times, obs)
     net, hist, t_train = scan.fit_surrogate(X, Y, epochs=args.scan_epochs, stream=stream)
-    # held-out couplings: fresh lattice runs (R seeds each, batched) as the judge
+    # held-out couplings: fresh lattice runs (R seeds each, batched) as the reference
     Q, R = args.scan_heldout, args.scan_seeds
     qh = scan.log_uniform_q(Q, 1e2, 1e5, seed=4321)
     Nh = scan.cycle_sizes(Q * R, spec.sizes)

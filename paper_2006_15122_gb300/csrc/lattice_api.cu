@@ -430,7 +430,7 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev);
     L->buf.narr = 0;
     if (cl::array_count(mc) > cl::kMaxArrays) {
-        cl_status s = fail(nullptr, CL_ERR_ARG, "internal: too many arrays for this build");
+        cl_status s = fail(nullptr, CL_ERR_ARG, "internal: more stored arrays than the handle holds");
         lattice_destroy(L);
         return s;
     }
