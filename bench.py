@@ -445,6 +445,27 @@ def accuracy_measurement(args, stream):
     return out
 
 
+def replica_seed(rank):
+    """Under torchrun every rank evolves its own replica, drawn from seed = rank."""
+    return rank
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (all ranks start together after a barrier)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(sites, steps, world, ms):
+    """Site updates per second of all replicas together over the max-over-ranks time."""
+    return world * sites * steps / (ms / 1e3)
+
+
 def run_scan(args):
     import torch
 
@@ -487,7 +508,7 @@ def main():
     model = cl.make_model(n_fields=2, pexp=2, alpha=0.0, fstar_over_mp=FSTAR_MP, omega_over_fstar=OMEGA_FSTAR,
                           lam=1.0, q=QSTAR)
     grid = cl.make_grid(N, KIR, DT, "vv4", cl.CL_FP32)
-    lat = cl.Lattice(model, grid, cl.make_init(phi0=(1.0, 0.0), seed=rank), stream=stream)
+    lat = cl.Lattice(model, grid, cl.make_init(phi0=(1.0, 0.0), seed=replica_seed(rank)), stream=stream)
 
     for _ in range(args.warmup):
         lat.evolve(1)
@@ -506,13 +527,10 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     mm = lat.measure_means()
     npass = 3 * args.steps + 1
-    value = world * N ** 3 * args.steps / (ms / 1e3)
+    value = whole_job_rate(N ** 3, args.steps, world, ms)
     peak, peak_kind = measured_peaks()
     alg_bytes = BYTES_PER_SITE_PASS * N ** 3
     achieved = alg_bytes / (ms / 1e3 / npass) / 1e9

@@ -1,0 +1,54 @@
+"""The multi-rank logic of bench.py on CPU ranks (gloo, world size 2): every
+rank evolves an independent replica (seed = rank), the timing is the max over
+ranks after a barrier, and the whole-job rate counts every replica; under
+torchrun the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dist.barrier()
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, "cpu")
+        out[rank] = (ms, bench.replica_seed(rank), bench.whole_job_rate(64 ** 3, 10, world, ms))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_time_by_the_slowest_and_count_every_replica():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
+    assert sorted(out.keys()) == [0, 1]
+    assert out[0][0] == out[1][0] == 15.0  # both ranks see the slowest time
+    assert out[0][1] != out[1][1]  # independent replicas
+    assert out[0][2] == pytest.approx(2 * 64 ** 3 * 10 / 0.015)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import bench
+
+    import sys
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
+    bench.run_reference(bench.parse())
+    assert capsys.readouterr().out == ""  # the non-zero rank exits without work or output
