@@ -1,0 +1,110 @@
+"""Parity at the full sizes of the workloads, in the launch configurations
+that bench.py times:
+
+- the 1024^3 two-field lattice (FP32 fluctuations, VV4, the bench's tile and
+  grid): with chi = 0 and a static background every Fourier mode of phi is an
+  exact lattice oscillator, so sampled sites are checked one by one against the
+  closed form (the product of the VV2 maps of section 4.3.2);
+- the 32^3 FP64 phi^4 leapfrog with self-consistent expansion, 2000 steps,
+  against the oracle;
+- the 128^3 compact U(1) leapfrog in FP32: the Gauss law (a property that holds
+  at any size) over 400 steps."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2006_15122_gb300 as cl
+from oracle import ScalarLattice, ScalarModel
+
+pytestmark = pytest.mark.gpu
+
+
+def _vv_product(weights, h, w2, steps):
+    M = np.eye(2)
+    for wp in weights:
+        k = wp * h
+        c = 1.0 - 0.5 * k * k * w2
+        M = np.array([[c, k], [-k * w2 * (1.0 - 0.25 * k * k * w2), c]]) @ M
+    return np.linalg.matrix_power(M, steps)
+
+
+def test_1024_cubed_vv4_fp32_plane_wave_matches_closed_form():
+    torch = pytest.importorskip("torch")
+    import bench
+
+    N, steps, eps = 1024, 100, 1e-3
+    nvec = (3, 5, 7)
+    model = cl.make_model(n_fields=2, pexp=2, alpha=0.0, fstar_over_mp=0.0, omega_over_fstar=bench.OMEGA_FSTAR,
+                          lam=1.0, q=bench.QSTAR)
+    lat = cl.Lattice(model, cl.make_grid(N, bench.KIR, bench.DT, "vv4", cl.CL_FP32),
+                     cl.make_init(phi0=(1.0, 0.0), spectrum=0))
+    dx = 2 * math.pi / (bench.KIR * N)
+    x = torch.arange(N, device="cuda", dtype=torch.float64)
+    ang = 2 * math.pi / N
+    phase = (ang * nvec[2] * x).view(N, 1, 1) + (ang * nvec[1] * x).view(1, N, 1) + (ang * nvec[0] * x).view(1, 1, N)
+    field = 1.0 + eps * torch.cos(phase)
+    lat.set_field(cl.FIELD(0), field)
+    del field
+    lat.evolve(steps)
+    got = torch.empty((N, N, N), device="cuda", dtype=torch.float64)
+    lat.get_field(cl.FIELD(0), got)
+    # closed form: the mean (k = 0, w^2 = lam) and the plane wave (w^2 = lam + k_L^2), both from (1, 0)
+    w2k = 1.0 + sum(4 * math.sin(math.pi * c / N) ** 2 for c in nvec) / dx ** 2
+    X0 = _vv_product(oracle.VV4, bench.DT, 1.0, steps)[0, 0]
+    Xk = _vv_product(oracle.VV4, bench.DT, w2k, steps)[0, 0]
+    rng = np.random.default_rng(11)
+    idx = torch.as_tensor(rng.integers(0, N, size=(3, 4096)), device="cuda")
+    sample = got[idx[0], idx[1], idx[2]]
+    ph = phase[idx[0], idx[1], idx[2]]
+    ref = X0 + eps * Xk * torch.cos(ph)
+    err = (sample - ref).abs().max().item()
+    assert err < 2e-3 * eps, (err, X0, Xk)  # FP32 fluctuation of size eps
+    mm = lat.measure_means()
+    assert abs(mm["mean"][0] - X0) < 1e-12 and mm["a"] == 1.0
+    lat.get_field(cl.FIELD(1), got)
+    assert got.abs().max().item() == 0.0  # chi = 0 is exact: its force is q phi^2 chi
+    lat.close()
+
+
+def test_32_cubed_phi4_fp64_leapfrog_2000_steps_matches_oracle():
+    """The phi^4 workload at its full size and length: 32^3, k_IR = 0.5,
+    dt = 0.01, scheme III with self-consistent expansion (alpha = 1, f*/m_p = 1,
+    omega*/f* = 1e-2), vacuum start (section 7), against the oracle."""
+    from oracle.ic import scalar_ic
+    N, kIR, dt, steps = 32, 0.5, 0.01, 2000
+    dx = 2 * math.pi / (kIR * N)
+    model = cl.make_model(n_fields=1, pexp=4, alpha=1.0, fstar_over_mp=1.0, omega_over_fstar=1e-2, lam=1.0)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, "lf", cl.CL_FP64), cl.make_init(phi0=(1.0,), seed=0))
+    om = ScalarModel(N=N, Ns=1, pexp=4, dx=dx, alpha=1.0, fmp2=1.0, lam=1.0)
+    phi, pi, _ = scalar_ic(om, kIR, [1.0], [0.0], seed=0, omega_over_fstar=1e-2)
+    ref = ScalarLattice(om, phi, pi)
+    ref.b = math.sqrt(1.0 / 3.0 * ref.energies().sum())
+    assert np.max(np.abs(lat.get_field(cl.FIELD(0)) - phi[0])) < 1e-13
+    ref.lf3_prepare(dt)
+    ref.lf3_steps(dt, steps)
+    lat.evolve(steps)
+    g = lat.get_field(cl.FIELD(0))
+    dphi = ref.phi[0] - ref.phi[0].mean()
+    assert abs(g.mean() - ref.phi[0].mean()) < 1e-9
+    assert np.max(np.abs((g - g.mean()) - dphi)) < 1e-6 * np.max(np.abs(dphi))
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-10 * ref.a
+    assert mm["hubble_violation"] < 1e-4
+    lat.close()
+
+
+def test_128_cubed_u1_fp32_leapfrog_keeps_gauss_law():
+    N, dx = 128, 0.5
+    model = cl.make_model(kind=cl.CL_MODEL_U1, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
+    lat = cl.Lattice(model, cl.make_grid(N, 2 * math.pi / (N * dx), 0.1 * dx, "lf", cl.CL_FP32),
+                     cl.make_init(seed=7))
+    g = []
+    for _ in range(4):
+        lat.evolve(100)
+        g.append(lat.measure_means()["gauss_violation"])
+    assert max(g) < 1e-5, g
+    mm = lat.measure_means()
+    assert mm["EG"][1] > 0 and np.isfinite(mm["rho"])
+    lat.close()
