@@ -108,3 +108,20 @@ def test_128_cubed_u1_fp32_leapfrog_keeps_gauss_law():
     mm = lat.measure_means()
     assert mm["EG"][1] > 0 and np.isfinite(mm["rho"])
     lat.close()
+
+
+def test_128_cubed_two_field_vv2_vv4_hubble_constraint():
+    """The q = 1e4 preheating lattice (128^3, k_IR = 0.1, dt = 0.005, FP32
+    fluctuations, f*/m_p = 1.396, omega*/f* = 5.13e-6) over 2000 steps: the Hubble
+    constraint stays satisfied, and VV4 keeps it better than VV2 (section 4.3.2)."""
+    de = {}
+    for integ in ("vv2", "vv4"):
+        model = cl.make_model(n_fields=2, pexp=2, alpha=0.0, fstar_over_mp=1.396, omega_over_fstar=5.13e-6, lam=1.0,
+                              q=4.0e4)
+        lat = cl.Lattice(model, cl.make_grid(128, 0.1, 0.005, integ, cl.CL_FP32), cl.make_init(phi0=(1.0, 0.0), seed=0))
+        lat.evolve(2000)
+        mm = lat.measure_means()
+        de[integ] = mm["hubble_violation"]
+        assert np.isfinite(mm["rho"]) and mm["a"] > 1.0
+        lat.close()
+    assert de["vv2"] < 1e-3 and de["vv4"] < de["vv2"], de
