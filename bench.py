@@ -312,7 +312,7 @@ def gauge_measurement(kind, N, steps, stream):
     if kind == "u1":
         model = cl.make_model(kind=cl.CL_MODEL_U1, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
         init = cl.make_init(seed=7)
-        integ, narr, kernel = "lf", 10, "u1_pass_kernel<float>"
+        integ, narr, kernel = "lf", 10, "u1_pass_kernel<float,false>"
     elif kind == "su2":
         model = cl.make_model(kind=cl.CL_MODEL_SU2, lam=1.0, vev2=1.0, gauge_e=1.0, omega_over_fstar=1.0)
         init = cl.make_init(phi0=(1.0, 0.0, 0.0, 0.0), spectrum=0)

@@ -59,12 +59,13 @@ template <> __device__ __forceinline__ void sc<float>(float x, float* s, float* 
 template <> __device__ __forceinline__ void sc<double>(double x, double* s, double* c) { sincos(x, s, c); }
 // link phases of the non-compact formulation: its angles are not wrapped, so FP32
 // takes the range-reduced sincosf
-template <typename T> __device__ __forceinline__ void sc_link(bool nc, T x, T* s, T* c) {
-    if (sizeof(T) == 4 && nc) sincosf(float(x), reinterpret_cast<float*>(s), reinterpret_cast<float*>(c));
+template <typename T, bool NC> __device__ __forceinline__ void sc_link(T x, T* s, T* c) {
+    if (sizeof(T) == 4 && NC) sincosf(float(x), reinterpret_cast<float*>(s), reinterpret_cast<float*>(c));
     else sc<T>(x, s, c);
 }
 
-template <typename T>
+// NC: the non-compact formulation (a separate instantiation, so the compact pass is unchanged)
+template <typename T, bool NC>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(const U1Args A) {
     DevState* st = A.st;
     if (st->error) return;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
     const T dx = T(A.mc.dx), idx = T(1.0 / A.mc.dx), idx2 = T(A.mc.idx2);
     const T lam = T(A.mc.lam), v2 = T(A.mc.vev2);
     const T cJ = T(2.0 * A.mc.e / A.mc.dx / A.mc.kappa), cB = T(1.0 / (A.mc.e * A.mc.dx * A.mc.dx * A.mc.dx));
-    const bool nc = A.mc.nc != 0;  // non-compact: the plaquette angle itself replaces sin, theta^2/2 replaces 1 - cos
+    constexpr bool nc = NC;  // non-compact: the plaquette angle itself replaces sin, theta^2/2 replaces 1 - cos
     (void)dx;
     const T* PR = static_cast<const T*>(A.in[0]);
     const T* PIm = static_cast<const T*>(A.in[1]);
@@ -120,12 +121,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
             const size_t np = at(ox, oy, oz), nm = at(-ox, -oy, -oz);
             const T ur0 = phr(np), ui0 = phi_(np);
             T s, cc;
-            sc_link<T>(nc, t0[d], &s, &cc);
+            sc_link<T, NC>(t0[d], &s, &cc);
             // V_i phi(n+i) = (cos t - i sin t)(ur0 + i ui0)
             const T ur = cc * ur0 + s * ui0, ui = cc * ui0 - s * ur0;
             const T tm = th(d, nm);
             T sm, cm;
-            sc_link<T>(nc, tm, &sm, &cm);
+            sc_link<T, NC>(tm, &sm, &cm);
             const T wr0 = phr(nm), wi0 = phi_(nm);
             // V_i*(n-i) phi(n-i) = (cos tm + i sin tm)(wr0 + i wi0)
             const T wr = cm * wr0 - sm * wi0, wi = cm * wi0 + sm * wr0;
@@ -305,8 +306,13 @@ void u1_geometry(Lattice* L) {
     g.threads = 256;
     const size_t n3 = (size_t)g.N * g.N * g.N;
     int per_sm = 1;
-    if (L->prec == CL_FP32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u1_pass_kernel<float>, 256, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, u1_pass_kernel<double>, 256, 0);
+    const bool nc = L->mc.nc != 0;
+    if (L->prec == CL_FP32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nc ? u1_pass_kernel<float, true> : u1_pass_kernel<float, false>,
+                                                      256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, nc ? u1_pass_kernel<double, true> : u1_pass_kernel<double, false>, 256, 0);
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)L->sm_count * per_sm;
     const long long need = (long long)((n3 + 255) / 256);
@@ -329,8 +335,15 @@ cudaError_t u1_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, boo
     A.mc = L->mc;
     A.pi = pi;
     A.write = write ? 1 : 0;
-    if (L->prec == CL_FP32) u1_pass_kernel<float><<<L->geo.grid, 256, 0, s>>>(A);
-    else u1_pass_kernel<double><<<L->geo.grid, 256, 0, s>>>(A);
+    const int grid = L->geo.grid;
+    if (L->mc.nc) {
+        if (L->prec == CL_FP32) u1_pass_kernel<float, true><<<grid, 256, 0, s>>>(A);
+        else u1_pass_kernel<double, true><<<grid, 256, 0, s>>>(A);
+    } else if (L->prec == CL_FP32) {
+        u1_pass_kernel<float, false><<<grid, 256, 0, s>>>(A);
+    } else {
+        u1_pass_kernel<double, false><<<grid, 256, 0, s>>>(A);
+    }
     return cudaGetLastError();
 }
 
