@@ -376,6 +376,63 @@ void observables(const DevState& s, const double* bins, int N, double dx, double
 
 // ------------------------------------------------------------------- host side
 
+namespace cl {
+
+// chi = phibar_1 + (stored - pending shift) of `count` members of one size into
+// consecutive N^3 blocks (the lattice_get_field value of field 1)
+template <typename T>
+__global__ void ens_chi_gather_kernel(const EnsLat* lat, const int* members, int cur, size_t n3, double* out) {
+    const EnsLat& L = lat[members[blockIdx.y]];
+    const T* src = static_cast<const T*>(L.buf[cur][1]);
+    const double mean = L.st->phibar[1];
+    const T shift = T(L.st->sphi[1]);
+    double* dst = out + (size_t)blockIdx.y * n3;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = mean + (double)(src[i] - shift);
+}
+
+// shell sums of |F|^2, |n~| and the mode count per member (blockIdx.y), as the
+// single-lattice binning does, into bins + y * 3 * nbins
+__global__ void ens_bin_kernel(const double2* F, int N, int nbins, double* bins) {
+    extern __shared__ double h[];
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) h[i] = 0.0;
+    __syncthreads();
+    const int NH = N / 2 + 1;
+    const size_t total = (size_t)N * N * NH;
+    const double2* Fm = F + (size_t)blockIdx.y * total;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % NH);
+        const int iy = (int)((i / NH) % N);
+        const int iz = (int)(i / ((size_t)NH * N));
+        const long long mx = ix, my = iy <= N / 2 ? iy : iy - N, mz = iz <= N / 2 ? iz : iz - N;
+        const long long n2 = mx * mx + my * my + mz * mz;
+        long long r = (long long)sqrt((double)n2);
+        while ((r + 1) * (r + 1) <= n2) ++r;
+        while (r * r > n2) --r;
+        const int b = (int)r;
+        const double w = (ix == 0 || ix == N / 2) ? 1.0 : 2.0;
+        const double2 v = Fm[i];
+        atomicAdd(&h[b], w * (v.x * v.x + v.y * v.y));
+        atomicAdd(&h[nbins + b], w * sqrt((double)n2));
+        atomicAdd(&h[2 * nbins + b], w);
+    }
+    __syncthreads();
+    double* out = bins + (size_t)blockIdx.y * 3 * nbins;
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x)
+        if (h[i] != 0.0) atomicAdd(&out[i], h[i]);
+}
+
+// every member's DevState into one array (member order)
+__global__ void ens_state_gather_kernel(const EnsLat* lat, int n, DevState* out) {
+    const int m = blockIdx.x;
+    if (m >= n) return;
+    const unsigned* src = reinterpret_cast<const unsigned*>(lat[m].st);
+    unsigned* dst = reinterpret_cast<unsigned*>(out + m);
+    for (size_t i = threadIdx.x; i < sizeof(DevState) / sizeof(unsigned); i += blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace cl
+
 struct cl_ensemble {
     std::vector<cl_lattice*> mem;
     std::map<int, cl::SharedFFT> fft;  // per lattice size
@@ -394,6 +451,20 @@ struct cl_ensemble {
     std::vector<G> graphs;
     std::vector<cl::EnsLat> host_lat;
     int max_smem = 0;
+    // batched observations: members grouped by size, chunks of at most obs_batch members
+    struct ObsChunk {
+        int N, first, count;   // members first .. first+count-1 of obs_members
+        cufftHandle plan;      // D2Z over `count` lattices of N^3
+    };
+    std::vector<int> obs_members;  // member indices grouped by size
+    std::vector<ObsChunk> obs_chunks;
+    int* d_obs_members = nullptr;
+    double* obs_in = nullptr;      // FP64 chi of one chunk
+    void* obs_out = nullptr;       // its half-spectrum
+    double* d_obs_bins = nullptr;  // 3 x nbins(N) per member, in obs_members order
+    cl::DevState* d_obs_st = nullptr;
+    std::vector<size_t> obs_bin_off;  // per position in obs_members
+    size_t obs_bin_total = 0;
 };
 
 namespace {
@@ -549,6 +620,12 @@ cl_status ensemble_destroy(cl_ensemble* E) {
     }
     if (E->d_lat) cudaFree(E->d_lat);
     if (E->d_tile_lat) cudaFree(E->d_tile_lat);
+    for (auto& c : E->obs_chunks) cufftDestroy(c.plan);
+    if (E->d_obs_members) cudaFree(E->d_obs_members);
+    if (E->obs_in) cudaFree(E->obs_in);
+    if (E->obs_out) cudaFree(E->obs_out);
+    if (E->d_obs_bins) cudaFree(E->d_obs_bins);
+    if (E->d_obs_st) cudaFree(E->d_obs_st);
     if (E->cstream) cudaStreamDestroy(E->cstream);
     delete E;
     return CL_OK;
@@ -654,6 +731,47 @@ cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const
         ensemble_destroy(E);
         return efail(CL_ERR_CUDA, "ensemble_init: synchronization");
     }
+    // batched observations: size classes, chunked so that one chunk's FP64 input stays under 2 GiB
+    {
+        std::map<int, std::vector<int>> by_size;
+        for (int i = 0; i < n; ++i) by_size[Ns[i]].push_back(i);
+        size_t in_max = 0, out_max = 0;
+        for (auto& kv : by_size) {
+            const int N = kv.first;
+            const size_t n3 = (size_t)N * N * N, nh = (size_t)N * N * (N / 2 + 1);
+            const int cap = (int)std::max<size_t>(1, ((size_t)1 << 31) / (n3 * sizeof(double)));
+            for (size_t k = 0; k < kv.second.size(); k += cap) {
+                cl_ensemble::ObsChunk c;
+                c.N = N;
+                c.first = (int)E->obs_members.size();
+                c.count = (int)std::min<size_t>(cap, kv.second.size() - k);
+                for (int m = 0; m < c.count; ++m) E->obs_members.push_back(kv.second[k + m]);
+                int dims[3] = {N, N, N};
+                if (cufftPlanMany(&c.plan, 3, dims, nullptr, 1, (int)n3, nullptr, 1, (int)nh, CUFFT_D2Z, c.count) !=
+                    CUFFT_SUCCESS) {
+                    ensemble_destroy(E);
+                    return efail(CL_ERR_OOM, "ensemble_init: batched FFT plans");
+                }
+                cufftSetStream(c.plan, E->stream);
+                E->obs_chunks.push_back(c);
+                in_max = std::max(in_max, (size_t)c.count * n3);
+                out_max = std::max(out_max, (size_t)c.count * nh);
+            }
+        }
+        for (int m : E->obs_members) {
+            E->obs_bin_off.push_back(E->obs_bin_total);
+            E->obs_bin_total += 3 * (size_t)cl::spectrum_bins(Ns[m]);
+        }
+        if (cudaMalloc(&E->d_obs_members, sizeof(int) * n) != cudaSuccess ||
+            cudaMalloc(&E->obs_in, sizeof(double) * in_max) != cudaSuccess ||
+            cudaMalloc(&E->obs_out, sizeof(double2) * out_max) != cudaSuccess ||
+            cudaMalloc(&E->d_obs_bins, sizeof(double) * E->obs_bin_total) != cudaSuccess ||
+            cudaMalloc(&E->d_obs_st, sizeof(cl::DevState) * n) != cudaSuccess ||
+            cudaMemcpy(E->d_obs_members, E->obs_members.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            ensemble_destroy(E);
+            return efail(CL_ERR_OOM, "ensemble_init: observation buffers");
+        }
+    }
     *out = E;
     return CL_OK;
 }
@@ -710,24 +828,56 @@ cl_status ensemble_member(cl_ensemble* E, int32_t i, cl_lattice** out) {
 cl_status ensemble_observe(cl_ensemble* E, float* obs, double* t) {
     if (!E || !obs) return efail(CL_ERR_ARG, "ensemble_observe: NULL argument");
     const int n = (int)E->mem.size();
-    // reductions of every member in one launch, then the chi spectra (cuFFT per member)
+    // reductions of every member in one launch; then, per size class, the chi of all its
+    // members gathered into one buffer, one batched D2Z and one binning launch; the
+    // states and bins come back in two copies
     cudaError_t e = ens_launch(E, E->cur, mkpass(cl::PK_MEASURE, E->dt, 0, 0, 0, 0), false, E->stream);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cl::launch_spectrum(E->mem[i], 1, 0, E->stream);
-    std::vector<cl::DevState> st(n);
-    std::vector<std::vector<double>> bins(n);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = cudaMemcpyAsync(&st[i], E->mem[i]->buf.st, sizeof(cl::DevState), cudaMemcpyDeviceToHost, E->stream);
-        bins[i].resize(3 * (size_t)cl::spectrum_bins(E->mem[i]->mc.N));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bins[i].data(), E->mem[i]->bins, bins[i].size() * sizeof(double),
-                                cudaMemcpyDeviceToHost, E->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->d_obs_bins, 0, sizeof(double) * E->obs_bin_total, E->stream);
+    int sm_count = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    for (const auto& c : E->obs_chunks) {
+        if (e != cudaSuccess) break;
+        const int N = c.N;
+        const size_t n3 = (size_t)N * N * N;
+        const int nb = cl::spectrum_bins(N);
+        const int gx = std::max(1, std::min(64, (int)((n3 + 255) / 256)));
+        const dim3 g(gx, c.count);
+        if (E->prec == CL_FP32)
+            cl::ens_chi_gather_kernel<float><<<g, 256, 0, E->stream>>>(E->d_lat, E->d_obs_members + c.first, E->cur, n3,
+                                                                       E->obs_in);
+        else
+            cl::ens_chi_gather_kernel<double><<<g, 256, 0, E->stream>>>(E->d_lat, E->d_obs_members + c.first, E->cur, n3,
+                                                                        E->obs_in);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && cufftExecD2Z(c.plan, E->obs_in, (cufftDoubleComplex*)E->obs_out) != CUFFT_SUCCESS)
+            e = cudaErrorUnknown;
+        if (e == cudaSuccess) {
+            const size_t nh = (size_t)N * N * (N / 2 + 1);
+            const int bx = std::max(1, std::min(2 * sm_count, (int)((nh + 511) / 512)));
+            cl::ens_bin_kernel<<<dim3(bx, c.count), 512, 3 * (size_t)nb * sizeof(double), E->stream>>>(
+                (const double2*)E->obs_out, N, nb, E->d_obs_bins + E->obs_bin_off[c.first]);
+            e = cudaGetLastError();
+        }
     }
+    if (e == cudaSuccess) {
+        cl::ens_state_gather_kernel<<<n, 128, 0, E->stream>>>(E->d_lat, n, E->d_obs_st);
+        e = cudaGetLastError();
+    }
+    std::vector<cl::DevState> st(n);
+    std::vector<double> bins(E->obs_bin_total);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st.data(), E->d_obs_st, sizeof(cl::DevState) * n, cudaMemcpyDeviceToHost, E->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bins.data(), E->d_obs_bins, sizeof(double) * bins.size(), cudaMemcpyDeviceToHost, E->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
     if (e != cudaSuccess) return efail(CL_ERR_CUDA, std::string("ensemble_observe: ") + cudaGetErrorString(e));
     const double kmax = 0.5 * E->nmin * E->kIR;
-    for (int i = 0; i < n; ++i)
-        cl::observables(st[i], bins[i].data(), E->mem[i]->mc.N, E->mem[i]->mc.dx, E->kIR, kmax,
+    for (size_t k = 0; k < E->obs_members.size(); ++k) {
+        const int i = E->obs_members[k];
+        cl::observables(st[i], bins.data() + E->obs_bin_off[k], E->mem[i]->mc.N, E->mem[i]->mc.dx, E->kIR, kmax,
                         obs + (size_t)i * CL_OBS_SIZE);
+    }
     if (t) *t = st.empty() ? 0.0 : st[0].t;
     return CL_OK;
 }
