@@ -239,5 +239,7 @@ def test_su2u1_checkpoint_continuation_is_bitwise(prec):
         b, mb = fetch(lat, m), lat.measure_means()
     for k in a:
         assert np.array_equal(a[k], b[k]), k
-    assert ma["a"] == mb["a"] and ma["b"] == mb["b"] and ma["gauss_violation"] == mb["gauss_violation"]
+    assert ma["a"] == mb["a"] and ma["b"] == mb["b"]
+    # the Gauss residual sums with FP64 atomics: equal up to their order
+    assert ma["gauss_violation"] == pytest.approx(mb["gauss_violation"], rel=1e-12)
     lat.close()
