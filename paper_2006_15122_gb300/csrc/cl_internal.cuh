@@ -288,6 +288,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// Hint: bring the line holding p into L2 (no register result, no fault semantics
+// needed: callers only pass addresses inside their arrays).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 // Per-thread asynchronous global -> shared copies (16 bytes, or 4/8 bytes for halo cells).
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");

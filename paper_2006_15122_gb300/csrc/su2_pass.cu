@@ -139,6 +139,27 @@ __device__ __forceinline__ void plaq(T* const* a, int i, int j, size_t m, int x,
     qmul(t2, c, P);
 }
 
+// backward staple of link i at n in the plane (i, j), transported to n:
+// U_j^dag(n-j) U_ij(n-j) U_j(n-j) = U_j^dag(n-j) U_i(n-j) U_j(n-j+i) U_i^dag(n),
+// the two factors U_j^dag(n-j) U_j(n-j) = 1 of the plaquette form cancelled
+// (unit links); uic = U_i^dag(n)
+template <typename T>
+__device__ __forceinline__ void back_staple(T* const* a, int i, int j, size_t n, int x, int y, int z, int N,
+                                            const T* uic, T* Q) {
+    const size_t mj = nb<T>(n, x, y, z, N, j, -1);
+    const int xj = j == 0 ? (x == 0 ? N - 1 : x - 1) : x;
+    const int yj = j == 1 ? (y == 0 ? N - 1 : y - 1) : y;
+    const int zj = j == 2 ? (z == 0 ? N - 1 : z - 1) : z;
+    T Uj[4], Ui[4], Ujp[4], c[4], t1[4], t2[4];
+    ldq(a, j, mj, Uj);
+    ldq(a, i, mj, Ui);
+    ldq(a, j, nb<T>(mj, xj, yj, zj, N, i, 1), Ujp);
+    qconj(Uj, c);
+    qmul(c, Ui, t1);
+    qmul(t1, Ujp, t2);
+    qmul(t2, uic, Q);
+}
+
 template <typename T, bool EXT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(const Su2Args A) {
     constexpr int NS = EXT ? kSu2ExtNS : U1NS;
@@ -155,10 +176,21 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
     const T cMA = hasA ? T(1.0 / (A.mc.e2 * A.mc.dx * A.mc.dx * A.mc.dx)) : T(0);
     const T qc = T(A.mc.q);
     const size_t n3 = (size_t)N * N * N;
+    // per-thread sums in T, folded into FP64 every 64 sites
     double acc[NS];
+    T ts[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
-    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += (size_t)gridDim.x * blockDim.x) {
+    for (int s = 0; s < NS; ++s) { acc[s] = 0.0; ts[s] = T(0); }
+    int cnt = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += stride) {
+        // the grid's next chunk of sites into L2 while this one computes: its loads
+        // (own sites and most neighbours) then wait on L2, not on DRAM
+        if (n + stride < n3) {
+#pragma unroll
+            for (int a = 0; a < (EXT ? 37 : 29); ++a)
+                if (a < 29 || (a < 35 ? hasA : hasC)) prefetch_l2(arr[a] + n + stride);
+        }
         const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((size_t)N * N));
         T f[4], lap[4], grad = T(0), eB = T(0);
         ldf(arr, n, f);
@@ -183,6 +215,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
             }
         }
         if (hasC) chi0 = arr[35][n];
+        // forward plaquettes U_01, U_02, U_12 at n: vector parts and magnetic energy
+        // (U_ji = U_ij^dag, so the plane (j, i) takes the vector part with the sign flipped)
+        T Pv[3][3];
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {
+            const int ii = pr == 2 ? 1 : 0, jj = pr == 0 ? 1 : 2;
+            T P[4];
+            plaq(arr, ii, jj, n, x, y, z, N, P);
+            eB += T(4) * (T(1) - P[0]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Pv[pr][k] = P[k + 1];
+        }
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const size_t np = nb<T>(n, x, y, z, N, i, 1), nm = nb<T>(n, x, y, z, N, i, -1);
@@ -214,23 +258,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
             T js[3];
             im_sigma(f, t, js);
             T mag[3] = {T(0), T(0), T(0)};
+            T uic[4];
+            qconj(q, uic);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 if (j == i) continue;
-                T P1[4], P2[4], Uj[4], Ujc[4], s1[4], Q[4];
-                plaq(arr, i, j, n, x, y, z, N, P1);
-                const size_t mj = nb<T>(n, x, y, z, N, j, -1);
-                const int xj = j == 0 ? (x == 0 ? N - 1 : x - 1) : x;
-                const int yj = j == 1 ? (y == 0 ? N - 1 : y - 1) : y;
-                const int zj = j == 2 ? (z == 0 ? N - 1 : z - 1) : z;
-                plaq(arr, i, j, mj, xj, yj, zj, N, P2);
-                ldq(arr, j, mj, Uj);
-                qconj(Uj, Ujc);
-                qmul(Ujc, P2, s1);
-                qmul(s1, Uj, Q);
+                const int pr = i + j - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+                const T sg = i < j ? T(1) : T(-1);
+                T Q[4];
+                back_staple(arr, i, j, n, x, y, z, N, uic, Q);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) mag[k] += P1[k + 1] - Q[k + 1];
-                if (j > i) eB += T(4) * (T(1) - P1[0]);
+                for (int k = 0; k < 3; ++k) mag[k] += sg * Pv[pr][k] - Q[k + 1];
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) KB[i][k] = A1 * cJ * js[k] + Am * cM * mag[k];
@@ -284,14 +322,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
                 sA += es * es;
                 if (A.write) arr[20 + 3 * i + k][n] = e + h * KB[i][k];
             }
-        acc[0] += double(f[0]); acc[1] += double(f[1]);
-        acc[2] += double(f[0] * f[0]); acc[3] += double(f[1] * f[1]);
-        acc[4] += double(pr0); acc[5] += double(pr1);
-        acc[6] += double(sp);
-        acc[7] += double(grad * idx2);
-        acc[8] += double(vpot);
-        acc[9] += double(sA);
-        acc[10] += double(eB);
+        ts[0] += f[0]; ts[1] += f[1];
+        ts[2] += f[0] * f[0]; ts[3] += f[1] * f[1];
+        ts[4] += pr0; ts[5] += pr1;
+        ts[6] += sp;
+        ts[7] += grad * idx2;
+        ts[8] += vpot;
+        ts[9] += sA;
+        ts[10] += eB;
         if (hasA) {
             T sAA = T(0);
 #pragma unroll
@@ -301,18 +339,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
                 sAA += es * es;
                 if (A.write) arr[32 + i][n] = e + h * KA[i];
             }
-            acc[11 % NS] += double(sAA);
-            acc[12 % NS] += double(eBA);
+            ts[11 % NS] += sAA;
+            ts[12 % NS] += eBA;
         }
         if (hasC) {
             const T Kc = -A3 * T(2) * qc * mod2 * chi0 + A1 * (lchi - T(6) * chi0) * idx2;
             const T p = arr[36][n];
             const T ps = p + h1 * Kc;
             if (A.write) arr[36][n] = p + h * Kc;
-            acc[13 % NS] += double(ps * ps);
-            acc[14 % NS] += double(gchi * idx2);
+            ts[13 % NS] += ps * ps;
+            ts[14 % NS] += gchi * idx2;
+        }
+        if (++cnt == 64) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) { acc[s] += double(ts[s]); ts[s] = T(0); }
+            cnt = 0;
         }
     }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) acc[s] += double(ts[s]);
     // block reduction, partials, last block
     __shared__ double red[8][NS];
     const int lin = threadIdx.x, lane = lin & 31, warp = lin >> 5, nwarps = (blockDim.x + 31) >> 5;

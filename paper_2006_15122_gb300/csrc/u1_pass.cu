@@ -92,7 +92,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) u1_pass_kernel(co
     for (int s = 0; s < U1NS; ++s) ts[s] = T(0);
     int cnt = 0;
 
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += stride) {
+        // the grid's next chunk of sites into L2 while this one computes
+        if (i + stride < n3) {
+#pragma unroll
+            for (int a = 0; a < 10; ++a) prefetch_l2(static_cast<const T*>(A.in[a]) + i + stride);
+        }
         const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
         const int c[3] = {x, y, z};
         auto at = [&](int dxs, int dys, int dzs) -> size_t {
