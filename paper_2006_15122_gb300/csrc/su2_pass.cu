@@ -35,6 +35,7 @@
 // Four more volume sums (sync piA^2, sum_{i<j} (1 - cos theta_ij), sync pchi^2,
 // grad chi^2) enter the shared background update.
 #include <math.h>
+#include <stdlib.h>
 
 #include "cl_internal.cuh"
 #include "gauge_finish.cuh"
@@ -124,49 +125,51 @@ template <typename T> __device__ __forceinline__ size_t nb(size_t n, int x, int 
     return n + (size_t)(zz - z) * NN;
 }
 
-// plaquette U_ij at site m (coordinates x, y, z)
-template <typename T>
-__device__ __forceinline__ void plaq(T* const* a, int i, int j, size_t m, int x, int y, int z, int N, T* P) {
-    T Ui[4], Ujp[4], Uip[4], Uj[4], t1[4], t2[4], c[4];
-    ldq(a, i, m, Ui);
-    ldq(a, j, nb<T>(m, x, y, z, N, i, 1), Ujp);
-    ldq(a, i, nb<T>(m, x, y, z, N, j, 1), Uip);
-    ldq(a, j, m, Uj);
-    qmul(Ui, Ujp, t1);
-    qconj(Uip, c);
-    qmul(t1, c, t2);
-    qconj(Uj, c);
-    qmul(t2, c, P);
-}
+// ------------------------------------------------------------ tiled kick
+//
+// The kick reads Phi and the links (and with EXT the U(1) angles and the
+// singlet) at the site and its neighbours: n +- i, and for the plaquettes
+// n + i + j, n - j + i.  A block of BX x 8 threads owns a BX x 8 tile in x-y,
+// one site per thread, and marches a run of planes in z.  Those arrays are
+// staged plane by plane in a ring of S shared-memory stages with cp.async:
+// planes z-1, z, z+1 (with a one-cell x-y halo, corners included) are
+// resident while plane z computes and the next plane is in flight, one
+// barrier per plane.  The momenta are read and written at the own site only.
+// Work split: the (x-y tile, z) plane tiles, x-y tile major and y-tiles
+// fastest, are cut into equal contiguous ranges, one per block, so every
+// block marches the same number of planes.
 
-// backward staple of link i at n in the plane (i, j), transported to n:
-// U_j^dag(n-j) U_ij(n-j) U_j(n-j) = U_j^dag(n-j) U_i(n-j) U_j(n-j+i) U_i^dag(n),
-// the two factors U_j^dag(n-j) U_j(n-j) = 1 of the plaquette form cancelled
-// (unit links); uic = U_i^dag(n)
-template <typename T>
-__device__ __forceinline__ void back_staple(T* const* a, int i, int j, size_t n, int x, int y, int z, int N,
-                                            const T* uic, T* Q) {
-    const size_t mj = nb<T>(n, x, y, z, N, j, -1);
-    const int xj = j == 0 ? (x == 0 ? N - 1 : x - 1) : x;
-    const int yj = j == 1 ? (y == 0 ? N - 1 : y - 1) : y;
-    const int zj = j == 2 ? (z == 0 ? N - 1 : z - 1) : z;
-    T Uj[4], Ui[4], Ujp[4], c[4], t1[4], t2[4];
-    ldq(a, j, mj, Uj);
-    ldq(a, i, mj, Ui);
-    ldq(a, j, nb<T>(mj, xj, yj, zj, N, i, 1), Ujp);
-    qconj(Uj, c);
-    qmul(c, Ui, t1);
-    qmul(t1, Ujp, t2);
-    qmul(t2, uic, Q);
+// staged array k -> slot in the 37-array layout: Phi 0-3, links 8-19,
+// U(1) angles 29-31, singlet 35
+__host__ __device__ constexpr int su2_stage_slot(int k) {
+    return k < 4 ? k : (k < 16 ? 8 + (k - 4) : (k < 19 ? 29 + (k - 16) : 35));
 }
+template <bool EXT> __host__ __device__ constexpr int su2_staged() { return EXT ? 20 : 16; }
+constexpr int kSu2TileBY = 8;
 
-template <typename T, bool EXT>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(const Su2Args A) {
+template <typename T, bool EXT, int BX>
+__global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512 : 256) / (BX * kSu2TileBY))
+    su2_kick_kernel(const Su2Args A, const int S) {
     constexpr int NS = EXT ? kSu2ExtNS : U1NS;
+    constexpr int BY = kSu2TileBY, NT = BX * BY;
+    constexpr int V = 16 / (int)sizeof(T);
+    constexpr int NA = su2_staged<EXT>();
+    constexpr int RW = BX + 2 * V, ROWS = BY + 2, ASZ = ROWS * RW, STG = NA * ASZ;
+    constexpr int VPR = BX / V;      // 16-byte vectors per row
+    constexpr int VPA = ROWS * VPR;  // vectors per array and plane, y-halo rows included
+    constexpr int HPA = 2 * ROWS;    // x-halo cells per array and plane, corners included
     DevState* st = A.st;
     if (st->error) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw + 128);
+    __shared__ const T* s_src[NA];
     const int N = A.mc.N;
     T* const* arr = reinterpret_cast<T* const*>(A.a);
+    const int tx = threadIdx.x, ty = threadIdx.y, lin = ty * BX + tx;
+    if (lin == 0) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) s_src[k] = arr[su2_stage_slot(k)];
+    }
     const T A1 = T(st->A1), A3 = T(st->A3), Am = T(st->Am);
     const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(A.mc.idx2);
     const T lam = T(A.mc.lam), v2 = T(A.mc.vev2);
@@ -175,196 +178,328 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
     const T cJA = hasA ? T(2.0 * A.mc.e2 / (A.mc.kappa * A.mc.dx)) : T(0);
     const T cMA = hasA ? T(1.0 / (A.mc.e2 * A.mc.dx * A.mc.dx * A.mc.dx)) : T(0);
     const T qc = T(A.mc.q);
-    const size_t n3 = (size_t)N * N * N;
+    const size_t n3 = (size_t)N * N * N, NN = (size_t)N * N;
+
+    // this block's range of plane tiles; a segment is its part inside one x-y tile
+    const int nty = N / BY;
+    const long long W = (long long)(N / BX) * nty * N;
+    const long long beg = W * blockIdx.x / gridDim.x, end = W * (blockIdx.x + 1) / gridDim.x;
+    struct Seg {
+        int x0, y0, z0, len;
+    };
+    auto seg_at = [&](long long cur) {
+        Seg g;
+        const long long xy = cur / N;
+        g.z0 = (int)(cur - xy * N);
+        g.len = (int)min((long long)(N - g.z0), end - cur);
+        g.y0 = (int)(xy % nty) * BY;
+        g.x0 = (int)(xy / nty) * BX;
+        return g;
+    };
+    __syncthreads();  // s_src
+
+    // loader: walks the same segments, planes z0-1 .. z0+len of each
+    long long ld_cur = beg;
+    Seg ls = seg_at(beg);
+    int ld_p = 0, ld_slot = 0;
+    auto issue = [&]() {
+        if (ld_cur < end) {
+            int z = ls.z0 - 1 + ld_p;
+            z = z < 0 ? z + N : (z >= N ? z - N : z);
+            T* dst = sm + ld_slot * STG;
+            const size_t zoff = (size_t)z * NN;
+#pragma unroll
+            for (int e0 = 0; e0 < NA * VPA; e0 += NT) {
+                const int e = e0 + lin;
+                if (e < NA * VPA) {
+                    const int a = e / VPA, r = (e % VPA) / VPR, v = e % VPR;
+                    int y = ls.y0 - 1 + r;
+                    y = y < 0 ? y + N : (y >= N ? y - N : y);
+                    cp_async16(dst + a * ASZ + r * RW + V + v * V, s_src[a] + zoff + (size_t)y * N + ls.x0 + v * V);
+                }
+            }
+#pragma unroll
+            for (int e0 = 0; e0 < NA * HPA; e0 += NT) {
+                const int e = e0 + lin;
+                if (e < NA * HPA) {
+                    const int a = e / HPA, side = (e % HPA) / ROWS, r = e % ROWS;
+                    int y = ls.y0 - 1 + r;
+                    y = y < 0 ? y + N : (y >= N ? y - N : y);
+                    const int x = side == 0 ? (ls.x0 == 0 ? N - 1 : ls.x0 - 1) : (ls.x0 + BX == N ? 0 : ls.x0 + BX);
+                    cp_async_elem(dst + a * ASZ + r * RW + (side == 0 ? V - 1 : V + BX), s_src[a] + zoff + (size_t)y * N + x);
+                }
+            }
+            if (++ld_p == ls.len + 2) {
+                ld_p = 0;
+                ld_cur += ls.len;
+                if (ld_cur < end) ls = seg_at(ld_cur);
+            }
+            if (++ld_slot == S) ld_slot = 0;
+        }
+        cp_async_commit();
+    };
+    int issued = 0;
+    auto wait_for = [&](int need) {  // load `need` landed for every thread
+        switch (issued - 1 - need) {
+            case 0: cp_async_wait<0>(); break;
+            case 1: cp_async_wait<1>(); break;
+            case 2: cp_async_wait<2>(); break;
+            case 3: cp_async_wait<3>(); break;
+            case 4: cp_async_wait<4>(); break;
+            default: cp_async_wait<5>(); break;
+        }
+        __syncthreads();
+    };
+
     // per-thread sums in T, folded into FP64 every 64 sites
     double acc[NS];
     T ts[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) { acc[s] = 0.0; ts[s] = T(0); }
     int cnt = 0;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += stride) {
-        // the grid's next chunk of sites into L2 while this one computes: its loads
-        // (own sites and most neighbours) then wait on L2, not on DRAM
-        if (n + stride < n3) {
+
+    for (int L = 0; L < S; ++L, ++issued) issue();
+    int sl_m = 0, need = 2;
+    const int own = (ty + 1) * RW + V + tx;
+    for (long long cur = beg; cur < end;) {
+        const Seg sg = seg_at(cur);
+        const int x = sg.x0 + tx, y = sg.y0 + ty;
+        for (int zz = 0; zz < sg.len; ++zz, ++need) {
+            wait_for(need);  // planes z-1, z, z+1 have landed
+            if (zz > 0) { issue(); ++issued; }  // refill the stage of plane z-2
+            const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
+            const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
+            const T* bs[3] = {sm + sl_m * STG + own, sm + sl_c * STG + own, sm + sl_p * STG + own};
+            const size_t n = (size_t)(sg.z0 + zz) * NN + (size_t)y * N + x;
+            if (zz + 1 < sg.len) {  // the momenta of the next plane into L2
 #pragma unroll
-            for (int a = 0; a < (EXT ? 37 : 29); ++a)
-                if (a < 29 || (a < 35 ? hasA : hasC)) prefetch_l2(arr[a] + n + stride);
-        }
-        const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / ((size_t)N * N));
-        T f[4], lap[4], grad = T(0), eB = T(0);
-        ldf(arr, n, f);
+                for (int k = 4; k < 8; ++k) prefetch_l2(arr[k] + n + NN);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) lap[c] = T(-6) * f[c];
-        T KB[3][3];
-        // U(1) sector: forward plaquette angles theta_01, theta_02, theta_12 at n (sines, cosines)
-        T KA[3] = {T(0), T(0), T(0)}, eBA = T(0), chi0 = T(0), lchi = T(0), gchi = T(0);
-        T psn[3] = {T(0), T(0), T(0)};
-        if (hasA) {
-            T th0[3];
+                for (int k = 20; k < 29; ++k) prefetch_l2(arr[k] + n + NN);
+                if (hasA) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) th0[d] = arr[29 + d][n];
+                    for (int k = 32; k < 35; ++k) prefetch_l2(arr[k] + n + NN);
+                }
+                if (hasC) prefetch_l2(arr[36] + n + NN);
+            }
+            // the own momenta, loaded before the compute so their latency hides behind it
+            T pm0[4], pe0[9];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pm0[c] = __ldcs(arr[4 + c] + n);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) pe0[k] = __ldcs(arr[20 + k] + n);
+            T pa0[3] = {T(0), T(0), T(0)}, pc0 = T(0);
+            if (hasA) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) pa0[k] = __ldcs(arr[32 + k] + n);
+            }
+            if (hasC) pc0 = __ldcs(arr[36] + n);
+            // staged array a at the neighbour (ox, oy, oz)
+            auto at = [&](int a, int ox, int oy, int oz) -> T { return bs[oz + 1][a * ASZ + oy * RW + ox]; };
+            auto ldq_s = [&](int i, int ox, int oy, int oz, T* q) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) q[c] = at(4 + 4 * i + c, ox, oy, oz);
+            };
+            auto ldf_s = [&](int ox, int oy, int oz, T* f) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) f[c] = at(c, ox, oy, oz);
+            };
+
+            T f[4], lap[4], grad = T(0), eB = T(0);
+            ldf_s(0, 0, 0, f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) lap[c] = T(-6) * f[c];
+            T KB[3][3];
+            // U(1) sector: forward plaquette angles theta_01, theta_02, theta_12 at n (sines, cosines)
+            T KA[3] = {T(0), T(0), T(0)}, eBA = T(0), chi0 = T(0), lchi = T(0), gchi = T(0);
+            T psn[3] = {T(0), T(0), T(0)};
+            if (hasA) {
+#pragma unroll
+                for (int pr = 0; pr < 3; ++pr) {
+                    const int ii = pr == 2 ? 1 : 0, jj = pr == 0 ? 1 : 2;
+                    const T p = at(16 + ii, 0, 0, 0) + at(16 + jj, ii == 0, ii == 1, ii == 2) -
+                                at(16 + ii, jj == 0, jj == 1, jj == 2) - at(16 + jj, 0, 0, 0);
+                    T cs;
+                    phase_sc(p, &psn[pr], &cs);
+                    eBA += T(1) - cs;
+                }
+            }
+            if (hasC) chi0 = at(19, 0, 0, 0);
+            // forward SU(2) plaquettes U_01, U_02, U_12 at n: vector parts and magnetic energy
+            // (U_ji = U_ij^dag, so the plane (j, i) takes the vector part with the sign flipped)
+            T Pv[3][3];
 #pragma unroll
             for (int pr = 0; pr < 3; ++pr) {
                 const int ii = pr == 2 ? 1 : 0, jj = pr == 0 ? 1 : 2;
-                const T p = th0[ii] + arr[29 + jj][nb<T>(n, x, y, z, N, ii, 1)] - arr[29 + ii][nb<T>(n, x, y, z, N, jj, 1)] -
-                            th0[jj];
-                T cs;
-                phase_sc(p, &psn[pr], &cs);
-                eBA += T(1) - cs;
-            }
-        }
-        if (hasC) chi0 = arr[35][n];
-        // forward plaquettes U_01, U_02, U_12 at n: vector parts and magnetic energy
-        // (U_ji = U_ij^dag, so the plane (j, i) takes the vector part with the sign flipped)
-        T Pv[3][3];
+                T Ui[4], Ujp[4], Uip[4], Uj[4], t1[4], t2[4], c[4], P[4];
+                ldq_s(ii, 0, 0, 0, Ui);
+                ldq_s(jj, ii == 0, ii == 1, ii == 2, Ujp);
+                ldq_s(ii, jj == 0, jj == 1, jj == 2, Uip);
+                ldq_s(jj, 0, 0, 0, Uj);
+                qmul(Ui, Ujp, t1);
+                qconj(Uip, c);
+                qmul(t1, c, t2);
+                qconj(Uj, c);
+                qmul(t2, c, P);
+                eB += T(4) * (T(1) - P[0]);
 #pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
-            const int ii = pr == 2 ? 1 : 0, jj = pr == 0 ? 1 : 2;
-            T P[4];
-            plaq(arr, ii, jj, n, x, y, z, N, P);
-            eB += T(4) * (T(1) - P[0]);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) Pv[pr][k] = P[k + 1];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const size_t np = nb<T>(n, x, y, z, N, i, 1), nm = nb<T>(n, x, y, z, N, i, -1);
-            T q[4], qm[4], c[4], fp[4], fm[4], t[4], t2[4];
-            ldq(arr, i, n, q);
-            ldq(arr, i, nm, qm);
-            qconj(qm, c);
-            ldf(arr, np, fp);
-            ldf(arr, nm, fm);
-            umul(q, fp, t);
-            umul(c, fm, t2);
-            if (hasA) {  // W_i Phi(n+i) = e^{-i theta_i(n)} U_i Phi(n+i); W_i^dag(n-i) = U^dag e^{+i theta_i(n-i)}
-                T sn, cs;
-                phase_sc(arr[29 + i][n], &sn, &cs);
-                phase_minus(t, sn, cs);
-                phase_sc(arr[29 + i][nm], &sn, &cs);
-                phase_plus(t2, sn, cs);
-            }
-            if (hasC) {
-                const T cp = arr[35][np];
-                lchi += cp + arr[35][nm];
-                gchi += (cp - chi0) * (cp - chi0);
+                for (int k = 0; k < 3; ++k) Pv[pr][k] = P[k + 1];
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                lap[k] += t[k] + t2[k];
-                grad += (t[k] - f[k]) * (t[k] - f[k]);
-            }
-            T js[3];
-            im_sigma(f, t, js);
-            T mag[3] = {T(0), T(0), T(0)};
-            T uic[4];
-            qconj(q, uic);
+            for (int i = 0; i < 3; ++i) {
+                const int ex = i == 0, ey = i == 1, ez = i == 2;
+                T q[4], qm[4], c[4], fp[4], fm[4], t[4], t2[4];
+                ldq_s(i, 0, 0, 0, q);
+                ldq_s(i, -ex, -ey, -ez, qm);
+                qconj(qm, c);
+                ldf_s(ex, ey, ez, fp);
+                ldf_s(-ex, -ey, -ez, fm);
+                umul(q, fp, t);
+                umul(c, fm, t2);
+                if (hasA) {  // W_i Phi(n+i) = e^{-i theta_i(n)} U_i Phi(n+i); W_i^dag(n-i) = U^dag e^{+i theta_i(n-i)}
+                    T sn, cs;
+                    phase_sc(at(16 + i, 0, 0, 0), &sn, &cs);
+                    phase_minus(t, sn, cs);
+                    phase_sc(at(16 + i, -ex, -ey, -ez), &sn, &cs);
+                    phase_plus(t2, sn, cs);
+                }
+                if (hasC) {
+                    const T cp = at(19, ex, ey, ez);
+                    lchi += cp + at(19, -ex, -ey, -ez);
+                    gchi += (cp - chi0) * (cp - chi0);
+                }
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (j == i) continue;
-                const int pr = i + j - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
-                const T sg = i < j ? T(1) : T(-1);
-                T Q[4];
-                back_staple(arr, i, j, n, x, y, z, N, uic, Q);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) mag[k] += sg * Pv[pr][k] - Q[k + 1];
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) KB[i][k] = A1 * cJ * js[k] + Am * cM * mag[k];
-            if (hasA) {
-                // sum_{j != i} [sin theta_ij(n-j) - sin theta_ij(n)], theta_ji = -theta_ij
-                T magA = T(0);
+                for (int k = 0; k < 4; ++k) {
+                    lap[k] += t[k] + t2[k];
+                    grad += (t[k] - f[k]) * (t[k] - f[k]);
+                }
+                T js[3];
+                im_sigma(f, t, js);
+                // backward staples U_j^dag(n-j) U_ij(n-j) U_j(n-j) = U_j^dag(n-j) U_i(n-j) U_j(n-j+i) U_i^dag(n),
+                // the factors U_j^dag(n-j) U_j(n-j) = 1 of the plaquette form cancelled (unit links)
+                T mag[3] = {T(0), T(0), T(0)};
+                T uic[4];
+                qconj(q, uic);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     if (j == i) continue;
-                    const int ii = i < j ? i : j, jj = i < j ? j : i;
-                    const T sgn = i < j ? T(1) : T(-1);
-                    const size_t mj = nb<T>(n, x, y, z, N, j, -1);
-                    const int xj = j == 0 ? (x == 0 ? N - 1 : x - 1) : x;
-                    const int yj = j == 1 ? (y == 0 ? N - 1 : y - 1) : y;
-                    const int zj = j == 2 ? (z == 0 ? N - 1 : z - 1) : z;
-                    // theta_ij(n-j) = theta_i(n-j) + theta_j(n-j+i) - theta_i(n) - theta_j(n-j)
-                    const T pm = arr[29 + i][mj] + arr[29 + j][nb<T>(mj, xj, yj, zj, N, i, 1)] - arr[29 + i][n] -
-                                 arr[29 + j][mj];
-                    T smm, cmm;
-                    phase_sc(pm, &smm, &cmm);
-                    magA += smm - sgn * psn[ii + jj - 1];
+                    const int fx = j == 0, fy = j == 1, fz = j == 2;
+                    const int pr = i + j - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+                    const T sg_ = i < j ? T(1) : T(-1);
+                    T Uj[4], Ui[4], Ujp[4], cj[4], s1[4], s2[4], Q[4];
+                    ldq_s(j, -fx, -fy, -fz, Uj);
+                    ldq_s(i, -fx, -fy, -fz, Ui);
+                    ldq_s(j, ex - fx, ey - fy, ez - fz, Ujp);
+                    qconj(Uj, cj);
+                    qmul(cj, Ui, s1);
+                    qmul(s1, Ujp, s2);
+                    qmul(s2, uic, Q);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) mag[k] += sg_ * Pv[pr][k] - Q[k + 1];
                 }
-                KA[i] = A1 * cJA * im_dot(f, t) + Am * cMA * magA;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) KB[i][k] = A1 * cJ * js[k] + Am * cM * mag[k];
+                if (hasA) {
+                    // sum_{j != i} [sin theta_ij(n-j) - sin theta_ij(n)], theta_ji = -theta_ij
+                    T magA = T(0);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        if (j == i) continue;
+                        const int fx = j == 0, fy = j == 1, fz = j == 2;
+                        const int ii = i < j ? i : j, jj = i < j ? j : i;
+                        const T sgn = i < j ? T(1) : T(-1);
+                        // theta_ij(n-j) = theta_i(n-j) + theta_j(n-j+i) - theta_i(n) - theta_j(n-j)
+                        const T pm = at(16 + i, -fx, -fy, -fz) + at(16 + j, ex - fx, ey - fy, ez - fz) -
+                                     at(16 + i, 0, 0, 0) - at(16 + j, -fx, -fy, -fz);
+                        T smm, cmm;
+                        phase_sc(pm, &smm, &cmm);
+                        magA += smm - sgn * psn[ii + jj - 1];
+                    }
+                    KA[i] = A1 * cJA * im_dot(f, t) + Am * cMA * magA;
+                }
             }
-        }
-        const T mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
-        T dv;
-        T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
-        if (hasC) {
-            dv += qc * chi0 * chi0;
-            vpot += qc * mod2 * chi0 * chi0;
-        }
-        T sp = T(0), pr0 = T(0), pr1 = T(0);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const T K = -A3 * dv * f[c] + A1 * lap[c] * idx2;
-            const T p = arr[4 + c][n];
-            const T ps = p + h1 * K;
-            sp += ps * ps;
-            if (c == 0) pr0 = ps;
-            if (c == 1) pr1 = ps;
-            if (A.write) arr[4 + c][n] = p + h * K;
-        }
-        T sA = T(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const T e = arr[20 + 3 * i + k][n];
-                const T es = e + h1 * KB[i][k];
-                sA += es * es;
-                if (A.write) arr[20 + 3 * i + k][n] = e + h * KB[i][k];
+            const T mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];
+            T dv;
+            T vpot = gauge_pot<T>(A.mc.gpot, A.mc.pexp, lam, v2, mod2, &dv);
+            if (hasC) {
+                dv += qc * chi0 * chi0;
+                vpot += qc * mod2 * chi0 * chi0;
             }
-        ts[0] += f[0]; ts[1] += f[1];
-        ts[2] += f[0] * f[0]; ts[3] += f[1] * f[1];
-        ts[4] += pr0; ts[5] += pr1;
-        ts[6] += sp;
-        ts[7] += grad * idx2;
-        ts[8] += vpot;
-        ts[9] += sA;
-        ts[10] += eB;
-        if (hasA) {
-            T sAA = T(0);
+            T sp = T(0), pr0 = T(0), pr1 = T(0);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const T e = arr[32 + i][n];
-                const T es = e + h1 * KA[i];
-                sAA += es * es;
-                if (A.write) arr[32 + i][n] = e + h * KA[i];
+            for (int c = 0; c < 4; ++c) {
+                const T K = -A3 * dv * f[c] + A1 * lap[c] * idx2;
+                const T p = pm0[c];
+                const T ps = p + h1 * K;
+                sp += ps * ps;
+                if (c == 0) pr0 = ps;
+                if (c == 1) pr1 = ps;
+                if (A.write) arr[4 + c][n] = p + h * K;
             }
-            ts[11 % NS] += sAA;
-            ts[12 % NS] += eBA;
-        }
-        if (hasC) {
-            const T Kc = -A3 * T(2) * qc * mod2 * chi0 + A1 * (lchi - T(6) * chi0) * idx2;
-            const T p = arr[36][n];
-            const T ps = p + h1 * Kc;
-            if (A.write) arr[36][n] = p + h * Kc;
-            ts[13 % NS] += ps * ps;
-            ts[14 % NS] += gchi * idx2;
-        }
-        if (++cnt == 64) {
+            T sA = T(0);
 #pragma unroll
-            for (int s = 0; s < NS; ++s) { acc[s] += double(ts[s]); ts[s] = T(0); }
-            cnt = 0;
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T e = pe0[3 * i + k];
+                    const T es = e + h1 * KB[i][k];
+                    sA += es * es;
+                    if (A.write) arr[20 + 3 * i + k][n] = e + h * KB[i][k];
+                }
+            ts[0] += f[0]; ts[1] += f[1];
+            ts[2] += f[0] * f[0]; ts[3] += f[1] * f[1];
+            ts[4] += pr0; ts[5] += pr1;
+            ts[6] += sp;
+            ts[7] += grad * idx2;
+            ts[8] += vpot;
+            ts[9] += sA;
+            ts[10] += eB;
+            if (hasA) {
+                T sAA = T(0);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const T e = pa0[i];
+                    const T es = e + h1 * KA[i];
+                    sAA += es * es;
+                    if (A.write) arr[32 + i][n] = e + h * KA[i];
+                }
+                ts[11 % NS] += sAA;
+                ts[12 % NS] += eBA;
+            }
+            if (hasC) {
+                const T Kc = -A3 * T(2) * qc * mod2 * chi0 + A1 * (lchi - T(6) * chi0) * idx2;
+                const T p = pc0;
+                const T ps = p + h1 * Kc;
+                if (A.write) arr[36][n] = p + h * Kc;
+                ts[13 % NS] += ps * ps;
+                ts[14 % NS] += gchi * idx2;
+            }
+            if (++cnt == 64) {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) { acc[s] += double(ts[s]); ts[s] = T(0); }
+                cnt = 0;
+            }
+            sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
         }
+        __syncthreads();  // the segment's last three stages are free
+        issue();
+        issue();
+        issue();
+        issued += 3;
+        need += 2;
+        sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
+        cur += sg.len;
     }
+    cp_async_wait<0>();
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] += double(ts[s]);
+
     // block reduction, partials, last block
-    __shared__ double red[8][NS];
-    const int lin = threadIdx.x, lane = lin & 31, warp = lin >> 5, nwarps = (blockDim.x + 31) >> 5;
-    const int nlanes = min(32, (int)blockDim.x - 32 * warp);
+    __shared__ double red[NT / 32][NS];
+    const int lane = lin & 31, warp = lin >> 5, nwarps = NT / 32;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const double v = partial_warp_sum(acc[s], lane, nlanes);
+        const double v = partial_warp_sum(acc[s], lane, 32);
         if (lane == 0) red[warp][s] = v;
     }
     __syncthreads();
@@ -384,12 +519,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) su2_kick_kernel(c
     const double invV = 1.0 / (double)n3;
     for (int s = warp; s < NS; s += nwarps) {
         double ks = 0.0, kc = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += nlanes) {
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
             const double yk = __ldcg(&A.partials[(size_t)b * NS + s]) - kc, tk = ks + yk;
             kc = (tk - ks) - yk;
             ks = tk;
         }
-        const double r = partial_warp_sum(ks - kc, lane, nlanes);
+        const double r = partial_warp_sum(ks - kc, lane, 32);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();
@@ -537,49 +672,85 @@ static Su2Args su2_args(Lattice* L, int copy) {
     return A;
 }
 
+template <typename T, bool EXT, int BX> static const void* su2_kick_ptr() {
+    return (const void*)su2_kick_kernel<T, EXT, BX>;
+}
+static const void* su2_kick_fn(const Lattice* L) {
+    const bool ext = L->mc.ext != 0;
+    if (L->prec == CL_FP32) {
+        if (L->geo.BX == 32) return ext ? su2_kick_ptr<float, true, 32>() : su2_kick_ptr<float, false, 32>();
+        return ext ? su2_kick_ptr<float, true, 8>() : su2_kick_ptr<float, false, 8>();
+    }
+    return ext ? su2_kick_ptr<double, true, 8>() : su2_kick_ptr<double, false, 8>();
+}
+
+// Tile of the kick: 32 x 8 sites in FP32 when 32 divides N, else 8 x 8 (FP64
+// always: its stages are twice as large).  Ring of S = 4 stages (5 if it fits
+// twice per SM); grid = blocks resident per SM x SMs, at most one per plane tile.
 void su2_geometry(Lattice* L) {
     Geometry& g = L->geo;
-    g.N = L->mc.N;
-    g.threads = 256;
-    const size_t n3 = (size_t)g.N * g.N * g.N;
+    const int N = L->mc.N;
+    g.N = N;
+    g.V = L->prec == CL_FP32 ? 4 : 2;
+    g.BX = (L->prec == CL_FP32 && N % 32 == 0) ? 32 : 8;
+    if (const char* env = getenv("CL_SU2_TILE_X"))  // override: 8 forces the 8 x 8 tile
+        if (atoi(env) == 8) g.BX = 8;
+    g.BY = kSu2TileBY;
+    g.threads = g.BX * g.BY;
+    g.ntx = N / g.BX;
+    g.nty = N / g.BY;
+    const int na = L->mc.ext ? su2_staged<true>() : su2_staged<false>();
+    const size_t stage = (size_t)na * (g.BY + 2) * (g.BX + 2 * g.V) * L->tsize;
+    const void* fn = su2_kick_fn(L);
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    cudaGetLastError();
+    g.S = 4;
+    g.smem = 128 + g.S * stage;
     int per_sm = 1;
-    const bool ext = L->mc.ext != 0;
-    if (L->prec == CL_FP32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ext ? su2_kick_kernel<float, true> : su2_kick_kernel<float, false>,
-                                                      256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, ext ? su2_kick_kernel<double, true> : su2_kick_kernel<double, false>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, g.threads, g.smem);
     if (per_sm < 1) per_sm = 1;
+    {
+        int per5 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per5, fn, g.threads, 128 + 5 * stage) == cudaSuccess &&
+            per5 >= per_sm) {
+            g.S = 5;
+            g.smem = 128 + 5 * stage;
+        }
+        cudaGetLastError();
+    }
+    const long long W = (long long)g.ntx * g.nty * N;
     long long grid = (long long)L->sm_count * per_sm;
-    const long long need = (long long)((n3 + 255) / 256);
-    if (grid > need) grid = need;
+    if (grid > W) grid = W;
     if (grid > kMaxBlocks) grid = kMaxBlocks;
     g.grid = (int)grid;
-    g.ntiles = g.grid;
-    g.smem = 0;
+    g.ntiles = (int)W;
+}
+
+template <typename T, bool EXT>
+static void su2_pass_t(Lattice* L, const Su2Args& S, const Su2Args& D, cudaStream_t s) {
+    const Geometry& g = L->geo;
+    su2_drift_kernel<T, EXT><<<L->sm_count * 8, 256, 0, s>>>(S, D);
+    const dim3 blk(g.BX, g.BY);
+    if (g.BX == 32) su2_kick_kernel<T, EXT, sizeof(T) == 4 ? 32 : 8><<<g.grid, blk, g.smem, s>>>(D, g.S);
+    else su2_kick_kernel<T, EXT, 8><<<g.grid, blk, g.smem, s>>>(D, g.S);
 }
 
 cudaError_t su2_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
     Su2Args S = su2_args(L, src), D = su2_args(L, dst);
     D.pi = pi;
     D.write = write ? 1 : 0;
-    const int dg = L->sm_count * 8;
-    const int grid = L->geo.grid;
     if (L->mc.ext) {
-        if (L->prec == CL_FP32) {
-            su2_drift_kernel<float, true><<<dg, 256, 0, s>>>(S, D);
-            su2_kick_kernel<float, true><<<grid, 256, 0, s>>>(D);
-        } else {
-            su2_drift_kernel<double, true><<<dg, 256, 0, s>>>(S, D);
-            su2_kick_kernel<double, true><<<grid, 256, 0, s>>>(D);
-        }
+        if (L->prec == CL_FP32) su2_pass_t<float, true>(L, S, D, s);
+        else su2_pass_t<double, true>(L, S, D, s);
     } else if (L->prec == CL_FP32) {
-        su2_drift_kernel<float, false><<<dg, 256, 0, s>>>(S, D);
-        su2_kick_kernel<float, false><<<grid, 256, 0, s>>>(D);
+        su2_pass_t<float, false>(L, S, D, s);
     } else {
-        su2_drift_kernel<double, false><<<dg, 256, 0, s>>>(S, D);
-        su2_kick_kernel<double, false><<<grid, 256, 0, s>>>(D);
+        su2_pass_t<double, false>(L, S, D, s);
     }
     return cudaGetLastError();
 }

@@ -111,6 +111,28 @@ def test_su2u1_fp64_velocity_verlet_matches_oracle(integ, fmp, alpha, pot, eA, c
     lat.close()
 
 
+@pytest.mark.parametrize("N,prec,tol", [(40, cl.CL_FP64, 1e-12), (24, cl.CL_FP32, 5e-5), (64, cl.CL_FP32, 5e-5)])
+def test_su2u1_many_tiles_match_oracle(N, prec, tol):
+    """Several x-y tiles of the kick, block runs of planes crossing tiles: three
+    expanding VV2 steps with the U(1) sector and the singlet against the oracle."""
+    dt, fmp = 0.04, 0.7
+    m = SU2U1Model(N=N, dx=0.6, alpha=1.0, fmp2=fmp * fmp, lam=1.2, v2=0.8, g=0.9, kappa=1.21, pot=1, p=4, eA=0.7,
+                   q=1.3, chi=1)
+    ref = random_state(N, m, 13)
+    ref.b = math.sqrt(fmp * fmp / 3.0 * ref.energies().sum())
+    lat = gpu_lattice(m, "vv2", prec, fmp)
+    load(lat, ref)
+    lat.evolve(3)
+    ref.vv_steps(oracle.VV2, dt, 3)
+    check_state(fetch(lat, m), ref, tol)
+    mm = lat.measure_means()
+    E = ref.energies()
+    got = [mm["EK"][0], mm["EG"][0], mm["EV"][0], mm["EK"][1], mm["EG"][1], mm["EK"][2], mm["EG"][2], mm["EK"][3],
+           mm["EG"][3]]
+    assert np.allclose(got, E, rtol=10 * tol, atol=1e-14), (got, E)
+    lat.close()
+
+
 def test_su2u1_leapfrog_equals_velocity_verlet_positions_static():
     N, dt, n = 8, 0.04, 9
     m = SU2U1Model(N=N, dx=0.6, alpha=0.0, fmp2=0.0, lam=1.0, v2=1.0, g=1.1, kappa=0.9, eA=0.8, q=1.2)
