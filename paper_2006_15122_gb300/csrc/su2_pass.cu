@@ -14,10 +14,11 @@
 // unit quaternions renormalised), and the discrete Gauss law
 //   (1/dx) sum_i [piB_i(n) - U_i^dag(n-i) piB_i(n-i) U_i(n-i)]^a = (g/kappa) Im[Phi^dag sigma^a pi].
 //
-// One pass = a drift kernel (src copy -> dst copy, pointwise) followed by a
-// kick kernel in place on dst (stencil through L1/L2), which also reduces the
-// volume sums and runs the FP64 background update in its last block, shared
-// with the U(1) sector.  Array slots: 0-3 Phi (Re/Im of the two components),
+// One pass = a drift kernel (fields and links, src copy -> dst copy,
+// pointwise) followed by a kick kernel that reads the drifted fields and links
+// of dst through a shared-memory plane ring, the momenta of src, and writes
+// the kicked momenta to dst; it also reduces the volume sums and runs the FP64
+// background update in its last block, shared with the U(1) sector.  Array slots: 0-3 Phi (Re/Im of the two components),
 // 4-7 pi, 8-19 links (4 i + c), 20-28 piB (3 i + a).
 //
 // SU(2) x U(1) + chi (section 8.3; the EXT kernels): the doublet also carries
@@ -149,7 +150,7 @@ constexpr int kSu2TileBY = 8;
 
 template <typename T, bool EXT, int BX>
 __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512 : 256) / (BX * kSu2TileBY))
-    su2_kick_kernel(const Su2Args A, const int S) {
+    su2_kick_kernel(const Su2Args A, const Su2Args P, const int S) {
     constexpr int NS = EXT ? kSu2ExtNS : U1NS;
     constexpr int BY = kSu2TileBY, NT = BX * BY;
     constexpr int V = 16 / (int)sizeof(T);
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
     __shared__ const T* s_src[NA];
     const int N = A.mc.N;
     T* const* arr = reinterpret_cast<T* const*>(A.a);
+    T* const* parr = reinterpret_cast<T* const*>(P.a);  // momenta before the kick (the pass's source copy)
     const int tx = threadIdx.x, ty = threadIdx.y, lin = ty * BX + tx;
     if (lin == 0) {
 #pragma unroll
@@ -273,27 +275,27 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
             const size_t n = (size_t)(sg.z0 + zz) * NN + (size_t)y * N + x;
             if (zz + 1 < sg.len) {  // the momenta of the next plane into L2
 #pragma unroll
-                for (int k = 4; k < 8; ++k) prefetch_l2(arr[k] + n + NN);
+                for (int k = 4; k < 8; ++k) prefetch_l2(parr[k] + n + NN);
 #pragma unroll
-                for (int k = 20; k < 29; ++k) prefetch_l2(arr[k] + n + NN);
+                for (int k = 20; k < 29; ++k) prefetch_l2(parr[k] + n + NN);
                 if (hasA) {
 #pragma unroll
-                    for (int k = 32; k < 35; ++k) prefetch_l2(arr[k] + n + NN);
+                    for (int k = 32; k < 35; ++k) prefetch_l2(parr[k] + n + NN);
                 }
-                if (hasC) prefetch_l2(arr[36] + n + NN);
+                if (hasC) prefetch_l2(parr[36] + n + NN);
             }
             // the own momenta, loaded before the compute so their latency hides behind it
             T pm0[4], pe0[9];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) pm0[c] = __ldcs(arr[4 + c] + n);
+            for (int c = 0; c < 4; ++c) pm0[c] = __ldcs(parr[4 + c] + n);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) pe0[k] = __ldcs(arr[20 + k] + n);
+            for (int k = 0; k < 9; ++k) pe0[k] = __ldcs(parr[20 + k] + n);
             T pa0[3] = {T(0), T(0), T(0)}, pc0 = T(0);
             if (hasA) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) pa0[k] = __ldcs(arr[32 + k] + n);
+                for (int k = 0; k < 3; ++k) pa0[k] = __ldcs(parr[32 + k] + n);
             }
-            if (hasC) pc0 = __ldcs(arr[36] + n);
+            if (hasC) pc0 = __ldcs(parr[36] + n);
             // staged array a at the neighbour (ox, oy, oz)
             auto at = [&](int a, int ox, int oy, int oz) -> T { return bs[oz + 1][a * ASZ + oy * RW + ox]; };
             auto ldq_s = [&](int i, int ox, int oy, int oz, T* q) {
@@ -375,27 +377,36 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
                 }
                 T js[3];
                 im_sigma(f, t, js);
-                // backward staples U_j^dag(n-j) U_ij(n-j) U_j(n-j) = U_j^dag(n-j) U_i(n-j) U_j(n-j+i) U_i^dag(n),
-                // the factors U_j^dag(n-j) U_j(n-j) = 1 of the plaquette form cancelled (unit links)
+                // backward staples U_j^dag(n-j) U_ij(n-j) U_j(n-j) = X_j U_i^dag(n) with
+                // X_j = U_j^dag(n-j) U_i(n-j) U_j(n-j+i) (the factors U_j^dag(n-j) U_j(n-j) = 1 of
+                // the plaquette form cancelled, unit links); the product with U_i^dag(n) is
+                // linear, so it is taken once on the sum over j
                 T mag[3] = {T(0), T(0), T(0)};
-                T uic[4];
-                qconj(q, uic);
+                T Xs[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     if (j == i) continue;
                     const int fx = j == 0, fy = j == 1, fz = j == 2;
                     const int pr = i + j - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
                     const T sg_ = i < j ? T(1) : T(-1);
-                    T Uj[4], Ui[4], Ujp[4], cj[4], s1[4], s2[4], Q[4];
+                    T Uj[4], Ui[4], Ujp[4], cj[4], s1[4], s2[4];
                     ldq_s(j, -fx, -fy, -fz, Uj);
                     ldq_s(i, -fx, -fy, -fz, Ui);
                     ldq_s(j, ex - fx, ey - fy, ez - fz, Ujp);
                     qconj(Uj, cj);
                     qmul(cj, Ui, s1);
                     qmul(s1, Ujp, s2);
-                    qmul(s2, uic, Q);
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) mag[k] += sg_ * Pv[pr][k] - Q[k + 1];
+                    for (int k = 0; k < 4; ++k) Xs[k] += s2[k];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) mag[k] += sg_ * Pv[pr][k];
+                }
+                {
+                    T uic[4], Q[4];
+                    qconj(q, uic);
+                    qmul(Xs, uic, Q);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) mag[k] -= Q[k + 1];
                 }
 #pragma unroll
                 for (int k = 0; k < 3; ++k) KB[i][k] = A1 * cJ * js[k] + Am * cM * mag[k];
@@ -535,7 +546,9 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
 }
 
 // Drift with the coefficients prepared by the last pass: phi += cd pi,
-// U_i <- exp(-i cdA piB_i.sigma/2) U_i (renormalised); momenta copied.
+// U_i <- exp(-i cdA piB_i.sigma/2) U_i (renormalised).  The momenta are left to
+// the kick, which writes them to dst; the ones it does not kick (piA without the
+// U(1) sector, pchi without the singlet) are carried over here.
 // EXT: also theta_i += (eA/g) cdA piA_i (wrapped to [-pi, pi]) and chi += cd pchi.
 // src and dst may coincide (pointwise).
 template <typename T, bool EXT>
@@ -548,11 +561,7 @@ __global__ void su2_drift_kernel(const Su2Args S, const Su2Args D) {
     T* const* dst = reinterpret_cast<T* const*>(D.a);
     for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n3; n += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const T p = src[4 + c][n];
-            dst[c][n] = src[c][n] + cd * p;
-            dst[4 + c][n] = p;
-        }
+        for (int c = 0; c < 4; ++c) dst[c][n] = src[c][n] + cd * src[4 + c][n];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             T e[3], q[4], ex[4], r[4];
@@ -570,8 +579,6 @@ __global__ void su2_drift_kernel(const Su2Args S, const Su2Args D) {
             const T nr = T(1) / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
 #pragma unroll
             for (int c2 = 0; c2 < 4; ++c2) dst[8 + 4 * i + c2][n] = r[c2] * nr;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) dst[20 + 3 * i + k][n] = e[k];
         }
         if (EXT) {
             const T cA = S.mc.e2 > 0 ? T(st->cdA * (S.mc.e2 / S.mc.e)) : T(0);
@@ -579,11 +586,11 @@ __global__ void su2_drift_kernel(const Su2Args S, const Su2Args D) {
             for (int i = 0; i < 3; ++i) {
                 const T e = src[32 + i][n];
                 dst[29 + i][n] = S.mc.e2 > 0 ? wrap_phase(src[29 + i][n] + cA * e) : src[29 + i][n];
-                dst[32 + i][n] = e;
+                if (!(S.mc.e2 > 0)) dst[32 + i][n] = e;  // not kicked: carried over
             }
             const T pc = src[36][n];
             dst[35][n] = src[35][n] + cd * pc;
-            dst[36][n] = pc;
+            if (!S.mc.chi) dst[36][n] = pc;
         }
     }
 }
@@ -736,8 +743,8 @@ static void su2_pass_t(Lattice* L, const Su2Args& S, const Su2Args& D, cudaStrea
     const Geometry& g = L->geo;
     su2_drift_kernel<T, EXT><<<L->sm_count * 8, 256, 0, s>>>(S, D);
     const dim3 blk(g.BX, g.BY);
-    if (g.BX == 32) su2_kick_kernel<T, EXT, sizeof(T) == 4 ? 32 : 8><<<g.grid, blk, g.smem, s>>>(D, g.S);
-    else su2_kick_kernel<T, EXT, 8><<<g.grid, blk, g.smem, s>>>(D, g.S);
+    if (g.BX == 32) su2_kick_kernel<T, EXT, sizeof(T) == 4 ? 32 : 8><<<g.grid, blk, g.smem, s>>>(D, S, g.S);
+    else su2_kick_kernel<T, EXT, 8><<<g.grid, blk, g.smem, s>>>(D, S, g.S);
 }
 
 cudaError_t su2_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
