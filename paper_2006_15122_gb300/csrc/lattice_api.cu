@@ -307,6 +307,9 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
             return fail(nullptr, CL_ERR_ARG, "unknown gauge potential");
         if (model->noncompact != 0 && (model->noncompact != 1 || model->kind != CL_MODEL_U1))
             return fail(nullptr, CL_ERR_ARG, "noncompact is 0, or 1 for the U(1) model");
+        // the U(1) pass indexes sites in 32 bits (its 20 arrays of N^3 would not fit in memory beyond that)
+        if (model->kind == CL_MODEL_U1 && (long long)N * N * N >= (1LL << 32))
+            return fail(nullptr, CL_ERR_ARG, "U(1): N^3 must be below 2^32");
         if (model->potential == CL_POT_MONOMIAL && model->pexp != 2 && model->pexp != 4 && model->pexp != 6)
             return fail(nullptr, CL_ERR_ARG, "pexp must be 2, 4 or 6");
         if (model->kind == CL_MODEL_SU2) {

@@ -40,6 +40,7 @@
 
 #include "cl_internal.cuh"
 #include "gauge_finish.cuh"
+#include "plane_ring.cuh"
 
 namespace cl {
 
@@ -130,15 +131,9 @@ template <typename T> __device__ __forceinline__ size_t nb(size_t n, int x, int 
 //
 // The kick reads Phi and the links (and with EXT the U(1) angles and the
 // singlet) at the site and its neighbours: n +- i, and for the plaquettes
-// n + i + j, n - j + i.  A block of BX x 8 threads owns a BX x 8 tile in x-y,
-// one site per thread, and marches a run of planes in z.  Those arrays are
-// staged plane by plane in a ring of S shared-memory stages with cp.async:
-// planes z-1, z, z+1 (with a one-cell x-y halo, corners included) are
-// resident while plane z computes and the next plane is in flight, one
-// barrier per plane.  The momenta are read and written at the own site only.
-// Work split: the (x-y tile, z) plane tiles, x-y tile major and y-tiles
-// fastest, are cut into equal contiguous ranges, one per block, so every
-// block marches the same number of planes.
+// n + i + j, n - j + i.  Those arrays go through the shared-memory plane ring
+// of plane_ring.cuh (BX x 8 tiles, one site per thread); the momenta are read
+// and written at the own site only.
 
 // staged array k -> slot in the 37-array layout: Phi 0-3, links 8-19,
 // U(1) angles 29-31, singlet 35
@@ -153,12 +148,9 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
     su2_kick_kernel(const Su2Args A, const Su2Args P, const int S) {
     constexpr int NS = EXT ? kSu2ExtNS : U1NS;
     constexpr int BY = kSu2TileBY, NT = BX * BY;
-    constexpr int V = 16 / (int)sizeof(T);
     constexpr int NA = su2_staged<EXT>();
-    constexpr int RW = BX + 2 * V, ROWS = BY + 2, ASZ = ROWS * RW, STG = NA * ASZ;
-    constexpr int VPR = BX / V;      // 16-byte vectors per row
-    constexpr int VPA = ROWS * VPR;  // vectors per array and plane, y-halo rows included
-    constexpr int HPA = 2 * ROWS;    // x-halo cells per array and plane, corners included
+    using Ring = PlaneRing<T, NA, BX, BY>;
+    constexpr int V = Ring::V, RW = Ring::RW, ASZ = Ring::ASZ;
     DevState* st = A.st;
     if (st->error) return;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -182,76 +174,9 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
     const T qc = T(A.mc.q);
     const size_t n3 = (size_t)N * N * N, NN = (size_t)N * N;
 
-    // this block's range of plane tiles; a segment is its part inside one x-y tile
-    const int nty = N / BY;
-    const long long W = (long long)(N / BX) * nty * N;
-    const long long beg = W * blockIdx.x / gridDim.x, end = W * (blockIdx.x + 1) / gridDim.x;
-    struct Seg {
-        int x0, y0, z0, len;
-    };
-    auto seg_at = [&](long long cur) {
-        Seg g;
-        const long long xy = cur / N;
-        g.z0 = (int)(cur - xy * N);
-        g.len = (int)min((long long)(N - g.z0), end - cur);
-        g.y0 = (int)(xy % nty) * BY;
-        g.x0 = (int)(xy / nty) * BX;
-        return g;
-    };
     __syncthreads();  // s_src
-
-    // loader: walks the same segments, planes z0-1 .. z0+len of each
-    long long ld_cur = beg;
-    Seg ls = seg_at(beg);
-    int ld_p = 0, ld_slot = 0;
-    auto issue = [&]() {
-        if (ld_cur < end) {
-            int z = ls.z0 - 1 + ld_p;
-            z = z < 0 ? z + N : (z >= N ? z - N : z);
-            T* dst = sm + ld_slot * STG;
-            const size_t zoff = (size_t)z * NN;
-#pragma unroll
-            for (int e0 = 0; e0 < NA * VPA; e0 += NT) {
-                const int e = e0 + lin;
-                if (e < NA * VPA) {
-                    const int a = e / VPA, r = (e % VPA) / VPR, v = e % VPR;
-                    int y = ls.y0 - 1 + r;
-                    y = y < 0 ? y + N : (y >= N ? y - N : y);
-                    cp_async16(dst + a * ASZ + r * RW + V + v * V, s_src[a] + zoff + (size_t)y * N + ls.x0 + v * V);
-                }
-            }
-#pragma unroll
-            for (int e0 = 0; e0 < NA * HPA; e0 += NT) {
-                const int e = e0 + lin;
-                if (e < NA * HPA) {
-                    const int a = e / HPA, side = (e % HPA) / ROWS, r = e % ROWS;
-                    int y = ls.y0 - 1 + r;
-                    y = y < 0 ? y + N : (y >= N ? y - N : y);
-                    const int x = side == 0 ? (ls.x0 == 0 ? N - 1 : ls.x0 - 1) : (ls.x0 + BX == N ? 0 : ls.x0 + BX);
-                    cp_async_elem(dst + a * ASZ + r * RW + (side == 0 ? V - 1 : V + BX), s_src[a] + zoff + (size_t)y * N + x);
-                }
-            }
-            if (++ld_p == ls.len + 2) {
-                ld_p = 0;
-                ld_cur += ls.len;
-                if (ld_cur < end) ls = seg_at(ld_cur);
-            }
-            if (++ld_slot == S) ld_slot = 0;
-        }
-        cp_async_commit();
-    };
-    int issued = 0;
-    auto wait_for = [&](int need) {  // load `need` landed for every thread
-        switch (issued - 1 - need) {
-            case 0: cp_async_wait<0>(); break;
-            case 1: cp_async_wait<1>(); break;
-            case 2: cp_async_wait<2>(); break;
-            case 3: cp_async_wait<3>(); break;
-            case 4: cp_async_wait<4>(); break;
-            default: cp_async_wait<5>(); break;
-        }
-        __syncthreads();
-    };
+    Ring ring;
+    ring.start(sm, s_src, N, S, lin);
 
     // per-thread sums in T, folded into FP64 every 64 sites
     double acc[NS];
@@ -260,18 +185,13 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
     for (int s = 0; s < NS; ++s) { acc[s] = 0.0; ts[s] = T(0); }
     int cnt = 0;
 
-    for (int L = 0; L < S; ++L, ++issued) issue();
-    int sl_m = 0, need = 2;
     const int own = (ty + 1) * RW + V + tx;
-    for (long long cur = beg; cur < end;) {
-        const Seg sg = seg_at(cur);
+    for (long long cur = ring.beg; cur < ring.end;) {
+        const typename Ring::Seg sg = ring.seg_at(cur);
         const int x = sg.x0 + tx, y = sg.y0 + ty;
-        for (int zz = 0; zz < sg.len; ++zz, ++need) {
-            wait_for(need);  // planes z-1, z, z+1 have landed
-            if (zz > 0) { issue(); ++issued; }  // refill the stage of plane z-2
-            const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
-            const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
-            const T* bs[3] = {sm + sl_m * STG + own, sm + sl_c * STG + own, sm + sl_p * STG + own};
+        for (int zz = 0; zz < sg.len; ++zz) {
+            ring.begin_plane(zz);  // planes z-1, z, z+1 resident
+            const T* bs[3] = {ring.stage(-1) + own, ring.stage(0) + own, ring.stage(1) + own};
             const size_t n = (size_t)(sg.z0 + zz) * NN + (size_t)y * N + x;
             if (zz + 1 < sg.len) {  // the momenta of the next plane into L2
 #pragma unroll
@@ -490,18 +410,12 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
                 for (int s = 0; s < NS; ++s) { acc[s] += double(ts[s]); ts[s] = T(0); }
                 cnt = 0;
             }
-            sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
+            ring.end_plane();
         }
-        __syncthreads();  // the segment's last three stages are free
-        issue();
-        issue();
-        issue();
-        issued += 3;
-        need += 2;
-        sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
+        ring.end_segment();
         cur += sg.len;
     }
-    cp_async_wait<0>();
+    ring.finish();
 #pragma unroll
     for (int s = 0; s < NS; ++s) acc[s] += double(ts[s]);
 

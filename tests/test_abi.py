@@ -67,7 +67,8 @@ def test_init_rejects_unstable_time_step():
 
 
 @pytest.mark.parametrize("bad", ["integrator", "pexp", "fields", "kir", "u1_charge", "u1_integrator",
-                                 "gauge_potential", "gauge_pexp", "su2_fields", "su2_u1_charge", "noncompact_su2"])
+                                 "gauge_potential", "gauge_pexp", "su2_fields", "su2_u1_charge", "noncompact_su2",
+                                 "u1_too_many_sites"])
 def test_init_rejects_bad_arguments(bad):
     m = cl.make_model(n_fields=1, pexp=2)
     g = cl.make_grid(16, 0.5, 0.01)
@@ -97,6 +98,10 @@ def test_init_rejects_bad_arguments(bad):
         m.gauge_e = 1.0
         m.n_fields = 3 if bad == "su2_fields" else 1
         m.gauge_e_u1 = -1.0 if bad == "su2_u1_charge" else 0.0
+    if bad == "u1_too_many_sites":  # 32-bit site indices of the U(1) pass
+        m.kind = cl.CL_MODEL_U1
+        m.gauge_e = 1.0
+        g.N = 1632
     if bad == "noncompact_su2":  # the non-compact form exists for U(1) only
         m.kind = cl.CL_MODEL_SU2
         m.gauge_e = 1.0

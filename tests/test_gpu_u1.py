@@ -69,6 +69,40 @@ def test_u1_fp64_leapfrog_matches_oracle(fmp, alpha):
     lat.close()
 
 
+@pytest.mark.parametrize("N,prec,tol,nc", [(40, cl.CL_FP64, 1e-12, 0), (40, cl.CL_FP64, 1e-12, 1),
+                                           (24, cl.CL_FP32, 5e-5, 0), (64, cl.CL_FP32, 5e-5, 0)])
+def test_u1_many_tiles_match_oracle(N, prec, tol, nc):
+    """Lattices of several x-y tiles of the pass (8 x 8 sites in FP64 and when 32
+    does not divide N, 32 x 8 in FP32 otherwise), with each block's run of planes
+    crossing from one tile to the next: expanding leapfrog steps against the
+    oracle, compact and (FP64) non-compact."""
+    fmp, alpha, dx = 0.8, 0.5, 0.5
+    kIR, dt = 2 * math.pi / (N * dx), 0.05
+    lat = gpu_u1(N, kIR, dt, prec, fmp=fmp, alpha=alpha, e=0.9, lam=1.2, v2=0.7, omega=1.1, nc=nc)
+    om = U1Model(N=N, dx=dx, alpha=alpha, fmp2=fmp * fmp, lam=1.2, v2=0.7, e=0.9, kappa=1.21, noncompact=nc)
+    phi = inputs.fields(2, N, seed=13, amp=0.6, kmax=4, means=[0.4, -0.1])
+    pi = inputs.fields(2, N, seed=14, amp=0.3, kmax=4)
+    th = inputs.angles(N, 15, scale=0.4)
+    pa = inputs.fields(3, N, seed=16, amp=0.2, kmax=4)
+    ref = U1Lattice(om, phi, pi, th, pa)
+    ref.b = math.sqrt(fmp * fmp / 3 * ref.energies().sum())
+    for i in range(2):
+        lat.set_field(cl.FIELD(i), phi[i])
+        lat.set_field(cl.MOMENTUM(i), pi[i])
+    for i in range(3):
+        lat.set_field(cl.LINK(i), th[i])
+        lat.set_field(cl.EMOMENTUM(i), pa[i])
+    lat.set_background(1.0, ref.b, 0.0)
+    ref.lf_prepare(dt)
+    lat.evolve(3)
+    ref.lf_steps(dt, 3)
+    gphi, gpi, gth, gpa = get_all(lat)
+    errs = (rel(gphi, ref.phi), rel(gpi, ref.pi), angle_err(gth, ref.theta) if not nc else rel(gth, ref.theta),
+            rel(gpa, ref.piA))
+    assert max(errs) < tol, errs
+    lat.close()
+
+
 def test_u1_initial_conditions_match_oracle():
     N, dx = 16, 0.5
     kIR = 2 * math.pi / (N * dx)
