@@ -15,7 +15,7 @@ namespace cl {
 constexpr int U1NS = 11;
 
 static __device__ double Ka_u1(const ModelConst& mc, double a, double EKp, double EGp, double EV, double EKA, double EGA) {
-    return mc.fmp2 / 3.0 * pow(a, 2.0 * mc.alpha + 1.0) *
+    return mc.fmp2 / 3.0 * apow(a, 2.0 * mc.alpha + 1.0) *
            ((mc.alpha - 2.0) * EKp + mc.alpha * EGp + (mc.alpha + 1.0) * EV + (mc.alpha - 1.0) * (EKA + EGA));
 }
 
@@ -43,7 +43,7 @@ static __device__ void u1_finish(DevState* st, const double* tot, const ModelCon
     for (int s = 0; s < ns; ++s) st->sums[s] = tot[s];
     const double Et = EKp + EGp + EV + EKA + EGA;
     if (!isfinite(Et)) { st->error = CL_ERR_NONFINITE; return; }
-    auto rhs = [&](double aa, double E) { return mc.fmp2 / 3.0 * pow(aa, 2.0 * (mc.alpha + 1.0)) * E; };
+    auto rhs = [&](double aa, double E) { return mc.fmp2 / 3.0 * apow(aa, 2.0 * (mc.alpha + 1.0)) * E; };
     const int kind = pi.kind;
     if (kind == PK_MEASURE) {
         if (mc.bg) {
@@ -65,8 +65,8 @@ static __device__ void u1_finish(DevState* st, const double* tot, const ModelCon
         return;
     }
     if (kind == PK_LF_EKM) {
-        st->EKm = Sp / pow(st->ahm, 6.0);
-        st->EKAm = mc.kappa * SA / (2.0 * pow(st->ahm, 4.0));
+        st->EKm = Sp / apow(st->ahm, 6.0);
+        st->EKAm = mc.kappa * SA / (2.0 * apow(st->ahm, 4.0));
         return;
     }
     if (kind == PK_LF_PREPARE) {
@@ -109,12 +109,12 @@ static __device__ void u1_finish(DevState* st, const double* tot, const ModelCon
             an = a + h * bn;
         }
         const double ah = 0.5 * (a + an);
-        st->cd = h * pow(ah, -(3.0 - mc.alpha));
-        st->cdA = mc.e * mc.dx * h * pow(ah, -(1.0 - mc.alpha));
+        st->cd = h * apow(ah, -(3.0 - mc.alpha));
+        st->cdA = mc.e * mc.dx * h * apow(ah, -(1.0 - mc.alpha));
         st->a = an;
-        st->A1 = pow(an, 1.0 + mc.alpha);
-        st->A3 = pow(an, 3.0 + mc.alpha);
-        st->Am = pow(an, mc.alpha - 1.0);
+        st->A1 = apow(an, 1.0 + mc.alpha);
+        st->A3 = apow(an, 3.0 + mc.alpha);
+        st->Am = apow(an, mc.alpha - 1.0);
         st->t += h;
         return;
     }
@@ -127,25 +127,25 @@ static __device__ void u1_finish(DevState* st, const double* tot, const ModelCon
     double bp = st->b, ekp = 0, eka = 0;
     for (int it = 0; it < 100; ++it) {
         const double ah = a + 0.5 * pi.dt * bp;
-        ekp = Sp / pow(ah, 6.0);
-        eka = mc.kappa * SA / (2.0 * pow(ah, 4.0));
+        ekp = Sp / apow(ah, 6.0);
+        eka = mc.kappa * SA / (2.0 * apow(ah, 4.0));
         const double bn = st->b + pi.dt * Ka_u1(mc, a, 0.5 * (st->EKm + ekp), EGp, EV, 0.5 * (st->EKAm + eka), EGA);
         const double d = fabs(bn - bp);
         bp = bn;
         if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
     }
     const double an = a + pi.dt * bp, ah = 0.5 * (a + an);
-    st->EKm = Sp / pow(ah, 6.0);
-    st->EKAm = mc.kappa * SA / (2.0 * pow(ah, 4.0));
+    st->EKm = Sp / apow(ah, 6.0);
+    st->EKAm = mc.kappa * SA / (2.0 * apow(ah, 4.0));
     st->b = bp;
     st->ahm = ah;
     st->EGm = EGp; st->EVm = EV; st->EGAm = EGA;
-    st->cd = pi.dt * pow(ah, -(3.0 - mc.alpha));
-    st->cdA = mc.e * mc.dx * pi.dt * pow(ah, -(1.0 - mc.alpha));
+    st->cd = pi.dt * apow(ah, -(3.0 - mc.alpha));
+    st->cdA = mc.e * mc.dx * pi.dt * apow(ah, -(1.0 - mc.alpha));
     st->a = an;
-    st->A1 = pow(an, 1.0 + mc.alpha);
-    st->A3 = pow(an, 3.0 + mc.alpha);
-    st->Am = pow(an, mc.alpha - 1.0);
+    st->A1 = apow(an, 1.0 + mc.alpha);
+    st->A3 = apow(an, 3.0 + mc.alpha);
+    st->Am = apow(an, mc.alpha - 1.0);
     st->t += pi.dt;
 }
 

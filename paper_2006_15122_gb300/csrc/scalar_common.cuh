@@ -47,18 +47,18 @@ static __device__ void potential_bar(const ModelConst& mc, const double* fb, dou
 }
 
 static __device__ double Ka_of(const ModelConst& mc, double a, double EK, double EG, double EV) {
-    return mc.fmp2 / 3.0 * pow(a, 1.0 + 2.0 * mc.alpha) *
+    return mc.fmp2 / 3.0 * apow(a, 1.0 + 2.0 * mc.alpha) *
            ((mc.alpha - 2.0) * EK + mc.alpha * EG + (mc.alpha + 1.0) * EV);
 }
 
 static __device__ double hubble_rhs(const ModelConst& mc, double a, double Etot) {
-    return mc.fmp2 / 3.0 * pow(a, 2.0 * (mc.alpha + 1.0)) * Etot;
+    return mc.fmp2 / 3.0 * apow(a, 2.0 * (mc.alpha + 1.0)) * Etot;
 }
 
 static __device__ void set_kick_powers(DevState* st, const ModelConst& mc, double a) {
-    st->A1 = pow(a, 1.0 + mc.alpha);
-    st->A3 = pow(a, 3.0 + mc.alpha);
-    st->Am = pow(a, mc.alpha - 1.0);
+    st->A1 = apow(a, 1.0 + mc.alpha);
+    st->A3 = apow(a, 3.0 + mc.alpha);
+    st->Am = apow(a, mc.alpha - 1.0);
 }
 
 // Scalar update of the last block (thread 0).  tot[] are sums / N^3.
@@ -104,7 +104,7 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
         return;
     }
     if (kind == PK_LF_EKM) {  // E_K of the momenta half a step behind
-        const double ah6 = pow(st->ahm, 6.0);
+        const double ah6 = apow(st->ahm, 6.0);
         st->EKm = S / (2.0 * ah6);
         return;
     }
@@ -146,7 +146,7 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
         double bp = st->b;
         for (int it = 0; it < 100; ++it) {
             const double ahh = a + 0.5 * pi.dt * bp;
-            const double EKp = S / (2.0 * pow(ahh, 6.0));
+            const double EKp = S / (2.0 * apow(ahh, 6.0));
             const double bn = st->b + pi.dt * Ka_of(mc, a, 0.5 * (st->EKm + EKp), EGt, EVt);
             const double d = fabs(bn - bp);
             bp = bn;
@@ -154,7 +154,7 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
         }
         anew = a + pi.dt * bp;
         ah = 0.5 * (a + anew);
-        st->EKm = S / (2.0 * pow(ah, 6.0));
+        st->EKm = S / (2.0 * apow(ah, 6.0));
         st->b = bp;
         st->ahm = ah;
         st->EGm = EGt;
@@ -181,8 +181,8 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
     }
     // prepare the drift of the next pass
     double cd = 0.0, dtn = 0.0;
-    if (kind == PK_VV_FIRST || kind == PK_VV_MID) { cd = pi.wn * pi.dt * pow(ah, -(3.0 - mc.alpha)); dtn = pi.wn * pi.dt; }
-    if (kind == PK_LF) { cd = pi.dt * pow(ah, -(3.0 - mc.alpha)); dtn = pi.dt; }
+    if (kind == PK_VV_FIRST || kind == PK_VV_MID) { cd = pi.wn * pi.dt * apow(ah, -(3.0 - mc.alpha)); dtn = pi.wn * pi.dt; }
+    if (kind == PK_LF) { cd = pi.dt * apow(ah, -(3.0 - mc.alpha)); dtn = pi.dt; }
     st->cd = cd;
     if (cd != 0.0) {
         for (int f = 0; f < nf; ++f) st->phibar[f] += cd * st->pibar[f];
