@@ -265,6 +265,30 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Sum over the nl existing lanes of a possibly partial warp (nl = 1..32);
 // the result is valid in lane 0.  Shuffles name only existing lanes.
+// One lane's share of a block-partials reduction: the Kahan sum of
+// partials[b * ns + s] over b = lane, lane + nl, ... < nb in that order, with
+// the loads issued eight at a time so that their L2 latencies overlap.
+__device__ __forceinline__ double lane_kahan(const double* partials, int nb, int ns, int s, int lane, int nl) {
+    double ks = 0.0, kc = 0.0;
+    for (int b0 = lane; b0 < nb; b0 += 8 * nl) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int b = b0 + k * nl;
+            v[k] = b < nb ? __ldcg(&partials[(size_t)b * ns + s]) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (b0 + k * nl < nb) {
+                const double yk = v[k] - kc, tk = ks + yk;
+                kc = (tk - ks) - yk;
+                ks = tk;
+            }
+        }
+    }
+    return ks - kc;
+}
+
 template <typename T> __device__ __forceinline__ T partial_warp_sum(T v, int lane, int nl) {
     const unsigned mask = nl >= 32 ? 0xffffffffu : ((1u << nl) - 1u);
 #pragma unroll

@@ -316,13 +316,7 @@ __global__ void __launch_bounds__(32) ensemble_finish_kernel(const EnsLat* lat, 
     const int lane = threadIdx.x;
     const double invV = 1.0 / ((double)L.N * L.N * L.N);
     for (int s = 0; s < NS; ++s) {
-        double ks = 0.0, kc = 0.0;
-        for (int b = lane; b < L.ntiles; b += 32) {
-            const double yk = L.partials[(size_t)b * NS + s] - kc, tk = ks + yk;
-            kc = (tk - ks) - yk;
-            ks = tk;
-        }
-        const double r = warp_sum(ks - kc);
+        const double r = warp_sum(lane_kahan(L.partials, L.ntiles, NS, s, lane, 32));
         if (lane == 0) tot[s] = r * invV;
     }
     __syncwarp();

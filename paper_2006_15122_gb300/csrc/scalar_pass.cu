@@ -355,14 +355,7 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
     __shared__ double tot[kMaxSums];
     const double invV = 1.0 / ((double)N * N * N);
     for (int s = warp; s < NS; s += nwarps) {
-        double ks = 0.0, kc = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += nlanes) {
-            const double xv = __ldcg(&A.partials[(size_t)b * NS + s]);
-            const double yk = xv - kc, tk = ks + yk;
-            kc = (tk - ks) - yk;
-            ks = tk;
-        }
-        const double r = partial_warp_sum(ks - kc, lane, nlanes);
+        const double r = partial_warp_sum(lane_kahan(A.partials, (int)gridDim.x, NS, s, lane, nlanes), lane, nlanes);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();

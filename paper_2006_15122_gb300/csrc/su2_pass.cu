@@ -443,13 +443,7 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
     __shared__ double tot[NS];
     const double invV = 1.0 / (double)n3;
     for (int s = warp; s < NS; s += nwarps) {
-        double ks = 0.0, kc = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const double yk = __ldcg(&A.partials[(size_t)b * NS + s]) - kc, tk = ks + yk;
-            kc = (tk - ks) - yk;
-            ks = tk;
-        }
-        const double r = partial_warp_sum(ks - kc, lane, 32);
+        const double r = partial_warp_sum(lane_kahan(A.partials, (int)gridDim.x, NS, s, lane, 32), lane, 32);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();

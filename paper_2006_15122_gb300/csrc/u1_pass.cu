@@ -249,14 +249,7 @@ __global__ void __launch_bounds__(BX * kU1TileBY, (sizeof(T) == 4 ? 512 : 256) /
     __shared__ double tot[U1NS];
     const double invV = 1.0 / (double)n3;
     for (int s = warp; s < U1NS; s += nwarps) {
-        double ks = 0.0, kc = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += nlanes) {
-            const double xv = __ldcg(&A.partials[(size_t)b * U1NS + s]);
-            const double yk = xv - kc, tk = ks + yk;
-            kc = (tk - ks) - yk;
-            ks = tk;
-        }
-        const double r = partial_warp_sum(ks - kc, lane, nlanes);
+        const double r = partial_warp_sum(lane_kahan(A.partials, (int)gridDim.x, U1NS, s, lane, nlanes), lane, nlanes);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();
