@@ -82,6 +82,13 @@ struct ModelConst {
     double e2;
     int chi, ext;
     int nc;  // U(1): non-compact gauge kinetics (section 5.2)
+    // host-computed factors of the FP64 background update (one thread on the
+    // device, where every division is a long dependent chain)
+    double fmp2_3;      // (f*/m_p)^2 / 3
+    double inv_vol;     // 1 / N^3
+    double inv_e_sq;    // 1 / e^2 (gauge models)
+    double inv_e2_sq;   // 1 / e_A^2 (SU(2) x U(1); 0 without the U(1) sector)
+    double inv_dx4;     // 1 / dx^4
 };
 
 // Potential of the charged scalar of the gauge models as a function of
@@ -265,11 +272,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Sum over the nl existing lanes of a possibly partial warp (nl = 1..32);
 // the result is valid in lane 0.  Shuffles name only existing lanes.
-// One lane's share of a block-partials reduction: the Kahan sum of
-// partials[b * ns + s] over b = lane, lane + nl, ... < nb in that order, with
-// the loads issued eight at a time so that their L2 latencies overlap.
-__device__ __forceinline__ double lane_kahan(const double* partials, int nb, int ns, int s, int lane, int nl) {
-    double ks = 0.0, kc = 0.0;
+// One warp's sum of partials[b * ns + s] over b < nb: each lane adds its share
+// (b = lane, lane + nl, ...) pairwise, eight loads at a time, then a shuffle
+// tree.  The order is fixed, so every run gives the same bits; the error is that
+// of pairwise summation, O(log2(nb)) ulp.
+__device__ __forceinline__ double warp_partials_sum(const double* partials, int nb, int ns, int s, int lane, int nl) {
+    double acc = 0.0;
     for (int b0 = lane; b0 < nb; b0 += 8 * nl) {
         double v[8];
 #pragma unroll
@@ -277,16 +285,15 @@ __device__ __forceinline__ double lane_kahan(const double* partials, int nb, int
             const int b = b0 + k * nl;
             v[k] = b < nb ? __ldcg(&partials[(size_t)b * ns + s]) : 0.0;
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (b0 + k * nl < nb) {
-                const double yk = v[k] - kc, tk = ks + yk;
-                kc = (tk - ks) - yk;
-                ks = tk;
-            }
-        }
+        acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     }
-    return ks - kc;
+    const unsigned mask = nl >= 32 ? 0xffffffffu : ((1u << nl) - 1u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_down_sync(mask, acc, o);
+        if (lane + o < nl) acc += t;
+    }
+    return acc;
 }
 
 template <typename T> __device__ __forceinline__ T partial_warp_sum(T v, int lane, int nl) {

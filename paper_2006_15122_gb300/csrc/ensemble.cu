@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
 }
 
 
-// Member finish of a pass: warp-strided Kahan sums of the member's per-tile
+// Member finish of a pass: fixed-order pairwise sums of the member's per-tile
 // partials (lane l takes tiles l, l+32, ...; fixed order, then a fixed shuffle
 // tree), normalised to volume averages, then the FP64 background update.
 template <typename T>
@@ -314,9 +314,9 @@ __global__ void __launch_bounds__(32) ensemble_finish_kernel(const EnsLat* lat, 
     const EnsLat& L = lat[blockIdx.x];
     __shared__ double tot[16];
     const int lane = threadIdx.x;
-    const double invV = 1.0 / ((double)L.N * L.N * L.N);
+    const double invV = L.mc.inv_vol;
     for (int s = 0; s < NS; ++s) {
-        const double r = warp_sum(lane_kahan(L.partials, L.ntiles, NS, s, lane, 32));
+        const double r = warp_partials_sum(L.partials, L.ntiles, NS, s, lane, 32);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncwarp();

@@ -14,9 +14,16 @@ namespace cl {
 
 constexpr int U1NS = 11;
 
+// K_a of the gauge models (fmp2_3 = (f*/m_p)^2 / 3).
 static __device__ double Ka_u1(const ModelConst& mc, double a, double EKp, double EGp, double EV, double EKA, double EGA) {
-    return mc.fmp2 / 3.0 * apow(a, 2.0 * mc.alpha + 1.0) *
+    return mc.fmp2_3 * apow(a, 2.0 * mc.alpha + 1.0) *
            ((mc.alpha - 2.0) * EKp + mc.alpha * EGp + (mc.alpha + 1.0) * EV + (mc.alpha - 1.0) * (EKA + EGA));
+}
+
+// x^e from x and 1/x: a non-negative power of whichever of the two makes the
+// exponent non-negative (no division).
+static __device__ __forceinline__ double apow2(double x, double ix, double e) {
+    return e >= 0.0 ? apow(x, e) : apow(ix, -e);
 }
 
 // SU(2) x U(1) + chi (ns = 15) adds {<sum piA_sync^2>, <sum_{i<j} (1 - cos theta_ij)>,
@@ -24,53 +31,54 @@ static __device__ double Ka_u1(const ModelConst& mc, double a, double EKp, doubl
 // scalar sectors (Phi, chi) and the gauge sectors (SU(2), U(1)) in aggregate,
 // which is exact because every energy of one class scales with the same power
 // of a (chi's kinetic and gradient energies carry the 1/2 of a real field).
+// The state is read once and written once, and powers of a come from 1/a, so
+// that the chain of dependent FP64 operations of this one thread stays short.
 static __device__ void u1_finish(DevState* st, const double* tot, const ModelConst& mc, const PassInfo& pi,
                                  int ns = U1NS) {
-    const double a = st->a, a2 = a * a, a4 = a2 * a2, a6 = a4 * a2;
-    const double dx4 = mc.dx * mc.dx * mc.dx * mc.dx;
-    double Sp = tot[6], SA = tot[9], SG = tot[7], SM = tot[10] / (mc.e * mc.e);
+    const double a = st->a, b = st->b, bh = st->bh, t = st->t, ahm = st->ahm;
+    const double EKm0 = st->EKm, EKAm0 = st->EKAm, EGm0 = st->EGm, EVm0 = st->EVm, EGAm0 = st->EGAm;
+    const int staggered = st->staggered;
+    const double ia = 1.0 / a, ia2 = ia * ia, ia4 = ia2 * ia2, ia6 = ia4 * ia2;
+    double Sp = tot[6], SA = tot[9], SG = tot[7], SM = tot[10] * mc.inv_e_sq;
     if (ns > U1NS) {
         Sp += 0.5 * tot[13];
         SG += 0.5 * tot[14];
         if (mc.e2 > 0) {
             SA += tot[11];
-            SM += tot[12] / (mc.e2 * mc.e2);
+            SM += tot[12] * mc.inv_e2_sq;
         }
     }
-    const double EKp = Sp / a6, EGp = SG / a2, EV = tot[8];
-    const double EKA = mc.kappa * SA / (2.0 * a4), EGA = mc.kappa * SM / (a4 * dx4);
+    const double hk = 0.5 * mc.kappa;
+    const double EKp = Sp * ia6, EGp = SG * ia2, EV = tot[8];
+    const double EKA = hk * SA * ia4, EGA = mc.kappa * SM * ia4 * mc.inv_dx4;
     st->E[0] = EKp; st->E[1] = EGp; st->E[2] = EV; st->E[3] = EKA; st->E[4] = EGA;
     for (int s = 0; s < ns; ++s) st->sums[s] = tot[s];
     const double Et = EKp + EGp + EV + EKA + EGA;
     if (!isfinite(Et)) { st->error = CL_ERR_NONFINITE; return; }
-    auto rhs = [&](double aa, double E) { return mc.fmp2 / 3.0 * apow(aa, 2.0 * (mc.alpha + 1.0)) * E; };
+    auto rhs = [&](double aa, double E) { return mc.fmp2_3 * apow(aa, 2.0 * (mc.alpha + 1.0)) * E; };
+    auto violation = [&](double bb, double r) { return r > 0 ? fabs(bb * bb - r) / r : 0.0; };
     const int kind = pi.kind;
     if (kind == PK_MEASURE) {
-        if (mc.bg) {
-            st->hc = 0.0;
-        } else if (st->staggered) {
-            const double r = rhs(st->ahm, st->EKm + st->EKAm + 0.5 * (st->EGm + EGp) + 0.5 * (st->EVm + EV) +
-                                              0.5 * (st->EGAm + EGA));
-            st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
-        } else {
-            const double r = rhs(a, Et);
-            st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
-        }
+        if (mc.bg) st->hc = 0.0;
+        else if (staggered)
+            st->hc = violation(b, rhs(ahm, EKm0 + EKAm0 + 0.5 * (EGm0 + EGp) + 0.5 * (EVm0 + EV) + 0.5 * (EGAm0 + EGA)));
+        else st->hc = violation(b, rhs(a, Et));
         return;
     }
     if (kind == PK_INIT_B) {
-        if (mc.bg) st->b = bg_b(mc, st->t);
+        if (mc.bg) st->b = bg_b(mc, t);
         else st->b = mc.fmp2 > 0 ? sqrt(fmax(rhs(a, Et), 0.0)) : 0.0;
         st->hc = 0.0;
         return;
     }
     if (kind == PK_LF_EKM) {
-        st->EKm = Sp / apow(st->ahm, 6.0);
-        st->EKAm = mc.kappa * SA / (2.0 * apow(st->ahm, 4.0));
+        const double ih = 1.0 / ahm, ih2 = ih * ih, ih4 = ih2 * ih2;
+        st->EKm = Sp * ih4 * ih2;
+        st->EKAm = hk * SA * ih4;
         return;
     }
     if (kind == PK_LF_PREPARE) {
-        const double bm = st->b - 0.5 * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
+        const double bm = b - 0.5 * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
         st->b = bm;
         st->ahm = a - 0.5 * pi.dt * bm;
         st->EGm = EGp; st->EVm = EV; st->EGAm = EGA;
@@ -79,18 +87,29 @@ static __device__ void u1_finish(DevState* st, const double* tot, const ModelCon
         st->cdA = 0.0;
         return;
     }
+    // the drift of the next pass (a_{1/2} = ah) and the kick powers at the new a
+    auto advance = [&](double h, double an) {
+        const double ah = 0.5 * (a + an), iah = 1.0 / ah, ian = 1.0 / an;
+        st->cd = h * apow(iah, 3.0 - mc.alpha);
+        st->cdA = mc.e * mc.dx * h * apow2(iah, ah, 1.0 - mc.alpha);
+        st->a = an;
+        st->A1 = apow2(an, ian, 1.0 + mc.alpha);
+        st->A3 = apow2(an, ian, 3.0 + mc.alpha);
+        st->Am = apow2(an, ian, mc.alpha - 1.0);
+        st->t = t + h;
+        return iah;
+    };
     if (kind == PK_VV_FIRST || kind == PK_VV_MID || kind == PK_VV_LAST) {
         // compact velocity-Verlet VVn (sections 5.3.2, 5.3.3): this pass closed
         // the kick of sub-step p-1 (energies E(p-1) of the synchronized momenta)
         // and opened the one of sub-step p; the next pass drifts with a_{1/2}
-        double bsync = st->b;
+        double bsync = b;
         if (mc.bg) {
-            bsync = bg_b(mc, st->t);  // prescribed background (section 4.1)
+            bsync = bg_b(mc, t);  // prescribed background (section 4.1)
             st->hc = 0.0;
         } else {
-            if (kind != PK_VV_FIRST) bsync = st->bh + 0.5 * pi.wc * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
-            const double r = rhs(a, Et);
-            st->hc = r > 0 ? fabs(bsync * bsync - r) / r : 0.0;
+            if (kind != PK_VV_FIRST) bsync = bh + 0.5 * pi.wc * pi.dt * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
+            st->hc = violation(bsync, rhs(a, Et));
         }
         if (kind == PK_VV_LAST) {
             st->b = bsync;
@@ -102,51 +121,36 @@ static __device__ void u1_finish(DevState* st, const double* tot, const ModelCon
         double an;
         if (mc.bg) {
             st->b = bsync;
-            an = bg_a(mc, st->t + h);
+            an = bg_a(mc, t + h);
         } else {
             const double bn = bsync + 0.5 * h * Ka_u1(mc, a, EKp, EGp, EV, EKA, EGA);
             st->bh = bn;
             an = a + h * bn;
         }
-        const double ah = 0.5 * (a + an);
-        st->cd = h * apow(ah, -(3.0 - mc.alpha));
-        st->cdA = mc.e * mc.dx * h * apow(ah, -(1.0 - mc.alpha));
-        st->a = an;
-        st->A1 = apow(an, 1.0 + mc.alpha);
-        st->A3 = apow(an, 3.0 + mc.alpha);
-        st->Am = apow(an, mc.alpha - 1.0);
-        st->t += h;
+        advance(h, an);
         return;
     }
     // PK_LF: b_{+1/2} with the averaged kinetic energies (fixed point in a_{+1/2})
-    if (st->staggered && st->ahm > 0) {
-        const double r = rhs(st->ahm, st->EKm + st->EKAm + 0.5 * (st->EGm + EGp) + 0.5 * (st->EVm + EV) +
-                                          0.5 * (st->EGAm + EGA));
-        st->hc = r > 0 ? fabs(st->b * st->b - r) / r : 0.0;
+    if (staggered && ahm > 0)
+        st->hc = violation(b, rhs(ahm, EKm0 + EKAm0 + 0.5 * (EGm0 + EGp) + 0.5 * (EVm0 + EV) + 0.5 * (EGAm0 + EGA)));
+    double bp = b;
+    if (mc.fmp2 > 0) {  // static background: b stays, no iteration
+        for (int it = 0; it < 100; ++it) {
+            const double ih = 1.0 / (a + 0.5 * pi.dt * bp), ih2 = ih * ih, ih4 = ih2 * ih2;
+            const double ekp = Sp * ih4 * ih2, eka = hk * SA * ih4;
+            const double bn = b + pi.dt * Ka_u1(mc, a, 0.5 * (EKm0 + ekp), EGp, EV, 0.5 * (EKAm0 + eka), EGA);
+            const double d = fabs(bn - bp);
+            bp = bn;
+            if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
+        }
     }
-    double bp = st->b, ekp = 0, eka = 0;
-    for (int it = 0; it < 100; ++it) {
-        const double ah = a + 0.5 * pi.dt * bp;
-        ekp = Sp / apow(ah, 6.0);
-        eka = mc.kappa * SA / (2.0 * apow(ah, 4.0));
-        const double bn = st->b + pi.dt * Ka_u1(mc, a, 0.5 * (st->EKm + ekp), EGp, EV, 0.5 * (st->EKAm + eka), EGA);
-        const double d = fabs(bn - bp);
-        bp = bn;
-        if (d <= 1e-17 * fabs(bn) || d == 0.0) break;
-    }
-    const double an = a + pi.dt * bp, ah = 0.5 * (a + an);
-    st->EKm = Sp / apow(ah, 6.0);
-    st->EKAm = mc.kappa * SA / (2.0 * apow(ah, 4.0));
+    const double an = a + pi.dt * bp;
+    const double iah = advance(pi.dt, an), ih2 = iah * iah, ih4 = ih2 * ih2;
+    st->EKm = Sp * ih4 * ih2;
+    st->EKAm = hk * SA * ih4;
     st->b = bp;
-    st->ahm = ah;
+    st->ahm = 0.5 * (a + an);
     st->EGm = EGp; st->EVm = EV; st->EGAm = EGA;
-    st->cd = pi.dt * apow(ah, -(3.0 - mc.alpha));
-    st->cdA = mc.e * mc.dx * pi.dt * apow(ah, -(1.0 - mc.alpha));
-    st->a = an;
-    st->A1 = apow(an, 1.0 + mc.alpha);
-    st->A3 = apow(an, 3.0 + mc.alpha);
-    st->Am = apow(an, mc.alpha - 1.0);
-    st->t += pi.dt;
 }
 
 

@@ -392,6 +392,11 @@ cl_status cl::lattice_create(const cl_model* model, const cl_grid* grid, const c
     mc.bg_p = mc.bg ? 2.0 / (3.0 * (1.0 + model->fluid_w) - 2.0 * model->alpha) : 1.0;
     mc.bg_H0 = mc.bg ? model->hubble0 : 0.0;
     mc.bg_a0 = L->init.a0;
+    mc.fmp2_3 = mc.fmp2 / 3.0;
+    mc.inv_vol = 1.0 / ((double)N * N * N);
+    mc.inv_e_sq = mc.e > 0 ? 1.0 / (mc.e * mc.e) : 0.0;
+    mc.inv_e2_sq = mc.e2 > 0 ? 1.0 / (mc.e2 * mc.e2) : 0.0;
+    mc.inv_dx4 = mc.idx2 * mc.idx2;
 
     // linear stability of the highest lattice mode
     {

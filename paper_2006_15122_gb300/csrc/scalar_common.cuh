@@ -47,18 +47,21 @@ static __device__ void potential_bar(const ModelConst& mc, const double* fb, dou
 }
 
 static __device__ double Ka_of(const ModelConst& mc, double a, double EK, double EG, double EV) {
-    return mc.fmp2 / 3.0 * apow(a, 1.0 + 2.0 * mc.alpha) *
+    return mc.fmp2_3 * apow(a, 1.0 + 2.0 * mc.alpha) *
            ((mc.alpha - 2.0) * EK + mc.alpha * EG + (mc.alpha + 1.0) * EV);
 }
 
 static __device__ double hubble_rhs(const ModelConst& mc, double a, double Etot) {
-    return mc.fmp2 / 3.0 * apow(a, 2.0 * (mc.alpha + 1.0)) * Etot;
+    return mc.fmp2_3 * apow(a, 2.0 * (mc.alpha + 1.0)) * Etot;
 }
 
+// a^{1+alpha}, a^{3+alpha}, a^{alpha-1}: non-negative powers of a or of 1/a
 static __device__ void set_kick_powers(DevState* st, const ModelConst& mc, double a) {
-    st->A1 = apow(a, 1.0 + mc.alpha);
-    st->A3 = apow(a, 3.0 + mc.alpha);
-    st->Am = apow(a, mc.alpha - 1.0);
+    const double ia = 1.0 / a;
+    auto pw = [&](double e) { return e >= 0.0 ? apow(a, e) : apow(ia, -e); };
+    st->A1 = pw(1.0 + mc.alpha);
+    st->A3 = pw(3.0 + mc.alpha);
+    st->Am = pw(mc.alpha - 1.0);
 }
 
 // Scalar update of the last block (thread 0).  tot[] are sums / N^3.
@@ -69,14 +72,14 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
     double V1, V2, dV[2];
     potential_bar(mc, st->phibar, &V1, &V2, dV);
     double Kbar[2] = {0, 0}, EK[2] = {0, 0}, EG[2] = {0, 0}, S = 0;
-    const double a2 = a * a, a6 = a2 * a2 * a2;
+    const double ia = 1.0 / a, ia2 = ia * ia, ia6 = ia2 * ia2 * ia2;
     for (int f = 0; f < nf; ++f) {
         Kbar[f] = -st->A3 * dV[f];
         const double pr = st->pibar[f] + pi.h1 * Kbar[f];
         const double s2 = pr * pr + 2.0 * pr * tot[6 * f + 2] + tot[6 * f + 3];
         S += s2;
-        EK[f] = s2 / (2.0 * a6);
-        EG[f] = tot[6 * f + 4] * mc.idx2 / (2.0 * a2);
+        EK[f] = 0.5 * s2 * ia6;
+        EG[f] = 0.5 * tot[6 * f + 4] * mc.idx2 * ia2;
     }
     const double EV1 = V1 + tot[6 * nf], EV2 = V2 + tot[6 * nf + 1];
     const double EKt = EK[0] + EK[1], EGt = EG[0] + EG[1], EVt = EV1 + EV2;
@@ -181,8 +184,11 @@ static __device__ void scalar_finish(DevState* st, const double* tot, const Mode
     }
     // prepare the drift of the next pass
     double cd = 0.0, dtn = 0.0;
-    if (kind == PK_VV_FIRST || kind == PK_VV_MID) { cd = pi.wn * pi.dt * apow(ah, -(3.0 - mc.alpha)); dtn = pi.wn * pi.dt; }
-    if (kind == PK_LF) { cd = pi.dt * apow(ah, -(3.0 - mc.alpha)); dtn = pi.dt; }
+    if (kind == PK_VV_FIRST || kind == PK_VV_MID || kind == PK_LF) {
+        dtn = kind == PK_LF ? pi.dt : pi.wn * pi.dt;
+        const double iah = 1.0 / ah, e = 3.0 - mc.alpha;
+        cd = dtn * (e >= 0.0 ? apow(iah, e) : apow(ah, -e));
+    }
     st->cd = cd;
     if (cd != 0.0) {
         for (int f = 0; f < nf; ++f) st->phibar[f] += cd * st->pibar[f];

@@ -351,11 +351,11 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // fixed-order FP64 Kahan sum of the partials: warp w handles sums w, w+nwarps, ...
+    // fixed-order FP64 pairwise sum of the partials: warp w handles sums w, w+nwarps, ...
     __shared__ double tot[kMaxSums];
-    const double invV = 1.0 / ((double)N * N * N);
+    const double invV = A.mc.inv_vol;
     for (int s = warp; s < NS; s += nwarps) {
-        const double r = partial_warp_sum(lane_kahan(A.partials, (int)gridDim.x, NS, s, lane, nlanes), lane, nlanes);
+        const double r = warp_partials_sum(A.partials, (int)gridDim.x, NS, s, lane, nlanes);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();

@@ -441,9 +441,9 @@ __global__ void __launch_bounds__(BX * kSu2TileBY, (sizeof(T) == 4 && !EXT ? 512
     if (!last) return;
     __threadfence();
     __shared__ double tot[NS];
-    const double invV = 1.0 / (double)n3;
+    const double invV = A.mc.inv_vol;
     for (int s = warp; s < NS; s += nwarps) {
-        const double r = partial_warp_sum(lane_kahan(A.partials, (int)gridDim.x, NS, s, lane, 32), lane, 32);
+        const double r = warp_partials_sum(A.partials, (int)gridDim.x, NS, s, lane, 32);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();

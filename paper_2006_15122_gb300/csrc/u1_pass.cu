@@ -247,9 +247,9 @@ __global__ void __launch_bounds__(BX * kU1TileBY, (sizeof(T) == 4 ? 512 : 256) /
     if (!last) return;
     __threadfence();
     __shared__ double tot[U1NS];
-    const double invV = 1.0 / (double)n3;
+    const double invV = A.mc.inv_vol;
     for (int s = warp; s < U1NS; s += nwarps) {
-        const double r = partial_warp_sum(lane_kahan(A.partials, (int)gridDim.x, U1NS, s, lane, nlanes), lane, nlanes);
+        const double r = warp_partials_sum(A.partials, (int)gridDim.x, U1NS, s, lane, nlanes);
         if (lane == 0) tot[s] = r * invV;
     }
     __syncthreads();
