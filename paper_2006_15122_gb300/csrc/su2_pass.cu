@@ -104,15 +104,6 @@ template <typename T> __device__ __forceinline__ T im_dot(const T* x, const T* y
     return x[0] * y[1] - x[1] * y[0] + x[2] * y[3] - x[3] * y[2];
 }
 
-template <typename T> __device__ __forceinline__ void ldq(T* const* a, int i, size_t n, T* q) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) q[c] = __ldg(a[8 + 4 * i + c] + n);
-}
-template <typename T> __device__ __forceinline__ void ldf(T* const* a, size_t n, T* f) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) f[c] = __ldg(a[c] + n);
-}
-
 template <typename T> __device__ __forceinline__ size_t nb(size_t n, int x, int y, int z, int N, int d, int s) {
     const size_t NN = (size_t)N * N;
     if (d == 0) {
