@@ -147,7 +147,7 @@ typedef struct {
 } cl_model;
 
 typedef struct {
-    int32_t N;          /* sites per dimension: multiple of 8, 8 <= N <= 2048 */
+    int32_t N;          /* sites per dimension: multiple of 8, 8 <= N <= 2048 (U(1): N^3 < 2^32) */
     int32_t integrator; /* cl_integrator */
     int32_t precision;  /* cl_precision of the fluctuation arrays */
     int32_t force_dt;   /* nonzero: accept dt beyond the stability bound */
