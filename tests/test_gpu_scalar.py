@@ -142,6 +142,27 @@ def test_fp32_pointwise_parity_100_steps():
     lat.close()
 
 
+def test_fp32_production_tile_matches_oracle():
+    """128^3 two-field lattice on the x-y tile the 1024^3 workload runs (32 x 8
+    threads of 4 sites, a 5-stage ring; shorter z runs): expanding VV4 steps
+    against the oracle within the FP32 pointwise bound."""
+    N = 128
+    lat, ref = make_pair(N, 2, 2, 0.0, fmp=1.4, lam=1.0, q=400.0, integ="vv4", prec=cl.CL_FP32, kIR=0.5, dt=0.005,
+                         seed=21, amp=1e-3, means=[1.0, 0.0])
+    lat.evolve(2)
+    lat.evolve(3)
+    ref.vv_steps(oracle.VV4, 0.005, 5)
+    phi, pi = fields_of(lat, 2)
+    for i in range(2):
+        assert rel(phi[i] - phi[i].mean(), ref.phi[i] - ref.phi[i].mean()) < 1e-5
+        assert rel(pi[i] - pi[i].mean(), ref.pi[i] - ref.pi[i].mean()) < 1e-5
+    mm = lat.measure_means()
+    E = ref.energies()
+    assert abs(mm["a"] - ref.a) < 1e-12
+    assert np.allclose(mm["EK"][:2], E[0:2], rtol=1e-5) and np.allclose(mm["EG"][:2], E[2:4], rtol=1e-5)
+    lat.close()
+
+
 def test_spectrum_matches_oracle():
     N, kIR = 32, 0.4
     lat, ref = make_pair(N, 2, 2, 0.0, fmp=0.0, lam=1.0, q=1.0, integ="vv2", prec=cl.CL_FP64, kIR=kIR)
