@@ -251,19 +251,6 @@ __device__ __forceinline__ void vstore_cs(double* p, const double (&r)[2]) {
     __stcs(reinterpret_cast<double2*>(p), make_double2(r[0], r[1]));
 }
 
-// Kahan-compensated accumulator (Kahan 1965) in the kernel's precision.
-template <typename T> struct Kahan {
-    T s, c;
-    __device__ __forceinline__ void init() { s = T(0); c = T(0); }
-    __device__ __forceinline__ void add(T x) {
-        T y = x - c;
-        T t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return double(s) - double(c); }
-};
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -272,12 +259,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Sum over the nl existing lanes of a possibly partial warp (nl = 1..32);
 // the result is valid in lane 0.  Shuffles name only existing lanes.
-// One warp's sum of partials[b * ns + s] over b < nb: each lane adds its share
-// (b = lane, lane + nl, ...) pairwise, eight loads at a time, then a shuffle
-// tree.  The order is fixed, so every run gives the same bits; the error is that
-// of pairwise summation, O(log2(nb)) ulp.
+// One warp's compensated sum of partials[b * ns + s] over b < nb: lane l takes
+// b = l, l + nl, ... in that order into a Kahan accumulator (Kahan 1965), with
+// the loads issued eight at a time so that their L2 latencies overlap; a
+// shuffle tree then adds the lanes' compensated sums.  The order is fixed, so
+// every run gives the same bits.  (The cost is set by GB300's FP64 throughput:
+// four FP64 operations per partial.)
 __device__ __forceinline__ double warp_partials_sum(const double* partials, int nb, int ns, int s, int lane, int nl) {
-    double acc = 0.0;
+    double ks = 0.0, kc = 0.0;
     for (int b0 = lane; b0 < nb; b0 += 8 * nl) {
         double v[8];
 #pragma unroll
@@ -285,8 +274,16 @@ __device__ __forceinline__ double warp_partials_sum(const double* partials, int 
             const int b = b0 + k * nl;
             v[k] = b < nb ? __ldcg(&partials[(size_t)b * ns + s]) : 0.0;
         }
-        acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (b0 + k * nl < nb) {
+                const double yk = v[k] - kc, tk = ks + yk;
+                kc = (tk - ks) - yk;
+                ks = tk;
+            }
+        }
     }
+    double acc = ks - kc;
     const unsigned mask = nl >= 32 ? 0xffffffffu : ((1u << nl) - 1u);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

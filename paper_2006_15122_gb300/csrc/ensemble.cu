@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, 2) ensemble_pass_kernel(const EnsArgs A) 
 }
 
 
-// Member finish of a pass: fixed-order pairwise sums of the member's per-tile
+// Member finish of a pass: fixed-order compensated sums of the member's per-tile
 // partials (lane l takes tiles l, l+32, ...; fixed order, then a fixed shuffle
 // tree), normalised to volume averages, then the FP64 background update.
 template <typename T>

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // fixed-order FP64 pairwise sum of the partials: warp w handles sums w, w+nwarps, ...
+    // fixed-order compensated FP64 sum of the partials: warp w handles sums w, w+nwarps, ...
     __shared__ double tot[kMaxSums];
     const double invV = A.mc.inv_vol;
     for (int s = warp; s < NS; s += nwarps) {
