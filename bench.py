@@ -181,21 +181,32 @@ class OracleSample:
         return time.perf_counter() - t0
 
 
-def oracle_cores():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-
-
-def cpu_baseline(sample_N=128, budget_s=12.0):
+def cpu_baseline(sample_N=128, budget_s=12.0, single_budget_s=4.0):
     """The oracle timed on a bounded sample: VV4 steps of a sample_N^3 lattice
-    of the same model until about budget_s seconds of CPU work."""
+    of the same model until about budget_s seconds of CPU work on all cores,
+    then single_budget_s seconds on one thread."""
     o = OracleSample(sample_N)
-    steps, spent = 0, 0.0
-    while spent < budget_s:
-        spent += o.step(1)
-        steps += 1
-    return {"value": sample_N ** 3 * steps / spent, "unit": "site-updates/s", "cores": oracle_cores(),
+
+    def timed(budget):
+        steps, spent = 0, 0.0
+        while spent < budget:
+            spent += o.step(1)
+            steps += 1
+        return steps, spent
+
+    steps, spent = timed(budget_s)
+    lib = o.oracle.core.lib()
+    cores = lib.orc_max_threads()
+    lib.orc_set_threads(1)
+    try:
+        steps1, spent1 = timed(single_budget_s)
+    finally:
+        lib.orc_set_threads(cores)
+    return {"value": sample_N ** 3 * steps / spent, "unit": "site-updates/s", "cores": cores,
             "kind": "oracle", "sample": "%d^3 lattice of the same model, %d VV4 steps, FP64, %.1f s"
-                                        % (sample_N, steps, spent)}
+                                        % (sample_N, steps, spent),
+            "single_thread": {"value": sample_N ** 3 * steps1 / spent1, "unit": "site-updates/s", "cores": 1,
+                              "sample": "%d VV4 steps, %.1f s" % (steps1, spent1)}}
 
 
 def run_reference(args):
@@ -215,7 +226,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * N ** 3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"kind": "oracle", "cores": oracle_cores(), "value": v,
+            "cpu_baseline": {"kind": "oracle", "cores": o.oracle.core.lib().orc_max_threads(), "value": v,
                              "sample": "each step: one VV4 step of a %d^3 lattice of the same model" % N},
             "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -46,6 +46,8 @@ def lib():
             ("orc_su2u1_Ka", [vp, C.c_double, d], C.c_double),
             ("orc_su2u1_gauss", [vp, d, d, d, d, d, d], None),
             ("orc_su2u1_vv_step", [vp, C.c_int, d, C.c_double, d, d, d, d, d, d, d, d, d, d], None),
+            ("orc_set_threads", [C.c_int], None),
+            ("orc_max_threads", [], C.c_int),
         ]:
             f = getattr(_lib, name)
             f.argtypes = args

@@ -32,6 +32,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXF 2
 
@@ -1354,4 +1357,21 @@ int orc_scalar_gl_step(const orc_scalar_model* m, int s, const double* A, const 
     *b += db;
     free(D0); free(D1); free(ps); free(qs);
     return it > maxit ? maxit : it;
+}
+
+/* Threads of the OpenMP loops above (the benchmark's CPU leg times the oracle
+ * on one thread and on all cores); without OpenMP both are no-ops on 1. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
