@@ -342,15 +342,16 @@ cl_status lattice_observe(cl_lattice* h, double kmax, float* obs, double* t);
 
 /* Volume-averaged energies and means of caller-owned scalar fields, computed
  * without allocating any device memory.  The paper has no counterpart: this
- * serves callers that cannot allocate -- code running under CUDA stream capture,
- * where cudaMalloc is not allowed, and programs that own all device memory
- * themselves (their own pool, or a loop that must never enter the allocator).
+ * serves callers that cannot call cudaMalloc -- programs that own all device
+ * memory themselves (their own pool has claimed the GPU, or a loop must never
+ * enter the allocator) -- and that hand over their arrays as they are.
  *
  * phi, pi: device arrays of n_fields x N^3 doubles (full fields, field-major,
  * site index (n3*N + n2)*N + n1), the momenta pi = a^{3-alpha} phi'.  out: a
  * device array of 10 doubles receiving {E_K[0], E_K[1], E_G[0], E_G[1],
  * <(lam/p)|phi|^p>, <(q/2)phi^2chi^2>, <phi_0>, <phi_1>, var[0], var[1]} with
- * the definitions of lattice_measure_means.  model->kind must be
+ * the definitions of lattice_measure_means (sums taken about the value at
+ * site 0, so a large mean does not cancel the variance).  model->kind must be
  * CL_MODEL_SCALAR; kIR fixes dx = 2 pi/(kIR N); a is the scale factor.
  * Enqueued on cuda_stream (NULL = legacy default stream); nothing is
  * synchronized.
@@ -362,7 +363,9 @@ cl_status lattice_observe(cl_lattice* h, double kmax, float* obs, double* t);
  * calls share the array and it keeps the last call's contents; the counter is
  * cleared at the start of each call.  Calls that overlap on the GPU race on it.
  * Rejects n_fields > 2, N outside [2, CL_NOALLOC_MAX_N] and NULL pointers with
- * CL_ERR_ARG (reason in cl_last_error(NULL)). */
+ * CL_ERR_ARG (reason in cl_last_error(NULL)).  CL_ERR_CUDA when a CUDA error
+ * from earlier work is pending on the calling thread (it is left pending), or
+ * when the launch fails (reason in cl_last_error(NULL)). */
 #define CL_NOALLOC_MAX_BLOCKS 1024
 #define CL_NOALLOC_MAX_N 2048
 cl_status lattice_energies_noalloc(const cl_model* model, int32_t N, double kIR, double a, const double* phi,

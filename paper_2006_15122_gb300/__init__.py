@@ -209,11 +209,20 @@ def make_init(phi0=(0, 0, 0, 0), dphi0=(0, 0, 0, 0), seed=0, spectrum=1, fluct_s
 
 def energies_noalloc(model, N, kIR, a, phi, pi, out, stream=None):
     """lattice_energies_noalloc on caller-owned device tensors (float64, CUDA):
-    phi, pi of n_fields x N^3, out of 10 doubles; allocates nothing on the device."""
-    for t in (phi, pi, out):
-        p, dev = _dev_ptr(t)
-        if not dev:
-            raise ValueError("phi, pi and out must be CUDA float64 tensors")
+    phi, pi of n_fields x N^3, out of 10 doubles; allocates nothing on the device.
+    Raises ValueError for tensors of the wrong dtype, layout, device or size."""
+    import torch  # only for device buffers
+    need = {"phi": model.n_fields * int(N) ** 3, "pi": model.n_fields * int(N) ** 3, "out": 10}
+    dev0 = None
+    for name, t in (("phi", phi), ("pi", pi), ("out", out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA float64 tensor" % name)
+        if t.numel() < need[name]:
+            raise ValueError("%s holds %d elements, needs %d" % (name, t.numel(), need[name]))
+        if dev0 is None:
+            dev0 = t.device
+        elif t.device != dev0:
+            raise ValueError("phi, pi and out must be on one device")
     _check(load().lattice_energies_noalloc(C.byref(model), int(N), float(kIR), float(a), _dev_ptr(phi)[0],
                                            _dev_ptr(pi)[0], _dev_ptr(out)[0], _stream_ptr(stream)))
 

@@ -46,7 +46,8 @@ struct DevState {
     double gl_Da[2][5], gl_Db[2][5];  // Gauss-Legendre: scalar stage derivatives (two buffers)
     int gl_cur, gl_conv, gl_it;       // latest buffer, converged flag, sweeps of this step
     long long step;
-    int error;          // nonzero: a reduction saw NaN/Inf (evolution stops)
+    int error;          // nonzero: a reduction saw NaN/Inf, or (CL_ERR_TIMEOUT) a Gauss-Legendre
+                        // step did not converge; evolution stops
     int staggered;      // leapfrog momenta live half a step behind the fields
 };
 
@@ -188,7 +189,7 @@ struct Lattice {
     long long steps_done;
     std::string err;
     // graphs cached by (steps, parity)
-    struct G { long long steps; int parity; int end_parity; cudaGraphExec_t exec; };
+    struct G { long long steps; int parity; int part; int end_parity; cudaGraphExec_t exec; };
     std::vector<G> graphs;
     cufftHandle plan_c2r, plan_r2c;
     bool plans;
@@ -291,6 +292,49 @@ __device__ __forceinline__ double warp_partials_sum(const double* partials, int 
         if (lane + o < nl) acc += t;
     }
     return acc;
+}
+
+// Adds the per-thread sums ts[0..NS-1] of a warp into the warp's FP64
+// accumulators acc[0..NS-1] and clears ts.  Full warps use a butterfly whose
+// every exchange halves the values a lane carries (16 -> 8 -> 4 -> 2 -> 1;
+// 16 shuffles in all instead of 5 per sum); lane 2s then holds the warp total
+// of sum s = lane/2.  The order of additions is fixed, so results repeat bit
+// for bit.  Partial warps take one shuffle tree per sum.
+template <typename T, int NS>
+__device__ __forceinline__ void fold_warp_sums(T (&ts)[NS], double* acc, int lane, int nlanes) {
+    static_assert(NS <= 16, "at most 16 sums per fold");
+    if (nlanes == 32) {
+        // in place on ts; entries at and beyond NS count as zero
+#pragma unroll
+        for (int w = 8, o = 16; w >= 1; w >>= 1, o >>= 1) {
+            const bool hi = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < w; ++j) {
+                if (j >= NS) continue;
+                const T lo_v = ts[j], hi_v = (j + w < NS) ? ts[j + w] : T(0);
+                const T send = hi ? lo_v : hi_v;
+                const T keep = hi ? hi_v : lo_v;
+                ts[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        ts[0] += __shfl_xor_sync(0xffffffffu, ts[0], 1);
+        const int s = lane >> 1;
+        if ((lane & 1) == 0 && s < NS) acc[s] += double(ts[0]);
+    } else {
+        const unsigned mask = (1u << nlanes) - 1u;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            T v = ts[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T t = __shfl_down_sync(mask, v, o);
+                if (lane + o < nlanes) v += t;
+            }
+            if (lane == 0) acc[i] += double(v);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) ts[i] = T(0);
 }
 
 template <typename T> __device__ __forceinline__ T partial_warp_sum(T v, int lane, int nl) {

@@ -170,10 +170,11 @@ __global__ void __launch_bounds__(256) gl_sweep_kernel(const GlArgs G) {
     if (dd <= G.tol * G.tol * nn) st->gl_conv = 1;
 }
 
-// y(n0 + 1) = y(n0) + dt sum_m c_m D^(m) from the latest buffer (pointwise)
+// y(n0 + 1) = y(n0) + dt sum_m c_m D^(m) from the latest buffer (pointwise);
+// a step whose stage sweeps did not converge is not applied
 __global__ void gl_final_kernel(const GlArgs G, int nf) {
     const DevState* st = G.st;
-    if (st->error) return;
+    if (st->error || !st->gl_conv) return;
     const int b = st->gl_cur;
     const size_t n3 = (size_t)G.mc.N * G.mc.N * G.mc.N;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
@@ -194,10 +195,16 @@ __global__ void gl_begin_kernel(DevState* st) {
     st->gl_it = 0;
 }
 
-// end of a step: the scalars with the final weights
+// end of a step: the scalars with the final weights.  Without convergence of
+// the stage equations the step is refused: the error flag stops the lattice at
+// the last completed step and the host reports CL_ERR_TIMEOUT.
 __global__ void gl_end_kernel(DevState* st, ModelConst mc, int s, double dt, double c0, double c1, double c2,
                               double c3, double c4) {
     if (st->error) return;
+    if (!st->gl_conv) {
+        st->error = CL_ERR_TIMEOUT;
+        return;
+    }
     const double c[kGlMaxS] = {c0, c1, c2, c3, c4};
     const int b = st->gl_cur;
     double a = st->rk[0], bb = st->rk[1];

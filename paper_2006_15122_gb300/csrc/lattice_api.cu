@@ -113,31 +113,54 @@ cl::PassInfo make_pass(int kind, double dt, double wc, double wn, double h1, dou
     return p;
 }
 
+// Parts of one evolve call that is recorded as several graphs: the passes of
+// a long call are one sequence, cut into graphs of at most 64 steps without
+// synchronizing the state at the cuts (no extra pass per graph).
+enum GraphPart : int {
+    GP_WHOLE = 0,  // the whole call: opening kick ... closing kick (or closing drift)
+    GP_HEAD = 1,   // opens the call, ends inside it
+    GP_BODY = 2,   // starts and ends inside the call
+    GP_TAIL = 3    // starts inside the call and closes it
+};
+
 // Enqueue m steps starting from copy `cur`; returns the copy holding the result.
-cudaError_t enqueue_steps(cl::Lattice* L, long long m, int* cur, cudaStream_t s) {
+// `part` selects whether this piece opens (GP_WHOLE, GP_HEAD) and closes
+// (GP_WHOLE, GP_TAIL) the evolve call; RK4 and Gauss-Legendre steps are
+// self-contained and take every piece as whole.
+cudaError_t enqueue_steps(cl::Lattice* L, long long m, int* cur, cudaStream_t s, int part) {
     const double dt = L->grid.dt;
     if (L->integ == CL_INT_RK4) return cl::rk4_enqueue(L, m, *cur, s);  // the state stays in copy `cur`
     if (L->integ >= CL_INT_GL2) return cl::gl_enqueue(L, m, *cur, s);
+    const bool opens = part == GP_WHOLE || part == GP_HEAD, closes = part == GP_WHOLE || part == GP_TAIL;
     if (L->integ == CL_INT_LF) {
         for (long long j = 0; j < m; ++j) {
             cudaError_t e = launch_pass(L, *cur, 1 - *cur, make_pass(cl::PK_LF, dt, 0, 0, dt, dt), true, s);
             if (e != cudaSuccess) return e;
             *cur ^= 1;
         }
-        return launch_drift(L, *cur, s);
+        return closes ? launch_drift(L, *cur, s) : cudaSuccess;
     }
+    // VVn: global pass j of the call (j = 0 the opening kick, j = 1.. merged
+    // kicks with wc = w[(j-1) mod S], wn = w[j mod S]); a piece that does not
+    // open the call starts at a merged kick whose wc is the last weight.
     const std::vector<double>& w = L->weights;
     const long long S = (long long)w.size(), P = m * S;
-    cudaError_t e = launch_pass(L, *cur, 1 - *cur, make_pass(cl::PK_VV_FIRST, dt, 0, w[0], 0, 0.5 * w[0] * dt), true, s);
-    if (e != cudaSuccess) return e;
-    *cur ^= 1;
-    for (long long j = 1; j < P; ++j) {
-        const double wc = w[(j - 1) % S], wn = w[j % S];
+    cudaError_t e = cudaSuccess;
+    long long j0 = 0;
+    if (opens) {
+        e = launch_pass(L, *cur, 1 - *cur, make_pass(cl::PK_VV_FIRST, dt, 0, w[0], 0, 0.5 * w[0] * dt), true, s);
+        if (e != cudaSuccess) return e;
+        *cur ^= 1;
+        j0 = 1;
+    }
+    for (long long j = j0; j < P; ++j) {
+        const double wc = w[(j + S - 1) % S], wn = w[j % S];
         e = launch_pass(L, *cur, 1 - *cur, make_pass(cl::PK_VV_MID, dt, wc, wn, 0.5 * wc * dt, 0.5 * (wc + wn) * dt), true, s);
         if (e != cudaSuccess) return e;
         *cur ^= 1;
     }
-    const double wc = w[(P - 1) % S];
+    if (!closes) return cudaSuccess;
+    const double wc = w[S - 1];
     e = launch_pass(L, *cur, 1 - *cur, make_pass(cl::PK_VV_LAST, dt, wc, 0, 0.5 * wc * dt, 0.5 * wc * dt), true, s);
     if (e != cudaSuccess) return e;
     *cur ^= 1;
@@ -156,14 +179,14 @@ cl_status ensure_staggered(cl::Lattice* L) {
     return CL_OK;
 }
 
-cudaGraphExec_t get_graph(cl::Lattice* L, long long m, int parity, cudaError_t* err) {
+cudaGraphExec_t get_graph(cl::Lattice* L, long long m, int parity, int part, cudaError_t* err) {
     for (auto& g : L->graphs)
-        if (g.steps == m && g.parity == parity) return g.exec;
+        if (g.steps == m && g.parity == parity && g.part == part) return g.exec;
     int cur = parity;
     cudaGraph_t graph;
     *err = cudaStreamBeginCapture(L->cstream, cudaStreamCaptureModeThreadLocal);
     if (*err != cudaSuccess) return nullptr;
-    cudaError_t e = enqueue_steps(L, m, &cur, L->cstream);
+    cudaError_t e = enqueue_steps(L, m, &cur, L->cstream, part);
     cudaError_t e2 = cudaStreamEndCapture(L->cstream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         *err = e != cudaSuccess ? e : e2;
@@ -176,15 +199,16 @@ cudaGraphExec_t get_graph(cl::Lattice* L, long long m, int parity, cudaError_t* 
     cl::Lattice::G g;
     g.steps = m;
     g.parity = parity;
+    g.part = part;
     g.exec = exec;
     g.end_parity = cur;
     L->graphs.push_back(g);
     return exec;
 }
 
-int graph_end_parity(cl::Lattice* L, long long m, int parity) {
+int graph_end_parity(cl::Lattice* L, long long m, int parity, int part) {
     for (auto& g : L->graphs)
-        if (g.steps == m && g.parity == parity) return g.end_parity;
+        if (g.steps == m && g.parity == parity && g.part == part) return g.end_parity;
     return parity;
 }
 
@@ -525,17 +549,23 @@ cl_status lattice_evolve(cl_lattice* h, int64_t nsteps) {
     if (nsteps == 0) return CL_OK;
     cl_status s = ensure_staggered(h);
     if (s != CL_OK) return s;
+    // Graphs of at most 64 steps; the pieces of one call continue each other's
+    // pass sequence, so a call of n velocity-Verlet steps runs n*s + 1 passes.
     const long long chunk = 64;
     long long left = nsteps;
+    bool first = true;
     while (left > 0) {
         const long long m = left < chunk ? left : chunk;
+        const bool last = m == left;
+        const int part = first ? (last ? GP_WHOLE : GP_HEAD) : (last ? GP_TAIL : GP_BODY);
         cudaError_t e = cudaSuccess;
-        cudaGraphExec_t g = get_graph(h, m, h->cur, &e);
+        cudaGraphExec_t g = get_graph(h, m, h->cur, part, &e);
         if (!g) return cuda_fail(h, e, "recording the evolve graph");
         e = cudaGraphLaunch(g, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "launching the evolve graph");
-        h->cur = graph_end_parity(h, m, h->cur);
+        h->cur = graph_end_parity(h, m, h->cur, part);
         left -= m;
+        first = false;
     }
     h->steps_done += nsteps;
     return CL_OK;
@@ -545,6 +575,10 @@ static cl_status read_state(cl_lattice* h, cl::DevState* st) {
     cudaError_t e = cudaMemcpyAsync(st, h->buf.st, sizeof(*st), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reading the device state");
+    if (st->error == CL_ERR_TIMEOUT)
+        return fail(h, CL_ERR_TIMEOUT,
+                    "the Gauss-Legendre stage equations did not converge within 60 sweeps; the lattice stopped at "
+                    "the last completed step");
     if (st->error) return fail(h, CL_ERR_NONFINITE, "a reduction produced a non-finite value; the lattice stopped");
     return CL_OK;
 }

@@ -1,10 +1,10 @@
 // lattice_energies_noalloc: volume-averaged energies and means of scalar fields
 // that the caller owns, computed without any device allocation.
 //
-// Some callers cannot allocate device memory: code that runs inside CUDA stream
-// capture (where cudaMalloc is not allowed), or host programs that manage every
-// byte of the GPU themselves (a simulation code with its own memory pool, a
-// real-time loop that must never enter the allocator).  This entry point takes
+// Some callers cannot allocate device memory: host programs that manage every
+// byte of the GPU themselves (a simulation code with its own memory pool that has
+// already claimed the device, a real-time loop that must never enter the
+// allocator, a plug-in whose host owns the device).  This entry point takes
 // their device arrays as they are and keeps its only scratch -- per-block partial
 // sums and a completion counter -- in a fixed file-scope device array, so a call
 // needs no cudaMalloc, cudaFree or allocating library routine.
@@ -15,6 +15,7 @@
 // at the start of every call.  Two calls that overlap on the GPU (different streams,
 // or different host threads on one device) race on it.
 #include <math.h>
+#include <stdio.h>
 
 #include <mutex>
 
@@ -46,9 +47,12 @@ struct NoAllocArgs {
     double lam, q, idx2, a;
 };
 
-// One thread per site (grid-stride): sums of phi, phi^2, pi^2, (D^+ phi)^2 per field
-// and of the two potential terms; the last block to finish reduces the partials in a
-// fixed order and writes E_K, E_G, E_V, means and variances (section 4.4.1).
+// One thread per site (grid-stride): sums of phi - r, (phi - r)^2, pi^2, (D^+ phi)^2
+// per field and of the two potential terms; the last block to finish reduces the
+// partials in a fixed order and writes E_K, E_G, E_V, means and variances (section
+// 4.4.1).  The shift r is the field's value at site 0: a field that is a large
+// homogeneous value plus small fluctuations then keeps the digits of its variance,
+// which <phi^2> - <phi>^2 of the full field would cancel away.
 __global__ void energies_noalloc_kernel(const NoAllocArgs A) {
     const int N = A.N;
     const size_t n3 = (size_t)N * N * N;
@@ -64,11 +68,11 @@ __global__ void energies_noalloc_kernel(const NoAllocArgs A) {
         for (int c = 0; c < A.nf; ++c) {
             const double* F = A.phi + (size_t)c * n3;
             const double* P = A.pi + (size_t)c * n3;
-            const double v = F[i], p = P[i];
+            const double v = F[i], p = P[i], d = v - __ldg(F);
             const double gx = F[ix] - v, gy = F[iy] - v, gz = F[iz] - v;
             f[c] = v;
-            s[4 * c + 0] += v;
-            s[4 * c + 1] += v * v;
+            s[4 * c + 0] += d;
+            s[4 * c + 1] += d * d;
             s[4 * c + 2] += p * p;
             s[4 * c + 3] += gx * gx + gy * gy + gz * gz;
         }
@@ -113,9 +117,10 @@ __global__ void energies_noalloc_kernel(const NoAllocArgs A) {
         const double a2 = A.a * A.a, a6 = a2 * a2 * a2;
         for (int c = 0; c < 2; ++c) {
             const bool on = c < A.nf;
+            const double r = on ? A.phi[(size_t)c * n3] : 0.0;  // the shift of the sums
             A.out[c] = on ? tot[4 * c + 2] / (2.0 * a6) : 0.0;                 // E_K
             A.out[2 + c] = on ? tot[4 * c + 3] * A.idx2 / (2.0 * a2) : 0.0;    // E_G
-            A.out[6 + c] = on ? tot[4 * c + 0] : 0.0;                          // <phi>
+            A.out[6 + c] = on ? r + tot[4 * c + 0] : 0.0;                      // <phi>
             A.out[8 + c] = on ? tot[4 * c + 1] - tot[4 * c + 0] * tot[4 * c + 0] : 0.0;  // variance
         }
         A.out[4] = tot[8];  // <(lam/p)|phi|^p>
@@ -129,6 +134,15 @@ __global__ void energies_noalloc_kernel(const NoAllocArgs A) {
 namespace cl {
 void set_global_error(const char* msg);
 }
+
+namespace {
+cl_status cuda_error(const char* where, cudaError_t e) {
+    char msg[256];
+    snprintf(msg, sizeof(msg), "lattice_energies_noalloc: %s: %s", where, cudaGetErrorString(e));
+    cl::set_global_error(msg);
+    return CL_ERR_CUDA;
+}
+}  // namespace
 
 extern "C" cl_status lattice_energies_noalloc(const cl_model* model, int32_t N, double kIR, double a,
                                               const double* phi, const double* pi, double* out, void* cuda_stream) {
@@ -171,7 +185,13 @@ extern "C" cl_status lattice_energies_noalloc(const cl_model* model, int32_t N, 
     const long long need = (long long)((n3 + 255) / 256);
     if (grid > need) grid = need;
     if (grid > CL_NOALLOC_MAX_BLOCKS) grid = CL_NOALLOC_MAX_BLOCKS;
-    if (cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned int), s) != cudaSuccess) return CL_ERR_CUDA;
+    // A launch error is read with cudaGetLastError, which also returns (and clears)
+    // an error left pending by earlier, unrelated work on this thread; refuse to
+    // start while one is pending, so that the status below is this call's own.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_error("a CUDA error from earlier work is pending", e);
+    e = cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_error("clearing the scratch counter", e);
     NoAllocArgs A;
     A.phi = phi;
     A.pi = pi;
@@ -186,5 +206,6 @@ extern "C" cl_status lattice_energies_noalloc(const cl_model* model, int32_t N, 
     A.idx2 = 1.0 / (dx * dx);
     A.a = a;
     energies_noalloc_kernel<<<(unsigned)grid, 256, 0, s>>>(A);
-    return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CL_OK : cuda_error("launching the energies kernel", e);
 }

@@ -134,3 +134,25 @@ def test_surrogate_null_arguments_are_rejected():
     assert lib.surrogate_predict(None, None, 1, None) == cl.CL_ERR_ARG
     assert lib.surrogate_loss_grad(None, None, None, 1, None, None) == cl.CL_ERR_ARG
     assert lib.surrogate_destroy(None) == cl.CL_OK
+
+
+def test_noalloc_binding_rejects_host_tensors_and_wrong_dtypes():
+    """energies_noalloc refuses, before any CUDA call, buffers that are not
+    contiguous CUDA float64 tensors (the C side would read them as device memory)."""
+    torch = pytest.importorskip("torch")
+    model = cl.make_model(n_fields=1)
+    t = torch.zeros(64, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        cl.energies_noalloc(model, 4, 0.5, 1.0, t, t, torch.zeros(10, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        cl.energies_noalloc(model, 4, 0.5, 1.0, t.float(), t.float(), t.float())
+
+
+def test_noalloc_rejects_bad_arguments_on_the_host():
+    lib = cl.load()
+    m = cl.make_model(n_fields=3)
+    assert lib.lattice_energies_noalloc(C.byref(m), 8, 0.5, 1.0, None, None, None, None) == cl.CL_ERR_ARG
+    assert b"non-NULL" in lib.cl_last_error(None)
+    dummy = C.c_void_p(16)  # never dereferenced: the model is rejected first
+    assert lib.lattice_energies_noalloc(C.byref(m), 8, 0.5, 1.0, dummy, dummy, dummy, None) == cl.CL_ERR_ARG
+    assert b"1 or 2 fields" in lib.cl_last_error(None)

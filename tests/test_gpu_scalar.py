@@ -20,7 +20,7 @@ from tests import inputs
 
 pytestmark = pytest.mark.gpu
 
-WEIGHTS = {"vv2": oracle.VV2, "vv4": oracle.VV4, "vv6": oracle.VV6}
+WEIGHTS = {"vv2": oracle.VV2, "vv4": oracle.VV4, "vv6": oracle.VV6, "vv8": oracle.VV8, "vv10": oracle.VV10}
 
 
 def rel(x, y):
@@ -52,7 +52,8 @@ def fields_of(lat, Ns):
 
 
 @pytest.mark.parametrize("N,Ns,pexp,alpha,integ", [
-    (24, 1, 4, 1.0, "vv2"), (40, 2, 2, 0.0, "vv4"), (64, 2, 4, 0.5, "vv4"), (32, 1, 6, 1.5, "vv6")])
+    (24, 1, 4, 1.0, "vv2"), (40, 2, 2, 0.0, "vv4"), (64, 2, 4, 0.5, "vv4"), (32, 1, 6, 1.5, "vv6"),
+    (32, 2, 2, 0.5, "vv8"), (40, 2, 4, 1.0, "vv10")])
 def test_fp64_single_step_matches_oracle(N, Ns, pexp, alpha, integ):
     lat, ref = make_pair(N, Ns, pexp, alpha, fmp=1.2, lam=1.0, q=3.0, integ=integ, prec=cl.CL_FP64,
                          means=[0.9, 0.1][:Ns])
@@ -64,6 +65,45 @@ def test_fp64_single_step_matches_oracle(N, Ns, pexp, alpha, integ):
         assert rel(pi[i], ref.pi[i]) < 1e-12
     mm = lat.measure_means()
     assert abs(mm["a"] - ref.a) < 1e-14 * ref.a and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
+    lat.close()
+
+
+@pytest.mark.parametrize("integ", ["vv8", "vv10"])
+def test_fp64_vv8_vv10_several_steps_match_oracle(integ):
+    """The VV8 and VV10 weights of the library (appendix table) against the
+    oracle's own copy: 5 expanding steps of the two-field model in two calls."""
+    lat, ref = make_pair(32, 2, 2, 0.0, fmp=1.0, lam=1.0, q=5.0, integ=integ, prec=cl.CL_FP64, means=[1.0, 0.0])
+    lat.evolve(2)
+    lat.evolve(3)
+    ref.vv_steps(WEIGHTS[integ], 0.01, 5)
+    phi, pi = fields_of(lat, 2)
+    for i in range(2):
+        assert rel(phi[i], ref.phi[i]) < 1e-12
+        assert rel(pi[i], ref.pi[i]) < 1e-12
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-14 * ref.a and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
+    lat.close()
+
+
+@pytest.mark.parametrize("integ", ["vv4", "lf"])
+def test_fp64_long_call_crosses_graph_pieces(integ):
+    """One evolve call of 150 steps runs as three recorded graphs (64 + 64 + 22
+    steps) that continue one pass sequence: it must equal the oracle's 150 steps
+    (velocity-Verlet: 3 x 150 + 1 passes; leapfrog: one closing drift)."""
+    N, dt, steps = 16, 0.01, 150
+    lat, ref = make_pair(N, 2, 2, 0.0, fmp=1.0, lam=1.0, q=5.0, integ=integ, prec=cl.CL_FP64, means=[1.0, 0.0])
+    lat.evolve(steps)
+    if integ == "lf":
+        ref.lf3_prepare(dt)
+        ref.lf3_steps(dt, steps)
+    else:
+        ref.vv_steps(oracle.VV4, dt, steps)
+    phi, pi = fields_of(lat, 2)
+    for i in range(2):
+        assert rel(phi[i], ref.phi[i]) < 1e-11
+        assert rel(pi[i], ref.pi[i]) < 1e-11
+    mm = lat.measure_means()
+    assert abs(mm["a"] - ref.a) < 1e-13 * ref.a and abs(mm["t"] - steps * dt) < 1e-12
     lat.close()
 
 
@@ -144,21 +184,21 @@ def test_fp32_pointwise_parity_100_steps():
 
 def test_fp32_production_tile_matches_oracle():
     """128^3 two-field lattice on the x-y tile the 1024^3 workload runs (32 x 8
-    threads of 4 sites, a 5-stage ring; shorter z runs): expanding VV4 steps
+    threads of 4 sites, a 5-stage ring; shorter z runs): 100 expanding VV4 steps
     against the oracle within the FP32 pointwise bound."""
     N = 128
     lat, ref = make_pair(N, 2, 2, 0.0, fmp=1.4, lam=1.0, q=400.0, integ="vv4", prec=cl.CL_FP32, kIR=0.5, dt=0.005,
                          seed=21, amp=1e-3, means=[1.0, 0.0])
-    lat.evolve(2)
-    lat.evolve(3)
-    ref.vv_steps(oracle.VV4, 0.005, 5)
+    lat.evolve(30)
+    lat.evolve(70)
+    ref.vv_steps(oracle.VV4, 0.005, 100)
     phi, pi = fields_of(lat, 2)
     for i in range(2):
         assert rel(phi[i] - phi[i].mean(), ref.phi[i] - ref.phi[i].mean()) < 1e-5
         assert rel(pi[i] - pi[i].mean(), ref.pi[i] - ref.pi[i].mean()) < 1e-5
     mm = lat.measure_means()
     E = ref.energies()
-    assert abs(mm["a"] - ref.a) < 1e-12
+    assert abs(mm["a"] - ref.a) < 1e-9  # a follows the FP32 energies through K_a
     assert np.allclose(mm["EK"][:2], E[0:2], rtol=1e-5) and np.allclose(mm["EG"][:2], E[2:4], rtol=1e-5)
     lat.close()
 
@@ -332,6 +372,24 @@ def test_gauss_legendre_matches_oracle(s, N):
     mm = lat.measure_means()
     assert abs(mm["a"] - ref.a) < 1e-13 and abs(mm["b"] - ref.b) < 1e-12 * abs(ref.b)
     assert abs(mm["t"] - 3 * dt) < 1e-13
+    lat.close()
+
+
+def test_gauss_legendre_reports_stage_equations_that_do_not_converge():
+    """A time step beyond the bound that keeps the stage sweeps contracting
+    (forced past the init check): the step is not applied, the lattice stops and
+    the next synchronizing call reports CL_ERR_TIMEOUT instead of a silent result."""
+    N, kIR, dt = 16, 0.5, 0.8  # omega_max dt ~ 3.6, sweep growth ~ 1.4 per sweep on GL2
+    model = cl.make_model(n_fields=1, pexp=2, alpha=0.0, lam=1.0, omega_over_fstar=0.05, fstar_over_mp=0.0)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, "gl2", cl.CL_FP64, force_dt=True), cl.make_init(phi0=(1.0,)))
+    phi = inputs.fields(1, N, seed=93, amp=0.05, means=[1.0])
+    lat.set_field(cl.FIELD(0), phi[0])
+    lat.set_background(1.0, 0.0, 0.0)
+    lat.evolve(2)
+    with pytest.raises(cl.LatticeError) as e:
+        lat.measure_means()
+    assert e.value.status == cl.CL_ERR_TIMEOUT and "did not converge" in str(e.value)
+    assert np.max(np.abs(lat.get_field(cl.FIELD(0)) - phi[0])) < 1e-14  # nothing applied
     lat.close()
 
 

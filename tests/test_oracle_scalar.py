@@ -257,6 +257,23 @@ def test_yoshida_weights():
     assert 1e-8 < abs(printed["w2"] - w[1]) < 1e-7
 
 
+@pytest.mark.parametrize("weights,order", [(oracle.VV4, 4), (oracle.VV6, 6), (oracle.VV8, 8), (oracle.VV10, 10)])
+def test_yoshida_compositions_reach_their_order(weights, order):
+    """One step of the composed velocity-Verlet map of the harmonic oscillator
+    x'' = -x differs from the exact rotation by O(h^(order+1)) (section 4.3.2):
+    halving h divides the local error by 2^(order+1).  A mistyped, dropped or
+    swapped weight of the appendix table lowers the order."""
+    errs = []
+    for h in (0.4, 0.2):
+        M = np.eye(2)
+        for w in weights:
+            M = _vv_map(w * h, np.float64(1.0)) @ M
+        exact = np.array([[np.cos(h), np.sin(h)], [-np.sin(h), np.cos(h)]])
+        errs.append(np.max(np.abs(M - exact)))
+    slope = np.log2(errs[0] / errs[1])
+    assert abs(slope - (order + 1)) < 0.3, (errs, slope)
+
+
 def test_fluid_background_massless_modes_match_closed_form():
     """Radiation fluid (w = 1/3) in conformal time (alpha = 1): p = 1 and
     a = a0 (1 + H0 eta) has a'' = 0, so for a free massless field u = a phi_k
