@@ -269,6 +269,20 @@ cl_status lattice_get_field(cl_lattice* h, int32_t which, double* dst, int32_t o
  * handle splits it into its mean and fluctuation.  Ordered on the stream. */
 cl_status lattice_set_field(cl_lattice* h, int32_t which, const double* src, int32_t on_device);
 
+/* The stored representation of array `which`, in the handle's precision:
+ * N^3 elements (float for CL_FP32, double for CL_FP64) and the FP64
+ * homogeneous value they fluctuate about, field = *mean + array (section 4.4's
+ * volume average as the mean; the models without a mean split, U(1) and SU(2),
+ * have mean 0 and their full arrays).  An FP32 lattice thus crosses the ABI in
+ * half the bytes of lattice_get_field, with nothing lost: mean + array is, in
+ * FP64, exactly the value lattice_get_field returns, and setting it back
+ * reproduces those field values bit for bit.  dst / src are host memory
+ * (on_device = 0) or device memory of the handle's device; both calls
+ * synchronize the stream.  set rejects a non-finite mean, and a non-zero mean
+ * for an array without a homogeneous part (CL_ERR_ARG). */
+cl_status lattice_get_stored(cl_lattice* h, int32_t which, void* dst, double* mean, int32_t on_device);
+cl_status lattice_set_stored(cl_lattice* h, int32_t which, const void* src, double mean, int32_t on_device);
+
 /* Set the background: scale factor a and b = a' at program time t.  A NaN b
  * is replaced by the positive root of the Hubble constraint of the current
  * fields.  Under CL_BG_FLUID a and b are ignored and follow t.  Marks the

@@ -88,6 +88,7 @@ class cl_train_cfg(C.Structure):
 
 SYMBOLS = ["cl_status_str", "cl_last_error", "lattice_init", "lattice_evolve", "lattice_measure_means",
            "lattice_spectrum_bins", "lattice_measure_spectrum", "lattice_measure_gauge_spectrum", "lattice_get_field", "lattice_set_field",
+           "lattice_get_stored", "lattice_set_stored",
            "lattice_set_background", "lattice_save", "lattice_restore", "lattice_destroy",
            "lattice_energies_noalloc", "ensemble_init", "ensemble_evolve", "ensemble_observe",
            "ensemble_member", "ensemble_destroy", "ensemble_get_tile", "ensemble_set_tile",
@@ -127,6 +128,8 @@ def load(build_if_missing=True):
         "lattice_measure_gauge_spectrum": ([vp, i32, i32, pd, pd, C.POINTER(C.c_int64)], C.c_int),
         "lattice_get_field": ([vp, i32, vp, i32], C.c_int),
         "lattice_set_field": ([vp, i32, vp, i32], C.c_int),
+        "lattice_get_stored": ([vp, i32, vp, pd, i32], C.c_int),
+        "lattice_set_stored": ([vp, i32, vp, d, i32], C.c_int),
         "lattice_set_background": ([vp, d, d, d], C.c_int),
         "lattice_save": ([vp, C.c_char_p], C.c_int),
         "lattice_restore": ([vp, C.c_char_p], C.c_int),
@@ -304,6 +307,32 @@ class Lattice:
             src = np.ascontiguousarray(src, dtype=np.float64)
         p, dev = _dev_ptr(src)
         _check(load().lattice_set_field(self.h, which, p, dev), self.h)
+
+    def _stored_ptr(self, t):
+        """(pointer, on_device) of a buffer in the handle's precision."""
+        want = np.float32 if self.grid.precision == CL_FP32 else np.float64
+        if isinstance(t, np.ndarray):
+            if t.dtype != want or not t.flags.c_contiguous or t.size != self.N ** 3:
+                raise ValueError("expected a contiguous %s array of N^3 elements" % np.dtype(want).name)
+            return C.c_void_p(t.ctypes.data), 0
+        import torch  # only for device or pinned buffers
+        tw = torch.float32 if want == np.float32 else torch.float64
+        if t.dtype != tw or not t.is_contiguous() or t.numel() != self.N ** 3:
+            raise ValueError("expected a contiguous %s tensor of N^3 elements" % tw)
+        return C.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0
+
+    def get_stored(self, which, out=None):
+        """The stored array (handle precision) and its FP64 mean: field = mean + array."""
+        if out is None:
+            out = np.zeros((self.N,) * 3, dtype=np.float32 if self.grid.precision == CL_FP32 else np.float64)
+        p, dev = self._stored_ptr(out)
+        mean = C.c_double(0.0)
+        _check(load().lattice_get_stored(self.h, which, p, C.byref(mean), dev), self.h)
+        return out, mean.value
+
+    def set_stored(self, which, src, mean):
+        p, dev = self._stored_ptr(src)
+        _check(load().lattice_set_stored(self.h, which, p, float(mean), dev), self.h)
 
     def set_background(self, a, b=math.nan, t=0.0):
         _check(load().lattice_set_background(self.h, a, b, t), self.h)

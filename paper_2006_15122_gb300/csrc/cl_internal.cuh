@@ -450,6 +450,9 @@ cudaError_t launch_finish_drift(Lattice* L, cudaStream_t s);
 // fields.cu
 cudaError_t launch_get_field(Lattice* L, int which, double* dst, cudaStream_t s);
 cudaError_t launch_set_field(Lattice* L, int which, const double* src, cudaStream_t s);
+cudaError_t launch_get_stored(Lattice* L, int slot, void* dst, double* mean_dev, cudaStream_t s);
+cudaError_t launch_set_stored_mean(Lattice* L, int slot, double mean, cudaStream_t s);
+int has_mean(const ModelConst& mc, int slot);
 cudaError_t launch_spectrum(Lattice* L, int slot, int accumulate, cudaStream_t s);
 // Gauge-field spectra: sector 0 U(1), 1 SU(2); what 0 electric momenta, 1 magnetic
 // field; accumulates every component into L->bins and returns their number.

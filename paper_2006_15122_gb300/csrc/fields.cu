@@ -119,6 +119,57 @@ cudaError_t launch_set_field(Lattice* L, int slot, const double* src, cudaStream
     return cudaGetLastError();
 }
 
+// The stored representation: array = stored - shift (in T, as the passes apply
+// it), mean = the FP64 homogeneous value; field = mean + array.
+template <typename T>
+__global__ void get_stored_kernel(const T* src, T* dst, size_t n, const DevState* st, int kind, int comp) {
+    T shift = T(0);
+    if (kind == 1) shift = T(st->sphi[comp]);
+    if (kind == 2) shift = T(st->spi[comp]);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] - shift;
+}
+
+__global__ void read_mean_kernel(const DevState* st, int kind, int comp, double* out) {
+    *out = kind == 1 ? st->phibar[comp] : kind == 2 ? st->pibar[comp] : 0.0;
+}
+
+__global__ void write_mean_kernel(DevState* st, int kind, int comp, double mean) {
+    if (kind == 1) { st->phibar[comp] = mean; st->sphi[comp] = 0.0; }
+    if (kind == 2) { st->pibar[comp] = mean; st->spi[comp] = 0.0; }
+}
+
+// Stored array of `slot` (pending shift applied) into dst, a device buffer of
+// N^3 elements of the handle's precision; its mean into *mean_dev (device).
+cudaError_t launch_get_stored(Lattice* L, int slot, void* dst, double* mean_dev, cudaStream_t s) {
+    const size_t n = (size_t)L->mc.N * L->mc.N * L->mc.N;
+    int kind, comp;
+    slot_kind(L->mc, slot, &kind, &comp);
+    const int grid = L->sm_count * 8;
+    const void* src = L->buf.f[L->cur][slot];
+    if (L->prec == CL_FP32)
+        get_stored_kernel<float><<<grid, 256, 0, s>>>((const float*)src, (float*)dst, n, L->buf.st, kind, comp);
+    else
+        get_stored_kernel<double><<<grid, 256, 0, s>>>((const double*)src, (double*)dst, n, L->buf.st, kind, comp);
+    read_mean_kernel<<<1, 1, 0, s>>>(L->buf.st, kind, comp, mean_dev);
+    return cudaGetLastError();
+}
+
+// The array of `slot` is overwritten by the caller (a copy into
+// L->buf.f[L->cur][slot]); this sets its mean and clears its pending shift.
+cudaError_t launch_set_stored_mean(Lattice* L, int slot, double mean, cudaStream_t s) {
+    int kind, comp;
+    slot_kind(L->mc, slot, &kind, &comp);
+    write_mean_kernel<<<1, 1, 0, s>>>(L->buf.st, kind, comp, mean);
+    return cudaGetLastError();
+}
+
+int has_mean(const ModelConst& mc, int slot) {
+    int kind, comp;
+    slot_kind(mc, slot, &kind, &comp);
+    return kind != 0;
+}
+
 int spectrum_bins(int N) {
     const long long half = N / 2, n2 = 3 * half * half;
     long long r = (long long)sqrt((double)n2);

@@ -783,6 +783,39 @@ cl_status lattice_set_field(cl_lattice* h, int32_t which, const double* src, int
     return CL_OK;
 }
 
+cl_status lattice_get_stored(cl_lattice* h, int32_t which, void* dst, double* mean, int32_t on_device) {
+    if (!h || !dst || !mean) return fail(h, CL_ERR_ARG, "NULL argument");
+    const int slot = cl::array_slot(h->mc, which);
+    if (slot < 0) return fail(h, CL_ERR_ARG, "array index out of range for this model");
+    const size_t n = (size_t)h->mc.N * h->mc.N * h->mc.N;
+    const size_t bytes = n * (h->prec == CL_FP32 ? sizeof(float) : sizeof(double));
+    // device scratch: the N^3-double work array holds either precision; its mean after it
+    double* mean_dev = h->bins;
+    cudaError_t e = cl::launch_get_stored(h, slot, on_device ? dst : (void*)h->work, mean_dev, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(dst, h->work, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mean, mean_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_stored");
+    return CL_OK;
+}
+
+cl_status lattice_set_stored(cl_lattice* h, int32_t which, const void* src, double mean, int32_t on_device) {
+    if (!h || !src) return fail(h, CL_ERR_ARG, "NULL argument");
+    const int slot = cl::array_slot(h->mc, which);
+    if (slot < 0) return fail(h, CL_ERR_ARG, "array index out of range for this model");
+    if (!isfinite(mean)) return fail(h, CL_ERR_ARG, "mean must be finite");
+    if (!cl::has_mean(h->mc, slot) && mean != 0.0)
+        return fail(h, CL_ERR_ARG, "this array has no homogeneous part: mean must be 0");
+    const size_t n = (size_t)h->mc.N * h->mc.N * h->mc.N;
+    const size_t bytes = n * (h->prec == CL_FP32 ? sizeof(float) : sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(h->buf.f[h->cur][slot], src, bytes,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cl::launch_set_stored_mean(h, slot, mean, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);  // host buffer may go away
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_stored");
+    return CL_OK;
+}
+
 }  // extern "C"
 
 namespace {

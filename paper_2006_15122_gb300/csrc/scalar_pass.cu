@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
     constexpr int V = VecT<T>::V;
     constexpr int NS = 6 * NF + 2;
     constexpr int NA = 2 * NF;
+    constexpr int kFold = sizeof(T) == 4 ? 8 : 1 << 30;  // planes per FP32 run of the thread sums
     const Geometry& G = A.geo;
     const int N = G.N, BX = G.BX, BY = G.BY, ZC = G.ZC, S = G.S;
     const int TX = BX * V, RW = TX + 2 * V, ROWS = BY + 2;
@@ -231,96 +232,102 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
 #pragma unroll
         for (int i = 0; i < NS; ++i) ts[i] = T(0);
         T fm[NF][V], fc[NF][V], fp[NF][V], pc[NF][V], pn[NF][V];
-        // FP32: unrolled by two, the register rotation of the z-queue (fm <- fc <- fp)
-        // is renamed away in every other plane instead of moved (FP64 keeps the
-        // loop rolled: unrolled it would spill)
+        // Runs of kFold planes: in FP32 the thread sums cover at most 4 kFold sites
+        // before the warp folds them into its FP64 accumulators (FP64: one run per
+        // tile).  FP32: unrolled by two, the register rotation of the z-queue
+        // (fm <- fc <- fp) is renamed away in every other plane instead of moved
+        // (FP64 keeps the loop rolled: unrolled it would spill).
+        for (int zf = 0; zf < ZC; zf += kFold) {
+            const int zend = ZC - zf < kFold ? ZC : zf + kFold;
 #pragma unroll(sizeof(T) == 4 ? 2 : 1)
-        for (int zz = 0; zz < ZC; ++zz, ++need) {
-            wait_for(need);  // planes z-1, z, z+1 have landed
-            // the stage of plane z-2 was released by the previous iteration and every
-            // thread has passed the barrier above: refill it now (one barrier per plane)
-            if (zz > 0) { issue(); ++issued; }
-            const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
-            const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
-            T* Sc = sm + sl_c * STG;
-            T* Sp = sm + sl_p * STG;
-            if (zz == 0) {
-                T* Sm = sm + sl_m * STG;
-                T dummy[NF][V];
-                drift_stage(Sm, fm, dummy);
-                drift_stage(Sc, fc, pc);
-            }
-            drift_stage(Sp, fp, pn);
-            if (zz == 0) __syncthreads();  // halos of the tile's first plane are drifted
-            T lap[NF][V];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const T* cF = Sc + f * ASZ;
-                // x-neighbours: shuffles of the drifted own vectors, shared memory at row/warp edges
-                const T fromL = __shfl_up_sync(wmask, fc[f][V - 1], 1);
-                const T fromR = __shfl_down_sync(wmask, fc[f][0], 1);
-                const bool useL = (tx > 0) && (lane > 0), useR = (tx < BX - 1) && (lane < nlanes - 1);
-                const T left = useL ? fromL : cF[ob - 1];
-                const T right = useR ? fromR : cF[ob + V];
-                T u[V], d[V];
-                vload_s(cF + ob - RW, u);
-                vload_s(cF + ob + RW, d);
-                T g = T(0);
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const T xl = (v == 0) ? left : fc[f][v - 1];
-                    const T xr = (v == V - 1) ? right : fc[f][v + 1];
-                    const T c = fc[f][v];
-                    lap[f][v] = (((xl + xr) + (u[v] + d[v])) + (fm[f][v] + fp[f][v]) - T(6) * c) * idx2;
-                    const T gx = xr - c, gy = d[v] - c, gz = fp[f][v] - c;
-                    g += gx * gx + gy * gy + gz * gz;
+            for (int zz = zf; zz < zend; ++zz, ++need) {
+                wait_for(need);  // planes z-1, z, z+1 have landed
+                // the stage of plane z-2 was released by the previous iteration and every
+                // thread has passed the barrier above: refill it now (one barrier per plane)
+                if (zz > 0) { issue(); ++issued; }
+                const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
+                const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
+                T* Sc = sm + sl_c * STG;
+                T* Sp = sm + sl_p * STG;
+                if (zz == 0) {
+                    T* Sm = sm + sl_m * STG;
+                    T dummy[NF][V];
+                    drift_stage(Sm, fm, dummy);
+                    drift_stage(Sc, fc, pc);
                 }
-                ts[6 * f + 4] += g;
-            }
-            T pout[NF][V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T d0 = fc[0][v];
-                const T d1 = NF > 1 ? fc[NF > 1 ? 1 : 0][v] : T(0);
-                T F[2];
-                F[0] = lam * Power<T, P>::dforce(fb[0], d0);
-                F[1] = T(0);
-                ts[6 * NF] += lam * Power<T, P>::dvalue(fb[0], d0);
-                if (NF > 1) {
-                    const T dP = d0 * (T(2) * fb[0] + d0), dC = d1 * (T(2) * fb[1] + d1);
-                    F[0] += q * (C0 * d0 + dC * (fb[0] + d0));
-                    F[1] = q * (P0 * d1 + dP * (fb[1] + d1));
-                    ts[6 * NF + 1] += T(0.5) * q * (dP * C0 + P0 * dC + dP * dC);
-                }
+                drift_stage(Sp, fp, pn);
+                if (zz == 0) __syncthreads();  // halos of the tile's first plane are drifted
+                T lap[NF][V];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const T K = A1 * lap[f][v] - A3 * F[f];
-                    const T pr = pc[f][v] + h1 * K;
-                    pout[f][v] = pc[f][v] + h * K;
-                    ts[6 * f + 0] += fc[f][v];
-                    ts[6 * f + 1] += fc[f][v] * fc[f][v];
-                    ts[6 * f + 2] += pr;
-                    ts[6 * f + 3] += pr * pr;
-                    ts[6 * f + 5] += pout[f][v];
-                }
-            }
-            if (A.write) {
-                const size_t o = (size_t)(tt.z0 + zz) * NN + (size_t)y * N + x;
+                    const T* cF = Sc + f * ASZ;
+                    // x-neighbours: shuffles of the drifted own vectors, shared memory at row/warp edges
+                    const T fromL = __shfl_up_sync(wmask, fc[f][V - 1], 1);
+                    const T fromR = __shfl_down_sync(wmask, fc[f][0], 1);
+                    const bool useL = (tx > 0) && (lane > 0), useR = (tx < BX - 1) && (lane < nlanes - 1);
+                    const T left = useL ? fromL : cF[ob - 1];
+                    const T right = useR ? fromR : cF[ob + V];
+                    T u[V], d[V];
+                    vload_s(cF + ob - RW, u);
+                    vload_s(cF + ob + RW, d);
+                    T g = T(0);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    vstore_cs(static_cast<T*>(A.out[f]) + o, fc[f]);
-                    vstore_cs(static_cast<T*>(A.out[NF + f]) + o, pout[f]);
+                    for (int v = 0; v < V; ++v) {
+                        const T xl = (v == 0) ? left : fc[f][v - 1];
+                        const T xr = (v == V - 1) ? right : fc[f][v + 1];
+                        const T c = fc[f][v];
+                        lap[f][v] = (((xl + xr) + (u[v] + d[v])) + (fm[f][v] + fp[f][v]) - T(6) * c) * idx2;
+                        const T gx = xr - c, gy = d[v] - c, gz = fp[f][v] - c;
+                        g += gx * gx + gy * gy + gz * gz;
+                    }
+                    ts[6 * f + 4] += g;
                 }
-            }
-            sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
+                T pout[NF][V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    fm[f][v] = fc[f][v];
-                    fc[f][v] = fp[f][v];
-                    pc[f][v] = pn[f][v];
+                    const T d0 = fc[0][v];
+                    const T d1 = NF > 1 ? fc[NF > 1 ? 1 : 0][v] : T(0);
+                    T F[2];
+                    F[0] = lam * Power<T, P>::dforce(fb[0], d0);
+                    F[1] = T(0);
+                    ts[6 * NF] += lam * Power<T, P>::dvalue(fb[0], d0);
+                    if (NF > 1) {
+                        const T dP = d0 * (T(2) * fb[0] + d0), dC = d1 * (T(2) * fb[1] + d1);
+                        F[0] += q * (C0 * d0 + dC * (fb[0] + d0));
+                        F[1] = q * (P0 * d1 + dP * (fb[1] + d1));
+                        ts[6 * NF + 1] += T(0.5) * q * (dP * C0 + P0 * dC + dP * dC);
+                    }
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const T K = A1 * lap[f][v] - A3 * F[f];
+                        const T pr = pc[f][v] + h1 * K;
+                        pout[f][v] = pc[f][v] + h * K;
+                        ts[6 * f + 0] += fc[f][v];
+                        ts[6 * f + 1] += fc[f][v] * fc[f][v];
+                        ts[6 * f + 2] += pr;
+                        ts[6 * f + 3] += pr * pr;
+                        ts[6 * f + 5] += pout[f][v];
+                    }
                 }
+                if (A.write) {
+                    const size_t o = (size_t)(tt.z0 + zz) * NN + (size_t)y * N + x;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        vstore_cs(static_cast<T*>(A.out[f]) + o, fc[f]);
+                        vstore_cs(static_cast<T*>(A.out[NF + f]) + o, pout[f]);
+                    }
+                }
+                sl_m = sl_m + 1 == S ? 0 : sl_m + 1;
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        fm[f][v] = fc[f][v];
+                        fc[f][v] = fp[f][v];
+                        pc[f][v] = pn[f][v];
+                    }
+            }
+            fold_warp_sums<T, NS>(ts, bacc[warp], lane, nlanes);
         }
         __syncthreads();  // the tile's last three stages are free
         issue();
@@ -329,11 +336,6 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
         issued += 3;
         need += 2;
         sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const T v = partial_warp_sum(ts[i], lane, nlanes);
-            if (lane == 0) bacc[warp][i] += double(v);
-        }
     }
     cp_async_wait<0>();
     __syncthreads();

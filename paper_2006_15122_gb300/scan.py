@@ -28,7 +28,7 @@ class ScanSpec:
     integrator: int = CL_INT_VV4
     precision: int = CL_FP32
     sizes: tuple = (32, 64, 96)
-    steps_per_slice: int = 32
+    steps_per_slice: int = 782  # 64 slices to t = 100.1, the q = 1e4 workload's horizon
     n_slices: int = 64
     phi0: float = 1.0
     nmin: int = field(default=0)
@@ -107,6 +107,37 @@ def plain_observations(spec, q, N, seed, stream=None):
     return obs, times
 
 
+def partition(n, world, rank):
+    """The runs of an n-run scan that rank `rank` of `world` evolves: a
+    contiguous block, the first n % world ranks one run longer.  The blocks
+    cover 0..n-1 once, in order."""
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    return list(range(lo, lo + base + (1 if rank < extra else 0)))
+
+
+def gather_runs(local, n, dist=None, device="cpu"):
+    """All ranks' observations of their partition() blocks, assembled in run
+    order on every rank: local has shape (len(block), ...).  One all_gather of
+    equally padded blocks (NCCL on GPUs, gloo on CPU ranks); without a process
+    group the local array is the whole scan."""
+    local = np.ascontiguousarray(local)
+    if dist is None:
+        assert local.shape[0] == n
+        return local
+    import torch
+
+    world = dist.get_world_size()
+    rows = -(-n // world)
+    pad = np.full((rows,) + local.shape[1:], np.nan, dtype=local.dtype)
+    pad[:local.shape[0]] = local
+    t = torch.from_numpy(pad).to(device)
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t)
+    out = [parts[r].cpu().numpy()[:len(partition(n, world, r))] for r in range(world)]
+    return np.concatenate(out, axis=0)
+
+
 def training_pairs(qs, times, obs):
     """(log10 q, t) -> observables, one row per run and slice."""
     n, S = len(qs), len(times)
@@ -123,6 +154,42 @@ def fit_surrogate(X, Y, width=256, depth=3, epochs=200, batch=512, lr=2e-3, lr_e
     t0 = time.perf_counter()
     hist = net.train(X, Y, epochs=epochs, batch=batch, lr=lr, lr_end=lr_end, shuffle=True)
     return net, hist, time.perf_counter() - t0
+
+
+def disagreement(pa, pb):
+    """Error estimate of a surrogate answer from two independently trained
+    networks: per (query, slice), the largest of |eps_a - eps_b|, |w_a - w_b|
+    and the spectrum's |10^(a - b) - 1| over its 32 momenta."""
+    d_eps = np.abs(pa[..., 0] - pb[..., 0])
+    d_w = np.abs(pa[..., 1] - pb[..., 1])
+    d_spec = np.max(np.abs(10.0 ** (pa[..., 2:].astype(np.float64) - pb[..., 2:]) - 1.0), axis=-1)
+    return np.maximum(np.maximum(d_eps, d_w), d_spec)
+
+
+def answer_queries(nets, qs, times, q_range, spec, tol=0.02, frac=0.9, seeds=None, size=None, stream=None):
+    """Observations at couplings qs and the given slice times, from the surrogate
+    where it can be trusted and from the lattice otherwise.  A query falls back
+    to a plain lattice run (size `size`, default the largest of spec.sizes) when
+    its q lies outside the trained range q_range, or when the two networks
+    disagree by more than tol on more than 1 - frac of its slices.  Returns
+    (answers (Q, S, CL_OBS_SIZE), fallback mask, estimate (Q, S), seconds of
+    the network queries, seconds of the fallback runs)."""
+    Q, S = len(qs), len(times)
+    X = np.stack([np.repeat(np.log10(qs), S), np.tile(times, Q)], axis=1).astype(np.float32)
+    t0 = time.perf_counter()
+    preds = [net.predict(X).reshape(Q, S, -1) for net in nets]
+    t_query = time.perf_counter() - t0
+    est = disagreement(preds[0], preds[1]) if len(preds) > 1 else np.zeros((Q, S))
+    out = np.mean(preds, axis=0).astype(np.float32)
+    lo, hi = q_range
+    fallback = (np.asarray(qs) < lo) | (np.asarray(qs) > hi) | (np.mean(est <= tol, axis=1) < frac)
+    size = size or max(spec.sizes)
+    seeds = seeds if seeds is not None else list(range(2 * 10 ** 6, 2 * 10 ** 6 + Q))
+    t0 = time.perf_counter()
+    for i in np.nonzero(fallback)[0]:
+        out[i], _ = plain_observations(spec, qs[i], size, seeds[i], stream=stream)
+    t_fallback = time.perf_counter() - t0
+    return out, fallback, est, t_query, t_fallback
 
 
 def score(pred, ref_runs):
@@ -147,5 +214,12 @@ def score(pred, ref_runs):
         return {"median": float(np.median(a)), "p95": float(np.percentile(a, 95)), "max": float(np.max(a)),
                 "within_2pct": float(np.mean(a <= 0.02))}
 
+    R = ref_runs.shape[1]
+    sq = np.sqrt(R)
     return {"eps_chi_abs": summ(e_eps), "w_abs": summ(e_w), "spectrum_rel": summ(e_spec),
-            "floor": {"eps_chi_abs": summ(f_eps), "w_abs": summ(f_w), "spectrum_rel": summ(f_spec)}}
+            "floor": {"eps_chi_abs": summ(f_eps), "w_abs": summ(f_w), "spectrum_rel": summ(f_spec)},
+            # the reference's own standard error (seed scatter of one run over sqrt(R))
+            "reference_stderr": {"eps_chi_abs": summ(np.nanstd(ref_runs[..., 0], axis=1) / sq),
+                                 "w_abs": summ(np.nanstd(ref_runs[..., 1], axis=1) / sq),
+                                 "spectrum_rel": summ(10.0 ** (np.nanstd(ref_runs[..., 2:].astype(np.float64),
+                                                                         axis=1) / sq) - 1.0)}}

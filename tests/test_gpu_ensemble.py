@@ -83,3 +83,50 @@ def test_ensemble_observations_agree_with_members():
         ref = np.interp(kj, lk, lD)
         assert np.allclose(obs[i, 2:], ref, atol=1e-4), (obs[i, 2:], ref)
     ens.close()
+
+
+def _oracle_run(N, q, seed, kIR, dt, steps, omega=0.05, fmp=1.0):
+    om = ScalarModel(N=N, Ns=2, pexp=2, dx=2 * math.pi / (kIR * N), alpha=0.0, fmp2=fmp * fmp, lam=1.0, q=q)
+    phi, pi, _ = scalar_ic(om, kIR, [1.0, 0.0], [0.0, 0.0], seed=seed, omega_over_fstar=omega)
+    ref = ScalarLattice(om, phi, pi)
+    ref.b = math.sqrt(ref.hubble_rhs())
+    ref.vv_steps(oracle.VV4, dt, steps)
+    return ref
+
+
+def _check_obs(got, want):
+    """FP32 outputs: eps_chi and w to their rounding, log10 Delta to 1e-5."""
+    assert abs(got[0] - want[0]) < 1e-6 * abs(want[0]) + 1e-12, (got[0], want[0])
+    assert abs(got[1] - want[1]) < 1e-6, (got[1], want[1])
+    assert np.allclose(got[2:], want[2:], rtol=0, atol=1e-5), (got[2:], want[2:])
+
+
+@pytest.mark.parametrize("kmax", [0.0, 3.1])
+def test_lattice_observe_matches_oracle_composition(kmax):
+    """lattice_observe of an FP64 lattice against the oracle's composition of
+    the same observables (oracle/observe.py) from the oracle's own run."""
+    from oracle.observe import observables
+    N, q, seed, kIR, dt, steps = 48, 2500.0, 17, 0.5, 0.004, 30
+    model = cl.make_model(n_fields=2, pexp=2, lam=1.0, q=q, omega_over_fstar=0.05, fstar_over_mp=1.0)
+    lat = cl.Lattice(model, cl.make_grid(N, kIR, dt, "vv4", cl.CL_FP64), cl.make_init(phi0=(1.0, 0.0), seed=seed))
+    lat.evolve(steps)
+    obs, t = lat.observe(kmax)
+    ref = _oracle_run(N, q, seed, kIR, dt, steps)
+    _check_obs(obs, observables(ref, kIR, kmax if kmax > 0 else None))
+    assert abs(t - steps * dt) < 1e-12
+    lat.close()
+
+
+def test_ensemble_observations_match_oracle_composition():
+    """ensemble_observe of a mixed-size FP64 ensemble: every member's 34 numbers
+    against the oracle composition of its own oracle run, with the spectrum
+    momenta up to the smallest member's axis Nyquist momentum."""
+    from oracle.observe import observables
+    Ns, qs, kIR, dt, steps = [32, 64, 32], [80.0, 900.0, 4000.0], 0.5, 0.004, 12
+    ens, seeds = make(Ns, qs, cl.CL_FP64, kIR=kIR, dt=dt)
+    ens.evolve(steps)
+    obs, _ = ens.observe()
+    kmax = 0.5 * min(Ns) * kIR
+    for i, (N, q, seed) in enumerate(zip(Ns, qs, seeds)):
+        _check_obs(obs[i], observables(_oracle_run(N, q, seed, kIR, dt, steps), kIR, kmax))
+    ens.close()

@@ -230,3 +230,46 @@ def test_128_cubed_u1_fp32_leapfrog_matches_oracle():
     gauss_of_gpu_state = U1Lattice(om, gphi, gpi, gth, gpa).gauss()
     assert gauss_of_gpu_state < 1e-5 and mm["gauss_violation"] < 1e-5, (gauss_of_gpu_state, mm["gauss_violation"])
     lat.close()
+
+
+def test_1024_cubed_fp32_reductions_match_fp64_sums_of_the_same_arrays():
+    """The throughput workload (1024^3, q* = 4e5, k_IR = 0.1, dt = 0.002, VV4,
+    FP32 fluctuations) from its vacuum start: the energies and variances that the
+    FP32 pass reduces (thread runs of at most 32 sites, folded per warp into FP64,
+    compensated FP64 sums across the grid) against FP64 sums of the same arrays.
+    The fluctuation-only quantities (variances, gradient energies) carry the
+    whole FP32 reduction error; the bound 1e-6 is 17 FP32 ulps."""
+    torch = pytest.importorskip("torch")
+    import bench
+
+    N = 1024
+    model = cl.make_model(n_fields=2, pexp=2, alpha=0.0, fstar_over_mp=bench.FSTAR_MP,
+                          omega_over_fstar=bench.OMEGA_FSTAR, lam=1.0, q=bench.QSTAR)
+    lat = cl.Lattice(model, cl.make_grid(N, bench.KIR, bench.DT, "vv4", cl.CL_FP32),
+                     cl.make_init(phi0=(1.0, 0.0), seed=0))
+    lat.evolve(3)
+    mm = lat.measure_means()
+    a = mm["a"]
+    dx = 2 * math.pi / (bench.KIR * N)
+    f = [torch.empty((N, N, N), device="cuda", dtype=torch.float64) for _ in range(2)]
+    for i in range(2):
+        lat.get_field(cl.FIELD(i), f[i])
+    for i in range(2):
+        mean = f[i].mean()
+        var = ((f[i] - mean) ** 2).mean().item()
+        eg = sum(((torch.roll(f[i], -1, d) - f[i]) ** 2).mean().item() for d in range(3)) / (2 * a * a * dx * dx)
+        assert abs(mm["var"][i] - var) < 1e-6 * var, (i, (mm["var"][i] - var) / var)
+        assert abs(mm["EG"][i] - eg) < 1e-6 * eg, (i, (mm["EG"][i] - eg) / eg)
+    ev1 = (0.5 * bench.QSTAR * (f[0] * f[1]) ** 2).mean().item()
+    assert abs(mm["EV"][1] - ev1) < 1e-6 * ev1, (mm["EV"][1] - ev1) / ev1
+    del f
+    p = torch.empty((N, N, N), device="cuda", dtype=torch.float64)
+    for i in range(2):
+        lat.get_field(cl.MOMENTUM(i), p)
+        ek = (p ** 2).mean().item() / (2 * a ** 6)
+        dvar = ((p - p.mean()) ** 2).mean().item()
+        # E_K of chi is all fluctuation; that of phi is dominated by the FP64 mean
+        assert abs(mm["EK"][i] - ek) < 1e-6 * ek, (i, (mm["EK"][i] - ek) / ek, dvar)
+    del p
+    lat.close()
+    torch.cuda.empty_cache()

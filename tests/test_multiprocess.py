@@ -52,3 +52,55 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
     bench.run_reference(bench.parse())
     assert capsys.readouterr().out == ""  # the non-zero rank exits without work or output
+
+
+def _scan_rank_main(rank, world, port, n, out):
+    import numpy as np
+    import torch.distributed as dist
+
+    from paper_2006_15122_gb300 import scan
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        block = scan.partition(n, world, rank)
+        # each run's "observations": its index and a few derived numbers, as the ensemble would return
+        local = np.stack([np.array([i, 2.0 * i, -float(i)], dtype=np.float32) for i in block]).reshape(len(block), 1, 3)
+        out[rank] = (block, scan.gather_runs(local, n, dist, "cpu"))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("n", [7, 8])
+def test_two_gloo_ranks_split_the_scan_and_gather_every_run_in_order(n):
+    """The scan's run list is split into contiguous blocks, one per rank (no
+    data-path exchange while the lattices evolve); one gather assembles every
+    run's observations in run order on every rank."""
+    import numpy as np
+
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.start_processes(_scan_rank_main, args=(world, _free_port(), n, out), nprocs=world, join=True,
+                       start_method="spawn")
+    blocks = [out[r][0] for r in range(world)]
+    assert sorted(blocks[0] + blocks[1]) == list(range(n)) and not set(blocks[0]) & set(blocks[1])
+    for r in range(world):
+        g = out[r][1]
+        assert g.shape == (n, 1, 3)
+        assert np.array_equal(g[:, 0, 0], np.arange(n, dtype=np.float32))
+        assert np.array_equal(g[:, 0, 2], -np.arange(n, dtype=np.float32))
+
+
+def test_partition_without_a_process_group_is_the_whole_scan():
+    import numpy as np
+
+    from paper_2006_15122_gb300 import scan
+
+    for n, world in ((10, 3), (3, 4), (512, 8)):
+        blocks = [scan.partition(n, world, r) for r in range(world)]
+        assert sum(blocks, []) == list(range(n))
+        assert max(map(len, blocks)) - min(map(len, blocks)) <= 1
+    a = np.zeros((5, 2))
+    assert scan.gather_runs(a, 5) is not None
