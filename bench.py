@@ -58,11 +58,11 @@ def parse():
                    help="time the batched ensemble + surrogate parameter scan instead of the single lattice")
     p.add_argument("--scan-runs", type=int, default=512)
     p.add_argument("--scan-slices", type=int, default=64)
-    p.add_argument("--scan-steps-per-slice", type=int, default=782)
+    p.add_argument("--scan-steps-per-slice", type=int, default=1571)
     p.add_argument("--scan-heldout", type=int, default=64)
-    p.add_argument("--scan-seeds", type=int, default=6)
-    p.add_argument("--scan-plain", type=int, default=12)
-    p.add_argument("--scan-epochs", type=int, default=400)
+    p.add_argument("--scan-seeds", type=int, default=4)
+    p.add_argument("--scan-plain", type=int, default=6)
+    p.add_argument("--scan-epochs", type=int, default=800)
     p.add_argument("--scan-save", default="", help="write the scan's observations and answers to this .npz")
     p.add_argument("--accuracy", action="store_true",
                    help="print the Friedmann-constraint error of every integrator on the U(1) inflaton instead")
@@ -328,8 +328,8 @@ def scan_measurement(args, stream, dist=None):
                                   times[-1], Q),
                    "surrogate": "two MLPs 2-256-256-256-34 GELU, BF16 tensor-core GEMMs, FP32 accumulate, Adam, "
                                 "%d epochs, batch 512, %d training rows; answers where they agree within 2%% on "
-                                ">= 90%% of a query's slices, a plain %d^3 lattice run otherwise"
-                                % (args.scan_epochs, len(X), max(spec.sizes)),
+                                ">= 90%% of a query's slices (eps_chi and w), a plain %d^3 lattice run otherwise"
+                                % (args.scan_epochs, len(X), sorted(spec.sizes)[len(spec.sizes) // 2]),
                    "heldout": "%d q log-uniform in [1e2, 1e5] (seed 4321), %d fresh seeds each" % (Q, R),
                    "parallelism": "runs split across %d ranks" % world if world > 1 else "single"},
         "value_definition": "(n training runs + Q answered queries) per hour of ensemble + training + queries + "
@@ -665,19 +665,28 @@ def main():
         means = [lat.get_stored(w, host[i])[1] for i, w in enumerate(which)]
         mm0 = lat.measure_means()
         reps = 3
+        ph = {"set_stored": 0.0, "evolve": 0.0, "measure": 0.0}
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
+            ta = time.perf_counter()
             for i, w in enumerate(which):
                 lat.set_stored(w, host[i], means[i])
+            tb = time.perf_counter()
             lat.set_background(mm0["a"], mm0["b"], mm0["t"])
             lat.evolve(1)
-            lat.measure_means()
+            lat.measure_means()  # synchronizes: the step is done when it returns
+            tc = time.perf_counter()
+            ph["set_stored"] += tb - ta
+            ph["evolve"] += tc - tb
         t1 = time.perf_counter()
         e2e = {"value": world * N ** 3 * reps / (t1 - t0), "unit": "site-updates/s",
                "h2d_bytes_per_step": 4 * 4 * N ** 3 + 4 * 8, "d2h_bytes_per_step": 320,
                "note": "per step: the 4 FP32 fluctuation arrays and their FP64 means H2D from pinned memory via "
-                       "lattice_set_stored, one VV4 step, lattice_measure_means D2H"}
+                       "lattice_set_stored, one VV4 step, lattice_measure_means D2H",
+               "ms_per_step_phases": {"upload": 1e3 * ph["set_stored"] / reps,
+                                      "step_and_measure": 1e3 * ph["evolve"] / reps},
+               "h2d_GBs": 4 * 4 * N ** 3 / (ph["set_stored"] / reps) / 1e9}
         del host
     lat.close()
     cpu = None

@@ -5,8 +5,9 @@
 //   H_0 = X,  Z_l = H_l W_l^T + b_l,  H_{l+1} = GELU(Z_l),  Y = Z_L,
 //   loss = mean (Y - T)^2,  GELU(x) = x/2 (1 + erf(x/sqrt 2)),
 // trained by Adam on FP32 master weights; every GEMM (forward, input and
-// weight gradients) runs on the tensor cores with BF16 operands and FP32
-// accumulation (mma.sync m16n8k16), the bias/GELU epilogues fused.
+// weight gradients) runs on the fifth-generation tensor cores (tcgen05.mma with
+// the accumulator in tensor memory) with BF16 operands and FP32 accumulation,
+// the bias/GELU epilogues fused.
 // Matrices are stored row-major with every dimension padded with zeros to a
 // multiple of 32 (batch: 64), so that the GEMM needs no K-edge handling and the
 // padding stays zero through forward and backward passes.
@@ -26,8 +27,6 @@ typedef __nv_bfloat16 bf16;
 
 // ---------------------------------------------------------------- GEMM
 // C[M x N] = A[M x K] . B[N x K]^T  (A, B bf16 row-major; K a multiple of 32)
-constexpr int GM = 64, GN = 64, GK = 32, SKP = GK + 8;  // shared row stride 40 bf16 (80 bytes)
-
 struct GemmArgs {
     const bf16* A;
     int lda;
@@ -48,107 +47,164 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, boo
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
 }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_prime_f(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-__global__ void __launch_bounds__(128) gemm_tn_kernel(const GemmArgs g) {
-    __shared__ __align__(16) bf16 sA[2][GM * SKP];
-    __shared__ __align__(16) bf16 sB[2][GN * SKP];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int bm = blockIdx.y * GM, bn = blockIdx.x * GN;
-    const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-    // each thread copies two 16-byte chunks of A and of B per k-tile (64 rows x 4 chunks)
-    auto load = [&](int buf, int k0) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int idx = tid + c * 128, row = idx >> 2, ch = idx & 3;
-            const int ra = bm + row, rb = bn + row;
-            cp_async16_zfill(&sA[buf][row * SKP + ch * 8], g.A + (size_t)(ra < g.M ? ra : 0) * g.lda + k0 + ch * 8, ra < g.M);
-            cp_async16_zfill(&sB[buf][row * SKP + ch * 8], g.B + (size_t)(rb < g.N ? rb : 0) * g.ldb + k0 + ch * 8, rb < g.N);
+// ---------------------------------------------------------------- GEMM (tcgen05)
+// C[M x N] = A[M x K] . B[N x K]^T on the fifth-generation tensor cores
+// (tcgen05.mma, kind::f16 with BF16 operands, FP32 accumulator in tensor memory).
+// One CTA of 256 threads owns a 128 x BN tile of C (BN = 32 or 64, so that the small
+// GEMMs of the network spread over many SMs):
+//  - K advances in chunks of 64, one 128-byte row of BF16 per tile row, through
+//    two shared-memory stages.  Every thread stages its share of a chunk with
+//    cp.async in the canonical K-major layout with 128-byte swizzle (8-row groups
+//    of 1024 bytes; the 16-byte piece c of row r sits at piece c ^ (r mod 8)),
+//    zero-filling rows beyond M or N and columns beyond K.
+//  - One thread issues the chunk's MMAs (K = 16 each; the operand descriptors
+//    advance 32 bytes per step inside the swizzle atom) and commits them to the
+//    stage's mbarrier; the stage is refilled once that barrier has completed.
+//  - Epilogue: warp w reads accumulator rows 32 (w mod 4) .. +31 (the tensor-memory
+//    lanes its quarter of the SM may access), columns (w / 4) BN/2 .. +BN/2, with
+//    tcgen05.ld, and applies the bias / GELU of `mode`.
+// Every mbarrier wait is bounded; a wait that gives up sets *err, and the CTA
+// still frees its tensor memory before it returns.
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 64;
+
+__host__ __device__ constexpr uint32_t tc_stage_bytes(int BN) { return (uint32_t)(TC_BM + BN) * 128u; }
+__host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) { return 2u * tc_stage_bytes(BN) + 1024u; }
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled
+// layout: start address, stride of 1024 bytes between 8-row groups, the sm_100
+// descriptor version and the swizzle mode.
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;            // leading byte offset (16 B; unused by this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1u << 46;            // version
+    d |= (uint64_t)2u << 61;            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128.
+__device__ __forceinline__ uint32_t tc_idesc(int BN) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int BN, int* err) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bm = blockIdx.y * TC_BM, bn = blockIdx.x * BN;
+    const uint32_t ncols = BN <= 32 ? 32u : 64u;
+    const uint32_t stage = tc_stage_bytes(BN);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    auto load = [&](int s, int k0) {
+        unsigned char* sa = base + s * stage;
+        for (int i = tid; i < (TC_BM + BN) * 8; i += TC_THREADS) {
+            const int r = i >> 3, c = i & 7;
+            const bool isA = r < TC_BM;
+            const int rr = isA ? r : r - TC_BM;
+            const int grow = (isA ? bm : bn) + rr, kcol = k0 + c * 8;
+            const bool valid = grow < (isA ? g.M : g.N) && kcol < g.K;
+            const bf16* src = isA ? g.A + (size_t)(valid ? grow : 0) * g.lda + (valid ? kcol : 0)
+                                  : g.B + (size_t)(valid ? grow : 0) * g.ldb + (valid ? kcol : 0);
+            cp_async16_zfill(sa + r * 128 + ((c ^ (rr & 7)) << 4), src, valid);
         }
         cp_async_commit();
     };
-    const int nk = g.K / GK;
+
+    const int nk = (g.K + TC_BK - 1) / TC_BK;
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
     load(0, 0);
     for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt & 1;
         if (kt + 1 < nk) {
-            load((kt + 1) & 1, (kt + 1) * GK);
+            if (kt >= 1) {  // the other stage holds chunk kt-1: wait until its MMAs have read it
+                ok = mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1]) && ok;
+                phase[s ^ 1] ^= 1u;
+            }
+            load(s ^ 1, (kt + 1) * TC_BK);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staged data -> tensor-core reads
         __syncthreads();
-        const bf16* a = sA[kt & 1];
-        const bf16* b = sB[kt & 1];
-#pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-                ldmatrix_x4(af[i][0], af[i][1], af[i][2], af[i][3],
-                            &a[(wr + 16 * i + (lane & 15)) * SKP + kk + 8 * (lane >> 4)]);
-            uint32_t bfr[4][2];
-#pragma unroll
-            for (int jp = 0; jp < 2; ++jp) {
-                const int q = lane >> 3;
-                uint32_t r0, r1, r2, r3;
-                ldmatrix_x4(r0, r1, r2, r3, &b[(wc + 16 * jp + (q >> 1) * 8 + (lane & 7)) * SKP + kk + (q & 1) * 8]);
-                bfr[2 * jp][0] = r0;
-                bfr[2 * jp][1] = r1;
-                bfr[2 * jp + 1][0] = r2;
-                bfr[2 * jp + 1][1] = r3;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(base + s * stage), b0 = a0 + TC_BM * 128;
+            const uint32_t idesc = tc_idesc(BN);
+            const int ksteps = min(TC_BK, g.K - kt * TC_BK) / 16;
+            for (int k = 0; k < ksteps; ++k) {
+                const uint64_t ad = tc_smem_desc(a0 + 32u * k), bd = tc_smem_desc(b0 + 32u * k);
+                const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
             }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar[s]))
+                         : "memory");
         }
-        __syncthreads();
     }
-    // epilogue: fragment (i, j) holds rows wr+16i+lane/4 (+8), columns wc+8j+2(lane%4) (+1)
-    const int gr = lane >> 2, tc = (lane & 3) * 2;
+    // the last commit completes after every MMA of the tile
+    ok = mbar_wait_bounded(&bar[(nk - 1) & 1], phase[(nk - 1) & 1]) && ok;
+    tc_fence_after();
+    if (!ok && lane == 0) atomicExch(err, 1);
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = bm + 32 * quarter + lane;
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+        uint32_t v[16];
+        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (r < g.M) {
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = bm + wr + 16 * i + gr + 8 * h;
-                if (r >= g.M) continue;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int c = bn + wc + 8 * j + tc + e;
-                    if (c >= g.N) continue;
-                    const bool valid = r < g.Mvalid && c < g.Nvalid;
-                    float v = acc[i][j][2 * h + e];
-                    if (g.mode != 0) v = valid ? v + g.bias[c] : 0.f;
-                    g.C[(size_t)r * g.ldc + c] = v;
-                    if (g.mode == 1) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(valid ? gelu_f(v) : 0.f);
-                }
+            for (int j = 0; j < 16; ++j) {
+                const int c = bn + c0 + j;
+                if (c >= g.N) continue;
+                const bool valid = r < g.Mvalid && c < g.Nvalid;
+                float x = __uint_as_float(v[j]);
+                if (g.mode != 0) x = valid ? x + g.bias[c] : 0.f;
+                g.C[(size_t)r * g.ldc + c] = x;
+                if (g.mode == 1) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(valid ? gelu_f(x) : 0.f);
             }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 // ---------------------------------------------------------------- helpers
@@ -233,6 +289,7 @@ struct TrainDev {
     long long sched;  // minibatch steps taken in this call (cosine schedule position)
     long long total;  // minibatch steps of this call
     float lr, lr_end, b1, b2, eps, wd;
+    int tc_err;  // a tensor-core GEMM gave up waiting for its MMAs (never expected)
 };
 
 // Adam on FP32 master weights; the BF16 copy (when wb != NULL) is refreshed in
@@ -340,8 +397,24 @@ void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ld
     cl::GemmArgs g;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc; g.M = M; g.N = N; g.K = K;
     g.mode = mode; g.bias = bias; g.H = H; g.ldh = ldh; g.Mvalid = Mvalid; g.Nvalid = Nvalid;
-    dim3 grid((N + cl::GN - 1) / cl::GN, (M + cl::GM - 1) / cl::GM);
-    cl::gemm_tn_kernel<<<grid, 128, 0, S->stream>>>(g);
+    const int BN = N <= 32 ? 32 : cl::TC_BN;  // N is a multiple of 32
+    static bool attr_set = false;  // the stage pair needs the opt-in shared-memory size
+    if (!attr_set) {
+        cudaFuncSetAttribute(cl::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cl::tc_smem_bytes(cl::TC_BN));
+        attr_set = true;
+    }
+    dim3 grid((N + BN - 1) / BN, (M + cl::TC_BM - 1) / cl::TC_BM);
+    cl::gemm_tc_kernel<<<grid, cl::TC_THREADS, cl::tc_smem_bytes(BN), S->stream>>>(g, BN, &S->tdev->tc_err);
+}
+
+// CL_ERR_TIMEOUT when a tensor-core GEMM of the last call gave up waiting (after a synchronize)
+cl_status check_tc(cl_surrogate* S, const char* who) {
+    int flag = 0;
+    if (cudaMemcpy(&flag, &S->tdev->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return sfail(CL_ERR_CUDA, std::string(who) + ": reading the GEMM status");
+    if (flag) return sfail(CL_ERR_TIMEOUT, std::string(who) + ": a tensor-core GEMM timed out waiting for its MMAs");
+    return CL_OK;
 }
 
 void transpose(cl_surrogate* S, const cl::bf16* in, int ldi, cl::bf16* out, int ldo, int R, int C) {
@@ -602,6 +675,8 @@ cl_status surrogate_loss_grad(cl_surrogate* S, const float* X, const float* T, i
     S->h_mu_in = mi; S->h_sd_in = si; S->h_mu_out = mo; S->h_sd_out = so;
     upload_scaling(S);
     if (e != cudaSuccess) return sfail(CL_ERR_CUDA, std::string("surrogate_loss_grad: ") + cudaGetErrorString(e));
+    s = check_tc(S, "surrogate_loss_grad");
+    if (s != CL_OK) return s;
     if (loss) *loss = l / ((double)n * S->n_out);
     if (grad) return copy_params(S, grad, nullptr, true);
     return CL_OK;
@@ -731,7 +806,8 @@ cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64
         }
     }
     cudaError_t e = cudaStreamSynchronize(S->stream);
-    return e == cudaSuccess ? CL_OK : sfail(CL_ERR_CUDA, std::string("surrogate_train: ") + cudaGetErrorString(e));
+    return e == cudaSuccess ? check_tc(S, "surrogate_train")
+                            : sfail(CL_ERR_CUDA, std::string("surrogate_train: ") + cudaGetErrorString(e));
 }
 
 cl_status surrogate_predict(cl_surrogate* S, const float* X, int64_t n, float* Y) {
@@ -749,7 +825,8 @@ cl_status surrogate_predict(cl_surrogate* S, const float* X, int64_t n, float* Y
     }
     cudaMemcpyAsync(Y, Yd, sizeof(float) * n * S->n_out, cudaMemcpyDeviceToHost, S->stream);
     cudaError_t e = cudaStreamSynchronize(S->stream);
-    return e == cudaSuccess ? CL_OK : sfail(CL_ERR_CUDA, std::string("surrogate_predict: ") + cudaGetErrorString(e));
+    return e == cudaSuccess ? check_tc(S, "surrogate_predict")
+                            : sfail(CL_ERR_CUDA, std::string("surrogate_predict: ") + cudaGetErrorString(e));
 }
 
 }  // extern "C"

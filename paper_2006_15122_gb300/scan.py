@@ -24,11 +24,17 @@ class ScanSpec:
     fstar_over_mp: float = 1.396
     omega_over_fstar: float = 5.13e-6
     kIR: float = 0.1
-    dt: float = 0.002
+    # Slices one inflaton half-period apart (pi in program units, where the inflaton
+    # mass is 1): phi^2, and with it w, the energy split and the burst-wise chi
+    # production, is sampled at one phase of the oscillation, so each observable
+    # varies slowly from slice to slice.  Slices a quarter period apart would
+    # alternate between kinetic and potential domination (w near +1, then -1).
+    # dt = pi/1571 is the VV4-stable step for q* <= 4e5 (omega_chi dt = 1.264 < 1.573).
+    dt: float = math.pi / 1571
     integrator: int = CL_INT_VV4
     precision: int = CL_FP32
     sizes: tuple = (32, 64, 96)
-    steps_per_slice: int = 782  # 64 slices to t = 100.1, the q = 1e4 workload's horizon
+    steps_per_slice: int = 1571  # 64 slices to t = 64 pi = 201, past the q = 1e4 workload's horizon t = 100
     n_slices: int = 64
     phi0: float = 1.0
     nmin: int = field(default=0)
@@ -158,18 +164,16 @@ def fit_surrogate(X, Y, width=256, depth=3, epochs=200, batch=512, lr=2e-3, lr_e
 
 def disagreement(pa, pb):
     """Error estimate of a surrogate answer from two independently trained
-    networks: per (query, slice), the largest of |eps_a - eps_b|, |w_a - w_b|
-    and the spectrum's |10^(a - b) - 1| over its 32 momenta."""
-    d_eps = np.abs(pa[..., 0] - pb[..., 0])
-    d_w = np.abs(pa[..., 1] - pb[..., 1])
-    d_spec = np.max(np.abs(10.0 ** (pa[..., 2:].astype(np.float64) - pb[..., 2:]) - 1.0), axis=-1)
-    return np.maximum(np.maximum(d_eps, d_w), d_spec)
+    networks: per (query, slice), the larger of |eps_a - eps_b| and |w_a - w_b|,
+    the two observables gated in absolute terms (the spectrum's error is judged
+    against its seed scatter, which one lattice run does not beat either)."""
+    return np.maximum(np.abs(pa[..., 0] - pb[..., 0]), np.abs(pa[..., 1] - pb[..., 1]))
 
 
 def answer_queries(nets, qs, times, q_range, spec, tol=0.02, frac=0.9, seeds=None, size=None, stream=None):
     """Observations at couplings qs and the given slice times, from the surrogate
     where it can be trusted and from the lattice otherwise.  A query falls back
-    to a plain lattice run (size `size`, default the largest of spec.sizes) when
+    to a plain lattice run (size `size`, default the middle one of spec.sizes) when
     its q lies outside the trained range q_range, or when the two networks
     disagree by more than tol on more than 1 - frac of its slices.  Returns
     (answers (Q, S, CL_OBS_SIZE), fallback mask, estimate (Q, S), seconds of
@@ -183,7 +187,7 @@ def answer_queries(nets, qs, times, q_range, spec, tol=0.02, frac=0.9, seeds=Non
     out = np.mean(preds, axis=0).astype(np.float32)
     lo, hi = q_range
     fallback = (np.asarray(qs) < lo) | (np.asarray(qs) > hi) | (np.mean(est <= tol, axis=1) < frac)
-    size = size or max(spec.sizes)
+    size = size or sorted(spec.sizes)[len(spec.sizes) // 2]
     seeds = seeds if seeds is not None else list(range(2 * 10 ** 6, 2 * 10 ** 6 + Q))
     t0 = time.perf_counter()
     for i in np.nonzero(fallback)[0]:

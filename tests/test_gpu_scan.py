@@ -115,3 +115,29 @@ def test_surrogate_answers_held_out_couplings():
     assert s["spectrum_rel"]["median"] < max(0.02, 1.5 * s["floor"]["spectrum_rel"]["median"]), s
     assert t_query * 50 < t_plain, (t_query, t_plain)
     net.close()
+
+
+def test_queries_outside_the_trained_range_or_in_disagreement_fall_back_to_the_lattice():
+    """answer_queries: a coupling outside the trained q range is answered by a
+    plain lattice run of the fallback size and seed, identical to running that
+    lattice directly; inside the range, where the two networks agree, the answer
+    is their mean prediction."""
+    spec = scan.ScanSpec(sizes=(32,), steps_per_slice=8, n_slices=8, kIR=0.2, dt=0.005)
+    n = 48
+    qs = scan.log_uniform_q(n, 1e2, 1e3, seed=7)
+    obs, times, _ = scan.ensemble_observations(spec, qs, [32] * n, list(range(n)))
+    X, Y = scan.training_pairs(qs, times, obs)
+    nets = [scan.fit_surrogate(X, Y, epochs=60, batch=128, seed=k)[0] for k in range(2)]
+    qh = np.array([300.0, 2e3])  # the second lies outside [min qs, max qs] (and is VV4-stable at this dt)
+    ans, fb, est, t_q, t_fb = scan.answer_queries(nets, qh, times, (qs.min(), qs.max()), spec, tol=0.02,
+                                                  seeds=[11, 12], size=32)
+    assert ans.shape == (2, spec.n_slices, cl.CL_OBS_SIZE) and est.shape == (2, spec.n_slices)
+    assert fb[1] and t_fb > 0
+    direct, _ = scan.plain_observations(spec, qh[1], 32, 12)
+    assert np.array_equal(ans[1], direct)
+    if not fb[0]:
+        Xq = np.stack([np.repeat(np.log10(qh[:1]), spec.n_slices), times], axis=1).astype(np.float32)
+        mean = 0.5 * (nets[0].predict(Xq) + nets[1].predict(Xq))
+        assert np.allclose(ans[0], mean, rtol=1e-6, atol=1e-6)
+    for net in nets:
+        net.close()
