@@ -67,7 +67,8 @@ __device__ __forceinline__ float gelu_prime_f(float x) {
 //    stage's mbarrier; the stage is refilled once that barrier has completed.
 //  - Epilogue: warp w reads accumulator rows 32 (w mod 4) .. +31 (the tensor-memory
 //    lanes its quarter of the SM may access), columns (w / 4) BN/2 .. +BN/2, with
-//    tcgen05.ld, and applies the bias / GELU of `mode`.
+//    tcgen05.ld into the freed stages; the CTA then applies the bias / GELU of
+//    `mode` row by row with coalesced stores.
 // Every mbarrier wait is bounded; a wait that gives up sets *err, and the CTA
 // still frees its tensor memory before it returns.
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 64;
@@ -176,8 +177,11 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
     ok = mbar_wait_bounded(&bar[(nk - 1) & 1], phase[(nk - 1) & 1]) && ok;
     tc_fence_after();
     if (!ok && lane == 0) atomicExch(err, 1);
+    // accumulator -> shared memory (the stages are free: every MMA has completed and
+    // every copy has landed), then row-wise coalesced stores with the epilogue
+    float* tile = reinterpret_cast<float*>(base);  // TC_BM rows of BN + 1 floats
+    const int TW = BN + 1;
     const int quarter = warp & 3, half = warp >> 2;
-    const int r = bm + 32 * quarter + lane;
     for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
         uint32_t v[16];
         const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
@@ -188,18 +192,19 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (r < g.M) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int c = bn + c0 + j;
-                if (c >= g.N) continue;
-                const bool valid = r < g.Mvalid && c < g.Nvalid;
-                float x = __uint_as_float(v[j]);
-                if (g.mode != 0) x = valid ? x + g.bias[c] : 0.f;
-                g.C[(size_t)r * g.ldc + c] = x;
-                if (g.mode == 1) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(valid ? gelu_f(x) : 0.f);
-            }
-        }
+        for (int j = 0; j < 16; ++j) tile[(32 * quarter + lane) * TW + c0 + j] = __uint_as_float(v[j]);
+    }
+    __syncthreads();
+    for (int i = tid; i < TC_BM * BN; i += TC_THREADS) {
+        const int rr = i / BN, cc = i - rr * BN;
+        const int r = bm + rr, c = bn + cc;
+        if (r >= g.M || c >= g.N) continue;
+        const bool valid = r < g.Mvalid && c < g.Nvalid;
+        float x = tile[rr * TW + cc];
+        if (g.mode != 0) x = valid ? x + g.bias[c] : 0.f;
+        g.C[(size_t)r * g.ldc + c] = x;
+        if (g.mode == 1) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(valid ? gelu_f(x) : 0.f);
     }
     tc_fence_before();
     __syncthreads();
