@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--scan-plain", type=int, default=6)
     p.add_argument("--scan-epochs", type=int, default=800)
     p.add_argument("--scan-save", default="", help="write the scan's observations and answers to this .npz")
+    p.add_argument("--surrogate", action="store_true",
+                   help="time the surrogate's training and queries alone (scan-shaped synthetic data)")
+    p.add_argument("--surrogate-epochs", type=int, default=400)
     p.add_argument("--accuracy", action="store_true",
                    help="print the Friedmann-constraint error of every integrator on the U(1) inflaton instead")
     p.add_argument("--acc-N", type=int, default=64)
@@ -572,6 +575,40 @@ def whole_job_rate(sites, steps, world, ms):
     return world * sites * steps / (ms / 1e3)
 
 
+def surrogate_measurement(args, stream):
+    """Training and query time of the surrogate network (2-256-256-256-34) on
+    synthetic data of the scan's shape: 32768 rows of (log10 q, t) -> 34 smooth
+    observables, batch 512, args.surrogate_epochs epochs, Adam with a cosine step size."""
+    import numpy as np
+    import torch
+
+    import paper_2006_15122_gb300 as cl
+
+    rng = np.random.default_rng(0)
+    n = 32768
+    X = np.stack([rng.uniform(2, 5, n), rng.uniform(0, 200, n)], axis=1).astype(np.float32)
+    k = np.linspace(0.5, 2.0, 32)
+    Y = np.concatenate([np.tanh(X[:, 1:] / 50.0 - X[:, :1] / 2.0), np.cos(X[:, 1:] / 30.0) * np.sin(X[:, :1]),
+                        np.log1p(np.abs(np.outer(X[:, 0], k) - X[:, 1:] / 60.0))], axis=1).astype(np.float32)
+    net = cl.Surrogate(2, 34, 256, 3, seed=0, stream=stream)
+    net.train(X[:1024], Y[:1024], epochs=2, batch=512)  # records the epoch graph of a small set
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = net.train(X, Y, epochs=args.surrogate_epochs, batch=512, lr=2e-3, lr_end=2e-5, shuffle=True)
+    t_train = time.perf_counter() - t0
+    net.predict(X[:4096])
+    t0 = time.perf_counter()
+    net.predict(X[:4096])
+    t_query = time.perf_counter() - t0
+    net.close()
+    steps = args.surrogate_epochs * (n // 512)
+    return {"metric": "surrogate training time", "value": t_train, "unit": "s", "higher_is_better": False,
+            "config": {"workload": "MLP 2-256-256-256-34 GELU on 32768 synthetic rows shaped like the scan's "
+                                   "training set, batch 512, %d epochs" % args.surrogate_epochs},
+            "us_per_minibatch": 1e6 * t_train / steps, "loss_first_last": [float(hist[0]), float(hist[-1])],
+            "query_4096_rows_ms": 1e3 * t_query}
+
+
 def run_scan(args):
     import torch
 
@@ -599,6 +636,11 @@ def main():
         N = args.gauge_N or (256 if args.gauge_only == "u1" else 128)
         print(json.dumps(gauge_measurement(args.gauge_only, N, args.gauge_steps, torch.cuda.current_stream())),
               flush=True)
+        return
+    if args.surrogate:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(surrogate_measurement(args, torch.cuda.current_stream())), flush=True)
         return
     if args.accuracy:
         import torch
@@ -666,6 +708,9 @@ def main():
         mm0 = lat.measure_means()
         reps = 3
         ph = {"set_stored": 0.0, "evolve": 0.0, "measure": 0.0}
+        uploads = []
+        for i, w in enumerate(which):  # one untimed pass over the host buffers
+            lat.set_stored(w, host[i], means[i])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -679,6 +724,7 @@ def main():
             tc = time.perf_counter()
             ph["set_stored"] += tb - ta
             ph["evolve"] += tc - tb
+            uploads.append(1e3 * (tb - ta))
         t1 = time.perf_counter()
         e2e = {"value": world * N ** 3 * reps / (t1 - t0), "unit": "site-updates/s",
                "h2d_bytes_per_step": 4 * 4 * N ** 3 + 4 * 8, "d2h_bytes_per_step": 320,
@@ -686,7 +732,7 @@ def main():
                        "lattice_set_stored, one VV4 step, lattice_measure_means D2H",
                "ms_per_step_phases": {"upload": 1e3 * ph["set_stored"] / reps,
                                       "step_and_measure": 1e3 * ph["evolve"] / reps},
-               "h2d_GBs": 4 * 4 * N ** 3 / (ph["set_stored"] / reps) / 1e9}
+               "h2d_GBs": 4 * 4 * N ** 3 / (ph["set_stored"] / reps) / 1e9, "upload_ms_per_rep": uploads}
         del host
     lat.close()
     cpu = None

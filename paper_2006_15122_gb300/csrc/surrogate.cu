@@ -35,11 +35,20 @@ struct GemmArgs {
     float* C;
     int ldc;
     int M, N, K;
-    int mode;           // 0: C = acc;  1: C = Z = acc + bias, H = bf16(GELU(Z));  2: C = acc + bias
+    int mode;           // 0: C = acc;  1: C = Z = acc + bias, H = bf16(GELU(Z));  2: C = acc + bias;
+                        // 3: C = dZ = acc GELU'(Zp), H = bf16(dZ) (the backward step through a hidden layer)
     const float* bias;  // length >= Nvalid
     bf16* H;
     int ldh;
     int Mvalid, Nvalid;  // outside: written as zero (keeps the padding zero)
+    const float* Zp;     // mode 3: pre-activations of the layer below (M x N, leading dimension ldz)
+    int ldz;
+    bf16* HT;            // optional: the bf16 output transposed, HT[c * ldht + r]
+    int ldht;
+    float* cs;           // optional: sums over this CTA's rows of each column of C, cs[blockIdx.y * ldcs + c]
+    int ldcs;
+    int kchunk;          // K per split (a multiple of 64): CTA z of the grid sums K range [z kchunk, (z+1) kchunk)
+    size_t cstride;      // and writes its partial C at C + z cstride (mode 0 only)
 };
 
 __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
@@ -58,23 +67,30 @@ __device__ __forceinline__ float gelu_prime_f(float x) {
 // One CTA of 256 threads owns a 128 x BN tile of C (BN = 32 or 64, so that the small
 // GEMMs of the network spread over many SMs):
 //  - K advances in chunks of 64, one 128-byte row of BF16 per tile row, through
-//    two shared-memory stages.  Every thread stages its share of a chunk with
+//    S <= 8 shared-memory stages, all filled at once when K <= 512 (the sizes of
+//    this network), so the loads of a tile are in flight together.  Every thread
+//    stages its share of a chunk with
 //    cp.async in the canonical K-major layout with 128-byte swizzle (8-row groups
 //    of 1024 bytes; the 16-byte piece c of row r sits at piece c ^ (r mod 8)),
 //    zero-filling rows beyond M or N and columns beyond K.
 //  - One thread issues the chunk's MMAs (K = 16 each; the operand descriptors
 //    advance 32 bytes per step inside the swizzle atom) and commits them to the
-//    stage's mbarrier; the stage is refilled once that barrier has completed.
+//    stage's mbarrier; a stage is refilled (K > 512) once that barrier has completed.
 //  - Epilogue: warp w reads accumulator rows 32 (w mod 4) .. +31 (the tensor-memory
 //    lanes its quarter of the SM may access), columns (w / 4) BN/2 .. +BN/2, with
 //    tcgen05.ld into the freed stages; the CTA then applies the bias / GELU of
 //    `mode` row by row with coalesced stores.
 // Every mbarrier wait is bounded; a wait that gives up sets *err, and the CTA
 // still frees its tensor memory before it returns.
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 64;
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 64, TC_MAXS = 8;
 
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int BN) { return (uint32_t)(TC_BM + BN) * 128u; }
-__host__ __device__ constexpr uint32_t tc_smem_bytes(int BN) { return 2u * tc_stage_bytes(BN) + 1024u; }
+// S stages, and room for the epilogue's TC_BM x (BN + 1) float tile, plus 1024 bytes of alignment slack
+__host__ __device__ constexpr uint32_t tc_smem_bytes(int BN, int S) {
+    return ((uint32_t)S * tc_stage_bytes(BN) > (uint32_t)TC_BM * (BN + 1) * 4u ? (uint32_t)S * tc_stage_bytes(BN)
+                                                                                : (uint32_t)TC_BM * (BN + 1) * 4u) +
+           1024u;
+}
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled
 // layout: start address, stride of 1024 bytes between 8-row groups, the sm_100
@@ -96,13 +112,14 @@ __device__ __forceinline__ uint32_t tc_idesc(int BN) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int BN, int* err) {
+__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int BN, int S, int* err) {
     extern __shared__ unsigned char tc_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[TC_MAXS];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bm = blockIdx.y * TC_BM, bn = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
     const uint32_t ncols = BN <= 32 ? 32u : 64u;
     const uint32_t stage = tc_stage_bytes(BN);
     if (warp == 0) {
@@ -112,8 +129,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < S; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -128,7 +144,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
             const bool isA = r < TC_BM;
             const int rr = isA ? r : r - TC_BM;
             const int grow = (isA ? bm : bn) + rr, kcol = k0 + c * 8;
-            const bool valid = grow < (isA ? g.M : g.N) && kcol < g.K;
+            const bool valid = grow < (isA ? g.M : g.N) && kcol < kend;
             const bf16* src = isA ? g.A + (size_t)(valid ? grow : 0) * g.lda + (valid ? kcol : 0)
                                   : g.B + (size_t)(valid ? grow : 0) * g.ldb + (valid ? kcol : 0);
             cp_async16_zfill(sa + r * 128 + ((c ^ (rr & 7)) << 4), src, valid);
@@ -136,21 +152,23 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
         cp_async_commit();
     };
 
-    const int nk = (g.K + TC_BK - 1) / TC_BK;
-    uint32_t phase[2] = {0u, 0u};
+    const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
+    uint32_t phase[TC_MAXS];
+    for (int k = 0; k < TC_MAXS; ++k) phase[k] = 0u;
     bool ok = true;
-    load(0, 0);
+    int issued = 0;
+    for (; issued < S && issued < nk; ++issued) load(issued, kbeg + issued * TC_BK);
     for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt & 1;
-        if (kt + 1 < nk) {
-            if (kt >= 1) {  // the other stage holds chunk kt-1: wait until its MMAs have read it
-                ok = mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1]) && ok;
-                phase[s ^ 1] ^= 1u;
-            }
-            load(s ^ 1, (kt + 1) * TC_BK);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        const int s = kt % S;
+        switch (issued - 1 - kt) {  // chunk kt has landed; later chunks may still be in flight
+            case 0: cp_async_wait<0>(); break;
+            case 1: cp_async_wait<1>(); break;
+            case 2: cp_async_wait<2>(); break;
+            case 3: cp_async_wait<3>(); break;
+            case 4: cp_async_wait<4>(); break;
+            case 5: cp_async_wait<5>(); break;
+            case 6: cp_async_wait<6>(); break;
+            default: cp_async_wait<7>(); break;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staged data -> tensor-core reads
         __syncthreads();
@@ -158,7 +176,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
             tc_fence_after();
             const uint32_t a0 = smem_u32(base + s * stage), b0 = a0 + TC_BM * 128;
             const uint32_t idesc = tc_idesc(BN);
-            const int ksteps = min(TC_BK, g.K - kt * TC_BK) / 16;
+            const int ksteps = min(TC_BK, kend - kbeg - kt * TC_BK) / 16;
             for (int k = 0; k < ksteps; ++k) {
                 const uint64_t ad = tc_smem_desc(a0 + 32u * k), bd = tc_smem_desc(b0 + 32u * k);
                 const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
@@ -172,9 +190,15 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
                              smem_u32(&bar[s]))
                          : "memory");
         }
+        if (kt + S < nk) {  // refill this stage with chunk kt + S once its MMAs have read it
+            ok = mbar_wait_bounded(&bar[s], phase[s]) && ok;
+            phase[s] ^= 1u;
+            load(s, kbeg + (kt + S) * TC_BK);
+            ++issued;
+        }
     }
     // the last commit completes after every MMA of the tile
-    ok = mbar_wait_bounded(&bar[(nk - 1) & 1], phase[(nk - 1) & 1]) && ok;
+    ok = mbar_wait_bounded(&bar[(nk - 1) % S], phase[(nk - 1) % S]) && ok;
     tc_fence_after();
     if (!ok && lane == 0) atomicExch(err, 1);
     // accumulator -> shared memory (the stages are free: every MMA has completed and
@@ -196,15 +220,57 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
         for (int j = 0; j < 16; ++j) tile[(32 * quarter + lane) * TW + c0 + j] = __uint_as_float(v[j]);
     }
     __syncthreads();
-    for (int i = tid; i < TC_BM * BN; i += TC_THREADS) {
-        const int rr = i / BN, cc = i - rr * BN;
-        const int r = bm + rr, c = bn + cc;
-        if (r >= g.M || c >= g.N) continue;
-        const bool valid = r < g.Mvalid && c < g.Nvalid;
-        float x = tile[rr * TW + cc];
-        if (g.mode != 0) x = valid ? x + g.bias[c] : 0.f;
-        g.C[(size_t)r * g.ldc + c] = x;
-        if (g.mode == 1) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(valid ? gelu_f(x) : 0.f);
+    float* const Cz = g.C + (size_t)blockIdx.z * g.cstride;
+    // C (and H) row by row; the tile then holds the value H is made of (0 outside).
+    // Eight elements per thread and round: their global operands (bias, Z of the
+    // layer below) are loaded together before the arithmetic.
+    constexpr int EU = 8;
+    for (int i0 = tid; i0 < TC_BM * BN; i0 += TC_THREADS * EU) {
+        float xin[EU], aux[EU];
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+            const int i = i0 + u * TC_THREADS;
+            const int rr = i / BN, cc = i - rr * BN;
+            const int r = bm + rr, c = bn + cc;
+            const bool in = i < TC_BM * BN && r < g.M && c < g.N;
+            const bool valid = in && r < g.Mvalid && c < g.Nvalid;
+            xin[u] = i < TC_BM * BN ? tile[rr * TW + cc] : 0.f;
+            aux[u] = 0.f;
+            if (valid && (g.mode == 1 || g.mode == 2)) aux[u] = __ldg(&g.bias[c]);
+            if (valid && g.mode == 3) aux[u] = __ldg(&g.Zp[(size_t)r * g.ldz + c]);
+        }
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+            const int i = i0 + u * TC_THREADS;
+            if (i >= TC_BM * BN) continue;
+            const int rr = i / BN, cc = i - rr * BN;
+            const int r = bm + rr, c = bn + cc;
+            float out = 0.f;
+            if (r < g.M && c < g.N) {
+                const bool valid = r < g.Mvalid && c < g.Nvalid;
+                float x = xin[u];
+                if (g.mode == 1 || g.mode == 2) x = valid ? x + aux[u] : 0.f;
+                if (g.mode == 3) x = valid ? x * gelu_prime_f(aux[u]) : 0.f;
+                Cz[(size_t)r * g.ldc + c] = x;
+                out = g.mode == 1 ? (valid ? gelu_f(x) : 0.f) : x;
+                if (g.mode == 1 || g.mode == 3) g.H[(size_t)r * g.ldh + c] = __float2bfloat16(out);
+            }
+            tile[rr * TW + cc] = out;
+        }
+    }
+    if (g.HT || g.cs) {
+        __syncthreads();
+        if (g.HT)  // transposed, coalesced along the rows of C
+            for (int i = tid; i < TC_BM * BN; i += TC_THREADS) {
+                const int rr = i % TC_BM, cc = i / TC_BM;
+                const int r = bm + rr, c = bn + cc;
+                if (r < g.M && c < g.N) g.HT[(size_t)c * g.ldht + r] = __float2bfloat16(tile[rr * TW + cc]);
+            }
+        if (g.cs && tid < BN && bn + tid < g.N) {  // fixed order over the tile's rows
+            float sum = 0.f;
+            for (int rr = 0; rr < TC_BM; ++rr) sum += tile[rr * TW + tid];
+            g.cs[(size_t)blockIdx.y * g.ldcs + bn + tid] = sum;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -213,23 +279,14 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
 }
 
 // ---------------------------------------------------------------- helpers
-__global__ void transpose_bf16_kernel(const bf16* in, int ldi, bf16* out, int ldo, int R, int Cc) {
-    __shared__ bf16 t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        t[k][threadIdx.x] = (r < R && c < Cc) ? in[(size_t)r * ldi + c] : __float2bfloat16(0.f);
+// BF16 copies of a weight matrix (rows x cols) and of its transpose
+__global__ void weights_to_bf16_kernel(const float* W, bf16* Wb, bf16* WbT, int rows, int cols) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)rows * cols; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const bf16 v = __float2bfloat16(W[i]);
+        Wb[i] = v;
+        WbT[(size_t)c * rows + r] = v;
     }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (c < Cc && r < R) out[(size_t)c * ldo + r] = t[threadIdx.x][k];
-    }
-}
-
-__global__ void f32_to_bf16_kernel(const float* in, bf16* out, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16(in[i]);
 }
 
 // standardized inputs into the padded bf16 H_0 (rows >= n and columns >= n_in are zero)
@@ -239,51 +296,86 @@ __device__ __forceinline__ size_t sample_row(const int* idx, int64_t r0, int r) 
 }
 
 __global__ void load_inputs_kernel(const float* X, const int* idx, int64_t r0, int n, int n_in, const float* mu,
-                                   const float* sd, bf16* H0, int ld, int Bp) {
+                                   const float* sd, bf16* H0, int ld, int Bp, bf16* H0T) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)Bp * ld; i += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / ld), c = (int)(i % ld);
         float v = 0.f;
         if (r < n && c < n_in) v = (X[sample_row(idx, r0, r) * n_in + c] - mu[c]) / sd[c];
         H0[i] = __float2bfloat16(v);
+        if (H0T) H0T[(size_t)c * Bp + r] = __float2bfloat16(v);  // the transpose for the weight gradient
     }
 }
 
-// dY = 2 (Y - T_std) / (n n_out) into fp32 and bf16 (padding zero), and the loss sum
-__global__ void loss_grad_kernel(const float* Y, int ldy, const float* T, const int* idx, int64_t r0, int n, int n_out,
-                                 const float* mu, const float* sd, float* dZ, bf16* dZb, int ld, int Bp, double* loss) {
+// dY = 2 (Y - T_std) / (n n_out) into fp32, bf16 and transposed bf16 (padding zero),
+// the loss sum, and per 128-row tile the column sums of dY in a fixed order (the
+// output bias gradient; cs[blockIdx.x * ld + c]).  One block per 128 x 64 tile
+// (grid: row tiles x column tiles), coalesced along the columns; the transposed
+// copy and the column sums go through a shared-memory tile.
+__global__ void __launch_bounds__(256) loss_grad_kernel(const float* Y, int ldy, const float* T, const int* idx,
+                                                        int64_t r0, int n, int n_out, const float* mu, const float* sd,
+                                                        float* dZ, bf16* dZb, bf16* dZbT, int ld, int Bp, float* cs,
+                                                        double* loss) {
+    __shared__ float tile[TC_BM][65];
     double s = 0.0;
     const float scale = 2.0f / ((float)n * (float)n_out);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)Bp * ld; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / ld), c = (int)(i % ld);
-        float g = 0.f;
-        if (r < n && c < n_out) {
-            const float d = Y[(size_t)r * ldy + c] - (T[sample_row(idx, r0, r) * n_out + c] - mu[c]) / sd[c];
-            s += (double)d * d;
-            g = scale * d;
+    const int rbeg = blockIdx.x * TC_BM, cbeg = blockIdx.y * 64;
+    constexpr int EU = 8;  // elements per thread and round, their loads issued together
+    for (int i0 = threadIdx.x; i0 < TC_BM * 64; i0 += blockDim.x * EU) {
+        float yv[EU], tv[EU];
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+            const int i = i0 + u * blockDim.x, rr = i >> 6, cc = i & 63, r = rbeg + rr, c = cbeg + cc;
+            const bool in = i < TC_BM * 64 && r < n && c < n_out;
+            yv[u] = in ? __ldg(&Y[(size_t)r * ldy + c]) : 0.f;
+            tv[u] = in ? __ldg(&T[sample_row(idx, r0, r) * n_out + c]) : 0.f;
         }
-        dZ[i] = g;
-        dZb[i] = __float2bfloat16(g);
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+            const int i = i0 + u * blockDim.x, rr = i >> 6, cc = i & 63, r = rbeg + rr, c = cbeg + cc;
+            if (i >= TC_BM * 64) continue;
+            float g = 0.f;
+            if (r < Bp && c < ld) {
+                if (r < n && c < n_out) {
+                    const float d = yv[u] - (tv[u] - mu[c]) / sd[c];
+                    s += (double)d * d;
+                    g = scale * d;
+                }
+                dZ[(size_t)r * ld + c] = g;
+                dZb[(size_t)r * ld + c] = __float2bfloat16(g);
+            }
+            tile[rr][cc] = g;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TC_BM * 64; i += blockDim.x) {
+        const int rr = i % TC_BM, cc = i / TC_BM, r = rbeg + rr, c = cbeg + cc;
+        if (r < Bp && c < ld) dZbT[(size_t)c * Bp + r] = __float2bfloat16(tile[rr][cc]);
+    }
+    if (threadIdx.x < 64 && cbeg + threadIdx.x < ld) {
+        float csum = 0.f;
+        for (int rr = 0; rr < TC_BM; ++rr) csum += tile[rr][threadIdx.x];
+        cs[(size_t)blockIdx.x * ld + cbeg + threadIdx.x] = csum;
     }
     s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(loss, s);
 }
 
-// dZ = dH * GELU'(Z) (fp32 and bf16)
-__global__ void gelu_back_kernel(const float* dH, const float* Z, float* dZ, bf16* dZb, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float g = dH[i] * gelu_prime_f(Z[i]);
-        dZ[i] = g;
-        dZb[i] = __float2bfloat16(g);
+// weight gradients: the split-K partials summed in order into the first one
+__global__ void weight_grad_kernel(float* gW, int ksplit, size_t nw) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (size_t)gridDim.x * blockDim.x) {
+        float s = gW[i];
+        for (int z = 1; z < ksplit; ++z) s += gW[(size_t)z * nw + i];
+        gW[i] = s;
     }
 }
 
-// column sums of dZ (rows < Bp) -> bias gradient
-__global__ void colsum_kernel(const float* dZ, int ld, int rows, int cols, float* out) {
+// bias gradients: the tile column sums summed in tile order
+__global__ void bias_grad_kernel(const float* cs, int ntiles, int cols, float* gb) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cols) return;
     float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += dZ[(size_t)r * ld + c];
-    out[c] = s;
+    for (int m = 0; m < ntiles; ++m) s += cs[(size_t)m * cols + c];
+    gb[c] = s;
 }
 
 // Optimizer state on the device, so that a captured training epoch can be
@@ -297,26 +389,67 @@ struct TrainDev {
     int tc_err;  // a tensor-core GEMM gave up waiting for its MMAs (never expected)
 };
 
-// Adam on FP32 master weights; the BF16 copy (when wb != NULL) is refreshed in
-// the same pass.  decay = 1 applies the L2 coefficient (weights), 0 not (biases).
-__global__ void adam_kernel(float* w, const float* g, float* m, float* v, size_t n, const TrainDev* td, int decay,
-                            bf16* wb) {
+// Adam on FP32 master weights for every layer in one launch: weights (L2 decay)
+// with their BF16 copy and its transpose refreshed, then biases, whose gradient
+// is the sum of the tile column sums in tile order.
+constexpr int kMaxLayers = 17;
+struct AdamLayer {
+    float *W, *gW, *mW, *vW, *b, *mb, *vb;
+    const float* cs;
+    bf16 *Wb, *WbT;
+    int rows, cols, ntiles;
+    int ksplit;  // gW holds ksplit partial gradients of rows x cols, summed in order
+};
+struct AdamArgs {
+    AdamLayer l[kMaxLayers];
+    int L;
+    const TrainDev* td;
+};
+
+__global__ void adam_all_kernel(const AdamArgs A) {
+    const TrainDev* td = A.td;
     const float t = (float)(td->t + 1);
-    const float b1 = td->b1, b2 = td->b2, eps = td->eps, wd = decay ? td->wd : 0.f;
+    const float b1 = td->b1, b2 = td->b2, eps = td->eps;
     const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
     float lr = td->lr;
     if (td->lr_end >= 0.f)
         lr = td->lr_end + 0.5f * (td->lr - td->lr_end) *
                               (1.f + cospif((float)td->sched / (float)(td->total > 0 ? td->total : 1)));
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float gi = g[i] + wd * w[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float wn = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        w[i] = wn;
-        if (wb) wb[i] = __float2bfloat16(wn);
+    size_t total = 0;
+    for (int l = 0; l < A.L; ++l) total += (size_t)A.l[l].rows * (A.l[l].cols + 1);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        size_t k = i;
+        int l = 0;
+        while (k >= (size_t)A.l[l].rows * (A.l[l].cols + 1)) {
+            k -= (size_t)A.l[l].rows * (A.l[l].cols + 1);
+            ++l;
+        }
+        const AdamLayer& Ly = A.l[l];
+        const size_t nw = (size_t)Ly.rows * Ly.cols;
+        float *w, *m, *v, gi;
+        if (k < nw) {
+            w = Ly.W + k; m = Ly.mW + k; v = Ly.vW + k;
+            gi = 0.f;
+            for (int z = 0; z < Ly.ksplit; ++z) gi += Ly.gW[(size_t)z * nw + k];
+            gi += td->wd * *w;
+        } else {
+            const int o = (int)(k - nw);
+            w = Ly.b + o; m = Ly.mb + o; v = Ly.vb + o;
+            gi = 0.f;
+            for (int mt = 0; mt < Ly.ntiles; ++mt) gi += Ly.cs[(size_t)mt * Ly.rows + o];
+        }
+        const float mi = b1 * *m + (1.f - b1) * gi;
+        const float vi = b2 * *v + (1.f - b2) * gi * gi;
+        *m = mi;
+        *v = vi;
+        const float wn = *w - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        *w = wn;
+        if (k < nw) {
+            const bf16 hb = __float2bfloat16(wn);
+            const int r = (int)(k / Ly.cols), c = (int)(k % Ly.cols);
+            Ly.Wb[k] = hb;
+            Ly.WbT[(size_t)c * Ly.rows + r] = hb;
+        }
     }
 }
 
@@ -363,11 +496,11 @@ struct cl_surrogate {
     int Bp = 0;  // batch capacity (padded)
     std::vector<float*> Z;         // per layer: Bp x P[l+1] fp32
     std::vector<cl::bf16*> H;      // per layer input: Bp x P[l] bf16
-    std::vector<cl::bf16*> HT;     // transposes: P[l] x Bp
-    float* dZ = nullptr;           // Bp x maxP fp32
-    float* dH = nullptr;           // Bp x maxP fp32
-    cl::bf16* dZb = nullptr;       // Bp x maxP
-    cl::bf16* dZbT = nullptr;      // maxP x Bp
+    std::vector<cl::bf16*> HT;     // transposes: P[l] x Bp (written by the producing kernel)
+    std::vector<float*> cs;        // per layer: column sums of dZ_l per 128-row tile (bias gradients)
+    float* dZ[2] = {nullptr, nullptr};          // Bp x maxP fp32, alternating between layers
+    cl::bf16* dZb[2] = {nullptr, nullptr};      // Bp x maxP
+    cl::bf16* dZbT[2] = {nullptr, nullptr};     // maxP x Bp
     float *Xd = nullptr, *Td = nullptr;  // raw data (n x n_in / n x n_out) for the current call
     size_t cap_n = 0;
     float *mu_in, *sd_in, *mu_out, *sd_out;  // standardization (device, length n_in / n_out)
@@ -397,20 +530,56 @@ cl_status sfail(cl_status s, const std::string& m) {
     return s;
 }
 
+// Optional fused outputs of a GEMM: the pre-activations of mode 3, the
+// transposed bf16 output, the per-tile column sums.
+struct GemmExtra {
+    const float* Zp = nullptr;
+    int ldz = 0;
+    cl::bf16* HT = nullptr;
+    int ldht = 0;
+    float* cs = nullptr;
+    int ldcs = 0;
+    int kchunk = 0;  // > 0: split K into chunks of this size, partial C matrices one after the other
+};
+
+// Split-K of the weight-gradient GEMMs (K = the batch): up to 4 splits of at least
+// 128 rows, so that more CTAs share the longest K loops.
+constexpr int kMaxSplits = 4;
+inline int dw_kchunk(int Bp) {
+    const int want = std::min(kMaxSplits, (Bp + 127) / 128);
+    return (Bp + want * cl::TC_BK - 1) / (want * cl::TC_BK) * cl::TC_BK;
+}
+inline int dw_splits(int Bp) { return (Bp + dw_kchunk(Bp) - 1) / dw_kchunk(Bp); }
+
 void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ldb, float* C, int ldc, int M, int N,
-          int K, int mode, const float* bias, cl::bf16* H, int ldh, int Mvalid, int Nvalid) {
+          int K, int mode, const float* bias, cl::bf16* H, int ldh, int Mvalid, int Nvalid,
+          const GemmExtra& x = GemmExtra()) {
     cl::GemmArgs g;
     g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc; g.M = M; g.N = N; g.K = K;
     g.mode = mode; g.bias = bias; g.H = H; g.ldh = ldh; g.Mvalid = Mvalid; g.Nvalid = Nvalid;
+    g.Zp = x.Zp; g.ldz = x.ldz; g.HT = x.HT; g.ldht = x.ldht; g.cs = x.cs; g.ldcs = x.ldcs;
+    g.kchunk = x.kchunk > 0 ? x.kchunk : K;
+    g.cstride = (size_t)M * ldc;
+    const int splits = (K + g.kchunk - 1) / g.kchunk;
     const int BN = N <= 32 ? 32 : cl::TC_BN;  // N is a multiple of 32
-    static bool attr_set = false;  // the stage pair needs the opt-in shared-memory size
+    const int nk = (g.kchunk + cl::TC_BK - 1) / cl::TC_BK;
+    const int stages = nk < cl::TC_MAXS ? nk : cl::TC_MAXS;
+    static bool attr_set = false;  // the stage ring needs the opt-in shared-memory size
     if (!attr_set) {
         cudaFuncSetAttribute(cl::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cl::tc_smem_bytes(cl::TC_BN));
+                             (int)cl::tc_smem_bytes(cl::TC_BN, cl::TC_MAXS));
+        // one shared-memory carveout for every kernel of a training step, so that
+        // consecutive launches need no reconfiguration of the SMs' L1/shared split
+        const void* fns[] = {(const void*)cl::gemm_tc_kernel, (const void*)cl::loss_grad_kernel,
+                             (const void*)cl::adam_all_kernel, (const void*)cl::adam_advance_kernel,
+                             (const void*)cl::load_inputs_kernel};
+        for (const void* f : fns) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaGetLastError();
         attr_set = true;
     }
-    dim3 grid((N + BN - 1) / BN, (M + cl::TC_BM - 1) / cl::TC_BM);
-    cl::gemm_tc_kernel<<<grid, cl::TC_THREADS, cl::tc_smem_bytes(BN), S->stream>>>(g, BN, &S->tdev->tc_err);
+    dim3 grid((N + BN - 1) / BN, (M + cl::TC_BM - 1) / cl::TC_BM, splits);
+    cl::gemm_tc_kernel<<<grid, cl::TC_THREADS, cl::tc_smem_bytes(BN, stages), S->stream>>>(g, BN, stages,
+                                                                                             &S->tdev->tc_err);
 }
 
 // CL_ERR_TIMEOUT when a tensor-core GEMM of the last call gave up waiting (after a synchronize)
@@ -422,21 +591,19 @@ cl_status check_tc(cl_surrogate* S, const char* who) {
     return CL_OK;
 }
 
-void transpose(cl_surrogate* S, const cl::bf16* in, int ldi, cl::bf16* out, int ldo, int R, int C) {
-    dim3 grid((C + 31) / 32, (R + 31) / 32);
-    cl::transpose_bf16_kernel<<<grid, dim3(32, 8), 0, S->stream>>>(in, ldi, out, ldo, R, C);
-}
-
 cl_status ensure_batch(cl_surrogate* S, int n) {
     const int Bp = (n + 63) / 64 * 64;
     if (Bp <= S->Bp) return CL_OK;
     for (auto p : S->Z) cudaFree(p);
     for (auto p : S->H) cudaFree(p);
     for (auto p : S->HT) cudaFree(p);
-    cudaFree(S->dZ); cudaFree(S->dH); cudaFree(S->dZb); cudaFree(S->dZbT);
+    for (auto p : S->cs) cudaFree(p);
+    for (int k = 0; k < 2; ++k) { cudaFree(S->dZ[k]); cudaFree(S->dZb[k]); cudaFree(S->dZbT[k]); }
     S->Z.assign(S->L, nullptr);
     S->H.assign(S->L, nullptr);
     S->HT.assign(S->L, nullptr);
+    S->cs.assign(S->L, nullptr);
+    const int ntiles = (Bp + cl::TC_BM - 1) / cl::TC_BM;
     int maxP = 0;
     for (int p : S->P) maxP = std::max(maxP, p);
     bool ok = true;
@@ -444,11 +611,13 @@ cl_status ensure_batch(cl_surrogate* S, int n) {
         ok = ok && cudaMalloc(&S->Z[l], sizeof(float) * Bp * S->P[l + 1]) == cudaSuccess;
         ok = ok && cudaMalloc(&S->H[l], sizeof(cl::bf16) * Bp * S->P[l]) == cudaSuccess;
         ok = ok && cudaMalloc(&S->HT[l], sizeof(cl::bf16) * Bp * S->P[l]) == cudaSuccess;
+        ok = ok && cudaMalloc(&S->cs[l], sizeof(float) * ntiles * S->P[l + 1]) == cudaSuccess;
     }
-    ok = ok && cudaMalloc(&S->dZ, sizeof(float) * Bp * maxP) == cudaSuccess;
-    ok = ok && cudaMalloc(&S->dH, sizeof(float) * Bp * maxP) == cudaSuccess;
-    ok = ok && cudaMalloc(&S->dZb, sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
-    ok = ok && cudaMalloc(&S->dZbT, sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        ok = ok && cudaMalloc(&S->dZ[k], sizeof(float) * Bp * maxP) == cudaSuccess;
+        ok = ok && cudaMalloc(&S->dZb[k], sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
+        ok = ok && cudaMalloc(&S->dZbT[k], sizeof(cl::bf16) * Bp * maxP) == cudaSuccess;
+    }
     if (!ok) return sfail(CL_ERR_OOM, "surrogate: activation buffers");
     S->Bp = Bp;
     ++S->gen;
@@ -468,44 +637,90 @@ cl_status ensure_data(cl_surrogate* S, size_t n) {
 }
 
 void refresh_bf16(cl_surrogate* S) {
-    for (int l = 0; l < S->L; ++l) {
-        const size_t n = (size_t)S->P[l + 1] * S->P[l];
-        cl::f32_to_bf16_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->W[l], S->Wb[l], n);
-    }
+    for (int l = 0; l < S->L; ++l)
+        cl::weights_to_bf16_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->W[l], S->Wb[l], S->WbT[l], S->P[l + 1],
+                                                                       S->P[l]);
 }
 
 // forward over batch rows r = 0..n-1, sample idx[r0 + r] (r0 + r without idx) of
-// the data in S->Xd, standardized by mu/sd
-void forward(cl_surrogate* S, const int* idx, int64_t r0, int n) {
+// the data in S->Xd, standardized by mu/sd; `training` also writes the transposed
+// activations that the weight gradients read
+void forward(cl_surrogate* S, const int* idx, int64_t r0, int n, bool training) {
     cl::load_inputs_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->Xd, idx, r0, n, S->n_in, S->mu_in, S->sd_in, S->H[0],
-                                                              S->P[0], S->Bp);
+                                                              S->P[0], S->Bp, training ? S->HT[0] : nullptr);
     for (int l = 0; l < S->L; ++l) {
         const bool last = l == S->L - 1;
+        GemmExtra x;
+        if (training && !last) {
+            x.HT = S->HT[l + 1];
+            x.ldht = S->Bp;
+        }
         gemm(S, S->H[l], S->P[l], S->Wb[l], S->P[l], S->Z[l], S->P[l + 1], S->Bp, S->P[l + 1], S->P[l], last ? 2 : 1,
-             S->b[l], last ? nullptr : S->H[l + 1], S->P[l + 1], n, S->d[l + 1]);
+             S->b[l], last ? nullptr : S->H[l + 1], S->P[l + 1], n, S->d[l + 1], x);
     }
 }
 
-// backward: gradients of the mean squared error into gW, gb (loss sum added into S->dloss)
+// backward: weight gradients into gW, the bias gradients as tile column sums in
+// cs (summed by the optimizer, or by bias_grads); loss sum added into S->dloss.
+// Per layer two GEMMs: dW_l = dZ_l^T H_l, and dZ_{l-1} = (dZ_l W_l) GELU'(Z_{l-1})
+// with the elementwise factor, the transposed copy and the column sums fused
+// into its epilogue.
 void backward(cl_surrogate* S, const int* idx, int64_t r0, int n) {
     const int L = S->L, Bp = S->Bp;
-    cl::loss_grad_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->Z[L - 1], S->P[L], S->Td, idx, r0, n, S->n_out,
-                                                            S->mu_out, S->sd_out, S->dZ, S->dZb, S->P[L], Bp,
-                                                            S->dloss);
+    const int ntiles = (Bp + cl::TC_BM - 1) / cl::TC_BM;
+    int cur = 0;
+    cl::loss_grad_kernel<<<dim3(ntiles, (S->P[L] + 63) / 64), 256, 0, S->stream>>>(
+        S->Z[L - 1], S->P[L], S->Td, idx, r0, n, S->n_out, S->mu_out, S->sd_out, S->dZ[cur], S->dZb[cur],
+        S->dZbT[cur], S->P[L], Bp, S->cs[L - 1], S->dloss);
     for (int l = L - 1; l >= 0; --l) {
         const int Pin = S->P[l], Pout = S->P[l + 1];
-        // bias gradient and weight gradient dW = dZ^T H_l
-        cl::colsum_kernel<<<(Pout + 127) / 128, 128, 0, S->stream>>>(S->dZ, Pout, Bp, Pout, S->gb[l]);
-        transpose(S, S->dZb, Pout, S->dZbT, Bp, Bp, Pout);
-        transpose(S, S->H[l], Pin, S->HT[l], Bp, Bp, Pin);
-        gemm(S, S->dZbT, Bp, S->HT[l], Bp, S->gW[l], Pin, Pout, Pin, Bp, 0, nullptr, nullptr, 0, Pout, Pin);
+        GemmExtra xw;
+        xw.kchunk = dw_kchunk(Bp);  // partial gradients, summed by the optimizer
+        gemm(S, S->dZbT[cur], Bp, S->HT[l], Bp, S->gW[l], Pin, Pout, Pin, Bp, 0, nullptr, nullptr, 0, Pout, Pin, xw);
         if (l > 0) {
-            // dH = dZ W_l, then dZ_{l-1} = dH * GELU'(Z_{l-1})
-            transpose(S, S->Wb[l], Pin, S->WbT[l], Pout, Pout, Pin);
-            gemm(S, S->dZb, Pout, S->WbT[l], Pout, S->dH, Pin, Bp, Pin, Pout, 0, nullptr, nullptr, 0, Bp, Pin);
-            cl::gelu_back_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->dH, S->Z[l - 1], S->dZ, S->dZb, (size_t)Bp * Pin);
+            GemmExtra x;
+            x.Zp = S->Z[l - 1];
+            x.ldz = Pin;
+            x.HT = S->dZbT[1 - cur];
+            x.ldht = Bp;
+            x.cs = S->cs[l - 1];
+            x.ldcs = Pin;
+            gemm(S, S->dZb[cur], Pout, S->WbT[l], Pout, S->dZ[1 - cur], Pin, Bp, Pin, Pout, 3, nullptr, S->dZb[1 - cur],
+                 Pin, n, S->d[l], x);
+            cur = 1 - cur;
         }
     }
+}
+
+cl::AdamArgs adam_args(cl_surrogate* S) {
+    cl::AdamArgs a;
+    memset(&a, 0, sizeof(a));
+    a.L = S->L;
+    a.td = S->tdev;
+    const int ntiles = (S->Bp + cl::TC_BM - 1) / cl::TC_BM;
+    for (int l = 0; l < S->L; ++l) {
+        cl::AdamLayer& y = a.l[l];
+        y.W = S->W[l]; y.gW = S->gW[l]; y.mW = S->mW[l]; y.vW = S->vW[l];
+        y.b = S->b[l]; y.mb = S->mb[l]; y.vb = S->vb[l];
+        y.cs = S->cs[l];
+        y.Wb = S->Wb[l]; y.WbT = S->WbT[l];
+        y.rows = S->P[l + 1];
+        y.cols = S->P[l];
+        y.ntiles = ntiles;
+        y.ksplit = dw_splits(S->Bp);
+    }
+    return a;
+}
+
+// bias gradients gb from the tile column sums and the weight gradients from the
+// split partials (for the gradient query)
+void bias_grads(cl_surrogate* S) {
+    for (int l = 0; l < S->L; ++l)
+        cl::weight_grad_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->gW[l], dw_splits(S->Bp),
+                                                                  (size_t)S->P[l + 1] * S->P[l]);
+    const int ntiles = (S->Bp + cl::TC_BM - 1) / cl::TC_BM;
+    for (int l = 0; l < S->L; ++l)
+        cl::bias_grad_kernel<<<(S->P[l + 1] + 127) / 128, 128, 0, S->stream>>>(S->cs[l], ntiles, S->P[l + 1], S->gb[l]);
 }
 
 void set_identity_scaling(cl_surrogate* S) {
@@ -535,7 +750,8 @@ cl_status surrogate_destroy(cl_surrogate* S) {
     for (auto p : S->Z) cudaFree(p);
     for (auto p : S->H) cudaFree(p);
     for (auto p : S->HT) cudaFree(p);
-    cudaFree(S->dZ); cudaFree(S->dH); cudaFree(S->dZb); cudaFree(S->dZbT);
+    for (auto p : S->cs) cudaFree(p);
+    for (int k = 0; k < 2; ++k) { cudaFree(S->dZ[k]); cudaFree(S->dZb[k]); cudaFree(S->dZbT[k]); }
     cudaFree(S->Xd); cudaFree(S->Td);
     cudaFree(S->mu_in); cudaFree(S->sd_in); cudaFree(S->mu_out); cudaFree(S->sd_out);
     cudaFree(S->dloss);
@@ -569,7 +785,7 @@ cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t d
         const size_t nw = (size_t)S->P[l + 1] * S->P[l], nb = S->P[l + 1];
         float *w, *gw, *mw, *vw, *bb, *gbb, *mbb, *vbb;
         cl::bf16 *wb, *wbt;
-        ok = ok && cudaMalloc(&w, nw * 4) == cudaSuccess && cudaMalloc(&gw, nw * 4) == cudaSuccess &&
+        ok = ok && cudaMalloc(&w, nw * 4) == cudaSuccess && cudaMalloc(&gw, nw * 4 * kMaxSplits) == cudaSuccess &&
              cudaMalloc(&mw, nw * 4) == cudaSuccess && cudaMalloc(&vw, nw * 4) == cudaSuccess &&
              cudaMalloc(&bb, nb * 4) == cudaSuccess && cudaMalloc(&gbb, nb * 4) == cudaSuccess &&
              cudaMalloc(&mbb, nb * 4) == cudaSuccess && cudaMalloc(&vbb, nb * 4) == cudaSuccess &&
@@ -578,7 +794,7 @@ cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t d
         S->W.push_back(w); S->gW.push_back(gw); S->mW.push_back(mw); S->vW.push_back(vw);
         S->b.push_back(bb); S->gb.push_back(gbb); S->mb.push_back(mbb); S->vb.push_back(vbb);
         S->Wb.push_back(wb); S->WbT.push_back(wbt);
-        cudaMemsetAsync(gw, 0, nw * 4, S->stream); cudaMemsetAsync(mw, 0, nw * 4, S->stream);
+        cudaMemsetAsync(gw, 0, nw * 4 * kMaxSplits, S->stream); cudaMemsetAsync(mw, 0, nw * 4, S->stream);
         cudaMemsetAsync(vw, 0, nw * 4, S->stream); cudaMemsetAsync(bb, 0, nb * 4, S->stream);
         cudaMemsetAsync(gbb, 0, nb * 4, S->stream); cudaMemsetAsync(mbb, 0, nb * 4, S->stream);
         cudaMemsetAsync(vbb, 0, nb * 4, S->stream);
@@ -672,8 +888,9 @@ cl_status surrogate_loss_grad(cl_surrogate* S, const float* X, const float* T, i
     cudaMemcpyAsync(S->Xd, X, sizeof(float) * n * S->n_in, cudaMemcpyHostToDevice, S->stream);
     cudaMemcpyAsync(S->Td, T, sizeof(float) * n * S->n_out, cudaMemcpyHostToDevice, S->stream);
     cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
-    forward(S, nullptr, 0, (int)n);
+    forward(S, nullptr, 0, (int)n, true);
     backward(S, nullptr, 0, (int)n);
+    bias_grads(S);
     double l = 0;
     cudaMemcpyAsync(&l, S->dloss, sizeof(double), cudaMemcpyDeviceToHost, S->stream);
     cudaError_t e = cudaStreamSynchronize(S->stream);
@@ -759,15 +976,9 @@ cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64
             const int* idx = shuf ? S->d_perm : nullptr;
             for (int64_t r0 = 0; r0 < n; r0 += bs) {
                 const int nb = (int)std::min<int64_t>(bs, n - r0);
-                forward(S, idx, r0, nb);
+                forward(S, idx, r0, nb, true);
                 backward(S, idx, r0, nb);
-                for (int l = 0; l < S->L; ++l) {
-                    const size_t nw = (size_t)S->P[l + 1] * S->P[l];
-                    cl::adam_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->W[l], S->gW[l], S->mW[l], S->vW[l], nw,
-                                                                       S->tdev, 1, S->Wb[l]);
-                    cl::adam_kernel<<<1, 256, 0, S->stream>>>(S->b[l], S->gb[l], S->mb[l], S->vb[l], S->P[l + 1],
-                                                              S->tdev, 0, nullptr);
-                }
+                cl::adam_all_kernel<<<S->sms * 2, 256, 0, S->stream>>>(adam_args(S));
                 cl::adam_advance_kernel<<<1, 1, 0, S->stream>>>(S->tdev);
             }
             e = cudaStreamEndCapture(S->stream, &graph);
@@ -824,7 +1035,7 @@ cl_status surrogate_predict(cl_surrogate* S, const float* X, int64_t n, float* Y
     cudaMemcpyAsync(S->Xd, X, sizeof(float) * n * S->n_in, cudaMemcpyHostToDevice, S->stream);
     for (int64_t r0 = 0; r0 < n; r0 += S->Bp) {
         const int nb = (int)std::min<int64_t>(S->Bp, n - r0);
-        forward(S, nullptr, r0, nb);
+        forward(S, nullptr, r0, nb, false);
         cl::destandardize_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->Z[S->L - 1], S->P[S->L], nb, S->n_out, S->mu_out,
                                                                     S->sd_out, Yd + r0 * S->n_out);
     }

@@ -149,7 +149,7 @@ def test_training_fits_a_smooth_map_and_predict_undoes_standardization():
     c = r.uniform(10.0, 100.0, 34)
     Y = c * np.tanh(np.array([[1.0, 0.01]]) * X @ A) + 5.0 * c
     net = cl.Surrogate(2, 34, 256, 3, seed=4)
-    hist = net.train(X[:3584], Y[:3584], epochs=60, batch=256, lr=2e-3)
+    hist = net.train(X[:3584], Y[:3584], epochs=100, batch=256, lr=2e-3)
     assert np.all(np.isfinite(hist)) and hist[-1] < 1e-2 * hist[0], hist[[0, -1]]
     P = net.predict(X[3584:]).astype(np.float64)
     err = np.sqrt(np.mean((P - Y[3584:]) ** 2, axis=0)) / Y[:3584].std(axis=0)
