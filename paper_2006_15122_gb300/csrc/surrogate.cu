@@ -64,7 +64,7 @@ __device__ __forceinline__ float gelu_prime_f(float x) {
 // ---------------------------------------------------------------- GEMM (tcgen05)
 // C[M x N] = A[M x K] . B[N x K]^T on the fifth-generation tensor cores
 // (tcgen05.mma, kind::f16 with BF16 operands, FP32 accumulator in tensor memory).
-// One CTA of 256 threads owns a 128 x BN tile of C (BN = 32 or 64, so that the small
+// One CTA of 256 threads owns a 128 x BN tile of C (BN = 32, so that the small
 // GEMMs of the network spread over many SMs):
 //  - K advances in chunks of 64, one 128-byte row of BF16 per tile row, through
 //    S <= 8 shared-memory stages, all filled at once when K <= 512 (the sizes of
@@ -82,7 +82,7 @@ __device__ __forceinline__ float gelu_prime_f(float x) {
 //    `mode` row by row with coalesced stores.
 // Every mbarrier wait is bounded; a wait that gives up sets *err, and the CTA
 // still frees its tensor memory before it returns.
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 64, TC_MAXS = 8;
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 32, TC_MAXS = 8;
 
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int BN) { return (uint32_t)(TC_BM + BN) * 128u; }
 // S stages, and room for the epilogue's TC_BM x (BN + 1) float tile, plus 1024 bytes of alignment slack
@@ -112,7 +112,8 @@ __device__ __forceinline__ uint32_t tc_idesc(int BN) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int BN, int S, int* err) {
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int S, int* err) {
     extern __shared__ unsigned char tc_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t bar[TC_MAXS];
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bm = blockIdx.y * TC_BM, bn = blockIdx.x * BN;
     const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
-    const uint32_t ncols = BN <= 32 ? 32u : 64u;
+    constexpr uint32_t ncols = BN <= 32 ? 32u : 64u;
     const uint32_t stage = tc_stage_bytes(BN);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
     // accumulator -> shared memory (the stages are free: every MMA has completed and
     // every copy has landed), then row-wise coalesced stores with the epilogue
     float* tile = reinterpret_cast<float*>(base);  // TC_BM rows of BN + 1 floats
-    const int TW = BN + 1;
+    constexpr int TW = BN + 1;
     const int quarter = warp & 3, half = warp >> 2;
     for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
         uint32_t v[16];
@@ -307,32 +308,33 @@ __global__ void load_inputs_kernel(const float* X, const int* idx, int64_t r0, i
 }
 
 // dY = 2 (Y - T_std) / (n n_out) into fp32, bf16 and transposed bf16 (padding zero),
-// the loss sum, and per 128-row tile the column sums of dY in a fixed order (the
-// output bias gradient; cs[blockIdx.x * ld + c]).  One block per 128 x 64 tile
+// the loss sum, and per LG_ROWS-row tile the column sums of dY in a fixed order (the
+// output bias gradient; cs[blockIdx.x * ld + c]).  One block per LG_ROWS x 64 tile
 // (grid: row tiles x column tiles), coalesced along the columns; the transposed
 // copy and the column sums go through a shared-memory tile.
+constexpr int LG_ROWS = 32;
 __global__ void __launch_bounds__(256) loss_grad_kernel(const float* Y, int ldy, const float* T, const int* idx,
                                                         int64_t r0, int n, int n_out, const float* mu, const float* sd,
                                                         float* dZ, bf16* dZb, bf16* dZbT, int ld, int Bp, float* cs,
                                                         double* loss) {
-    __shared__ float tile[TC_BM][65];
+    __shared__ float tile[LG_ROWS][65];
     double s = 0.0;
     const float scale = 2.0f / ((float)n * (float)n_out);
-    const int rbeg = blockIdx.x * TC_BM, cbeg = blockIdx.y * 64;
+    const int rbeg = blockIdx.x * LG_ROWS, cbeg = blockIdx.y * 64;
     constexpr int EU = 8;  // elements per thread and round, their loads issued together
-    for (int i0 = threadIdx.x; i0 < TC_BM * 64; i0 += blockDim.x * EU) {
+    for (int i0 = threadIdx.x; i0 < LG_ROWS * 64; i0 += blockDim.x * EU) {
         float yv[EU], tv[EU];
 #pragma unroll
         for (int u = 0; u < EU; ++u) {
             const int i = i0 + u * blockDim.x, rr = i >> 6, cc = i & 63, r = rbeg + rr, c = cbeg + cc;
-            const bool in = i < TC_BM * 64 && r < n && c < n_out;
+            const bool in = i < LG_ROWS * 64 && r < n && c < n_out;
             yv[u] = in ? __ldg(&Y[(size_t)r * ldy + c]) : 0.f;
             tv[u] = in ? __ldg(&T[sample_row(idx, r0, r) * n_out + c]) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < EU; ++u) {
             const int i = i0 + u * blockDim.x, rr = i >> 6, cc = i & 63, r = rbeg + rr, c = cbeg + cc;
-            if (i >= TC_BM * 64) continue;
+            if (i >= LG_ROWS * 64) continue;
             float g = 0.f;
             if (r < Bp && c < ld) {
                 if (r < n && c < n_out) {
@@ -347,13 +349,13 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float* Y, int ldy,
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < TC_BM * 64; i += blockDim.x) {
-        const int rr = i % TC_BM, cc = i / TC_BM, r = rbeg + rr, c = cbeg + cc;
+    for (int i = threadIdx.x; i < LG_ROWS * 64; i += blockDim.x) {
+        const int rr = i % LG_ROWS, cc = i / LG_ROWS, r = rbeg + rr, c = cbeg + cc;
         if (r < Bp && c < ld) dZbT[(size_t)c * Bp + r] = __float2bfloat16(tile[rr][cc]);
     }
     if (threadIdx.x < 64 && cbeg + threadIdx.x < ld) {
         float csum = 0.f;
-        for (int rr = 0; rr < TC_BM; ++rr) csum += tile[rr][threadIdx.x];
+        for (int rr = 0; rr < LG_ROWS; ++rr) csum += tile[rr][threadIdx.x];
         cs[(size_t)blockIdx.x * ld + cbeg + threadIdx.x] = csum;
     }
     s = warp_sum(s);
@@ -561,16 +563,16 @@ void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ld
     g.kchunk = x.kchunk > 0 ? x.kchunk : K;
     g.cstride = (size_t)M * ldc;
     const int splits = (K + g.kchunk - 1) / g.kchunk;
-    const int BN = N <= 32 ? 32 : cl::TC_BN;  // N is a multiple of 32
+    constexpr int BN = cl::TC_BN;  // N is a multiple of 32
     const int nk = (g.kchunk + cl::TC_BK - 1) / cl::TC_BK;
     const int stages = nk < cl::TC_MAXS ? nk : cl::TC_MAXS;
     static bool attr_set = false;  // the stage ring needs the opt-in shared-memory size
     if (!attr_set) {
-        cudaFuncSetAttribute(cl::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cl::tc_smem_bytes(cl::TC_BN, cl::TC_MAXS));
+        cudaFuncSetAttribute(cl::gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cl::tc_smem_bytes(BN, cl::TC_MAXS));
         // one shared-memory carveout for every kernel of a training step, so that
         // consecutive launches need no reconfiguration of the SMs' L1/shared split
-        const void* fns[] = {(const void*)cl::gemm_tc_kernel, (const void*)cl::loss_grad_kernel,
+        const void* fns[] = {(const void*)cl::gemm_tc_kernel<BN>, (const void*)cl::loss_grad_kernel,
                              (const void*)cl::adam_all_kernel, (const void*)cl::adam_advance_kernel,
                              (const void*)cl::load_inputs_kernel};
         for (const void* f : fns) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -578,8 +580,8 @@ void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ld
         attr_set = true;
     }
     dim3 grid((N + BN - 1) / BN, (M + cl::TC_BM - 1) / cl::TC_BM, splits);
-    cl::gemm_tc_kernel<<<grid, cl::TC_THREADS, cl::tc_smem_bytes(BN, stages), S->stream>>>(g, BN, stages,
-                                                                                             &S->tdev->tc_err);
+    cl::gemm_tc_kernel<BN><<<grid, cl::TC_THREADS, cl::tc_smem_bytes(BN, stages), S->stream>>>(g, stages,
+                                                                                                 &S->tdev->tc_err);
 }
 
 // CL_ERR_TIMEOUT when a tensor-core GEMM of the last call gave up waiting (after a synchronize)
@@ -589,6 +591,14 @@ cl_status check_tc(cl_surrogate* S, const char* who) {
         return sfail(CL_ERR_CUDA, std::string(who) + ": reading the GEMM status");
     if (flag) return sfail(CL_ERR_TIMEOUT, std::string(who) + ": a tensor-core GEMM timed out waiting for its MMAs");
     return CL_OK;
+}
+
+// row tiles of the bias gradient's column sums of layer l: the output layer's come
+// from the loss gradient (LG_ROWS rows each), the others from the GEMM epilogue
+// that produces dZ_l (TC_BM rows each)
+int bias_tiles(const cl_surrogate* S, int l, int Bp) {
+    const int rows = l == S->L - 1 ? cl::LG_ROWS : cl::TC_BM;
+    return (Bp + rows - 1) / rows;
 }
 
 cl_status ensure_batch(cl_surrogate* S, int n) {
@@ -603,11 +613,11 @@ cl_status ensure_batch(cl_surrogate* S, int n) {
     S->H.assign(S->L, nullptr);
     S->HT.assign(S->L, nullptr);
     S->cs.assign(S->L, nullptr);
-    const int ntiles = (Bp + cl::TC_BM - 1) / cl::TC_BM;
     int maxP = 0;
     for (int p : S->P) maxP = std::max(maxP, p);
     bool ok = true;
     for (int l = 0; l < S->L; ++l) {
+        const int ntiles = bias_tiles(S, l, Bp);
         ok = ok && cudaMalloc(&S->Z[l], sizeof(float) * Bp * S->P[l + 1]) == cudaSuccess;
         ok = ok && cudaMalloc(&S->H[l], sizeof(cl::bf16) * Bp * S->P[l]) == cudaSuccess;
         ok = ok && cudaMalloc(&S->HT[l], sizeof(cl::bf16) * Bp * S->P[l]) == cudaSuccess;
@@ -667,9 +677,8 @@ void forward(cl_surrogate* S, const int* idx, int64_t r0, int n, bool training) 
 // into its epilogue.
 void backward(cl_surrogate* S, const int* idx, int64_t r0, int n) {
     const int L = S->L, Bp = S->Bp;
-    const int ntiles = (Bp + cl::TC_BM - 1) / cl::TC_BM;
     int cur = 0;
-    cl::loss_grad_kernel<<<dim3(ntiles, (S->P[L] + 63) / 64), 256, 0, S->stream>>>(
+    cl::loss_grad_kernel<<<dim3((Bp + cl::LG_ROWS - 1) / cl::LG_ROWS, (S->P[L] + 63) / 64), 256, 0, S->stream>>>(
         S->Z[L - 1], S->P[L], S->Td, idx, r0, n, S->n_out, S->mu_out, S->sd_out, S->dZ[cur], S->dZb[cur],
         S->dZbT[cur], S->P[L], Bp, S->cs[L - 1], S->dloss);
     for (int l = L - 1; l >= 0; --l) {
@@ -697,7 +706,6 @@ cl::AdamArgs adam_args(cl_surrogate* S) {
     memset(&a, 0, sizeof(a));
     a.L = S->L;
     a.td = S->tdev;
-    const int ntiles = (S->Bp + cl::TC_BM - 1) / cl::TC_BM;
     for (int l = 0; l < S->L; ++l) {
         cl::AdamLayer& y = a.l[l];
         y.W = S->W[l]; y.gW = S->gW[l]; y.mW = S->mW[l]; y.vW = S->vW[l];
@@ -706,7 +714,7 @@ cl::AdamArgs adam_args(cl_surrogate* S) {
         y.Wb = S->Wb[l]; y.WbT = S->WbT[l];
         y.rows = S->P[l + 1];
         y.cols = S->P[l];
-        y.ntiles = ntiles;
+        y.ntiles = bias_tiles(S, l, S->Bp);
         y.ksplit = dw_splits(S->Bp);
     }
     return a;
@@ -718,9 +726,9 @@ void bias_grads(cl_surrogate* S) {
     for (int l = 0; l < S->L; ++l)
         cl::weight_grad_kernel<<<S->sms * 2, 256, 0, S->stream>>>(S->gW[l], dw_splits(S->Bp),
                                                                   (size_t)S->P[l + 1] * S->P[l]);
-    const int ntiles = (S->Bp + cl::TC_BM - 1) / cl::TC_BM;
     for (int l = 0; l < S->L; ++l)
-        cl::bias_grad_kernel<<<(S->P[l + 1] + 127) / 128, 128, 0, S->stream>>>(S->cs[l], ntiles, S->P[l + 1], S->gb[l]);
+        cl::bias_grad_kernel<<<(S->P[l + 1] + 127) / 128, 128, 0, S->stream>>>(S->cs[l], bias_tiles(S, l, S->Bp),
+                                                                               S->P[l + 1], S->gb[l]);
 }
 
 void set_identity_scaling(cl_surrogate* S) {
