@@ -25,6 +25,9 @@ constexpr int kMaxBlocks = 4096;
 
 // Background, means and bookkeeping shared by all passes; lives in device
 // memory and is updated by the last block of each pass (all FP64).
+// DevState::error value of a pass whose tensor copies did not land within its wait limit
+constexpr int kErrCopyTimeout = 1001;
+
 struct DevState {
     double a;        // scale factor at the fields' time (where the next kick is evaluated)
     double b;        // a' (synchronized for VV; at the momenta's half step for LF)
@@ -46,8 +49,9 @@ struct DevState {
     double gl_Da[2][5], gl_Db[2][5];  // Gauss-Legendre: scalar stage derivatives (two buffers)
     int gl_cur, gl_conv, gl_it;       // latest buffer, converged flag, sweeps of this step
     long long step;
-    int error;          // nonzero: a reduction saw NaN/Inf, or (CL_ERR_TIMEOUT) a Gauss-Legendre
-                        // step did not converge; evolution stops
+    int error;          // nonzero: a reduction saw NaN/Inf, (CL_ERR_TIMEOUT) a Gauss-Legendre
+                        // step did not converge, or (kErrCopyTimeout) a pass gave up waiting
+                        // for its tensor copies; evolution stops
     int staggered;      // leapfrog momenta live half a step behind the fields
 };
 
@@ -366,6 +370,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+// try_wait that may suspend the thread (it issues nothing meanwhile) until the
+// phase completes or about `ns` nanoseconds pass
+__device__ __forceinline__ bool mbar_try_wait_for(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+// The same wait with a time limit (about 2 s of SM clock); false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait_for(bar, parity, 1000000u)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait_for(bar, parity, 1000000u))
+        if (clock64() - t0 > 4000000000LL) return false;
+    return true;
 }
 // Wait for a phase with a time limit (about 2 s of SM clock); false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {

@@ -579,6 +579,8 @@ static cl_status read_state(cl_lattice* h, cl::DevState* st) {
         return fail(h, CL_ERR_TIMEOUT,
                     "the Gauss-Legendre stage equations did not converge within 60 sweeps; the lattice stopped at "
                     "the last completed step");
+    if (st->error == cl::kErrCopyTimeout)
+        return fail(h, CL_ERR_TIMEOUT, "a field pass gave up waiting for its tensor copies; the lattice stopped");
     if (st->error) return fail(h, CL_ERR_NONFINITE, "a reduction produced a non-finite value; the lattice stopped");
     return CL_OK;
 }
@@ -846,6 +848,8 @@ extern "C" cl_status lattice_set_background(cl_lattice* h, double a, double b, d
     // a pending leapfrog drift is never left between calls, so shifts of phi are already applied
     set_background_kernel<<<1, 1, 0, h->stream>>>(h->buf.st, a, isnan(b) ? 0.0 : b, t, h->mc.alpha);
     cudaError_t e = cudaGetLastError();
+    // a pass that stopped on an error may have left its block counter part-way
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf.counter, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess && isnan(b))
         e = launch_pass(h, h->cur, 1 - h->cur, make_pass(cl::PK_INIT_B, h->grid.dt, 0, 0, 0, 0), false, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -27,17 +27,22 @@
 // phibar/pibar after every pass (a pending shift subtracted on the next
 // read), which keeps phi = phibar + delta exact.
 //
-// Tiling: a block of BX x BY threads owns a tile of BX*V x BY sites in x-y
-// (V = 4 floats or 2 doubles per thread, 16-byte accesses) and marches ZC
+// Tiling: a block of BX x BY threads owns a tile of TX = BX*V by BY sites in
+// x-y (V = 4 floats or 2 doubles per thread, 16-byte accesses) and marches ZC
 // planes in z; z-neighbours live in registers, x-y neighbours of the drifted
-// plane in shared memory (double-buffered, one barrier per plane), halo
-// cells are loaded by the tile-edge threads.  Loads of plane z+2 and of the
-// halo of plane z+1 are issued before the compute of plane z.  The grid is
-// persistent (grid-stride over tiles, y-tiles fastest so that y-halos are
-// L2 hits of concurrently running tiles).
+// plane in a ring of S shared-memory stages, one plane each (one barrier per
+// plane).  Each plane arrives by tensor-memory-access copies (TMA) issued by
+// the first warp: per array the interior box (TX x BY), the two halo rows
+// (TX x 1) and the two halo column strips (V x BY), periodic wrap by the
+// choice of each box's coordinates; one mbarrier per stage counts the bytes.
+// Plane z+S-2 is requested while plane z is computed.  The grid is persistent
+// (grid-stride over tiles, y-tiles fastest so that y-halos are L2 hits of
+// concurrently running tiles).
+#include <cuda.h>  // CUtensorMap; the encoder is resolved through the runtime at first use
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "cl_internal.cuh"
 #include "scalar_common.cuh"
@@ -45,6 +50,9 @@
 namespace cl {
 
 struct ScalarArgs {
+    // tensor maps of the source arrays, [slot][box]: box 0 the tile interior
+    // (TX x BY x 1), box 1 one row (TX x 1 x 1), box 2 one column strip (V x BY x 1)
+    CUtensorMap tm[4][3];
     const void* in[4];  // slots 0..nf-1: delta phi, nf..2nf-1: delta pi (source copy)
     void* out[4];       // same slots, destination copy
     DevState* st;
@@ -55,6 +63,36 @@ struct ScalarArgs {
     PassInfo pi;
     int write;
 };
+
+// Byte layout of one array's block in a ring stage.  Every region starts on a
+// 128-byte boundary (the alignment of a tensor copy's destination): the tile
+// interior [BY][TX], the row y0-1 [TX] ("up"), the row y0+BY [TX] ("down"),
+// the columns x0-V..x0-1 [BY][V] ("left") and x0+TX..x0+TX+V-1 [BY][V] ("right").
+struct StageLayout {
+    uint32_t up, down, left, right, arr;  // byte offsets in the block; arr: the block's size
+};
+__host__ __device__ __forceinline__ uint32_t round128(uint32_t b) { return (b + 127u) & ~127u; }
+__host__ __device__ __forceinline__ StageLayout stage_layout(int BX, int BY, int V, int tsize) {
+    const uint32_t row = (uint32_t)(BX * V * tsize), col = (uint32_t)(BY * V * tsize);
+    StageLayout s;
+    s.up = round128(row * (uint32_t)BY);
+    s.down = s.up + round128(row);
+    s.left = s.down + round128(row);
+    s.right = s.left + round128(col);
+    s.arr = s.right + round128(col);
+    return s;
+}
+
+// Tiled tensor copy of one box of a 3-D map into shared memory, completion
+// counted in bytes on the mbarrier (no cluster: the destination is this CTA's).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // --------------------------------------------------------------- the pass
 
@@ -74,8 +112,11 @@ __device__ __forceinline__ TileXYZ decode_tile(const Geometry& g, int tile) {
     return t;
 }
 
-template <typename T, int NF, int P>
-__global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A) {
+// FIXED: the tile of 32 x 8 threads is compiled in (the shape of every lattice
+// with N a multiple of 128 in FP32, 64 in FP64), so the stage layout and the
+// neighbour offsets are constants; otherwise they come from the geometry.
+template <typename T, int NF, int P, bool FIXED>
+__global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const __grid_constant__ ScalarArgs A) {
     DevState* st = A.st;
     if (st->error) return;
     constexpr int V = VecT<T>::V;
@@ -83,20 +124,36 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
     constexpr int NA = 2 * NF;
     constexpr int kFold = sizeof(T) == 4 ? 8 : 1 << 30;  // planes per FP32 run of the thread sums
     const Geometry& G = A.geo;
-    const int N = G.N, BX = G.BX, BY = G.BY, ZC = G.ZC, S = G.S;
-    const int TX = BX * V, RW = TX + 2 * V, ROWS = BY + 2;
-    const int ASZ = ROWS * RW;  // elements of one array in one stage
-    const int STG = NA * ASZ;   // elements of one stage
-    extern __shared__ __align__(128) unsigned char smraw[];
-    T* sm = reinterpret_cast<T*>(smraw + 128);
+    const int N = G.N, BX = FIXED ? 32 : G.BX, BY = FIXED ? 8 : G.BY, ZC = G.ZC, S = G.S;
+    const int TX = BX * V;
+    const StageLayout SL = stage_layout(BX, BY, V, (int)sizeof(T));
+    const int AE = (int)(SL.arr / sizeof(T));  // elements of one array block
+    const int STG = NA * AE;                   // elements of one stage
+    const uint32_t plane_bytes = (uint32_t)(NA * sizeof(T)) * (uint32_t)(TX * BY + 2 * TX + 2 * BY * V);
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~(uintptr_t)127);
+    const uint32_t sm_addr = smem_u32(sm);
     __shared__ double bacc[8][16];
+    __shared__ __align__(8) uint64_t full[8];  // one per stage: the plane's bytes have landed
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int lin = ty * BX + tx;
     const int nthr = BX * BY;
-    const int lane = lin & 31, warp = lin >> 5, nwarps = (nthr + 31) >> 5;
+    const int lane = FIXED ? tx : lin & 31, warp = FIXED ? ty : lin >> 5, nwarps = (nthr + 31) >> 5;
     const int nlanes = min(32, nthr - 32 * warp);
     const unsigned wmask = nlanes >= 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
     for (int i = lin; i < 8 * 16; i += nthr) (&bacc[0][0])[i] = 0.0;
+    // nprod producer warps issue the copies, producer pw those of arrays pw, pw + nprod, ...
+    // They are taken from the middle of the block, away from the first and last
+    // thread rows, which drift the y-halo rows.  Producer warps need five lanes:
+    // blocks have at least 16 threads (N >= 8), and only the last warp can be partial.
+    const int full5 = nwarps - (nthr - 32 * (nwarps - 1) < 5 ? 1 : 0);
+    const int nprod = full5 < NA ? full5 : NA;
+    const int pw = warp - (full5 - nprod) / 2;
+    const bool producer = pw >= 0 && pw < nprod;
+    if (lin == 0) {
+        for (int i = 0; i < S; ++i) mbar_init(&full[i], (uint32_t)nprod);
+        fence_mbar_init();
+    }
 
     const T cd = T(st->cd), A1 = T(st->A1), A3 = T(st->A3);
     const T h1 = T(A.pi.h1), h = T(A.pi.h), idx2 = T(A.mc.idx2);
@@ -112,114 +169,116 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
 
     const int my_tiles = (blockIdx.x < (unsigned)G.ntiles) ? (G.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-    // Load sequence of this block: for each of its tiles, planes z0-1 .. z0+ZC.  The
-    // producer side walks it with counters (tile k, plane p, stage slot) so that no
-    // division is needed per plane; the tile decode happens once per tile.
+    // This thread's vector and its four x-y neighbours inside an array block
+    // (elements): interior rows, or the halo regions at the tile's edges.
+    const int o_own = ty * TX + tx * V;
+    const int o_u = ty > 0 ? o_own - TX : (int)(SL.up / sizeof(T)) + tx * V;
+    const int o_d = ty < BY - 1 ? o_own + TX : (int)(SL.down / sizeof(T)) + tx * V;
+    const int o_l = tx > 0 ? o_own - 1 : (int)(SL.left / sizeof(T)) + ty * V + (V - 1);
+    const int o_r = tx < BX - 1 ? o_own + V : (int)(SL.right / sizeof(T)) + ty * V;
+
+    // Load sequence of this block: for each of its tiles, planes z0-1 .. z0+ZC,
+    // load i into stage i mod S.  Each producer warp walks it with counters (tile
+    // k, plane p, stage slot); its lane 0 posts the byte count of its arrays on
+    // the stage's mbarrier (one arrival per producer warp, before its copies),
+    // and lanes 0-4 each copy one box kind of those arrays.
     int ld_k = 0, ld_p = 0, ld_slot = 0;
+    int pending = 0;  // producer lanes: loads issued and not yet waited for
     TileXYZ ld_t = decode_tile(G, (int)blockIdx.x);
-    const bool yhalo = (ty == 0) || (ty == BY - 1);
-    const bool xhalo = (tx == 0) || (tx == BX - 1);
-    const int yh_row = (ty == 0) ? 0 : BY + 1;
-    const int xh_col = (tx == 0) ? V - 1 : V + TX;
-
-    // Every thread copies its own part of the next load into its stage with cp.async:
-    // its 16-byte vector of every array, the y-halo row vector (first/last thread row)
-    // and the x-halo cell (first/last thread column), periodic indices.  One commit
-    // group per load, empty past the end, so every thread counts groups alike.
-    auto issue = [&]() {
-        if (ld_k < my_tiles) {
-            int z = ld_t.z0 - 1 + ld_p;
-            z = z < 0 ? z + N : (z >= N ? z - N : z);
-            T* dst = sm + ld_slot * STG;
-            const int x = ld_t.x0 + tx * V, y = ld_t.y0 + ty;
-            const size_t zoff = (size_t)z * N * N;
-            const int yh = (ty == 0) ? (y == 0 ? N - 1 : y - 1) : (y == N - 1 ? 0 : y + 1);
-            const int xh = (tx == 0) ? (x == 0 ? N - 1 : x - 1) : (x + V == N ? 0 : x + V);
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const T* src = static_cast<const T*>(A.in[a]) + zoff;
-                T* d = dst + a * ASZ;
-                cp_async16(d + (ty + 1) * RW + V + tx * V, src + (size_t)y * N + x);
-                if (yhalo) {
-                    cp_async16(d + yh_row * RW + V + tx * V, src + (size_t)yh * N + x);
-                    if (BY == 1) cp_async16(d + (BY + 1) * RW + V + tx * V, src + (size_t)(y == N - 1 ? 0 : y + 1) * N + x);
-                }
-                if (xhalo) {
-                    cp_async_elem(d + (ty + 1) * RW + xh_col, src + (size_t)y * N + xh);
-                    if (BX == 1) cp_async_elem(d + (ty + 1) * RW + V + TX, src + (size_t)y * N + (x + V == N ? 0 : x + V));
-                }
-            }
-            if (++ld_p == ZC + 2) {
-                ld_p = 0;
-                if (++ld_k < my_tiles) ld_t = decode_tile(G, (int)blockIdx.x + ld_k * (int)gridDim.x);
-            }
-            if (++ld_slot == S) ld_slot = 0;
+    const int my_arrays = producer ? (NA - 1 - pw) / nprod + 1 : 0;
+    const uint32_t warp_bytes = plane_bytes / NA * (uint32_t)my_arrays;
+    auto issue = [&]() {  // producer warps only
+        if (ld_k >= my_tiles) return;
+        int z = ld_t.z0 - 1 + ld_p;
+        z = z < 0 ? z + N : (z >= N ? z - N : z);
+        uint64_t* bar = &full[ld_slot];
+        if (lane == 0) mbar_arrive_expect_tx(bar, warp_bytes);
+        __syncwarp(wmask);
+        if (lane < 5) {
+            const int kind = lane, x0 = ld_t.x0, y0 = ld_t.y0;
+            int cx = x0, cy = y0, box = 0;
+            uint32_t off = 0;
+            if (kind == 1) { cy = y0 == 0 ? N - 1 : y0 - 1; box = 1; off = SL.up; }
+            if (kind == 2) { cy = y0 + BY == N ? 0 : y0 + BY; box = 1; off = SL.down; }
+            if (kind == 3) { cx = x0 == 0 ? N - V : x0 - V; box = 2; off = SL.left; }
+            if (kind == 4) { cx = x0 + TX == N ? 0 : x0 + TX; box = 2; off = SL.right; }
+            const uint32_t dst = sm_addr + (uint32_t)ld_slot * (uint32_t)(STG * sizeof(T)) + off;
+            for (int a = pw; a < NA; a += nprod) tma_load_3d(dst + (uint32_t)a * SL.arr, &A.tm[a][box], cx, cy, z, bar);
         }
-        cp_async_commit();
-    };
-    // wait until load `need` has landed for every thread: `issued - 1 - need`
-    // newer commit groups may stay pending
-    int issued = 0;
-    auto wait_for = [&](int need) {
-        switch (issued - 1 - need) {
-            case 0: cp_async_wait<0>(); break;
-            case 1: cp_async_wait<1>(); break;
-            case 2: cp_async_wait<2>(); break;
-            case 3: cp_async_wait<3>(); break;
-            case 4: cp_async_wait<4>(); break;
-            default: cp_async_wait<5>(); break;
+        ++pending;
+        if (++ld_p == ZC + 2) {
+            ld_p = 0;
+            if (++ld_k < my_tiles) ld_t = decode_tile(G, (int)blockIdx.x + ld_k * (int)gridDim.x);
         }
-        __syncthreads();
+        if (++ld_slot == S) ld_slot = 0;
+    };
+    // Loads are taken in order (stage wslot, phase parity wpar).  One warp, the
+    // poller (neither a producer nor a halo row), waits for them before the plane's
+    // barrier, suspended in try_wait, so that only one warp spends issue slots on
+    // waiting.  The completion of a tensor copy carries an implicit async-to-generic
+    // proxy fence, the poller's wait acquires the completed phase, and the barrier
+    // (release/acquire at CTA scope) orders that before every thread's reads of the
+    // stage.  A wait that gives up sets `late`; the barrier makes the block leave its
+    // tile loop together.
+    const bool poller = warp == (nwarps > 2 ? nwarps - 2 : 0);
+    int wslot = 0;
+    uint32_t wpar = 0;
+    bool late = false, failed = false;
+    auto wait_loads = [&](int k) {  // poller, before the barrier
+        int sl = wslot;
+        uint32_t par = wpar;
+        for (int i = 0; i < k; ++i) {
+            if (!mbar_wait_bounded_sleep(&full[sl], par)) late = true;
+            if (++sl == S) { sl = 0; par ^= 1u; }
+        }
+    };
+    auto take_loads = [&](int k) {  // every thread, after the barrier
+        for (int i = 0; i < k; ++i) {
+            --pending;
+            if (++wslot == S) { wslot = 0; wpar ^= 1u; }
+        }
     };
 
-    for (int L = 0; L < S; ++L, ++issued) issue();
+    __syncthreads();  // barriers initialized
+    if (producer)
+        for (int L = 0; L < S; ++L) issue();
     int sl_m = 0;   // stage slot of plane z-1; z and z+1 follow cyclically
-    int need = 2;   // index of the load holding plane z+1
 
     // In-place drift of this thread's part of a landed stage: phi <- (phi - sphi) + cd (pi - spi)
-    // for its own vector and the halo cells it copied, so that neighbours read drifted
-    // values (each site is drifted once per pass).  Returns its own drifted vector and
-    // shifted momentum.
+    // for its own vector and the halo cells that it reads for its neighbours at the tile's
+    // edges, so that neighbours read drifted values (each site is drifted once per pass).
+    // Returns its own drifted vector and shifted momentum.
     const T c0[2] = {sf[0] + cd * sp[0], sf[1] + cd * sp[1]};
     auto drift_stage = [&](T* Sx, T (&fo)[NF][V], T (&po)[NF][V]) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            T* F = Sx + f * ASZ;
-            const T* Pp = Sx + (NF + f) * ASZ;
-            const int ob = (ty + 1) * RW + V + tx * V;
+            T* F = Sx + f * AE;
+            const T* Pp = Sx + (NF + f) * AE;
             T rf[V], rp[V];
-            vload_s(F + ob, rf);
-            vload_s(Pp + ob, rp);
+            vload_s(F + o_own, rf);
+            vload_s(Pp + o_own, rp);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 po[f][v] = rp[v] - sp[f];
                 fo[f][v] = (rf[v] + cd * rp[v]) - c0[f];
             }
-            vstore(F + ob, fo[f]);
-            if (yhalo) {
-                const int oh = yh_row * RW + V + tx * V;
-                vload_s(F + oh, rf);
-                vload_s(Pp + oh, rp);
+            vstore(F + o_own, fo[f]);
+            if (ty == 0) {
+                vload_s(F + o_u, rf);
+                vload_s(Pp + o_u, rp);
 #pragma unroll
                 for (int v = 0; v < V; ++v) rf[v] = (rf[v] + cd * rp[v]) - c0[f];
-                vstore(F + oh, rf);
-                if (BY == 1) {
-                    const int ob2 = (BY + 1) * RW + V + tx * V;
-                    vload_s(F + ob2, rf);
-                    vload_s(Pp + ob2, rp);
+                vstore(F + o_u, rf);
+            }
+            if (ty == BY - 1) {
+                vload_s(F + o_d, rf);
+                vload_s(Pp + o_d, rp);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) rf[v] = (rf[v] + cd * rp[v]) - c0[f];
-                    vstore(F + ob2, rf);
-                }
+                for (int v = 0; v < V; ++v) rf[v] = (rf[v] + cd * rp[v]) - c0[f];
+                vstore(F + o_d, rf);
             }
-            if (xhalo) {
-                const int oc = (ty + 1) * RW + xh_col;
-                F[oc] = (F[oc] + cd * Pp[oc]) - c0[f];
-                if (BX == 1) {
-                    const int oc2 = (ty + 1) * RW + V + TX;
-                    F[oc2] = (F[oc2] + cd * Pp[oc2]) - c0[f];
-                }
-            }
+            if (tx == 0) F[o_l] = (F[o_l] + cd * Pp[o_l]) - c0[f];
+            if (tx == BX - 1) F[o_r] = (F[o_r] + cd * Pp[o_r]) - c0[f];
         }
     };
 
@@ -227,7 +286,6 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
         const TileXYZ tt = decode_tile(G, (int)blockIdx.x + k * (int)gridDim.x);
         const int x = tt.x0 + tx * V, y = tt.y0 + ty;
         const size_t NN = (size_t)N * N;
-        const int ob = (ty + 1) * RW + V + tx * V;  // own vector inside an array block
         T ts[NS];
 #pragma unroll
         for (int i = 0; i < NS; ++i) ts[i] = T(0);
@@ -240,11 +298,26 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
         for (int zf = 0; zf < ZC; zf += kFold) {
             const int zend = ZC - zf < kFold ? ZC : zf + kFold;
 #pragma unroll(sizeof(T) == 4 ? 2 : 1)
-            for (int zz = zf; zz < zend; ++zz, ++need) {
-                wait_for(need);  // planes z-1, z, z+1 have landed
+            for (int zz = zf; zz < zend; ++zz) {
+                // planes z-1, z, z+1 have landed (z-1 and z were waited for earlier,
+                // except at the tile's first plane)
+                const int nload = zz == 0 ? 3 : 1;
+                if (poller) wait_loads(nload);
+                // Proxy fence: this thread's in-place drift writes (generic proxy) are
+                // ordered before later tensor copies into the same stage (async proxy).
+                // A stage written at plane z is refilled after the barrier of plane z+3
+                // at the earliest (z+1 for the tile's first plane, z = 0), or at the
+                // tile's end: a fence at every odd plane and one before the tile-end
+                // barrier cover every case.
+                if (zz & 1) fence_proxy_async_smem();
+                if (__syncthreads_or(late)) {
+                    failed = true;
+                    goto drain;
+                }
+                take_loads(nload);
                 // the stage of plane z-2 was released by the previous iteration and every
                 // thread has passed the barrier above: refill it now (one barrier per plane)
-                if (zz > 0) { issue(); ++issued; }
+                if (zz > 0 && producer) issue();
                 const int sl_c = sl_m + 1 == S ? 0 : sl_m + 1;
                 const int sl_p = sl_c + 1 == S ? 0 : sl_c + 1;
                 T* Sc = sm + sl_c * STG;
@@ -260,16 +333,16 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
                 T lap[NF][V];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const T* cF = Sc + f * ASZ;
+                    const T* cF = Sc + f * AE;
                     // x-neighbours: shuffles of the drifted own vectors, shared memory at row/warp edges
                     const T fromL = __shfl_up_sync(wmask, fc[f][V - 1], 1);
                     const T fromR = __shfl_down_sync(wmask, fc[f][0], 1);
                     const bool useL = (tx > 0) && (lane > 0), useR = (tx < BX - 1) && (lane < nlanes - 1);
-                    const T left = useL ? fromL : cF[ob - 1];
-                    const T right = useR ? fromR : cF[ob + V];
+                    const T left = useL ? fromL : cF[o_l];
+                    const T right = useR ? fromR : cF[o_r];
                     T u[V], d[V];
-                    vload_s(cF + ob - RW, u);
-                    vload_s(cF + ob + RW, d);
+                    vload_s(cF + o_u, u);
+                    vload_s(cF + o_d, d);
                     T g = T(0);
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -329,16 +402,31 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const ScalarArgs A)
             }
             fold_warp_sums<T, NS>(ts, bacc[warp], lane, nlanes);
         }
+        fence_proxy_async_smem();
         __syncthreads();  // the tile's last three stages are free
-        issue();
-        issue();
-        issue();
-        issued += 3;
-        need += 2;
+        if (producer) {
+            issue();
+            issue();
+            issue();
+        }
         sl_m = sl_m + 2 >= S ? sl_m + 2 - S : sl_m + 2;
     }
-    cp_async_wait<0>();
+drain:
+    if (failed) {
+        // a plane never arrived (not expected): flag the pass, let the copies still
+        // in flight land (each wait again bounded) before the block's memory is released
+        if (lane == 0 && producer) {
+            st->error = kErrCopyTimeout;
+            int slot = wslot;
+            uint32_t par = wpar;
+            for (int i = 0; i < pending; ++i) {
+                mbar_wait_bounded(&full[slot], par);
+                if (++slot == S) { slot = 0; par ^= 1u; }
+            }
+        }
+    }
     __syncthreads();
+
 
     // ---- block reduction (FP64) and last-block finish
     if (lin < NS) {
@@ -384,15 +472,20 @@ __global__ void scalar_drift_kernel(T* phi0, T* phi1, const T* pi0, const T* pi1
 
 // --------------------------------------------------------------- host side
 
-template <typename T, int NF> static const void* kptr_p(int pexp) {
-    if (pexp == 4) return (const void*)scalar_pass_kernel<T, NF, 4>;
-    if (pexp == 6) return (const void*)scalar_pass_kernel<T, NF, 6>;
-    return (const void*)scalar_pass_kernel<T, NF, 2>;
+static bool fixed_tile(const Geometry& g) { return g.BX == 32 && g.BY == 8; }
+
+template <typename T, int NF, bool FX> static const void* kptr_p(int pexp) {
+    if (pexp == 4) return (const void*)scalar_pass_kernel<T, NF, 4, FX>;
+    if (pexp == 6) return (const void*)scalar_pass_kernel<T, NF, 6, FX>;
+    return (const void*)scalar_pass_kernel<T, NF, 2, FX>;
+}
+template <typename T, int NF> static const void* kptr_f(const Lattice* L) {
+    return fixed_tile(L->geo) ? kptr_p<T, NF, true>(L->mc.pexp) : kptr_p<T, NF, false>(L->mc.pexp);
 }
 
 static const void* scalar_kernel_ptr(const Lattice* L) {
-    if (L->prec == CL_FP32) return L->mc.nf == 1 ? kptr_p<float, 1>(L->mc.pexp) : kptr_p<float, 2>(L->mc.pexp);
-    return L->mc.nf == 1 ? kptr_p<double, 1>(L->mc.pexp) : kptr_p<double, 2>(L->mc.pexp);
+    if (L->prec == CL_FP32) return L->mc.nf == 1 ? kptr_f<float, 1>(L) : kptr_f<float, 2>(L);
+    return L->mc.nf == 1 ? kptr_f<double, 1>(L) : kptr_f<double, 2>(L);
 }
 
 // Tile geometry.  CL_SCALAR_TILE="BY,ZC,S[,BX]" (rows per tile, planes per z
@@ -437,8 +530,7 @@ void scalar_geometry(Lattice* L) {
     g.ntz = N / g.ZC;
     g.ntiles = g.ntx * g.nty * g.ntz;
     g.threads = g.BX * g.BY;
-    const size_t RW = (size_t)g.BX * g.V + 2 * g.V;
-    const size_t stage = 2 * (size_t)L->mc.nf * (g.BY + 2) * RW * L->tsize;
+    const size_t stage = 2 * (size_t)L->mc.nf * stage_layout(g.BX, g.BY, g.V, (int)L->tsize).arr;
     g.S = want_s;
     while (g.S > 4 && 128 + (size_t)g.S * stage > 227 * 1024) --g.S;
     g.smem = 128 + (size_t)g.S * stage;
@@ -466,7 +558,7 @@ void scalar_geometry(Lattice* L) {
 template <typename T, int NF, int P>
 static cudaError_t launch_t(Lattice* L, const ScalarArgs& A, cudaStream_t s) {
     const Geometry& g = L->geo;
-    auto fn = scalar_pass_kernel<T, NF, P>;
+    auto fn = fixed_tile(g) ? scalar_pass_kernel<T, NF, P, true> : scalar_pass_kernel<T, NF, P, false>;
     fn<<<g.grid, dim3(g.BX, g.BY), g.smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -481,13 +573,52 @@ static cudaError_t launch_p(Lattice* L, const ScalarArgs& A, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// cuTensorMapEncodeTiled, resolved once through the runtime (no link against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn tensor_map_encoder() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        const bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                            cudaSuccess &&
+                        q == cudaDriverEntryPointSuccess;
+        cudaGetLastError();
+        return ok ? reinterpret_cast<EncodeTiledFn>(p) : nullptr;
+    }();
+    return fn;
+}
+
+// The three tensor maps of one N^3 array (x fastest): the tile interior
+// (TX x BY x 1), one row (TX x 1 x 1) and one column strip (V x BY x 1).
+// Out-of-range parts of a box are never requested (halos wrap by coordinate).
+static bool encode_array_maps(CUtensorMap (&tm)[3], const void* base, const Geometry& g, size_t tsize) {
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t n = (cuuint64_t)g.N;
+    const cuuint64_t dims[3] = {n, n, n};
+    const cuuint64_t strides[2] = {n * tsize, n * n * tsize};
+    const cuuint32_t TX = (cuuint32_t)(g.BX * g.V), BY = (cuuint32_t)g.BY, V = (cuuint32_t)g.V;
+    const cuuint32_t boxes[3][3] = {{TX, BY, 1}, {TX, 1, 1}, {V, BY, 1}};
+    const cuuint32_t unit[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = tsize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    for (int b = 0; b < 3; ++b)
+        if (enc(&tm[b], dt, 3, const_cast<void*>(base), dims, strides, boxes[b], unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    return true;
+}
+
 cudaError_t scalar_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
     ScalarArgs A;
+    memset(&A, 0, sizeof(A));
     const int nf = L->mc.nf;
-    for (int i = 0; i < 4; ++i) { A.in[i] = nullptr; A.out[i] = nullptr; }
     for (int i = 0; i < 2 * nf; ++i) {
         A.in[i] = L->buf.f[src][i];
         A.out[i] = L->buf.f[dst][i];
+        if (!encode_array_maps(A.tm[i], A.in[i], L->geo, L->tsize)) return cudaErrorInvalidValue;
     }
     A.st = L->buf.st;
     A.partials = L->buf.partials;
