@@ -246,7 +246,7 @@ def scan_measurement(args, stream, dist=None):
     (ii) the batched ensemble of all n runs (autotuned tiles, CUDA graphs),
     whose observations train two surrogate networks; the held-out couplings are
     then answered by the surrogate where the two networks agree within 2%, and
-    by a plain lattice run (the fallback) otherwise;
+    by a lattice run otherwise (the fallbacks evolve together as one ensemble);
     scored against fresh lattice runs (R seeds per held-out q).
     Under torchrun the runs of both ensembles are split across the ranks (one
     block each, no exchange while they evolve) and gathered once; rank 0 trains,
@@ -331,7 +331,8 @@ def scan_measurement(args, stream, dist=None):
                                   times[-1], Q),
                    "surrogate": "two MLPs 2-256-256-256-34 GELU, BF16 tensor-core GEMMs, FP32 accumulate, Adam, "
                                 "%d epochs, batch 512, %d training rows; answers where they agree within 2%% on "
-                                ">= 90%% of a query's slices (eps_chi and w), a plain %d^3 lattice run otherwise"
+                                ">= 90%% of a query's slices (eps_chi and w), a %d^3 lattice run otherwise (the "
+                                "fallback runs batched in one ensemble)"
                                 % (args.scan_epochs, len(X), sorted(spec.sizes)[len(spec.sizes) // 2]),
                    "heldout": "%d q log-uniform in [1e2, 1e5] (seed 4321), %d fresh seeds each" % (Q, R),
                    "parallelism": "runs split across %d ranks" % world if world > 1 else "single"},

@@ -313,17 +313,18 @@ cl_status lattice_destroy(cl_lattice* h);
  * ensemble_observe writes, per member, CL_OBS_SIZE floats: the daughter-field
  * energy fraction (E_K[1] + E_G[1]) / rho, the equation of state w, and log10
  * of the chi power spectrum (section 3.1) at the 32 momenta
- * k_j = k_IR (k_max/k_IR)^((j + 1/2)/32), j = 0..31, k_max = N_min k_IR / 2
+ * k_j = k_IR (k_max/k_IR)^((j + 1/2)/32), j = 0..31, interpolated linearly in
+ * (log k, log Delta) between the shells.  kmax <= 0 selects k_max = N_min k_IR / 2
  * (N_min the smallest member: its Nyquist momentum along an axis; shells
- * beyond it are incomplete), interpolated linearly in (log k, log Delta)
- * between the shells.  *t (may be NULL) receives the program time.
- * Synchronizes the stream. */
+ * beyond it are incomplete); a positive kmax is used as given, so that
+ * ensembles of different sizes observe at the same momenta.  *t (may be NULL)
+ * receives the program time.  Synchronizes the stream. */
 typedef struct cl_ensemble cl_ensemble;
 #define CL_OBS_SIZE 34
 cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const int32_t* N, const uint64_t* seeds,
                         const cl_grid* grid, const cl_init* init, void* cuda_stream, cl_ensemble** out);
 cl_status ensemble_evolve(cl_ensemble* e, int64_t nsteps);
-cl_status ensemble_observe(cl_ensemble* e, float* obs, double* t);
+cl_status ensemble_observe(cl_ensemble* e, double kmax, float* obs, double* t);
 cl_status ensemble_member(cl_ensemble* e, int32_t i, cl_lattice** out);
 cl_status ensemble_destroy(cl_ensemble* e);
 

@@ -138,7 +138,7 @@ def load(build_if_missing=True):
         "ensemble_init": ([i32, C.POINTER(cl_model), pd, C.POINTER(C.c_int32), C.POINTER(C.c_uint64),
                            C.POINTER(cl_grid), C.POINTER(cl_init), vp, C.POINTER(vp)], C.c_int),
         "ensemble_evolve": ([vp, i64], C.c_int),
-        "ensemble_observe": ([vp, C.POINTER(C.c_float), pd], C.c_int),
+        "ensemble_observe": ([vp, C.c_double, C.POINTER(C.c_float), pd], C.c_int),
         "ensemble_member": ([vp, i32, C.POINTER(vp)], C.c_int),
         "ensemble_destroy": ([vp], C.c_int),
         "ensemble_get_tile": ([vp, C.POINTER(C.c_int32)], C.c_int),
@@ -375,10 +375,10 @@ class Ensemble:
     def evolve(self, nsteps):
         _check(load().ensemble_evolve(self.h, int(nsteps)))
 
-    def observe(self):
+    def observe(self, kmax=0.0):
         out = np.zeros((self.n, CL_OBS_SIZE), dtype=np.float32)
         t = C.c_double(0.0)
-        _check(load().ensemble_observe(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), C.byref(t)))
+        _check(load().ensemble_observe(self.h, float(kmax), out.ctypes.data_as(C.POINTER(C.c_float)), C.byref(t)))
         return out, t.value
 
     def tile(self):

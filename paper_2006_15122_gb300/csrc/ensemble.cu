@@ -819,7 +819,7 @@ cl_status ensemble_member(cl_ensemble* E, int32_t i, cl_lattice** out) {
     return CL_OK;
 }
 
-cl_status ensemble_observe(cl_ensemble* E, float* obs, double* t) {
+cl_status ensemble_observe(cl_ensemble* E, double kmax_arg, float* obs, double* t) {
     if (!E || !obs) return efail(CL_ERR_ARG, "ensemble_observe: NULL argument");
     const int n = (int)E->mem.size();
     // reductions of every member in one launch; then, per size class, the chi of all its
@@ -866,7 +866,7 @@ cl_status ensemble_observe(cl_ensemble* E, float* obs, double* t) {
         e = cudaMemcpyAsync(bins.data(), E->d_obs_bins, sizeof(double) * bins.size(), cudaMemcpyDeviceToHost, E->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
     if (e != cudaSuccess) return efail(CL_ERR_CUDA, std::string("ensemble_observe: ") + cudaGetErrorString(e));
-    const double kmax = 0.5 * E->nmin * E->kIR;
+    const double kmax = kmax_arg > 0 ? kmax_arg : 0.5 * E->nmin * E->kIR;
     for (size_t k = 0; k < E->obs_members.size(); ++k) {
         const int i = E->obs_members[k];
         cl::observables(st[i], bins.data() + E->obs_bin_off[k], E->mem[i]->mc.N, E->mem[i]->mc.dx, E->kIR, kmax,

@@ -91,7 +91,7 @@ def ensemble_observations(spec, qs, Ns, seeds, autotune=True, stream=None):
     times = np.zeros(spec.n_slices)
     for j in range(spec.n_slices):
         ens.evolve(spec.steps_per_slice)
-        obs[:, j, :], times[j] = ens.observe()
+        obs[:, j, :], times[j] = ens.observe(spec.kmax)
     t3 = time.perf_counter()
     info = {"init_s": t1 - t0, "tune_s": t2 - t1, "evolve_observe_s": t3 - t2, "tile": ens.tile(),
             "candidates": tuned}
@@ -173,11 +173,14 @@ def disagreement(pa, pb):
 def answer_queries(nets, qs, times, q_range, spec, tol=0.02, frac=0.9, seeds=None, size=None, stream=None):
     """Observations at couplings qs and the given slice times, from the surrogate
     where it can be trusted and from the lattice otherwise.  A query falls back
-    to a plain lattice run (size `size`, default the middle one of spec.sizes) when
-    its q lies outside the trained range q_range, or when the two networks
-    disagree by more than tol on more than 1 - frac of its slices.  Returns
-    (answers (Q, S, CL_OBS_SIZE), fallback mask, estimate (Q, S), seconds of
-    the network queries, seconds of the fallback runs)."""
+    to a lattice run (size `size`, default the middle one of spec.sizes) when its
+    q lies outside the trained range q_range, or when the two networks disagree
+    by more than tol on more than 1 - frac of its slices.  The fallback runs
+    evolve together as one batched ensemble with the default tile (no tuning), so
+    each answer is the one a single-member ensemble of that query gives, whatever
+    else fell back.  Returns (answers (Q, S, CL_OBS_SIZE), fallback mask,
+    estimate (Q, S), seconds of the network queries, seconds of the fallback
+    runs)."""
     Q, S = len(qs), len(times)
     X = np.stack([np.repeat(np.log10(qs), S), np.tile(times, Q)], axis=1).astype(np.float32)
     t0 = time.perf_counter()
@@ -190,8 +193,11 @@ def answer_queries(nets, qs, times, q_range, spec, tol=0.02, frac=0.9, seeds=Non
     size = size or sorted(spec.sizes)[len(spec.sizes) // 2]
     seeds = seeds if seeds is not None else list(range(2 * 10 ** 6, 2 * 10 ** 6 + Q))
     t0 = time.perf_counter()
-    for i in np.nonzero(fallback)[0]:
-        out[i], _ = plain_observations(spec, qs[i], size, seeds[i], stream=stream)
+    idx = np.nonzero(fallback)[0]
+    if len(idx):
+        obs, _, _ = ensemble_observations(spec, np.asarray(qs)[idx], [size] * len(idx), [seeds[i] for i in idx],
+                                          autotune=False, stream=stream)
+        out[idx] = obs
     t_fallback = time.perf_counter() - t0
     return out, fallback, est, t_query, t_fallback
 

@@ -62,14 +62,17 @@ def test_ensemble_matches_single_lattices_fp32():
     ens.close()
 
 
-def test_ensemble_observations_agree_with_members():
+@pytest.mark.parametrize("kmax_arg", [0.0, 5.0])
+def test_ensemble_observations_agree_with_members(kmax_arg):
+    """ensemble_observe against each member's own measurements; the spectrum
+    momenta span [kIR, kmax], kmax = N_min kIR / 2 by default or as given."""
     Ns, qs, kIR = [32, 64, 96], [300.0, 3000.0, 30.0], 0.5
     ens, _ = make(Ns, qs, cl.CL_FP32, kIR=kIR, dt=0.004)
     ens.evolve(25)
-    obs, t = ens.observe()
+    obs, t = ens.observe(kmax_arg)
     assert obs.shape == (3, cl.CL_OBS_SIZE) and np.all(np.isfinite(obs))
     assert abs(t - 25 * 0.004) < 1e-9
-    kmax = 0.5 * min(Ns) * kIR
+    kmax = kmax_arg if kmax_arg > 0 else 0.5 * min(Ns) * kIR
     for i in range(3):
         m = ens.member(i)
         mm = m.measure_means()

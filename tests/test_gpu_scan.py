@@ -119,9 +119,9 @@ def test_surrogate_answers_held_out_couplings():
 
 def test_queries_outside_the_trained_range_or_in_disagreement_fall_back_to_the_lattice():
     """answer_queries: a coupling outside the trained q range is answered by a
-    plain lattice run of the fallback size and seed, identical to running that
-    lattice directly; inside the range, where the two networks agree, the answer
-    is their mean prediction."""
+    lattice run of the fallback size and seed (batched with the other fallbacks),
+    identical to a one-member ensemble of that lattice; inside the range, where
+    the two networks agree, the answer is their mean prediction."""
     spec = scan.ScanSpec(sizes=(32,), steps_per_slice=8, n_slices=8, kIR=0.2, dt=0.005)
     n = 48
     qs = scan.log_uniform_q(n, 1e2, 1e3, seed=7)
@@ -133,8 +133,10 @@ def test_queries_outside_the_trained_range_or_in_disagreement_fall_back_to_the_l
                                                   seeds=[11, 12], size=32)
     assert ans.shape == (2, spec.n_slices, cl.CL_OBS_SIZE) and est.shape == (2, spec.n_slices)
     assert fb[1] and t_fb > 0
-    direct, _ = scan.plain_observations(spec, qh[1], 32, 12)
-    assert np.array_equal(ans[1], direct)
+    direct, _, _ = scan.ensemble_observations(spec, qh[1:], [32], [12], autotune=False)
+    assert np.array_equal(ans[1], direct[0])
+    plain, _ = scan.plain_observations(spec, qh[1], 32, 12)  # the single-lattice path: FP32 round-off apart
+    assert np.allclose(ans[1], plain, rtol=1e-3, atol=1e-5)
     if not fb[0]:
         Xq = np.stack([np.repeat(np.log10(qh[:1]), spec.n_slices), times], axis=1).astype(np.float32)
         mean = 0.5 * (nets[0].predict(Xq) + nets[1].predict(Xq))
