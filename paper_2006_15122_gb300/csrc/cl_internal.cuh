@@ -7,6 +7,7 @@
 // pass never overwrites a value a neighbouring block still has to read.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is resolved through the runtime, no driver link)
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
@@ -220,6 +221,11 @@ struct SharedFFT {
 cl_status lattice_create(const cl_model* model, const cl_grid* grid, const cl_init* init, cudaStream_t stream,
                          const SharedFFT* shared, cl_lattice** out);
 void set_global_error(const char* msg);
+// Tensor map of one N^3 array of element size tsize (x fastest) for boxes of
+// bx x by x 1 elements (one z plane); no interleave, swizzle or out-of-range
+// fill beyond the default zeros.  false when the encoder is unavailable or
+// rejects the box.
+bool encode_plane_box(CUtensorMap* map, const void* base, int N, size_t tsize, int bx, int by);
 
 // ---- device helpers -------------------------------------------------------
 
@@ -356,9 +362,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -398,13 +401,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (clock64() - t0 > 4000000000LL) return false;
     return true;
 }
-// Global -> shared bulk copy (16-byte aligned addresses, size multiple of 16)
-// whose completion is counted on the mbarrier in bytes.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+// Tiled tensor copy of one box of a 3-D map (x, y, z) into shared memory,
+// completion counted in bytes on the mbarrier.  The map lives in kernel
+// parameter space (a __grid_constant__ argument); the destination is this
+// CTA's shared memory, 128-byte aligned; x times the element size is a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
 }
 // Hint: bring the line holding p into L2 (no register result, no fault semantics
 // needed: callers only pass addresses inside their arrays).

@@ -38,7 +38,6 @@
 // Plane z+S-2 is requested while plane z is computed.  The grid is persistent
 // (grid-stride over tiles, y-tiles fastest so that y-halos are L2 hits of
 // concurrently running tiles).
-#include <cuda.h>  // CUtensorMap; the encoder is resolved through the runtime at first use
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -81,17 +80,6 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(int BX, int BY, int
     s.right = s.left + round128(col);
     s.arr = s.right + round128(col);
     return s;
-}
-
-// Tiled tensor copy of one box of a 3-D map into shared memory, completion
-// counted in bytes on the mbarrier (no cluster: the destination is this CTA's).
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
 }
 
 // --------------------------------------------------------------- the pass
@@ -573,42 +561,13 @@ static cudaError_t launch_p(Lattice* L, const ScalarArgs& A, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
-// cuTensorMapEncodeTiled, resolved once through the runtime (no link against the driver library)
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-static EncodeTiledFn tensor_map_encoder() {
-    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        const bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                            cudaSuccess &&
-                        q == cudaDriverEntryPointSuccess;
-        cudaGetLastError();
-        return ok ? reinterpret_cast<EncodeTiledFn>(p) : nullptr;
-    }();
-    return fn;
-}
-
 // The three tensor maps of one N^3 array (x fastest): the tile interior
-// (TX x BY x 1), one row (TX x 1 x 1) and one column strip (V x BY x 1).
+// (TX x BY), one row (TX x 1) and one column strip (V x BY), one z plane each.
 // Out-of-range parts of a box are never requested (halos wrap by coordinate).
 static bool encode_array_maps(CUtensorMap (&tm)[3], const void* base, const Geometry& g, size_t tsize) {
-    const EncodeTiledFn enc = tensor_map_encoder();
-    if (!enc) return false;
-    const cuuint64_t n = (cuuint64_t)g.N;
-    const cuuint64_t dims[3] = {n, n, n};
-    const cuuint64_t strides[2] = {n * tsize, n * n * tsize};
-    const cuuint32_t TX = (cuuint32_t)(g.BX * g.V), BY = (cuuint32_t)g.BY, V = (cuuint32_t)g.V;
-    const cuuint32_t boxes[3][3] = {{TX, BY, 1}, {TX, 1, 1}, {V, BY, 1}};
-    const cuuint32_t unit[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = tsize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    for (int b = 0; b < 3; ++b)
-        if (enc(&tm[b], dt, 3, const_cast<void*>(base), dims, strides, boxes[b], unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return false;
-    return true;
+    const int TX = g.BX * g.V;
+    return encode_plane_box(&tm[0], base, g.N, tsize, TX, g.BY) && encode_plane_box(&tm[1], base, g.N, tsize, TX, 1) &&
+           encode_plane_box(&tm[2], base, g.N, tsize, g.V, g.BY);
 }
 
 cudaError_t scalar_launch_pass(Lattice* L, int src, int dst, const PassInfo& pi, bool write, cudaStream_t s) {
