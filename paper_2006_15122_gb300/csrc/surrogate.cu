@@ -85,10 +85,12 @@ __device__ __forceinline__ float gelu_prime_f(float x) {
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256, TC_BN = 32, TC_MAXS = 8;
 
 __host__ __device__ constexpr uint32_t tc_stage_bytes(int BN) { return (uint32_t)(TC_BM + BN) * 128u; }
-// S stages, and room for the epilogue's TC_BM x (BN + 1) float tile, plus 1024 bytes of alignment slack
+// S stages, and room for the epilogue's TC_BM x (BN + 1) float tile and the column
+// sums' TC_THREADS partials, plus 1024 bytes of alignment slack
 __host__ __device__ constexpr uint32_t tc_smem_bytes(int BN, int S) {
-    return ((uint32_t)S * tc_stage_bytes(BN) > (uint32_t)TC_BM * (BN + 1) * 4u ? (uint32_t)S * tc_stage_bytes(BN)
-                                                                                : (uint32_t)TC_BM * (BN + 1) * 4u) +
+    return ((uint32_t)S * tc_stage_bytes(BN) > ((uint32_t)TC_BM * (BN + 1) + TC_THREADS) * 4u
+                ? (uint32_t)S * tc_stage_bytes(BN)
+                : ((uint32_t)TC_BM * (BN + 1) + TC_THREADS) * 4u) +
            1024u;
 }
 
@@ -112,31 +114,52 @@ __device__ __forceinline__ uint32_t tc_idesc(int BN) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <int BN>
-__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int S, int* err) {
-    extern __shared__ unsigned char tc_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar[TC_MAXS];
-    __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bm = blockIdx.y * TC_BM, bn = blockIdx.x * BN;
-    const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
-    constexpr uint32_t ncols = BN <= 32 ? 32u : 64u;
-    const uint32_t stage = tc_stage_bytes(BN);
+// Tensor memory and stage barriers of a CTA that computes GEMM tiles; the
+// barriers' phase parities carry over from tile to tile.
+struct TcCtx {
+    uint32_t tmem;
+    uint64_t* bar;            // TC_MAXS mbarriers in shared memory
+    uint32_t ph[TC_MAXS];     // parity of the next phase of each stage's barrier
+};
+__device__ __forceinline__ void tc_setup(TcCtx& c, uint64_t* bar, uint32_t* tmem_slot, uint32_t ncols) {
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int k = 0; k < S; ++k) mbar_init(&bar[k], 1);
+        for (int k = 0; k < TC_MAXS; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot;
+    c.tmem = *tmem_slot;
+    c.bar = bar;
+    for (int k = 0; k < TC_MAXS; ++k) c.ph[k] = 0u;
+}
+__device__ __forceinline__ void tc_teardown(const TcCtx& c, uint32_t ncols) {
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"(ncols) : "memory");
+}
+
+// One 128 x BN tile (column tile bx, row tile by, K split bz) of the GEMM g with
+// S stages, epilogue included; `base` is the CTA's 1024-byte aligned dynamic
+// shared memory.  Operands and the epilogue's inputs are read through L2 only, so
+// that tiles see what other CTAs of the same launch wrote before a grid barrier.
+// Returns false when a wait for the MMAs gave up.
+template <int BN>
+__device__ bool gemm_tile(const GemmArgs& g, int S, int bx, int by, int bz, TcCtx& ctx, unsigned char* base) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bm = by * TC_BM, bn = bx * BN;
+    const int kbeg = bz * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+    const uint32_t stage = tc_stage_bytes(BN);
+    const uint32_t tmem = ctx.tmem;
+    uint64_t* bar = ctx.bar;
 
     auto load = [&](int s, int k0) {
         unsigned char* sa = base + s * stage;
@@ -154,8 +177,8 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
     };
 
     const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
-    uint32_t phase[TC_MAXS];
-    for (int k = 0; k < TC_MAXS; ++k) phase[k] = 0u;
+    uint32_t* phase = ctx.ph;
+    uint32_t pend = 0;  // stages with a commit not yet waited for
     bool ok = true;
     int issued = 0;
     for (; issued < S && issued < nk; ++issued) load(issued, kbeg + issued * TC_BK);
@@ -191,17 +214,22 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
                              smem_u32(&bar[s]))
                          : "memory");
         }
+        pend |= 1u << s;
         if (kt + S < nk) {  // refill this stage with chunk kt + S once its MMAs have read it
             ok = mbar_wait_bounded(&bar[s], phase[s]) && ok;
             phase[s] ^= 1u;
+            pend &= ~(1u << s);
             load(s, kbeg + (kt + S) * TC_BK);
             ++issued;
         }
     }
-    // the last commit completes after every MMA of the tile
-    ok = mbar_wait_bounded(&bar[(nk - 1) % S], phase[(nk - 1) % S]) && ok;
+    // every commit of the tile completes (the last one after every MMA of the tile)
+    for (int s = 0; s < S; ++s)
+        if ((pend >> s) & 1u) {
+            ok = mbar_wait_bounded(&bar[s], phase[s]) && ok;
+            phase[s] ^= 1u;
+        }
     tc_fence_after();
-    if (!ok && lane == 0) atomicExch(err, 1);
     // accumulator -> shared memory (the stages are free: every MMA has completed and
     // every copy has landed), then row-wise coalesced stores with the epilogue
     float* tile = reinterpret_cast<float*>(base);  // TC_BM rows of BN + 1 floats
@@ -221,7 +249,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
         for (int j = 0; j < 16; ++j) tile[(32 * quarter + lane) * TW + c0 + j] = __uint_as_float(v[j]);
     }
     __syncthreads();
-    float* const Cz = g.C + (size_t)blockIdx.z * g.cstride;
+    float* const Cz = g.C + (size_t)bz * g.cstride;
     // C (and H) row by row; the tile then holds the value H is made of (0 outside).
     // Eight elements per thread and round: their global operands (bias, Z of the
     // layer below) are loaded together before the arithmetic.
@@ -237,8 +265,8 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
             const bool valid = in && r < g.Mvalid && c < g.Nvalid;
             xin[u] = i < TC_BM * BN ? tile[rr * TW + cc] : 0.f;
             aux[u] = 0.f;
-            if (valid && (g.mode == 1 || g.mode == 2)) aux[u] = __ldg(&g.bias[c]);
-            if (valid && g.mode == 3) aux[u] = __ldg(&g.Zp[(size_t)r * g.ldz + c]);
+            if (valid && (g.mode == 1 || g.mode == 2)) aux[u] = __ldcg(&g.bias[c]);
+            if (valid && g.mode == 3) aux[u] = __ldcg(&g.Zp[(size_t)r * g.ldz + c]);
         }
 #pragma unroll
         for (int u = 0; u < EU; ++u) {
@@ -267,16 +295,41 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, i
                 const int r = bm + rr, c = bn + cc;
                 if (r < g.M && c < g.N) g.HT[(size_t)c * g.ldht + r] = __float2bfloat16(tile[rr * TW + cc]);
             }
-        if (g.cs && tid < BN && bn + tid < g.N) {  // fixed order over the tile's rows
+        if (g.cs) {  // fixed order: eight partial sums of 16 rows per column, then their sum
+            constexpr int RG = TC_THREADS / BN, RPG = TC_BM / RG;
+            float* part = tile + TC_BM * TW;  // RG x BN floats after the tile
+            const int c = tid % BN, grp = tid / BN;
             float sum = 0.f;
-            for (int rr = 0; rr < TC_BM; ++rr) sum += tile[rr * TW + tid];
-            g.cs[(size_t)blockIdx.y * g.ldcs + bn + tid] = sum;
+#pragma unroll 4
+            for (int rr = grp * RPG; rr < (grp + 1) * RPG; ++rr) sum += tile[rr * TW + c];
+            part[grp * BN + c] = sum;
+            __syncthreads();
+            if (tid < BN && bn + tid < g.N) {
+                float tot = 0.f;
+                for (int k = 0; k < RG; ++k) tot += part[k * BN + tid];
+                g.cs[(size_t)by * g.ldcs + bn + tid] = tot;
+            }
         }
     }
+    // the tile's shared memory and accumulator are free again for the CTA's next tile
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    tc_fence_after();
+    return ok;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmArgs g, int S, int* err) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar[TC_MAXS];
+    __shared__ uint32_t tmem_slot;
+    constexpr uint32_t ncols = BN <= 32 ? 32u : 64u;
+    TcCtx ctx;
+    tc_setup(ctx, bar, &tmem_slot, ncols);
+    const bool ok = gemm_tile<BN>(g, S, blockIdx.x, blockIdx.y, blockIdx.z, ctx, base);
+    if (!ok && (threadIdx.x & 31) == 0) atomicExch(err, 1);
+    tc_teardown(ctx, ncols);
 }
 
 // ---------------------------------------------------------------- helpers
@@ -296,15 +349,21 @@ __device__ __forceinline__ size_t sample_row(const int* idx, int64_t r0, int r) 
     return idx ? (size_t)idx[r0 + r] : (size_t)(r0 + r);
 }
 
-__global__ void load_inputs_kernel(const float* X, const int* idx, int64_t r0, int n, int n_in, const float* mu,
-                                   const float* sd, bf16* H0, int ld, int Bp, bf16* H0T) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)Bp * ld; i += (size_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void load_inputs_dev(const float* X, const int* idx, int64_t r0, int n, int n_in,
+                                                const float* mu, const float* sd, bf16* H0, int ld, int Bp, bf16* H0T,
+                                                size_t first, size_t step) {
+    for (size_t i = first; i < (size_t)Bp * ld; i += step) {
         const int r = (int)(i / ld), c = (int)(i % ld);
         float v = 0.f;
         if (r < n && c < n_in) v = (X[sample_row(idx, r0, r) * n_in + c] - mu[c]) / sd[c];
         H0[i] = __float2bfloat16(v);
         if (H0T) H0T[(size_t)c * Bp + r] = __float2bfloat16(v);  // the transpose for the weight gradient
     }
+}
+__global__ void load_inputs_kernel(const float* X, const int* idx, int64_t r0, int n, int n_in, const float* mu,
+                                   const float* sd, bf16* H0, int ld, int Bp, bf16* H0T) {
+    load_inputs_dev(X, idx, r0, n, n_in, mu, sd, H0, ld, Bp, H0T, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+                    (size_t)gridDim.x * blockDim.x);
 }
 
 // dY = 2 (Y - T_std) / (n n_out) into fp32, bf16 and transposed bf16 (padding zero),
@@ -313,14 +372,35 @@ __global__ void load_inputs_kernel(const float* X, const int* idx, int64_t r0, i
 // (grid: row tiles x column tiles), coalesced along the columns; the transposed
 // copy and the column sums go through a shared-memory tile.
 constexpr int LG_ROWS = 32;
-__global__ void __launch_bounds__(256) loss_grad_kernel(const float* Y, int ldy, const float* T, const int* idx,
-                                                        int64_t r0, int n, int n_out, const float* mu, const float* sd,
-                                                        float* dZ, bf16* dZb, bf16* dZbT, int ld, int Bp, float* cs,
-                                                        double* loss) {
-    __shared__ float tile[LG_ROWS][65];
+struct LossArgs {
+    const float* Y;
+    int ldy;
+    const float* T;
+    const int* idx;
+    int64_t r0;
+    int n, n_out;
+    const float *mu, *sd;
+    float* dZ;
+    bf16 *dZb, *dZbT;
+    int ld, Bp;
+    float* cs;
+    double* loss;
+};
+// The LG_ROWS x 64 tile (row tile bx, column tile by); `tile` is LG_ROWS x 65
+// floats of shared memory.  Y is read through L2 (written earlier in the same
+// launch by the fused epoch).
+__device__ void loss_grad_tile(const LossArgs& a, int bx, int by, float (*tile)[65]) {
+    const float* Y = a.Y;
+    const int ldy = a.ldy, n = a.n, n_out = a.n_out, ld = a.ld, Bp = a.Bp;
+    const float* T = a.T;
+    const int* idx = a.idx;
+    const int64_t r0 = a.r0;
+    const float *mu = a.mu, *sd = a.sd;
+    float* dZ = a.dZ;
+    bf16 *dZb = a.dZb, *dZbT = a.dZbT;
     double s = 0.0;
     const float scale = 2.0f / ((float)n * (float)n_out);
-    const int rbeg = blockIdx.x * LG_ROWS, cbeg = blockIdx.y * 64;
+    const int rbeg = bx * LG_ROWS, cbeg = by * 64;
     constexpr int EU = 8;  // elements per thread and round, their loads issued together
     for (int i0 = threadIdx.x; i0 < LG_ROWS * 64; i0 += blockDim.x * EU) {
         float yv[EU], tv[EU];
@@ -328,7 +408,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float* Y, int ldy,
         for (int u = 0; u < EU; ++u) {
             const int i = i0 + u * blockDim.x, rr = i >> 6, cc = i & 63, r = rbeg + rr, c = cbeg + cc;
             const bool in = i < LG_ROWS * 64 && r < n && c < n_out;
-            yv[u] = in ? __ldg(&Y[(size_t)r * ldy + c]) : 0.f;
+            yv[u] = in ? __ldcg(&Y[(size_t)r * ldy + c]) : 0.f;
             tv[u] = in ? __ldg(&T[sample_row(idx, r0, r) * n_out + c]) : 0.f;
         }
 #pragma unroll
@@ -353,13 +433,25 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float* Y, int ldy,
         const int rr = i % LG_ROWS, cc = i / LG_ROWS, r = rbeg + rr, c = cbeg + cc;
         if (r < Bp && c < ld) dZbT[(size_t)c * Bp + r] = __float2bfloat16(tile[rr][cc]);
     }
-    if (threadIdx.x < 64 && cbeg + threadIdx.x < ld) {
+    {  // column sums in a fixed order: four partials of LG_ROWS/4 rows per column, then their sum
+        __shared__ float part[4][64];
+        const int c = threadIdx.x & 63, grp = threadIdx.x >> 6;
         float csum = 0.f;
-        for (int rr = 0; rr < LG_ROWS; ++rr) csum += tile[rr][threadIdx.x];
-        cs[(size_t)blockIdx.x * ld + cbeg + threadIdx.x] = csum;
+        if (grp < 4)
+            for (int rr = grp * (LG_ROWS / 4); rr < (grp + 1) * (LG_ROWS / 4); ++rr) csum += tile[rr][c];
+        if (grp < 4) part[grp][c] = csum;
+        __syncthreads();
+        if (threadIdx.x < 64 && cbeg + threadIdx.x < ld)
+            a.cs[(size_t)bx * ld + cbeg + threadIdx.x] = ((part[0][threadIdx.x] + part[1][threadIdx.x]) +
+                                                          part[2][threadIdx.x]) + part[3][threadIdx.x];
     }
     s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(loss, s);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(a.loss, s);
+    __syncthreads();  // the tile is free for the CTA's next one
+}
+__global__ void __launch_bounds__(256) loss_grad_kernel(const LossArgs a) {
+    __shared__ float tile[LG_ROWS][65];
+    loss_grad_tile(a, blockIdx.x, blockIdx.y, tile);
 }
 
 // weight gradients: the split-K partials summed in order into the first one
@@ -408,20 +500,25 @@ struct AdamArgs {
     const TrainDev* td;
 };
 
-__global__ void adam_all_kernel(const AdamArgs A) {
+// Adam step number t0 + 1 at schedule position sched for layers lo .. hi-1,
+// elements first, first + step, ... of those layers' parameters.  The gradients
+// are read through L2 (written earlier in the same launch by the fused epoch).
+__device__ void adam_dev(const AdamArgs& A, long long t0, long long sched, size_t first, size_t step, int lo = 0,
+                         int hi = -1) {
+    if (hi < 0) hi = A.L;
     const TrainDev* td = A.td;
-    const float t = (float)(td->t + 1);
+    const float t = (float)(t0 + 1);
     const float b1 = td->b1, b2 = td->b2, eps = td->eps;
     const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
     float lr = td->lr;
     if (td->lr_end >= 0.f)
         lr = td->lr_end + 0.5f * (td->lr - td->lr_end) *
-                              (1.f + cospif((float)td->sched / (float)(td->total > 0 ? td->total : 1)));
+                              (1.f + cospif((float)sched / (float)(td->total > 0 ? td->total : 1)));
     size_t total = 0;
-    for (int l = 0; l < A.L; ++l) total += (size_t)A.l[l].rows * (A.l[l].cols + 1);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    for (int l = lo; l < hi; ++l) total += (size_t)A.l[l].rows * (A.l[l].cols + 1);
+    for (size_t i = first; i < total; i += step) {
         size_t k = i;
-        int l = 0;
+        int l = lo;
         while (k >= (size_t)A.l[l].rows * (A.l[l].cols + 1)) {
             k -= (size_t)A.l[l].rows * (A.l[l].cols + 1);
             ++l;
@@ -432,13 +529,13 @@ __global__ void adam_all_kernel(const AdamArgs A) {
         if (k < nw) {
             w = Ly.W + k; m = Ly.mW + k; v = Ly.vW + k;
             gi = 0.f;
-            for (int z = 0; z < Ly.ksplit; ++z) gi += Ly.gW[(size_t)z * nw + k];
+            for (int z = 0; z < Ly.ksplit; ++z) gi += __ldcg(&Ly.gW[(size_t)z * nw + k]);
             gi += td->wd * *w;
         } else {
             const int o = (int)(k - nw);
             w = Ly.b + o; m = Ly.mb + o; v = Ly.vb + o;
             gi = 0.f;
-            for (int mt = 0; mt < Ly.ntiles; ++mt) gi += Ly.cs[(size_t)mt * Ly.rows + o];
+            for (int mt = 0; mt < Ly.ntiles; ++mt) gi += __ldcg(&Ly.cs[(size_t)mt * Ly.rows + o]);
         }
         const float mi = b1 * *m + (1.f - b1) * gi;
         const float vi = b2 * *v + (1.f - b2) * gi * gi;
@@ -453,6 +550,10 @@ __global__ void adam_all_kernel(const AdamArgs A) {
             Ly.WbT[(size_t)c * Ly.rows + r] = hb;
         }
     }
+}
+
+__global__ void adam_all_kernel(const AdamArgs A) {
+    adam_dev(A, A.td->t, A.td->sched, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 __global__ void adam_advance_kernel(TrainDev* td) {
@@ -485,6 +586,139 @@ __global__ void destandardize_kernel(const float* Y, int ldy, int n, int n_out, 
     }
 }
 
+// ---------------------------------------------------------------- fused epoch
+// One training epoch in one cooperative launch.  Every CTA (one per SM) walks
+// the phases of each minibatch -- standardized inputs, the forward GEMMs layer
+// by layer, the loss gradient, the backward GEMMs of each layer (the weight
+// gradient and the input gradient together: both read only dZ_l) and Adam --
+// taking the phase's work items (GEMM tiles, loss tiles, element ranges) in
+// turn, with a grid barrier between phases: 2L + 2 barriers per minibatch (Adam
+// runs inside the backward phases, see below).
+// Tensor memory and the stage barriers are set up once per CTA.  The minibatch
+// loop needs no host round trip: rows, Adam step and schedule position follow
+// from the minibatch index, and the step count is written back at the end.
+struct GemmPlan {
+    GemmArgs g;
+    int S, tx, ty, tz;  // stages; tile grid (column tiles, row tiles, K splits)
+};
+struct EpochArgs {
+    GemmPlan fwd[kMaxLayers], dw[kMaxLayers], dz[kMaxLayers];  // dz[l]: dZ_{l-1} from dZ_l (l >= 1)
+    AdamArgs adam;
+    LossArgs loss;
+    int loss_tx, loss_ty;
+    const float* X;
+    const int* idx;
+    int n_in;
+    const float *mu_in, *sd_in;
+    bf16 *H0, *H0T;
+    int ld0, L, Bp, bs, nmb;
+    int64_t n;
+    TrainDev* td;
+    unsigned *bar_count, *bar_gen;  // grid barrier
+    int* abort_flag;                // a barrier wait gave up: every CTA leaves
+};
+
+// Grid barrier of a cooperative launch (all CTAs resident): arrive on a counter,
+// the last arrival resets it and advances the generation the others wait for.
+// Each wait is bounded (about 2 s of SM clock); one that gives up raises the
+// abort flag, which every CTA sees at its next barrier.  Returns false on abort.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* abort_flag) {
+    __shared__ int s_go;
+    __syncthreads();  // the CTA's writes before the barrier are ordered before thread 0's release
+    if (threadIdx.x == 0) {
+        volatile int* vabort = abort_flag;
+        const unsigned g0 = ld_acquire_gpu(gen);
+        int go = 1;
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(gen) == g0) {
+                if (*vabort || clock64() - t0 > 4000000000LL) {
+                    atomicExch(abort_flag, 1);
+                    go = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (*vabort) go = 0;
+        s_go = go;
+    }
+    __syncthreads();  // every thread's later reads are ordered after thread 0's acquire
+    return s_go != 0;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) train_epoch_kernel(const __grid_constant__ EpochArgs E) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar[TC_MAXS];
+    __shared__ uint32_t tmem_slot;
+    TcCtx ctx;
+    tc_setup(ctx, bar, &tmem_slot, 32u);
+    const long long t0 = E.td->t, s0 = E.td->sched;
+    const size_t first = (size_t)blockIdx.x * TC_THREADS + threadIdx.x, step = (size_t)gridDim.x * TC_THREADS;
+    bool ok = true, go = true;
+    // the tiles of one or two GEMMs as one work list
+    auto run = [&](const GemmPlan& p, int mv, const GemmPlan* q, int mvq) {
+        const int np = p.tx * p.ty * p.tz, nq = q ? q->tx * q->ty * q->tz : 0;
+        for (int t = blockIdx.x; t < np + nq; t += gridDim.x) {
+            const GemmPlan& pl = t < np ? p : *q;
+            const int u = t < np ? t : t - np;
+            GemmArgs g = pl.g;
+            const int mvalid = t < np ? mv : mvq;
+            if (mvalid >= 0) g.Mvalid = mvalid;
+            const int bx = u % pl.tx, rest = u / pl.tx;
+            ok = gemm_tile<TC_BN>(g, pl.S, bx, rest % pl.ty, rest / pl.ty, ctx, base) && ok;
+        }
+    };
+    // Adam of layer l runs in the backward phase of layer l-1 (which reads neither
+    // W_l nor its gradients' producers), Adam of layer 0 in the next minibatch's
+    // input phase (the first forward GEMM reads W_0 after that barrier) or in a
+    // last phase of its own
+    for (int mb = 0; mb < E.nmb && go; ++mb) {
+        const int64_t r0 = (int64_t)mb * E.bs;
+        const int nb = (int)min((int64_t)E.bs, E.n - r0);
+        load_inputs_dev(E.X, E.idx, r0, nb, E.n_in, E.mu_in, E.sd_in, E.H0, E.ld0, E.Bp, E.H0T, first, step);
+        if (mb > 0) adam_dev(E.adam, t0 + mb - 1, s0 + mb - 1, first, step, 0, 1);
+        go = grid_barrier(E.bar_count, E.bar_gen, E.abort_flag);
+        for (int l = 0; l < E.L && go; ++l) {
+            run(E.fwd[l], nb, nullptr, -1);
+            go = grid_barrier(E.bar_count, E.bar_gen, E.abort_flag);
+        }
+        if (!go) break;
+        LossArgs la = E.loss;
+        la.r0 = r0;
+        la.n = nb;
+        for (int t = blockIdx.x; t < E.loss_tx * E.loss_ty; t += gridDim.x)
+            loss_grad_tile(la, t % E.loss_tx, t / E.loss_tx, reinterpret_cast<float(*)[65]>(base));
+        go = grid_barrier(E.bar_count, E.bar_gen, E.abort_flag);
+        for (int l = E.L - 1; l >= 0 && go; --l) {
+            run(E.dw[l], -1, l > 0 ? &E.dz[l] : nullptr, nb);
+            if (l + 1 < E.L) adam_dev(E.adam, t0 + mb, s0 + mb, first, step, l + 1, l + 2);
+            go = grid_barrier(E.bar_count, E.bar_gen, E.abort_flag);
+        }
+    }
+    if (go && E.nmb > 0) {
+        adam_dev(E.adam, t0 + E.nmb - 1, s0 + E.nmb - 1, first, step, 0, 1);
+        go = grid_barrier(E.bar_count, E.bar_gen, E.abort_flag);
+    }
+    if (go && blockIdx.x == 0 && threadIdx.x == 0) {
+        E.td->t = t0 + E.nmb;
+        E.td->sched = s0 + E.nmb;
+    }
+    if ((!ok || !go) && threadIdx.x == 0) atomicExch(&E.td->tc_err, 1);
+    tc_teardown(ctx, 32u);
+}
+
 }  // namespace cl
 
 // ---------------------------------------------------------------- host side
@@ -511,16 +745,12 @@ struct cl_surrogate {
     cl::TrainDev* tdev = nullptr;  // device optimizer state
     int* d_perm = nullptr;         // sample order of the current epoch
     int64_t perm_cap = 0;
-    cudaStream_t cstream = nullptr;  // private stream for graph capture
-    // captured training epoch, valid for (n, batch, shuffled) and the buffers
-    // it was captured with (gen counts reallocations)
-    cudaGraphExec_t epoch_exec = nullptr;
-    int64_t g_n = -1;
-    int g_bs = -1, g_shuf = -1;
-    long long g_gen = -1, gen = 0;
+    long long gen = 0;  // counts reallocations of the buffers
     long long epochs_done = 0;
     uint64_t seed = 0;
     int sms = 1;
+    std::vector<cl::GemmPlan>* record = nullptr;  // set: gemm() records its plan instead of launching
+    unsigned* d_gridbar = nullptr;                // fused epoch: barrier counter, generation, abort flag
 };
 
 namespace {
@@ -566,6 +796,16 @@ void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ld
     constexpr int BN = cl::TC_BN;  // N is a multiple of 32
     const int nk = (g.kchunk + cl::TC_BK - 1) / cl::TC_BK;
     const int stages = nk < cl::TC_MAXS ? nk : cl::TC_MAXS;
+    if (S->record) {
+        cl::GemmPlan p;
+        p.g = g;
+        p.S = stages;
+        p.tx = (N + BN - 1) / BN;
+        p.ty = (M + cl::TC_BM - 1) / cl::TC_BM;
+        p.tz = splits;
+        S->record->push_back(p);
+        return;
+    }
     static bool attr_set = false;  // the stage ring needs the opt-in shared-memory size
     if (!attr_set) {
         cudaFuncSetAttribute(cl::gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -656,8 +896,9 @@ void refresh_bf16(cl_surrogate* S) {
 // the data in S->Xd, standardized by mu/sd; `training` also writes the transposed
 // activations that the weight gradients read
 void forward(cl_surrogate* S, const int* idx, int64_t r0, int n, bool training) {
-    cl::load_inputs_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->Xd, idx, r0, n, S->n_in, S->mu_in, S->sd_in, S->H[0],
-                                                              S->P[0], S->Bp, training ? S->HT[0] : nullptr);
+    if (!S->record)
+        cl::load_inputs_kernel<<<S->sms * 4, 256, 0, S->stream>>>(S->Xd, idx, r0, n, S->n_in, S->mu_in, S->sd_in,
+                                                                  S->H[0], S->P[0], S->Bp, training ? S->HT[0] : nullptr);
     for (int l = 0; l < S->L; ++l) {
         const bool last = l == S->L - 1;
         GemmExtra x;
@@ -670,6 +911,15 @@ void forward(cl_surrogate* S, const int* idx, int64_t r0, int n, bool training) 
     }
 }
 
+cl::LossArgs loss_args(cl_surrogate* S, const int* idx, int64_t r0, int n, int cur) {
+    const int L = S->L;
+    cl::LossArgs a;
+    a.Y = S->Z[L - 1]; a.ldy = S->P[L]; a.T = S->Td; a.idx = idx; a.r0 = r0; a.n = n; a.n_out = S->n_out;
+    a.mu = S->mu_out; a.sd = S->sd_out; a.dZ = S->dZ[cur]; a.dZb = S->dZb[cur]; a.dZbT = S->dZbT[cur];
+    a.ld = S->P[L]; a.Bp = S->Bp; a.cs = S->cs[L - 1]; a.loss = S->dloss;
+    return a;
+}
+
 // backward: weight gradients into gW, the bias gradients as tile column sums in
 // cs (summed by the optimizer, or by bias_grads); loss sum added into S->dloss.
 // Per layer two GEMMs: dW_l = dZ_l^T H_l, and dZ_{l-1} = (dZ_l W_l) GELU'(Z_{l-1})
@@ -678,9 +928,9 @@ void forward(cl_surrogate* S, const int* idx, int64_t r0, int n, bool training) 
 void backward(cl_surrogate* S, const int* idx, int64_t r0, int n) {
     const int L = S->L, Bp = S->Bp;
     int cur = 0;
-    cl::loss_grad_kernel<<<dim3((Bp + cl::LG_ROWS - 1) / cl::LG_ROWS, (S->P[L] + 63) / 64), 256, 0, S->stream>>>(
-        S->Z[L - 1], S->P[L], S->Td, idx, r0, n, S->n_out, S->mu_out, S->sd_out, S->dZ[cur], S->dZb[cur],
-        S->dZbT[cur], S->P[L], Bp, S->cs[L - 1], S->dloss);
+    if (!S->record)
+        cl::loss_grad_kernel<<<dim3((Bp + cl::LG_ROWS - 1) / cl::LG_ROWS, (S->P[L] + 63) / 64), 256, 0,
+                               S->stream>>>(loss_args(S, idx, r0, n, cur));
     for (int l = L - 1; l >= 0; --l) {
         const int Pin = S->P[l], Pout = S->P[l + 1];
         GemmExtra xw;
@@ -765,8 +1015,7 @@ cl_status surrogate_destroy(cl_surrogate* S) {
     cudaFree(S->dloss);
     cudaFree(S->tdev);
     cudaFree(S->d_perm);
-    if (S->epoch_exec) cudaGraphExecDestroy(S->epoch_exec);
-    if (S->cstream) cudaStreamDestroy(S->cstream);
+    cudaFree(S->d_gridbar);
     delete S;
     return CL_OK;
 }
@@ -814,7 +1063,7 @@ cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t d
     ok = ok && cudaMalloc(&S->mu_in, 4 * n_in) == cudaSuccess && cudaMalloc(&S->sd_in, 4 * n_in) == cudaSuccess &&
          cudaMalloc(&S->mu_out, 4 * n_out) == cudaSuccess && cudaMalloc(&S->sd_out, 4 * n_out) == cudaSuccess &&
          cudaMalloc(&S->dloss, sizeof(double)) == cudaSuccess && cudaMalloc(&S->tdev, sizeof(cl::TrainDev)) == cudaSuccess &&
-         cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking) == cudaSuccess;
+         cudaMalloc(&S->d_gridbar, 4 * sizeof(unsigned)) == cudaSuccess;
     if (!ok) {
         surrogate_destroy(S);
         return sfail(CL_ERR_OOM, "surrogate_create: parameters");
@@ -912,6 +1161,50 @@ cl_status surrogate_loss_grad(cl_surrogate* S, const float* X, const float* T, i
     return CL_OK;
 }
 
+// Arguments of the fused epoch for n rows in minibatches of bs (sample order idx)
+// on the current buffers: the GEMM plans are the ones forward() and backward()
+// would launch for a full minibatch, recorded instead of launched.
+cl_status make_epoch(cl_surrogate* S, const int* idx, int64_t n, int bs, cl::EpochArgs& E, size_t& smem) {
+    std::vector<cl::GemmPlan> rec;
+    S->record = &rec;
+    forward(S, idx, 0, bs, true);
+    backward(S, idx, 0, bs);
+    S->record = nullptr;
+    const int L = S->L;
+    if ((int)rec.size() != 3 * L - 1) return sfail(CL_ERR_CUDA, "surrogate_train: epoch plan");
+    memset(&E, 0, sizeof(E));
+    size_t k = 0;
+    for (int l = 0; l < L; ++l) E.fwd[l] = rec[k++];
+    for (int l = L - 1; l >= 0; --l) {
+        E.dw[l] = rec[k++];
+        if (l > 0) E.dz[l] = rec[k++];
+    }
+    E.adam = adam_args(S);
+    E.loss = loss_args(S, idx, 0, bs, 0);
+    E.loss_tx = (S->Bp + cl::LG_ROWS - 1) / cl::LG_ROWS;
+    E.loss_ty = (S->P[L] + 63) / 64;
+    E.X = S->Xd;
+    E.idx = idx;
+    E.n_in = S->n_in;
+    E.mu_in = S->mu_in;
+    E.sd_in = S->sd_in;
+    E.H0 = S->H[0];
+    E.H0T = S->HT[0];
+    E.ld0 = S->P[0];
+    E.L = L;
+    E.Bp = S->Bp;
+    E.bs = bs;
+    E.nmb = (int)((n + bs - 1) / bs);
+    E.n = n;
+    E.td = S->tdev;
+    E.bar_count = S->d_gridbar;
+    E.bar_gen = S->d_gridbar + 1;
+    E.abort_flag = reinterpret_cast<int*>(S->d_gridbar + 2);
+    smem = 1024 + (size_t)cl::LG_ROWS * 65 * sizeof(float);
+    for (const auto& p : rec) smem = std::max<size_t>(smem, cl::tc_smem_bytes(cl::TC_BN, p.S));
+    return CL_OK;
+}
+
 cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64_t n, const cl_train_cfg* cfg,
                           float* loss_history) {
     if (!S || !X || !Y || !cfg || n < 1 || n > (1 << 24) || cfg->epochs < 1 || cfg->batch < 1 || !(cfg->lr > 0))
@@ -970,41 +1263,25 @@ cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64
         }
         perm.resize(n);
     }
-    // one epoch = memset of the loss sum + every minibatch's forward, backward
-    // and Adam update, captured once as a CUDA graph and replayed per epoch
-    if (!S->epoch_exec || S->g_n != n || S->g_bs != bs || S->g_shuf != shuf || S->g_gen != S->gen) {
-        if (S->epoch_exec) cudaGraphExecDestroy(S->epoch_exec);
-        S->epoch_exec = nullptr;
-        cudaStream_t user = S->stream;
-        S->stream = S->cstream;
-        cudaGraph_t graph;
-        cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
-            const int* idx = shuf ? S->d_perm : nullptr;
-            for (int64_t r0 = 0; r0 < n; r0 += bs) {
-                const int nb = (int)std::min<int64_t>(bs, n - r0);
-                forward(S, idx, r0, nb, true);
-                backward(S, idx, r0, nb);
-                cl::adam_all_kernel<<<S->sms * 2, 256, 0, S->stream>>>(adam_args(S));
-                cl::adam_advance_kernel<<<1, 1, 0, S->stream>>>(S->tdev);
-            }
-            e = cudaStreamEndCapture(S->stream, &graph);
+    // one epoch = one cooperative launch of the fused epoch kernel (one CTA per SM)
+    cl::EpochArgs E;
+    size_t smem = 0;
+    s = make_epoch(S, shuf ? S->d_perm : nullptr, n, bs, E, smem);
+    if (s != CL_OK) return s;
+    {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(cl::train_epoch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cl::tc_smem_bytes(cl::TC_BN, cl::TC_MAXS));
+            attr_set = true;
         }
-        S->stream = user;
-        if (e == cudaSuccess) {
-            e = cudaGraphInstantiate(&S->epoch_exec, graph, 0);
-            cudaGraphDestroy(graph);
-        }
-        if (e != cudaSuccess) {
-            S->epoch_exec = nullptr;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cl::train_epoch_kernel, cl::TC_THREADS, smem) !=
+                cudaSuccess ||
+            per_sm < 1) {
             cudaGetLastError();
-            return sfail(CL_ERR_CUDA, std::string("surrogate_train: epoch graph: ") + cudaGetErrorString(e));
+            return sfail(CL_ERR_CUDA, "surrogate_train: the fused epoch does not fit on an SM");
         }
-        S->g_n = n;
-        S->g_bs = bs;
-        S->g_shuf = shuf;
-        S->g_gen = S->gen;
     }
     for (int ep = 0; ep < cfg->epochs; ++ep) {
         if (shuf) {
@@ -1019,7 +1296,13 @@ cl_status surrogate_train(cl_surrogate* S, const float* X, const float* Y, int64
             }
             cudaMemcpyAsync(S->d_perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, S->stream);
         }
-        if (cudaGraphLaunch(S->epoch_exec, S->stream) != cudaSuccess) return sfail(CL_ERR_CUDA, "surrogate_train: launch");
+        cudaMemsetAsync(S->dloss, 0, sizeof(double), S->stream);
+        cudaMemsetAsync(S->d_gridbar, 0, 4 * sizeof(unsigned), S->stream);
+        void* args[] = {&E};
+        cudaError_t le = cudaLaunchCooperativeKernel((const void*)cl::train_epoch_kernel, dim3(S->sms),
+                                                     dim3(cl::TC_THREADS), args, smem, S->stream);
+        if (le != cudaSuccess)
+            return sfail(CL_ERR_CUDA, std::string("surrogate_train: epoch launch: ") + cudaGetErrorString(le));
         ++S->epochs_done;
         if (loss_history || shuf) {
             // the host order buffer is rewritten next epoch: wait for this one
