@@ -707,7 +707,7 @@ def main():
         host = [torch.empty((N, N, N), dtype=torch.float32, pin_memory=True) for _ in range(4)]
         means = [lat.get_stored(w, host[i])[1] for i, w in enumerate(which)]
         mm0 = lat.measure_means()
-        reps = 3
+        reps = 8  # about 1 s: an occasional slow upload (0.33 s instead of 0.08 s) is averaged over more steps
         ph = {"set_stored": 0.0, "evolve": 0.0, "measure": 0.0}
         uploads = []
         for i, w in enumerate(which):  # one untimed pass over the host buffers
@@ -753,7 +753,6 @@ def main():
         except Exception as exc:  # the lattice number above stands on its own
             ens = {"error_running": repr(exc)}
     if rank == 0:
-        prof = os.path.join(ROOT, "profiles", "scalar_pass_vv4_1024_fp32.md")
         line = {
             "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
