@@ -100,11 +100,14 @@ __device__ __forceinline__ TileXYZ decode_tile(const Geometry& g, int tile) {
     return t;
 }
 
-// FIXED: the tile of 32 x 8 threads is compiled in (the shape of every lattice
-// with N a multiple of 128 in FP32, 64 in FP64), so the stage layout and the
-// neighbour offsets are constants; otherwise they come from the geometry.
-template <typename T, int NF, int P, bool FIXED>
-__global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const __grid_constant__ ScalarArgs A) {
+// FB = 8 or 16: the tile of 32 x FB threads is compiled in (32 x 8 is the shape
+// of every lattice with N a multiple of 128 in FP32, 64 in FP64; 32 x 16 one
+// 512-thread block per SM), so the stage layout and the neighbour offsets are
+// constants; FB = 0: they come from the geometry (at most 256 threads).
+template <typename T, int NF, int P, int FB>
+__global__ void __launch_bounds__(FB == 16 ? 512 : 256, FB == 16 ? 1 : 2)
+    scalar_pass_kernel(const __grid_constant__ ScalarArgs A) {
+    constexpr bool FIXED = FB != 0;
     DevState* st = A.st;
     if (st->error) return;
     constexpr int V = VecT<T>::V;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const __grid_consta
     constexpr int NA = 2 * NF;
     constexpr int kFold = sizeof(T) == 4 ? 8 : 1 << 30;  // planes per FP32 run of the thread sums
     const Geometry& G = A.geo;
-    const int N = G.N, BX = FIXED ? 32 : G.BX, BY = FIXED ? 8 : G.BY, ZC = G.ZC, S = G.S;
+    const int N = G.N, BX = FIXED ? 32 : G.BX, BY = FIXED ? FB : G.BY, ZC = G.ZC, S = G.S;
     const int TX = BX * V;
     const StageLayout SL = stage_layout(BX, BY, V, (int)sizeof(T));
     const int AE = (int)(SL.arr / sizeof(T));  // elements of one array block
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const __grid_consta
     extern __shared__ unsigned char smraw[];
     T* sm = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~(uintptr_t)127);
     const uint32_t sm_addr = smem_u32(sm);
-    __shared__ double bacc[8][16];
+    __shared__ double bacc[16][16];
     __shared__ __align__(8) uint64_t full[8];  // one per stage: the plane's bytes have landed
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int lin = ty * BX + tx;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(256, 2) scalar_pass_kernel(const __grid_consta
     const int lane = FIXED ? tx : lin & 31, warp = FIXED ? ty : lin >> 5, nwarps = (nthr + 31) >> 5;
     const int nlanes = min(32, nthr - 32 * warp);
     const unsigned wmask = nlanes >= 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
-    for (int i = lin; i < 8 * 16; i += nthr) (&bacc[0][0])[i] = 0.0;
+    for (int i = lin; i < 16 * 16; i += nthr) (&bacc[0][0])[i] = 0.0;
     // nprod producer warps issue the copies, producer pw those of arrays pw, pw + nprod, ...
     // They are taken from the middle of the block, away from the first and last
     // thread rows, which drift the y-halo rows.  Producer warps need five lanes:
@@ -460,15 +463,19 @@ __global__ void scalar_drift_kernel(T* phi0, T* phi1, const T* pi0, const T* pi1
 
 // --------------------------------------------------------------- host side
 
-static bool fixed_tile(const Geometry& g) { return g.BX == 32 && g.BY == 8; }
+// the compiled-in tile for this geometry: 8 or 16 rows of 32 threads, else 0
+static int fixed_tile(const Geometry& g) { return g.BX == 32 && (g.BY == 8 || g.BY == 16) ? g.BY : 0; }
 
-template <typename T, int NF, bool FX> static const void* kptr_p(int pexp) {
-    if (pexp == 4) return (const void*)scalar_pass_kernel<T, NF, 4, FX>;
-    if (pexp == 6) return (const void*)scalar_pass_kernel<T, NF, 6, FX>;
-    return (const void*)scalar_pass_kernel<T, NF, 2, FX>;
+template <typename T, int NF, int FB> static const void* kptr_p(int pexp) {
+    if (pexp == 4) return (const void*)scalar_pass_kernel<T, NF, 4, FB>;
+    if (pexp == 6) return (const void*)scalar_pass_kernel<T, NF, 6, FB>;
+    return (const void*)scalar_pass_kernel<T, NF, 2, FB>;
 }
 template <typename T, int NF> static const void* kptr_f(const Lattice* L) {
-    return fixed_tile(L->geo) ? kptr_p<T, NF, true>(L->mc.pexp) : kptr_p<T, NF, false>(L->mc.pexp);
+    const int fb = fixed_tile(L->geo);
+    if constexpr (sizeof(T) == 4)  // the 32 x 16 tile exists in FP32 only
+        if (fb == 16) return kptr_p<T, NF, 16>(L->mc.pexp);
+    return fb == 8 ? kptr_p<T, NF, 8>(L->mc.pexp) : kptr_p<T, NF, 0>(L->mc.pexp);
 }
 
 static const void* scalar_kernel_ptr(const Lattice* L) {
@@ -481,7 +488,8 @@ static const void* scalar_kernel_ptr(const Lattice* L) {
 // values that do not fit N are ignored.
 void scalar_geometry(Lattice* L) {
     Geometry& g = L->geo;
-    int want_by = 8, want_zc = 128, want_s = 5, want_bx = 32;
+    // FP32: 32 x 16 threads (one 512-thread block per SM, half the y-halo re-reads of 32 x 8); FP64: 32 x 8
+    int want_by = L->prec == CL_FP32 ? 16 : 8, want_zc = 128, want_s = 5, want_bx = 32;
     if (const char* env = getenv("CL_SCALAR_TILE")) {
         int a = 0, b = 0, c = 0, d = 0;
         const int got = sscanf(env, "%d,%d,%d,%d", &a, &b, &c, &d);
@@ -499,8 +507,10 @@ void scalar_geometry(Lattice* L) {
     int bx = nv < want_bx ? nv : want_bx;
     while (nv % bx != 0) --bx;
     g.BX = bx;
+    // at most 256 threads, except the compiled-in 32 x 16 tile in FP32 (one 512-thread block per SM)
     int by = 256 / g.BX;
     if (g.BX == want_bx && want_by < by) by = want_by;
+    if (g.BX == 32 && want_bx == 32 && want_by == 16 && L->prec == CL_FP32) by = 16;
     if (by > N) by = N;
     while (N % by != 0) --by;
     g.BY = by;
@@ -546,7 +556,10 @@ void scalar_geometry(Lattice* L) {
 template <typename T, int NF, int P>
 static cudaError_t launch_t(Lattice* L, const ScalarArgs& A, cudaStream_t s) {
     const Geometry& g = L->geo;
-    auto fn = fixed_tile(g) ? scalar_pass_kernel<T, NF, P, true> : scalar_pass_kernel<T, NF, P, false>;
+    const int fb = fixed_tile(g);
+    auto fn = fb == 8 ? scalar_pass_kernel<T, NF, P, 8> : scalar_pass_kernel<T, NF, P, 0>;
+    if constexpr (sizeof(T) == 4)
+        if (fb == 16) fn = scalar_pass_kernel<T, NF, P, 16>;
     fn<<<g.grid, dim3(g.BX, g.BY), g.smem, s>>>(A);
     return cudaGetLastError();
 }

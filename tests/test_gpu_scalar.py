@@ -182,16 +182,18 @@ def test_fp32_pointwise_parity_100_steps():
     lat.close()
 
 
-def test_fp32_production_tile_matches_oracle():
-    """128^3 two-field lattice on the x-y tile the 1024^3 workload runs (32 x 8
-    threads of 4 sites, a 5-stage ring; shorter z runs): 100 expanding VV4 steps
-    against the oracle within the FP32 pointwise bound."""
-    N = 128
+@pytest.mark.parametrize("N,steps", [(128, 100), (256, 40)])
+def test_fp32_production_tile_matches_oracle(N, steps):
+    """Two-field lattices on the compiled-in x-y tiles of the FP32 pass: 32 x 8
+    threads of 4 sites at 128^3 (after the small-lattice halving of the rows)
+    and 32 x 16 at 256^3 (the tile of the 1024^3 workload), a 5-stage ring,
+    several tiles in every direction: expanding VV4 steps in two calls against
+    the oracle within the FP32 pointwise bound."""
     lat, ref = make_pair(N, 2, 2, 0.0, fmp=1.4, lam=1.0, q=400.0, integ="vv4", prec=cl.CL_FP32, kIR=0.5, dt=0.005,
                          seed=21, amp=1e-3, means=[1.0, 0.0])
     lat.evolve(30)
-    lat.evolve(70)
-    ref.vv_steps(oracle.VV4, 0.005, 100)
+    lat.evolve(steps - 30)
+    ref.vv_steps(oracle.VV4, 0.005, steps)
     phi, pi = fields_of(lat, 2)
     for i in range(2):
         assert rel(phi[i] - phi[i].mean(), ref.phi[i] - ref.phi[i].mean()) < 1e-5

@@ -161,3 +161,22 @@ def test_training_fits_a_smooth_map_and_predict_undoes_standardization():
     Ye, _ = forward_bf16(Ws, bs, (X[3584:] - mu) / sd)
     assert rel_fro((P - muy) / sdy, Ye) < 1e-3, rel_fro((P - muy) / sdy, Ye)
     net.close()
+
+
+def test_one_epoch_launch_equals_one_minibatch_per_call():
+    """The fused epoch walks its minibatches in order inside one launch: its
+    result equals, bit for bit, that of one call per minibatch (same rows, same
+    Adam step count, constant step size), a ragged last minibatch included; and
+    training is deterministic."""
+    X, T = data(300, 21)
+    nets = [make_net(seed=8)[0] for _ in range(3)]
+    kw = dict(batch=128, lr=1e-3, standardize=False)
+    nets[0].train(X, T, epochs=1, **kw)
+    nets[1].train(X, T, epochs=1, **kw)
+    for lo, hi in ((0, 128), (128, 256), (256, 300)):
+        nets[2].train(X[lo:hi], T[lo:hi], epochs=1, **kw)
+    p = [net.get_params() for net in nets]
+    assert np.array_equal(p[0], p[1])
+    assert np.array_equal(p[0], p[2]), np.max(np.abs(p[0] - p[2]))
+    for net in nets:
+        net.close()
