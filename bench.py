@@ -760,7 +760,7 @@ def main():
             "config": dict(workload_config(N), parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": measured_traffic(N), "peak_kind": peak_kind,
-                         "kernel": "scalar_pass_kernel<float,2,2,1>", "bytes_per_launch": alg_bytes,
+                         "kernel": "scalar_pass_kernel<float,2,2,16>", "bytes_per_launch": alg_bytes,
                          "launch_ms": ms / npass},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": npass, "clocks": clk,
             "hubble_violation": mm["hubble_violation"], "a": mm["a"], "error_vs_fp64": err64,
