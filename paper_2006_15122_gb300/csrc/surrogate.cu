@@ -472,15 +472,16 @@ __global__ void bias_grad_kernel(const float* cs, int ntiles, int cols, float* g
     gb[c] = s;
 }
 
-// Optimizer state on the device, so that a captured training epoch can be
-// replayed unchanged: the Adam step count, the schedule position and the
-// hyper-parameters of the current call.
+// Optimizer state on the device: the Adam step count, the schedule position and
+// the hyper-parameters of the current call.  An epoch launch reads the step
+// count and schedule position at its start, derives each minibatch's from its
+// index, and writes them back at its end.
 struct TrainDev {
     long long t;      // Adam steps taken by this handle (bias corrections use t + 1)
     long long sched;  // minibatch steps taken in this call (cosine schedule position)
     long long total;  // minibatch steps of this call
     float lr, lr_end, b1, b2, eps, wd;
-    int tc_err;  // a tensor-core GEMM gave up waiting for its MMAs (never expected)
+    int tc_err;  // a tensor-core GEMM or a grid barrier gave up waiting (never expected)
 };
 
 // Adam on FP32 master weights for every layer in one launch: weights (L2 decay)
@@ -550,15 +551,6 @@ __device__ void adam_dev(const AdamArgs& A, long long t0, long long sched, size_
             Ly.WbT[(size_t)c * Ly.rows + r] = hb;
         }
     }
-}
-
-__global__ void adam_all_kernel(const AdamArgs A) {
-    adam_dev(A, A.td->t, A.td->sched, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
-}
-
-__global__ void adam_advance_kernel(TrainDev* td) {
-    td->t += 1;
-    td->sched += 1;
 }
 
 // W ~ N(0, 1/fan_in) in the valid region (Box-Muller on Philox draws), zero padding
@@ -810,10 +802,9 @@ void gemm(cl_surrogate* S, const cl::bf16* A, int lda, const cl::bf16* B, int ld
     if (!attr_set) {
         cudaFuncSetAttribute(cl::gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cl::tc_smem_bytes(BN, cl::TC_MAXS));
-        // one shared-memory carveout for every kernel of a training step, so that
-        // consecutive launches need no reconfiguration of the SMs' L1/shared split
+        // one shared-memory carveout for the per-launch kernels, so that consecutive
+        // launches need no reconfiguration of the SMs' L1/shared split
         const void* fns[] = {(const void*)cl::gemm_tc_kernel<BN>, (const void*)cl::loss_grad_kernel,
-                             (const void*)cl::adam_all_kernel, (const void*)cl::adam_advance_kernel,
                              (const void*)cl::load_inputs_kernel};
         for (const void* f : fns) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaGetLastError();
