@@ -32,10 +32,11 @@
 // planes in z; z-neighbours live in registers, x-y neighbours of the drifted
 // plane in a ring of S shared-memory stages, one plane each (one barrier per
 // plane).  Each plane arrives by tensor-memory-access copies (TMA) issued by
-// the first warp: per array the interior box (TX x BY), the two halo rows
-// (TX x 1) and the two halo column strips (V x BY), periodic wrap by the
-// choice of each box's coordinates; one mbarrier per stage counts the bytes.
-// Plane z+S-2 is requested while plane z is computed.  The grid is persistent
+// up to four warps from the middle of the block, one array each: per array the
+// interior box (TX x BY), the two halo rows (TX x 1) and the two halo column
+// strips (V x BY), periodic wrap by the choice of each box's coordinates; one
+// mbarrier per stage counts the bytes, and one other warp waits on it for the
+// block.  Plane z+S-2 is requested while plane z is computed.  The grid is persistent
 // (grid-stride over tiles, y-tiles fastest so that y-halos are L2 hits of
 // concurrently running tiles).
 #include <math.h>
