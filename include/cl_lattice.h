@@ -39,6 +39,12 @@
 extern "C" {
 #endif
 
+/* Status of every call; cl_last_error gives the reason.  CL_ERR_TIMEOUT: a
+ * Gauss-Legendre step whose stage equations did not converge (the lattice
+ * stops at the last completed step), or a bounded device-side wait that gave
+ * up -- a field pass waiting for its tensor copies, a tensor-core GEMM waiting
+ * for its MMAs, a training epoch waiting at a grid barrier (none expected);
+ * errors found on the device are reported by the next call that synchronizes. */
 typedef enum {
     CL_OK = 0,
     CL_ERR_ARG = 1,
