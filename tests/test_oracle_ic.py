@@ -64,6 +64,31 @@ def test_vacuum_fluctuations_have_the_target_mode_variance():
     assert abs(phi[0].mean() - 1.0) < 1e-14 and abs(phi[1].mean()) < 1e-14
 
 
+def test_self_conjugate_modes_have_the_target_variance():
+    """The modes equal to their own conjugate (components in {0, N/2}) are real;
+    drawn as sqrt(2) Re of a complex draw they keep the target variance of the
+    other modes (reading 9 of the design).  Over 60 seeds the mean of
+    |dphi(n~)|^2 / T over the seven nonzero such modes is 1 within its sampling
+    error (chi-squared with one degree of freedom: standard error
+    sqrt(2 / (7 x 60)) = 0.069), and likewise for the momenta."""
+    N, kIR, seeds = 8, 0.5, 60
+    dx = 2 * np.pi / (kIR * N)
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=0.0, fmp2=0.0, lam=1.0, q=0.0)
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    sel = selfc & ~zero
+    assert sel.sum() == 7
+    w = np.sqrt((kIR * nabs[sel]) ** 2 + 1.0)  # V'' = lam for V = phi^2 / 2
+    T = 0.1 ** 2 * (N / dx) ** 3 / (2 * w)
+    rf, rp = [], []
+    for seed in range(seeds):
+        phi, pi, _ = scalar_ic(m, kIR, [1.0], [0.0], seed=seed, omega_over_fstar=0.1)
+        rf.append(np.abs(dft_forward(phi[0] - phi[0].mean()))[sel] ** 2 / T)
+        rp.append(np.abs(dft_forward(pi[0]))[sel] ** 2 / (T * w * w))
+    se = np.sqrt(2.0 / (7 * seeds))
+    assert abs(np.mean(rf) - 1.0) < 4 * se, np.mean(rf)
+    assert abs(np.mean(rp) - 1.0) < 4 * se, np.mean(rp)
+
+
 def test_ic_is_deterministic_in_the_seed():
     _, a, _, _ = _scalar_setup(seed=11)
     _, b, _, _ = _scalar_setup(seed=11)
