@@ -181,13 +181,18 @@ def _stream_ptr(stream):
     return C.c_void_p(int(stream))
 
 
-def _dev_ptr(t):
-    """(pointer, on_device) of a float64 buffer: numpy array or torch tensor."""
+def _dev_ptr(t, n=None):
+    """(pointer, on_device) of a contiguous float64 buffer: numpy array or torch
+    tensor, of exactly n elements when n is given.  Raises ValueError otherwise,
+    so that a short buffer never reaches a copy of n elements."""
     if isinstance(t, np.ndarray):
-        assert t.dtype == np.float64 and t.flags.c_contiguous
+        if t.dtype != np.float64 or not t.flags.c_contiguous or (n is not None and t.size != n):
+            raise ValueError("expected a contiguous float64 array of %s elements, got %s %s" % (n, t.dtype, t.shape))
         return C.c_void_p(t.ctypes.data), 0
     import torch  # only for device buffers
-    assert t.dtype == torch.float64 and t.is_contiguous()
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous() or \
+            (n is not None and t.numel() != n):
+        raise ValueError("expected a contiguous float64 array or tensor of %s elements" % n)
     return C.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0
 
 
@@ -298,14 +303,14 @@ class Lattice:
         N = self.N
         if out is None:
             out = np.zeros((N, N, N))
-        p, dev = _dev_ptr(out)
+        p, dev = _dev_ptr(out, N ** 3)
         _check(load().lattice_get_field(self.h, which, p, dev), self.h)
         return out
 
     def set_field(self, which, src):
         if isinstance(src, np.ndarray):
             src = np.ascontiguousarray(src, dtype=np.float64)
-        p, dev = _dev_ptr(src)
+        p, dev = _dev_ptr(src, self.N ** 3)
         _check(load().lattice_set_field(self.h, which, p, dev), self.h)
 
     def _stored_ptr(self, t):
@@ -347,9 +352,10 @@ class Lattice:
 class _Member(Lattice):
     """Borrowed handle of an ensemble member (owned by the ensemble)."""
 
-    def __init__(self, h, N):
+    def __init__(self, h, N, grid):
         self.h = h
         self.N = N
+        self.grid = grid
 
     def close(self):
         self.h = None
@@ -371,6 +377,7 @@ class Ensemble:
         self.h = h
         self.n = n
         self.Ns = list(Na)
+        self.grid = grid
 
     def evolve(self, nsteps):
         _check(load().ensemble_evolve(self.h, int(nsteps)))
@@ -401,7 +408,7 @@ class Ensemble:
     def member(self, i):
         h = C.c_void_p()
         _check(load().ensemble_member(self.h, int(i), C.byref(h)))
-        return _Member(h, self.Ns[i])
+        return _Member(h, self.Ns[i], self.grid)
 
     def close(self):
         if getattr(self, "h", None):

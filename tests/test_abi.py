@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2006_15122_gb300 as cl
@@ -156,3 +157,49 @@ def test_noalloc_rejects_bad_arguments_on_the_host():
     dummy = C.c_void_p(16)  # never dereferenced: the model is rejected first
     assert lib.lattice_energies_noalloc(C.byref(m), 8, 0.5, 1.0, dummy, dummy, dummy, None) == cl.CL_ERR_ARG
     assert b"1 or 2 fields" in lib.cl_last_error(None)
+
+
+def _unbound_lattice(N, precision=cl.CL_FP64):
+    """A Lattice object with no handle: the binding's own checks run, and any
+    call that got past them would fail on the NULL handle, not on memory."""
+    lat = object.__new__(cl.Lattice)
+    lat.h, lat.N, lat.grid = None, N, cl.make_grid(N, 0.5, 0.01, precision=precision)
+    return lat
+
+
+@pytest.mark.parametrize("buf", ["short", "long", "float32", "strided"])
+def test_field_copies_reject_buffers_of_the_wrong_size_or_type(buf):
+    """get_field / set_field copy exactly N^3 doubles; any other buffer is
+    refused before the library is called, so a short host array or device
+    tensor never takes a copy of N^3 elements."""
+    N = 4
+    a = {"short": np.zeros(N ** 3 - 1), "long": np.zeros(N ** 3 + 1), "float32": np.zeros(N ** 3, np.float32),
+         "strided": np.zeros(2 * N ** 3)[::2]}[buf]
+    lat = _unbound_lattice(N)
+    with pytest.raises(ValueError):
+        lat.get_field(cl.FIELD(0), a)
+    if buf != "float32" and buf != "strided":  # set_field converts dtype and layout of host arrays
+        with pytest.raises(ValueError):
+            lat.set_field(cl.FIELD(0), a)
+
+
+def test_field_copies_reject_short_tensors():
+    torch = pytest.importorskip("torch")
+    lat = _unbound_lattice(4)
+    for t in (torch.zeros(63, dtype=torch.float64), torch.zeros(64, dtype=torch.float32),
+              torch.zeros(128, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            lat.get_field(cl.FIELD(0), t)
+        with pytest.raises(ValueError):
+            lat.set_field(cl.FIELD(0), t)
+
+
+@pytest.mark.parametrize("precision", [cl.CL_FP32, cl.CL_FP64])
+def test_stored_copies_take_the_handle_precision(precision):
+    lat = _unbound_lattice(4, precision)
+    other = np.float64 if precision == cl.CL_FP32 else np.float32
+    for a in (np.zeros(64, other), np.zeros(63, np.float32 if precision == cl.CL_FP32 else np.float64)):
+        with pytest.raises(ValueError):
+            lat.get_stored(cl.FIELD(0), a)
+        with pytest.raises(ValueError):
+            lat.set_stored(cl.FIELD(0), a, 0.0)
