@@ -3,7 +3,7 @@
 import numpy as np
 import pytest
 
-from oracle import ScalarModel, U1Lattice, U1Model, philox
+from oracle import ScalarLattice, ScalarModel, U1Lattice, U1Model, philox
 from oracle.ic import mode_map, scalar_ic, u1_ic
 from oracle.spectra import dft_forward, shell_bins, spectrum
 
@@ -88,6 +88,43 @@ def test_self_conjugate_modes_have_the_target_variance():
     assert abs(np.mean(rf) - 1.0) < 4 * se, np.mean(rf)
     assert abs(np.mean(rp) - 1.0) < 4 * se, np.mean(rp)
 
+
+
+def test_vacuum_draw_in_an_expanding_background():
+    """At a = 2, alpha = 1/2 and a program Hubble rate H of order one (section 7.1):
+      - the homogeneous momentum is pi = a^{3-alpha} phi' (section 4.2.3), so the
+        state without fluctuations has E_K = phi'^2/(2 a^{2 alpha}) (section 4.4.1);
+      - H is the one of the evolution's Hubble constraint for that state, H = b/a;
+      - |dphi(n~)|^2 averages (w*/f*)^2 (N/dx)^3/(2 a^2 w_k), w_k = sqrt(k^2 + a^2 m^2);
+      - dphi'(n~) = -H dphi(n~) + a^{alpha-1} i w_k (l - r)/sqrt(2) with the second
+        part uncorrelated with dphi, so sum Re[dphi* dphi'] / sum |dphi|^2 -> -H and
+        |dphi' + H dphi|^2 averages a^{2(alpha-1)} w_k^2 times the field's variance.
+    Each mean is taken over the ~2000 independent modes of a 16^3 draw and held to
+    four standard errors."""
+    N, kIR, a, alpha, fmp2 = 16, 0.1, 2.0, 0.5, 6.0
+    dx = 2 * np.pi / (kIR * N)
+    m = ScalarModel(N=N, Ns=1, pexp=2, dx=dx, alpha=alpha, fmp2=fmp2, lam=1.0, q=0.0)  # m^2 = lam = 1
+    phibar, dphibar = 1.0, 0.3
+    phi0, pi0, _ = scalar_ic(m, kIR, [phibar], [dphibar], seed=0, omega_over_fstar=0.1, a=a, fluctuations=False)
+    hom = ScalarLattice(m, phi0, pi0, a=a)
+    assert abs(hom.energies()[0] / (dphibar ** 2 / (2 * a ** (2 * alpha))) - 1) < 1e-13
+    H = np.sqrt(hom.hubble_rhs()) / a
+    assert H > 1.0
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    sel = ~selfc & ~zero
+    M = sel.sum() / 2  # independent modes: n~ and -n~ carry conjugate values
+    w = np.sqrt((kIR * nabs) ** 2 + a * a * 1.0)
+    T = 0.1 ** 2 * (N / dx) ** 3 / (2 * a * a * w)
+    phi, pi, _ = scalar_ic(m, kIR, [phibar], [dphibar], seed=11, omega_over_fstar=0.1, a=a)
+    F = dft_forward(phi[0] - phibar)
+    Fd = dft_forward(pi[0] / a ** (3.0 - alpha) - dphibar)
+    r_var = np.mean(np.abs(F[sel]) ** 2 / T[sel])
+    assert abs(r_var - 1) < 4 / np.sqrt(M), r_var
+    corr = np.sum((np.conj(F) * Fd).real[sel]) / np.sum(np.abs(F[sel]) ** 2)
+    se = np.max(a ** (alpha - 1) * w) / np.sqrt(2 * M)
+    assert abs(corr + H) < 4 * se, (corr, -H, se)
+    r_mom = np.mean(np.abs(Fd + H * F)[sel] ** 2 / (a ** (2 * (alpha - 1)) * w * w * T)[sel])
+    assert abs(r_mom - 1) < 4 / np.sqrt(M), r_mom
 
 def test_ic_is_deterministic_in_the_seed():
     _, a, _, _ = _scalar_setup(seed=11)

@@ -7,13 +7,21 @@ subprocess and requires at least one pin to fail: a real test failure, not a
 build or collection error.  An unmutated copy must pass the same files, so a
 failure is the mistake's doing.
 
-The cases cover the scalar sector (section 4: the Laplacian of the kernel,
-the section-8.1 potential, the Hamiltonian energies and the scale-factor
-kernel of section 4.3.2), the compact U(1) sector (section 5.3: the magnetic
-force, the current, the parallel transport), the SU(2) toolkit (section
-3.2.3: quaternion conjugate and product), the spectra and the vacuum initial
-conditions of section 3.1, the counter-based generator, the surrogate MLP's
-activation derivative and the equation of state.
+The cases cover:
+  - the scalar sector of section 4: the Laplacian, the section-8.1 potential,
+    the Hamiltonian energies, the scale-factor kernel, the drifts and kicks of
+    velocity-Verlet and of leapfrog scheme III, the Yoshida weights, the
+    prescribed fluid background, RK4 and the Gauss-Legendre stages;
+  - the U(1) sector of section 5: forces, currents, parallel transport, the
+    gauge energies and their weight in the Friedmann kernel, the Gauss law;
+  - the SU(2) toolkit of section 3.2.3 and the sector of section 6: quaternion
+    algebra, the doublet action of a link, the Pauli projections, the adjoint
+    transport of the Gauss law, the exact link drift;
+  - the SU(2) x U(1) + chi working example of section 8.3: the combined hop,
+    the U(1) current, the singlet's kernel and energies, both Gauss laws;
+  - the spectra of section 3.1 and the vacuum initial conditions of section 7
+    (mode variances, the Hubble term, the charge constraints, the Gauss solve);
+  - the counter-based generator, the surrogate MLP and the scan observables.
 
 Only oracle/ is touched, and only in a temporary directory; no GPU is used.
 """
@@ -71,6 +79,138 @@ CASES = [
      "x * np.exp(-x * x) / np.sqrt(2.0 * np.pi)", ["test_oracle_mlp.py"]),
     ("w-pressure", "observe.py", "out[1] = (EK - EG / 3.0 - EV) / rho", "out[1] = (EK - EG - EV) / rho",
      ["test_oracle_observe.py"]),
+    ("lf3-drift-scale-factor", "lattice_oracle.c",
+     "const double ah = 0.5 * (*a + an);\n    drift(m, phi, pi, dt * pow(ah",
+     "const double ah = *a;\n    drift(m, phi, pi, dt * pow(ah", ["test_oracle_scalar.py"]),
+    ("lf3-prepare-kinetic-a", "lattice_oracle.c",
+     "*EKm = S / V / (2.0 * pow(ahm, 6.0));",
+     "*EKm = S / V / (2.0 * pow(a, 6.0));", ["test_oracle_scalar.py"]),
+    ("u1-electric-energy-factor", "lattice_oracle.c",
+     "out[3] = m->kappa * ska / V / (2.0 * a4);\n    out[4] = m->kappa * sga",
+     "out[3] = m->kappa * ska / V / a4;\n    out[4] = m->kappa * sga", ["test_oracle_u1.py"]),
+    ("u1-magnetic-energy-a-power", "lattice_oracle.c",
+     "out[4] = m->kappa * sga / V / (a4 * m->e * m->e * dx4);",
+     "out[4] = m->kappa * sga / V / (a2 * m->e * m->e * dx4);", ["test_oracle_u1.py"]),
+    ("u1-Ka-gauge-weight", "lattice_oracle.c",
+     "(m->alpha + 1.0) * EV + (m->alpha - 1.0) * (EKA + EGA));",
+     "(m->alpha + 1.0) * EV + (m->alpha - 2.0) * (EKA + EGA));", ["test_oracle_u1.py"]),
+    ("u1-gauss-charge-factor", "lattice_oracle.c",
+     "const double r = 2.0 * m->e / m->kappa * rho;",
+     "const double r = m->e / m->kappa * rho;", ["test_oracle_u1.py", "test_oracle_ic.py"]),
+    ("u1-lf-link-drift-a-power", "lattice_oracle.c",
+     "const double cth = m->e * m->dx * dt * pow(ah, -(1.0 - m->alpha));",
+     "const double cth = m->e * m->dx * dt * pow(ah, -(3.0 - m->alpha));", ["test_oracle_u1.py"]),
+    ("u1-vv-scalar-drift-weight", "lattice_oracle.c",
+     "const double cphi = h * pow(ah, -(3.0 - m->alpha));\n        const double cth = m->e",
+     "const double cphi = dt * pow(ah, -(3.0 - m->alpha));\n        const double cth = m->e", ["test_oracle_u1.py"]),
+    ("fluid-drift-midpoint", "lattice_oracle.c",
+     "drift(m, phi, pi, h * pow(0.5 * (a + an), -(3.0 - m->alpha)));",
+     "drift(m, phi, pi, h * pow(a, -(3.0 - m->alpha)));", ["test_oracle_scalar.py"]),
+    ("fluid-exponent-alpha", "core.py",
+     "return 2.0 / (3.0 * (1.0 + self.w) - 2.0 * self.alpha)",
+     "return 2.0 / (3.0 * (1.0 + self.w) - self.alpha)", ["test_oracle_scalar.py"]),
+    ("rk4-weights", "lattice_oracle.c",
+     "w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}",
+     "w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 6.0, 1.0 / 3.0}", ["test_oracle_scalar.py"]),
+    ("rk4-friction", "lattice_oracle.c",
+     "c2 = (3.0 - m->alpha) * b / a",
+     "c2 = (2.0 - m->alpha) * b / a", ["test_oracle_scalar.py"]),
+    ("rk4-stage-node", "lattice_oracle.c",
+     "c[4] = {0.0, 0.5, 0.5, 1.0}",
+     "c[4] = {0.0, 0.5, 1.0, 1.0}", ["test_oracle_scalar.py"]),
+    ("su2-gauss-transport-direction", "lattice_oracle.c",
+     "qmul(qc, e, t);\n                    qmul(t, q, tr);",
+     "qmul(q, e, t);\n                    qmul(t, qc, tr);", ["test_oracle_su2.py"]),
+    ("su2-magnetic-energy-factor", "lattice_oracle.c",
+     "out[4] = 2.0 * m->kappa * sgb / V / (a4 * dx4 * m->g * m->g);\n}",
+     "out[4] = m->kappa * sgb / V / (a4 * dx4 * m->g * m->g);\n}", ["test_oracle_su2.py"]),
+    ("su2-drift-half-angle", "lattice_oracle.c",
+     "const double s = th > 0 ? sin(0.5 * th) / th : 0.5;",
+     "const double s = th > 0 ? sin(th) / th : 0.5;", ["test_oracle_su2.py"]),
+    ("su2-umul-entry", "lattice_oracle.c",
+     "cr = -q[2], ci = q[1], dr = q[0]",
+     "cr = -q[2], ci = -q[1], dr = q[0]", ["test_oracle_su2.py"]),
+    ("su2-im-sigma2-sign", "lattice_oracle.c",
+     "z[0] = y[3]; z[1] = -y[2]; z[2] = -y[1]; z[3] = y[0];",
+     "z[0] = -y[3]; z[1] = y[2]; z[2] = y[1]; z[3] = -y[0];", ["test_oracle_su2.py"]),
+    ("su2-current-coefficient", "lattice_oracle.c",
+     "const double cJ = m->g / (m->kappa * m->dx), cM = 2.0 / (m->g * m->dx * m->dx * m->dx);\n#pragma omp parallel for schedule(static)\n    for (int64_t z = 0; z < N; ++z)\n        for (int64_t y = 0; y < N; ++y)\n            for (int64_t x = 0; x < N; ++x) {\n                const int64_t n = site(N, x, y, z);\n                double f[4], lap[4] = {0, 0, 0, 0};",
+     "const double cJ = 2.0 * m->g / (m->kappa * m->dx), cM = 2.0 / (m->g * m->dx * m->dx * m->dx);\n#pragma omp parallel for schedule(static)\n    for (int64_t z = 0; z < N; ++z)\n        for (int64_t y = 0; y < N; ++y)\n            for (int64_t x = 0; x < N; ++x) {\n                const int64_t n = site(N, x, y, z);\n                double f[4], lap[4] = {0, 0, 0, 0};", ["test_oracle_su2.py"]),
+    ("su2u1-whop-phase-sign", "lattice_oracle.c",
+     "o[0] = c * u[0] + s * u[1];\n    o[1] = c * u[1] - s * u[0];\n    o[2] = c * u[2] + s * u[3];\n    o[3] = c * u[3] - s * u[2];",
+     "o[0] = c * u[0] - s * u[1];\n    o[1] = c * u[1] + s * u[0];\n    o[2] = c * u[2] - s * u[3];\n    o[3] = c * u[3] + s * u[2];", ["test_oracle_su2u1.py"]),
+    ("su2u1-KA-current-factor", "lattice_oracle.c",
+     "KA[(int64_t)i * V + n] = A1 * 2.0 * m->eA / (m->kappa * m->dx) * im_dot(f, t)",
+     "KA[(int64_t)i * V + n] = A1 * m->eA / (m->kappa * m->dx) * im_dot(f, t)", ["test_oracle_su2u1.py"]),
+    ("su2u1-chi-kernel-factor", "lattice_oracle.c",
+     "Kc[n] = -A3 * 2.0 * m->q * mod2 * chi[n]",
+     "Kc[n] = -A3 * m->q * mod2 * chi[n]", ["test_oracle_su2u1.py"]),
+    ("su2u1-Ka-drops-chi-kinetic", "lattice_oracle.c",
+     "((m->alpha - 2.0) * (E[0] + E[7]) + m->alpha * (E[1] + E[8])",
+     "((m->alpha - 2.0) * E[0] + m->alpha * (E[1] + E[8])", ["test_oracle_su2u1.py"]),
+    ("su2u1-u1-gauss-charge", "lattice_oracle.c",
+     "const double r = 2.0 * m->eA / m->kappa * im_dot(f, p);",
+     "const double r = m->eA / m->kappa * im_dot(f, p);", ["test_oracle_su2u1.py"]),
+    ("su2u1-chi-gradient-energy-factor", "lattice_oracle.c",
+     "out[8] = sgc / V / dx2 / (2.0 * a2);",
+     "out[8] = sgc / V / dx2 / a2;", ["test_oracle_su2u1.py"]),
+    ("gl-stage-matrix-transposed", "lattice_oracle.c",
+     "x += dt * A[l * s + mm] * Dold[(int64_t)(2 * mm) * M + n];\n                    y += dt * A[l * s + mm]",
+     "x += dt * A[mm * s + l] * Dold[(int64_t)(2 * mm) * M + n];\n                    y += dt * A[mm * s + l]", ["test_oracle_scalar.py"]),
+    ("gl-tableau-transposed", "core.py",
+     "A[i, j] = P(tau[i]) - P(0.0)",
+     "A[j, i] = P(tau[i]) - P(0.0)", ["test_oracle_scalar.py"]),
+    ("vv8-weight-digit-slip", "core.py",
+     "-0.40910082580003159400",
+     "-0.40910028580003159400", ["test_oracle_scalar.py", "test_oracle_u1.py"]),
+    ("vv4-closed-form", "core.py",
+     "VV4 = (1.0 / (2.0 - _C3), -_C3 / (2.0 - _C3), 1.0 / (2.0 - _C3))",
+     "VV4 = (1.0 / (2.0 - _C3), _C3 / (2.0 - _C3), 1.0 / (2.0 - _C3))", ["test_oracle_scalar.py"]),
+    ("spectrum-volume-factor", "spectra.py",
+     "(dx / N) ** 3 * sP",
+     "(dx / N) ** 2 * sP", ["test_oracle_ic.py", "test_oracle_observe.py"]),
+    ("spectrum-bins-rounded", "spectra.py",
+     "    b = isqrt_array(n2)\n",
+     "    b = np.rint(np.sqrt(n2)).astype(np.int64)\n", ["test_oracle_ic.py", "test_oracle_observe.py"]),
+    ("observe-eps-chi-takes-interaction", "observe.py",
+     "out[0] = (E[1] + E[3]) / rho",
+     "out[0] = (E[1] + E[3] + E[5]) / rho", ["test_oracle_observe.py"]),
+    ("observe-momentum-offset", "observe.py",
+     "(np.arange(NK) + 0.5) / NK",
+     "np.arange(NK) / NK", ["test_oracle_observe.py"]),
+    ("mlp-bias-grad-mean", "mlp.py",
+     "gb[l] = dZ.sum(axis=0)",
+     "gb[l] = dZ.mean(axis=0)", ["test_oracle_mlp.py"]),
+    ("mlp-loss-normalisation", "mlp.py",
+     "dZ = 2.0 * (Y - T) / (B * n_out)",
+     "dZ = 2.0 * (Y - T) / B", ["test_oracle_mlp.py"]),
+    ("mlp-activation-derivative-argument", "mlp.py",
+     "dZ = dH * gelu_prime(Z[l - 1])",
+     "dZ = dH * gelu_prime(H[l])", ["test_oracle_mlp.py"]),
+    ("mlp-flatten-order", "mlp.py",
+     "np.concatenate([W.ravel(), b.ravel()])",
+     "np.concatenate([b.ravel(), W.ravel()])", ["test_oracle_mlp.py"]),
+    ("ic-charge-cancelling-phase", "ic.py",
+     "th1r = th0r + th1l - th0l",
+     "th1r = th0r - th1l + th0l", ["test_oracle_ic.py", "test_oracle_u1.py"]),
+    ("ic-gauss-forward-difference", "ic.py",
+     "    betas = [(1.0 - np.exp(2j * np.pi * c / N)) / dx for c in (nx, ny, nz)]",
+     "    betas = [(1.0 - np.exp(-2j * np.pi * c / N)) / dx for c in (nx, ny, nz)]", ["test_oracle_ic.py", "test_oracle_u1.py"]),
+    ("ic-singlet-hubble-sign", "ic.py",
+     "(L * el - R * er) - H * G\n    return",
+     "(L * el - R * er) + H * G\n    return", ["test_oracle_ic.py"]),
+    ("ic-frequency-mass-a", "ic.py",
+     "return np.sqrt(k * k + a * a * m2)",
+     "return np.sqrt(k * k + m2)", ["test_oracle_ic.py"]),
+    ("ic-rayleigh-mean-square", "ic.py",
+     "\n    L = np.sqrt(-T * np.log(u[0]))\n",
+     "\n    L = np.sqrt(-2.0 * T * np.log(u[0]))\n", ["test_oracle_ic.py"]),
+    ("ic-su2-charge-removal-sign", "ic.py",
+     "P1 = P1 - (cq[0] * 1j * F2",
+     "P1 = P1 + (cq[0] * 1j * F2", ["test_oracle_ic.py", "test_oracle_su2.py"]),
+    ("ic-momentum-a-power", "ic.py",
+     "        pi[i] = a ** (3.0 - alpha) * (dphibar[i] + ddphi)",
+     "        pi[i] = a ** (2.0 - alpha) * (dphibar[i] + ddphi)", ["test_oracle_ic.py", "test_oracle_scalar.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
@@ -82,8 +222,12 @@ def _scratch_copy(dst):
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
     os.makedirs(os.path.join(dst, "tests"))
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
-    for f in ["__init__.py", "conftest.py", "inputs.py"] + PIN_FILES:
+    for f in ["__init__.py", "inputs.py"] + PIN_FILES:
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    # the pin files need no GPU check: a conftest without the torch import
+    with open(os.path.join(dst, "tests", "conftest.py"), "w") as fh:
+        fh.write("def pytest_configure(config):\n"
+                 "    config.addinivalue_line('markers', 'gpu: needs a CUDA GPU')\n")
 
 
 def _run_pins(dst, pins):
@@ -116,12 +260,12 @@ def _one(tmp, case):
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
-    """Run the unmutated copy and every mutant, four at a time."""
+    """Run the unmutated copy and every mutant, a few at a time."""
     tmp = str(tmp_path_factory.mktemp("oracle_mutants"))
     base = os.path.join(tmp, "unmutated")
     _scratch_copy(base)
     clean = _run_pins(base, PIN_FILES)
-    with ThreadPoolExecutor(max_workers=4) as pool:
+    with ThreadPoolExecutor(max_workers=max(2, min(6, (os.cpu_count() or 2) - 1))) as pool:
         res = dict(pool.map(lambda c: _one(tmp, c), CASES))
     return clean, res
 

@@ -243,6 +243,22 @@ def test_staggered_leapfrog_hubble_constraint_second_order():
     assert 1.7 < slope < 2.3, (de, slope)
 
 
+
+def test_staggered_leapfrog_start_stores_the_half_step_kinetic_energy():
+    """The backward half kick that starts scheme III (section 4.2.1) leaves
+    pi_{-1/2}, b_{-1/2} and E_K at -1/2, which the first step averages with
+    E_K at +1/2.  That stored value is the kinetic energy <pi^2>/(2 a^6) of
+    section 4.4.1 of the momenta pi_{-1/2} at the staggered scale factor
+    a_{-1/2} = a - (dt/2) b_{-1/2}, evaluated here by the energy functional."""
+    dt = 0.1
+    m, phi, pi, lat = _fluct_lattice(alpha=0.5, pexp=4, Ns=2, fmp2=3.0)
+    a0 = lat.a
+    lat.lf3_prepare(dt)
+    ahm = a0 - 0.5 * dt * lat.b
+    assert abs(ahm - a0) > 1e-2 * a0  # expansion strong enough to tell a_{-1/2} from a
+    E = ScalarLattice(m, lat.phi, lat.pi, a=ahm).energies()
+    assert abs(lat.EKm - (E[0] + E[1])) <= 1e-13 * (E[0] + E[1]), (lat.EKm, E[0] + E[1])
+
 def test_yoshida_weights():
     """Closed-form VV4 weights satisfy sum w = 1 and sum w^3 = 0 (fourth order);
     the tabulated VV6/8/10 weights sum to one."""

@@ -278,3 +278,45 @@ def test_su2u1_vacuum_initial_conditions():
     f, fd = _singlet_draw(N, 1.0, kIR, 2 * m.q * s2, H, 3, 4, omega, 1.0, 1.0)
     assert np.max(np.abs(f - chi)) == 0.0 and np.max(np.abs(fd - pchi)) < 1e-15
     assert abs(chi.mean()) < 1e-14 and chi.std() > 0.0
+
+
+
+@pytest.mark.parametrize("sector,alpha", [("chi", 0.0), ("chi", 1.0), ("su2", 0.0), ("su2", 1.0), ("u1", 0.0)])
+def test_homogeneous_fields_give_the_closed_form_expansion(sector, alpha):
+    """With Phi = 0 and unit links, a uniform velocity of the singlet is pure
+    kinetic energy (rho ~ a^-6, kination) and a uniform electric field of one
+    colour (SU(2)) or of the U(1) is radiation (rho ~ a^-4).  The Friedmann
+    equations (section 4.1; a' = b, b^2 = (f*/m_p)^2 a^{2(alpha+1)} rho / 3) make
+    a^n grow linearly in program time, a^n - a0^n = n a0^(n-1) b0 t, with
+    n = 3 - alpha for kination and n = 2 - alpha for radiation."""
+    N = 4
+    m = SU2U1Model(N=N, dx=0.7, alpha=alpha, fmp2=3.0, lam=1.0, v2=0.0, g=0.8, kappa=1.0, pot=1, p=4,
+                   eA=0.5, q=1.5, chi=1)
+    z4 = np.zeros((4, N, N, N))
+    u = np.zeros((3, 4, N, N, N))
+    u[:, 0] = 1.0
+    piB = np.zeros((3, 3, N, N, N))
+    piA = np.zeros((3, N, N, N))
+    pchi = np.zeros((N, N, N))
+    if sector == "chi":
+        pchi[:] = 0.7
+    elif sector == "su2":
+        for i, c in enumerate((0.3, -0.2, 0.5)):
+            piB[i, 2] = c  # one colour: the links stay commuting, the plaquettes unity
+    else:
+        for i, c in enumerate((0.3, -0.2, 0.5)):
+            piA[i] = c
+    lat = SU2U1Lattice(m, z4, z4, u, piB, None, piA, None, pchi, a=1.3)
+    E = lat.energies()
+    live = {"chi": [7], "su2": [3], "u1": [5]}[sector]
+    assert np.all(E[live] > 0) and np.all(np.delete(E, live) == 0), E
+    a0 = lat.a
+    b0 = np.sqrt(m.fmp2 / 3.0 * a0 ** (2 * (alpha + 1)) * E.sum())
+    lat.b = b0
+    dt, steps = 0.02, 100
+    lat.vv_steps(VV4, dt, steps)
+    t = dt * steps
+    n = (3.0 - alpha) if sector == "chi" else (2.0 - alpha)
+    a_exact = (a0 ** n + n * a0 ** (n - 1) * b0 * t) ** (1.0 / n)
+    assert abs(lat.a / a_exact - 1) < 1e-8, (lat.a, a_exact)  # VV4 at dt = 0.02: ~1e-10
+    assert abs(lat.a / a0 - 1) > 0.1  # a grows by a sizeable factor

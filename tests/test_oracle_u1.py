@@ -4,7 +4,7 @@ law to round-off, gauge invariance, energy conservation and B = 0 at start."""
 import numpy as np
 import pytest
 
-from oracle import U1Lattice, U1Model
+from oracle import VV4, U1Lattice, U1Model
 from oracle.ic import u1_ic
 from tests import inputs
 
@@ -326,3 +326,31 @@ def test_u1_field_strengths_carry_the_gauge_energies(nc, a, alpha):
                                                                      rel=1e-13)
     B2 = (lat.magnetic() ** 2).sum(axis=0).mean()
     assert B2 == pytest.approx(2 * a ** 4 * E[4] / m.kappa, rel=1e-13 if nc else 1e-3)
+
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_homogeneous_electric_field_expands_like_radiation(alpha):
+    """A uniform electric field with phi = 0 and unit links carries no charge
+    and no plaquette, so piA stays constant and the energy is kappa piA^2/(2 a^4):
+    radiation.  The Friedmann equations (section 4.1) then fix the expansion in
+    closed form: with a' = b and b^2 = (f*/m_p)^2 a^{2(alpha+1)} rho / 3,
+    a^2 = a0^2 + 2 a0 b0 t in cosmic time (alpha = 0) and a = a0 + b0 eta in
+    conformal time (alpha = 1)."""
+    N = 4
+    m = U1Model(N=N, dx=0.7, alpha=alpha, fmp2=3.0, lam=1.0, e=0.5, kappa=1.0, pot=1, p=4)
+    piA = np.stack([np.full((N, N, N), c) for c in (0.3, -0.2, 0.5)])
+    z = np.zeros((2, N, N, N))
+    lat = U1Lattice(m, z, z, np.zeros((3, N, N, N)), piA, a=1.3)
+    E = lat.energies()
+    assert E[3] > 0 and np.all(E[[0, 1, 2, 4]] == 0)
+    a0 = lat.a
+    b0 = np.sqrt(m.fmp2 / 3.0 * a0 ** (2 * (alpha + 1)) * E.sum())
+    lat.b = b0
+    dt, n = 0.02, 100
+    lat.vv_steps(VV4, dt, n)
+    t = dt * n
+    a_exact = np.sqrt(a0 * a0 + 2 * a0 * b0 * t) if alpha == 0.0 else a0 + b0 * t
+    assert abs(lat.a / a_exact - 1) < 1e-8, (lat.a, a_exact)  # VV4 at dt = 0.02: ~1e-10
+    assert abs(lat.a / a0 - 1) > 0.2  # a grows by a sizeable factor
+    assert np.max(np.abs(lat.piA - piA)) < 1e-15
