@@ -653,11 +653,17 @@ cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const
     for (int i = 0; i < n; ++i) {
         const int N = Ns[i];
         if (E->fft.count(N)) continue;
-        cl::SharedFFT f;
+        cl::SharedFFT f{};
         const size_t n3 = (size_t)N * N * N, nh = (size_t)N * N * (N / 2 + 1);
-        if (cufftPlan3d(&f.c2r, N, N, N, CUFFT_Z2D) != CUFFT_SUCCESS ||
-            cufftPlan3d(&f.r2c, N, N, N, CUFFT_D2Z) != CUFFT_SUCCESS || cudaMalloc(&f.work, n3 * sizeof(double)) != cudaSuccess ||
+        const bool c2r = cufftPlan3d(&f.c2r, N, N, N, CUFFT_Z2D) == CUFFT_SUCCESS;
+        const bool r2c = c2r && cufftPlan3d(&f.r2c, N, N, N, CUFFT_D2Z) == CUFFT_SUCCESS;
+        if (!r2c || cudaMalloc(&f.work, n3 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&f.cwork, 2 * nh * sizeof(double2)) != cudaSuccess) {
+            // release what this size got before the failure (cudaFree of NULL is a no-op)
+            if (c2r) cufftDestroy(f.c2r);
+            if (r2c) cufftDestroy(f.r2c);
+            cudaFree(f.work);
+            cudaFree(f.cwork);
             ensemble_destroy(E);
             return efail(CL_ERR_OOM, "ensemble_init: FFT resources");
         }

@@ -1031,14 +1031,21 @@ cl_status surrogate_create(int32_t n_in, int32_t n_out, int32_t width, int32_t d
     bool ok = true;
     for (int l = 0; l < S->L; ++l) {
         const size_t nw = (size_t)S->P[l + 1] * S->P[l], nb = S->P[l + 1];
-        float *w, *gw, *mw, *vw, *bb, *gbb, *mbb, *vbb;
-        cl::bf16 *wb, *wbt;
+        float *w = nullptr, *gw = nullptr, *mw = nullptr, *vw = nullptr, *bb = nullptr, *gbb = nullptr,
+              *mbb = nullptr, *vbb = nullptr;
+        cl::bf16 *wb = nullptr, *wbt = nullptr;
         ok = ok && cudaMalloc(&w, nw * 4) == cudaSuccess && cudaMalloc(&gw, nw * 4 * kMaxSplits) == cudaSuccess &&
              cudaMalloc(&mw, nw * 4) == cudaSuccess && cudaMalloc(&vw, nw * 4) == cudaSuccess &&
              cudaMalloc(&bb, nb * 4) == cudaSuccess && cudaMalloc(&gbb, nb * 4) == cudaSuccess &&
              cudaMalloc(&mbb, nb * 4) == cudaSuccess && cudaMalloc(&vbb, nb * 4) == cudaSuccess &&
              cudaMalloc(&wb, nw * 2) == cudaSuccess && cudaMalloc(&wbt, nw * 2) == cudaSuccess;
-        if (!ok) break;
+        if (!ok) {
+            // this layer's buffers are not yet owned by S: release the ones that were allocated
+            for (void* p : {(void*)w, (void*)gw, (void*)mw, (void*)vw, (void*)bb, (void*)gbb, (void*)mbb, (void*)vbb,
+                            (void*)wb, (void*)wbt})
+                cudaFree(p);
+            break;
+        }
         S->W.push_back(w); S->gW.push_back(gw); S->mW.push_back(mw); S->vW.push_back(vw);
         S->b.push_back(bb); S->gb.push_back(gbb); S->mb.push_back(mbb); S->vb.push_back(vbb);
         S->Wb.push_back(wb); S->WbT.push_back(wbt);
