@@ -324,7 +324,18 @@ cl_status lattice_destroy(cl_lattice* h);
  * (N_min the smallest member: its Nyquist momentum along an axis; shells
  * beyond it are incomplete); a positive kmax is used as given, so that
  * ensembles of different sizes observe at the same momenta.  *t (may be NULL)
- * receives the program time.  Synchronizes the stream. */
+ * receives the program time.  Synchronizes the stream.
+ *
+ * q, N and seeds are host arrays of n entries, read during ensemble_init only;
+ * obs is a host array of n x CL_OBS_SIZE floats (member-major).  The handle
+ * owns every member and its device memory until ensemble_destroy (NULL is
+ * accepted).  ensemble_init refuses with CL_ERR_ARG (reason in
+ * cl_last_error(NULL), nothing left allocated): n < 1, a NULL array or struct, a
+ * model other than the two-field pexp = 2 scalar model, an integrator other
+ * than VV2 / VV4, an N that is not a multiple of 32 in [32, 1024], a q < 0 or
+ * NaN, and any member that lattice_init would refuse (its reason is passed
+ * on); allocation failures give CL_ERR_OOM.  ensemble_member refuses an index
+ * outside [0, n). */
 typedef struct cl_ensemble cl_ensemble;
 #define CL_OBS_SIZE 34
 cl_status ensemble_init(int32_t n, const cl_model* model, const double* q, const int32_t* N, const uint64_t* seeds,
