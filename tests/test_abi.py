@@ -203,3 +203,51 @@ def test_stored_copies_take_the_handle_precision(precision):
             lat.get_stored(cl.FIELD(0), a)
         with pytest.raises(ValueError):
             lat.set_stored(cl.FIELD(0), a, 0.0)
+
+
+@pytest.mark.parametrize("bad", ["n", "null_q", "model", "pexp", "integrator", "size", "size_cap", "q_negative",
+                                 "q_nan"])
+def test_ensemble_init_rejects_bad_arguments_before_any_device_work(bad):
+    """ensemble_init refuses, with CL_ERR_ARG and a reason, what the header lists:
+    n < 1, NULL arrays, a model other than the two-field pexp = 2 scalar model,
+    an integrator other than VV2/VV4, N outside the multiples of 32 in [32, 1024],
+    q < 0 or NaN."""
+    lib = cl.load()
+    n = 2
+    model = cl.make_model(n_fields=2, pexp=2)
+    grid = cl.make_grid(32, 0.5, 0.01, "vv4", cl.CL_FP32)
+    q = np.array([1.0, 2.0])
+    Ns = np.array([32, 64], dtype=np.int32)
+    seeds = np.array([1, 2], dtype=np.uint64)
+    if bad == "n":
+        n = 0
+    if bad == "model":
+        model.kind = cl.CL_MODEL_U1
+    if bad == "pexp":
+        model.pexp = 4
+    if bad == "integrator":
+        grid.integrator = cl.CL_INT_LF
+    if bad == "size":
+        Ns[1] = 48
+    if bad == "size_cap":
+        Ns[1] = 2048
+    if bad == "q_negative":
+        q[0] = -1.0
+    if bad == "q_nan":
+        q[1] = np.nan
+    pq = None if bad == "null_q" else q.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    st = lib.ensemble_init(n, C.byref(model), pq, Ns.ctypes.data_as(C.POINTER(C.c_int32)),
+                           seeds.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(grid), C.byref(cl.make_init()), None,
+                           C.byref(h))
+    assert st == cl.CL_ERR_ARG and not h.value
+    assert b"ensemble_init" in lib.cl_last_error(None)
+
+
+def test_ensemble_null_handles_are_rejected():
+    lib = cl.load()
+    out = C.c_void_p()
+    assert lib.ensemble_member(None, 0, C.byref(out)) == cl.CL_ERR_ARG
+    assert lib.ensemble_evolve(None, 1) == cl.CL_ERR_ARG
+    assert lib.ensemble_observe(None, 0.0, None, None) == cl.CL_ERR_ARG
+    assert lib.ensemble_destroy(None) == cl.CL_OK
