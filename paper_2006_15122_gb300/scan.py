@@ -85,17 +85,19 @@ def ensemble_observations(spec, qs, Ns, seeds, autotune=True, stream=None):
     ens = Ensemble(spec.model(), 4.0 * np.asarray(qs, dtype=np.float64), Ns, seeds, spec.grid(spec.nmin),
                    spec.init(), stream=stream)
     t1 = time.perf_counter()
-    tuned = ens.autotune() if autotune else []
-    t2 = time.perf_counter()
-    obs = np.zeros((len(qs), spec.n_slices, CL_OBS_SIZE), dtype=np.float32)
-    times = np.zeros(spec.n_slices)
-    for j in range(spec.n_slices):
-        ens.evolve(spec.steps_per_slice)
-        obs[:, j, :], times[j] = ens.observe(spec.kmax)
-    t3 = time.perf_counter()
-    info = {"init_s": t1 - t0, "tune_s": t2 - t1, "evolve_observe_s": t3 - t2, "tile": ens.tile(),
-            "candidates": tuned}
-    ens.close()
+    try:
+        tuned = ens.autotune() if autotune else []
+        t2 = time.perf_counter()
+        obs = np.zeros((len(qs), spec.n_slices, CL_OBS_SIZE), dtype=np.float32)
+        times = np.zeros(spec.n_slices)
+        for j in range(spec.n_slices):
+            ens.evolve(spec.steps_per_slice)
+            obs[:, j, :], times[j] = ens.observe(spec.kmax)
+        t3 = time.perf_counter()
+        info = {"init_s": t1 - t0, "tune_s": t2 - t1, "evolve_observe_s": t3 - t2, "tile": ens.tile(),
+                "candidates": tuned}
+    finally:
+        ens.close()
     return obs, times, info
 
 
@@ -104,12 +106,14 @@ def plain_observations(spec, q, N, seed, stream=None):
     without batching): (obs (n_slices, CL_OBS_SIZE), times)."""
     m = spec.model(q)
     lat = Lattice(m, spec.grid(N), spec.init(seed), stream=stream)
-    obs = np.zeros((spec.n_slices, CL_OBS_SIZE), dtype=np.float32)
-    times = np.zeros(spec.n_slices)
-    for j in range(spec.n_slices):
-        lat.evolve(spec.steps_per_slice)
-        obs[j], times[j] = lat.observe(spec.kmax)
-    lat.close()
+    try:
+        obs = np.zeros((spec.n_slices, CL_OBS_SIZE), dtype=np.float32)
+        times = np.zeros(spec.n_slices)
+        for j in range(spec.n_slices):
+            lat.evolve(spec.steps_per_slice)
+            obs[j], times[j] = lat.observe(spec.kmax)
+    finally:
+        lat.close()
     return obs, times
 
 
@@ -129,7 +133,9 @@ def gather_runs(local, n, dist=None, device="cpu"):
     group the local array is the whole scan."""
     local = np.ascontiguousarray(local)
     if dist is None:
-        assert local.shape[0] == n
+        if local.shape[0] != n:
+            raise ValueError("without a process group the local block is the whole scan: %d rows, not %d"
+                             % (local.shape[0], n))
         return local
     import torch
 
