@@ -99,12 +99,6 @@ def scalar_ic(model, kIR, phibar, dphibar, seed, omega_over_fstar, a=1.0, fluct_
     return phi, pi, dx
 
 
-def hubble_b(model, phi, pi, a, energies):
-    """b = a' from the Hubble constraint b^2 = (1/3)(f*/m_p)^2 a^{2(alpha+1)} (E_K+E_G+E_V)."""
-    E = energies
-    return float(np.sqrt(max(model.fmp2 / 3.0 * a ** (2 * (model.alpha + 1)) * (E[0] + E[1] + E[2] + E[3] + E[4] + E[5]), 0.0)))
-
-
 def _charged_potential(model, mod2):
     """V, dV/dmod2 and d^2V/dmod2^2 of a gauge model's charged scalar at
     mod2 = |phi|^2: (lam/4)(mod2 - v2)^2 (sections 5, 6) or the monomial
