@@ -211,6 +211,51 @@ CASES = [
     ("ic-momentum-a-power", "ic.py",
      "        pi[i] = a ** (3.0 - alpha) * (dphibar[i] + ddphi)",
      "        pi[i] = a ** (2.0 - alpha) * (dphibar[i] + ddphi)", ["test_oracle_ic.py", "test_oracle_scalar.py"]),
+    ("su2u1-ic-phase-constraint", "ic.py",
+     "er = np.exp(1j * thl[c]), np.exp(1j * (th0r + thl[c] - thl[0]))",
+     "er = np.exp(1j * thl[c]), np.exp(1j * (th0r - thl[c] + thl[0]))", ["test_oracle_su2u1.py", "test_oracle_ic.py"]),
+    ("su2-ic-charge-normalisation", "ic.py",
+     "cq = rho.sum(axis=(1, 2, 3)) / (phi ** 2).sum()",
+     "cq = rho.sum(axis=(1, 2, 3)) / (phi ** 2).mean()", ["test_oracle_su2.py", "test_oracle_ic.py"]),
+    ("su2-charge-sigma2-sign", "ic.py",
+     "np.imag(np.conj(x1) * (-1j * y2) + np.conj(x2) * (1j * y1))",
+     "np.imag(np.conj(x1) * (1j * y2) + np.conj(x2) * (-1j * y1))", ["test_oracle_su2.py", "test_oracle_su2u1.py", "test_oracle_ic.py"]),
+    ("gauss-solve-conjugate", "ic.py",
+     "return [dft_inverse(np.where(den > 0, np.conj(bb) * R / den, 0.0)).real for bb in betas]",
+     "return [dft_inverse(np.where(den > 0, bb * R / den, 0.0)).real for bb in betas]", ["test_oracle_su2.py", "test_oracle_su2u1.py", "test_oracle_ic.py"]),
+    ("u1-magnetic-field-orientation", "core.py",
+     "t = theta[j] + _shift(theta[k], j) - _shift(theta[j], k) - theta[k]",
+     "t = theta[j] + _shift(theta[k], k) - _shift(theta[j], j) - theta[k]", ["test_oracle_u1.py", "test_oracle_su2u1.py"]),
+    ("observe-interpolation-in-k", "observe.py",
+     "return np.interp(np.log(kj), lk, lD)",
+     "return np.interp(kj, np.exp(lk), lD)", ["test_oracle_observe.py"]),
+    ("mode-map-axis-modes", "ic.py",
+     "canon = (sx > 0) | ((sx == 0) & (sy > 0)) | ((sx == 0) & (sy == 0) & (sz > 0))",
+     "canon = (sx > 0) | ((sx == 0) & (sy > 0))", ["test_oracle_ic.py"]),
+    ("gelu-erf-argument", "mlp.py",
+     "return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))",
+     "return 0.5 * x * (1.0 + erf(x / 2.0))", ["test_oracle_mlp.py"]),
+    ("potential-curvature-factor", "core.py",
+     "out = [(m.pexp - 1) * m.lam * abs(f0) ** (m.pexp - 2)",
+     "out = [m.pexp * m.lam * abs(f0) ** (m.pexp - 2)", ["test_oracle_ic.py"]),
+    ("gradient-energy-factor", "lattice_oracle.c",
+     "out[2 + i] = sg[i] / V / (2.0 * a2);",
+     "out[2 + i] = sg[i] / V / a2;", ["test_oracle_scalar.py"]),
+    ("hubble-rhs-a-power", "lattice_oracle.c",
+     "return m->fmp2 / 3.0 * pow(a, 2.0 * (m->alpha + 1.0)) * (EK + EG + EV);",
+     "return m->fmp2 / 3.0 * pow(a, 2.0 * m->alpha + 1.0) * (EK + EG + EV);", ["test_oracle_scalar.py"]),
+    ("potential-normalisation", "lattice_oracle.c",
+     "*v1 = m->lam / m->pexp * ipow(fabs(phi), m->pexp);",
+     "*v1 = m->lam * ipow(fabs(phi), m->pexp);", ["test_oracle_scalar.py"]),
+    ("potential-gradient-power", "lattice_oracle.c",
+     "*dphi = m->lam * ipow(fabs(phi), m->pexp - 2) * phi;",
+     "*dphi = m->lam * ipow(fabs(phi), m->pexp - 1) * phi;", ["test_oracle_scalar.py"]),
+    ("gauge-higgs-derivative", "lattice_oracle.c",
+     "*dv = 0.5 * lam * (mod2 - v2);",
+     "*dv = lam * (mod2 - v2);", ["test_oracle_u1.py", "test_oracle_su2.py"]),
+    ("gauge-monomial-derivative", "lattice_oracle.c",
+     "*dv = lam * pow(s, 0.5 * p - 1.0);",
+     "*dv = 0.5 * lam * pow(s, 0.5 * p - 1.0);", ["test_oracle_u1.py", "test_oracle_su2.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
