@@ -390,8 +390,9 @@ cl_status lattice_observe(cl_lattice* h, double kmax, float* obs, double* t);
  *
  * Scratch: a fixed device array of CL_NOALLOC_MAX_BLOCKS x 16 partial sums and
  * a counter (about 128 KiB), present on every GPU that loads the library until
- * the process exits.  The first call on a device looks its address up (with
- * that device current); make that first call before any stream capture.  All
+ * the process exits.  The first call on a device looks its address up with
+ * cudaGetSymbolAddress (that device current) and keeps it; every call then
+ * enqueues one memset of the counter and one kernel launch.  All
  * calls share the array and it keeps the last call's contents; the counter is
  * cleared at the start of each call.  Calls that overlap on the GPU race on it.
  * Rejects n_fields > 2, N outside [2, CL_NOALLOC_MAX_N] and NULL pointers with
