@@ -80,7 +80,11 @@ def ensemble_observations(spec, qs, Ns, seeds, autotune=True, stream=None):
 
     Returns (obs of shape (n, n_slices, CL_OBS_SIZE), times, info) where info
     holds the wall-clock seconds of initialisation, tuning and evolution (each
-    phase ends synchronized) and the tile shape used."""
+    phase ends synchronized) and the tile shape used.  An empty run list (a rank
+    whose partition() block is empty) gives no observations and launches nothing."""
+    if len(qs) == 0:
+        return (np.zeros((0, spec.n_slices, CL_OBS_SIZE), dtype=np.float32), spec.times(),
+                {"init_s": 0.0, "tune_s": 0.0, "evolve_observe_s": 0.0, "tile": None, "candidates": []})
     t0 = time.perf_counter()
     ens = Ensemble(spec.model(), 4.0 * np.asarray(qs, dtype=np.float64), Ns, seeds, spec.grid(spec.nmin),
                    spec.init(), stream=stream)

@@ -1,4 +1,4 @@
-"""The multi-rank logic of bench.py on CPU ranks (gloo, world size 2): every
+"""The multi-rank logic of bench.py on CPU ranks (gloo, world sizes 2 and 3): every
 rank evolves an independent replica (seed = rank), the timing is the max over
 ranks after a barrier, and the whole-job rate counts every replica; under
 torchrun the reference arm runs on rank 0 only."""
@@ -66,26 +66,29 @@ def _scan_rank_main(rank, world, port, n, out):
     try:
         block = scan.partition(n, world, rank)
         # each run's "observations": its index and a few derived numbers, as the ensemble would return
-        local = np.stack([np.array([i, 2.0 * i, -float(i)], dtype=np.float32) for i in block]).reshape(len(block), 1, 3)
+        local = np.array([[i, 2.0 * i, -float(i)] for i in block], dtype=np.float32).reshape(len(block), 1, 3)
+        if not block:  # fewer runs than ranks: this rank's ensemble call returns nothing
+            spec = scan.ScanSpec(n_slices=1)
+            local = scan.ensemble_observations(spec, [], [], [])[0][:, :, :3]
         out[rank] = (block, scan.gather_runs(local, n, dist, "cpu"))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("n", [7, 8])
-def test_two_gloo_ranks_split_the_scan_and_gather_every_run_in_order(n):
+@pytest.mark.parametrize("world,n", [(2, 7), (2, 8), (3, 2)])
+def test_gloo_ranks_split_the_scan_and_gather_every_run_in_order(world, n):
     """The scan's run list is split into contiguous blocks, one per rank (no
     data-path exchange while the lattices evolve); one gather assembles every
-    run's observations in run order on every rank."""
+    run's observations in run order on every rank, also when some rank's block
+    is empty (fewer runs than ranks)."""
     import numpy as np
 
-    world = 2
     mgr = mp.Manager()
     out = mgr.dict()
     mp.start_processes(_scan_rank_main, args=(world, _free_port(), n, out), nprocs=world, join=True,
                        start_method="spawn")
     blocks = [out[r][0] for r in range(world)]
-    assert sorted(blocks[0] + blocks[1]) == list(range(n)) and not set(blocks[0]) & set(blocks[1])
+    assert sorted(sum(blocks, [])) == list(range(n)) and sum(map(len, blocks)) == n
     for r in range(world):
         g = out[r][1]
         assert g.shape == (n, 1, 3)
