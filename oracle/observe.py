@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (part of the oracle).
 
 The paper defines the quantities (section 4.4: volume-averaged energies and
 the equation of state; section 3.1: the power spectrum); the selection of 34
-numbers per lattice is this build's reading of a parameter-scan workload:
+numbers per lattice is a reading of a parameter-scan workload, not the paper's:
   - the daughter-field fraction eps_chi = (E_K[chi] + E_G[chi]) / rho, the
     kinetic plus gradient energy of chi over the total energy density
     rho = E_K + E_G + E_V (chi's potential energy is shared with phi through
