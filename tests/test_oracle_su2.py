@@ -271,3 +271,37 @@ def test_su2_magnetic_field_of_an_abelian_configuration():
     small = SU2Lattice(m, np.zeros((4, N, N, N)), np.zeros((4, N, N, N)), u, np.zeros((3, 3, N, N, N)))
     B2 = (small.magnetic() ** 2).sum(axis=(0, 1)).mean()
     assert B2 == pytest.approx(2 * small.energies()[4] / m.kappa, rel=1e-3)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0])
+def test_one_colour_electric_field_expands_like_radiation(alpha):
+    """Phi = 0, unit links and a uniform electric field of one colour (sigma_3)
+    in every direction: the links stay commuting, the plaquettes unity, so piB is
+    constant and its energy kappa piB^2/(2 a^4) is radiation.  The Friedmann
+    equations (section 4.1) give a^n linear in t, a^n - a0^n = n a0^(n-1) b0 t with
+    n = 2 - alpha, and the link U_i = exp(-i Phi_i sigma_3/2) turns at the rate
+    g dx piB_i a^{alpha-1} (the drift of section 6.2), so
+    Phi_i(t) = g dx piB_i (a - a0)/(a0^(n-1) b0)."""
+    N = 4
+    m = SU2Model(N=N, dx=0.7, alpha=alpha, fmp2=3.0, lam=1.0, v2=0.0, g=0.8, kappa=1.0, pot=1, p=4)
+    z4 = np.zeros((4, N, N, N))
+    u = np.zeros((3, 4, N, N, N))
+    u[:, 0] = 1.0
+    piB = np.zeros((3, 3, N, N, N))
+    c = np.array([0.3, -0.2, 0.5])
+    for i in range(3):
+        piB[i, 2] = c[i]
+    lat = SU2Lattice(m, z4, z4, u, piB, a=1.3)
+    E = lat.energies()
+    assert E[3] > 0 and np.all(E[[0, 1, 2, 4]] == 0), E
+    a0 = lat.a
+    b0 = np.sqrt(m.fmp2 / 3.0 * a0 ** (2 * (alpha + 1)) * E.sum())
+    lat.b = b0
+    dt, steps = 0.02, 100
+    lat.vv_steps(VV4, dt, steps)
+    n = 2.0 - alpha
+    a_exact = (a0 ** n + n * a0 ** (n - 1) * b0 * dt * steps) ** (1.0 / n)
+    assert abs(lat.a / a_exact - 1) < 1e-8, (lat.a, a_exact)
+    Phi = 2 * np.arctan2(-lat.u[:, 3, 0, 0, 0], lat.u[:, 0, 0, 0, 0])
+    Phi_exact = m.g * m.dx * c * (a_exact - a0) / (a0 ** (n - 1) * b0)
+    assert np.allclose(Phi, Phi_exact, rtol=1e-8, atol=0), (Phi, Phi_exact)

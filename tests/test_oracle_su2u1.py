@@ -320,3 +320,17 @@ def test_homogeneous_fields_give_the_closed_form_expansion(sector, alpha):
     a_exact = (a0 ** n + n * a0 ** (n - 1) * b0 * t) ** (1.0 / n)
     assert abs(lat.a / a_exact - 1) < 1e-8, (lat.a, a_exact)  # VV4 at dt = 0.02: ~1e-10
     assert abs(lat.a / a0 - 1) > 0.1  # a grows by a sizeable factor
+    # the drifts: chi' = pchi a^{alpha-3} and the link angles' rate a^{alpha-1}, integrated
+    # over a^n linear in t: int a^-n dt = ln(a/a0)/(a0^(n-1) b0) (kination),
+    # int a^(1-n) dt = (a - a0)/(a0^(n-1) b0) (radiation)
+    if sector == "chi":
+        chi_exact = 0.7 * np.log(a_exact / a0) / (a0 ** (n - 1) * b0)
+        assert abs(lat.chi[0, 0, 0] / chi_exact - 1) < 1e-8, (lat.chi[0, 0, 0], chi_exact)
+    elif sector == "su2":
+        # U_i = exp(-i Phi_i sigma_3 / 2): q0 = cos(Phi/2), q3 = -sin(Phi/2)
+        Phi = 2 * np.arctan2(-lat.u[:, 3, 0, 0, 0], lat.u[:, 0, 0, 0, 0])
+        Phi_exact = m.g * m.dx * np.array([0.3, -0.2, 0.5]) * (a_exact - a0) / (a0 ** (n - 1) * b0)
+        assert np.allclose(Phi, Phi_exact, rtol=1e-8, atol=0), (Phi, Phi_exact)
+    else:
+        th_exact = m.eA * m.dx * np.array([0.3, -0.2, 0.5]) * (a_exact - a0) / (a0 ** (n - 1) * b0)
+        assert np.allclose(lat.theta[:, 0, 0, 0], th_exact, rtol=1e-8, atol=0), (lat.theta[:, 0, 0, 0], th_exact)

@@ -354,3 +354,32 @@ def test_homogeneous_electric_field_expands_like_radiation(alpha):
     assert abs(lat.a / a_exact - 1) < 1e-8, (lat.a, a_exact)  # VV4 at dt = 0.02: ~1e-10
     assert abs(lat.a / a0 - 1) > 0.2  # a grows by a sizeable factor
     assert np.max(np.abs(lat.piA - piA)) < 1e-15
+    # theta_i' = e dx piA_i a^{alpha-1} (section 5.3): with a^n linear in t (n = 2 - alpha),
+    # theta_i(t) - theta_i(0) = e dx piA_i (a - a0) / (a0^{n-1} b0)
+    n_ = 2.0 - alpha
+    th_exact = m.e * m.dx * piA[:, 0, 0, 0] * (a_exact - a0) / (a0 ** (n_ - 1) * b0)
+    assert np.allclose(lat.theta[:, 0, 0, 0], th_exact, rtol=1e-8, atol=0), (lat.theta[:, 0, 0, 0], th_exact)
+    assert np.ptp(lat.theta, axis=(1, 2, 3)).max() < 1e-14
+
+
+def test_homogeneous_electric_field_leapfrog_converges_at_second_order():
+    """The staggered leapfrog of section 5.3.1, started by its backward half
+    kick, on the same radiation-dominated expansion (alpha = 0): a and the link
+    angles at the integer steps approach the closed form as dt^2."""
+    N = 4
+    m = U1Model(N=N, dx=0.7, alpha=0.0, fmp2=3.0, lam=1.0, e=0.5, kappa=1.0, pot=1, p=4)
+    piA = np.stack([np.full((N, N, N), c) for c in (0.3, -0.2, 0.5)])
+    z = np.zeros((2, N, N, N))
+    T, errs = 2.0, []
+    for dt in (0.04, 0.02):
+        lat = U1Lattice(m, z, z, np.zeros((3, N, N, N)), piA, a=1.3)
+        a0 = lat.a
+        b0 = np.sqrt(m.fmp2 / 3.0 * a0 ** 2 * lat.energies().sum())
+        lat.b = b0
+        lat.lf_prepare(dt)
+        lat.lf_steps(dt, int(round(T / dt)))
+        a_exact = np.sqrt(a0 * a0 + 2 * a0 * b0 * T)
+        th_exact = m.e * m.dx * piA[:, 0, 0, 0] * (a_exact - a0) / (a0 * b0)
+        errs.append(max(abs(lat.a / a_exact - 1), np.max(np.abs(lat.theta[:, 0, 0, 0] / th_exact - 1))))
+    assert errs[1] < 1e-4, errs
+    assert abs(np.log2(errs[0] / errs[1]) - 2) < 0.2, errs
