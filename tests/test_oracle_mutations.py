@@ -256,6 +256,51 @@ CASES = [
     ("gauge-monomial-derivative", "lattice_oracle.c",
      "*dv = lam * pow(s, 0.5 * p - 1.0);",
      "*dv = 0.5 * lam * pow(s, 0.5 * p - 1.0);", ["test_oracle_u1.py", "test_oracle_su2.py"]),
+    ("su2u1-vv-closing-b-half-kick", "lattice_oracle.c",
+     "        *b += 0.5 * h * orc_su2u1_Ka(m, *a, E);\n    }",
+     "        *b += h * orc_su2u1_Ka(m, *a, E);\n    }", ["test_oracle_su2u1.py"]),
+    ("su2u1-vv-chi-drift-power", "lattice_oracle.c",
+     "for (int64_t n = 0; n < V; ++n) chi[n] += cphi * pchi[n];",
+     "for (int64_t n = 0; n < V; ++n) chi[n] += h * pchi[n];", ["test_oracle_su2u1.py"]),
+    ("su2u1-vv-u1-link-drift-power", "lattice_oracle.c",
+     "const double cth = m->eA * m->dx * h * pow(ah, -(1.0 - m->alpha));",
+     "const double cth = m->eA * m->dx * h * pow(ah, -(3.0 - m->alpha));", ["test_oracle_su2u1.py"]),
+    ("su2-vv-link-drift-coupling", "lattice_oracle.c",
+     "su2_drift(m, phi, pi, u, piB, h * pow(ah, -(3.0 - m->alpha)), m->g * m->dx * h * pow(ah, -(1.0 - m->alpha)));",
+     "su2_drift(m, phi, pi, u, piB, h * pow(ah, -(3.0 - m->alpha)), m->dx * h * pow(ah, -(1.0 - m->alpha)));", ["test_oracle_su2.py"]),
+    ("u1-lf-prepare-electric-kinetic-power", "lattice_oracle.c",
+     "*EKm_A = m->kappa * sa / V / (2.0 * pow(ahm, 4.0));",
+     "*EKm_A = m->kappa * sa / V / (2.0 * pow(ahm, 6.0));", ["test_oracle_u1.py"]),
+    ("u1-lf-prepare-b-half-kick", "lattice_oracle.c",
+     "    *b -= 0.5 * dt * orc_u1_Ka(m, a, E);",
+     "    *b -= dt * orc_u1_Ka(m, a, E);", ["test_oracle_u1.py"]),
+    ("rk4-scale-factor-stage", "lattice_oracle.c",
+     "const double an = *a + c[p] * dt * bp, bn = *b + c[p] * dt * ka;",
+     "const double an = *a + c[p] * dt * *b, bn = *b + c[p] * dt * ka;", ["test_oracle_scalar.py"]),
+    ("rk4-kinetic-energy-power", "lattice_oracle.c",
+     "const double EK = sk / V / (2.0 * pow(a, 2.0 * m->alpha))",
+     "const double EK = sk / V / (2.0 * pow(a, 2.0 * m->alpha + 2.0))", ["test_oracle_scalar.py"]),
+    ("gl-scale-factor-weights", "lattice_oracle.c",
+     "        da += dt * c[mm] * Daold[mm];",
+     "        da += dt * c[0] * Daold[mm];", ["test_oracle_scalar.py"]),
+    ("gl-drift-power", "lattice_oracle.c",
+     "const double cdr = pow(al, -(3.0 - m->alpha));",
+     "const double cdr = pow(al, -(2.0 - m->alpha));", ["test_oracle_scalar.py"]),
+    ("fluid-scale-factor-power", "lattice_oracle.c",
+     "static double fluid_a(const orc_fluid* f, double t) { return f->a0 * pow(1.0 + f->H0 * t / f->p, f->p); }",
+     "static double fluid_a(const orc_fluid* f, double t) { return f->a0 * pow(1.0 + f->H0 * t, f->p); }", ["test_oracle_scalar.py"]),
+    ("vv-scalar-first-half-kick", "lattice_oracle.c",
+     "        kick(m, phi, pi, *a, 0.5 * h, K);\n        const double ah = *a + 0.5 * h * bh;",
+     "        kick(m, phi, pi, *a, h, K);\n        const double ah = *a + 0.5 * h * bh;", ["test_oracle_scalar.py"]),
+    ("u1-noncompact-magnetic-energy", "lattice_oracle.c",
+     "return m->noncompact ? 0.5 * t * t : 1.0 - cos(t); }",
+     "return m->noncompact ? t * t : 1.0 - cos(t); }", ["test_oracle_u1.py"]),
+    ("su2-plaquette-order", "lattice_oracle.c",
+     "    qmul(Ui, Uj_i, t1);\n    qmul(t1, c1, t2);\n    qmul(t2, c2, P);",
+     "    qmul(Uj_i, Ui, t1);\n    qmul(t1, c1, t2);\n    qmul(t2, c2, P);", ["test_oracle_su2.py"]),
+    ("su2-staple-conjugation", "lattice_oracle.c",
+     "                        qmul(Ujc, P2, s1);\n                        qmul(s1, Uj, Q);\n                        for (int c = 0; c < 3; ++c) mag[c] += P1[c + 1] - Q[c + 1];\n                    }\n                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];\n                }\n                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];\n                double dv;\n                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);\n                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;",
+     "                        qmul(Uj, P2, s1);\n                        qmul(s1, Ujc, Q);\n                        for (int c = 0; c < 3; ++c) mag[c] += P1[c + 1] - Q[c + 1];\n                    }\n                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];\n                }\n                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];\n                double dv;\n                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);\n                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;", ["test_oracle_su2.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
