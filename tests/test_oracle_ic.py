@@ -3,8 +3,8 @@
 import numpy as np
 import pytest
 
-from oracle import ScalarLattice, ScalarModel, U1Lattice, U1Model, philox
-from oracle.ic import mode_map, scalar_ic, u1_ic
+from oracle import ScalarLattice, ScalarModel, SU2Model, U1Lattice, U1Model, philox
+from oracle.ic import mode_map, scalar_ic, su2_ic, u1_ic
 from oracle.spectra import dft_forward, shell_bins, spectrum
 
 
@@ -177,6 +177,54 @@ def test_u1_ic_has_zero_charge_and_satisfies_gauss():
     # both components fluctuate with the same statistics
     assert 0.5 < phi[0].var() / phi[1].var() < 2.0
 
+
+
+def _higgs_curvature(stored, c, lam, v2, h=1e-3):
+    """d^2V/dchi_c^2 of V = (lam/4)(|Phi|^2 - v2)^2 along the canonical component
+    chi_c = sqrt(2) Phi_c (|Phi|^2 = sum of the stored components squared), by
+    central differences of the potential itself."""
+    def V(chi):
+        f = np.array(stored, dtype=float)
+        f[c] = chi / np.sqrt(2.0)
+        return 0.25 * lam * (np.sum(f * f) - v2) ** 2
+    x0 = np.sqrt(2.0) * stored[c]
+    return (V(x0 + h) - 2 * V(x0) + V(x0 - h)) / (h * h)
+
+
+@pytest.mark.parametrize("sector", ["u1", "su2"])
+def test_charged_draws_follow_the_canonical_curvature(sector):
+    """Charged scalars (sections 5, 6, 7.2) are stored as components Phi_c with
+    |Phi|^2 = sum_c Phi_c^2 and canonical fields chi_c = sqrt(2) Phi_c.  Each
+    canonical component fluctuates like a real scalar (section 7.1) whose mass is
+    the potential's curvature along it, so the stored component's per-mode
+    variance is (w*/f*)^2 (N/dx)^3 / (4 a^2 w_k) with w_k^2 = k^2 + a^2 V''(chi_c),
+    V'' taken here by finite differences of the Higgs potential.  The U(1)
+    homogeneous value is given canonically, so its stored mean is phibar/sqrt(2).
+    Held to four standard errors over the ~2000 independent modes of 16^3 (the
+    U(1) draw's equal moduli double the per-mode variance of |dphi|^2)."""
+    N, kIR, lam, v2 = 16, 0.1, 1.0, 1.0
+    dx = 2 * np.pi / (kIR * N)
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    sel = ~selfc & ~zero
+    M = sel.sum() / 2
+    if sector == "u1":
+        m = U1Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=lam, v2=v2, e=1.0, kappa=1.0, pot=0)
+        pb = [1.6, 0.4]
+        phi = u1_ic(m, kIR, pb, [0.0, 0.0], seed=31, omega_over_fstar=0.1)[0]
+        stored_mean = [x / np.sqrt(2.0) for x in pb]
+        sigma = np.sqrt(2.0)
+    else:
+        m = SU2Model(N=N, dx=dx, alpha=0.0, fmp2=0.0, lam=lam, v2=v2, g=1.0, kappa=1.0, pot=0)
+        stored_mean = [1.1, 0.0, 0.3, 0.0]
+        phi = su2_ic(m, kIR, stored_mean, [0.0] * 4, seed=31, omega_over_fstar=0.1)[0]
+        sigma = 1.0
+    assert np.allclose([p.mean() for p in phi], stored_mean, rtol=0, atol=1e-13)
+    for c in range(len(stored_mean)):
+        m2 = _higgs_curvature(stored_mean, c, lam, v2)
+        w = np.sqrt((kIR * nabs) ** 2 + abs(m2))
+        T = 0.1 ** 2 * (N / dx) ** 3 / (4 * w)
+        r = np.mean(np.abs(dft_forward(phi[c] - phi[c].mean()))[sel] ** 2 / T[sel])
+        assert abs(r - 1) < 4 * sigma / np.sqrt(M), (c, m2, r)
 
 @pytest.mark.parametrize("N", [4, 8])
 def test_isqrt_bins_are_exact(N):
