@@ -301,6 +301,57 @@ CASES = [
     ("su2-staple-conjugation", "lattice_oracle.c",
      "                        qmul(Ujc, P2, s1);\n                        qmul(s1, Uj, Q);\n                        for (int c = 0; c < 3; ++c) mag[c] += P1[c + 1] - Q[c + 1];\n                    }\n                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];\n                }\n                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];\n                double dv;\n                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);\n                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;",
      "                        qmul(Uj, P2, s1);\n                        qmul(s1, Ujc, Q);\n                        for (int c = 0; c < 3; ++c) mag[c] += P1[c + 1] - Q[c + 1];\n                    }\n                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];\n                }\n                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];\n                double dv;\n                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);\n                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;", ["test_oracle_su2.py"]),
+    ("u1-kernel-magnetic-a-power", "lattice_oracle.c",
+     "a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;",
+     "a1 * (2.0 * m->e / dx) / m->kappa * cur + a1 / (m->e * dx * dx * dx) * mag;", ["test_oracle_u1.py"]),
+    ("u1-kernel-current-a-power", "lattice_oracle.c",
+     "a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;",
+     "am * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;", ["test_oracle_u1.py"]),
+    ("u1-kernel-magnetic-coupling", "lattice_oracle.c",
+     "a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * dx * dx * dx) * mag;",
+     "a1 * (2.0 * m->e / dx) / m->kappa * cur + am / (m->e * m->e * dx * dx * dx) * mag;", ["test_oracle_u1.py"]),
+    ("u1-vv-closing-b-half-kick", "lattice_oracle.c",
+     "        orc_u1_energies(m, phi, pi, th, piA, *a, E);\n        *b = bh + 0.5 * h * orc_u1_Ka(m, *a, E);",
+     "        *b = bh + 0.5 * h * orc_u1_Ka(m, *a, E);\n        orc_u1_energies(m, phi, pi, th, piA, *a, E);", ["test_oracle_u1.py"]),
+    ("u1-vv-link-drift-a-power", "lattice_oracle.c",
+     "const double cth = m->e * m->dx * h * pow(ah, -(1.0 - m->alpha));",
+     "const double cth = m->e * m->dx * h * pow(ah, -(3.0 - m->alpha));", ["test_oracle_u1.py"]),
+    ("su2-kernel-magnetic-a-power", "lattice_oracle.c",
+     "                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + Am * cM * mag[c];\n                }\n                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];\n                double dv;\n                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);\n                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;",
+     "                    for (int c = 0; c < 3; ++c) KB[((int64_t)i * 3 + c) * V + n] = A1 * cJ * js[c] + A1 * cM * mag[c];\n                }\n                const double mod2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + f[3] * f[3];\n                double dv;\n                gauge_potential(m->pot, m->p, m->lam, m->v2, mod2, &dv);\n                for (int c = 0; c < 4; ++c) Kp[(int64_t)c * V + n] = -A3 * dv * f[c] + A1 * lap[c] * idx2;", ["test_oracle_su2.py"]),
+    ("su2u1-KA-magnetic-coupling", "lattice_oracle.c",
+     "Am / (m->eA * m->dx * m->dx * m->dx) * magA;",
+     "Am / (m->eA * m->eA * m->dx * m->dx * m->dx) * magA;", ["test_oracle_su2u1.py"]),
+    ("su2u1-backward-hop-phase", "lattice_oracle.c",
+     "whop(qmc, -tm, fm, tb);",
+     "whop(qmc, tm, fm, tb);", ["test_oracle_su2u1.py"]),
+    ("su2u1-u1-magnetic-energy-coupling", "lattice_oracle.c",
+     "out[6] = u1 ? m->kappa * sga / V / (a4 * dx4 * m->eA * m->eA) : 0.0;",
+     "out[6] = u1 ? m->kappa * sga / V / (a4 * dx4 * m->eA) : 0.0;", ["test_oracle_su2u1.py"]),
+    ("rk4-potential-a-power", "lattice_oracle.c",
+     "c3 = pow(a, 2.0 * m->alpha);",
+     "c3 = pow(a, 2.0 + 2.0 * m->alpha);", ["test_oracle_scalar.py"]),
+    ("rk4-gradient-a-power", "lattice_oracle.c",
+     "const double c1 = pow(a, -2.0 * (1.0 - m->alpha))",
+     "const double c1 = pow(a, -(1.0 - m->alpha))", ["test_oracle_scalar.py"]),
+    ("fluid-closing-kick-a", "lattice_oracle.c",
+     "        kick(m, phi, pi, an, 0.5 * h, K);\n        *t += h;",
+     "        kick(m, phi, pi, a, 0.5 * h, K);\n        *t += h;", ["test_oracle_scalar.py"]),
+    ("u1-ic-canonical-normalisation", "ic.py",
+     "    phi = np.stack([comps[0], comps[1]]) / np.sqrt(2.0)",
+     "    phi = np.stack([comps[0], comps[1]])", ["test_oracle_ic.py", "test_oracle_u1.py"]),
+    ("su2-ic-curvature-canonical-factor", "ic.py",
+     "    m2 = [dv + d2 * 2.0 * pb[c] ** 2 for c in range(4)]  # canonical component sqrt(2) Phi_c",
+     "    m2 = [dv + d2 * pb[c] ** 2 for c in range(4)]  # canonical component sqrt(2) Phi_c", ["test_oracle_ic.py", "test_oracle_su2.py"]),
+    ("dft-normalisation", "spectra.py",
+     "return np.fft.ifftn(f) * f.size",
+     "return np.fft.ifftn(f)", ["test_oracle_ic.py", "test_oracle_observe.py", "test_oracle_scalar.py"]),
+    ("observe-spectrum-of-phi", "observe.py",
+     "k, D, _ = spectrum(lattice.phi[1], m.dx, kIR)",
+     "k, D, _ = spectrum(lattice.phi[0], m.dx, kIR)", ["test_oracle_observe.py"]),
+    ("lf3-b-uses-average-kinetic", "lattice_oracle.c",
+     "        const double EKbar = 0.5 * (EKm + EKp);",
+     "        const double EKbar = EKp;", ["test_oracle_scalar.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
