@@ -334,3 +334,23 @@ def test_homogeneous_fields_give_the_closed_form_expansion(sector, alpha):
     else:
         th_exact = m.eA * m.dx * np.array([0.3, -0.2, 0.5]) * (a_exact - a0) / (a0 ** (n - 1) * b0)
         assert np.allclose(lat.theta[:, 0, 0, 0], th_exact, rtol=1e-8, atol=0), (lat.theta[:, 0, 0, 0], th_exact)
+
+@pytest.mark.parametrize("a,alpha", [(1.0, 0.0), (1.4, 0.5), (0.8, 1.0)])
+def test_electric_fields_carry_the_electric_energies(a, alpha):
+    """E = pi_gauge/a^{1-alpha} for both gauge sectors (sections 5.4, 6.3):
+    sum_i <|E_i|^2> = 2 a^{2+2 alpha} E_K/kappa exactly, for the U(1) field
+    (E_K^A) and for the SU(2) field summed over colours (E_K^B); the same holds
+    for the SU(2)-only model."""
+    N = 6
+    m = SU2U1Model(N=N, dx=0.6, alpha=alpha, fmp2=0.0, lam=1.0, v2=1.0, g=0.9, kappa=1.3, pot=0, eA=0.7, q=1.2,
+                   chi=1)
+    lat = random_state(N, m, 47, a=a)
+    E = lat.energies()
+    EA2 = (lat.electric(0) ** 2).sum(axis=0).mean()
+    EB2 = (lat.electric(1) ** 2).sum(axis=(0, 1)).mean()
+    assert EA2 == pytest.approx(2 * a ** (2 + 2 * alpha) * E[5] / m.kappa, rel=1e-13)
+    assert EB2 == pytest.approx(2 * a ** (2 + 2 * alpha) * E[3] / m.kappa, rel=1e-13)
+    s2 = SU2Lattice(m.su2(), lat.phi, lat.pi, lat.u, lat.piB, a=a)
+    E2 = s2.energies()
+    assert (s2.electric() ** 2).sum(axis=(0, 1)).mean() == pytest.approx(2 * a ** (2 + 2 * alpha) * E2[3] / m.kappa,
+                                                                          rel=1e-13)
