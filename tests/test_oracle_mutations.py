@@ -352,6 +352,30 @@ CASES = [
     ("lf3-b-uses-average-kinetic", "lattice_oracle.c",
      "        const double EKbar = 0.5 * (EKm + EKp);",
      "        const double EKbar = EKp;", ["test_oracle_scalar.py"]),
+    ("u1-electric-field-a-power", "core.py",
+     "        return self.piA / self.a ** (1.0 - self.m.alpha)",
+     "        return self.piA / self.a ** (3.0 - self.m.alpha)", ["test_oracle_u1.py"]),
+    ("su2u1-electric-field-a-power", "core.py",
+     "return (self.piA if sector == 0 else self.piB) / self.a ** (1.0 - self.m.alpha)",
+     "return (self.piA if sector == 0 else self.piB) / self.a ** (2.0 - self.m.alpha)", ["test_oracle_su2u1.py"]),
+    ("u1-magnetic-field-scale", "core.py",
+     "out[i] = (t if noncompact else np.sin(t)) / (e * dx * dx)",
+     "out[i] = (t if noncompact else np.sin(t)) / (e * dx)", ["test_oracle_u1.py", "test_oracle_su2u1.py"]),
+    ("su2-electric-field-a-power", "core.py",
+     "        return self.piB / self.a ** (1.0 - self.m.alpha)",
+     "        return self.piB / self.a ** (2.0 - self.m.alpha)", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("su2-magnetic-field-scale", "core.py",
+     "out[i] = -2.0 * P[1:] / (g * dx * dx)",
+     "out[i] = -1.0 * P[1:] / (g * dx * dx)", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("philox-rounds", "philox.py",
+     "    for r in range(10):",
+     "    for r in range(9):", ["test_oracle_ic.py"]),
+    ("gl-convergence-test", "lattice_oracle.c",
+     "if (dd <= tol * tol * nn) break;",
+     "if (dd <= tol * nn) break;", ["test_oracle_scalar.py"]),
+    ("lf3-b-kernel-at-half-step", "lattice_oracle.c",
+     "        const double bn = bm + dt * Ka_scalar(m, a, EKbar, EG, EV);",
+     "        const double bn = bm + dt * Ka_scalar(m, ah, EKbar, EG, EV);", ["test_oracle_scalar.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
