@@ -376,6 +376,27 @@ CASES = [
     ("lf3-b-kernel-at-half-step", "lattice_oracle.c",
      "        const double bn = bm + dt * Ka_scalar(m, a, EKbar, EG, EV);",
      "        const double bn = bm + dt * Ka_scalar(m, ah, EKbar, EG, EV);", ["test_oracle_scalar.py"]),
+    ("u1-gradient-energy-half", "lattice_oracle.c",
+     "    out[1] = sg / V / a2;\n    out[2] = sv / V;\n    out[3] = m->kappa * ska",
+     "    out[1] = sg / V / (2.0 * a2);\n    out[2] = sv / V;\n    out[3] = m->kappa * ska", ["test_oracle_u1.py"]),
+    ("su2-gradient-energy-half", "lattice_oracle.c",
+     "    out[1] = sg / V / (m->dx * m->dx) / a2;",
+     "    out[1] = sg / V / (m->dx * m->dx) / (2.0 * a2);", ["test_oracle_su2.py"]),
+    ("su2u1-gradient-energy-half", "lattice_oracle.c",
+     "    out[1] = sg / V / dx2 / a2;",
+     "    out[1] = sg / V / dx2 / (2.0 * a2);", ["test_oracle_su2u1.py"]),
+    ("su2-gauss-charge-factor", "lattice_oracle.c",
+     "const double r = m->g / m->kappa * rho[c];",
+     "const double r = 2.0 * m->g / m->kappa * rho[c];", ["test_oracle_su2.py", "test_oracle_ic.py"]),
+    ("su2-kinetic-energy-half", "lattice_oracle.c",
+     "    out[0] = sk / V / a6;\n    out[1] = sg / V / (m->dx * m->dx) / a2;",
+     "    out[0] = sk / V / (2.0 * a6);\n    out[1] = sg / V / (m->dx * m->dx) / a2;", ["test_oracle_su2.py"]),
+    ("su2u1-interaction-energy-factor", "lattice_oracle.c",
+     "sv += m->q * mod2 * chi[n] * chi[n];",
+     "sv += 0.5 * m->q * mod2 * chi[n] * chi[n];", ["test_oracle_su2u1.py"]),
+    ("u1-higgs-potential-factor", "lattice_oracle.c",
+     "return 0.25 * lam * (mod2 - v2) * (mod2 - v2);",
+     "return 0.5 * lam * (mod2 - v2) * (mod2 - v2);", ["test_oracle_u1.py", "test_oracle_su2.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
