@@ -3,7 +3,7 @@
 import numpy as np
 import pytest
 
-from oracle import ScalarLattice, ScalarModel, SU2Model, U1Lattice, U1Model, philox
+from oracle import ScalarLattice, ScalarModel, SU2Lattice, SU2Model, U1Lattice, U1Model, philox
 from oracle.ic import mode_map, scalar_ic, su2_ic, u1_ic
 from oracle.spectra import dft_forward, shell_bins, spectrum
 
@@ -225,6 +225,86 @@ def test_charged_draws_follow_the_canonical_curvature(sector):
         T = 0.1 ** 2 * (N / dx) ** 3 / (4 * w)
         r = np.mean(np.abs(dft_forward(phi[c] - phi[c].mean()))[sel] ** 2 / T[sel])
         assert abs(r - 1) < 4 * sigma / np.sqrt(M), (c, m2, r)
+
+
+@pytest.mark.parametrize("sector", ["u1", "su2"])
+def test_charged_draws_carry_the_hubble_term(sector):
+    """dphi' = -H dphi + (a part uncorrelated with dphi) for every stored component
+    of a charged scalar (section 7.1, with the charged fields of sections 7.2 and
+    6), H the program Hubble rate of the homogeneous state: H = b/a with b^2 =
+    (f*/m_p)^2 a^{2(alpha+1)} (sum of the lattice energies of that state) / 3
+    (section 4.1), the energies taken by the sector's energy functional.  The
+    homogeneous velocity carries most of the energy, so its kinetic term decides H."""
+    N, kIR, a, alpha, fmp2 = 16, 0.1, 1.5, 0.5, 6.0
+    dx = 2 * np.pi / (kIR * N)
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    sel = ~selfc & ~zero
+    M = sel.sum() / 2
+    if sector == "u1":
+        m = U1Model(N=N, dx=dx, alpha=alpha, fmp2=fmp2, lam=1.0, v2=1.0, e=1.0, kappa=1.0, pot=0)
+        pb, db = [1.2, 0.3], [1.5, -0.8]
+        draw = lambda seed, fs: u1_ic(m, kIR, pb, db, seed=seed, omega_over_fstar=0.1, a=a, fluct_scale=fs)
+        hom = draw(0, 0.0)
+        E = U1Lattice(m, hom[0], hom[1], hom[2], hom[3], a=a).energies()
+        mean_phi, mean_dphi = [x / np.sqrt(2.0) for x in pb], [x / np.sqrt(2.0) for x in db]
+    else:
+        m = SU2Model(N=N, dx=dx, alpha=alpha, fmp2=fmp2, lam=1.0, v2=1.0, g=1.0, kappa=1.0, pot=0)
+        pb = [0.9, 0.0, 0.2, 0.0]
+        db = [1.2 * x for x in pb]  # parallel to Phi: no homogeneous charge
+        draw = lambda seed, fs: su2_ic(m, kIR, pb, db, seed=seed, omega_over_fstar=0.1, a=a, fluct_scale=fs)
+        hom = draw(0, 0.0)
+        E = SU2Lattice(m, hom[0], hom[1], hom[2], hom[3], a=a).energies()
+        mean_phi, mean_dphi = pb, db
+    H = np.sqrt(fmp2 / 3.0 * a ** (2 * (alpha + 1)) * E.sum()) / a
+    assert H > 1.5
+    phi, pi = draw(7, 1.0)[:2]
+    num = den = 0.0
+    for c in range(len(pb)):
+        F = dft_forward(phi[c] - mean_phi[c])
+        Fd = dft_forward(pi[c] / a ** (3.0 - alpha) - mean_dphi[c])
+        num += np.sum((np.conj(F) * Fd).real[sel])
+        den += np.sum(np.abs(F[sel]) ** 2)
+    w_max = np.sqrt((kIR * nabs.max()) ** 2 + 4.0)
+    se = a ** (alpha - 1) * w_max / np.sqrt(2 * M * len(pb))
+    assert abs(num / den + H) < 4 * se, (num / den, -H, se)
+
+
+def test_scalar_draw_follows_the_potential_curvature():
+    """Each scalar fluctuates with the curvature of V = (lam/p)|phi|^p + (q/2) phi^2 chi^2
+    (section 8.1) along itself at the homogeneous values (section 7.1), here with
+    both homogeneous values non-zero so that the interaction enters both
+    curvatures; V'' by finite differences of the potential."""
+    N, kIR, lam, q, p = 16, 0.1, 1.0, 3.0, 4
+    dx = 2 * np.pi / (kIR * N)
+    m = ScalarModel(N=N, Ns=2, pexp=p, dx=dx, alpha=0.0, fmp2=0.0, lam=lam, q=q)
+    pb = [0.5, 1.0]
+    phi = scalar_ic(m, kIR, pb, [0.0, 0.0], seed=17, omega_over_fstar=0.1)[0]
+    lin, conj, selfc, zero, nabs = mode_map(N)
+    sel = ~selfc & ~zero
+    M = sel.sum() / 2
+
+    def V(f0, f1):
+        return lam / p * abs(f0) ** p + 0.5 * q * f0 * f0 * f1 * f1
+
+    h = 1e-3
+    curv = [(V(pb[0] + h, pb[1]) - 2 * V(*pb) + V(pb[0] - h, pb[1])) / h ** 2,
+            (V(pb[0], pb[1] + h) - 2 * V(*pb) + V(pb[0], pb[1] - h)) / h ** 2]
+    for i in range(2):
+        w = np.sqrt((kIR * nabs) ** 2 + curv[i])
+        T = 0.1 ** 2 * (N / dx) ** 3 / (2 * w)
+        r = np.mean(np.abs(dft_forward(phi[i] - pb[i]))[sel] ** 2 / T[sel])
+        assert abs(r - 1) < 4 / np.sqrt(M), (i, curv[i], r)
+
+
+@pytest.mark.parametrize("N", [6, 12, 16])
+def test_shell_count_is_the_number_of_shells(N):
+    """|n~| runs up to sqrt(3) N/2 (the corner mode), so there are
+    floor(sqrt(3) N/2) + 1 shells [b, b+1), every one of them occupied, and the
+    spectrum reports each."""
+    b, nabs, nb = shell_bins(N)
+    assert nb == int(np.floor(np.sqrt(3) * N / 2 + 1e-12)) + 1
+    k, D, cnt = spectrum(np.random.default_rng(N).standard_normal((N, N, N)), 1.0, 1.0)
+    assert len(cnt) == nb and np.all(cnt > 0) and cnt.sum() == N ** 3
 
 @pytest.mark.parametrize("N", [4, 8])
 def test_isqrt_bins_are_exact(N):

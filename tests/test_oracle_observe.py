@@ -102,3 +102,24 @@ def test_zero_mode_and_empty_shells_are_skipped():
     kj = _kj(0.1, 0.3)
     ref = -4.0 + (np.log(kj) - math.log(0.1)) / math.log(3.0) * 2.0
     assert np.allclose(v, ref, rtol=0, atol=1e-12)
+
+
+def test_default_upper_momentum_is_the_axis_nyquist_momentum():
+    """Without kmax the 32 momenta end at the lattice's Nyquist momentum along an
+    axis, pi/dx (beyond it the shells are incomplete corners of the cube): the
+    default equals an explicit kmax = pi/dx, and with the equal-power k^3
+    spectrum the last sample sits at that momentum's line value."""
+    N, dx, c = 8, 0.6, 3.0
+    kIR = 2 * np.pi / (N * dx)
+    G = dft_forward(np.random.default_rng(5).standard_normal((N, N, N)))
+    F = c * G / np.abs(G)
+    F[0, 0, 0] = 0.0
+    chi = dft_inverse(F).real
+    phi = np.stack([np.full((N, N, N), 1.0), chi])
+    lat = ScalarLattice(_model(N, dx), phi, np.zeros_like(phi))
+    o_default = observables(lat, kIR)
+    o_nyquist = observables(lat, kIR, math.pi / dx)
+    assert np.allclose(o_default, o_nyquist, rtol=0, atol=1e-12)  # pi/dx = N k_IR/2 up to rounding
+    norm = (dx / N) ** 3 / (2 * np.pi ** 2)
+    k_last = _kj(kIR, math.pi / dx)[-1]
+    assert abs(o_default[-1] - (math.log10(norm * c * c) + 3 * math.log10(k_last))) < 1e-12
