@@ -397,6 +397,24 @@ CASES = [
     ("u1-higgs-potential-factor", "lattice_oracle.c",
      "return 0.25 * lam * (mod2 - v2) * (mod2 - v2);",
      "return 0.5 * lam * (mod2 - v2) * (mod2 - v2);", ["test_oracle_u1.py", "test_oracle_su2.py"]),
+    ("su2u1-ic-singlet-curvature", "ic.py",
+     "chi, dchi = _singlet_draw(N, alpha, kIR, 2.0 * model.q * s2,",
+     "chi, dchi = _singlet_draw(N, alpha, kIR, model.q * s2,", ["test_oracle_su2u1.py", "test_oracle_ic.py"]),
+    ("u1-ic-homogeneous-kinetic-energy", "ic.py",
+     "    EK0 = 0.5 * (db[0] ** 2 + db[1] ** 2) / a ** (2 * alpha)",
+     "    EK0 = (db[0] ** 2 + db[1] ** 2) / a ** (2 * alpha)", ["test_oracle_ic.py", "test_oracle_u1.py"]),
+    ("su2-ic-homogeneous-kinetic-energy", "ic.py",
+     "    EK0 = sum(d * d for d in db) / a ** (2 * alpha)\n    H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))\n    lin, conj, selfc, zero, nabs = mode_map(N)\n    k = kIR * nabs\n    phi = np.zeros((4, N, N, N))",
+     "    EK0 = 0.5 * sum(d * d for d in db) / a ** (2 * alpha)\n    H = np.sqrt(max(a ** (2 * alpha) / 3.0 * model.fmp2 * (EK0 + Vbar), 0.0))\n    lin, conj, selfc, zero, nabs = mode_map(N)\n    k = kIR * nabs\n    phi = np.zeros((4, N, N, N))", ["test_oracle_ic.py", "test_oracle_su2.py"]),
+    ("scalar-curvature-interaction-term", "core.py",
+     "(m.q * f1 * f1 if m.Ns > 1 else 0.0)]",
+     "(2.0 * m.q * f1 * f1 if m.Ns > 1 else 0.0)]", ["test_oracle_ic.py", "test_oracle_scalar.py"]),
+    ("spectrum-drops-last-shell", "spectra.py",
+     "return b, np.sqrt(n2.astype(np.float64)), int(b.max()) + 1",
+     "return b, np.sqrt(n2.astype(np.float64)), int(b.max())", ["test_oracle_ic.py", "test_oracle_observe.py"]),
+    ("observe-default-kmax", "observe.py",
+     "        kmax = 0.5 * m.N * kIR",
+     "        kmax = m.N * kIR", ["test_oracle_observe.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
