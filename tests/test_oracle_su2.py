@@ -271,6 +271,20 @@ def test_su2_magnetic_field_of_an_abelian_configuration():
     small = SU2Lattice(m, np.zeros((4, N, N, N)), np.zeros((4, N, N, N)), u, np.zeros((3, 3, N, N, N)))
     B2 = (small.magnetic() ** 2).sum(axis=(0, 1)).mean()
     assert B2 == pytest.approx(2 * small.energies()[4] / m.kappa, rel=1e-3)
+    # non-commuting small links (every colour): to first order in the angles
+    # theta_i^a = -2 q_i^a = g dx A_i^a, B_i^a is the lattice curl of each colour's
+    # angles over g dx^2 (written out here with rolls); the O(theta^2) rest is ~1%
+    u = np.stack([random_quaternions((N, N, N), 71 + i, 0.01) for i in range(3)])
+    mixed = SU2Lattice(m, np.zeros((4, N, N, N)), np.zeros((4, N, N, N)), u, np.zeros((3, 3, N, N, N)))
+    B = mixed.magnetic()
+    fwd = lambda f, d: np.roll(f, -1, axis=2 - d)  # f(n + d^), arrays indexed [z, y, x]
+    for a in range(3):
+        th = -2.0 * u[:, a + 1]
+        for i in range(3):
+            j, k = (i + 1) % 3, (i + 2) % 3
+            curl = (th[j] + fwd(th[k], j) - fwd(th[j], k) - th[k]) / (g * dx * dx)
+            assert np.max(np.abs(B[i, a] - curl)) < 0.05 * np.max(np.abs(curl)), (i, a)
+    assert (B ** 2).sum(axis=(0, 1)).mean() == pytest.approx(2 * mixed.energies()[4] / m.kappa, rel=1e-3)
 
 
 @pytest.mark.parametrize("alpha", [0.0, 1.0])
