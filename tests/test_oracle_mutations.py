@@ -415,6 +415,24 @@ CASES = [
     ("observe-default-kmax", "observe.py",
      "        kmax = 0.5 * m.N * kIR",
      "        kmax = m.N * kIR", ["test_oracle_observe.py"]),
+    ("su2-drift-rotation-direction", "lattice_oracle.c",
+     "for (int c = 0; c < 3; ++c) ex[c + 1] = -s * e[c];",
+     "for (int c = 0; c < 3; ++c) ex[c + 1] = s * e[c];", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("su2-im-sigma1-swap", "lattice_oracle.c",
+     "z[0] = y[2]; z[1] = y[3]; z[2] = y[0]; z[3] = y[1];",
+     "z[0] = y[2]; z[1] = -y[3]; z[2] = y[0]; z[3] = -y[1];", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("su2-im-sigma3-sign", "lattice_oracle.c",
+     "z[0] = y[0]; z[1] = y[1]; z[2] = -y[2]; z[3] = -y[3];",
+     "z[0] = y[0]; z[1] = y[1]; z[2] = y[2]; z[3] = y[3];", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("su2-umul-diagonal-phase", "lattice_oracle.c",
+     "const double ar = q[0], ai = q[3], br = q[2]",
+     "const double ar = q[0], ai = -q[3], br = q[2]", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("su2-magnetic-plaquette-helper-conjugate", "core.py",
+     "conj = np.array([1.0, -1.0, -1.0, -1.0])[:, None, None, None]",
+     "conj = np.array([1.0, 1.0, -1.0, -1.0])[:, None, None, None]", ["test_oracle_su2.py", "test_oracle_su2u1.py"]),
+    ("su2-gauss-divergence-sign", "lattice_oracle.c",
+     "div[c] += (piB[((int64_t)i * 3 + c) * V + n] - tr[c + 1]) / m->dx;",
+     "div[c] += (piB[((int64_t)i * 3 + c) * V + n] + tr[c + 1]) / m->dx;", ["test_oracle_su2.py", "test_oracle_su2u1.py", "test_oracle_ic.py"]),
 ]
 
 PIN_FILES = sorted({p for case in CASES for p in case[4]})
