@@ -54,6 +54,29 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     assert capsys.readouterr().out == ""  # the non-zero rank exits without work or output
 
 
+
+def test_reference_arm_prints_the_contract_line_on_rank_zero(monkeypatch, capsys):
+    """Rank 0 times the oracle (a small lattice here) and prints one JSON line with
+    the reference arm's keys: impl, the metric of the ours arm, a cpu_baseline
+    describing the run and an e2e entry that moves no bytes."""
+    import json
+    import sys
+
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1", "--N", "16"])
+    bench.run_reference(bench.parse())
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "site-updates/s" and d["unit"] == "site-updates/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
 def _scan_rank_main(rank, world, port, n, out):
     import numpy as np
     import torch.distributed as dist
