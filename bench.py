@@ -140,27 +140,45 @@ class ClockSampler:
             self.p = None
 
     def stop(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
+        """Ends the sampling, removes the sample file and summarizes it (once)."""
+        if self.f.closed:
+            return self.result
+        text = None
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+            self.f.flush()
+            self.f.seek(0)
+            text = self.f.read()
+        self.f.close()
         try:
-            self.p.wait(5)
-        except Exception:
-            self.p.kill()
-        self.f.flush()
-        self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+            os.unlink(self.f.name)
+        except OSError:
+            pass
+        self.result = (self.summarize(text) if text is not None else
+                       {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+        return self.result
+
+    @staticmethod
+    def summarize(text):
+        """Median SM clock, the largest max clock and the throttle reasons seen
+        Active in rows of the query above (unparsable rows are skipped)."""
+        rows = [r.split(",") for r in text.strip().splitlines() if r.strip()]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-                for nm, v in zip(names, r[5:9]):
-                    if v.strip().lower() == "active":
-                        reasons.add(nm)
-            except Exception:
+                s_, m_ = float(r[1]), float(r[2])
+            except (IndexError, ValueError):
                 continue
+            sm.append(s_)
+            smax.append(m_)
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 

@@ -130,3 +130,37 @@ def test_partition_without_a_process_group_is_the_whole_scan():
         assert max(map(len, blocks)) - min(map(len, blocks)) <= 1
     a = np.zeros((5, 2))
     assert scan.gather_runs(a, 5) is not None
+
+
+def test_clock_samples_are_summarized_with_their_throttle_reasons():
+    """The nvidia-smi rows sampled during the timed region (index, clocks.sm,
+    clocks.max.sm, power, active mask, then hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap as Active / Not Active) reduce to the
+    median SM clock, the max clock and the reasons seen Active."""
+    import bench
+
+    text = ("0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+            "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+            "garbage line\n"
+            "0, 2055, 2070, 1200.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+    d = bench.ClockSampler.summarize(text)
+    assert d == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.ClockSampler.summarize("")["sm_mhz"] is None
+
+
+def test_clock_sampler_without_nvidia_smi_reports_unavailable_and_cleans_up(monkeypatch):
+    import os
+    import subprocess
+
+    import bench
+
+    def no_smi(*a, **k):
+        raise FileNotFoundError("nvidia-smi")
+
+    monkeypatch.setattr(subprocess, "Popen", no_smi)
+    c = bench.ClockSampler(0)
+    c.start()
+    d = c.stop()
+    assert d["sm_mhz"] is None and d["reasons"] == ["nvidia-smi unavailable"]
+    assert not os.path.exists(c.f.name)
+    assert c.stop() is d  # a second stop returns the same summary
