@@ -34,7 +34,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_time_by_the_slowest_and_count_every_replica():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of this multi-threaded process
     out = mgr.dict()
     mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
     assert sorted(out.keys()) == [0, 1]
@@ -106,7 +106,7 @@ def test_gloo_ranks_split_the_scan_and_gather_every_run_in_order(world, n):
     is empty (fewer runs than ranks)."""
     import numpy as np
 
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of this multi-threaded process
     out = mgr.dict()
     mp.start_processes(_scan_rank_main, args=(world, _free_port(), n, out), nprocs=world, join=True,
                        start_method="spawn")
